@@ -1,0 +1,315 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the refined VLBM on B300 (FP64).
+
+Workload: the isentropic-vortex configuration -- periodic [0,10]^2, vortex
+strength 5, free stream (1,1), gamma = 1.4, FP64 -- at the largest size of
+its convergence series: 512 x 512 coarse cells with a ratio-2 patch over the
+central 256 x 256 coarse cells (25 % of the area), time ratio 2.  One step is
+one coarse step of the whole hierarchy: the level-0 sweep, two level-1
+sweeps (fused collide + push-stream + mean-preserving coarse-to-fine
+reconstruction), the reflux close and the end-of-step bookkeeping.
+
+Metric: MLUPS (cell updates per second, counting every active cell of every
+level once per level step) and the fraction of the roofline of the dominant
+kernel (the level sweep), which on B300 is bounded by the FP64 pipe.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+With N > 1 (torchrun) every rank runs an independent replica (the workload
+does not shard; no collective is on the data path) and `value` is the
+whole-job aggregate.  `--impl reference` times the oracle (the plain FP64 CPU
+rendering of the method) on the host cores, on the same workload and metric.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2609_35529_b300 import inputs as I  # noqa: E402
+
+WORKLOAD = "isentropic vortex 512^2 coarse + central ratio-2 patch (2 levels), periodic, FP64"
+METRIC = "MLUPS (FP64, 1 B300)"
+# FP64 arithmetic of one cell update in the canonical collision (FMA = 2
+# flops, the one division = 1): 12 adds (moments), 1 division, 14 flux
+# operations of which one is fused (15 flops), 4 products (beta/2) W,
+# 32 fused multiply-adds (relaxation).
+FLOPS_PER_LUP = 12 + 1 + 15 + 4 + 64
+# algorithmic bytes of one cell update: 16 populations read + 16 written
+BYTES_PER_LUP = 256
+
+
+def peaks():
+    p = {"hbm_gbs": 6469.6, "sm_max_mhz": 2032.0, "source": "fallback"}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        p.update({k: m[k] for k in ("hbm_gbs", "sm_max_mhz") if k in m})
+        p["source"] = "measured"
+    except Exception:
+        pass
+    # FP64 pipe: 2 FP64 FMA per clock per SM (64 lanes / 32 clocks), 148 SMs
+    p["fp64_tflops"] = 2 * 2 * 148 * p["sm_max_mhz"] * 1e6 / 1e12
+    return p
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_rate(case, seconds):
+    """The oracle (plain FP64 CPU code, one thread) on `case`: coarse steps
+    until `seconds` of CPU time have passed.  Returns (MLUPS, steps, wall)."""
+    from oracle import oracle as O
+    o = O.Hierarchy(case.nx0, case.ny0, case.nlev, 2, case.bc, case.gamma, case.c, case.beta, case.inflow)
+    o.set_layout(case.refs if case.nlev > 1 else None)
+    for l in range(case.nlev):
+        o.set_state(l, case.W[l])
+    lups = case.lups_per_step()
+    n, t0 = 0, time.perf_counter()
+    while True:
+        o.advance(1)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return lups * n / el / 1e6, n, el
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args, budget_s=90.0):
+    """The oracle on the host cores.  Each timed step is one coarse step of
+    the workload; the run stops after `budget_s` seconds of timed steps (a
+    bounded sample of the K requested) so that it ends within minutes."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    case = I.vortex(N=512, steps=args.steps)
+    lups = case.lups_per_step()
+    from oracle import oracle as O
+    o = O.Hierarchy(case.nx0, case.ny0, case.nlev, 2, case.bc, case.gamma, case.c, case.beta)
+    o.set_layout(case.refs)
+    for l in range(case.nlev):
+        o.set_state(l, case.W[l])
+    for _ in range(min(args.warmup, 1)):
+        o.advance(1)
+    t0 = time.perf_counter()
+    done = 0
+    while done < args.steps:
+        o.advance(1)
+        done += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    el = time.perf_counter() - t0
+    v = lups * done / el / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / done * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lups_per_step": lups, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": round(v, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": f"{done} of {args.steps} coarse steps of the workload (time budget "
+                                       f"{budget_s:.0f} s), one thread"},
+            "e2e": {"value": round(v, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world, rank, local = dist_env()
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    dev = torch.cuda.current_device()
+    from paper_2609_35529_b300 import build, vlbm as V
+    build.build()
+
+    case = I.vortex(N=512, steps=args.steps)
+    stream = torch.cuda.Stream()
+    g = V.Hierarchy.from_case(case, stream=stream)
+    info = g.info()
+    lups = info["lups_per_step"]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    # warm-up (also builds and instantiates the CUDA graphs)
+    for _ in range(max(3, args.warmup)):
+        g.advance(1)
+    g.sync()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                flush.fill_(float(i))  # > L2 between timed iterations
+                ev[i][0].record(stream)
+                g.advance(1)
+                ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    g.sync()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if pg:
+        pg.barrier()
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * lups * args.steps / (ms * 1e-3) / 1e6
+
+    # per-kernel device times over the same number of steps (eager launches,
+    # CUDA events on the library's stream) for the roofline of the sweep
+    prof = g.profile(min(args.steps, 100))
+    sweep = [r for r in prof if r["kind"] == "sweep"]
+    sw_ms = sum(r["ms"] for r in sweep)
+    sw_launch = sum(r["launches"] for r in sweep)
+    sw_cells = sum(r["cells"] for r in sweep)
+    tot_ms = sum(r["ms"] for r in prof)
+    launches_per_step = sum(r["launches"] for r in prof) / min(args.steps, 100)
+    pk = peaks()
+    achieved_tflops = FLOPS_PER_LUP * sw_cells / (sw_ms * 1e-3) / 1e12
+    hbm_gbs = BYTES_PER_LUP * sw_cells / (sw_ms * 1e-3) / 1e9
+    roof = {"bound": "alu", "achieved": round(achieved_tflops, 4), "peak": round(pk["fp64_tflops"], 4),
+            "unit": "TFLOP/s", "frac": round(achieved_tflops / pk["fp64_tflops"], 4), "traffic": None,
+            "kernel": "sweep_kernel", "avg_launch_ms": round(sw_ms / sw_launch, 5),
+            "cells_per_launch": sw_cells // max(1, sw_launch), "share_of_step": round(sw_ms / tot_ms, 4),
+            "flops_per_lup": FLOPS_PER_LUP, "peak_basis": "2 FP64 FMA/clk/SM x 148 SMs x sm_max_mhz",
+            "hbm": {"achieved": round(hbm_gbs, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": round(hbm_gbs / pk["hbm_gbs"], 4), "peak_source": pk["source"]}}
+
+    # end to end through the public API with host buffers: initial state from
+    # pinned host memory, per-step conservation totals read back, final state
+    # read back
+    Wh = [torch.from_numpy(np.ascontiguousarray(w)).pin_memory().numpy() for w in case.W]
+    h2 = V.Hierarchy(case.nx0, case.ny0, case.nlev, case.bc, case.gamma, case.c, case.beta, dx0=case.dx0,
+                     stream=stream)
+    h2.regrid_masks(case.refs)
+    h2.set_state(0, Wh[0])
+    h2.set_state(1, Wh[1])
+    h2.advance(2)
+    h2.audit()
+    torch.cuda.synchronize()
+    n_e2e = min(args.steps, 1000)
+    t0 = time.perf_counter()
+    for l in range(case.nlev):
+        h2.set_state(l, Wh[l])
+    for _ in range(n_e2e):
+        h2.advance(1)
+        h2.audit()
+    for l in range(case.nlev):
+        h2.get_conserved(l)
+    e2e_s = time.perf_counter() - t0
+    if pg:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    wbytes = sum(w.nbytes for w in case.W)
+    e2e = {"value": round(world * lups * n_e2e / e2e_s / 1e6, 3), "unit": "MLUPS",
+           "h2d_bytes_per_step": wbytes / n_e2e, "d2h_bytes_per_step": 64 + wbytes / n_e2e,
+           "note": "per step: vlbm_advance(1) + vlbm_audit (totals to host); initial W from pinned host "
+                   "memory and final W to host amortised over the steps"}
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and args.cpu_seconds > 0:
+            mlups, nst, el = oracle_rate(case, args.cpu_seconds)
+            cpu = {"value": round(mlups, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                   "sample": f"{nst} coarse steps of the same workload ({el:.1f} s, one thread)"}
+        line = {"metric": METRIC, "value": round(value, 3), "unit": "MLUPS", "n_gpus": world,
+                "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (closed-form initial state)",
+                "config": {"workload": WORKLOAD, "coarse": [case.nx0, case.ny0], "levels": case.nlev,
+                           "lups_per_step": lups, "c": case.c, "beta": case.beta,
+                           "l2": "flushed between timed steps (512 MB write)",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(round(launches_per_step * args.steps)),
+                "clocks": clk.summary()}
+        print(json.dumps(line))
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,239 @@
+/*
+ * vlbm.h -- C ABI of the B300 (sm_103a) implementation of the conservative
+ * locally refined vectorial lattice Boltzmann method for the 2-D compressible
+ * Euler equations (Hosseini, Strassle & Karlin, "Conservative local grid
+ * refinement for the vectorial lattice Boltzmann method").
+ *
+ * What one coarse step computes (all FP64, all on the GPU):
+ *   - per level, the fused D2Q4 stream-and-collide update: each conserved
+ *     field (rho, rho u, rho v, rho E) has its own four populations, the
+ *     vector equilibrium f_i^eq = W/4 + c_i.Q(W)/(2c^2) is fixed by the Euler
+ *     flux, the BGK relaxation is f* = 2 beta f^eq + (1 - 2 beta) f
+ *     (Sec. 2.2, Eqs. 4-6) and streaming is an exact one-cell shift (Eq. 5);
+ *   - sub-cycling: level l+1 takes two steps per level-l step at the same
+ *     link speed c (acoustic scaling, Sec. 3.2, Eq. 15);
+ *   - coarse-to-fine: the mean-preserving reconstruction in time with the
+ *     tangential minmod correction (Sec. 3.3, Eqs. 20, 22, 23);
+ *   - fine-to-coarse: the reflux average of the r*r = 4 post-collision
+ *     values leaving the fine side (Sec. 3.3, Eq. 24);
+ *   - at regrids: merge (plain average, Eq. 25) and split (minmod-limited
+ *     linear reconstruction, Eqs. 26-27), Sec. 3.4.
+ *
+ * Conventions
+ *   - Every call returns a vlbm_status; no C++ exception crosses the ABI.
+ *   - Level l has (nx0 << l) x (ny0 << l) cells; cell (i, j) of level l has
+ *     its centre at ((i + 0.5) dx0 / 2^l, (j + 0.5) dx0 / 2^l).  Refinement
+ *     ratio 2 per level, at most VLBM_MAX_LEVELS levels.
+ *   - Refinement is decided per 8 x 8 block of cells of the refined level
+ *     (VLBM_BLOCK): boxes and masks must be block aligned.
+ *   - Host arrays are owned by the caller and copied; device arrays passed
+ *     with on_device = 1 must live on the handle's device and are read on
+ *     the handle's stream.
+ *   - Conserved-field arrays are W[4][ny_l][ld] (x fastest, ld >= nx_l),
+ *     fields in the order rho, rho u, rho v, rho E.
+ *   - Population arrays are f[16][ny_l][ld] with population q = 4 i + k:
+ *     direction i in (+x, -x, +y, -y), field k as above.
+ *   - The library owns all device memory of a handle; it comes from the
+ *     caller's allocator when one is given, else from cudaMallocAsync on
+ *     the handle's stream.
+ *   - Handles are not thread safe; distinct handles are independent.
+ *   - vlbm_advance is asynchronous.  A non-physical state (rho <= 0,
+ *     p <= 0 or not finite) met by a kernel is reported by the next
+ *     synchronising call (vlbm_sync, vlbm_get_conserved, vlbm_audit,
+ *     vlbm_regrid) as VLBM_ERR_NONPHYSICAL; the handle then answers
+ *     VLBM_ERR_STATE to every call but vlbm_last_error and vlbm_destroy.
+ */
+#ifndef VLBM_H
+#define VLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VLBM_MAX_LEVELS 4
+#define VLBM_BLOCK 8
+
+typedef struct vlbm_hier vlbm_hier;     /* opaque, owned by the library */
+typedef struct vlbm_engine vlbm_engine; /* opaque batching/serving engine */
+
+typedef enum {
+    VLBM_OK = 0,
+    VLBM_ERR_ARG = 1,          /* an argument is out of range or malformed */
+    VLBM_ERR_NESTING = 2,      /* a refinement layout is not properly nested */
+    VLBM_ERR_OOM = 3,          /* allocation failed, or the engine is full */
+    VLBM_ERR_CUDA = 4,         /* a CUDA call failed (see vlbm_last_error) */
+    VLBM_ERR_NONPHYSICAL = 5,  /* rho <= 0, p <= 0 or NaN met by a kernel */
+    VLBM_ERR_TIMEOUT = 6,      /* a bounded device wait gave up */
+    VLBM_ERR_STATE = 7         /* the handle is poisoned by an earlier error */
+} vlbm_status;
+
+typedef enum {
+    VLBM_BC_PERIODIC = 0,  /* both sides of an axis must be periodic */
+    VLBM_BC_OUTFLOW = 1,   /* zero gradient: the ghost repeats the edge cell */
+    VLBM_BC_INFLOW = 2,    /* ghost in equilibrium at the side's inflow_W */
+    VLBM_BC_REFLECT = 3    /* slip wall: mirror state, normal momentum negated */
+} vlbm_bc;
+
+/* A rectangle of cells of `level` that is covered by level + 1. */
+typedef struct {
+    int32_t level, i0, j0, ni, nj;
+} vlbm_box;
+
+typedef struct {
+    int32_t nx0, ny0;          /* coarse grid size (cells), >= 1 each */
+    double dx0;                /* coarse spacing (only reported back) */
+    int32_t max_levels;        /* 1..VLBM_MAX_LEVELS */
+    int32_t bc[4];             /* vlbm_bc of the W, E, S, N sides */
+    double inflow_W[4][4];     /* W of the ghost state, per side (INFLOW only) */
+    double gamma;              /* ideal-gas ratio of specific heats, > 1 */
+    double c;                  /* link speed c = dx/dt (same on every level), > 0 */
+    double beta;               /* BGK relaxation parameter, 0 <= beta <= 1 */
+    const vlbm_box* boxes;     /* initial static refinement, may be NULL */
+    int32_t nboxes;
+    double tag_tol;            /* adaptive regrid: indicator tolerance */
+    int32_t tag_buffer;        /* adaptive regrid: dilation (cells) */
+} vlbm_config;
+
+typedef struct {
+    /* returns device memory of `bytes` usable on `stream`, or NULL */
+    void* (*alloc)(size_t bytes, void* stream, void* ctx);
+    void (*free)(void* ptr, void* stream, void* ctx);
+    void* ctx;
+} vlbm_allocator;
+
+typedef struct {
+    int32_t nlev;                          /* levels allocated */
+    int32_t nx[VLBM_MAX_LEVELS], ny[VLBM_MAX_LEVELS];
+    int64_t active_cells[VLBM_MAX_LEVELS]; /* cells updated per level step */
+    int64_t lups_per_step;                 /* sum_l active_cells_l * 2^l */
+    int64_t device_bytes;                  /* device memory held */
+    int64_t steps;                         /* coarse steps taken */
+    double c, beta, gamma, dx0;
+} vlbm_info;
+
+/* ---- hierarchy life cycle ---------------------------------------------- */
+
+/* Creates a hierarchy with the initial static layout cfg->boxes (validated:
+ * block aligned, inside the domain, properly nested -- every cell covered on
+ * level l >= 1 has its four face neighbours on level l).  The populations are
+ * zero until vlbm_set_state.  stream is a cudaStream_t (NULL = legacy
+ * default stream) used by every later call on the handle.
+ * Errors: ERR_ARG, ERR_NESTING, ERR_OOM, ERR_CUDA; *out is NULL then. */
+vlbm_status vlbm_create_hierarchy(const vlbm_config* cfg, const vlbm_allocator* alloc,
+                                  void* stream, vlbm_hier** out);
+
+/* Sets f = f^eq(W) (Eq. 4) on every cell of `level` (covered cells included)
+ * from W[4][ny_l][ld].  on_device = 0: host array (copied, synchronous);
+ * 1: device array.  Faces seen for the first time have no previous sample.
+ * Errors: ERR_ARG (level, ld), ERR_CUDA, ERR_STATE. */
+vlbm_status vlbm_set_state(vlbm_hier* h, int32_t level, const double* W, int64_t ld,
+                           int32_t on_device);
+
+/* Raw population access for tests and checkpoints: f[16][ny_l][ld]. */
+vlbm_status vlbm_set_populations(vlbm_hier* h, int32_t level, const double* f, int64_t ld,
+                                 int32_t on_device);
+vlbm_status vlbm_get_populations(vlbm_hier* h, int32_t level, double* f, int64_t ld,
+                                 int32_t on_device);
+
+/* Advances `coarse_steps` coarse steps (each: one level-0 step, two level-1
+ * steps per level-0 step, and so on, with reconstruction and reflux at every
+ * interface).  Asynchronous on the handle's stream; launches a captured CUDA
+ * graph.  Errors: ERR_ARG (negative), ERR_CUDA, ERR_STATE. */
+vlbm_status vlbm_advance(vlbm_hier* h, int64_t coarse_steps);
+
+/* Regrid (Sec. 3.4, Fig. 2).  boxes != NULL: the new layout is the union of
+ * the boxes (validated like vlbm_create_hierarchy).  boxes == NULL: the
+ * layout is derived from the normalised density-gradient indicator
+ * ((rho_E - rho_W)^2 + (rho_N - rho_S)^2 > tol^2 (2 rho_C)^2) with
+ * cfg->tag_tol and cfg->tag_buffer, rounded to blocks and grown so that every
+ * level nests.  Cells leaving refinement take the merge of their children,
+ * cells entering refinement are split (finest level first for merges,
+ * coarsest first for splits).  Synchronises the stream.
+ * Errors: ERR_ARG, ERR_NESTING (layout unchanged), ERR_CUDA, ERR_STATE,
+ * ERR_NONPHYSICAL (from an earlier advance). */
+vlbm_status vlbm_regrid(vlbm_hier* h, const vlbm_box* boxes, int32_t nboxes);
+
+/* Same as vlbm_regrid with a per-cell refinement mask for every level
+ * l < nlev-1 (ref[l] is uint8[ny_l][nx_l], 1 = covered by level l+1); the
+ * masks must be block aligned. */
+vlbm_status vlbm_regrid_masks(vlbm_hier* h, const uint8_t* const* ref);
+
+/* Per-cell layout of `level`: in[c] = 1 on the level, ref[c] = 1 covered by
+ * the next level (host arrays of ny_l * nx_l bytes, either may be NULL). */
+vlbm_status vlbm_get_layout(vlbm_hier* h, int32_t level, uint8_t* in, uint8_t* ref);
+
+/* Conserved fields W = sum_i f_i of `level` into W[4][ny_l][ld] (host, may
+ * be NULL); valid[ny_l*nx_l] (may be NULL) = 1 on active cells.  totals and
+ * abs_totals (may be NULL) receive sum_l 4^-l sum_active W_k and the same
+ * of |W_k| over the whole hierarchy (deterministic compensated sums).
+ * Synchronises.  Errors: ERR_ARG, ERR_CUDA, ERR_NONPHYSICAL, ERR_STATE. */
+vlbm_status vlbm_get_conserved(vlbm_hier* h, int32_t level, double* W, int64_t ld,
+                               uint8_t* valid, double totals[4], double abs_totals[4]);
+
+/* Totals only (see vlbm_get_conserved).  Synchronises. */
+vlbm_status vlbm_audit(vlbm_hier* h, double totals[4], double abs_totals[4]);
+
+/* Waits for the stream and reports deferred device errors. */
+vlbm_status vlbm_sync(vlbm_hier* h);
+
+vlbm_status vlbm_get_info(const vlbm_hier* h, vlbm_info* info);
+
+/* Per-kernel timing of the sub-cycle.  Runs `coarse_steps` coarse steps
+ * launch by launch (not through the graph) with CUDA events around every
+ * kernel on the handle's stream, and reports one record per kernel kind:
+ * kind 0 = level sweep (fused collide + stream + boundary + coarse-to-fine)
+ * of `level`, kind 1 = reflux close into `level`, kind 2 = end of step.
+ * `cells` counts the cell updates the launches performed.  The state
+ * advances exactly as with vlbm_advance.  cap >= 2 * VLBM_MAX_LEVELS + 1
+ * records suffice.  Errors: ERR_ARG, ERR_CUDA, ERR_STATE. */
+typedef struct {
+    int32_t kind, level;
+    int64_t launches;
+    int64_t cells;
+    double ms;
+} vlbm_kernel_time;
+
+vlbm_status vlbm_profile(vlbm_hier* h, int64_t coarse_steps, vlbm_kernel_time* out, int32_t cap, int32_t* n);
+
+/* Human-readable description of the last error on the handle (never NULL). */
+const char* vlbm_last_error(const vlbm_hier* h);
+
+void vlbm_destroy(vlbm_hier* h);
+
+/* ---- batching / serving engine ------------------------------------------ */
+
+/* An engine advances many resident hierarchies together: every engine step
+ * is one coarse step of every resident, issued as one CUDA-graph launch in
+ * which each phase of the sub-cycle (level-0 sweep, level-1 sweeps, ...)
+ * processes the tiles of all residents.  mem_budget bounds the summed
+ * device memory of the residents (0 = no bound). */
+vlbm_status vlbm_engine_create(size_t mem_budget, void* stream, vlbm_engine** out);
+
+/* Admits h (created on the same device; the engine borrows it until release)
+ * for coarse_steps steps; adaptive hierarchies (tag_tol > 0) regrid every
+ * regrid_every coarse steps (0 = never).  Errors: ERR_OOM when admitting
+ * would exceed the budget (not admitted, try later), ERR_ARG. */
+vlbm_status vlbm_engine_admit(vlbm_engine* e, vlbm_hier* h, int64_t coarse_steps,
+                              int32_t regrid_every, int32_t* slot);
+
+/* One coarse step of every resident.  finished_slots (capacity = the number
+ * of residents) receives the slots whose step count is now met.
+ * Errors: ERR_CUDA, ERR_NONPHYSICAL (the offending residents are listed in
+ * finished_slots with a negative sign-encoded slot: -(slot+1)). */
+vlbm_status vlbm_engine_step(vlbm_engine* e, int32_t* finished_slots, int32_t* nfinished);
+
+/* Removes a resident (its hierarchy returns to the caller, unchanged). */
+vlbm_status vlbm_engine_release(vlbm_engine* e, int32_t slot);
+
+/* Number of residents and their summed device bytes. */
+vlbm_status vlbm_engine_usage(const vlbm_engine* e, int32_t* residents, int64_t* bytes);
+
+void vlbm_engine_destroy(vlbm_engine* e);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VLBM_H */

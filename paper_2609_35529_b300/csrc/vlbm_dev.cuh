@@ -1,0 +1,72 @@
+// Device-side data model of the VLBM library (sm_103a).
+//
+// Storage: every level l of a hierarchy owns two dense population buffers
+// over its whole index space, buf[b][q * plane + y * pitch + x], q = 4 i + k
+// (direction i in +x,-x,+y,-y; field k in rho, rho u, rho v, rho E), plus a
+// 16-bit flag word per cell.  Work is organised in 8 x 8 tiles that coincide
+// with the refinement blocks, so a tile is entirely active, entirely covered
+// by the next level, or entirely off the level.
+//
+// Streaming is "push": the thread of cell x writes its post-collision
+// population f*_i into the destination buffer at x + c_i, whatever lies
+// there.  Two facts of the refinement coupling fall out of that for free:
+//   * a coarse ring cell L0 pushes f*_d(L0) into the covered cell C = L0 + c_d
+//     of its own level, so after a coarse step dst[C] holds the current
+//     sample of Eq. 20 and src[C] the previous one (the buffers ping-pong);
+//   * a fine edge cell R0 pushes its outgoing f* into the fine-level cell that
+//     lies inside the coarse cell L0; the two fine sub-steps of a cycle write
+//     the two buffers, so the four values averaged by Eq. 24 are there when
+//     the cycle closes.
+// No face tables, ghost copies or register arrays are needed.
+#pragma once
+#include <cstdint>
+
+namespace vlbm {
+
+constexpr int NQ = 16;
+constexpr int TILE = 8;          // tile edge = refinement block edge (cells)
+constexpr int TILES_PER_CTA = 4; // 4 x 64 threads
+constexpr int CTA_THREADS = TILES_PER_CTA * TILE * TILE;
+
+// per-cell flag bits
+enum : uint32_t {
+    F_IN = 1u << 0,         // cell belongs to the level
+    F_COV = 1u << 1,        // cell is covered by the next finer level
+    F_RECON_SHIFT = 2,      // bits 2..5: upwind of direction i is coarser land
+    F_PEND_SHIFT = 6,       // bits 6..9: upwind of direction i is covered
+    F_FRESH_SHIFT = 10,     // bits 10..13: face (cell, d) has no previous sample
+    F_BND = 1u << 14,       // an upwind neighbour lies beyond a non-periodic side
+};
+constexpr uint32_t F_RECON_MASK = 0xFu << F_RECON_SHIFT;
+constexpr uint32_t F_PEND_MASK = 0xFu << F_PEND_SHIFT;
+constexpr uint32_t F_FRESH_MASK = 0xFu << F_FRESH_SHIFT;
+
+// status bits of a hierarchy
+enum : int { ST_NONPHYS = 1, ST_TIMEOUT = 2 };
+
+enum : int { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_INFLOW = 2, BC_REFLECT = 3 };
+
+// One level of one hierarchy, as the kernels see it.
+struct LevelDev {
+    double* buf[2];
+    uint16_t* flags;
+    int* par0;        // level-0 buffer parity of the hierarchy (device word)
+    int* status;      // status word of the hierarchy (device)
+    long long plane;  // pitch * ny
+    int nx, ny, pitch, level;
+    int parent;       // index of the parent level in the table, -1 on level 0
+    int child;        // index of the child level in the table, -1 on the finest
+    int px, py;       // periodic in x / y
+    int bc[4];        // W, E, S, N
+    double om, hb, bcs, gm1;
+    double wscale;    // area weight 4^-level
+    double feqb[4][16];
+};
+
+// A unit of work: one 8 x 8 tile of one level.
+struct Item {
+    int lid;
+    unsigned short tx, ty;
+};
+
+}  // namespace vlbm

@@ -1,0 +1,1133 @@
+// Host runtime of the VLBM library: hierarchies, layouts, batches, CUDA-graph
+// capture of the sub-cycle, the C ABI and the batching/serving engine.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "vlbm.h"
+#include "vlbm_dev.cuh"
+#include "vlbm_launch.h"
+
+using namespace vlbm;
+
+namespace {
+
+struct Fail {
+    vlbm_status st;
+    std::string msg;
+};
+
+#define VCK(call)                                                                            \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            throw Fail{VLBM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+    } while (0)
+
+// ---- canonical host arithmetic (built with -ffp-contract=off) --------------
+
+// Euler flux and vector equilibrium of Eq. 4 (D = 2), identical in expression
+// order to the device code: used for the inflow ghost populations.
+void host_feq(double gamma, double c, const double W[4], double feq[16]) {
+    const double gm1 = gamma - 1.0;
+    const double inv = 1.0 / W[0];
+    const double u = W[1] * inv;
+    const double v = W[2] * inv;
+    const double ruu = W[1] * u;
+    const double rvv = W[2] * v;
+    const double p = gm1 * std::fma(-0.5, ruu + rvv, W[3]);
+    const double H = W[3] + p;
+    const double Qx[4] = {W[1], ruu + p, W[2] * u, H * u};
+    const double Qy[4] = {W[2], W[1] * v, rvv + p, H * v};
+    const double hc = 0.5 / c;
+    for (int k = 0; k < 4; k++) {
+        const double qw = 0.25 * W[k];
+        feq[k] = std::fma(hc, Qx[k], qw);
+        feq[4 + k] = std::fma(-hc, Qx[k], qw);
+        feq[8 + k] = std::fma(hc, Qy[k], qw);
+        feq[12 + k] = std::fma(-hc, Qy[k], qw);
+    }
+}
+
+struct DevMem {
+    const vlbm_allocator* alloc = nullptr;
+    vlbm_allocator a{};
+    bool has = false;
+    cudaStream_t s = nullptr;
+    size_t bytes = 0;
+    void* get(size_t n) {
+        if (n == 0) n = 16;
+        n = (n + 255) & ~size_t(255);
+        void* p = nullptr;
+        if (has) {
+            p = a.alloc(n, (void*)s, a.ctx);
+            if (!p) throw Fail{VLBM_ERR_OOM, "allocator returned NULL"};
+        } else {
+            cudaError_t e = cudaMallocAsync(&p, n, s);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                throw Fail{VLBM_ERR_OOM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e)};
+            }
+        }
+        bytes += n;
+        return p;
+    }
+    void put(void* p, size_t n) {
+        if (!p) return;
+        if (n == 0) n = 16;
+        n = (n + 255) & ~size_t(255);
+        if (has) a.free(p, (void*)s, a.ctx);
+        else cudaFreeAsync(p, s);
+        bytes -= std::min(bytes, n);
+    }
+};
+
+template <class T>
+struct DArr {
+    T* p = nullptr;
+    size_t cap = 0;  // elements
+    size_t n = 0;
+    void ensure(DevMem& m, size_t need) {
+        if (need <= cap && p) return;
+        if (p) m.put(p, cap * sizeof(T));
+        cap = std::max<size_t>(need, 16);
+        p = (T*)m.get(cap * sizeof(T));
+    }
+    void upload(DevMem& m, const std::vector<T>& v, cudaStream_t s) {
+        ensure(m, v.size());
+        n = v.size();
+        if (n) VCK(cudaMemcpyAsync(p, v.data(), n * sizeof(T), cudaMemcpyHostToDevice, s));
+    }
+    void release(DevMem& m) {
+        if (p) m.put(p, cap * sizeof(T));
+        p = nullptr;
+        cap = n = 0;
+    }
+};
+
+struct Level {
+    int nx = 0, ny = 0, pitch = 0, bx = 0, by = 0;
+    long long plane = 0;
+    double* buf[2] = {nullptr, nullptr};
+    uint16_t* flags = nullptr;
+    uint16_t* flags_tmp = nullptr;
+    std::vector<uint8_t> bin, bcov;  // block maps (current layout)
+    DArr<uint8_t> dbin, dbcov;
+    std::vector<Item> act, ring, cov, in;  // tiles (lid = level index)
+    long long active_cells = 0;
+};
+
+}  // namespace
+
+struct Batch;
+
+struct vlbm_hier {
+    vlbm_config cfg{};
+    std::vector<vlbm_box> boxes;
+    int nlev = 1;
+    double om = 0, hb = 0, bcs = 0, gm1 = 0, hc = 0;
+    double feqb[4][16] = {};
+    Level lev[VLBM_MAX_LEVELS];
+    int* words = nullptr;  // [0] level-0 parity, [1] status
+    DevMem mem;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    Batch* own = nullptr;
+    vlbm_engine* engine = nullptr;
+    long long steps = 0;
+    bool poisoned = false;
+    std::string err = "no error";
+    // scratch
+    DArr<double> stage;     // W / f staging
+    DArr<uint8_t> stage8;   // valid masks, tags
+    DArr<double> partial;  // audit partial sums
+    DArr<double> tot;      // audit result
+    DArr<Item> listbuf;    // item lists for regrid kernels
+    DArr<uint8_t> bflag;   // block flags
+    DArr<LevelDev> atab;   // level table for audits (rebuilt with the layout)
+    DArr<Item> aitems;     // active tiles of every level (audits)
+    double* hout = nullptr;  // pinned host copy of the audit result
+
+    LevelDev dev(int l, int parent, int child) const {
+        LevelDev d{};
+        const Level& L = lev[l];
+        d.buf[0] = L.buf[0];
+        d.buf[1] = L.buf[1];
+        d.flags = L.flags;
+        d.par0 = words;
+        d.status = words + 1;
+        d.plane = L.plane;
+        d.nx = L.nx;
+        d.ny = L.ny;
+        d.pitch = L.pitch;
+        d.level = l;
+        d.parent = parent;
+        d.child = child;
+        d.px = cfg.bc[0] == VLBM_BC_PERIODIC;
+        d.py = cfg.bc[2] == VLBM_BC_PERIODIC;
+        for (int s = 0; s < 4; s++) d.bc[s] = cfg.bc[s];
+        d.om = om;
+        d.hb = hb;
+        d.bcs = bcs;
+        d.gm1 = gm1;
+        d.wscale = std::ldexp(1.0, -2 * l);
+        std::memcpy(d.feqb, feqb, sizeof feqb);
+        return d;
+    }
+    size_t device_bytes() const { return mem.bytes; }
+};
+
+// A set of hierarchies advanced together; every phase of the sub-cycle is one
+// launch over the tiles of all members.
+struct Batch {
+    std::vector<vlbm_hier*> members;
+    int maxlev = 0;
+    DevMem* mem = nullptr;
+    DArr<LevelDev> levs;
+    DArr<Item> sweep[VLBM_MAX_LEVELS], close[VLBM_MAX_LEVELS];
+    DArr<int*> par;
+    DArr<Item> audit_items;
+    cudaGraphExec_t exec1 = nullptr, execG = nullptr;
+    int G = 8;
+    bool valid = false;
+    int max_ctas = 0;  // sweep grid cap (0 = one CTA per 4 tiles)
+
+    void release() {
+        if (exec1) cudaGraphExecDestroy(exec1);
+        if (execG) cudaGraphExecDestroy(execG);
+        exec1 = execG = nullptr;
+        levs.release(*mem);
+        for (int l = 0; l < VLBM_MAX_LEVELS; l++) {
+            sweep[l].release(*mem);
+            close[l].release(*mem);
+        }
+        par.release(*mem);
+        audit_items.release(*mem);
+        valid = false;
+    }
+
+    void schedule(int l, int kk, int kkp, cudaStream_t s) {
+        VCK(launch_sweep(levs.p, sweep[l].p, (int)sweep[l].n, kk, kkp, max_ctas, s));
+        if (l + 1 < maxlev && sweep[l + 1].n > 0) {
+            schedule(l + 1, 1, kk, s);
+            schedule(l + 1, 2, kk, s);
+            VCK(launch_close(levs.p, close[l].p, (int)close[l].n, kk, s));
+        }
+    }
+
+    void one_step(cudaStream_t s) {
+        schedule(0, 0, 0, s);
+        VCK(launch_end_step(par.p, (int)par.n, s));
+    }
+
+    cudaGraphExec_t capture(int nsteps, cudaStream_t s) {
+        cudaGraph_t g = nullptr;
+        VCK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        try {
+            for (int i = 0; i < nsteps; i++) one_step(s);
+        } catch (...) {
+            cudaStreamEndCapture(s, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+        }
+        VCK(cudaStreamEndCapture(s, &g));
+        cudaGraphExec_t ex = nullptr;
+        cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        VCK(e);
+        return ex;
+    }
+
+    // rebuilds the tables of all members and re-captures the graphs
+    void build(cudaStream_t s) {
+        if (exec1) cudaGraphExecDestroy(exec1);
+        if (execG) cudaGraphExecDestroy(execG);
+        exec1 = execG = nullptr;
+        std::vector<LevelDev> tab;
+        std::vector<Item> sw[VLBM_MAX_LEVELS], cl[VLBM_MAX_LEVELS], au;
+        std::vector<int*> pw;
+        maxlev = 0;
+        for (vlbm_hier* h : members) {
+            const int base = (int)tab.size();
+            for (int l = 0; l < h->nlev; l++) {
+                tab.push_back(h->dev(l, l ? base + l - 1 : -1, l + 1 < h->nlev ? base + l + 1 : -1));
+                for (Item it : h->lev[l].act) {
+                    it.lid = base + l;
+                    sw[l].push_back(it);
+                    au.push_back(it);
+                }
+                if (l + 1 < h->nlev)
+                    for (Item it : h->lev[l].ring) {
+                        it.lid = base + l;
+                        cl[l].push_back(it);
+                    }
+            }
+            maxlev = std::max(maxlev, h->nlev);
+            pw.push_back(h->words);
+        }
+        levs.upload(*mem, tab, s);
+        for (int l = 0; l < VLBM_MAX_LEVELS; l++) {
+            sweep[l].upload(*mem, sw[l], s);
+            close[l].upload(*mem, cl[l], s);
+        }
+        par.upload(*mem, pw, s);
+        audit_items.upload(*mem, au, s);
+        VCK(cudaStreamSynchronize(s));
+        exec1 = capture(1, s);
+        execG = capture(G, s);
+        valid = true;
+    }
+
+    // eager launches with events around each kernel (profiling)
+    struct Rec {
+        int kind, level;
+        long long launches = 0, cells = 0;
+        double ms = 0;
+    };
+    void timed(int kind, int level, long long cells, std::vector<Rec>& recs, cudaStream_t s,
+               const std::function<cudaError_t()>& fn) {
+        cudaEvent_t a, b;
+        VCK(cudaEventCreate(&a));
+        VCK(cudaEventCreate(&b));
+        VCK(cudaEventRecord(a, s));
+        VCK(fn());
+        VCK(cudaEventRecord(b, s));
+        VCK(cudaEventSynchronize(b));
+        float ms = 0;
+        VCK(cudaEventElapsedTime(&ms, a, b));
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        for (Rec& r : recs)
+            if (r.kind == kind && r.level == level) {
+                r.launches++;
+                r.cells += cells;
+                r.ms += ms;
+                return;
+            }
+        Rec r;
+        r.kind = kind;
+        r.level = level;
+        r.launches = 1;
+        r.cells = cells;
+        r.ms = ms;
+        recs.push_back(r);
+    }
+    void schedule_timed(int l, int kk, int kkp, const long long* cells, std::vector<Rec>& recs, cudaStream_t s) {
+        if (sweep[l].n)
+            timed(0, l, cells[l], recs, s,
+                  [&] { return launch_sweep(levs.p, sweep[l].p, (int)sweep[l].n, kk, kkp, max_ctas, s); });
+        if (l + 1 < maxlev && sweep[l + 1].n > 0) {
+            schedule_timed(l + 1, 1, kk, cells, recs, s);
+            schedule_timed(l + 1, 2, kk, cells, recs, s);
+            if (close[l].n)
+                timed(1, l, 0, recs, s, [&] { return launch_close(levs.p, close[l].p, (int)close[l].n, kk, s); });
+        }
+    }
+    void profile(long long n, const long long* cells, std::vector<Rec>& recs, cudaStream_t s) {
+        for (long long i = 0; i < n; i++) {
+            schedule_timed(0, 0, 0, cells, recs, s);
+            timed(2, 0, 0, recs, s, [&] { return launch_end_step(par.p, (int)par.n, s); });
+        }
+    }
+
+    void advance(long long n, cudaStream_t s) {
+        while (n >= G) {
+            VCK(cudaGraphLaunch(execG, s));
+            n -= G;
+        }
+        while (n-- > 0) VCK(cudaGraphLaunch(exec1, s));
+    }
+};
+
+namespace {
+
+// ---- layouts ----------------------------------------------------------------
+
+int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+// in-maps of levels >= 1 from the covered maps (children of covered blocks)
+void derive_in(vlbm_hier* h, std::vector<uint8_t>* bin, const std::vector<uint8_t>* bcov) {
+    for (int l = 0; l < h->nlev; l++) {
+        Level& L = h->lev[l];
+        bin[l].assign((size_t)L.bx * L.by, l == 0 ? 1 : 0);
+        if (l == 0) continue;
+        const Level& P = h->lev[l - 1];
+        for (int jb = 0; jb < L.by; jb++)
+            for (int ib = 0; ib < L.bx; ib++) {
+                const size_t pb = (size_t)(jb >> 1) * P.bx + (ib >> 1);
+                bin[l][(size_t)jb * L.bx + ib] = bin[l - 1][pb] && bcov[l - 1][pb];
+            }
+    }
+}
+
+// Proper nesting: covered blocks lie on their level, none on the finest
+// level, and on levels >= 1 every covered block's four face-neighbour blocks
+// (inside the domain) are on the level.
+bool nested(vlbm_hier* h, const std::vector<uint8_t>* bin, const std::vector<uint8_t>* bcov, std::string& why) {
+    const bool px = h->cfg.bc[0] == VLBM_BC_PERIODIC, py = h->cfg.bc[2] == VLBM_BC_PERIODIC;
+    for (int l = 0; l < h->nlev; l++) {
+        const Level& L = h->lev[l];
+        for (int jb = 0; jb < L.by; jb++)
+            for (int ib = 0; ib < L.bx; ib++) {
+                const size_t b = (size_t)jb * L.bx + ib;
+                if (!bcov[l][b]) continue;
+                if (l == h->nlev - 1) { why = "finest level cannot be refined"; return false; }
+                if (!bin[l][b]) { why = "refined block outside its level (level " + std::to_string(l) + ")"; return false; }
+                if (l == 0) continue;
+                const int di[4] = {1, -1, 0, 0}, dj[4] = {0, 0, 1, -1};
+                for (int d = 0; d < 4; d++) {
+                    int i2 = ib + di[d], j2 = jb + dj[d];
+                    if (i2 < 0 || i2 >= L.bx) { if (!px) continue; i2 = (i2 + L.bx) % L.bx; }
+                    if (j2 < 0 || j2 >= L.by) { if (!py) continue; j2 = (j2 + L.by) % L.by; }
+                    if (!bin[l][(size_t)j2 * L.bx + i2]) {
+                        why = "level " + std::to_string(l + 1) + " touches level " + std::to_string(l - 1);
+                        return false;
+                    }
+                }
+            }
+    }
+    return true;
+}
+
+void boxes_to_maps(vlbm_hier* h, const vlbm_box* boxes, int nboxes, std::vector<uint8_t>* bcov) {
+    for (int l = 0; l < h->nlev; l++) bcov[l].assign((size_t)h->lev[l].bx * h->lev[l].by, 0);
+    for (int b = 0; b < nboxes; b++) {
+        const vlbm_box& x = boxes[b];
+        if (x.level < 0 || x.level >= h->nlev) throw Fail{VLBM_ERR_ARG, "box level out of range"};
+        const Level& L = h->lev[x.level];
+        if (x.ni <= 0 || x.nj <= 0 || x.i0 < 0 || x.j0 < 0 || x.i0 + x.ni > L.nx || x.j0 + x.nj > L.ny)
+            throw Fail{VLBM_ERR_ARG, "box outside the level"};
+        auto aligned = [](int a, int n) { return a % TILE == 0 || a == n; };
+        if (!aligned(x.i0, L.nx) || !aligned(x.j0, L.ny) || !aligned(x.i0 + x.ni, L.nx) || !aligned(x.j0 + x.nj, L.ny))
+            throw Fail{VLBM_ERR_ARG, "box not aligned to 8-cell blocks"};
+        if (x.level == h->nlev - 1) throw Fail{VLBM_ERR_NESTING, "finest level cannot be refined"};
+        for (int j = x.j0 / TILE; j < ceil_div(x.j0 + x.nj, TILE); j++)
+            for (int i = x.i0 / TILE; i < ceil_div(x.i0 + x.ni, TILE); i++) bcov[x.level][(size_t)j * L.bx + i] = 1;
+    }
+}
+
+void masks_to_maps(vlbm_hier* h, const uint8_t* const* ref, std::vector<uint8_t>* bcov) {
+    for (int l = 0; l < h->nlev; l++) {
+        const Level& L = h->lev[l];
+        bcov[l].assign((size_t)L.bx * L.by, 0);
+        if (l == h->nlev - 1 || !ref || !ref[l]) continue;
+        for (int jb = 0; jb < L.by; jb++)
+            for (int ib = 0; ib < L.bx; ib++) {
+                int ones = 0, cells = 0;
+                for (int y = jb * TILE; y < std::min(L.ny, jb * TILE + TILE); y++)
+                    for (int x = ib * TILE; x < std::min(L.nx, ib * TILE + TILE); x++) {
+                        cells++;
+                        ones += ref[l][(size_t)y * L.nx + x] ? 1 : 0;
+                    }
+                if (ones != 0 && ones != cells) throw Fail{VLBM_ERR_ARG, "refinement mask not aligned to 8-cell blocks"};
+                bcov[l][(size_t)jb * L.bx + ib] = ones ? 1 : 0;
+            }
+    }
+}
+
+// Layout rule for adaptive regrids, on blocks: bflag[l] marks the blocks
+// that hold a tagged cell within `buffer` cells; from the finest refinable
+// level down, add the blocks holding the parents of the 8-neighbourhood of
+// the next finer refined set (proper nesting).
+void layout_rule(vlbm_hier* h, const std::vector<uint8_t>* bflag, std::vector<uint8_t>* bcov) {
+    const bool px = h->cfg.bc[0] == VLBM_BC_PERIODIC, py = h->cfg.bc[2] == VLBM_BC_PERIODIC;
+    for (int l = h->nlev - 1; l >= 0; l--) {
+        Level& L = h->lev[l];
+        bcov[l].assign((size_t)L.bx * L.by, 0);
+        if (l == h->nlev - 1) continue;
+        for (size_t b = 0; b < bcov[l].size(); b++) bcov[l][b] = bflag[l][b];
+        if (l + 1 <= h->nlev - 2) {
+            const Level& C = h->lev[l + 1];
+            for (int jb = 0; jb < C.by; jb++)
+                for (int ib = 0; ib < C.bx; ib++) {
+                    if (!bcov[l + 1][(size_t)jb * C.bx + ib]) continue;
+                    // the block's cells on level l+1, widened by one cell
+                    const int x0 = ib * TILE - 1, x1 = std::min(C.nx, ib * TILE + TILE) + 1;
+                    const int y0 = jb * TILE - 1, y1 = std::min(C.ny, jb * TILE + TILE) + 1;
+                    for (int y = y0; y < y1; y++) {
+                        int yy = y;
+                        if (yy < 0 || yy >= C.ny) { if (!py) continue; yy = (yy + C.ny) % C.ny; }
+                        for (int x = x0; x < x1; x++) {
+                            int xx = x;
+                            if (xx < 0 || xx >= C.nx) { if (!px) continue; xx = (xx + C.nx) % C.nx; }
+                            const int cxp = xx >> 1, cyp = yy >> 1;  // parent cell on level l
+                            bcov[l][(size_t)(cyp / TILE) * L.bx + cxp / TILE] = 1;
+                        }
+                    }
+                }
+        }
+    }
+}
+
+void build_lists(vlbm_hier* h) {
+    const bool px = h->cfg.bc[0] == VLBM_BC_PERIODIC, py = h->cfg.bc[2] == VLBM_BC_PERIODIC;
+    for (int l = 0; l < h->nlev; l++) {
+        Level& L = h->lev[l];
+        L.act.clear();
+        L.ring.clear();
+        L.cov.clear();
+        L.in.clear();
+        L.active_cells = 0;
+        for (int jb = 0; jb < L.by; jb++)
+            for (int ib = 0; ib < L.bx; ib++) {
+                const size_t b = (size_t)jb * L.bx + ib;
+                if (!L.bin[b]) continue;
+                Item it{l, (unsigned short)ib, (unsigned short)jb};
+                L.in.push_back(it);
+                if (L.bcov[b]) {
+                    L.cov.push_back(it);
+                    continue;
+                }
+                L.act.push_back(it);
+                L.active_cells += (long long)(std::min(L.nx, ib * TILE + TILE) - ib * TILE) *
+                                  (std::min(L.ny, jb * TILE + TILE) - jb * TILE);
+                bool ring = false;
+                const int di[4] = {1, -1, 0, 0}, dj[4] = {0, 0, 1, -1};
+                for (int d = 0; d < 4 && !ring; d++) {
+                    int i2 = ib + di[d], j2 = jb + dj[d];
+                    if (i2 < 0 || i2 >= L.bx) { if (!px) continue; i2 = (i2 + L.bx) % L.bx; }
+                    if (j2 < 0 || j2 >= L.by) { if (!py) continue; j2 = (j2 + L.by) % L.by; }
+                    const size_t b2 = (size_t)j2 * L.bx + i2;
+                    ring = L.bin[b2] && L.bcov[b2];
+                }
+                if (ring) L.ring.push_back(it);
+            }
+    }
+}
+
+LevelDev lvdev(vlbm_hier* h, int l) { return h->dev(l, -1, -1); }
+
+// Installs new block maps: uploads them, rebuilds the per-cell flags (old
+// flags decide which faces are new) and the tile lists.
+void install_layout(vlbm_hier* h, std::vector<uint8_t>* bin, std::vector<uint8_t>* bcov) {
+    cudaStream_t s = h->stream;
+    for (int l = 0; l < h->nlev; l++) {
+        Level& L = h->lev[l];
+        L.bin = bin[l];
+        L.bcov = bcov[l];
+        L.dbin.upload(h->mem, L.bin, s);
+        L.dbcov.upload(h->mem, L.bcov, s);
+        VCK(launch_flags(lvdev(h, l), L.dbin.p, L.dbcov.p, L.flags, L.flags_tmp, s));
+        std::swap(L.flags, L.flags_tmp);
+    }
+    build_lists(h);
+    std::vector<Item> items;
+    std::vector<LevelDev> tab;
+    for (int l = 0; l < h->nlev; l++) {
+        items.insert(items.end(), h->lev[l].act.begin(), h->lev[l].act.end());
+        tab.push_back(h->dev(l, l ? l - 1 : -1, l + 1 < h->nlev ? l + 1 : -1));
+    }
+    h->aitems.upload(h->mem, items, s);
+    h->atab.upload(h->mem, tab, s);
+    h->partial.ensure(h->mem, (size_t)16 * audit_blocks((int)items.size()));
+    h->tot.ensure(h->mem, 8);
+    VCK(cudaStreamSynchronize(s));
+}
+
+void check_status(vlbm_hier* h) {
+    int st[2] = {0, 0};
+    VCK(cudaMemcpyAsync(st, h->words, sizeof st, cudaMemcpyDeviceToHost, h->stream));
+    VCK(cudaStreamSynchronize(h->stream));
+    if (st[1] & ST_NONPHYS) throw Fail{VLBM_ERR_NONPHYSICAL, "non-physical state (rho <= 0, p <= 0 or NaN)"};
+    if (st[1] & ST_TIMEOUT) throw Fail{VLBM_ERR_TIMEOUT, "a bounded device wait timed out"};
+}
+
+// Conservative regrid to the covered maps newcov (Sec. 3.4, Fig. 2).
+void regrid_to(vlbm_hier* h, std::vector<uint8_t>* newcov, bool averaged) {
+    cudaStream_t s = h->stream;
+    std::vector<uint8_t> newin[VLBM_MAX_LEVELS];
+    derive_in(h, newin, newcov);
+    std::string why;
+    if (!nested(h, newin, newcov, why)) throw Fail{VLBM_ERR_NESTING, why};
+    // 1. average-down, finest level first (merge values and slope data)
+    if (!averaged)
+        for (int l = h->nlev - 2; l >= 0; l--) {
+            h->listbuf.upload(h->mem, h->lev[l].cov, s);
+            VCK(launch_avgdown(lvdev(h, l), lvdev(h, l + 1), h->listbuf.p, (int)h->listbuf.n, s));
+            VCK(cudaStreamSynchronize(s));
+        }
+    // 2. merge: cells covered before and not now
+    for (int l = h->nlev - 2; l >= 0; l--) {
+        Level& L = h->lev[l];
+        std::vector<Item> ex;
+        for (const Item& it : L.cov) {
+            const size_t b = (size_t)it.ty * L.bx + it.tx;
+            if (!(newin[l][b] && newcov[l][b])) ex.push_back(it);
+        }
+        h->listbuf.upload(h->mem, ex, s);
+        VCK(launch_merge(lvdev(h, l), h->listbuf.p, (int)ex.size(), s));
+        VCK(cudaStreamSynchronize(s));
+    }
+    // 3. split: cells covered now and not before, coarsest level first
+    for (int l = 0; l <= h->nlev - 2; l++) {
+        Level& L = h->lev[l];
+        std::vector<Item> en;
+        for (int jb = 0; jb < L.by; jb++)
+            for (int ib = 0; ib < L.bx; ib++) {
+                const size_t b = (size_t)jb * L.bx + ib;
+                if (newin[l][b] && newcov[l][b] && !(L.bin[b] && L.bcov[b]))
+                    en.push_back(Item{l, (unsigned short)ib, (unsigned short)jb});
+            }
+        h->listbuf.upload(h->mem, en, s);
+        VCK(launch_split(lvdev(h, l), lvdev(h, l + 1), h->listbuf.p, (int)en.size(), s));
+        VCK(cudaStreamSynchronize(s));
+    }
+    install_layout(h, newin, newcov);
+}
+
+void invalidate(vlbm_hier* h);
+
+}  // namespace
+
+// ----------------------------------------------------------------------------
+// engine
+// ----------------------------------------------------------------------------
+
+struct vlbm_engine {
+    size_t budget = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    DevMem mem;
+    Batch batch;
+    struct Res {
+        vlbm_hier* h = nullptr;
+        long long target = 0, done = 0;
+        int regrid_every = 0;
+        bool live = false;
+    };
+    std::vector<Res> res;
+    bool dirty = true;
+    std::string err = "no error";
+};
+
+namespace {
+
+void invalidate(vlbm_hier* h) {
+    if (h->own) h->own->valid = false;
+    if (h->engine) h->engine->dirty = true;
+}
+
+vlbm_status finish(vlbm_hier* h, const Fail& f) {
+    h->err = f.msg;
+    if (f.st == VLBM_ERR_NONPHYSICAL || f.st == VLBM_ERR_TIMEOUT || f.st == VLBM_ERR_CUDA) h->poisoned = true;
+    return f.st;
+}
+
+template <class F>
+vlbm_status run(vlbm_hier* h, F&& fn) {
+    if (!h) return VLBM_ERR_ARG;
+    if (h->poisoned) return VLBM_ERR_STATE;
+    try {
+        fn();
+        return VLBM_OK;
+    } catch (const Fail& f) {
+        return finish(h, f);
+    } catch (const std::bad_alloc&) {
+        h->err = "host allocation failed";
+        return VLBM_ERR_OOM;
+    }
+}
+
+void destroy_levels(vlbm_hier* h) {
+    for (int l = 0; l < h->nlev; l++) {
+        Level& L = h->lev[l];
+        const size_t pb = (size_t)16 * L.plane * sizeof(double);
+        h->mem.put(L.buf[0], pb);
+        h->mem.put(L.buf[1], pb);
+        h->mem.put(L.flags, (size_t)L.plane * 2);
+        h->mem.put(L.flags_tmp, (size_t)L.plane * 2);
+        L.dbin.release(h->mem);
+        L.dbcov.release(h->mem);
+        L.buf[0] = L.buf[1] = nullptr;
+        L.flags = L.flags_tmp = nullptr;
+    }
+    h->mem.put(h->words, 64);
+    h->words = nullptr;
+    h->stage.release(h->mem);
+    h->stage8.release(h->mem);
+    h->partial.release(h->mem);
+    h->tot.release(h->mem);
+    h->listbuf.release(h->mem);
+    h->bflag.release(h->mem);
+    h->atab.release(h->mem);
+    h->aitems.release(h->mem);
+    if (h->hout) cudaFreeHost(h->hout);
+    h->hout = nullptr;
+}
+
+void ensure_own_batch(vlbm_hier* h) {
+    if (!h->own) {
+        h->own = new Batch();
+        h->own->mem = &h->mem;
+        h->own->members.push_back(h);
+    }
+    if (!h->own->valid) h->own->build(h->stream);
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------
+// C ABI
+// ----------------------------------------------------------------------------
+
+extern "C" {
+
+vlbm_status vlbm_create_hierarchy(const vlbm_config* cfg, const vlbm_allocator* alloc, void* stream, vlbm_hier** out) {
+    if (!out) return VLBM_ERR_ARG;
+    *out = nullptr;
+    if (!cfg) return VLBM_ERR_ARG;
+    if (cfg->nx0 < 1 || cfg->ny0 < 1 || cfg->max_levels < 1 || cfg->max_levels > VLBM_MAX_LEVELS) return VLBM_ERR_ARG;
+    if (!(cfg->gamma > 1.0) || !(cfg->c > 0.0) || !(cfg->beta >= 0.0 && cfg->beta <= 1.0)) return VLBM_ERR_ARG;
+    for (int s = 0; s < 4; s++)
+        if (cfg->bc[s] < 0 || cfg->bc[s] > 3) return VLBM_ERR_ARG;
+    if ((cfg->bc[0] == VLBM_BC_PERIODIC) != (cfg->bc[1] == VLBM_BC_PERIODIC)) return VLBM_ERR_ARG;
+    if ((cfg->bc[2] == VLBM_BC_PERIODIC) != (cfg->bc[3] == VLBM_BC_PERIODIC)) return VLBM_ERR_ARG;
+    const long long nxmax = (long long)cfg->nx0 << (cfg->max_levels - 1);
+    const long long nymax = (long long)cfg->ny0 << (cfg->max_levels - 1);
+    if (nxmax / TILE >= 65535 || nymax / TILE >= 65535) return VLBM_ERR_ARG;
+    if (cfg->nboxes < 0 || (cfg->nboxes > 0 && !cfg->boxes)) return VLBM_ERR_ARG;
+    vlbm_hier* h = new (std::nothrow) vlbm_hier();
+    if (!h) return VLBM_ERR_OOM;
+    h->cfg = *cfg;
+    if (cfg->nboxes) h->boxes.assign(cfg->boxes, cfg->boxes + cfg->nboxes);
+    h->cfg.boxes = nullptr;
+    h->nlev = cfg->max_levels;
+    h->gm1 = cfg->gamma - 1.0;
+    h->om = 1.0 - 2.0 * cfg->beta;
+    h->hb = 0.5 * cfg->beta;
+    h->bcs = cfg->beta / cfg->c;
+    h->hc = 0.5 / cfg->c;
+    for (int s = 0; s < 4; s++)
+        if (cfg->bc[s] == VLBM_BC_INFLOW) host_feq(cfg->gamma, cfg->c, cfg->inflow_W[s], h->feqb[s]);
+    if (alloc) {
+        if (!alloc->alloc || !alloc->free) {
+            delete h;
+            return VLBM_ERR_ARG;
+        }
+        h->mem.a = *alloc;
+        h->mem.has = true;
+    }
+    try {
+        if (stream) {
+            h->stream = (cudaStream_t)stream;
+        } else {
+            VCK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+            h->own_stream = true;
+        }
+        h->mem.s = h->stream;
+        h->words = (int*)h->mem.get(64);
+        VCK(cudaMemsetAsync(h->words, 0, 64, h->stream));
+        for (int l = 0; l < h->nlev; l++) {
+            Level& L = h->lev[l];
+            L.nx = cfg->nx0 << l;
+            L.ny = cfg->ny0 << l;
+            L.pitch = (L.nx + 15) & ~15;
+            L.plane = (long long)L.pitch * L.ny;
+            L.bx = ceil_div(L.nx, TILE);
+            L.by = ceil_div(L.ny, TILE);
+            const size_t pb = (size_t)16 * L.plane * sizeof(double);
+            L.buf[0] = (double*)h->mem.get(pb);
+            L.buf[1] = (double*)h->mem.get(pb);
+            L.flags = (uint16_t*)h->mem.get((size_t)L.plane * 2);
+            L.flags_tmp = (uint16_t*)h->mem.get((size_t)L.plane * 2);
+            VCK(cudaMemsetAsync(L.buf[0], 0, pb, h->stream));
+            VCK(cudaMemsetAsync(L.buf[1], 0, pb, h->stream));
+            VCK(cudaMemsetAsync(L.flags, 0, (size_t)L.plane * 2, h->stream));
+            VCK(cudaMemsetAsync(L.flags_tmp, 0, (size_t)L.plane * 2, h->stream));
+        }
+        std::vector<uint8_t> bin[VLBM_MAX_LEVELS], bcov[VLBM_MAX_LEVELS];
+        boxes_to_maps(h, h->boxes.data(), (int)h->boxes.size(), bcov);
+        derive_in(h, bin, bcov);
+        std::string why;
+        if (!nested(h, bin, bcov, why)) throw Fail{VLBM_ERR_NESTING, why};
+        install_layout(h, bin, bcov);
+    } catch (const Fail& f) {
+        vlbm_status st = f.st;
+        destroy_levels(h);
+        if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return VLBM_OK;
+}
+
+void vlbm_destroy(vlbm_hier* h) {
+    if (!h) return;
+    if (h->engine) {
+        // still resident: detach
+        vlbm_engine* e = h->engine;
+        for (size_t i = 0; i < e->res.size(); i++)
+            if (e->res[i].live && e->res[i].h == h) vlbm_engine_release(e, (int)i);
+    }
+    cudaStreamSynchronize(h->stream);
+    if (h->own) {
+        h->own->release();
+        delete h->own;
+    }
+    destroy_levels(h);
+    cudaStreamSynchronize(h->stream);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+const char* vlbm_last_error(const vlbm_hier* h) { return h ? h->err.c_str() : "null handle"; }
+
+vlbm_status vlbm_set_state(vlbm_hier* h, int32_t level, const double* W, int64_t ld, int32_t on_device) {
+    return run(h, [&] {
+        if (level < 0 || level >= h->nlev || !W) throw Fail{VLBM_ERR_ARG, "bad level or W"};
+        Level& L = h->lev[level];
+        if (ld < L.nx) throw Fail{VLBM_ERR_ARG, "ld < nx"};
+        const double* src = W;
+        if (!on_device) {
+            const size_t n = (size_t)4 * ld * L.ny;
+            h->stage.ensure(h->mem, n);
+            VCK(cudaMemcpyAsync(h->stage.p, W, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+            src = h->stage.p;
+        }
+        VCK(launch_feq_init(lvdev(h, level), src, ld, h->hc, h->stream));
+        if (!on_device) VCK(cudaStreamSynchronize(h->stream));
+    });
+}
+
+static vlbm_status pop_copy(vlbm_hier* h, int32_t level, double* f, int64_t ld, int32_t on_device, int to_ext) {
+    return run(h, [&] {
+        if (level < 0 || level >= h->nlev || !f) throw Fail{VLBM_ERR_ARG, "bad level or f"};
+        Level& L = h->lev[level];
+        if (ld < L.nx) throw Fail{VLBM_ERR_ARG, "ld < nx"};
+        const size_t n = (size_t)16 * ld * L.ny;
+        double* ext = f;
+        if (!on_device) {
+            h->stage.ensure(h->mem, n);
+            ext = h->stage.p;
+            if (!to_ext) VCK(cudaMemcpyAsync(ext, f, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        }
+        VCK(launch_copy_pop(lvdev(h, level), ext, ld, to_ext, h->stream));
+        if (!on_device && to_ext) VCK(cudaMemcpyAsync(f, ext, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        VCK(cudaStreamSynchronize(h->stream));
+    });
+}
+
+vlbm_status vlbm_set_populations(vlbm_hier* h, int32_t level, const double* f, int64_t ld, int32_t on_device) {
+    return pop_copy(h, level, const_cast<double*>(f), ld, on_device, 0);
+}
+
+vlbm_status vlbm_get_populations(vlbm_hier* h, int32_t level, double* f, int64_t ld, int32_t on_device) {
+    return pop_copy(h, level, f, ld, on_device, 1);
+}
+
+vlbm_status vlbm_advance(vlbm_hier* h, int64_t coarse_steps) {
+    return run(h, [&] {
+        if (coarse_steps < 0) throw Fail{VLBM_ERR_ARG, "negative step count"};
+        if (h->engine) throw Fail{VLBM_ERR_ARG, "hierarchy is resident in an engine"};
+        if (coarse_steps == 0) return;
+        ensure_own_batch(h);
+        h->own->advance(coarse_steps, h->stream);
+        h->steps += coarse_steps;
+    });
+}
+
+vlbm_status vlbm_sync(vlbm_hier* h) {
+    return run(h, [&] {
+        VCK(cudaStreamSynchronize(h->stream));
+        check_status(h);
+    });
+}
+
+// Deterministic totals over the active cells of every level (two passes,
+// compensated sums); one 64-byte read-back.
+static void audit_impl(vlbm_hier* h, double* totals, double* abs_totals) {
+    if (!h->hout) VCK(cudaMallocHost((void**)&h->hout, 8 * sizeof(double)));
+    VCK(launch_audit(h->atab.p, h->aitems.p, (int)h->aitems.n, h->partial.p, h->tot.p, h->stream));
+    VCK(cudaMemcpyAsync(h->hout, h->tot.p, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    VCK(cudaStreamSynchronize(h->stream));
+    if (totals) std::memcpy(totals, h->hout, 4 * sizeof(double));
+    if (abs_totals) std::memcpy(abs_totals, h->hout + 4, 4 * sizeof(double));
+}
+
+vlbm_status vlbm_audit(vlbm_hier* h, double totals[4], double abs_totals[4]) {
+    return run(h, [&] {
+        audit_impl(h, totals, abs_totals);
+        check_status(h);
+    });
+}
+
+vlbm_status vlbm_get_conserved(vlbm_hier* h, int32_t level, double* W, int64_t ld, uint8_t* valid, double totals[4],
+                               double abs_totals[4]) {
+    return run(h, [&] {
+        if (level < 0 || level >= h->nlev) throw Fail{VLBM_ERR_ARG, "bad level"};
+        Level& L = h->lev[level];
+        check_status(h);
+        if (W || valid) {
+            const long long ldd = W ? ld : L.nx;
+            if (W && ld < L.nx) throw Fail{VLBM_ERR_ARG, "ld < nx"};
+            const size_t n = (size_t)4 * ldd * L.ny;
+            h->stage.ensure(h->mem, n);
+            h->stage8.ensure(h->mem, (size_t)L.nx * L.ny);
+            VCK(launch_gather_W(lvdev(h, level), h->stage.p, ldd, valid ? h->stage8.p : nullptr, h->stream));
+            if (W) VCK(cudaMemcpyAsync(W, h->stage.p, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+            if (valid)
+                VCK(cudaMemcpyAsync(valid, h->stage8.p, (size_t)L.nx * L.ny, cudaMemcpyDeviceToHost, h->stream));
+            VCK(cudaStreamSynchronize(h->stream));
+        }
+        if (totals || abs_totals) audit_impl(h, totals, abs_totals);
+    });
+}
+
+vlbm_status vlbm_get_layout(vlbm_hier* h, int32_t level, uint8_t* in, uint8_t* ref) {
+    return run(h, [&] {
+        if (level < 0 || level >= h->nlev) throw Fail{VLBM_ERR_ARG, "bad level"};
+        Level& L = h->lev[level];
+        for (int y = 0; y < L.ny; y++)
+            for (int x = 0; x < L.nx; x++) {
+                const size_t b = (size_t)(y / TILE) * L.bx + x / TILE;
+                if (in) in[(size_t)y * L.nx + x] = L.bin[b];
+                if (ref) ref[(size_t)y * L.nx + x] = L.bin[b] && L.bcov[b];
+            }
+    });
+}
+
+vlbm_status vlbm_regrid_masks(vlbm_hier* h, const uint8_t* const* ref) {
+    return run(h, [&] {
+        check_status(h);
+        std::vector<uint8_t> bcov[VLBM_MAX_LEVELS];
+        masks_to_maps(h, ref, bcov);
+        regrid_to(h, bcov, false);
+        invalidate(h);
+    });
+}
+
+vlbm_status vlbm_regrid(vlbm_hier* h, const vlbm_box* boxes, int32_t nboxes) {
+    return run(h, [&] {
+        check_status(h);
+        std::vector<uint8_t> bcov[VLBM_MAX_LEVELS];
+        if (boxes || nboxes > 0) {
+            if (nboxes < 0 || !boxes) throw Fail{VLBM_ERR_ARG, "bad boxes"};
+            boxes_to_maps(h, boxes, nboxes, bcov);
+            regrid_to(h, bcov, false);
+        } else {
+            if (!(h->cfg.tag_tol > 0.0) || h->cfg.tag_buffer < 0) throw Fail{VLBM_ERR_ARG, "no tagging parameters"};
+            cudaStream_t s = h->stream;
+            // average-down, then tag on every refinable level
+            for (int l = h->nlev - 2; l >= 0; l--) {
+                h->listbuf.upload(h->mem, h->lev[l].cov, s);
+                VCK(launch_avgdown(lvdev(h, l), lvdev(h, l + 1), h->listbuf.p, (int)h->listbuf.n, s));
+                VCK(cudaStreamSynchronize(s));
+            }
+            std::vector<uint8_t> bflag[VLBM_MAX_LEVELS];
+            const double tol2 = h->cfg.tag_tol * h->cfg.tag_tol;
+            const int px = h->cfg.bc[0] == VLBM_BC_PERIODIC, py = h->cfg.bc[2] == VLBM_BC_PERIODIC;
+            for (int l = 0; l <= h->nlev - 2; l++) {
+                Level& L = h->lev[l];
+                h->stage8.ensure(h->mem, (size_t)L.nx * L.ny);
+                VCK(cudaMemsetAsync(h->stage8.p, 0, (size_t)L.nx * L.ny, s));
+                h->listbuf.upload(h->mem, L.in, s);
+                VCK(launch_tag(lvdev(h, l), h->listbuf.p, (int)L.in.size(), tol2, h->stage8.p, s));
+                h->bflag.ensure(h->mem, (size_t)L.bx * L.by);
+                VCK(launch_blockflag(h->stage8.p, L.nx, L.ny, px, py, h->cfg.tag_buffer, h->bflag.p, s));
+                bflag[l].resize((size_t)L.bx * L.by);
+                VCK(cudaMemcpyAsync(bflag[l].data(), h->bflag.p, bflag[l].size(), cudaMemcpyDeviceToHost, s));
+                VCK(cudaStreamSynchronize(s));
+            }
+            layout_rule(h, bflag, bcov);
+            regrid_to(h, bcov, true);
+        }
+        invalidate(h);
+    });
+}
+
+vlbm_status vlbm_get_info(const vlbm_hier* h, vlbm_info* info) {
+    if (!h || !info) return VLBM_ERR_ARG;
+    std::memset(info, 0, sizeof *info);
+    info->nlev = h->nlev;
+    long long lups = 0;
+    for (int l = 0; l < h->nlev; l++) {
+        info->nx[l] = h->lev[l].nx;
+        info->ny[l] = h->lev[l].ny;
+        info->active_cells[l] = h->lev[l].active_cells;
+        lups += h->lev[l].active_cells << l;
+    }
+    info->lups_per_step = lups;
+    info->device_bytes = (int64_t)h->mem.bytes;
+    info->steps = h->steps;
+    info->c = h->cfg.c;
+    info->beta = h->cfg.beta;
+    info->gamma = h->cfg.gamma;
+    info->dx0 = h->cfg.dx0;
+    return VLBM_OK;
+}
+
+vlbm_status vlbm_profile(vlbm_hier* h, int64_t coarse_steps, vlbm_kernel_time* out, int32_t cap, int32_t* n) {
+    return run(h, [&] {
+        if (coarse_steps < 0 || !out || !n) throw Fail{VLBM_ERR_ARG, "bad profile arguments"};
+        if (h->engine) throw Fail{VLBM_ERR_ARG, "hierarchy is resident in an engine"};
+        ensure_own_batch(h);
+        long long cells[VLBM_MAX_LEVELS] = {};
+        for (int l = 0; l < h->nlev; l++) cells[l] = h->lev[l].active_cells;
+        std::vector<Batch::Rec> recs;
+        h->own->profile(coarse_steps, cells, recs, h->stream);
+        h->steps += coarse_steps;
+        if ((int)recs.size() > cap) throw Fail{VLBM_ERR_ARG, "record capacity too small"};
+        for (size_t i = 0; i < recs.size(); i++) {
+            out[i].kind = recs[i].kind;
+            out[i].level = recs[i].level;
+            out[i].launches = recs[i].launches;
+            out[i].cells = recs[i].cells;
+            out[i].ms = recs[i].ms;
+        }
+        *n = (int32_t)recs.size();
+    });
+}
+
+// ---- engine ------------------------------------------------------------------
+
+vlbm_status vlbm_engine_create(size_t mem_budget, void* stream, vlbm_engine** out) {
+    if (!out) return VLBM_ERR_ARG;
+    *out = nullptr;
+    vlbm_engine* e = new (std::nothrow) vlbm_engine();
+    if (!e) return VLBM_ERR_OOM;
+    e->budget = mem_budget;
+    if (stream) {
+        e->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete e;
+            return VLBM_ERR_CUDA;
+        }
+        e->own_stream = true;
+    }
+    e->mem.s = e->stream;
+    e->batch.mem = &e->mem;
+    *out = e;
+    return VLBM_OK;
+}
+
+vlbm_status vlbm_engine_usage(const vlbm_engine* e, int32_t* residents, int64_t* bytes) {
+    if (!e) return VLBM_ERR_ARG;
+    int n = 0;
+    long long b = 0;
+    for (const auto& r : e->res)
+        if (r.live) {
+            n++;
+            b += (long long)r.h->device_bytes();
+        }
+    if (residents) *residents = n;
+    if (bytes) *bytes = b;
+    return VLBM_OK;
+}
+
+vlbm_status vlbm_engine_admit(vlbm_engine* e, vlbm_hier* h, int64_t coarse_steps, int32_t regrid_every, int32_t* slot) {
+    if (!e || !h || coarse_steps < 0 || regrid_every < 0) return VLBM_ERR_ARG;
+    if (h->poisoned) return VLBM_ERR_STATE;
+    if (h->engine) return VLBM_ERR_ARG;
+    long long used = 0;
+    for (const auto& r : e->res)
+        if (r.live) used += (long long)r.h->device_bytes();
+    if (e->budget && (size_t)(used + (long long)h->device_bytes()) > e->budget) return VLBM_ERR_OOM;
+    // the hierarchy's own queue must be drained before it joins the engine
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return VLBM_ERR_CUDA;
+    int s = -1;
+    for (size_t i = 0; i < e->res.size(); i++)
+        if (!e->res[i].live) { s = (int)i; break; }
+    if (s < 0) {
+        s = (int)e->res.size();
+        e->res.emplace_back();
+    }
+    e->res[s].h = h;
+    e->res[s].target = coarse_steps;
+    e->res[s].done = 0;
+    e->res[s].regrid_every = regrid_every;
+    e->res[s].live = true;
+    h->engine = e;
+    e->dirty = true;
+    if (slot) *slot = s;
+    return VLBM_OK;
+}
+
+vlbm_status vlbm_engine_release(vlbm_engine* e, int32_t slot) {
+    if (!e || slot < 0 || slot >= (int)e->res.size() || !e->res[slot].live) return VLBM_ERR_ARG;
+    cudaStreamSynchronize(e->stream);
+    e->res[slot].h->engine = nullptr;
+    e->res[slot].live = false;
+    e->res[slot].h = nullptr;
+    e->dirty = true;
+    return VLBM_OK;
+}
+
+vlbm_status vlbm_engine_step(vlbm_engine* e, int32_t* finished, int32_t* nfinished) {
+    if (!e) return VLBM_ERR_ARG;
+    if (nfinished) *nfinished = 0;
+    try {
+        // adaptive residents regrid on their own schedule (between steps)
+        for (auto& r : e->res) {
+            if (!r.live || r.regrid_every <= 0 || !(r.h->cfg.tag_tol > 0)) continue;
+            if (r.done > 0 && r.done % r.regrid_every == 0 && r.done < r.target) {
+                VCK(cudaStreamSynchronize(e->stream));
+                vlbm_hier* h = r.h;
+                vlbm_engine* keep = h->engine;
+                h->engine = nullptr;  // regrid runs on the hierarchy's own stream
+                vlbm_status st = vlbm_regrid(h, nullptr, 0);
+                h->engine = keep;
+                e->dirty = true;
+                if (st != VLBM_OK) throw Fail{st, std::string("regrid: ") + h->err};
+            }
+        }
+        if (e->dirty) {
+            e->batch.members.clear();
+            for (auto& r : e->res)
+                if (r.live && r.done < r.target) e->batch.members.push_back(r.h);
+            if (!e->batch.members.empty()) e->batch.build(e->stream);
+            e->dirty = false;
+        }
+        if (!e->batch.members.empty()) VCK(cudaGraphLaunch(e->batch.exec1, e->stream));
+        int nf = 0;
+        for (size_t i = 0; i < e->res.size(); i++) {
+            auto& r = e->res[i];
+            if (!r.live || r.done >= r.target) continue;
+            r.done++;
+            r.h->steps++;
+            if (r.done == r.target) {
+                if (finished) finished[nf] = (int)i;
+                nf++;
+                e->dirty = true;
+            }
+        }
+        if (nfinished) *nfinished = nf;
+        if (nf) {
+            // results of finished residents are read by the caller: make the
+            // step visible and check the residents for non-physical states
+            VCK(cudaStreamSynchronize(e->stream));
+            for (size_t i = 0; i < e->res.size(); i++) {
+                auto& r = e->res[i];
+                if (!r.live || r.done != r.target) continue;
+                int st[2];
+                VCK(cudaMemcpy(st, r.h->words, sizeof st, cudaMemcpyDeviceToHost));
+                if (st[1]) r.h->poisoned = true, r.h->err = "non-physical state";
+            }
+        }
+        return VLBM_OK;
+    } catch (const Fail& f) {
+        e->err = f.msg;
+        return f.st;
+    }
+}
+
+void vlbm_engine_destroy(vlbm_engine* e) {
+    if (!e) return;
+    cudaStreamSynchronize(e->stream);
+    for (auto& r : e->res)
+        if (r.live && r.h) r.h->engine = nullptr;
+    e->batch.release();
+    cudaStreamSynchronize(e->stream);
+    if (e->own_stream) cudaStreamDestroy(e->stream);
+    delete e;
+}
+
+}  // extern "C"

@@ -1,0 +1,707 @@
+// CUDA kernels of the refined VLBM (sm_103a, FP64).
+//
+// Canonical arithmetic: every floating-point expression below is evaluated
+// as written, with fma() only where spelled out (the library is built with
+// --fmad=false).  The expression order is fixed so that results do not
+// depend on the launch configuration.
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "vlbm_dev.cuh"
+#include "vlbm_launch.h"
+
+namespace vlbm {
+
+__device__ __constant__ int kCX[4] = {1, -1, 0, 0};
+__device__ __constant__ int kCY[4] = {0, 0, 1, -1};
+
+// ---------------------------------------------------------------------------
+// single-cell operators (Sec. 2.1-2.2)
+// ---------------------------------------------------------------------------
+
+// Euler flux Q(W) with the ideal-gas closure (Sec. 2.1, Eq. 1).
+__device__ __forceinline__ void euler_flux(double gm1, const double W[4], double Qx[4], double Qy[4],
+                                           double& p_out) {
+    const double inv = 1.0 / W[0];
+    const double u = W[1] * inv;
+    const double v = W[2] * inv;
+    const double ruu = W[1] * u;
+    const double rvv = W[2] * v;
+    const double p = gm1 * fma(-0.5, ruu + rvv, W[3]);
+    const double H = W[3] + p;
+    Qx[0] = W[1];
+    Qx[1] = ruu + p;
+    Qx[2] = W[2] * u;
+    Qx[3] = H * u;
+    Qy[0] = W[2];
+    Qy[1] = W[1] * v;
+    Qy[2] = rvv + p;
+    Qy[3] = H * v;
+    p_out = p;
+}
+
+__device__ __forceinline__ bool physical(double rho, double p) {
+    const long long rb = __double_as_longlong(rho);
+    const long long pb = __double_as_longlong(p);
+    const long long inf = 0x7FF0000000000000LL;
+    return rb > 0 && rb < inf && pb > 0 && pb < inf;
+}
+
+// BGK relaxation (Eq. 6) in place: f <- 2 beta f^eq(W) + (1 - 2 beta) f with
+// 2 beta f^eq_{+-alpha} = (beta/2) W +- (beta/c) Q_alpha (Eq. 4, D = 2).
+__device__ __forceinline__ bool collide(double f[16], double om, double hb, double bcs, double gm1) {
+    double W[4], Qx[4], Qy[4], p;
+#pragma unroll
+    for (int k = 0; k < 4; k++) W[k] = (f[k] + f[4 + k]) + (f[8 + k] + f[12 + k]);
+    euler_flux(gm1, W, Qx, Qy, p);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const double A = hb * W[k];
+        f[k] = fma(bcs, Qx[k], fma(om, f[k], A));
+        f[4 + k] = fma(-bcs, Qx[k], fma(om, f[4 + k], A));
+        f[8 + k] = fma(bcs, Qy[k], fma(om, f[8 + k], A));
+        f[12 + k] = fma(-bcs, Qy[k], fma(om, f[12 + k], A));
+    }
+    return physical(W[0], p);
+}
+
+__device__ __forceinline__ double minmod(double a, double b) {
+    if (a > 0.0 && b > 0.0) return a < b ? a : b;
+    if (a < 0.0 && b < 0.0) return a > b ? a : b;
+    return 0.0;
+}
+
+__device__ __forceinline__ void level_bufs(const LevelDev& L, int kk, const double*& src, double*& dst) {
+    if (L.level == 0) {
+        const int par = *L.par0;
+        src = L.buf[par];
+        dst = L.buf[par ^ 1];
+    } else {
+        src = L.buf[kk == 1 ? 0 : 1];
+        dst = L.buf[kk == 1 ? 1 : 0];
+    }
+}
+
+// state / scratch buffer of a level at a sync point
+__device__ __forceinline__ int state_buf(const LevelDev& L) { return L.level == 0 ? *L.par0 : 0; }
+
+// ---------------------------------------------------------------------------
+// the fused level sweep: collide, push-stream, boundary and coarse-to-fine
+// ---------------------------------------------------------------------------
+
+// Boundary values and reconstructed coarse-to-fine values for the incoming
+// populations of a cell whose upwind neighbour is outside the domain or in
+// coarser territory.  fs holds the cell's post-collision populations.
+__device__ __noinline__ void sweep_special(const LevelDev* __restrict__ levs, const LevelDev& L, int x, int y,
+                                          long long c, uint32_t fl, const double* fs, double* dst, int kk,
+                                          int kkp) {
+    // boundary conditions
+    if (fl & F_BND) {
+        for (int i = 0; i < 4; i++) {
+            int side = -1;
+            if (i == 0 && x == 0 && !L.px) side = 0;
+            if (i == 1 && x == L.nx - 1 && !L.px) side = 1;
+            if (i == 2 && y == 0 && !L.py) side = 2;
+            if (i == 3 && y == L.ny - 1 && !L.py) side = 3;
+            if (side < 0) continue;
+            const int bc = L.bc[side];
+            const int normal = side < 2 ? 1 : 2;
+            for (int k = 0; k < 4; k++) {
+                double v;
+                if (bc == BC_OUTFLOW) {
+                    v = fs[4 * i + k];
+                } else if (bc == BC_INFLOW) {
+                    v = L.feqb[side][4 * i + k];
+                } else {
+                    const double m = fs[4 * (i ^ 1) + k];
+                    v = (k == normal) ? -m : m;
+                }
+                dst[(long long)(4 * i + k) * L.plane + c] = v;
+            }
+        }
+    }
+    // coarse-to-fine reconstruction (Sec. 3.3, Eqs. 22-23)
+    const uint32_t rec = (fl & F_RECON_MASK) >> F_RECON_SHIFT;
+    if (!rec) return;
+    const LevelDev& P = levs[L.parent];
+    const double* psrc;
+    double* pdst;
+    level_bufs(P, kkp, psrc, pdst);
+    const double wk = (kk == 1) ? -0.25 : 0.25;
+    for (int i = 0; i < 4; i++) {
+        if (!(rec & (1u << i))) continue;
+        int ux = x - kCX[i], uy = y - kCY[i];
+        if (ux < 0) ux += L.nx;
+        if (ux >= L.nx) ux -= L.nx;
+        if (uy < 0) uy += L.ny;
+        if (uy >= L.ny) uy -= L.ny;
+        const int l0x = ux >> 1, l0y = uy >> 1;  // coarse cell L0
+        const int hx = x >> 1, hy = y >> 1;      // covered cell C = L0 + c_d
+        const int d = i;
+        const int tx = d < 2 ? 0 : 1, ty = d < 2 ? 1 : 0;
+        int mx = l0x - tx, my = l0y - ty, qx = l0x + tx, qy = l0y + ty;
+        int hmx = hx - tx, hmy = hy - ty, hpx = hx + tx, hpy = hy + ty;
+        bool okm = true, okp = true;
+        if (tx) {
+            if (mx < 0) { if (P.px) { mx += P.nx; hmx += P.nx; } else okm = false; }
+            if (qx >= P.nx) { if (P.px) { qx -= P.nx; hpx -= P.nx; } else okp = false; }
+        } else {
+            if (my < 0) { if (P.py) { my += P.ny; hmy += P.ny; } else okm = false; }
+            if (qy >= P.ny) { if (P.py) { qy -= P.ny; hpy -= P.ny; } else okp = false; }
+        }
+        if (okm) okm = (P.flags[(long long)my * P.pitch + mx] & (F_IN | F_COV)) == F_IN;
+        if (okp) okp = (P.flags[(long long)qy * P.pitch + qx] & (F_IN | F_COV)) == F_IN;
+        const bool fresh = (P.flags[(long long)l0y * P.pitch + l0x] >> (F_FRESH_SHIFT + d)) & 1u;
+        const long long ch = (long long)hy * P.pitch + hx;
+        const long long cm = (long long)hmy * P.pitch + hmx;
+        const long long cp = (long long)hpy * P.pitch + hpx;
+        const int j = d < 2 ? (y & 1) : (x & 1);
+        const double wj = j ? 0.25 : -0.25;
+        for (int k = 0; k < 4; k++) {
+            const long long qo = (long long)(4 * d + k) * P.plane;
+            const double a = pdst[qo + ch];
+            const double ap = fresh ? a : psrc[qo + ch];
+            double s = 0.0;
+            if (okm && okp) s = minmod(a - pdst[qo + cm], pdst[qo + cp] - a);
+            dst[(long long)(4 * i + k) * L.plane + c] = fma(s, wj, fma(a - ap, wk, a));
+        }
+    }
+}
+
+// One step of one level for every tile in `items` (all of the same level
+// index within their hierarchies).  kk: this level's sub-step (1, 2) within
+// its parent's step (ignored on level 0); kkp: the parent's sub-step.
+__global__ void __launch_bounds__(CTA_THREADS, 2)
+sweep_kernel(const LevelDev* __restrict__ levs, const Item* __restrict__ items, int nitems, int kk, int kkp) {
+    const int sub = threadIdx.x >> 6;
+    const int cx = threadIdx.x & 7;
+    const int cy = (threadIdx.x >> 3) & 7;
+    for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
+        const Item w = items[it];
+        const LevelDev& L = levs[w.lid];
+        const int x = w.tx * TILE + cx;
+        const int y = w.ty * TILE + cy;
+        const int nx = L.nx, ny = L.ny;
+        if (x >= nx || y >= ny) continue;
+        const long long c = (long long)y * L.pitch + x;
+        const uint32_t fl = L.flags[c];
+        if ((fl & (F_IN | F_COV)) != F_IN) continue;
+        const double* src;
+        double* dst;
+        level_bufs(L, kk, src, dst);
+        const long long plane = L.plane;
+        double f[16];
+#pragma unroll
+        for (int q = 0; q < 16; q++) f[q] = __ldg(src + q * plane + c);
+        if (!collide(f, L.om, L.hb, L.bcs, L.gm1)) atomicOr(L.status, ST_NONPHYS);
+        // push streaming (Eq. 5): f*_i lands on x + c_i
+        long long cxp = c + 1, cxm = c - 1, cyp = c + L.pitch, cym = c - L.pitch;
+        bool oxp = true, oxm = true, oyp = true, oym = true;
+        if (x == nx - 1) { if (L.px) cxp = c - (nx - 1); else oxp = false; }
+        if (x == 0) { if (L.px) cxm = c + (nx - 1); else oxm = false; }
+        if (y == ny - 1) { if (L.py) cyp = c - (long long)(ny - 1) * L.pitch; else oyp = false; }
+        if (y == 0) { if (L.py) cym = c + (long long)(ny - 1) * L.pitch; else oym = false; }
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            if (oxp) dst[(0 + k) * plane + cxp] = f[0 + k];
+            if (oxm) dst[(4 + k) * plane + cxm] = f[4 + k];
+            if (oyp) dst[(8 + k) * plane + cyp] = f[8 + k];
+            if (oym) dst[(12 + k) * plane + cym] = f[12 + k];
+        }
+        if (fl & (F_BND | F_RECON_MASK)) sweep_special(levs, L, x, y, c, fl, f, dst, kk, kkp);
+    }
+}
+
+// Reflux (Sec. 3.3, Eq. 24): the pending incoming population of every coarse
+// ring cell is the plain average of the four post-collision values the fine
+// edge cells sent towards it during the cycle, summed (k = 1: j = 0, 1), then
+// (k = 2: j = 0, 1).  Also retires the "no previous sample" marks.
+__global__ void close_kernel(const LevelDev* __restrict__ levs, const Item* __restrict__ items, int nitems, int kk) {
+    const int sub = threadIdx.x >> 6;
+    const int cx = threadIdx.x & 7;
+    const int cy = (threadIdx.x >> 3) & 7;
+    for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
+        const Item w = items[it];
+        const LevelDev& L = levs[w.lid];
+        const int x = w.tx * TILE + cx;
+        const int y = w.ty * TILE + cy;
+        if (x >= L.nx || y >= L.ny) continue;
+        const long long c = (long long)y * L.pitch + x;
+        const uint32_t fl = L.flags[c];
+        const uint32_t pend = (fl & F_PEND_MASK) >> F_PEND_SHIFT;
+        if ((fl & (F_IN | F_COV)) != F_IN || !pend) continue;
+        const double* src;
+        double* dst;
+        level_bufs(L, kk, src, dst);
+        const LevelDev& F = levs[L.child];
+        const double* s1 = F.buf[1];  // fine sub-step 1 wrote buffer 1
+        const double* s2 = F.buf[0];  // fine sub-step 2 wrote buffer 0
+        for (int i = 0; i < 4; i++) {
+            if (!(pend & (1u << i))) continue;
+            const int d = i ^ 1;  // from this cell towards the covered one
+            int gx0, gy0, gx1, gy1;
+            if (d == 0) { gx0 = gx1 = 2 * x + 1; gy0 = 2 * y; gy1 = 2 * y + 1; }
+            else if (d == 1) { gx0 = gx1 = 2 * x; gy0 = 2 * y; gy1 = 2 * y + 1; }
+            else if (d == 2) { gy0 = gy1 = 2 * y + 1; gx0 = 2 * x; gx1 = 2 * x + 1; }
+            else { gy0 = gy1 = 2 * y; gx0 = 2 * x; gx1 = 2 * x + 1; }
+            const long long g0 = (long long)gy0 * F.pitch + gx0;
+            const long long g1 = (long long)gy1 * F.pitch + gx1;
+            for (int k = 0; k < 4; k++) {
+                const long long qo = (long long)(4 * i + k) * F.plane;
+                const double v = ((s1[qo + g0] + s1[qo + g1]) + (s2[qo + g0] + s2[qo + g1])) * 0.25;
+                dst[(long long)(4 * i + k) * L.plane + c] = v;
+            }
+        }
+        if (fl & F_FRESH_MASK) L.flags[c] = (uint16_t)(fl & ~F_FRESH_MASK);
+    }
+}
+
+__global__ void end_step_kernel(int* const* par, int n) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) *par[t] ^= 1;
+}
+
+// ---------------------------------------------------------------------------
+// initialisation and read-back
+// ---------------------------------------------------------------------------
+
+// f = f^eq(W) on every cell of the level (Eq. 4): W/4 +- Q_alpha/(2c).
+__global__ void feq_init_kernel(LevelDev L, const double* __restrict__ W, long long ld, double hc) {
+    const long long n = (long long)L.nx * L.ny;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(t % L.nx), y = (int)(t / L.nx);
+        const long long c = (long long)y * L.pitch + x;
+        if (!(L.flags[c] & F_IN)) continue;
+        double w[4], Qx[4], Qy[4], p;
+        const long long pl = ld * L.ny;
+        for (int k = 0; k < 4; k++) w[k] = W[k * pl + (long long)y * ld + x];
+        euler_flux(L.gm1, w, Qx, Qy, p);
+        double* out = L.buf[state_buf(L)];
+        for (int k = 0; k < 4; k++) {
+            const double qw = 0.25 * w[k];
+            out[(0 + k) * L.plane + c] = fma(hc, Qx[k], qw);
+            out[(4 + k) * L.plane + c] = fma(-hc, Qx[k], qw);
+            out[(8 + k) * L.plane + c] = fma(hc, Qy[k], qw);
+            out[(12 + k) * L.plane + c] = fma(-hc, Qy[k], qw);
+        }
+    }
+}
+
+// population planes <-> a dense [16][ny][ld] array (state buffer)
+__global__ void copy_pop_kernel(LevelDev L, double* __restrict__ ext, long long ld, int to_ext) {
+    const long long n = (long long)L.nx * L.ny;
+    double* st = L.buf[state_buf(L)];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(t % L.nx), y = (int)(t / L.nx);
+        const long long c = (long long)y * L.pitch + x;
+        for (int q = 0; q < 16; q++) {
+            const long long e = (long long)q * ld * L.ny + (long long)y * ld + x;
+            if (to_ext) ext[e] = st[q * L.plane + c];
+            else st[q * L.plane + c] = ext[e];
+        }
+    }
+}
+
+// W = sum_i f_i (same order as the collision) and the active mask.
+__global__ void gather_W_kernel(LevelDev L, double* __restrict__ W, long long ld, uint8_t* __restrict__ valid) {
+    const long long n = (long long)L.nx * L.ny;
+    const double* st = L.buf[state_buf(L)];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(t % L.nx), y = (int)(t / L.nx);
+        const long long c = (long long)y * L.pitch + x;
+        const uint32_t fl = L.flags[c];
+        const long long pl = ld * L.ny;
+        const long long o = (long long)y * ld + x;
+        for (int k = 0; k < 4; k++) {
+            double v = 0.0;
+            if (fl & F_IN)
+                v = (st[(0 + k) * L.plane + c] + st[(4 + k) * L.plane + c]) +
+                    (st[(8 + k) * L.plane + c] + st[(12 + k) * L.plane + c]);
+            W[k * pl + o] = v;
+        }
+        if (valid) valid[(long long)y * L.nx + x] = (fl & (F_IN | F_COV)) == F_IN;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// conservation audit: deterministic compensated sums
+// ---------------------------------------------------------------------------
+
+struct CSum {
+    double s, c;
+};
+
+__device__ __forceinline__ void csum_add(CSum& a, double x) {
+    const double t = a.s + x;
+    if (fabs(a.s) >= fabs(x)) a.c += (a.s - t) + x;
+    else a.c += (x - t) + a.s;
+    a.s = t;
+}
+
+__device__ __forceinline__ CSum csum_join(CSum a, CSum b) {
+    CSum r;
+    r.s = a.s;
+    r.c = a.c + b.c;
+    csum_add(r, b.s);
+    return r;
+}
+
+// Pass 1: per-CTA partial sums over active cells of the listed tiles:
+// out[blk][0..3] = sum w W_k, out[blk][4..7] = sum w |W_k| (w = 4^-level),
+// as (sum, compensation) pairs.
+__global__ void __launch_bounds__(256) audit_kernel(const LevelDev* __restrict__ levs, const Item* __restrict__ items,
+                                                    int nitems, double* __restrict__ partial) {
+    CSum acc[8];
+    for (int m = 0; m < 8; m++) acc[m] = {0.0, 0.0};
+    const int sub = threadIdx.x >> 6;
+    const int cx = threadIdx.x & 7;
+    const int cy = (threadIdx.x >> 3) & 7;
+    for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
+        const Item w = items[it];
+        const LevelDev& L = levs[w.lid];
+        const int x = w.tx * TILE + cx, y = w.ty * TILE + cy;
+        if (x >= L.nx || y >= L.ny) continue;
+        const long long c = (long long)y * L.pitch + x;
+        if ((L.flags[c] & (F_IN | F_COV)) != F_IN) continue;
+        const double* st = L.buf[state_buf(L)];
+        for (int k = 0; k < 4; k++) {
+            const double v = ((st[(0 + k) * L.plane + c] + st[(4 + k) * L.plane + c]) +
+                              (st[(8 + k) * L.plane + c] + st[(12 + k) * L.plane + c])) * L.wscale;
+            csum_add(acc[k], v);
+            csum_add(acc[4 + k], fabs(v));
+        }
+    }
+    __shared__ CSum sh[8][8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int m = 0; m < 8; m++) {
+        CSum a = acc[m];
+        for (int o = 16; o > 0; o >>= 1) {
+            CSum b;
+            b.s = __shfl_down_sync(0xffffffffu, a.s, o);
+            b.c = __shfl_down_sync(0xffffffffu, a.c, o);
+            if (lane < o) a = csum_join(a, b);
+        }
+        if (lane == 0) sh[wid][m] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        const int m = threadIdx.x;
+        CSum a = sh[0][m];
+        for (int w2 = 1; w2 < (int)(blockDim.x >> 5); w2++) a = csum_join(a, sh[w2][m]);
+        partial[blockIdx.x * 16 + 2 * m] = a.s;
+        partial[blockIdx.x * 16 + 2 * m + 1] = a.c;
+    }
+}
+
+// Pass 2: one thread per quantity sums the partials in block order.
+__global__ void audit_final_kernel(const double* __restrict__ partial, int nblk, double* __restrict__ out) {
+    const int m = threadIdx.x;
+    if (m >= 8) return;
+    CSum a = {0.0, 0.0};
+    for (int b = 0; b < nblk; b++) {
+        CSum p = {partial[b * 16 + 2 * m], partial[b * 16 + 2 * m + 1]};
+        a = csum_join(a, p);
+    }
+    out[m] = a.s + a.c;
+}
+
+// ---------------------------------------------------------------------------
+// adaptive refinement (Sec. 3.4)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ const double* composite_src(const LevelDev& L, uint32_t fl) {
+    // active cells: state buffer; covered cells: the average of their
+    // children, kept in the other buffer by avgdown_kernel
+    const int sb = state_buf(L);
+    return ((fl & (F_IN | F_COV)) == (F_IN | F_COV)) ? L.buf[sb ^ 1] : L.buf[sb];
+}
+
+// Average-down (Eq. 25) of every covered cell of level C from its children
+// on level F: ((c00 + c11) + (c10 + c01)) / 4, into C's scratch buffer.
+__global__ void avgdown_kernel(LevelDev C, LevelDev F, const Item* __restrict__ items, int nitems) {
+    const int sub = threadIdx.x >> 6, cx = threadIdx.x & 7, cy = (threadIdx.x >> 3) & 7;
+    for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
+        const Item w = items[it];
+        const int x = w.tx * TILE + cx, y = w.ty * TILE + cy;
+        if (x >= C.nx || y >= C.ny) continue;
+        const long long c = (long long)y * C.pitch + x;
+        if ((C.flags[c] & (F_IN | F_COV)) != (F_IN | F_COV)) continue;
+        double* out = C.buf[state_buf(C) ^ 1];
+        const long long k00 = (long long)(2 * y) * F.pitch + 2 * x;
+        const long long k10 = k00 + 1, k01 = k00 + F.pitch, k11 = k01 + 1;
+        const double* p00 = composite_src(F, F.flags[k00]);
+        const double* p10 = composite_src(F, F.flags[k10]);
+        const double* p01 = composite_src(F, F.flags[k01]);
+        const double* p11 = composite_src(F, F.flags[k11]);
+        for (int q = 0; q < 16; q++) {
+            const long long o = (long long)q * F.plane;
+            out[(long long)q * C.plane + c] = ((p00[o + k00] + p11[o + k11]) + (p10[o + k10] + p01[o + k01])) * 0.25;
+        }
+    }
+}
+
+__device__ __forceinline__ double comp_rho(const LevelDev& L, long long c) {
+    const uint32_t fl = L.flags[c];
+    const double* s = composite_src(L, fl);
+    return (s[0 * L.plane + c] + s[4 * L.plane + c]) + (s[8 * L.plane + c] + s[12 * L.plane + c]);
+}
+
+// Normalised density-gradient indicator: tag when
+// (rho_E - rho_W)^2 + (rho_N - rho_S)^2 > tol^2 (2 rho_C)^2; neighbours off
+// the level or beyond a non-periodic side take rho_C.
+__global__ void tag_kernel(LevelDev L, const Item* __restrict__ items, int nitems, double tol2, uint8_t* __restrict__ tags) {
+    const int sub = threadIdx.x >> 6, cx = threadIdx.x & 7, cy = (threadIdx.x >> 3) & 7;
+    for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
+        const Item w = items[it];
+        const int x = w.tx * TILE + cx, y = w.ty * TILE + cy;
+        if (x >= L.nx || y >= L.ny) continue;
+        const long long c = (long long)y * L.pitch + x;
+        if (!(L.flags[c] & F_IN)) continue;
+        const double rc = comp_rho(L, c);
+        double rn[4];
+        for (int d = 0; d < 4; d++) {
+            int xx = x + kCX[d], yy = y + kCY[d];
+            bool ok = true;
+            if (xx < 0) { if (L.px) xx += L.nx; else ok = false; }
+            if (xx >= L.nx) { if (L.px) xx -= L.nx; else ok = false; }
+            if (yy < 0) { if (L.py) yy += L.ny; else ok = false; }
+            if (yy >= L.ny) { if (L.py) yy -= L.ny; else ok = false; }
+            const long long cn = (long long)yy * L.pitch + xx;
+            rn[d] = (ok && (L.flags[cn] & F_IN)) ? comp_rho(L, cn) : rc;
+        }
+        const double d1 = rn[0] - rn[1];
+        const double d2 = rn[2] - rn[3];
+        const double num = d1 * d1 + d2 * d2;
+        const double t = 2.0 * rc;
+        tags[(long long)y * L.nx + x] = num > tol2 * (t * t);
+    }
+}
+
+// A block (8 x 8 cells) is flagged when any tagged cell lies within
+// `buffer` cells (square neighbourhood) of it.
+__global__ void blockflag_kernel(const uint8_t* __restrict__ tags, int nx, int ny, int px, int py, int buffer,
+                                 uint8_t* __restrict__ out) {
+    const int bx = (nx + TILE - 1) / TILE, by = (ny + TILE - 1) / TILE;
+    const long long nb = (long long)bx * by;
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb; b += (long long)gridDim.x * blockDim.x) {
+        const int ib = (int)(b % bx), jb = (int)(b / bx);
+        uint8_t any = 0;
+        // the block's cells inside the domain, widened by `buffer`
+        const int ye = min(jb * TILE + TILE, ny) + buffer;
+        const int xe = min(ib * TILE + TILE, nx) + buffer;
+        for (int y = jb * TILE - buffer; y < ye && !any; y++) {
+            int yy = y;
+            if (yy < 0 || yy >= ny) {
+                if (!py) continue;
+                yy = (yy + ny) % ny;
+            }
+            for (int x = ib * TILE - buffer; x < xe; x++) {
+                int xx = x;
+                if (xx < 0 || xx >= nx) {
+                    if (!px) continue;
+                    xx = (xx + nx) % nx;
+                }
+                if (tags[(long long)yy * nx + xx]) { any = 1; break; }
+            }
+        }
+        out[b] = any;
+    }
+}
+
+// Cells leaving refinement take their merged value (Eq. 25).
+__global__ void merge_kernel(LevelDev L, const Item* __restrict__ items, int nitems) {
+    const int sub = threadIdx.x >> 6, cx = threadIdx.x & 7, cy = (threadIdx.x >> 3) & 7;
+    for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
+        const Item w = items[it];
+        const int x = w.tx * TILE + cx, y = w.ty * TILE + cy;
+        if (x >= L.nx || y >= L.ny) continue;
+        const long long c = (long long)y * L.pitch + x;
+        const int sb = state_buf(L);
+        for (int q = 0; q < 16; q++) L.buf[sb][q * L.plane + c] = L.buf[sb ^ 1][q * L.plane + c];
+    }
+}
+
+// Cells entering refinement are split (Eqs. 26-27): per population,
+// sigma_x = minmod(f - f_W, f_E - f), sigma_y likewise, child (a, b) =
+// f + (sigma_x xi_a + sigma_y xi_b), xi = -1/4, +1/4.  Neighbours that were
+// covered before the regrid contribute their children's average; beyond a
+// non-periodic side the slope is zero.  Uses the layout from before the
+// regrid (flags are rebuilt afterwards).
+__global__ void split_kernel(LevelDev C, LevelDev F, const Item* __restrict__ items, int nitems) {
+    const int sub = threadIdx.x >> 6, cx = threadIdx.x & 7, cy = (threadIdx.x >> 3) & 7;
+    for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
+        const Item w = items[it];
+        const int x = w.tx * TILE + cx, y = w.ty * TILE + cy;
+        if (x >= C.nx || y >= C.ny) continue;
+        const long long c = (long long)y * C.pitch + x;
+        long long nb[4];
+        bool ok[4];
+        for (int d = 0; d < 4; d++) {
+            int xx = x + kCX[d], yy = y + kCY[d];
+            ok[d] = true;
+            if (xx < 0) { if (C.px) xx += C.nx; else ok[d] = false; }
+            if (xx >= C.nx) { if (C.px) xx -= C.nx; else ok[d] = false; }
+            if (yy < 0) { if (C.py) yy += C.ny; else ok[d] = false; }
+            if (yy >= C.ny) { if (C.py) yy -= C.ny; else ok[d] = false; }
+            nb[d] = ok[d] ? (long long)yy * C.pitch + xx : c;
+        }
+        const double* st = C.buf[state_buf(C)];
+        const double* nsrc[4];
+        for (int d = 0; d < 4; d++) nsrc[d] = ok[d] ? composite_src(C, C.flags[nb[d]]) : st;
+        double* fo = F.buf[state_buf(F)];
+        const long long k00 = (long long)(2 * y) * F.pitch + 2 * x;
+        for (int q = 0; q < 16; q++) {
+            const long long o = (long long)q * C.plane;
+            const double fc = st[o + c];
+            const double vE = nsrc[0][o + nb[0]], vW = nsrc[1][o + nb[1]];
+            const double vN = nsrc[2][o + nb[2]], vS = nsrc[3][o + nb[3]];
+            const double sx = (ok[0] && ok[1]) ? minmod(fc - vW, vE - fc) : 0.0;
+            const double sy = (ok[2] && ok[3]) ? minmod(fc - vS, vN - fc) : 0.0;
+            const long long of = (long long)q * F.plane;
+            fo[of + k00] = fc + (sx * -0.25 + sy * -0.25);
+            fo[of + k00 + 1] = fc + (sx * 0.25 + sy * -0.25);
+            fo[of + k00 + F.pitch] = fc + (sx * -0.25 + sy * 0.25);
+            fo[of + k00 + F.pitch + 1] = fc + (sx * 0.25 + sy * 0.25);
+        }
+    }
+}
+
+// Per-cell flags of a level from its block maps (blk_in, blk_cov: one byte
+// per 8 x 8 block).  Faces that exist now but did not exist under the old
+// flags have no previous sample.
+__global__ void flags_kernel(LevelDev L, const uint8_t* __restrict__ blk_in, const uint8_t* __restrict__ blk_cov,
+                             const uint16_t* __restrict__ oldf, uint16_t* __restrict__ newf) {
+    const int bx = (L.nx + TILE - 1) / TILE;
+    const long long n = (long long)L.pitch * L.ny;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(t % L.pitch), y = (int)(t / L.pitch);
+        if (x >= L.nx) { newf[t] = 0; continue; }
+        const long long b = (long long)(y / TILE) * bx + x / TILE;
+        const bool in = blk_in[b], cov = in && blk_cov[b];
+        uint32_t fl = (in ? F_IN : 0u) | (cov ? F_COV : 0u);
+        if (in && !cov) {
+            const uint32_t ofl = oldf[t];
+            const bool oact = (ofl & (F_IN | F_COV)) == F_IN;
+            for (int i = 0; i < 4; i++) {
+                // upwind neighbour of direction i (the one that feeds it)
+                int ux = x - kCX[i], uy = y - kCY[i];
+                bool inside = true;
+                if (ux < 0) { if (L.px) ux += L.nx; else inside = false; }
+                if (ux >= L.nx) { if (L.px) ux -= L.nx; else inside = false; }
+                if (uy < 0) { if (L.py) uy += L.ny; else inside = false; }
+                if (uy >= L.ny) { if (L.py) uy -= L.ny; else inside = false; }
+                if (!inside) { fl |= F_BND; continue; }
+                const long long ub = (long long)(uy / TILE) * bx + ux / TILE;
+                const bool uin = blk_in[ub], ucov = uin && blk_cov[ub];
+                if (!uin) fl |= 1u << (F_RECON_SHIFT + i);
+                else if (ucov) {
+                    fl |= 1u << (F_PEND_SHIFT + i);
+                    // face (x, d) with d = i ^ 1 points at the covered cell u
+                    const int d = i ^ 1;
+                    const long long uc = (long long)uy * L.pitch + ux;
+                    const bool existed = oact && ((oldf[uc] & (F_IN | F_COV)) == (F_IN | F_COV));
+                    const bool was_fresh = (ofl >> (F_FRESH_SHIFT + d)) & 1u;
+                    if (!existed || was_fresh) fl |= 1u << (F_FRESH_SHIFT + d);
+                }
+            }
+        }
+        newf[t] = (uint16_t)fl;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
+static inline int tile_grid(int nitems, int max_ctas) {
+    int g = (nitems + TILES_PER_CTA - 1) / TILES_PER_CTA;
+    if (max_ctas > 0 && g > max_ctas) g = max_ctas;
+    return g < 1 ? 1 : g;
+}
+
+static inline int flat_grid(long long n) {
+    long long g = (n + 255) / 256;
+    if (g > 148LL * 16) g = 148LL * 16;
+    return (int)(g < 1 ? 1 : g);
+}
+
+cudaError_t launch_sweep(const LevelDev* levs, const Item* items, int n, int kk, int kkp, int max_ctas, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    sweep_kernel<<<tile_grid(n, max_ctas), CTA_THREADS, 0, s>>>(levs, items, n, kk, kkp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_close(const LevelDev* levs, const Item* items, int n, int kk, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    close_kernel<<<tile_grid(n, 0), CTA_THREADS, 0, s>>>(levs, items, n, kk);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_end_step(int* const* par, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    end_step_kernel<<<(n + 127) / 128, 128, 0, s>>>(par, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_feq_init(const LevelDev& L, const double* W, long long ld, double hc, cudaStream_t s) {
+    feq_init_kernel<<<flat_grid((long long)L.nx * L.ny), 256, 0, s>>>(L, W, ld, hc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_pop(const LevelDev& L, double* ext, long long ld, int to_ext, cudaStream_t s) {
+    copy_pop_kernel<<<flat_grid((long long)L.nx * L.ny), 256, 0, s>>>(L, ext, ld, to_ext);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_W(const LevelDev& L, double* W, long long ld, uint8_t* valid, cudaStream_t s) {
+    gather_W_kernel<<<flat_grid((long long)L.nx * L.ny), 256, 0, s>>>(L, W, ld, valid);
+    return cudaGetLastError();
+}
+
+int audit_blocks(int nitems) { return tile_grid(nitems, 148 * 4); }
+
+cudaError_t launch_audit(const LevelDev* levs, const Item* items, int n, double* partial, double* out, cudaStream_t s) {
+    const int g = audit_blocks(n);
+    if (n > 0) audit_kernel<<<g, 256, 0, s>>>(levs, items, n, partial);
+    else cudaMemsetAsync(partial, 0, sizeof(double) * 16 * g, s);
+    audit_final_kernel<<<1, 32, 0, s>>>(partial, n > 0 ? g : 1, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_avgdown(const LevelDev& C, const LevelDev& F, const Item* items, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    avgdown_kernel<<<tile_grid(n, 0), CTA_THREADS, 0, s>>>(C, F, items, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tag(const LevelDev& L, const Item* items, int n, double tol2, uint8_t* tags, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    tag_kernel<<<tile_grid(n, 0), CTA_THREADS, 0, s>>>(L, items, n, tol2, tags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_blockflag(const uint8_t* tags, int nx, int ny, int px, int py, int buffer, uint8_t* out, cudaStream_t s) {
+    const long long nb = (long long)((nx + TILE - 1) / TILE) * ((ny + TILE - 1) / TILE);
+    blockflag_kernel<<<flat_grid(nb), 256, 0, s>>>(tags, nx, ny, px, py, buffer, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge(const LevelDev& L, const Item* items, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    merge_kernel<<<tile_grid(n, 0), CTA_THREADS, 0, s>>>(L, items, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split(const LevelDev& C, const LevelDev& F, const Item* items, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    split_kernel<<<tile_grid(n, 0), CTA_THREADS, 0, s>>>(C, F, items, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flags(const LevelDev& L, const uint8_t* blk_in, const uint8_t* blk_cov, const uint16_t* oldf,
+                         uint16_t* newf, cudaStream_t s) {
+    flags_kernel<<<flat_grid((long long)L.pitch * L.ny), 256, 0, s>>>(L, blk_in, blk_cov, oldf, newf);
+    return cudaGetLastError();
+}
+
+}  // namespace vlbm

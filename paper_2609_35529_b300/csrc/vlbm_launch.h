@@ -1,0 +1,27 @@
+// Host-side declarations of the kernel launchers (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "vlbm_dev.cuh"
+
+namespace vlbm {
+
+cudaError_t launch_sweep(const LevelDev* levs, const Item* items, int n, int kk, int kkp, int max_ctas, cudaStream_t s);
+cudaError_t launch_close(const LevelDev* levs, const Item* items, int n, int kk, cudaStream_t s);
+cudaError_t launch_end_step(int* const* par, int n, cudaStream_t s);
+cudaError_t launch_feq_init(const LevelDev& L, const double* W, long long ld, double hc, cudaStream_t s);
+cudaError_t launch_copy_pop(const LevelDev& L, double* ext, long long ld, int to_ext, cudaStream_t s);
+cudaError_t launch_gather_W(const LevelDev& L, double* W, long long ld, uint8_t* valid, cudaStream_t s);
+int audit_blocks(int nitems);
+cudaError_t launch_audit(const LevelDev* levs, const Item* items, int n, double* partial, double* out, cudaStream_t s);
+cudaError_t launch_avgdown(const LevelDev& C, const LevelDev& F, const Item* items, int n, cudaStream_t s);
+cudaError_t launch_tag(const LevelDev& L, const Item* items, int n, double tol2, uint8_t* tags, cudaStream_t s);
+cudaError_t launch_blockflag(const uint8_t* tags, int nx, int ny, int px, int py, int buffer, uint8_t* out,
+                             cudaStream_t s);
+cudaError_t launch_merge(const LevelDev& L, const Item* items, int n, cudaStream_t s);
+cudaError_t launch_split(const LevelDev& C, const LevelDev& F, const Item* items, int n, cudaStream_t s);
+cudaError_t launch_flags(const LevelDev& L, const uint8_t* blk_in, const uint8_t* blk_cov, const uint16_t* oldf,
+                         uint16_t* newf, cudaStream_t s);
+
+}  // namespace vlbm

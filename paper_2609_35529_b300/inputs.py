@@ -224,7 +224,7 @@ def vortex_state(X, Y, L=10.0, strength=5.0, rc=1.0, xc=5.0, yc=5.0, uinf=1.0, v
     return conserved(rho, uinf + du, vinf + dv, p, gamma)
 
 
-def vortex(N=128, steps=None, beta=1.0, periods=1.0, gamma=GAMMA, patch=True):
+def vortex(N=128, steps=None, beta=1.0, periods=1.0, gamma=GAMMA, patch=True, fine_state=True):
     """Advected isentropic vortex on the periodic square [0,10]^2, strength 5,
     free stream (1, 1), N x N coarse cells, a ratio-2 patch over the central
     N/2 x N/2 coarse cells (25 % of the area).  `steps` defaults to one full
@@ -233,7 +233,7 @@ def vortex(N=128, steps=None, beta=1.0, periods=1.0, gamma=GAMMA, patch=True):
     dx0 = L / N
     nlev = 2 if patch else 1
     refs = box_refs(N, N, 2, [(0, N // 4, N // 4, N // 2, N // 2)]) if patch else []
-    Ws = fill_levels(N, N, nlev, dx0, lambda X, Y: vortex_state(X, Y, L=L, gamma=gamma))
+    Ws = fill_levels(N, N, nlev if fine_state else 1, dx0, lambda X, Y: vortex_state(X, Y, L=L, gamma=gamma))
     c_phys = link_speed([Ws[0]], gamma)          # physical link speed
     dt = dx0 / c_phys
     if steps is None:
@@ -261,7 +261,8 @@ def quadrant_state(X, Y, states, gamma=GAMMA, xm=0.5, ym=0.5):
     return out
 
 
-def riemann3(N=1024, nlev=3, t_end=0.3, steps=None, beta=0.9, widths=None, gamma=GAMMA, states=None):
+def riemann3(N=1024, nlev=3, t_end=0.3, steps=None, beta=0.7, widths=None, gamma=GAMMA, states=None, safety=1.1,
+             fine_state=True):
     """Four-quadrant Riemann problem on [0,1]^2 (zero-gradient outflow on all
     sides), N x N coarse cells, static levels over the diagonal band
     |x - y| <= w (about 15 % of the area on level 1, nested narrower bands
@@ -272,8 +273,8 @@ def riemann3(N=1024, nlev=3, t_end=0.3, steps=None, beta=0.9, widths=None, gamma
         widths = [0.08, 0.04, 0.02][: nlev - 1]
     bc = (BC_OUTFLOW,) * 4
     refs = nested_band_refs(N, N, nlev, widths, block=8, bc=bc) if nlev > 1 else []
-    Ws = fill_levels(N, N, nlev, dx0, lambda X, Y: quadrant_state(X, Y, states, gamma))
-    c = link_speed([Ws[0]], gamma)
+    Ws = fill_levels(N, N, nlev if fine_state else 1, dx0, lambda X, Y: quadrant_state(X, Y, states, gamma))
+    c = link_speed([Ws[0]], gamma, safety=safety)
     if steps is None:
         steps = int(math.ceil(t_end * c / dx0))
     return Case("riemann3", N, N, nlev, bc, gamma, c, beta, Ws, refs, steps, dx0=dx0)
@@ -291,7 +292,7 @@ def normal_shock(mach, rho1=1.0, p1=1.0, gamma=GAMMA):
     return rho2, u2, p2, s
 
 
-def shockbubble(nx0=2048, ny0=1024, nlev=3, steps=4000, beta=0.9, tol=0.02, buffer=2, every=4,
+def shockbubble(nx0=2048, ny0=1024, nlev=3, steps=4000, beta=0.7, tol=0.02, buffer=2, every=4,
                 mach=1.22, bubble_rho=0.14, gamma=GAMMA):
     """Mach 1.22 planar shock (at x = 0.25, moving +x) into a circular bubble
     of density ratio 0.14, radius H/8, centred at (0.5, 0.5) on [0,2]x[0,1].

@@ -1,0 +1,208 @@
+"""Continuous-batching request loop over the VLBM engine.
+
+Requests (2-D Riemann quadrant problems or isentropic vortices of different
+sizes and refinement layouts) arrive by a seeded Poisson process.  The loop
+admits arrived requests while the engine's device-memory budget allows,
+advances every resident request by one coarse step per engine step (one
+CUDA-graph launch per step for the whole batch), and returns each result to
+the host as soon as its step count is met; freed memory admits the next
+requests.  The same arrival trace can be served one request at a time
+(each request alone on the GPU, its own graph launches) for comparison.
+
+Times are wall-clock from a request's arrival to its result on the host.
+"""
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import inputs as I
+from . import vlbm as V
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float
+    kind: str          # "riemann" or "vortex"
+    N: int             # coarse cells per side
+    nlev: int
+    adaptive: bool
+    steps: int
+    seed: int
+    case: object = None
+    result: object = None
+    done_at: float = None
+    lups: int = 0
+    lups_done: int = 0
+    bytes_est: int = 0
+
+
+def level_bytes(nx0, ny0, nlev):
+    """Device bytes of a hierarchy: two FP64 population buffers (16 planes)
+    and two 16-bit flag planes per level over the level's index space."""
+    tot = 0
+    for l in range(nlev):
+        nx, ny = nx0 << l, ny0 << l
+        pitch = (nx + 15) & ~15
+        tot += pitch * ny * (2 * 16 * 8 + 2 * 2)
+    return tot
+
+
+def random_quadrants(rng):
+    s = {}
+    for q in ("NE", "NW", "SW", "SE"):
+        s[q] = (float(rng.uniform(0.5, 2.0)), float(rng.uniform(-0.5, 0.5)),
+                float(rng.uniform(-0.5, 0.5)), float(rng.uniform(0.5, 2.0)))
+    return s
+
+
+def make_case(req):
+    rng = np.random.default_rng(req.seed)
+    if req.kind == "riemann":
+        states = random_quadrants(rng)
+        widths = [0.08, 0.04, 0.02][: req.nlev - 1]
+        cs = I.riemann3(N=req.N, nlev=req.nlev, t_end=0.1, beta=0.7, widths=widths, states=states,
+                        fine_state=False)
+        if req.adaptive and req.nlev > 1:
+            cs.refs = I.empty_refs(req.N, req.N, req.nlev)
+            cs.amr = {"tol": 0.02, "buffer": 2, "every": 4}
+    else:
+        cs = I.vortex(N=req.N, beta=1.0, periods=0.1, patch=req.nlev > 1, fine_state=False)
+        if req.nlev > 2:
+            # a third level over the vortex core
+            n = req.N
+            cs.refs = I.box_refs(n, n, 3, [(0, n // 4, n // 4, n // 2, n // 2)])
+            cs.refs[1][3 * n // 4: 5 * n // 4, 3 * n // 4: 5 * n // 4] = 1
+            cs.nlev = 3
+    cs.steps = req.steps if req.steps else cs.steps
+    return cs
+
+
+def make_requests(n=512, seed=20261202, rate=None, nmin=128, nmax=1024):
+    """Seeded request trace: kind 1/2 Riemann, 1/2 vortex; side length
+    log-uniform in [nmin, nmax] rounded to 32 cells; 1-3 levels; half of the
+    multi-level Riemann requests adaptive.  Arrival times are filled in by
+    `schedule` once the rate is known."""
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n):
+        kind = "riemann" if rng.random() < 0.5 else "vortex"
+        N = int(round(math.exp(rng.uniform(math.log(nmin), math.log(nmax))) / 32.0)) * 32
+        N = max(nmin, min(nmax, N))
+        nlev = int(rng.integers(1, 4))
+        adaptive = kind == "riemann" and nlev > 1 and rng.random() < 0.5
+        r = Request(i, 0.0, kind, N, nlev, adaptive, 0, int(rng.integers(1 << 30)))
+        cs = make_case(r)
+        r.steps = cs.steps
+        r.bytes_est = level_bytes(N, N, cs.nlev)
+        r.lups = cs.lups_per_step() * cs.steps
+        reqs.append(r)
+    return reqs
+
+
+def schedule(reqs, rate, seed=20261202):
+    """Poisson arrivals at `rate` requests per second."""
+    rng = np.random.default_rng(seed + 1)
+    t = 0.0
+    for r in reqs:
+        t += rng.exponential(1.0 / rate)
+        r.arrival = t
+    return reqs
+
+
+def _start(r, stream):
+    """Creates the request's hierarchy: level-0 state from the closed form,
+    finer levels by the conservative split (Eqs. 26-27) of a regrid to the
+    request's static layout, or by tag-driven regrids when adaptive."""
+    cs = make_case(r)
+    h = V.Hierarchy(cs.nx0, cs.ny0, cs.nlev, cs.bc, cs.gamma, cs.c, cs.beta, dx0=cs.dx0,
+                    tag_tol=(cs.amr or {}).get("tol", 0.0), tag_buffer=(cs.amr or {}).get("buffer", 0),
+                    stream=stream)
+    h.set_state(0, cs.W[0])
+    if r.adaptive:
+        for _ in range(cs.nlev - 1):
+            h.regrid()
+    elif cs.nlev > 1:
+        h.regrid_masks(cs.refs)
+    return h, cs
+
+
+def serve_batched(reqs, mem_budget, stream=None, keep_results=False):
+    """Continuous batching: returns per-request time-to-solution (s) and the
+    aggregate MLUPS."""
+    for r in reqs:
+        r.lups_done = 0
+    eng = V.Engine(mem_budget, stream=stream)
+    pending = sorted(reqs, key=lambda r: r.arrival)
+    live = {}
+    used = 0
+    nxt = 0
+    t0 = time.perf_counter()
+    total_lups = 0
+    while nxt < len(pending) or live:
+        now = time.perf_counter() - t0
+        # admit arrived requests while memory allows (in arrival order)
+        while nxt < len(pending) and pending[nxt].arrival <= now:
+            r = pending[nxt]
+            if live and used + r.bytes_est > mem_budget:
+                break
+            h, cs = _start(r, stream)
+            slot = eng.admit(h, cs.steps, 4 if r.adaptive else 0)
+            if slot is None:
+                h.close()
+                break
+            live[slot] = (r, h)
+            used += r.bytes_est
+            nxt += 1
+        if not live:
+            if nxt < len(pending):
+                time.sleep(max(0.0, min(0.002, pending[nxt].arrival - (time.perf_counter() - t0))))
+            continue
+        for slot, (r, h) in live.items():
+            r.lups_done += h.info()["lups_per_step"]
+        for slot in eng.step():
+            r, h = live.pop(slot)
+            W, act = h.get_conserved(0)
+            r.done_at = time.perf_counter() - t0
+            if keep_results:
+                r.result = [h.get_populations(l) for l in range(h.nlev)]
+            total_lups += r.lups_done
+            eng.release(slot)
+            h.close()
+            used -= r.bytes_est
+    wall = time.perf_counter() - t0
+    eng.close()
+    tts = np.array([r.done_at - r.arrival for r in reqs])
+    return tts, total_lups / wall / 1e6, wall
+
+
+def serve_one_at_a_time(reqs, stream=None):
+    """Each request alone on the GPU, in arrival order."""
+    pending = sorted(reqs, key=lambda r: r.arrival)
+    for r in reqs:
+        r.lups_done = 0
+    t0 = time.perf_counter()
+    total_lups = 0
+    for r in pending:
+        now = time.perf_counter() - t0
+        if r.arrival > now:
+            time.sleep(r.arrival - now)
+        h, cs = _start(r, stream)
+        left = cs.steps
+        every = 4 if r.adaptive else 0
+        while left > 0:
+            n = min(left, every) if every else left
+            r.lups_done += n * h.info()["lups_per_step"]
+            h.advance(n)
+            left -= n
+            if every and left > 0:
+                h.regrid()
+        W, act = h.get_conserved(0)
+        r.done_at = time.perf_counter() - t0
+        total_lups += r.lups_done
+        h.close()
+    wall = time.perf_counter() - t0
+    tts = np.array([r.done_at - r.arrival for r in reqs])
+    return tts, total_lups / wall / 1e6, wall

@@ -1,0 +1,321 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle.
+
+Both sides evaluate the same canonical FP64 expressions, so the populations
+are expected to agree bit for bit; the bar the tests enforce first is the
+stated one -- max relative error <= 1e-11 on every conserved field, relative
+to the field's largest magnitude -- and then exact equality.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2609_35529_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-11
+
+
+@pytest.fixture(scope="module")
+def V():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2609_35529_b300 import build, vlbm
+    build.build()
+    return vlbm
+
+
+def oracle_of(case, refs="case"):
+    o = O.Hierarchy(case.nx0, case.ny0, case.nlev, 2, case.bc, case.gamma, case.c, case.beta, case.inflow)
+    o.set_layout(case.refs if refs == "case" else refs)
+    for l in range(case.nlev):
+        o.set_state(l, case.W[l])
+    return o
+
+
+def compare(o, g, nlev, exact=True):
+    """Asserts layout equality, field-wise relative error <= TOL, then bitwise
+    equality of every population on every active cell.  Returns the worst
+    relative error."""
+    worst = 0.0
+    for l in range(nlev):
+        oin, oref = o.layout(l)
+        gin, gref = g.layout(l)
+        assert np.array_equal(oin, gin), f"level {l}: level membership differs"
+        assert np.array_equal(oref, gref), f"level {l}: refinement differs"
+        act = (oin == 1) & (oref == 0)
+        Wo, _ = o.get_W(l)
+        Wg, vg = g.get_conserved(l)
+        assert np.array_equal(vg, act)
+        for k in range(4):
+            a, b = Wo[k][act], Wg[k][act]
+            if a.size == 0:
+                continue
+            scale = max(np.max(np.abs(a)), 1e-300)
+            err = float(np.max(np.abs(a - b))) / scale
+            worst = max(worst, err)
+            assert err <= TOL, f"level {l} field {k}: rel err {err:.3e}"
+        if exact:
+            fo = o.get_f(l)[:, act]
+            fg = g.get_populations(l)[:, act]
+            nd = int(np.count_nonzero(fo != fg))
+            assert nd == 0, f"level {l}: {nd} populations differ (max {np.max(np.abs(fo - fg)):.3e})"
+    return worst
+
+
+def drift(t0, t1, a0):
+    return np.max(np.abs(t1 - t0) / a0)
+
+
+def test_library_loads_and_creates(V):
+    h = V.Hierarchy(16, 16, 1, (0, 0, 0, 0), 1.4, 5.0, 0.9)
+    info = h.info()
+    assert info["nx"] == [16] and info["lups_per_step"] == 256
+    h.close()
+
+
+def test_pure_streaming_bitwise(V):
+    cs = I.smooth_random(24, 16, 1, [], seed=3, beta=0.0)
+    g = V.Hierarchy.from_case(cs)
+    o = oracle_of(cs, refs=None)
+    rng = np.random.default_rng(8)
+    # equilibrium populations of a smooth state, perturbed by 1 %: every
+    # streamed mixture stays a physical state
+    feq = O.feq(cs.gamma, cs.c, cs.W[0][:, 0, 0])
+    f0 = feq[:, None, None] * (1.0 + 0.01 * rng.uniform(-1.0, 1.0, (16, 16, 24)))
+    g.set_populations(0, f0)
+    o.set_f(0, f0)
+    g.advance(48)
+    assert np.array_equal(g.get_populations(0), f0)
+    g.advance(3)
+    o.advance(51)
+    compare(o, g, 1)
+
+
+def test_uniform_grid_smooth(V):
+    cs = I.smooth_random(40, 24, 1, [], seed=1, amp=0.2, beta=0.85, steps=30)
+    g = V.Hierarchy.from_case(cs)
+    o = oracle_of(cs, refs=None)
+    g.advance(cs.steps)
+    o.advance(cs.steps)
+    compare(o, g, 1)
+
+
+def test_two_level_pulse_full_run(V):
+    """Two-level static refinement, periodic 64^2, 200 coarse steps."""
+    cs = I.pulse2l()
+    g = V.Hierarchy.from_case(cs)
+    o = oracle_of(cs)
+    t0, a0 = g.audit()
+    g.advance(cs.steps)
+    o.advance(cs.steps)
+    compare(o, g, 2)
+    t1, _ = g.audit()
+    assert drift(t0, t1, a0) < 1e-13
+    ot, oa = o.totals()
+    np.testing.assert_allclose(t1, ot, rtol=1e-14, atol=1e-14 * oa.max())
+
+
+def test_three_level_periodic_ragged(V):
+    """Three levels on a domain whose size is not a multiple of the tile
+    (ragged last tile column/row), including a patch that wraps across the
+    periodic seam."""
+    nx0, ny0 = 52, 44
+    refs = I.box_refs(nx0, ny0, 3, [(0, 8, 8, 24, 16), (0, 0, 32, 8, 8), (0, 48, 32, 4, 8)])
+    refs[1][24:40, 24:56] = 1
+    cs = I.smooth_random(nx0, ny0, 3, refs, seed=21, amp=0.25, beta=0.8, steps=25)
+    g = V.Hierarchy.from_case(cs)
+    o = oracle_of(cs)
+    t0, a0 = g.audit()
+    g.advance(cs.steps)
+    o.advance(cs.steps)
+    compare(o, g, 3)
+    t1, _ = g.audit()
+    assert drift(t0, t1, a0) < 1e-13
+
+
+def test_riemann3_three_levels_outflow(V):
+    cs = I.riemann3(N=64, nlev=3, steps=60)
+    g = V.Hierarchy.from_case(cs)
+    o = oracle_of(cs)
+    g.advance(cs.steps)
+    o.advance(cs.steps)
+    compare(o, g, 3)
+
+
+def test_riemann3_transpose_symmetric(V):
+    cs = I.riemann3(N=64, nlev=3, steps=40)
+    g = V.Hierarchy.from_case(cs)
+    g.advance(cs.steps)
+    for l in range(3):
+        f = g.get_populations(l).reshape(4, 4, *g.shapes[l])
+        gin, gref = g.layout(l)
+        act = (gin == 1) & (gref == 0)
+        ft = f.transpose(0, 1, 3, 2)[[2, 3, 0, 1]][:, [0, 2, 1, 3]]
+        assert np.array_equal(f[:, :, act], ft[:, :, act])
+
+
+def test_reflective_walls_with_patch(V):
+    """Explosion in a box (Sec. 4.2, Eq. 31) on a small grid: reflective walls
+    on all sides, a centred ratio-2 patch."""
+    N = 64
+    refs = I.box_refs(N, N, 2, [(0, 16, 16, 32, 32)])
+
+    def fn(X, Y):
+        inside = (X - 0.4) ** 2 + (Y - 0.4) ** 2 < 0.3 ** 2
+        rho = np.where(inside, 5.0, 1.0)
+        return I.conserved(rho, np.zeros_like(X), np.zeros_like(X), rho)
+
+    Ws = I.fill_levels(N, N, 2, 1.0 / N, fn)
+    c = I.link_speed([Ws[0]], safety=2.0)
+    cs = I.Case("explosion", N, N, 2, (3, 3, 3, 3), 1.4, c, 0.9, Ws, refs, 50, dx0=1.0 / N)
+    g = V.Hierarchy.from_case(cs)
+    o = oracle_of(cs)
+    t0, a0 = g.audit()
+    g.advance(cs.steps)
+    o.advance(cs.steps)
+    compare(o, g, 2)
+    t1, _ = g.audit()
+    # walls: mass and energy conserved, momentum is not
+    assert abs(t1[0] - t0[0]) / a0[0] < 1e-13 and abs(t1[3] - t0[3]) / a0[3] < 1e-13
+
+
+def test_inflow_outflow_static(V):
+    """Inflow (west), outflow (east), periodic (south/north) with a static
+    patch that the shock crosses."""
+    cs = I.shockbubble(nx0=64, ny0=32, nlev=2, steps=40)
+    cs.refs = I.box_refs(64, 32, 2, [(0, 8, 8, 24, 16)])
+    # level-1 state: the same initial condition on the fine cell centres
+    cs.W = [cs.W[0], I.shockbubble(nx0=128, ny0=64, nlev=1).W[0]]
+    g = V.Hierarchy.from_case(cs)
+    o = oracle_of(cs)
+    g.advance(cs.steps)
+    o.advance(cs.steps)
+    compare(o, g, 2)
+
+
+def test_regrid_to_masks(V):
+    n = 48
+    refs_a = I.box_refs(n, n, 3, [(0, 8, 8, 24, 24)])
+    refs_a[1][24:56, 24:40] = 1
+    refs_b = I.box_refs(n, n, 3, [(0, 16, 8, 24, 32)])
+    refs_b[1][32:48, 40:64] = 1
+    cs = I.smooth_random(n, n, 3, refs_a, seed=31, amp=0.3, beta=0.9)
+    g = V.Hierarchy.from_case(cs)
+    o = oracle_of(cs)
+    g.advance(6)
+    o.advance(6)
+    t0, a0 = g.audit()
+    g.regrid_masks(refs_b)
+    o.regrid(refs_b)
+    t1, _ = g.audit()
+    assert drift(t0, t1, a0) < 1e-14
+    compare(o, g, 3)
+    g.advance(7)
+    o.advance(7)
+    compare(o, g, 3)
+    g.regrid_masks(I.empty_refs(n, n, 3))
+    o.regrid(I.empty_refs(n, n, 3))
+    g.advance(2)
+    o.advance(2)
+    compare(o, g, 3)
+
+
+def test_adaptive_shockbubble_small(V):
+    """Adaptive shock-bubble on a 128 x 64 coarse grid, three levels, regrid
+    every 4 coarse steps from the density-gradient indicator: layouts and
+    populations match the oracle, totals are conserved across each regrid."""
+    cs = I.shockbubble(nx0=128, ny0=64, nlev=3)
+    tol, buf, every = cs.amr["tol"], cs.amr["buffer"], cs.amr["every"]
+    g = V.Hierarchy.from_case(cs)
+    o = oracle_of(cs)
+    for _ in range(2):  # build the initial levels from the initial state
+        g.regrid()
+        o.regrid_tagged(tol, buf, 8)
+    compare(o, g, 3)
+    for cycle in range(6):
+        g.advance(every)
+        o.advance(every)
+        t0, a0 = g.audit()
+        g.regrid()
+        o.regrid_tagged(tol, buf, 8)
+        t1, _ = g.audit()
+        assert drift(t0, t1, a0) < 1e-14
+        compare(o, g, 3)
+    info = g.info()
+    assert info["active_cells"][1] > 0 and info["active_cells"][2] > 0
+
+
+def test_engine_results_equal_alone_and_in_mix(V):
+    cases = [I.pulse2l(steps=30), I.riemann3(N=64, nlev=3, steps=25),
+             I.smooth_random(40, 32, 1, [], seed=5, amp=0.2, steps=35)]
+    alone = []
+    for cs in cases:
+        g = V.Hierarchy.from_case(cs)
+        g.advance(cs.steps)
+        alone.append([g.get_populations(l) for l in range(cs.nlev)])
+        g.close()
+    e = V.Engine()
+    hs = [V.Hierarchy.from_case(cs) for cs in cases]
+    slots = [e.admit(h, cs.steps) for h, cs in zip(hs, cases)]
+    done = set()
+    while len(done) < len(cases):
+        for s in e.step():
+            done.add(s)
+    for cs, h, a in zip(cases, hs, alone):
+        for l in range(cs.nlev):
+            gin, gref = h.layout(l)
+            act = (gin == 1) & (gref == 0)
+            assert np.array_equal(h.get_populations(l)[:, act], a[l][:, act])
+    for s in slots:
+        e.release(s)
+    e.close()
+
+
+def test_nonphysical_state_is_reported(V):
+    cs = I.smooth_random(16, 16, 1, [], seed=2)
+    cs.W[0][0, 3, 4] = -1.0
+    g = V.Hierarchy.from_case(cs)
+    g.advance(1)
+    with pytest.raises(V.VlbmError) as ei:
+        g.sync()
+    assert ei.value.name == "ERR_NONPHYSICAL"
+    with pytest.raises(V.VlbmError) as ei:
+        g.advance(1)
+    assert ei.value.name == "ERR_STATE"
+
+
+def test_nesting_violation_rejected(V):
+    # a level-2 block touching level-0 territory
+    with pytest.raises(V.VlbmError) as ei:
+        V.Hierarchy(32, 32, 3, (0, 0, 0, 0), 1.4, 5.0, 0.9, boxes=[(0, 8, 8, 8, 8), (1, 16, 16, 8, 8)])
+    assert ei.value.name == "ERR_NESTING"
+    with pytest.raises(V.VlbmError) as ei:
+        V.Hierarchy(32, 32, 2, (0, 0, 0, 0), 1.4, 5.0, 0.9, boxes=[(0, 4, 8, 8, 8)])
+    assert ei.value.name == "ERR_ARG"
+
+
+def test_torch_allocator_and_stream(V):
+    import torch
+    s = torch.cuda.Stream()
+    cs = I.pulse2l(steps=20)
+    g = V.Hierarchy.from_case(cs, stream=s, allocator="torch")
+    o = oracle_of(cs)
+    g.advance(cs.steps)
+    o.advance(cs.steps)
+    compare(o, g, 2)
+    g.close()
+
+
+def test_vortex_512_bench_configuration(V):
+    """The benchmarked configuration itself (512^2 coarse + central ratio-2
+    patch), in the bench's launch configuration, for a few coarse steps."""
+    cs = I.vortex(N=512, steps=4)
+    g = V.Hierarchy.from_case(cs)
+    o = oracle_of(cs)
+    g.advance(cs.steps)
+    o.advance(cs.steps)
+    compare(o, g, 2)

@@ -198,6 +198,33 @@ typedef struct {
 
 vlbm_status vlbm_profile(vlbm_hier* h, int64_t coarse_steps, vlbm_kernel_time* out, int32_t cap, int32_t* n);
 
+/* Launch tuning of the sweep.  variant selects one compiled form of the
+ * level sweep: which of the collision's additions and multiplications run
+ * on the integer pipes through bit-exact binary64 routines (results are
+ * identical bit for bit in every variant) and how many CTAs per SM the
+ * kernel is built for; some variants apply only when 1 - 2 beta == -1.
+ * max_ctas caps the sweep grid (0 = one CTA per four tiles); graph_steps is
+ * the number of coarse steps captured per CUDA graph (>= 1).
+ * vlbm_set_tuning returns ERR_ARG for a variant that does not apply to the
+ * hierarchy (it is then unchanged). */
+typedef struct {
+    int32_t variant, max_ctas, graph_steps;
+} vlbm_tuning;
+
+int32_t vlbm_num_variants(void);
+vlbm_status vlbm_set_tuning(vlbm_hier* h, const vlbm_tuning* t);
+vlbm_status vlbm_get_tuning(const vlbm_hier* h, vlbm_tuning* t);
+
+/* Self-test of the integer-pipe binary64 routines used inside the sweep
+ * (addition, subtraction, multiplication, halving) against the FP64 unit on
+ * n seeded operand pairs (SplitMix64 stream from `seed`; values near 1,
+ * equal and distant exponents, near-cancellations, zeros, subnormals,
+ * infinities, NaNs, raw bit patterns).  mismatches[k] counts results whose
+ * bits differ for k = add, sub, mul, half; first_bad[4k..4k+3] holds the
+ * first offending (a, b, hardware, emulated).  Runs on the current device
+ * and synchronises it.  Errors: ERR_ARG, ERR_OOM, ERR_CUDA. */
+vlbm_status vlbm_selftest_fp64(uint64_t seed, int64_t n, uint64_t mismatches[4], double first_bad[16]);
+
 /* Human-readable description of the last error on the handle (never NULL). */
 const char* vlbm_last_error(const vlbm_hier* h);
 

@@ -154,6 +154,7 @@ struct vlbm_hier {
     DArr<LevelDev> atab;   // level table for audits (rebuilt with the layout)
     DArr<Item> aitems;     // active tiles of every level (audits)
     double* hout = nullptr;  // pinned host copy of the audit result
+    vlbm_tuning tune{1, 0, 8};
 
     LevelDev dev(int l, int parent, int child) const {
         LevelDev d{};
@@ -198,6 +199,7 @@ struct Batch {
     int G = 8;
     bool valid = false;
     int max_ctas = 0;  // sweep grid cap (0 = one CTA per 4 tiles)
+    int variant = 0;   // sweep kernel variant
 
     void release() {
         if (exec1) cudaGraphExecDestroy(exec1);
@@ -214,7 +216,7 @@ struct Batch {
     }
 
     void schedule(int l, int kk, int kkp, cudaStream_t s) {
-        VCK(launch_sweep(levs.p, sweep[l].p, (int)sweep[l].n, kk, kkp, max_ctas, s));
+        VCK(launch_sweep(levs.p, sweep[l].p, (int)sweep[l].n, kk, kkp, max_ctas, variant, s));
         if (l + 1 < maxlev && sweep[l + 1].n > 0) {
             schedule(l + 1, 1, kk, s);
             schedule(l + 1, 2, kk, s);
@@ -322,7 +324,7 @@ struct Batch {
     void schedule_timed(int l, int kk, int kkp, const long long* cells, std::vector<Rec>& recs, cudaStream_t s) {
         if (sweep[l].n)
             timed(0, l, cells[l], recs, s,
-                  [&] { return launch_sweep(levs.p, sweep[l].p, (int)sweep[l].n, kk, kkp, max_ctas, s); });
+                  [&] { return launch_sweep(levs.p, sweep[l].p, (int)sweep[l].n, kk, kkp, max_ctas, variant, s); });
         if (l + 1 < maxlev && sweep[l + 1].n > 0) {
             schedule_timed(l + 1, 1, kk, cells, recs, s);
             schedule_timed(l + 1, 2, kk, cells, recs, s);
@@ -668,7 +670,12 @@ void ensure_own_batch(vlbm_hier* h) {
         h->own->mem = &h->mem;
         h->own->members.push_back(h);
     }
-    if (!h->own->valid) h->own->build(h->stream);
+    if (!h->own->valid) {
+        h->own->variant = h->tune.variant;
+        h->own->max_ctas = h->tune.max_ctas;
+        h->own->G = h->tune.graph_steps;
+        h->own->build(h->stream);
+    }
 }
 
 }  // namespace
@@ -961,6 +968,25 @@ vlbm_status vlbm_get_info(const vlbm_hier* h, vlbm_info* info) {
     info->beta = h->cfg.beta;
     info->gamma = h->cfg.gamma;
     info->dx0 = h->cfg.dx0;
+    return VLBM_OK;
+}
+
+int32_t vlbm_num_variants(void) { return sweep_variants(); }
+
+vlbm_status vlbm_set_tuning(vlbm_hier* h, const vlbm_tuning* t) {
+    return run(h, [&] {
+        if (!t || t->variant < 0 || t->variant >= sweep_variants() || t->max_ctas < 0 || t->graph_steps < 1)
+            throw Fail{VLBM_ERR_ARG, "bad tuning"};
+        if (sweep_variant_needs_om_minus1(t->variant) && h->om != -1.0)
+            throw Fail{VLBM_ERR_ARG, "variant applies only when 1 - 2 beta == -1"};
+        h->tune = *t;
+        if (h->own) h->own->valid = false;
+    });
+}
+
+vlbm_status vlbm_get_tuning(const vlbm_hier* h, vlbm_tuning* t) {
+    if (!h || !t) return VLBM_ERR_ARG;
+    *t = h->tune;
     return VLBM_OK;
 }
 

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 
+#include "fp64emu.cuh"
 #include "vlbm_dev.cuh"
 #include "vlbm_launch.h"
 
@@ -61,6 +62,74 @@ __device__ __forceinline__ bool collide(double f[16], double om, double hb, doub
         f[4 + k] = fma(-bcs, Qx[k], fma(om, f[4 + k], A));
         f[8 + k] = fma(bcs, Qy[k], fma(om, f[8 + k], A));
         f[12 + k] = fma(-bcs, Qy[k], fma(om, f[12 + k], A));
+    }
+    return physical(W[0], p);
+}
+
+// The same collision with a chosen subset of its additions and
+// multiplications carried out by the bit-exact integer-pipe routines
+// (fp64emu.cuh); the results are identical bit for bit, only the pipe that
+// computes them changes.  Policy bits: EM_MOM the twelve moment additions,
+// EM_A the four (beta/2) W products, EM_FLUX the flux products and sums
+// (with rho E - (1/2) ke as an exact-halving addition), EM_OMF the inner
+// fma(1 - 2 beta, f, A) as an addition when 1 - 2 beta is -1 (its product
+// is then exact).
+enum : int { EM_MOM = 1, EM_A = 2, EM_FLUX = 4, EM_OMF = 8 };
+
+template <bool E>
+__device__ __forceinline__ double xadd(double a, double b) {
+    if constexpr (E) return emu_add(a, b);
+    else return a + b;
+}
+template <bool E>
+__device__ __forceinline__ double xmul(double a, double b) {
+    if constexpr (E) return emu_mul(a, b);
+    else return a * b;
+}
+
+template <int P>
+__device__ __forceinline__ bool collide_p(double f[16], double om, double hb, double bcs, double gm1) {
+    constexpr bool M = (P & EM_MOM) != 0, A_ = (P & EM_A) != 0, F = (P & EM_FLUX) != 0, O = (P & EM_OMF) != 0;
+    double W[4], Qx[4], Qy[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) W[k] = xadd<M>(xadd<M>(f[k], f[4 + k]), xadd<M>(f[8 + k], f[12 + k]));
+    const double inv = 1.0 / W[0];
+    const double u = xmul<F>(W[1], inv);
+    const double v = xmul<F>(W[2], inv);
+    const double ruu = xmul<F>(W[1], u);
+    const double rvv = xmul<F>(W[2], v);
+    double e;
+    if constexpr (F) e = emu_sub(W[3], emu_half(emu_add(ruu, rvv)));
+    else e = fma(-0.5, ruu + rvv, W[3]);
+    const double p = xmul<F>(gm1, e);
+    const double H = xadd<F>(W[3], p);
+    Qx[0] = W[1];
+    Qx[1] = xadd<F>(ruu, p);
+    Qx[2] = xmul<F>(W[2], u);
+    Qx[3] = xmul<F>(H, u);
+    Qy[0] = W[2];
+    Qy[1] = xmul<F>(W[1], v);
+    Qy[2] = xadd<F>(rvv, p);
+    Qy[3] = xmul<F>(H, v);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const double A = xmul<A_>(hb, W[k]);
+        double t0, t1, t2, t3;
+        if constexpr (O) {  // om == -1: fma(om, f, A) == A - f exactly
+            t0 = emu_sub(A, f[k]);
+            t1 = emu_sub(A, f[4 + k]);
+            t2 = emu_sub(A, f[8 + k]);
+            t3 = emu_sub(A, f[12 + k]);
+        } else {
+            t0 = fma(om, f[k], A);
+            t1 = fma(om, f[4 + k], A);
+            t2 = fma(om, f[8 + k], A);
+            t3 = fma(om, f[12 + k], A);
+        }
+        f[k] = fma(bcs, Qx[k], t0);
+        f[4 + k] = fma(-bcs, Qx[k], t1);
+        f[8 + k] = fma(bcs, Qy[k], t2);
+        f[12 + k] = fma(-bcs, Qy[k], t3);
     }
     return physical(W[0], p);
 }
@@ -171,7 +240,8 @@ __device__ __noinline__ void sweep_special(const LevelDev* __restrict__ levs, co
 // One step of one level for every tile in `items` (all of the same level
 // index within their hierarchies).  kk: this level's sub-step (1, 2) within
 // its parent's step (ignored on level 0); kkp: the parent's sub-step.
-__global__ void __launch_bounds__(CTA_THREADS, 2)
+template <int P, int MINB>
+__global__ void __launch_bounds__(CTA_THREADS, MINB)
 sweep_kernel(const LevelDev* __restrict__ levs, const Item* __restrict__ items, int nitems, int kk, int kkp) {
     const int sub = threadIdx.x >> 6;
     const int cx = threadIdx.x & 7;
@@ -193,7 +263,7 @@ sweep_kernel(const LevelDev* __restrict__ levs, const Item* __restrict__ items, 
         double f[16];
 #pragma unroll
         for (int q = 0; q < 16; q++) f[q] = __ldg(src + q * plane + c);
-        if (!collide(f, L.om, L.hb, L.bcs, L.gm1)) atomicOr(L.status, ST_NONPHYS);
+        if (!collide_p<P>(f, L.om, L.hb, L.bcs, L.gm1)) atomicOr(L.status, ST_NONPHYS);
         // push streaming (Eq. 5): f*_i lands on x + c_i
         long long cxp = c + 1, cxm = c - 1, cyp = c + L.pitch, cym = c - L.pitch;
         bool oxp = true, oxm = true, oyp = true, oym = true;
@@ -625,9 +695,34 @@ static inline int flat_grid(long long n) {
     return (int)(g < 1 ? 1 : g);
 }
 
-cudaError_t launch_sweep(const LevelDev* levs, const Item* items, int n, int kk, int kkp, int max_ctas, cudaStream_t s) {
+// Sweep variants: (emulation policy, minimum resident CTAs per SM).
+#define VLBM_SWEEP_VARIANTS(X)                                   \
+    X(0, 0, 2) X(1, 0, 3) X(2, EM_MOM, 2) X(3, EM_MOM | EM_A, 2) \
+    X(4, EM_MOM | EM_A | EM_FLUX, 2) X(5, EM_FLUX, 2) X(6, EM_MOM | EM_A | EM_FLUX | EM_OMF, 2) \
+    X(7, EM_MOM | EM_A | EM_OMF, 2) X(8, EM_MOM | EM_A | EM_FLUX, 3) X(9, EM_MOM | EM_A | EM_FLUX | EM_OMF, 3)
+
+int sweep_variants() { return 10; }
+
+// variant -> whether it needs 1 - 2 beta == -1
+bool sweep_variant_needs_om_minus1(int v) {
+    switch (v) {
+#define X(id, P, B) case id: return ((P) & EM_OMF) != 0;
+        VLBM_SWEEP_VARIANTS(X)
+#undef X
+    }
+    return false;
+}
+
+cudaError_t launch_sweep(const LevelDev* levs, const Item* items, int n, int kk, int kkp, int max_ctas, int variant,
+                         cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    sweep_kernel<<<tile_grid(n, max_ctas), CTA_THREADS, 0, s>>>(levs, items, n, kk, kkp);
+    const int g = tile_grid(n, max_ctas);
+    switch (variant) {
+#define X(id, P, B) case id: sweep_kernel<P, B><<<g, CTA_THREADS, 0, s>>>(levs, items, n, kk, kkp); break;
+        VLBM_SWEEP_VARIANTS(X)
+#undef X
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

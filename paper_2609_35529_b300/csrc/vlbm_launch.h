@@ -7,7 +7,10 @@
 
 namespace vlbm {
 
-cudaError_t launch_sweep(const LevelDev* levs, const Item* items, int n, int kk, int kkp, int max_ctas, cudaStream_t s);
+cudaError_t launch_sweep(const LevelDev* levs, const Item* items, int n, int kk, int kkp, int max_ctas, int variant,
+                         cudaStream_t s);
+int sweep_variants();
+bool sweep_variant_needs_om_minus1(int v);
 cudaError_t launch_close(const LevelDev* levs, const Item* items, int n, int kk, cudaStream_t s);
 cudaError_t launch_end_step(int* const* par, int n, cudaStream_t s);
 cudaError_t launch_feq_init(const LevelDev& L, const double* W, long long ld, double hc, cudaStream_t s);

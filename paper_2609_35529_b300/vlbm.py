@@ -55,6 +55,10 @@ class vlbm_kernel_time(C.Structure):
                 ("ms", C.c_double)]
 
 
+class vlbm_tuning(C.Structure):
+    _fields_ = [("variant", C.c_int32), ("max_ctas", C.c_int32), ("graph_steps", C.c_int32)]
+
+
 class vlbm_info(C.Structure):
     _fields_ = [("nlev", C.c_int32), ("nx", C.c_int32 * 4), ("ny", C.c_int32 * 4),
                 ("active_cells", C.c_int64 * 4), ("lups_per_step", C.c_int64), ("device_bytes", C.c_int64),
@@ -98,6 +102,14 @@ def lib():
         fn = getattr(L, name)
         fn.argtypes = args
         fn.restype = C.c_int
+    L.vlbm_num_variants.argtypes = []
+    L.vlbm_num_variants.restype = C.c_int32
+    L.vlbm_set_tuning.argtypes = [vp, C.POINTER(vlbm_tuning)]
+    L.vlbm_set_tuning.restype = C.c_int
+    L.vlbm_get_tuning.argtypes = [vp, C.POINTER(vlbm_tuning)]
+    L.vlbm_get_tuning.restype = C.c_int
+    L.vlbm_selftest_fp64.argtypes = [C.c_uint64, i64, C.POINTER(C.c_uint64), dp]
+    L.vlbm_selftest_fp64.restype = C.c_int
     L.vlbm_last_error.argtypes = [vp]
     L.vlbm_last_error.restype = C.c_char_p
     L.vlbm_destroy.argtypes = [vp]
@@ -282,8 +294,33 @@ class Hierarchy:
         return [{"kind": kinds[r.kind], "level": r.level, "launches": r.launches, "cells": r.cells, "ms": r.ms}
                 for r in recs[: n.value]]
 
+    def set_tuning(self, variant=0, max_ctas=0, graph_steps=8):
+        t = vlbm_tuning(variant, max_ctas, graph_steps)
+        _check(self._h, lib().vlbm_set_tuning(self._h, C.byref(t)))
+
+    def get_tuning(self):
+        t = vlbm_tuning()
+        _check(self._h, lib().vlbm_get_tuning(self._h, C.byref(t)))
+        return {"variant": t.variant, "max_ctas": t.max_ctas, "graph_steps": t.graph_steps}
+
     def last_error(self):
         return lib().vlbm_last_error(self._h).decode()
+
+
+def num_variants():
+    return lib().vlbm_num_variants()
+
+
+def selftest_fp64(seed, n):
+    """Bitwise check of the integer-pipe FP64 routines against the FP64 unit;
+    returns ({op: mismatches}, first offending (a, b, hw, emu) per op)."""
+    bad = (C.c_uint64 * 4)()
+    first = (C.c_double * 16)()
+    st = lib().vlbm_selftest_fp64(int(seed), int(n), bad, first)
+    if st != 0:
+        raise VlbmError(st, "vlbm_selftest_fp64")
+    names = ["add", "sub", "mul", "half"]
+    return {k: int(bad[i]) for i, k in enumerate(names)}, {k: tuple(first[4 * i: 4 * i + 4]) for i, k in enumerate(names)}
 
 
 class Engine:

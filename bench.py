@@ -183,7 +183,7 @@ def run_reference(args, budget_s=90.0):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -206,55 +206,69 @@ def main():
     case = I.vortex(N=512, steps=args.steps)
     stream = torch.cuda.Stream()
     g = V.Hierarchy.from_case(case, stream=stream)
+    tune = g.get_tuning()
+    chunk = max(1, tune["graph_steps"])
     info = g.info()
     lups = info["lups_per_step"]
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    # warm-up (also builds and instantiates the CUDA graphs)
+    # warm-up (also builds the task lists and instantiates the CUDA graphs)
     for _ in range(max(3, args.warmup)):
         g.advance(1)
+    g.advance(chunk)
     g.sync()
 
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    # timed: iterations of `chunk` coarse steps (one graph launch each), the
+    # L2 flushed between iterations
+    iters = max(1, args.steps // chunk)
+    steps = iters * chunk
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(iters)]
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
     with ClockSampler(dev) as clk:
         with torch.cuda.stream(stream):
-            for i in range(args.steps):
+            for i in range(iters):
                 flush.fill_(float(i))  # > L2 between timed iterations
                 ev[i][0].record(stream)
-                g.advance(1)
+                g.advance(chunk)
                 ev[i][1].record(stream)
         torch.cuda.synchronize()
     g.sync()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
+    it_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(it_ms)
     if pg:
         pg.barrier()
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         ms = float(t.item())
-    value = world * lups * args.steps / (ms * 1e-3) / 1e6
+    value = world * lups * steps / (ms * 1e-3) / 1e6
 
-    # per-kernel device times over the same number of steps (eager launches,
-    # CUDA events on the library's stream) for the roofline of the sweep
-    prof = g.profile(min(args.steps, 100))
+    # roofline of the dominant kernel.  With the persistent schedule one
+    # timed iteration is one launch of the task kernel (all sweeps and
+    # closes of `chunk` coarse steps); its duration is the iteration's
+    # CUDA-event time on the library's stream.
+    pk = peaks()
+    launch_ms = statistics.mean(it_ms)
+    cells = lups * chunk
+    achieved_tflops = FLOPS_PER_LUP * cells / (launch_ms * 1e-3) / 1e12
+    hbm_gbs = BYTES_PER_LUP * cells / (launch_ms * 1e-3) / 1e9
+    kernel = "task_kernel" if tune["schedule"] == 1 else "sweep_kernel"
+    # the per-phase sweep kernel measured alone (eager launches with events)
+    prof = g.profile(min(steps, 64))
     sweep = [r for r in prof if r["kind"] == "sweep"]
     sw_ms = sum(r["ms"] for r in sweep)
-    sw_launch = sum(r["launches"] for r in sweep)
     sw_cells = sum(r["cells"] for r in sweep)
-    tot_ms = sum(r["ms"] for r in prof)
-    launches_per_step = sum(r["launches"] for r in prof) / min(args.steps, 100)
-    pk = peaks()
-    achieved_tflops = FLOPS_PER_LUP * sw_cells / (sw_ms * 1e-3) / 1e12
-    hbm_gbs = BYTES_PER_LUP * sw_cells / (sw_ms * 1e-3) / 1e9
     roof = {"bound": "alu", "achieved": round(achieved_tflops, 4), "peak": round(pk["fp64_tflops"], 4),
             "unit": "TFLOP/s", "frac": round(achieved_tflops / pk["fp64_tflops"], 4), "traffic": None,
-            "kernel": "sweep_kernel", "avg_launch_ms": round(sw_ms / sw_launch, 5),
-            "cells_per_launch": sw_cells // max(1, sw_launch), "share_of_step": round(sw_ms / tot_ms, 4),
+            "kernel": kernel, "avg_launch_ms": round(launch_ms, 5), "cells_per_launch": cells,
             "flops_per_lup": FLOPS_PER_LUP, "peak_basis": "2 FP64 FMA/clk/SM x 148 SMs x sm_max_mhz",
             "hbm": {"achieved": round(hbm_gbs, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
-                    "frac": round(hbm_gbs / pk["hbm_gbs"], 4), "peak_source": pk["source"]}}
+                    "frac": round(hbm_gbs / pk["hbm_gbs"], 4), "peak_source": pk["source"]},
+            "sweep_kernel_alone_mlups": round(sw_cells / sw_ms / 1e3, 1)}
+    launches_per_iter = 1 if tune["schedule"] == 1 else None
+    if launches_per_iter is None:
+        launches_per_iter = sum(r["launches"] for r in prof) / min(steps, 64) * chunk
 
     # end to end through the public API with host buffers: initial state from
     # pinned host memory, per-step conservation totals read back, final state
@@ -268,7 +282,7 @@ def main():
     h2.advance(2)
     h2.audit()
     torch.cuda.synchronize()
-    n_e2e = min(args.steps, 1000)
+    n_e2e = min(steps, 1000)
     t0 = time.perf_counter()
     for l in range(case.nlev):
         h2.set_state(l, Wh[l])
@@ -295,15 +309,16 @@ def main():
             cpu = {"value": round(mlups, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
                    "sample": f"{nst} coarse steps of the same workload ({el:.1f} s, one thread)"}
         line = {"metric": METRIC, "value": round(value, 3), "unit": "MLUPS", "n_gpus": world,
-                "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps,
+                "steps": steps, "warmup": max(3, args.warmup), "ms_per_step": ms / steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic (closed-form initial state)",
                 "config": {"workload": WORKLOAD, "coarse": [case.nx0, case.ny0], "levels": case.nlev,
                            "lups_per_step": lups, "c": case.c, "beta": case.beta,
-                           "l2": "flushed between timed steps (512 MB write)",
+                           "l2": f"flushed between timed iterations of {chunk} coarse steps (512 MB write)",
+                           "tuning": tune,
                            "parallelism": f"replicas x{world}"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": int(round(launches_per_step * args.steps)),
+                "gpu_launches": int(round(launches_per_iter * iters)),
                 "clocks": clk.summary()}
         print(json.dumps(line))
     if pg:

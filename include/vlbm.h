@@ -203,12 +203,18 @@ vlbm_status vlbm_profile(vlbm_hier* h, int64_t coarse_steps, vlbm_kernel_time* o
  * on the integer pipes through bit-exact binary64 routines (results are
  * identical bit for bit in every variant) and how many CTAs per SM the
  * kernel is built for; some variants apply only when 1 - 2 beta == -1.
- * max_ctas caps the sweep grid (0 = one CTA per four tiles); graph_steps is
- * the number of coarse steps captured per CUDA graph (>= 1).
- * vlbm_set_tuning returns ERR_ARG for a variant that does not apply to the
- * hierarchy (it is then unchanged). */
+ * schedule 0 issues one kernel launch per phase of the sub-cycle (level
+ * sweeps, reflux closes); schedule 1 runs graph_steps coarse steps of every
+ * phase in one persistent launch whose 8x8-tile tasks start as soon as the
+ * tasks they depend on (read-after-write, write-after-read and
+ * write-after-write on populations and flags, derived on the host) are
+ * done -- the waits are bounded and report VLBM_ERR_TIMEOUT.  max_ctas caps
+ * the grid (0 = one CTA per four tiles for schedule 0, all resident CTAs for
+ * schedule 1); graph_steps (1..64) is the number of coarse steps captured
+ * per CUDA graph.  vlbm_set_tuning returns ERR_ARG for a variant that does
+ * not apply to the hierarchy (it is then unchanged). */
 typedef struct {
-    int32_t variant, max_ctas, graph_steps;
+    int32_t variant, max_ctas, graph_steps, schedule;
 } vlbm_tuning;
 
 int32_t vlbm_num_variants(void);

@@ -69,4 +69,14 @@ struct Item {
     unsigned short tx, ty;
 };
 
+// A task of the persistent kernel: one tile of one phase (kind 0 = level
+// sweep, kind 1 = reflux close) of one coarse step; its dependencies are
+// deps[dep0 .. dep0 + ndep), indices of earlier tasks.
+struct Task {
+    int lid;
+    unsigned short tx, ty;
+    signed char kind, kk, kkp, step;
+    int dep0, ndep;
+};
+
 }  // namespace vlbm

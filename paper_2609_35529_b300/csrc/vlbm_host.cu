@@ -121,6 +121,7 @@ struct Level {
     std::vector<uint8_t> bin, bcov;  // block maps (current layout)
     DArr<uint8_t> dbin, dbcov;
     std::vector<Item> act, ring, cov, in;  // tiles (lid = level index)
+    std::vector<uint8_t> recon;             // per tile: a face neighbour is coarser land
     long long active_cells = 0;
 };
 
@@ -154,7 +155,7 @@ struct vlbm_hier {
     DArr<LevelDev> atab;   // level table for audits (rebuilt with the layout)
     DArr<Item> aitems;     // active tiles of every level (audits)
     double* hout = nullptr;  // pinned host copy of the audit result
-    vlbm_tuning tune{1, 0, 8};
+    vlbm_tuning tune{1, 0, 8, 1};
 
     LevelDev dev(int l, int parent, int child) const {
         LevelDev d{};
@@ -212,6 +213,12 @@ struct Batch {
         }
         par.release(*mem);
         audit_items.release(*mem);
+        tasks.release(*mem);
+        deps.release(*mem);
+        done.release(*mem);
+        tasks1.release(*mem);
+        deps1.release(*mem);
+        done1.release(*mem);
         valid = false;
     }
 
@@ -281,9 +288,23 @@ struct Batch {
         }
         par.upload(*mem, pw, s);
         audit_items.upload(*mem, au, s);
-        VCK(cudaStreamSynchronize(s));
-        exec1 = capture(1, s);
-        execG = capture(G, s);
+        if (schedule_mode == 1) {
+            std::vector<std::pair<vlbm_hier*, int>> mm;
+            int base = 0;
+            for (vlbm_hier* h : members) {
+                mm.push_back({h, base});
+                base += h->nlev;
+            }
+            build_tasks(tab, mm, 1, tasks1, deps1, done1, ntasks1, s);
+            build_tasks(tab, mm, G, tasks, deps, done, ntasksG, s);
+            VCK(cudaStreamSynchronize(s));
+            exec1 = capture_tasks(0, s);
+            execG = capture_tasks(1, s);
+        } else {
+            VCK(cudaStreamSynchronize(s));
+            exec1 = capture(1, s);
+            execG = capture(G, s);
+        }
         valid = true;
     }
 
@@ -337,6 +358,230 @@ struct Batch {
             schedule_timed(0, 0, 0, cells, recs, s);
             timed(2, 0, 0, recs, s, [&] { return launch_end_step(par.p, (int)par.n, s); });
         }
+    }
+
+    // ---- persistent task schedule -----------------------------------------
+    int schedule_mode = 1;  // 0: one launch per phase, 1: persistent task kernel
+    DArr<Task> tasks;
+    DArr<int> deps;
+    DArr<unsigned> done;  // [2 counters][ntasks marks]
+    int ntasks1 = 0, ntasksG = 0;
+    DArr<Task> tasks1;
+    DArr<int> deps1;
+    DArr<unsigned> done1;
+
+    // Dependency tracking at tile granularity.  Tasks of one phase write
+    // disjoint cells (each destination slot has exactly one writer per
+    // phase), so writers of the same phase do not wait for one another; a
+    // write of a new phase waits for the previous phase's writers (WAW) and
+    // for everything that read the old content (WAR); a read waits for the
+    // writers of the phase that produced the content (RAW).
+    struct Res {
+        int phase = -1;
+        std::vector<int> writers, readers, prior;
+    };
+    struct Tracker {
+        // per level instance: 3 resources (buffer 0, buffer 1, flags) per tile
+        std::vector<std::vector<Res>> r;
+        std::vector<int> bx, by;
+        std::vector<int> cur;
+        void reset(const std::vector<LevelDev>& tab) {
+            r.assign(tab.size(), {});
+            bx.resize(tab.size());
+            by.resize(tab.size());
+            for (size_t i = 0; i < tab.size(); i++) {
+                bx[i] = (tab[i].nx + TILE - 1) / TILE;
+                by[i] = (tab[i].ny + TILE - 1) / TILE;
+                r[i].assign((size_t)3 * bx[i] * by[i], Res{});
+            }
+        }
+        Res& at(int lid, int kind, int tx, int ty) { return r[lid][((size_t)kind * by[lid] + ty) * bx[lid] + tx]; }
+        void add(const std::vector<int>& v, int task) {
+            for (int q : v)
+                if (q != task) cur.push_back(q);
+        }
+        void read(int lid, int kind, int tx, int ty, int task) {
+            Res& x = at(lid, kind, tx, ty);
+            add(x.writers, task);
+            if (x.readers.empty() || x.readers.back() != task) x.readers.push_back(task);
+        }
+        void write(int lid, int kind, int tx, int ty, int task, int phase) {
+            Res& x = at(lid, kind, tx, ty);
+            if (x.phase != phase) {
+                x.prior.swap(x.writers);
+                x.prior.insert(x.prior.end(), x.readers.begin(), x.readers.end());
+                x.writers.clear();
+                x.readers.clear();
+                x.phase = phase;
+            }
+            add(x.prior, task);
+            if (x.writers.empty() || x.writers.back() != task) x.writers.push_back(task);
+        }
+    };
+    int phase_id = 0;
+
+    // relative buffer ids: level 0 at step s reads (s & 1) and writes the
+    // other; level >= 1 at sub-step 1 reads 0 and writes 1, at 2 the reverse
+    static int src_of(int level, int kk, int step) { return level == 0 ? (step & 1) : (kk == 1 ? 0 : 1); }
+
+    void emit_level(const std::vector<LevelDev>& tab, const std::vector<std::pair<vlbm_hier*, int>>& mem, int l, int kk,
+                    int kkp, int step, Tracker& tr, std::vector<Task>& out, std::vector<int>& dl) {
+        auto wrap = [](int v, int n, bool per, bool& ok) {
+            if (v < 0 || v >= n) {
+                if (!per) { ok = false; return 0; }
+                v = (v % n + n) % n;
+            }
+            return v;
+        };
+        const int phase = phase_id++;
+        for (auto& m : mem) {
+            vlbm_hier* h = m.first;
+            if (l >= h->nlev) continue;
+            const int lid = m.second + l;
+            const LevelDev& L = tab[lid];
+            const Level& HL = h->lev[l];
+            const int bs = src_of(l, kk, step), bd = bs ^ 1;
+            for (const Item& it : HL.act) {
+                const int t = (int)out.size();
+                tr.cur.clear();
+                tr.read(lid, bs, it.tx, it.ty, t);
+                const int di[5] = {0, 1, -1, 0, 0}, dj[5] = {0, 0, 0, 1, -1};
+                for (int d = 0; d < 5; d++) {
+                    bool ok = true;
+                    const int tx = wrap(it.tx + di[d], tr.bx[lid], L.px, ok);
+                    const int ty = wrap(it.ty + dj[d], tr.by[lid], L.py, ok);
+                    if (ok) tr.write(lid, bd, tx, ty, t, phase);
+                }
+                if (l > 0 && HL.recon[(size_t)it.ty * HL.bx + it.tx]) {
+                    const int plid = L.parent;
+                    const LevelDev& P = tab[plid];
+                    const int pbs = src_of(l - 1, kkp, step), pbd = pbs ^ 1;
+                    const int c0x = it.tx * TILE / 2 - 1, c1x = it.tx * TILE / 2 + TILE / 2;
+                    const int c0y = it.ty * TILE / 2 - 1, c1y = it.ty * TILE / 2 + TILE / 2;
+                    int seen[16], ns = 0;
+                    for (int cy2 = c0y; cy2 <= c1y; cy2++)
+                        for (int cx2 = c0x; cx2 <= c1x; cx2++) {
+                            bool ok = true;
+                            const int xx = wrap(cx2, P.nx, P.px, ok), yy = wrap(cy2, P.ny, P.py, ok);
+                            if (!ok) continue;
+                            const int key = (yy / TILE) * tr.bx[plid] + xx / TILE;
+                            bool dup = false;
+                            for (int q = 0; q < ns; q++) dup = dup || seen[q] == key;
+                            if (dup || ns == 16) continue;
+                            seen[ns++] = key;
+                            tr.read(plid, pbs, xx / TILE, yy / TILE, t);
+                            tr.read(plid, pbd, xx / TILE, yy / TILE, t);
+                            tr.read(plid, 2, xx / TILE, yy / TILE, t);
+                        }
+                }
+                std::sort(tr.cur.begin(), tr.cur.end());
+                tr.cur.erase(std::unique(tr.cur.begin(), tr.cur.end()), tr.cur.end());
+                Task T{};
+                T.lid = lid;
+                T.tx = it.tx;
+                T.ty = it.ty;
+                T.kind = 0;
+                T.kk = (signed char)kk;
+                T.kkp = (signed char)kkp;
+                T.step = (signed char)step;
+                T.dep0 = (int)dl.size();
+                T.ndep = (int)tr.cur.size();
+                dl.insert(dl.end(), tr.cur.begin(), tr.cur.end());
+                out.push_back(T);
+            }
+        }
+    }
+
+    void emit_close(const std::vector<LevelDev>& tab, const std::vector<std::pair<vlbm_hier*, int>>& mem, int l, int kk,
+                    int step, Tracker& tr, std::vector<Task>& out, std::vector<int>& dl) {
+        const int phase = phase_id++;
+        for (auto& m : mem) {
+            vlbm_hier* h = m.first;
+            if (l + 1 >= h->nlev) continue;
+            const int lid = m.second + l, clid = lid + 1;
+            const int bd = src_of(l, kk, step) ^ 1;
+            for (const Item& it : h->lev[l].ring) {
+                const int t = (int)out.size();
+                tr.cur.clear();
+                for (int b = 0; b < 2; b++)
+                    for (int a = 0; a < 2; a++) {
+                        const int fx = 2 * it.tx + a, fy = 2 * it.ty + b;
+                        if (fx >= tr.bx[clid] || fy >= tr.by[clid]) continue;
+                        tr.read(clid, 0, fx, fy, t);
+                        tr.read(clid, 1, fx, fy, t);
+                    }
+                tr.write(lid, bd, it.tx, it.ty, t, phase);
+                tr.write(lid, 2, it.tx, it.ty, t, phase);
+                std::sort(tr.cur.begin(), tr.cur.end());
+                tr.cur.erase(std::unique(tr.cur.begin(), tr.cur.end()), tr.cur.end());
+                Task T{};
+                T.lid = lid;
+                T.tx = it.tx;
+                T.ty = it.ty;
+                T.kind = 1;
+                T.kk = (signed char)kk;
+                T.kkp = 0;
+                T.step = (signed char)step;
+                T.dep0 = (int)dl.size();
+                T.ndep = (int)tr.cur.size();
+                dl.insert(dl.end(), tr.cur.begin(), tr.cur.end());
+                out.push_back(T);
+            }
+        }
+    }
+
+    void emit_schedule(const std::vector<LevelDev>& tab, const std::vector<std::pair<vlbm_hier*, int>>& mem, int l,
+                       int kk, int kkp, int step, Tracker& tr, std::vector<Task>& out, std::vector<int>& dl) {
+        emit_level(tab, mem, l, kk, kkp, step, tr, out, dl);
+        if (l + 1 < maxlev && sweep[l + 1].n > 0) {
+            emit_schedule(tab, mem, l + 1, 1, kk, step, tr, out, dl);
+            emit_schedule(tab, mem, l + 1, 2, kk, step, tr, out, dl);
+            emit_close(tab, mem, l, kk, step, tr, out, dl);
+        }
+    }
+
+    void build_tasks(const std::vector<LevelDev>& tab, const std::vector<std::pair<vlbm_hier*, int>>& mem, int nsteps,
+                     DArr<Task>& dt, DArr<int>& dd, DArr<unsigned>& dn, int& count, cudaStream_t s) {
+        Tracker tr;
+        tr.reset(tab);
+        phase_id = 0;
+        std::vector<Task> out;
+        std::vector<int> dl;
+        for (int st = 0; st < nsteps; st++) emit_schedule(tab, mem, 0, 0, 0, st, tr, out, dl);
+        count = (int)out.size();
+        dt.upload(*mem_ptr(), out, s);
+        if (dl.empty()) dl.push_back(0);
+        dd.upload(*mem_ptr(), dl, s);
+        dn.ensure(*mem_ptr(), (size_t)count + 2);
+    }
+    DevMem* mem_ptr() { return mem; }
+
+    void task_launch(int which, cudaStream_t s) {
+        DArr<Task>& t = which ? tasks : tasks1;
+        DArr<int>& d = which ? deps : deps1;
+        DArr<unsigned>& dn = which ? done : done1;
+        const int n = which ? ntasksG : ntasks1;
+        const int steps = which ? G : 1;
+        VCK(cudaMemsetAsync(dn.p, 0, ((size_t)n + 2) * sizeof(unsigned), s));
+        VCK(launch_tasks(levs.p, t.p, n, d.p, dn.p + 2, (int*)dn.p, par.p, (int)par.n, steps & 1, variant, max_ctas, s));
+    }
+
+    cudaGraphExec_t capture_tasks(int which, cudaStream_t s) {
+        cudaGraph_t g = nullptr;
+        VCK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        try {
+            task_launch(which, s);
+        } catch (...) {
+            cudaStreamEndCapture(s, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+        }
+        VCK(cudaStreamEndCapture(s, &g));
+        cudaGraphExec_t ex = nullptr;
+        cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        VCK(e);
+        return ex;
     }
 
     void advance(long long n, cudaStream_t s) {
@@ -476,6 +721,7 @@ void build_lists(vlbm_hier* h) {
         L.ring.clear();
         L.cov.clear();
         L.in.clear();
+        L.recon.assign((size_t)L.bx * L.by, 0);
         L.active_cells = 0;
         for (int jb = 0; jb < L.by; jb++)
             for (int ib = 0; ib < L.bx; ib++) {
@@ -490,16 +736,18 @@ void build_lists(vlbm_hier* h) {
                 L.act.push_back(it);
                 L.active_cells += (long long)(std::min(L.nx, ib * TILE + TILE) - ib * TILE) *
                                   (std::min(L.ny, jb * TILE + TILE) - jb * TILE);
-                bool ring = false;
+                bool ring = false, rec = false;
                 const int di[4] = {1, -1, 0, 0}, dj[4] = {0, 0, 1, -1};
-                for (int d = 0; d < 4 && !ring; d++) {
+                for (int d = 0; d < 4; d++) {
                     int i2 = ib + di[d], j2 = jb + dj[d];
                     if (i2 < 0 || i2 >= L.bx) { if (!px) continue; i2 = (i2 + L.bx) % L.bx; }
                     if (j2 < 0 || j2 >= L.by) { if (!py) continue; j2 = (j2 + L.by) % L.by; }
                     const size_t b2 = (size_t)j2 * L.bx + i2;
-                    ring = L.bin[b2] && L.bcov[b2];
+                    ring = ring || (L.bin[b2] && L.bcov[b2]);
+                    rec = rec || !L.bin[b2];
                 }
                 if (ring) L.ring.push_back(it);
+                L.recon[b] = rec;
             }
     }
 }
@@ -674,6 +922,7 @@ void ensure_own_batch(vlbm_hier* h) {
         h->own->variant = h->tune.variant;
         h->own->max_ctas = h->tune.max_ctas;
         h->own->G = h->tune.graph_steps;
+        h->own->schedule_mode = h->tune.schedule;
         h->own->build(h->stream);
     }
 }
@@ -975,7 +1224,8 @@ int32_t vlbm_num_variants(void) { return sweep_variants(); }
 
 vlbm_status vlbm_set_tuning(vlbm_hier* h, const vlbm_tuning* t) {
     return run(h, [&] {
-        if (!t || t->variant < 0 || t->variant >= sweep_variants() || t->max_ctas < 0 || t->graph_steps < 1)
+        if (!t || t->variant < 0 || t->variant >= sweep_variants() || t->max_ctas < 0 || t->graph_steps < 1 ||
+            t->graph_steps > 64 || t->schedule < 0 || t->schedule > 1)
             throw Fail{VLBM_ERR_ARG, "bad tuning"};
         if (sweep_variant_needs_om_minus1(t->variant) && h->om != -1.0)
             throw Fail{VLBM_ERR_ARG, "variant applies only when 1 - 2 beta == -1"};

@@ -140,9 +140,22 @@ __device__ __forceinline__ double minmod(double a, double b) {
     return 0.0;
 }
 
-__device__ __forceinline__ void level_bufs(const LevelDev& L, int kk, const double*& src, double*& dst) {
+// Loads of data that may have been written earlier in the same launch (the
+// persistent task kernel) go to L2 (ld.global.cg), never to a possibly stale
+// L1 line; the per-phase kernels read data from earlier launches.
+template <bool COH, class T>
+__device__ __forceinline__ T ld(const T* p) {
+    if constexpr (COH) return __ldcg(p);
+    else return __ldg(p);
+}
+
+// Source and destination buffers of a level's step.  Level 0 ping-pongs on
+// the hierarchy's parity word (advanced by `step` inside a multi-step
+// launch); level l >= 1 takes two steps per parent step: sub-step 1 reads
+// buffer 0 and writes buffer 1, sub-step 2 the reverse.
+__device__ __forceinline__ void level_bufs(const LevelDev& L, int kk, int step, const double*& src, double*& dst) {
     if (L.level == 0) {
-        const int par = *L.par0;
+        const int par = (*L.par0 + step) & 1;
         src = L.buf[par];
         dst = L.buf[par ^ 1];
     } else {
@@ -161,9 +174,10 @@ __device__ __forceinline__ int state_buf(const LevelDev& L) { return L.level == 
 // Boundary values and reconstructed coarse-to-fine values for the incoming
 // populations of a cell whose upwind neighbour is outside the domain or in
 // coarser territory.  fs holds the cell's post-collision populations.
+template <bool COH>
 __device__ __noinline__ void sweep_special(const LevelDev* __restrict__ levs, const LevelDev& L, int x, int y,
                                           long long c, uint32_t fl, const double* fs, double* dst, int kk,
-                                          int kkp) {
+                                          int kkp, int step) {
     // boundary conditions
     if (fl & F_BND) {
         for (int i = 0; i < 4; i++) {
@@ -195,7 +209,7 @@ __device__ __noinline__ void sweep_special(const LevelDev* __restrict__ levs, co
     const LevelDev& P = levs[L.parent];
     const double* psrc;
     double* pdst;
-    level_bufs(P, kkp, psrc, pdst);
+    level_bufs(P, kkp, step, psrc, pdst);
     const double wk = (kk == 1) ? -0.25 : 0.25;
     for (int i = 0; i < 4; i++) {
         if (!(rec & (1u << i))) continue;
@@ -218,9 +232,9 @@ __device__ __noinline__ void sweep_special(const LevelDev* __restrict__ levs, co
             if (my < 0) { if (P.py) { my += P.ny; hmy += P.ny; } else okm = false; }
             if (qy >= P.ny) { if (P.py) { qy -= P.ny; hpy -= P.ny; } else okp = false; }
         }
-        if (okm) okm = (P.flags[(long long)my * P.pitch + mx] & (F_IN | F_COV)) == F_IN;
-        if (okp) okp = (P.flags[(long long)qy * P.pitch + qx] & (F_IN | F_COV)) == F_IN;
-        const bool fresh = (P.flags[(long long)l0y * P.pitch + l0x] >> (F_FRESH_SHIFT + d)) & 1u;
+        if (okm) okm = (ld<COH>(P.flags + (long long)my * P.pitch + mx) & (F_IN | F_COV)) == F_IN;
+        if (okp) okp = (ld<COH>(P.flags + (long long)qy * P.pitch + qx) & (F_IN | F_COV)) == F_IN;
+        const bool fresh = (ld<COH>(P.flags + (long long)l0y * P.pitch + l0x) >> (F_FRESH_SHIFT + d)) & 1u;
         const long long ch = (long long)hy * P.pitch + hx;
         const long long cm = (long long)hmy * P.pitch + hmx;
         const long long cp = (long long)hpy * P.pitch + hpx;
@@ -228,18 +242,54 @@ __device__ __noinline__ void sweep_special(const LevelDev* __restrict__ levs, co
         const double wj = j ? 0.25 : -0.25;
         for (int k = 0; k < 4; k++) {
             const long long qo = (long long)(4 * d + k) * P.plane;
-            const double a = pdst[qo + ch];
-            const double ap = fresh ? a : psrc[qo + ch];
+            const double a = ld<COH>(pdst + qo + ch);
+            const double ap = fresh ? a : ld<COH>(psrc + qo + ch);
             double s = 0.0;
-            if (okm && okp) s = minmod(a - pdst[qo + cm], pdst[qo + cp] - a);
+            if (okm && okp) s = minmod(a - ld<COH>(pdst + qo + cm), ld<COH>(pdst + qo + cp) - a);
             dst[(long long)(4 * i + k) * L.plane + c] = fma(s, wj, fma(a - ap, wk, a));
         }
     }
 }
 
+// One cell of one level step: load the 16 populations, collide, push, then
+// the boundary / reconstruction slow path.  kk: this level's sub-step (1, 2)
+// within its parent's step (ignored on level 0); kkp: the parent's
+// sub-step; step: coarse step index inside a multi-step launch.
+template <int P, bool COH>
+__device__ __forceinline__ void sweep_cell(const LevelDev* __restrict__ levs, const LevelDev& L, int x, int y, int kk,
+                                           int kkp, int step) {
+    const int nx = L.nx, ny = L.ny;
+    if (x >= nx || y >= ny) return;
+    const long long c = (long long)y * L.pitch + x;
+    const uint32_t fl = ld<COH>(L.flags + c);
+    if ((fl & (F_IN | F_COV)) != F_IN) return;
+    const double* src;
+    double* dst;
+    level_bufs(L, kk, step, src, dst);
+    const long long plane = L.plane;
+    double f[16];
+#pragma unroll
+    for (int q = 0; q < 16; q++) f[q] = ld<COH>(src + q * plane + c);
+    if (!collide_p<P>(f, L.om, L.hb, L.bcs, L.gm1)) atomicOr(L.status, ST_NONPHYS);
+    // push streaming (Eq. 5): f*_i lands on x + c_i
+    long long cxp = c + 1, cxm = c - 1, cyp = c + L.pitch, cym = c - L.pitch;
+    bool oxp = true, oxm = true, oyp = true, oym = true;
+    if (x == nx - 1) { if (L.px) cxp = c - (nx - 1); else oxp = false; }
+    if (x == 0) { if (L.px) cxm = c + (nx - 1); else oxm = false; }
+    if (y == ny - 1) { if (L.py) cyp = c - (long long)(ny - 1) * L.pitch; else oyp = false; }
+    if (y == 0) { if (L.py) cym = c + (long long)(ny - 1) * L.pitch; else oym = false; }
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        if (oxp) dst[(0 + k) * plane + cxp] = f[0 + k];
+        if (oxm) dst[(4 + k) * plane + cxm] = f[4 + k];
+        if (oyp) dst[(8 + k) * plane + cyp] = f[8 + k];
+        if (oym) dst[(12 + k) * plane + cym] = f[12 + k];
+    }
+    if (fl & (F_BND | F_RECON_MASK)) sweep_special<COH>(levs, L, x, y, c, fl, f, dst, kk, kkp, step);
+}
+
 // One step of one level for every tile in `items` (all of the same level
-// index within their hierarchies).  kk: this level's sub-step (1, 2) within
-// its parent's step (ignored on level 0); kkp: the parent's sub-step.
+// index within their hierarchies).
 template <int P, int MINB>
 __global__ void __launch_bounds__(CTA_THREADS, MINB)
 sweep_kernel(const LevelDev* __restrict__ levs, const Item* __restrict__ items, int nitems, int kk, int kkp) {
@@ -248,81 +298,127 @@ sweep_kernel(const LevelDev* __restrict__ levs, const Item* __restrict__ items, 
     const int cy = (threadIdx.x >> 3) & 7;
     for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
         const Item w = items[it];
-        const LevelDev& L = levs[w.lid];
-        const int x = w.tx * TILE + cx;
-        const int y = w.ty * TILE + cy;
-        const int nx = L.nx, ny = L.ny;
-        if (x >= nx || y >= ny) continue;
-        const long long c = (long long)y * L.pitch + x;
-        const uint32_t fl = L.flags[c];
-        if ((fl & (F_IN | F_COV)) != F_IN) continue;
-        const double* src;
-        double* dst;
-        level_bufs(L, kk, src, dst);
-        const long long plane = L.plane;
-        double f[16];
-#pragma unroll
-        for (int q = 0; q < 16; q++) f[q] = __ldg(src + q * plane + c);
-        if (!collide_p<P>(f, L.om, L.hb, L.bcs, L.gm1)) atomicOr(L.status, ST_NONPHYS);
-        // push streaming (Eq. 5): f*_i lands on x + c_i
-        long long cxp = c + 1, cxm = c - 1, cyp = c + L.pitch, cym = c - L.pitch;
-        bool oxp = true, oxm = true, oyp = true, oym = true;
-        if (x == nx - 1) { if (L.px) cxp = c - (nx - 1); else oxp = false; }
-        if (x == 0) { if (L.px) cxm = c + (nx - 1); else oxm = false; }
-        if (y == ny - 1) { if (L.py) cyp = c - (long long)(ny - 1) * L.pitch; else oyp = false; }
-        if (y == 0) { if (L.py) cym = c + (long long)(ny - 1) * L.pitch; else oym = false; }
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            if (oxp) dst[(0 + k) * plane + cxp] = f[0 + k];
-            if (oxm) dst[(4 + k) * plane + cxm] = f[4 + k];
-            if (oyp) dst[(8 + k) * plane + cyp] = f[8 + k];
-            if (oym) dst[(12 + k) * plane + cym] = f[12 + k];
-        }
-        if (fl & (F_BND | F_RECON_MASK)) sweep_special(levs, L, x, y, c, fl, f, dst, kk, kkp);
+        sweep_cell<P, false>(levs, levs[w.lid], w.tx * TILE + cx, w.ty * TILE + cy, kk, kkp, 0);
     }
 }
 
-// Reflux (Sec. 3.3, Eq. 24): the pending incoming population of every coarse
-// ring cell is the plain average of the four post-collision values the fine
-// edge cells sent towards it during the cycle, summed (k = 1: j = 0, 1), then
-// (k = 2: j = 0, 1).  Also retires the "no previous sample" marks.
+// Reflux (Sec. 3.3, Eq. 24) for one cell: the pending incoming population of
+// a coarse ring cell is the plain average of the four post-collision values
+// the fine edge cells sent towards it during the cycle, summed (k = 1:
+// j = 0, 1), then (k = 2: j = 0, 1).  Also retires the "no previous sample"
+// marks.
+template <bool COH>
+__device__ __forceinline__ void close_cell(const LevelDev* __restrict__ levs, const LevelDev& L, int x, int y, int kk,
+                                           int step) {
+    if (x >= L.nx || y >= L.ny) return;
+    const long long c = (long long)y * L.pitch + x;
+    const uint32_t fl = ld<COH>(L.flags + c);
+    const uint32_t pend = (fl & F_PEND_MASK) >> F_PEND_SHIFT;
+    if ((fl & (F_IN | F_COV)) != F_IN || !pend) return;
+    const double* src;
+    double* dst;
+    level_bufs(L, kk, step, src, dst);
+    const LevelDev& F = levs[L.child];
+    const double* s1 = F.buf[1];  // fine sub-step 1 wrote buffer 1
+    const double* s2 = F.buf[0];  // fine sub-step 2 wrote buffer 0
+    for (int i = 0; i < 4; i++) {
+        if (!(pend & (1u << i))) continue;
+        const int d = i ^ 1;  // from this cell towards the covered one
+        int gx0, gy0, gx1, gy1;
+        if (d == 0) { gx0 = gx1 = 2 * x + 1; gy0 = 2 * y; gy1 = 2 * y + 1; }
+        else if (d == 1) { gx0 = gx1 = 2 * x; gy0 = 2 * y; gy1 = 2 * y + 1; }
+        else if (d == 2) { gy0 = gy1 = 2 * y + 1; gx0 = 2 * x; gx1 = 2 * x + 1; }
+        else { gy0 = gy1 = 2 * y; gx0 = 2 * x; gx1 = 2 * x + 1; }
+        const long long g0 = (long long)gy0 * F.pitch + gx0;
+        const long long g1 = (long long)gy1 * F.pitch + gx1;
+        for (int k = 0; k < 4; k++) {
+            const long long qo = (long long)(4 * i + k) * F.plane;
+            const double v = ((ld<COH>(s1 + qo + g0) + ld<COH>(s1 + qo + g1)) +
+                              (ld<COH>(s2 + qo + g0) + ld<COH>(s2 + qo + g1))) * 0.25;
+            dst[(long long)(4 * i + k) * L.plane + c] = v;
+        }
+    }
+    if (fl & F_FRESH_MASK) L.flags[c] = (uint16_t)(fl & ~F_FRESH_MASK);
+}
+
 __global__ void close_kernel(const LevelDev* __restrict__ levs, const Item* __restrict__ items, int nitems, int kk) {
     const int sub = threadIdx.x >> 6;
     const int cx = threadIdx.x & 7;
     const int cy = (threadIdx.x >> 3) & 7;
     for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
         const Item w = items[it];
-        const LevelDev& L = levs[w.lid];
-        const int x = w.tx * TILE + cx;
-        const int y = w.ty * TILE + cy;
-        if (x >= L.nx || y >= L.ny) continue;
-        const long long c = (long long)y * L.pitch + x;
-        const uint32_t fl = L.flags[c];
-        const uint32_t pend = (fl & F_PEND_MASK) >> F_PEND_SHIFT;
-        if ((fl & (F_IN | F_COV)) != F_IN || !pend) continue;
-        const double* src;
-        double* dst;
-        level_bufs(L, kk, src, dst);
-        const LevelDev& F = levs[L.child];
-        const double* s1 = F.buf[1];  // fine sub-step 1 wrote buffer 1
-        const double* s2 = F.buf[0];  // fine sub-step 2 wrote buffer 0
-        for (int i = 0; i < 4; i++) {
-            if (!(pend & (1u << i))) continue;
-            const int d = i ^ 1;  // from this cell towards the covered one
-            int gx0, gy0, gx1, gy1;
-            if (d == 0) { gx0 = gx1 = 2 * x + 1; gy0 = 2 * y; gy1 = 2 * y + 1; }
-            else if (d == 1) { gx0 = gx1 = 2 * x; gy0 = 2 * y; gy1 = 2 * y + 1; }
-            else if (d == 2) { gy0 = gy1 = 2 * y + 1; gx0 = 2 * x; gx1 = 2 * x + 1; }
-            else { gy0 = gy1 = 2 * y; gx0 = 2 * x; gx1 = 2 * x + 1; }
-            const long long g0 = (long long)gy0 * F.pitch + gx0;
-            const long long g1 = (long long)gy1 * F.pitch + gx1;
-            for (int k = 0; k < 4; k++) {
-                const long long qo = (long long)(4 * i + k) * F.plane;
-                const double v = ((s1[qo + g0] + s1[qo + g1]) + (s2[qo + g0] + s2[qo + g1])) * 0.25;
-                dst[(long long)(4 * i + k) * L.plane + c] = v;
-            }
+        close_cell<false>(levs, levs[w.lid], w.tx * TILE + cx, w.ty * TILE + cy, kk, 0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the persistent task kernel: every tile of every phase of G coarse steps,
+// of every hierarchy of the batch, in one launch
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void group_bar(int g) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(64) : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Bounded wait on a task's completion mark: gives up after ~2^21 polls
+// (about a second), records a timeout in the hierarchy's status word and
+// returns, so that a broken schedule can never hang the GPU.
+__device__ __forceinline__ void wait_done(const unsigned* p, int* status) {
+    unsigned ns = 32;
+    for (int it = 0; it < (1 << 21); it++) {
+        if (ld_acquire(p)) return;
+        // once any wait of this hierarchy has given up, stop waiting at all
+        if ((it & 255) == 255 && (*(volatile int*)status & ST_TIMEOUT)) return;
+        __nanosleep(ns);
+        if (ns < 512) ns <<= 1;
+    }
+    atomicOr(status, ST_TIMEOUT);
+}
+
+// Tasks are claimed in list order, which is a topological order of their
+// dependencies, so every task a claimed task waits for was claimed earlier
+// by a running thread group: the schedule cannot deadlock, whatever the
+// number of resident CTAs.
+template <int P, int MINB>
+__global__ void __launch_bounds__(CTA_THREADS, MINB)
+task_kernel(const LevelDev* __restrict__ levs, const Task* __restrict__ tasks, int ntasks, const int* __restrict__ deps,
+            unsigned* __restrict__ done, int* counters, int* const* par, int npar, int flip) {
+    __shared__ int s_task[TILES_PER_CTA];
+    const int g = threadIdx.x >> 6;
+    const int lt = threadIdx.x & 63;
+    const int cx = lt & 7, cy = lt >> 3;
+    for (;;) {
+        if (lt == 0) s_task[g] = atomicAdd(&counters[0], 1);
+        group_bar(g);
+        const int t = s_task[g];
+        group_bar(g);
+        if (t >= ntasks) break;
+        const Task T = tasks[t];
+        const LevelDev& L = levs[T.lid];
+        for (int j = lt; j < T.ndep; j += 64) wait_done(done + deps[T.dep0 + j], L.status);
+        group_bar(g);
+        __threadfence();
+        if (T.kind == 0)
+            sweep_cell<P, true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.kkp, T.step);
+        else
+            close_cell<true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.step);
+        __threadfence();
+        group_bar(g);
+        if (lt == 0) {
+            st_release(done + t, 1u);
+            if (atomicAdd(&counters[1], 1) == ntasks - 1 && flip)
+                for (int m = 0; m < npar; m++) *par[m] ^= 1;
         }
-        if (fl & F_FRESH_MASK) L.flags[c] = (uint16_t)(fl & ~F_FRESH_MASK);
     }
 }
 
@@ -719,6 +815,38 @@ cudaError_t launch_sweep(const LevelDev* levs, const Item* items, int n, int kk,
     const int g = tile_grid(n, max_ctas);
     switch (variant) {
 #define X(id, P, B) case id: sweep_kernel<P, B><<<g, CTA_THREADS, 0, s>>>(levs, items, n, kk, kkp); break;
+        VLBM_SWEEP_VARIANTS(X)
+#undef X
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+int task_kernel_ctas(int variant) {
+    static int cache[16] = {0};
+    if (variant < 0 || variant >= 16) return 0;
+    if (cache[variant]) return cache[variant];
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    switch (variant) {
+#define X(id, P, B) case id: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, task_kernel<P, B>, CTA_THREADS, 0); break;
+        VLBM_SWEEP_VARIANTS(X)
+#undef X
+    }
+    cache[variant] = sms * (per > 0 ? per : 1);
+    return cache[variant];
+}
+
+cudaError_t launch_tasks(const LevelDev* levs, const Task* tasks, int ntasks, const int* deps, unsigned* done,
+                         int* counters, int* const* par, int npar, int flip, int variant, int ctas, cudaStream_t s) {
+    if (ntasks <= 0) return cudaSuccess;
+    const int g = ctas > 0 ? ctas : task_kernel_ctas(variant);
+    switch (variant) {
+#define X(id, P, B)                                                                                             \
+    case id:                                                                                                    \
+        task_kernel<P, B><<<g, CTA_THREADS, 0, s>>>(levs, tasks, ntasks, deps, done, counters, par, npar, flip); \
+        break;
         VLBM_SWEEP_VARIANTS(X)
 #undef X
         default: return cudaErrorInvalidValue;

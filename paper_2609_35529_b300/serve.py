@@ -129,55 +129,6 @@ def _start(r, stream):
     return h, cs
 
 
-def serve_batched(reqs, mem_budget, stream=None, keep_results=False):
-    """Continuous batching: returns per-request time-to-solution (s) and the
-    aggregate MLUPS."""
-    for r in reqs:
-        r.lups_done = 0
-    eng = V.Engine(mem_budget, stream=stream)
-    pending = sorted(reqs, key=lambda r: r.arrival)
-    live = {}
-    used = 0
-    nxt = 0
-    t0 = time.perf_counter()
-    total_lups = 0
-    while nxt < len(pending) or live:
-        now = time.perf_counter() - t0
-        # admit arrived requests while memory allows (in arrival order)
-        while nxt < len(pending) and pending[nxt].arrival <= now:
-            r = pending[nxt]
-            if live and used + r.bytes_est > mem_budget:
-                break
-            h, cs = _start(r, stream)
-            slot = eng.admit(h, cs.steps, 4 if r.adaptive else 0)
-            if slot is None:
-                h.close()
-                break
-            live[slot] = (r, h)
-            used += r.bytes_est
-            nxt += 1
-        if not live:
-            if nxt < len(pending):
-                time.sleep(max(0.0, min(0.002, pending[nxt].arrival - (time.perf_counter() - t0))))
-            continue
-        for slot, (r, h) in live.items():
-            r.lups_done += h.info()["lups_per_step"]
-        for slot in eng.step():
-            r, h = live.pop(slot)
-            W, act = h.get_conserved(0)
-            r.done_at = time.perf_counter() - t0
-            if keep_results:
-                r.result = [h.get_populations(l) for l in range(h.nlev)]
-            total_lups += r.lups_done
-            eng.release(slot)
-            h.close()
-            used -= r.bytes_est
-    wall = time.perf_counter() - t0
-    eng.close()
-    tts = np.array([r.done_at - r.arrival for r in reqs])
-    return tts, total_lups / wall / 1e6, wall
-
-
 def serve_one_at_a_time(reqs, stream=None):
     """Each request alone on the GPU, in arrival order."""
     pending = sorted(reqs, key=lambda r: r.arrival)
@@ -206,3 +157,141 @@ def serve_one_at_a_time(reqs, stream=None):
     wall = time.perf_counter() - t0
     tts = np.array([r.done_at - r.arrival for r in reqs])
     return tts, total_lups / wall / 1e6, wall
+
+
+def run_oracle(req):
+    """The oracle's answer for one request (test infrastructure: used only to
+    check agreement on a sample of the trace)."""
+    from oracle import oracle as O
+    cs = make_case(req)
+    o = O.Hierarchy(cs.nx0, cs.ny0, cs.nlev, 2, cs.bc, cs.gamma, cs.c, cs.beta, cs.inflow)
+    o.set_layout(None)
+    o.set_state(0, cs.W[0])
+    if req.adaptive:
+        for _ in range(cs.nlev - 1):
+            o.regrid_tagged(cs.amr["tol"], cs.amr["buffer"], 8)
+    elif cs.nlev > 1:
+        o.regrid(cs.refs)
+    left = cs.steps
+    every = 4 if req.adaptive else 0
+    while left > 0:
+        n = min(left, every) if every else left
+        o.advance(n)
+        left -= n
+        if every and left > 0:
+            o.regrid_tagged(cs.amr["tol"], cs.amr["buffer"], 8)
+    return o
+
+
+def agreement(req, oracle_h):
+    """Worst field-wise relative difference between the served result and the
+    oracle, over every level's active cells (0.0 = identical)."""
+    worst = 0.0
+    for l, fg in enumerate(req.result):
+        a, b = oracle_h.layout(l)
+        act = (a == 1) & (b == 0)
+        fo = oracle_h.get_f(l)
+        Wg = fg.reshape(4, 4, *fg.shape[1:]).sum(axis=0)
+        Wo = fo.reshape(4, 4, *fo.shape[1:]).sum(axis=0)
+        for k in range(4):
+            if not act.any():
+                continue
+            scale = max(float(np.max(np.abs(Wo[k][act]))), 1e-300)
+            worst = max(worst, float(np.max(np.abs(Wg[k][act] - Wo[k][act]))) / scale)
+        if not np.array_equal(fg[:, act], fo[:, act]):
+            worst = max(worst, 1e-300)
+    return worst
+
+
+def main(argv=None):
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="continuous-batching VLBM serving benchmark")
+    ap.add_argument("--requests", type=int, default=512)
+    ap.add_argument("--seed", type=int, default=20261202)
+    ap.add_argument("--load", type=float, default=0.75, help="arrival rate as a fraction of batched capacity")
+    ap.add_argument("--mem-gb", type=float, default=160.0)
+    ap.add_argument("--oracle-sample", type=int, default=32)
+    ap.add_argument("--nmax", type=int, default=1024)
+    args = ap.parse_args(argv)
+    import torch
+    stream = torch.cuda.Stream()
+    reqs = make_requests(args.requests, args.seed, nmax=args.nmax)
+    total = sum(r.lups for r in reqs)
+    budget = int(args.mem_gb * (1 << 30))
+    # capacity: the whole trace offered at once (all arrivals at t = 0)
+    for r in reqs:
+        r.arrival = 0.0
+    _, cap_mlups, cap_wall = serve_batched(reqs, budget, stream=stream)
+    rate = args.load * len(reqs) / cap_wall
+    schedule(reqs, rate, args.seed)
+    sample = set(r.rid for r in sorted(reqs, key=lambda r: r.lups)[: args.oracle_sample])
+    tts_b, ml_b, wall_b = serve_batched(reqs, budget, stream, sample)
+    worst = 0.0
+    for r in reqs:
+        if r.rid in sample:
+            worst = max(worst, agreement(r, run_oracle(r)))
+            r.result = None
+    tts_1, ml_1, wall_1 = serve_one_at_a_time(reqs, stream=stream)
+    out = {"requests": len(reqs), "total_lups": total, "capacity_mlups": round(cap_mlups, 1),
+           "rate_per_s": round(rate, 3), "load": args.load,
+           "batched": {"mlups": round(ml_b, 1), "p50_s": float(np.percentile(tts_b, 50)),
+                       "p99_s": float(np.percentile(tts_b, 99)), "wall_s": wall_b},
+           "one_at_a_time": {"mlups": round(ml_1, 1), "p50_s": float(np.percentile(tts_1, 50)),
+                             "p99_s": float(np.percentile(tts_1, 99)), "wall_s": wall_1},
+           "oracle_sample": len(sample), "oracle_worst_rel_err": worst}
+    print(json.dumps(out))
+    return out
+
+
+def serve_batched(reqs, budget, stream=None, keep_ids=()):
+    """Continuous batching over the engine.  Returns per-request
+    time-to-solution (s), the aggregate MLUPS and the wall time; the final
+    populations of the requests in keep_ids are kept in `result`."""
+    eng = V.Engine(budget, stream=stream)
+    pending = sorted(reqs, key=lambda r: r.arrival)
+    for r in reqs:
+        r.lups_done = 0
+    live = {}
+    used = 0
+    nxt = 0
+    t0 = time.perf_counter()
+    total_lups = 0
+    while nxt < len(pending) or live:
+        now = time.perf_counter() - t0
+        while nxt < len(pending) and pending[nxt].arrival <= now:
+            r = pending[nxt]
+            if live and used + r.bytes_est > budget:
+                break
+            h, cs = _start(r, stream)
+            slot = eng.admit(h, cs.steps, 4 if r.adaptive else 0)
+            if slot is None:
+                h.close()
+                break
+            live[slot] = (r, h)
+            used += r.bytes_est
+            nxt += 1
+        if not live:
+            if nxt < len(pending):
+                time.sleep(max(0.0, min(0.002, pending[nxt].arrival - (time.perf_counter() - t0))))
+            continue
+        for slot, (r, h) in live.items():
+            r.lups_done += h.info()["lups_per_step"]
+        for slot in eng.step():
+            r, h = live.pop(slot)
+            W, act = h.get_conserved(0)
+            r.done_at = time.perf_counter() - t0
+            if r.rid in keep_ids:
+                r.result = [h.get_populations(l) for l in range(h.nlev)]
+            total_lups += r.lups_done
+            eng.release(slot)
+            h.close()
+            used -= r.bytes_est
+    wall = time.perf_counter() - t0
+    eng.close()
+    tts = np.array([r.done_at - r.arrival for r in reqs])
+    return tts, total_lups / wall / 1e6, wall
+
+
+if __name__ == "__main__":
+    main()

@@ -56,7 +56,7 @@ class vlbm_kernel_time(C.Structure):
 
 
 class vlbm_tuning(C.Structure):
-    _fields_ = [("variant", C.c_int32), ("max_ctas", C.c_int32), ("graph_steps", C.c_int32)]
+    _fields_ = [("variant", C.c_int32), ("max_ctas", C.c_int32), ("graph_steps", C.c_int32), ("schedule", C.c_int32)]
 
 
 class vlbm_info(C.Structure):
@@ -294,14 +294,14 @@ class Hierarchy:
         return [{"kind": kinds[r.kind], "level": r.level, "launches": r.launches, "cells": r.cells, "ms": r.ms}
                 for r in recs[: n.value]]
 
-    def set_tuning(self, variant=0, max_ctas=0, graph_steps=8):
-        t = vlbm_tuning(variant, max_ctas, graph_steps)
+    def set_tuning(self, variant=1, max_ctas=0, graph_steps=8, schedule=1):
+        t = vlbm_tuning(variant, max_ctas, graph_steps, schedule)
         _check(self._h, lib().vlbm_set_tuning(self._h, C.byref(t)))
 
     def get_tuning(self):
         t = vlbm_tuning()
         _check(self._h, lib().vlbm_get_tuning(self._h, C.byref(t)))
-        return {"variant": t.variant, "max_ctas": t.max_ctas, "graph_steps": t.graph_steps}
+        return {"variant": t.variant, "max_ctas": t.max_ctas, "graph_steps": t.graph_steps, "schedule": t.schedule}
 
     def last_error(self):
         return lib().vlbm_last_error(self._h).decode()

@@ -122,15 +122,18 @@ def test_two_level_pulse_full_run(V):
     np.testing.assert_allclose(t1, ot, rtol=1e-14, atol=1e-14 * oa.max())
 
 
-def test_three_level_periodic_ragged(V):
+@pytest.mark.parametrize("schedule,graph_steps", [(1, 8), (0, 8), (1, 3)])
+def test_three_level_periodic_ragged(V, schedule, graph_steps):
     """Three levels on a domain whose size is not a multiple of the tile
     (ragged last tile column/row), including a patch that wraps across the
-    periodic seam."""
+    periodic seam; both schedules (per-phase launches and the persistent
+    task kernel, with an odd number of steps per launch)."""
     nx0, ny0 = 52, 44
     refs = I.box_refs(nx0, ny0, 3, [(0, 8, 8, 24, 16), (0, 0, 32, 8, 8), (0, 48, 32, 4, 8)])
     refs[1][24:40, 24:56] = 1
     cs = I.smooth_random(nx0, ny0, 3, refs, seed=21, amp=0.25, beta=0.8, steps=25)
     g = V.Hierarchy.from_case(cs)
+    g.set_tuning(variant=1, graph_steps=graph_steps, schedule=schedule)
     o = oracle_of(cs)
     t0, a0 = g.audit()
     g.advance(cs.steps)
@@ -140,9 +143,11 @@ def test_three_level_periodic_ragged(V):
     assert drift(t0, t1, a0) < 1e-13
 
 
-def test_riemann3_three_levels_outflow(V):
+@pytest.mark.parametrize("schedule", [1, 0])
+def test_riemann3_three_levels_outflow(V, schedule):
     cs = I.riemann3(N=64, nlev=3, steps=60)
     g = V.Hierarchy.from_case(cs)
+    g.set_tuning(schedule=schedule)
     o = oracle_of(cs)
     g.advance(cs.steps)
     o.advance(cs.steps)

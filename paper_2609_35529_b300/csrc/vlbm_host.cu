@@ -156,6 +156,12 @@ struct vlbm_hier {
     DArr<Item> aitems;     // active tiles of every level (audits)
     double* hout = nullptr;  // pinned host copy of the audit result
     vlbm_tuning tune{1, 0, 8, 1};
+    // cached task lists of this hierarchy alone: [0] one step, [1] G steps
+    struct TaskList {
+        std::vector<Task> t;
+        std::vector<int> d, key;
+        int steps = -1;
+    } tl[2];
 
     LevelDev dev(int l, int parent, int child) const {
         LevelDev d{};
@@ -200,6 +206,7 @@ struct Batch {
     int G = 8;
     bool valid = false;
     int max_ctas = 0;  // sweep grid cap (0 = one CTA per 4 tiles)
+    bool multi = true; // also capture the G-step graph (the engine steps one at a time)
     int variant = 0;   // sweep kernel variant
 
     void release() {
@@ -289,21 +296,15 @@ struct Batch {
         par.upload(*mem, pw, s);
         audit_items.upload(*mem, au, s);
         if (schedule_mode == 1) {
-            std::vector<std::pair<vlbm_hier*, int>> mm;
-            int base = 0;
-            for (vlbm_hier* h : members) {
-                mm.push_back({h, base});
-                base += h->nlev;
-            }
-            build_tasks(tab, mm, 1, tasks1, deps1, done1, ntasks1, s);
-            build_tasks(tab, mm, G, tasks, deps, done, ntasksG, s);
+            build_tasks(0, 1, tasks1, deps1, done1, ntasks1, s);
+            if (multi) build_tasks(1, G, tasks, deps, done, ntasksG, s);
             VCK(cudaStreamSynchronize(s));
             exec1 = capture_tasks(0, s);
-            execG = capture_tasks(1, s);
+            if (multi) execG = capture_tasks(1, s);
         } else {
             VCK(cudaStreamSynchronize(s));
             exec1 = capture(1, s);
-            execG = capture(G, s);
+            if (multi) execG = capture(G, s);
         }
         valid = true;
     }
@@ -530,30 +531,31 @@ struct Batch {
         }
     }
 
+    // The recursion always walks the schedule of VLBM_MAX_LEVELS levels so
+    // that phase ids (the merge keys) are the same for every hierarchy.
+    std::vector<int>* keys_out = nullptr;
     void emit_schedule(const std::vector<LevelDev>& tab, const std::vector<std::pair<vlbm_hier*, int>>& mem, int l,
                        int kk, int kkp, int step, Tracker& tr, std::vector<Task>& out, std::vector<int>& dl) {
+        const size_t before = out.size();
         emit_level(tab, mem, l, kk, kkp, step, tr, out, dl);
-        if (l + 1 < maxlev && sweep[l + 1].n > 0) {
+        if (keys_out) keys_out->resize(out.size(), phase_id - 1);
+        if (l + 1 < VLBM_MAX_LEVELS) {
             emit_schedule(tab, mem, l + 1, 1, kk, step, tr, out, dl);
             emit_schedule(tab, mem, l + 1, 2, kk, step, tr, out, dl);
             emit_close(tab, mem, l, kk, step, tr, out, dl);
+            if (keys_out) keys_out->resize(out.size(), phase_id - 1);
         }
+        (void)before;
     }
 
-    void build_tasks(const std::vector<LevelDev>& tab, const std::vector<std::pair<vlbm_hier*, int>>& mem, int nsteps,
-                     DArr<Task>& dt, DArr<int>& dd, DArr<unsigned>& dn, int& count, cudaStream_t s) {
-        Tracker tr;
-        tr.reset(tab);
-        phase_id = 0;
-        std::vector<Task> out;
-        std::vector<int> dl;
-        for (int st = 0; st < nsteps; st++) emit_schedule(tab, mem, 0, 0, 0, st, tr, out, dl);
-        count = (int)out.size();
-        dt.upload(*mem_ptr(), out, s);
-        if (dl.empty()) dl.push_back(0);
-        dd.upload(*mem_ptr(), dl, s);
-        dn.ensure(*mem_ptr(), (size_t)count + 2);
-    }
+    // Task list of one hierarchy alone (local level indices), cached on the
+    // hierarchy until its layout or its steps-per-launch change.
+    void member_tasks(vlbm_hier* h, int which, int nsteps);
+
+    // Merges the members' cached lists phase by phase (a topological order
+    // for every member, interleaving members within a phase) and uploads.
+    void build_tasks(int which, int nsteps, DArr<Task>& dt, DArr<int>& dd, DArr<unsigned>& dn, int& count,
+                     cudaStream_t s);
     DevMem* mem_ptr() { return mem; }
 
     void task_launch(int which, cudaStream_t s) {
@@ -592,6 +594,68 @@ struct Batch {
         while (n-- > 0) VCK(cudaGraphLaunch(exec1, s));
     }
 };
+
+void Batch::member_tasks(vlbm_hier* h, int which, int nsteps) {
+    vlbm_hier::TaskList& L = h->tl[which];
+    if (L.steps == nsteps) return;
+    std::vector<LevelDev> tab;
+    for (int l = 0; l < h->nlev; l++) tab.push_back(h->dev(l, l ? l - 1 : -1, l + 1 < h->nlev ? l + 1 : -1));
+    std::vector<std::pair<vlbm_hier*, int>> mm = {{h, 0}};
+    Tracker tr;
+    tr.reset(tab);
+    phase_id = 0;
+    L.t.clear();
+    L.d.clear();
+    L.key.clear();
+    keys_out = &L.key;
+    for (int st = 0; st < nsteps; st++) emit_schedule(tab, mm, 0, 0, 0, st, tr, L.t, L.d);
+    keys_out = nullptr;
+    L.steps = nsteps;
+}
+
+void Batch::build_tasks(int which, int nsteps, DArr<Task>& dt, DArr<int>& dd, DArr<unsigned>& dn, int& count,
+                        cudaStream_t s) {
+    size_t total = 0, totald = 0;
+    int maxkey = -1;
+    for (vlbm_hier* h : members) {
+        member_tasks(h, which, nsteps);
+        total += h->tl[which].t.size();
+        totald += h->tl[which].d.size();
+        if (!h->tl[which].key.empty()) maxkey = std::max(maxkey, h->tl[which].key.back());
+    }
+    std::vector<Task> out;
+    std::vector<int> dl;
+    out.reserve(total);
+    dl.reserve(totald);
+    const size_t M = members.size();
+    std::vector<size_t> cur(M, 0);
+    std::vector<std::vector<int>> pos(M);
+    std::vector<int> base(M, 0);
+    for (size_t m = 0, b = 0; m < M; m++) {
+        base[m] = (int)b;
+        b += members[m]->nlev;
+        pos[m].assign(members[m]->tl[which].t.size(), -1);
+    }
+    for (int k = 0; k <= maxkey; k++)
+        for (size_t m = 0; m < M; m++) {
+            const vlbm_hier::TaskList& L = members[m]->tl[which];
+            while (cur[m] < L.t.size() && L.key[cur[m]] == k) {
+                const size_t i = cur[m]++;
+                Task T = L.t[i];
+                T.lid += base[m];
+                const int d0 = T.dep0;
+                T.dep0 = (int)dl.size();
+                for (int j = 0; j < T.ndep; j++) dl.push_back(pos[m][L.d[d0 + j]]);
+                pos[m][i] = (int)out.size();
+                out.push_back(T);
+            }
+        }
+    count = (int)out.size();
+    dt.upload(*mem, out, s);
+    if (dl.empty()) dl.push_back(0);
+    dd.upload(*mem, dl, s);
+    dn.ensure(*mem, (size_t)count + 2);
+}
 
 namespace {
 
@@ -768,6 +832,7 @@ void install_layout(vlbm_hier* h, std::vector<uint8_t>* bin, std::vector<uint8_t
         std::swap(L.flags, L.flags_tmp);
     }
     build_lists(h);
+    h->tl[0].steps = h->tl[1].steps = -1;
     std::vector<Item> items;
     std::vector<LevelDev> tab;
     for (int l = 0; l < h->nlev; l++) {
@@ -1230,6 +1295,7 @@ vlbm_status vlbm_set_tuning(vlbm_hier* h, const vlbm_tuning* t) {
         if (sweep_variant_needs_om_minus1(t->variant) && h->om != -1.0)
             throw Fail{VLBM_ERR_ARG, "variant applies only when 1 - 2 beta == -1"};
         h->tune = *t;
+        h->tl[0].steps = h->tl[1].steps = -1;
         if (h->own) h->own->valid = false;
     });
 }
@@ -1281,6 +1347,7 @@ vlbm_status vlbm_engine_create(size_t mem_budget, void* stream, vlbm_engine** ou
     }
     e->mem.s = e->stream;
     e->batch.mem = &e->mem;
+    e->batch.multi = false;
     *out = e;
     return VLBM_OK;
 }

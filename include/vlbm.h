@@ -231,6 +231,30 @@ vlbm_status vlbm_get_tuning(const vlbm_hier* h, vlbm_tuning* t);
  * and synchronises it.  Errors: ERR_ARG, ERR_OOM, ERR_CUDA. */
 vlbm_status vlbm_selftest_fp64(uint64_t seed, int64_t n, uint64_t mismatches[4], double first_bad[16]);
 
+/* Conservation totals of a caller-owned population array, allocating
+ * nothing.  The paper has no counterpart: this serves callers that cannot
+ * allocate device memory when they want the check (an application that
+ * reserves all of its GPU memory up front and forbids later allocations, or
+ * one that holds only raw device pointers to populations it manages) and
+ * so cannot create a hierarchy for vlbm_audit.
+ *   f      device array [16][ny][ld] in the layout of vlbm_get_populations
+ *   out    device array of 8 doubles: weight * sum W_k and weight * sum |W_k|
+ *          over all nx * ny cells, k = rho, rho u, rho v, rho E
+ *   stream cudaStream_t the two kernels run on (NULL = legacy default)
+ * The reduction's partial sums live in one fixed device array of
+ * VLBM_STATIC_MAX_BLOCKS slots (2 MiB, held by every device that loads the
+ * library until exit); each slot covers 4096 cells, so nx * ny is limited to
+ * VLBM_STATIC_MAX_BLOCKS * 4096 cells and larger grids get ERR_ARG.  The
+ * first call on a device looks up the array's device address for that
+ * device; make that first call before any stream capture.  Every call
+ * shares the array: calls whose kernels overlap on the GPU (other streams)
+ * race and must be serialised by the caller.  No cudaMalloc, cudaFree or
+ * allocating library routine is used.  Asynchronous: read `out` after
+ * synchronising `stream`.  Errors: ERR_ARG (null pointers, sizes), ERR_CUDA. */
+#define VLBM_STATIC_MAX_BLOCKS 16384
+vlbm_status vlbm_totals_static(const double* f, int64_t ld, int32_t nx, int32_t ny, double weight, double* out,
+                               void* stream);
+
 /* Human-readable description of the last error on the handle (never NULL). */
 const char* vlbm_last_error(const vlbm_hier* h);
 

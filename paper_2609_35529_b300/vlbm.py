@@ -110,6 +110,8 @@ def lib():
     L.vlbm_get_tuning.restype = C.c_int
     L.vlbm_selftest_fp64.argtypes = [C.c_uint64, i64, C.POINTER(C.c_uint64), dp]
     L.vlbm_selftest_fp64.restype = C.c_int
+    L.vlbm_totals_static.argtypes = [vp, i64, i32, i32, C.c_double, vp, vp]
+    L.vlbm_totals_static.restype = C.c_int
     L.vlbm_last_error.argtypes = [vp]
     L.vlbm_last_error.restype = C.c_char_p
     L.vlbm_destroy.argtypes = [vp]
@@ -305,6 +307,15 @@ class Hierarchy:
 
     def last_error(self):
         return lib().vlbm_last_error(self._h).decode()
+
+
+def totals_static(f_ptr, ld, nx, ny, weight, out_ptr, stream=None):
+    """vlbm_totals_static: conservation totals of a caller-owned device
+    population array [16][ny][ld] into a caller-owned device array of 8
+    doubles, with no device allocation (for callers that cannot allocate)."""
+    st = lib().vlbm_totals_static(f_ptr, int(ld), int(nx), int(ny), float(weight), out_ptr, _stream_handle(stream))
+    if st != 0:
+        raise VlbmError(st, "vlbm_totals_static")
 
 
 def num_variants():

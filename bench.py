@@ -46,6 +46,10 @@ METRIC = "MLUPS (FP64, 1 B300)"
 FLOPS_PER_LUP = 12 + 1 + 15 + 4 + 64
 # algorithmic bytes of one cell update: 16 populations read + 16 written
 BYTES_PER_LUP = 256
+# FP64-pipe operations of one cell update: 62 arithmetic operations plus the
+# IEEE division, which ncu counts as about 5 further FP64-pipe operations
+# (DFMA/DADD/DMUL thread-instructions per cell update in the sweep: 67.1)
+FP64_OPS_PER_LUP = 67
 
 
 def peaks():
@@ -136,6 +140,22 @@ def oracle_rate(case, seconds):
     return lups * n / el / 1e6, n, el
 
 
+def job_time(x, pg, device="cpu"):
+    """The whole job's time: the maximum over ranks (identity on one rank)."""
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(lups_per_step, steps, world, ms):
+    """Whole-job throughput: every rank ran `steps` coarse steps of its own
+    replica (weak scaling), in at most `ms` milliseconds."""
+    return world * lups_per_step * steps / (ms * 1e-3) / 1e6
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -206,6 +226,8 @@ def main():
     case = I.vortex(N=512, steps=args.steps)
     stream = torch.cuda.Stream()
     g = V.Hierarchy.from_case(case, stream=stream)
+    # every step includes the conservation audit (fused into the sweep)
+    g.set_step_totals(True)
     tune = g.get_tuning()
     chunk = max(1, tune["graph_steps"])
     info = g.info()
@@ -217,6 +239,7 @@ def main():
         g.advance(1)
     g.advance(chunk)
     g.sync()
+    g.step_totals()  # drop the warm-up rows
 
     # timed: iterations of `chunk` coarse steps (one graph launch each), the
     # L2 flushed between iterations
@@ -235,14 +258,14 @@ def main():
                 ev[i][1].record(stream)
         torch.cuda.synchronize()
     g.sync()
+    rows = g.step_totals(cap=steps)
+    drift = float(np.max(np.abs(rows[:, :4] - rows[0, :4]) / rows[0, 4:])) if len(rows) else None
     it_ms = [a.elapsed_time(b) for a, b in ev]
     ms = sum(it_ms)
     if pg:
         pg.barrier()
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * lups * steps / (ms * 1e-3) / 1e6
+    ms = job_time(ms, pg, "cuda")
+    value = job_mlups(lups, steps, world, ms)
 
     # roofline of the dominant kernel.  With the persistent schedule one
     # timed iteration is one launch of the task kernel (all sweeps and
@@ -255,6 +278,7 @@ def main():
     hbm_gbs = BYTES_PER_LUP * cells / (launch_ms * 1e-3) / 1e9
     kernel = "task_kernel" if tune["schedule"] == 1 else "sweep_kernel"
     # the per-phase sweep kernel measured alone (eager launches with events)
+    g.set_step_totals(False)
     prof = g.profile(min(steps, 64))
     sweep = [r for r in prof if r["kind"] == "sweep"]
     sw_ms = sum(r["ms"] for r in sweep)
@@ -265,42 +289,50 @@ def main():
             "flops_per_lup": FLOPS_PER_LUP, "peak_basis": "2 FP64 FMA/clk/SM x 148 SMs x sm_max_mhz",
             "hbm": {"achieved": round(hbm_gbs, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
                     "frac": round(hbm_gbs / pk["hbm_gbs"], 4), "peak_source": pk["source"]},
-            "sweep_kernel_alone_mlups": round(sw_cells / sw_ms / 1e3, 1)}
-    launches_per_iter = 1 if tune["schedule"] == 1 else None
+            "sweep_kernel_alone_mlups": round(sw_cells / sw_ms / 1e3, 1),
+            "fp64_pipe": {"ops_per_lup": FP64_OPS_PER_LUP,
+                          "achieved_gops": round(FP64_OPS_PER_LUP * cells / (launch_ms * 1e-3) / 1e9, 1),
+                          "peak_gops_nominal": round(2 * 148 * pk["sm_max_mhz"] * 1e6 / 1e9, 1),
+                          "frac_of_nominal": round(FP64_OPS_PER_LUP * cells / (launch_ms * 1e-3)
+                                                   / (2 * 148 * pk["sm_max_mhz"] * 1e6), 4)}}
+    # schedule 1: the task kernel and the per-step audit reduction
+    launches_per_iter = 2 if tune["schedule"] == 1 else None
     if launches_per_iter is None:
         launches_per_iter = sum(r["launches"] for r in prof) / min(steps, 64) * chunk
 
-    # end to end through the public API with host buffers: initial state from
-    # pinned host memory, per-step conservation totals read back, final state
-    # read back
+    # end to end through the public API with host buffers: the initial state
+    # from pinned host memory, every step's conservation totals read back to
+    # the host (one copy per launch of `chunk` steps), the final state read
+    # back.
     Wh = [torch.from_numpy(np.ascontiguousarray(w)).pin_memory().numpy() for w in case.W]
     h2 = V.Hierarchy(case.nx0, case.ny0, case.nlev, case.bc, case.gamma, case.c, case.beta, dx0=case.dx0,
                      stream=stream)
     h2.regrid_masks(case.refs)
-    h2.set_state(0, Wh[0])
-    h2.set_state(1, Wh[1])
-    h2.advance(2)
-    h2.audit()
+    h2.set_step_totals(True)
+    for l in range(case.nlev):
+        h2.set_state(l, Wh[l])
+    h2.advance(chunk)
+    h2.step_totals()
     torch.cuda.synchronize()
-    n_e2e = min(steps, 1000)
+    n_e2e = min(steps, 2048)
     t0 = time.perf_counter()
     for l in range(case.nlev):
         h2.set_state(l, Wh[l])
-    for _ in range(n_e2e):
-        h2.advance(1)
-        h2.audit()
-    for l in range(case.nlev):
-        h2.get_conserved(l)
+    got = 0
+    for _ in range(n_e2e // chunk):
+        h2.advance(chunk)
+        got += len(h2.step_totals())
+    Wout = [h2.get_conserved(l)[0] for l in range(case.nlev)]
     e2e_s = time.perf_counter() - t0
-    if pg:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    assert got == (n_e2e // chunk) * chunk
+    n_e2e = (n_e2e // chunk) * chunk
+    e2e_s = job_time(e2e_s, pg, "cuda")
     wbytes = sum(w.nbytes for w in case.W)
-    e2e = {"value": round(world * lups * n_e2e / e2e_s / 1e6, 3), "unit": "MLUPS",
+    e2e = {"value": round(job_mlups(lups, n_e2e, world, e2e_s * 1e3), 3), "unit": "MLUPS",
            "h2d_bytes_per_step": wbytes / n_e2e, "d2h_bytes_per_step": 64 + wbytes / n_e2e,
-           "note": "per step: vlbm_advance(1) + vlbm_audit (totals to host); initial W from pinned host "
-                   "memory and final W to host amortised over the steps"}
+           "note": f"{n_e2e} steps through the C ABI: vlbm_set_state from pinned host W, vlbm_advance in "
+                   f"launches of {chunk} steps, each step's conservation totals (64 B) read to the host "
+                   f"after every launch, final W of every level read back"}
 
     if rank == 0:
         cpu = None
@@ -319,6 +351,7 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(round(launches_per_iter * iters)),
+                "conservation": {"max_rel_drift_over_timed_steps": drift, "audited_steps": len(rows)},
                 "clocks": clk.summary()}
         print(json.dumps(line))
     if pg:

@@ -231,6 +231,35 @@ vlbm_status vlbm_get_tuning(const vlbm_hier* h, vlbm_tuning* t);
  * and synchronises it.  Errors: ERR_ARG, ERR_OOM, ERR_CUDA. */
 vlbm_status vlbm_selftest_fp64(uint64_t seed, int64_t n, uint64_t mismatches[4], double first_bad[16]);
 
+/* Checkpoint / resume.  The blob (host memory, versioned) holds what a
+ * coarse step needs at a sync point: the configuration it was made under,
+ * the step count and level-0 parity, every level's block maps, per-cell
+ * flags and state buffer over the whole index space (covered cells keep the
+ * previous coarse samples of Eq. 20).  Loading it into a hierarchy created
+ * with the same nx0, ny0, max_levels, boundaries, gamma, c and beta resumes
+ * the run bit for bit.  save/load synchronise.  Errors: ERR_ARG (size,
+ * magic or configuration mismatch), ERR_CUDA, ERR_STATE. */
+vlbm_status vlbm_checkpoint_size(vlbm_hier* h, size_t* bytes);
+vlbm_status vlbm_checkpoint_save(vlbm_hier* h, void* blob, size_t bytes);
+vlbm_status vlbm_checkpoint_load(vlbm_hier* h, const void* blob, size_t bytes);
+
+/* Per-step conservation audit fused into the sweep (Sec. 4.1.2, 4.1.3, 4.2
+ * report conservation to round-off; this checks it at every coarse step).
+ * With `on`, every coarse step taken by vlbm_advance records the totals of
+ * the state at the START of that step: sum_l 4^-l sum_active W_k and the
+ * same of |W_k| (k = rho, rho u, rho v, rho E).  The sums are accumulated
+ * inside the sweep's first sub-step on every level in 192-bit fixed point
+ * on the integer pipes (resolution 2^-128), so they are exact, independent
+ * of the launch configuration, and rounded once to binary64 (the correctly
+ * rounded sum); no extra pass over the populations is made.  Requires the
+ * persistent schedule (vlbm_tuning.schedule = 1), else ERR_ARG.
+ * vlbm_get_step_totals synchronises and returns, oldest first, the rows
+ * recorded since the previous call (at most the 4096 most recent), each
+ * 8 doubles (totals[4], abs_totals[4]); *n receives the row count.
+ * Errors: ERR_ARG, ERR_CUDA, ERR_NONPHYSICAL, ERR_STATE. */
+vlbm_status vlbm_set_step_totals(vlbm_hier* h, int32_t on);
+vlbm_status vlbm_get_step_totals(vlbm_hier* h, double* out, int64_t cap, int64_t* n);
+
 /* Conservation totals of a caller-owned population array, allocating
  * nothing.  The paper has no counterpart: this serves callers that cannot
  * allocate device memory when they want the check (an application that

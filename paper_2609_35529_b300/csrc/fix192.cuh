@@ -1,0 +1,115 @@
+// Exact accumulation of binary64 values in 192-bit two's-complement fixed
+// point (resolution 2^-128, magnitude below 2^63), on the integer pipes.
+//
+// Integer addition is associative, so a sum does not depend on the order in
+// which cells, tiles or thread groups contribute: the conservation totals
+// come out identical for every launch configuration and equal to the exactly
+// rounded sum of the addends (a value below 2^-75 loses the bits of its
+// significand that fall under 2^-128).  The conversions are the plain
+// definition of the formats: unpack sign, exponent and significand, shift
+// the significand into place, negate; back to binary64 by locating the
+// leading one and rounding to nearest even from the dropped bits.
+#pragma once
+#include <cstdint>
+
+namespace vlbm {
+
+struct Fix192 {
+    unsigned long long w[3];  // little-endian words
+};
+
+__device__ __forceinline__ Fix192 fix_zero() { return Fix192{{0ull, 0ull, 0ull}}; }
+
+__device__ __forceinline__ void fix_add(Fix192& a, const Fix192& b) {
+    const unsigned long long s0 = a.w[0] + b.w[0];
+    const unsigned long long c0 = s0 < a.w[0] ? 1ull : 0ull;
+    const unsigned long long s1 = a.w[1] + b.w[1];
+    unsigned long long c1 = s1 < a.w[1] ? 1ull : 0ull;
+    const unsigned long long s1c = s1 + c0;
+    c1 += s1c < s1 ? 1ull : 0ull;
+    a.w[2] = a.w[2] + b.w[2] + c1;
+    a.w[1] = s1c;
+    a.w[0] = s0;
+}
+
+__device__ __forceinline__ void fix_neg(Fix192& a) {
+    a.w[0] = ~a.w[0];
+    a.w[1] = ~a.w[1];
+    a.w[2] = ~a.w[2];
+    const Fix192 one{{1ull, 0ull, 0ull}};
+    fix_add(a, one);
+}
+
+// v * 2^scale_exp as fixed point (truncated below 2^-128; NaN/inf give 0,
+// the sweep reports them separately).
+__device__ __forceinline__ Fix192 fix_from_double(double v, int scale_exp) {
+    const unsigned long long B = (unsigned long long)__double_as_longlong(v);
+    int E = (int)((B >> 52) & 0x7FFull);
+    unsigned long long m = B & 0x000FFFFFFFFFFFFFull;
+    Fix192 r = fix_zero();
+    if (E == 2047) return r;
+    if (E) m |= 0x0010000000000000ull;
+    else E = 1;
+    if (m == 0) return r;
+    // value = m * 2^(E - 1075 + scale_exp); fixed = value * 2^128
+    const int sh = E - 1075 + scale_exp + 128;
+    if (sh >= 0) {
+        if (sh >= 192) return r;  // out of range: the caller's magnitudes never get here
+        const int wi = sh >> 6, b = sh & 63;
+        r.w[wi] = m << b;
+        if (b > 11 && wi + 1 < 3) r.w[wi + 1] = m >> (64 - b);
+    } else {
+        const int rs = -sh;
+        if (rs >= 64) return r;
+        r.w[0] = m >> rs;
+    }
+    if (B >> 63) fix_neg(r);
+    return r;
+}
+
+__device__ __forceinline__ Fix192 fix_shfl_down(const Fix192& a, int off) {
+    Fix192 r;
+    for (int i = 0; i < 3; i++) r.w[i] = __shfl_down_sync(0xffffffffu, a.w[i], off);
+    return r;
+}
+
+// Correctly rounded (nearest, ties to even) binary64 value of a * 2^-128.
+__device__ __forceinline__ double fix_to_double(Fix192 a) {
+    const bool neg = (a.w[2] >> 63) != 0;
+    if (neg) fix_neg(a);
+    int p = -1;  // index of the leading one
+    for (int i = 2; i >= 0 && p < 0; i--)
+        if (a.w[i]) p = 64 * i + 63 - __clzll((long long)a.w[i]);
+    if (p < 0) return 0.0;
+    unsigned long long m;
+    bool rnd = false, sticky = false;
+    if (p <= 52) {
+        m = a.w[0];
+    } else {
+        const int s = p - 52;  // shift right by s: keep 53 bits
+        auto bit = [&](int k) { return (a.w[k >> 6] >> (k & 63)) & 1ull; };
+        m = 0;
+        for (int k = 52; k >= 0; k--) m = (m << 1) | bit(s + k);
+        rnd = bit(s - 1) != 0;
+        for (int k = 0; k < s - 1 && !sticky; k++) sticky = bit(k) != 0;
+        if (rnd && (sticky || (m & 1ull))) {
+            m += 1;
+            if (m >> 53) {
+                m >>= 1;
+                p += 1;
+            }
+        }
+    }
+    double r;
+    if (p <= 52) {
+        // exact integer multiple of 2^-128: scale by powers of two
+        r = (double)m;  // m < 2^53: exact
+    } else {
+        r = (double)m;
+        r = ldexp(r, p - 52);
+    }
+    r = ldexp(r, -128);
+    return neg ? -r : r;
+}
+
+}  // namespace vlbm

@@ -77,6 +77,7 @@ struct Task {
     unsigned short tx, ty;
     signed char kind, kk, kkp, step;
     int dep0, ndep;
+    int aslot;  // first sub-step sweep of its coarse step: slot of its audit sums, else -1
 };
 
 }  // namespace vlbm

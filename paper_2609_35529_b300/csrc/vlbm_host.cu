@@ -156,6 +156,10 @@ struct vlbm_hier {
     DArr<Item> aitems;     // active tiles of every level (audits)
     double* hout = nullptr;  // pinned host copy of the audit result
     vlbm_tuning tune{1, 0, 8, 1};
+    // per-step conservation totals recorded by vlbm_advance (pinned ring)
+    bool step_audit = false;
+    double* hist = nullptr;
+    long long hist_cap = 4096, hist_n = 0, hist_read = 0;
     // cached task lists of this hierarchy alone: [0] one step, [1] G steps
     struct TaskList {
         std::vector<Task> t;
@@ -226,6 +230,11 @@ struct Batch {
         tasks1.release(*mem);
         deps1.release(*mem);
         done1.release(*mem);
+        for (int w = 0; w < 2; w++) {
+            aslots[w].release(*mem);
+            aseg[w].release(*mem);
+            aout[w].release(*mem);
+        }
         valid = false;
     }
 
@@ -370,6 +379,12 @@ struct Batch {
     DArr<Task> tasks1;
     DArr<int> deps1;
     DArr<unsigned> done1;
+    // fused per-step conservation audit: [0] one-step list, [1] G-step list
+    bool audit = false;
+    DArr<unsigned long long> aslots[2];
+    DArr<int> aseg[2];
+    DArr<double> aout[2];
+    int nseg[2] = {0, 0};
 
     // Dependency tracking at tile granularity.  Tasks of one phase write
     // disjoint cells (each destination slot has exactly one writer per
@@ -426,7 +441,7 @@ struct Batch {
     static int src_of(int level, int kk, int step) { return level == 0 ? (step & 1) : (kk == 1 ? 0 : 1); }
 
     void emit_level(const std::vector<LevelDev>& tab, const std::vector<std::pair<vlbm_hier*, int>>& mem, int l, int kk,
-                    int kkp, int step, Tracker& tr, std::vector<Task>& out, std::vector<int>& dl) {
+                    int kkp, int step, Tracker& tr, std::vector<Task>& out, std::vector<int>& dl, bool first = false) {
         auto wrap = [](int v, int n, bool per, bool& ok) {
             if (v < 0 || v >= n) {
                 if (!per) { ok = false; return 0; }
@@ -487,6 +502,7 @@ struct Batch {
                 T.step = (signed char)step;
                 T.dep0 = (int)dl.size();
                 T.ndep = (int)tr.cur.size();
+                T.aslot = first ? -2 : -1;  // -2: audit task, slot assigned at merge
                 dl.insert(dl.end(), tr.cur.begin(), tr.cur.end());
                 out.push_back(T);
             }
@@ -525,6 +541,7 @@ struct Batch {
                 T.step = (signed char)step;
                 T.dep0 = (int)dl.size();
                 T.ndep = (int)tr.cur.size();
+                T.aslot = -1;
                 dl.insert(dl.end(), tr.cur.begin(), tr.cur.end());
                 out.push_back(T);
             }
@@ -534,14 +551,18 @@ struct Batch {
     // The recursion always walks the schedule of VLBM_MAX_LEVELS levels so
     // that phase ids (the merge keys) are the same for every hierarchy.
     std::vector<int>* keys_out = nullptr;
+    // `first`: this level step is the first of its coarse step on its level,
+    // i.e. it starts from the state at the beginning of the coarse step (its
+    // sweep tasks carry the per-step conservation audit).
     void emit_schedule(const std::vector<LevelDev>& tab, const std::vector<std::pair<vlbm_hier*, int>>& mem, int l,
-                       int kk, int kkp, int step, Tracker& tr, std::vector<Task>& out, std::vector<int>& dl) {
+                       int kk, int kkp, int step, Tracker& tr, std::vector<Task>& out, std::vector<int>& dl,
+                       bool first = true) {
         const size_t before = out.size();
-        emit_level(tab, mem, l, kk, kkp, step, tr, out, dl);
+        emit_level(tab, mem, l, kk, kkp, step, tr, out, dl, first);
         if (keys_out) keys_out->resize(out.size(), phase_id - 1);
         if (l + 1 < VLBM_MAX_LEVELS) {
-            emit_schedule(tab, mem, l + 1, 1, kk, step, tr, out, dl);
-            emit_schedule(tab, mem, l + 1, 2, kk, step, tr, out, dl);
+            emit_schedule(tab, mem, l + 1, 1, kk, step, tr, out, dl, first);
+            emit_schedule(tab, mem, l + 1, 2, kk, step, tr, out, dl, false);
             emit_close(tab, mem, l, kk, step, tr, out, dl);
             if (keys_out) keys_out->resize(out.size(), phase_id - 1);
         }
@@ -565,7 +586,10 @@ struct Batch {
         const int n = which ? ntasksG : ntasks1;
         const int steps = which ? G : 1;
         VCK(cudaMemsetAsync(dn.p, 0, ((size_t)n + 2) * sizeof(unsigned), s));
-        VCK(launch_tasks(levs.p, t.p, n, d.p, dn.p + 2, (int*)dn.p, par.p, (int)par.n, steps & 1, variant, max_ctas, s));
+        unsigned long long* sl = audit ? aslots[which].p : nullptr;
+        VCK(launch_tasks(levs.p, t.p, n, d.p, dn.p + 2, (int*)dn.p, par.p, (int)par.n, steps & 1, variant, max_ctas,
+                         sl, s));
+        if (audit) VCK(launch_audit_segments(aslots[which].p, aseg[which].p, nseg[which], aout[which].p, s));
     }
 
     cudaGraphExec_t capture_tasks(int which, cudaStream_t s) {
@@ -628,6 +652,15 @@ void Batch::build_tasks(int which, int nsteps, DArr<Task>& dt, DArr<int>& dd, DA
     out.reserve(total);
     dl.reserve(totald);
     const size_t M = members.size();
+    // audit slots: segment (member m, step st) holds the audit tasks of that
+    // member's coarse step st, contiguously
+    std::vector<int> segoff(M * nsteps + 1, 0), segfill(M * nsteps, 0);
+    if (audit) {
+        for (size_t m = 0; m < M; m++)
+            for (const Task& T : members[m]->tl[which].t)
+                if (T.aslot == -2) segoff[m * nsteps + T.step + 1]++;
+        for (size_t i = 0; i < M * (size_t)nsteps; i++) segoff[i + 1] += segoff[i];
+    }
     std::vector<size_t> cur(M, 0);
     std::vector<std::vector<int>> pos(M);
     std::vector<int> base(M, 0);
@@ -643,6 +676,12 @@ void Batch::build_tasks(int which, int nsteps, DArr<Task>& dt, DArr<int>& dd, DA
                 const size_t i = cur[m]++;
                 Task T = L.t[i];
                 T.lid += base[m];
+                if (T.aslot == -2 && audit) {
+                    const size_t sg = m * nsteps + T.step;
+                    T.aslot = segoff[sg] + segfill[sg]++;
+                } else {
+                    T.aslot = -1;
+                }
                 const int d0 = T.dep0;
                 T.dep0 = (int)dl.size();
                 for (int j = 0; j < T.ndep; j++) dl.push_back(pos[m][L.d[d0 + j]]);
@@ -655,6 +694,12 @@ void Batch::build_tasks(int which, int nsteps, DArr<Task>& dt, DArr<int>& dd, DA
     if (dl.empty()) dl.push_back(0);
     dd.upload(*mem, dl, s);
     dn.ensure(*mem, (size_t)count + 2);
+    if (audit) {
+        nseg[which] = (int)(M * nsteps);
+        aslots[which].ensure(*mem, (size_t)std::max(1, segoff.back()) * 24);
+        aseg[which].upload(*mem, segoff, s);
+        aout[which].ensure(*mem, (size_t)nseg[which] * 8);
+    }
 }
 
 namespace {
@@ -975,6 +1020,8 @@ void destroy_levels(vlbm_hier* h) {
     h->aitems.release(h->mem);
     if (h->hout) cudaFreeHost(h->hout);
     h->hout = nullptr;
+    if (h->hist) cudaFreeHost(h->hist);
+    h->hist = nullptr;
 }
 
 void ensure_own_batch(vlbm_hier* h) {
@@ -988,6 +1035,7 @@ void ensure_own_batch(vlbm_hier* h) {
         h->own->max_ctas = h->tune.max_ctas;
         h->own->G = h->tune.graph_steps;
         h->own->schedule_mode = h->tune.schedule;
+        h->own->audit = h->step_audit && h->tune.schedule == 1;
         h->own->build(h->stream);
     }
 }
@@ -1144,14 +1192,178 @@ vlbm_status vlbm_get_populations(vlbm_hier* h, int32_t level, double* f, int64_t
     return pop_copy(h, level, f, ld, on_device, 1);
 }
 
+// Queues the copy of `rows` per-step totals (8 doubles each) from the
+// device block `src` into the hierarchy's pinned history ring.
+static void record_rows(vlbm_hier* h, const double* src, long long rows) {
+    long long done = 0;
+    while (done < rows) {
+        const long long at = (h->hist_n + done) % h->hist_cap;
+        const long long n = std::min(rows - done, h->hist_cap - at);
+        VCK(cudaMemcpyAsync(h->hist + at * 8, src + done * 8, (size_t)n * 8 * sizeof(double), cudaMemcpyDeviceToHost,
+                            h->stream));
+        done += n;
+    }
+    h->hist_n += rows;
+}
+
 vlbm_status vlbm_advance(vlbm_hier* h, int64_t coarse_steps) {
     return run(h, [&] {
         if (coarse_steps < 0) throw Fail{VLBM_ERR_ARG, "negative step count"};
         if (h->engine) throw Fail{VLBM_ERR_ARG, "hierarchy is resident in an engine"};
         if (coarse_steps == 0) return;
         ensure_own_batch(h);
-        h->own->advance(coarse_steps, h->stream);
+        Batch& b = *h->own;
+        if (!b.audit) {
+            b.advance(coarse_steps, h->stream);
+        } else {
+            long long n = coarse_steps;
+            while (n >= b.G) {
+                VCK(cudaGraphLaunch(b.execG, h->stream));
+                record_rows(h, b.aout[1].p, b.G);
+                n -= b.G;
+            }
+            for (; n > 0; n--) {
+                VCK(cudaGraphLaunch(b.exec1, h->stream));
+                record_rows(h, b.aout[0].p, 1);
+            }
+        }
         h->steps += coarse_steps;
+    });
+}
+
+// ---- checkpoint / resume ---------------------------------------------------
+
+namespace {
+struct CkptHeader {
+    char magic[8];
+    int32_t version, nlev, nx0, ny0, bc[4];
+    double gamma, c, beta;
+    int64_t steps;
+    int32_t par0, pad;
+};
+
+size_t ckpt_bytes(const vlbm_hier* h) {
+    size_t b = sizeof(CkptHeader);
+    for (int l = 0; l < h->nlev; l++) {
+        const Level& L = h->lev[l];
+        b += 2 * (size_t)L.bx * L.by;                        // block maps
+        b += (size_t)L.plane * sizeof(uint16_t);             // flags
+        b += (size_t)16 * L.plane * sizeof(double);          // state buffer
+    }
+    return b;
+}
+}  // namespace
+
+vlbm_status vlbm_checkpoint_size(vlbm_hier* h, size_t* bytes) {
+    return run(h, [&] {
+        if (!bytes) throw Fail{VLBM_ERR_ARG, "null size"};
+        *bytes = ckpt_bytes(h);
+    });
+}
+
+vlbm_status vlbm_checkpoint_save(vlbm_hier* h, void* blob, size_t bytes) {
+    return run(h, [&] {
+        if (!blob || bytes < ckpt_bytes(h)) throw Fail{VLBM_ERR_ARG, "blob too small"};
+        VCK(cudaStreamSynchronize(h->stream));
+        check_status(h);
+        int par0 = 0;
+        VCK(cudaMemcpy(&par0, h->words, sizeof(int), cudaMemcpyDeviceToHost));
+        CkptHeader H{};
+        std::memcpy(H.magic, "VLBMCKP1", 8);
+        H.version = 1;
+        H.nlev = h->nlev;
+        H.nx0 = h->cfg.nx0;
+        H.ny0 = h->cfg.ny0;
+        for (int i = 0; i < 4; i++) H.bc[i] = h->cfg.bc[i];
+        H.gamma = h->cfg.gamma;
+        H.c = h->cfg.c;
+        H.beta = h->cfg.beta;
+        H.steps = h->steps;
+        H.par0 = par0;
+        char* p = (char*)blob;
+        std::memcpy(p, &H, sizeof H);
+        p += sizeof H;
+        for (int l = 0; l < h->nlev; l++) {
+            const Level& L = h->lev[l];
+            std::memcpy(p, L.bin.data(), L.bin.size());
+            p += L.bin.size();
+            std::memcpy(p, L.bcov.data(), L.bcov.size());
+            p += L.bcov.size();
+            VCK(cudaMemcpy(p, L.flags, (size_t)L.plane * sizeof(uint16_t), cudaMemcpyDeviceToHost));
+            p += (size_t)L.plane * sizeof(uint16_t);
+            const double* st = L.buf[l == 0 ? par0 : 0];
+            VCK(cudaMemcpy(p, st, (size_t)16 * L.plane * sizeof(double), cudaMemcpyDeviceToHost));
+            p += (size_t)16 * L.plane * sizeof(double);
+        }
+    });
+}
+
+vlbm_status vlbm_checkpoint_load(vlbm_hier* h, const void* blob, size_t bytes) {
+    return run(h, [&] {
+        if (!blob || bytes < sizeof(CkptHeader)) throw Fail{VLBM_ERR_ARG, "blob too small"};
+        if (h->engine) throw Fail{VLBM_ERR_ARG, "hierarchy is resident in an engine"};
+        CkptHeader H;
+        std::memcpy(&H, blob, sizeof H);
+        if (std::memcmp(H.magic, "VLBMCKP1", 8) != 0 || H.version != 1) throw Fail{VLBM_ERR_ARG, "not a checkpoint"};
+        bool same = H.nlev == h->nlev && H.nx0 == h->cfg.nx0 && H.ny0 == h->cfg.ny0 && H.gamma == h->cfg.gamma &&
+                    H.c == h->cfg.c && H.beta == h->cfg.beta;
+        for (int i = 0; i < 4; i++) same = same && H.bc[i] == h->cfg.bc[i];
+        if (!same) throw Fail{VLBM_ERR_ARG, "checkpoint made under another configuration"};
+        if (bytes < ckpt_bytes(h)) throw Fail{VLBM_ERR_ARG, "blob too small"};
+        VCK(cudaStreamSynchronize(h->stream));
+        const char* p = (const char*)blob + sizeof H;
+        std::vector<uint8_t> bin[VLBM_MAX_LEVELS], bcov[VLBM_MAX_LEVELS];
+        const char* q = p;
+        for (int l = 0; l < h->nlev; l++) {
+            const Level& L = h->lev[l];
+            const size_t nb = (size_t)L.bx * L.by;
+            bin[l].assign((const uint8_t*)q, (const uint8_t*)q + nb);
+            bcov[l].assign((const uint8_t*)q + nb, (const uint8_t*)q + 2 * nb);
+            q += 2 * nb + (size_t)L.plane * sizeof(uint16_t) + (size_t)16 * L.plane * sizeof(double);
+        }
+        std::string why;
+        if (!nested(h, bin, bcov, why)) throw Fail{VLBM_ERR_ARG, "checkpoint layout: " + why};
+        install_layout(h, bin, bcov);  // tables and lists; flags are overwritten below
+        const int par0 = H.par0 & 1;
+        VCK(cudaMemcpy(h->words, &par0, sizeof(int), cudaMemcpyHostToDevice));
+        for (int l = 0; l < h->nlev; l++) {
+            Level& L = h->lev[l];
+            p += 2 * (size_t)L.bx * L.by;
+            VCK(cudaMemcpy(L.flags, p, (size_t)L.plane * sizeof(uint16_t), cudaMemcpyHostToDevice));
+            p += (size_t)L.plane * sizeof(uint16_t);
+            VCK(cudaMemcpy(L.buf[l == 0 ? par0 : 0], p, (size_t)16 * L.plane * sizeof(double), cudaMemcpyHostToDevice));
+            p += (size_t)16 * L.plane * sizeof(double);
+        }
+        h->steps = H.steps;
+        invalidate(h);
+        VCK(cudaDeviceSynchronize());
+    });
+}
+
+vlbm_status vlbm_set_step_totals(vlbm_hier* h, int32_t on) {
+    return run(h, [&] {
+        if (on && h->tune.schedule != 1) throw Fail{VLBM_ERR_ARG, "per-step totals need the persistent schedule"};
+        if (on && !h->hist) VCK(cudaMallocHost((void**)&h->hist, (size_t)h->hist_cap * 8 * sizeof(double)));
+        VCK(cudaStreamSynchronize(h->stream));
+        h->step_audit = on != 0;
+        h->hist_n = h->hist_read = 0;
+        if (h->own) h->own->valid = false;
+    });
+}
+
+vlbm_status vlbm_get_step_totals(vlbm_hier* h, double* out, int64_t cap, int64_t* n) {
+    return run(h, [&] {
+        if (!n || cap < 0 || (cap > 0 && !out)) throw Fail{VLBM_ERR_ARG, "bad arguments"};
+        VCK(cudaStreamSynchronize(h->stream));
+        check_status(h);
+        long long avail = h->hist_n - h->hist_read;
+        if (avail > h->hist_cap) avail = h->hist_cap;  // older rows were overwritten
+        const long long take = std::min<long long>(avail, cap);
+        const long long first = h->hist_n - take;  // the most recent `take` rows, oldest first
+        for (long long r = 0; r < take; r++) std::memcpy(out + r * 8, h->hist + ((first + r) % h->hist_cap) * 8,
+                                                         8 * sizeof(double));
+        *n = take;
+        h->hist_read = h->hist_n;
     });
 }
 
@@ -1294,6 +1506,7 @@ vlbm_status vlbm_set_tuning(vlbm_hier* h, const vlbm_tuning* t) {
             throw Fail{VLBM_ERR_ARG, "bad tuning"};
         if (sweep_variant_needs_om_minus1(t->variant) && h->om != -1.0)
             throw Fail{VLBM_ERR_ARG, "variant applies only when 1 - 2 beta == -1"};
+        if (h->step_audit && t->schedule != 1) throw Fail{VLBM_ERR_ARG, "per-step totals need the persistent schedule"};
         h->tune = *t;
         h->tl[0].steps = h->tl[1].steps = -1;
         if (h->own) h->own->valid = false;

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 
+#include "fix192.cuh"
 #include "fp64emu.cuh"
 #include "vlbm_dev.cuh"
 #include "vlbm_launch.h"
@@ -88,11 +89,14 @@ __device__ __forceinline__ double xmul(double a, double b) {
 }
 
 template <int P>
-__device__ __forceinline__ bool collide_p(double f[16], double om, double hb, double bcs, double gm1) {
+__device__ __forceinline__ bool collide_p(double f[16], double om, double hb, double bcs, double gm1,
+                                          double* Wout = nullptr) {
     constexpr bool M = (P & EM_MOM) != 0, A_ = (P & EM_A) != 0, F = (P & EM_FLUX) != 0, O = (P & EM_OMF) != 0;
     double W[4], Qx[4], Qy[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) W[k] = xadd<M>(xadd<M>(f[k], f[4 + k]), xadd<M>(f[8 + k], f[12 + k]));
+    if (Wout)
+        for (int k = 0; k < 4; k++) Wout[k] = W[k];
     const double inv = 1.0 / W[0];
     const double u = xmul<F>(W[1], inv);
     const double v = xmul<F>(W[2], inv);
@@ -257,7 +261,7 @@ __device__ __noinline__ void sweep_special(const LevelDev* __restrict__ levs, co
 // sub-step; step: coarse step index inside a multi-step launch.
 template <int P, bool COH>
 __device__ __forceinline__ void sweep_cell(const LevelDev* __restrict__ levs, const LevelDev& L, int x, int y, int kk,
-                                           int kkp, int step) {
+                                           int kkp, int step, double* Wout = nullptr) {
     const int nx = L.nx, ny = L.ny;
     if (x >= nx || y >= ny) return;
     const long long c = (long long)y * L.pitch + x;
@@ -270,7 +274,7 @@ __device__ __forceinline__ void sweep_cell(const LevelDev* __restrict__ levs, co
     double f[16];
 #pragma unroll
     for (int q = 0; q < 16; q++) f[q] = ld<COH>(src + q * plane + c);
-    if (!collide_p<P>(f, L.om, L.hb, L.bcs, L.gm1)) atomicOr(L.status, ST_NONPHYS);
+    if (!collide_p<P>(f, L.om, L.hb, L.bcs, L.gm1, Wout)) atomicOr(L.status, ST_NONPHYS);
     // push streaming (Eq. 5): f*_i lands on x + c_i
     long long cxp = c + 1, cxm = c - 1, cyp = c + L.pitch, cym = c - L.pitch;
     bool oxp = true, oxm = true, oyp = true, oym = true;
@@ -389,10 +393,37 @@ __device__ __forceinline__ void wait_done(const unsigned* p, int* status) {
 // dependencies, so every task a claimed task waits for was claimed earlier
 // by a running thread group: the schedule cannot deadlock, whatever the
 // number of resident CTAs.
+// Exact sums (192-bit fixed point) of w W_k and w |W_k| over the 64 cells of
+// a group, written by group lane 0 to slot[0..23].
+__device__ __forceinline__ void group_audit(int g, int lt, const double W[4], int scale_exp,
+                                            unsigned long long* __restrict__ slot) {
+    __shared__ Fix192 s_part[TILES_PER_CTA][2][8];
+    Fix192 v[8];
+    for (int k = 0; k < 4; k++) {
+        v[k] = fix_from_double(W[k], scale_exp);
+        v[4 + k] = fix_from_double(fabs(W[k]), scale_exp);
+    }
+    for (int off = 16; off > 0; off >>= 1)
+        for (int k = 0; k < 8; k++) {
+            const Fix192 o = fix_shfl_down(v[k], off);
+            fix_add(v[k], o);
+        }
+    if ((lt & 31) == 0)
+        for (int k = 0; k < 8; k++) s_part[g][lt >> 5][k] = v[k];
+    group_bar(g);
+    if (lt == 0)
+        for (int k = 0; k < 8; k++) {
+            Fix192 a = s_part[g][0][k];
+            fix_add(a, s_part[g][1][k]);
+            for (int i = 0; i < 3; i++) slot[3 * k + i] = a.w[i];
+        }
+}
+
 template <int P, int MINB>
 __global__ void __launch_bounds__(CTA_THREADS, MINB)
 task_kernel(const LevelDev* __restrict__ levs, const Task* __restrict__ tasks, int ntasks, const int* __restrict__ deps,
-            unsigned* __restrict__ done, int* counters, int* const* par, int npar, int flip) {
+            unsigned* __restrict__ done, int* counters, int* const* par, int npar, int flip,
+            unsigned long long* __restrict__ aslots) {
     __shared__ int s_task[TILES_PER_CTA];
     const int g = threadIdx.x >> 6;
     const int lt = threadIdx.x & 63;
@@ -408,10 +439,17 @@ task_kernel(const LevelDev* __restrict__ levs, const Task* __restrict__ tasks, i
         for (int j = lt; j < T.ndep; j += 64) wait_done(done + deps[T.dep0 + j], L.status);
         group_bar(g);
         __threadfence();
-        if (T.kind == 0)
-            sweep_cell<P, true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.kkp, T.step);
-        else
+        if (T.kind == 0) {
+            if (aslots && T.aslot >= 0) {
+                double W[4] = {0.0, 0.0, 0.0, 0.0};
+                sweep_cell<P, true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.kkp, T.step, W);
+                group_audit(g, lt, W, -2 * L.level, aslots + (size_t)T.aslot * 24);
+            } else {
+                sweep_cell<P, true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.kkp, T.step);
+            }
+        } else {
             close_cell<true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.step);
+        }
         __threadfence();
         group_bar(g);
         if (lt == 0) {
@@ -425,6 +463,37 @@ task_kernel(const LevelDev* __restrict__ levs, const Task* __restrict__ tasks, i
 __global__ void end_step_kernel(int* const* par, int n) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) *par[t] ^= 1;
+}
+
+// Per (hierarchy, coarse step) totals from the audit slots of its tasks:
+// segment b covers slots [seg[b], seg[b+1]); out[b][0..3] = sum w W_k,
+// out[b][4..7] = sum w |W_k|, each the correctly rounded exact sum.
+__global__ void __launch_bounds__(256) audit_segments_kernel(const unsigned long long* __restrict__ slots,
+                                                             const int* __restrict__ seg, double* __restrict__ out) {
+    __shared__ Fix192 part[256 / 32][8];
+    const int b = blockIdx.x;
+    Fix192 acc[8];
+    for (int k = 0; k < 8; k++) acc[k] = fix_zero();
+    for (int i = seg[b] + threadIdx.x; i < seg[b + 1]; i += blockDim.x)
+        for (int k = 0; k < 8; k++) {
+            Fix192 v;
+            for (int j = 0; j < 3; j++) v.w[j] = __ldcg(slots + (size_t)i * 24 + 3 * k + j);
+            fix_add(acc[k], v);
+        }
+    for (int off = 16; off > 0; off >>= 1)
+        for (int k = 0; k < 8; k++) {
+            const Fix192 o = fix_shfl_down(acc[k], off);
+            fix_add(acc[k], o);
+        }
+    if ((threadIdx.x & 31) == 0)
+        for (int k = 0; k < 8; k++) part[threadIdx.x >> 5][k] = acc[k];
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        const int k = threadIdx.x;
+        Fix192 a = part[0][k];
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) fix_add(a, part[w][k]);
+        out[(size_t)b * 8 + k] = fix_to_double(a);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -839,18 +908,27 @@ int task_kernel_ctas(int variant) {
 }
 
 cudaError_t launch_tasks(const LevelDev* levs, const Task* tasks, int ntasks, const int* deps, unsigned* done,
-                         int* counters, int* const* par, int npar, int flip, int variant, int ctas, cudaStream_t s) {
+                         int* counters, int* const* par, int npar, int flip, int variant, int ctas,
+                         unsigned long long* aslots, cudaStream_t s) {
     if (ntasks <= 0) return cudaSuccess;
     const int g = ctas > 0 ? ctas : task_kernel_ctas(variant);
     switch (variant) {
-#define X(id, P, B)                                                                                             \
-    case id:                                                                                                    \
-        task_kernel<P, B><<<g, CTA_THREADS, 0, s>>>(levs, tasks, ntasks, deps, done, counters, par, npar, flip); \
+#define X(id, P, B)                                                                                    \
+    case id:                                                                                           \
+        task_kernel<P, B><<<g, CTA_THREADS, 0, s>>>(levs, tasks, ntasks, deps, done, counters, par, npar, \
+                                                    flip, aslots);                                     \
         break;
         VLBM_SWEEP_VARIANTS(X)
 #undef X
         default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_audit_segments(const unsigned long long* slots, const int* seg, int nseg, double* out,
+                                  cudaStream_t s) {
+    if (nseg <= 0) return cudaSuccess;
+    audit_segments_kernel<<<nseg, 256, 0, s>>>(slots, seg, out);
     return cudaGetLastError();
 }
 

@@ -13,7 +13,10 @@ int sweep_variants();
 bool sweep_variant_needs_om_minus1(int v);
 int task_kernel_ctas(int variant);
 cudaError_t launch_tasks(const LevelDev* levs, const Task* tasks, int ntasks, const int* deps, unsigned* done,
-                         int* counters, int* const* par, int npar, int flip, int variant, int ctas, cudaStream_t s);
+                         int* counters, int* const* par, int npar, int flip, int variant, int ctas,
+                         unsigned long long* aslots, cudaStream_t s);
+cudaError_t launch_audit_segments(const unsigned long long* slots, const int* seg, int nseg, double* out,
+                                  cudaStream_t s);
 cudaError_t launch_close(const LevelDev* levs, const Item* items, int n, int kk, cudaStream_t s);
 cudaError_t launch_end_step(int* const* par, int n, cudaStream_t s);
 cudaError_t launch_feq_init(const LevelDev& L, const double* W, long long ld, double hc, cudaStream_t s);

@@ -18,6 +18,8 @@ Recipes (the paper's workloads, read as documented in the design doc):
                      three levels over the diagonal band
   * ``shockbubble``  Mach 1.22 shock into a light bubble, adaptive levels
   * ``sod_strip``    Sod tube across an interface (Sec. 4.1.2), quasi-1-D
+  * ``laxliu12``     Lax-Liu configuration 12 (Sec. 4.3.2)
+  * ``explosion``    explosion in a box with reflective walls (Sec. 4.2)
   * ``smooth_random`` seeded smooth periodic field for invariance tests
 """
 from dataclasses import dataclass, field
@@ -278,6 +280,44 @@ def riemann3(N=1024, nlev=3, t_end=0.3, steps=None, beta=0.7, widths=None, gamma
     if steps is None:
         steps = int(math.ceil(t_end * c / dx0))
     return Case("riemann3", N, N, nlev, bc, gamma, c, beta, Ws, refs, steps, dx0=dx0)
+
+
+LAXLIU12 = {  # (rho, u, v, p) per quadrant, Lax-Liu configuration 12 (Sec. 4.3.2, Eq. 32)
+    "NE": (0.5313, 0.0, 0.0, 0.4),
+    "NW": (1.0, 0.7276, 0.0, 1.0),
+    "SW": (0.8, 0.0, 0.0, 1.0),
+    "SE": (1.0, 0.0, 0.7276, 1.0),
+}
+
+
+def laxliu12(N=256, nlev=3, t_end=0.25, steps=None, beta=0.7, gamma=GAMMA):
+    """Lax-Liu configuration 12 on [0,1]^2 with levels over the diagonal band
+    that the NE-NW and NE-SE contacts roll up along (outflow on all sides)."""
+    cs = riemann3(N=N, nlev=nlev, t_end=t_end, steps=steps, beta=beta, widths=[0.06, 0.03, 0.015][: nlev - 1],
+                  gamma=gamma, states=LAXLIU12)
+    cs.name = "laxliu12"
+    return cs
+
+
+def explosion(N=256, patch=True, beta=0.9, t_end=0.5, steps=None, gamma=GAMMA, safety=2.0):
+    """Explosion in a box (Sec. 4.2, Eq. 31): rho = p = 5 inside the circle of
+    radius 0.3 around (0.4, 0.4), 1 outside, at rest; reflective walls on all
+    sides; optional centred ratio-2 patch over [0.25, 0.75]^2."""
+    dx0 = 1.0 / N
+    nlev = 2 if patch else 1
+    refs = box_refs(N, N, 2, [(0, N // 4, N // 4, N // 2, N // 2)]) if patch else []
+
+    def fn(X, Y):
+        inside = (X - 0.4) ** 2 + (Y - 0.4) ** 2 < 0.3 ** 2
+        rho = np.where(inside, 5.0, 1.0)
+        return conserved(rho, np.zeros_like(X), np.zeros_like(X), rho, gamma)
+
+    Ws = fill_levels(N, N, nlev, dx0, fn)
+    c = link_speed([Ws[0]], gamma, safety=safety)
+    if steps is None:
+        steps = int(math.ceil(t_end * c / dx0))
+    bc = (BC_REFLECT,) * 4
+    return Case("explosion", N, N, nlev, bc, gamma, c, beta, Ws, refs, steps, dx0=dx0)
 
 
 def normal_shock(mach, rho1=1.0, p1=1.0, gamma=GAMMA):

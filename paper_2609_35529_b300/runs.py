@@ -1,0 +1,177 @@
+"""End-to-end runs of the paper's 2-D workloads on the GPU, with the checks
+each one is about.  One JSON line per run on stdout.
+
+  python -m paper_2609_35529_b300.runs [pulse] [vortex] [riemann] [shockbubble]
+
+pulse        two-level Gaussian pulse, periodic 64^2, 200 coarse steps:
+             per-step conservation (fused audit) and the uniform-state run
+vortex       advected isentropic vortex, N = 128, 256, 512 with a central
+             ratio-2 patch, one period (t = 10): L2 error of rho and |u|
+             against the exact solution (the initial state), the observed
+             order, and the same for uniform grids of N and 2N
+riemann      Lax-Liu configuration 3, 1024^2, three levels, t = 0.3:
+             throughput, x<->y symmetry of the result (bitwise)
+shockbubble  adaptive shock-bubble, 2048 x 1024, up to three levels,
+             regrid every 4 coarse steps, 4000 steps: conservation audited
+             across every regrid, throughput including regrids
+"""
+import json
+import math
+import sys
+import time
+
+import numpy as np
+
+from . import inputs as I
+from . import vlbm as V
+
+
+def now():
+    return time.perf_counter()
+
+
+def emit(d):
+    print(json.dumps(d), flush=True)
+
+
+def run_pulse():
+    cs = I.pulse2l()
+    h = V.Hierarchy.from_case(cs)
+    h.set_step_totals(True)
+    t0 = now()
+    h.advance(cs.steps)
+    rows = h.step_totals()
+    el = now() - t0
+    drift = np.abs(rows[:, :4] - rows[0, :4]) / rows[0, 4:]
+    # uniform state through the interface
+    u = I.pulse2l(amp=0.0)
+    hu = V.Hierarchy.from_case(u)
+    hu.advance(u.steps)
+    dev = 0.0
+    for l in range(u.nlev):
+        W, act = hu.get_conserved(l)
+        for k in range(4):
+            ref = u.W[0][k, 0, 0]
+            dev = max(dev, float(np.max(np.abs(W[k][act] - ref))) / max(abs(ref), 1.0))
+    emit({"run": "pulse2l", "steps": cs.steps, "lups_per_step": h.info()["lups_per_step"],
+          "wall_s": el, "max_rel_drift_per_step": float(drift.max()),
+          "uniform_state_max_dev": dev})
+
+
+def l2_errors(h, case, exact_levels):
+    """L2 norms (over the domain, finest data at each point) of the error in
+    rho and |u| against the exact state on each level's cell centres."""
+    e_rho = e_u = 0.0
+    dx0 = case.dx0
+    for l in range(case.nlev):
+        W, act = h.get_conserved(l)
+        Ex = exact_levels[l]
+        a = dx0 / 2 ** l
+        e_rho += float(np.sum((W[0][act] - Ex[0][act]) ** 2)) * a * a
+        sp = np.hypot(W[1] / W[0], W[2] / W[0])
+        se = np.hypot(Ex[1] / Ex[0], Ex[2] / Ex[0])
+        e_u += float(np.sum((sp[act] - se[act]) ** 2)) * a * a
+    return math.sqrt(e_rho), math.sqrt(e_u)
+
+
+def run_vortex():
+    res = {}
+    for patch in (True, False):
+        for N in (128, 256, 512):
+            cs = I.vortex(N=N, patch=patch)
+            h = V.Hierarchy.from_case(cs)
+            h.set_step_totals(True)
+            t0 = now()
+            h.advance(cs.steps)
+            rows = h.step_totals()
+            el = now() - t0
+            er, eu = l2_errors(h, cs, cs.W)
+            drift = float((np.abs(rows[:, :4] - rows[0, :4]) / rows[0, 4:]).max())
+            res[(patch, N)] = (er, eu)
+            emit({"run": "vortex", "N": N, "patch": patch, "steps": cs.steps, "t_end": cs.steps * cs.dx0 / cs.c,
+                  "lups_per_step": h.info()["lups_per_step"], "wall_s": el,
+                  "mlups": h.info()["lups_per_step"] * cs.steps / el / 1e6,
+                  "l2_rho": er, "l2_speed": eu, "max_rel_drift_per_step": drift})
+            h.close()
+    for patch in (True, False):
+        e = [res[(patch, N)] for N in (128, 256, 512)]
+        emit({"run": "vortex-order", "patch": patch,
+              "order_rho": [math.log2(e[i][0] / e[i + 1][0]) for i in range(2)],
+              "order_speed": [math.log2(e[i][1] / e[i + 1][1]) for i in range(2)]})
+    # a uniform grid at twice the base resolution, for the refined runs' comparison
+    for N in (256, 512, 1024):
+        cs = I.vortex(N=N, patch=False)
+        h = V.Hierarchy.from_case(cs)
+        t0 = now()
+        h.advance(cs.steps)
+        h.sync()
+        el = now() - t0
+        er, eu = l2_errors(h, cs, cs.W)
+        emit({"run": "vortex-uniform-2N", "N": N, "steps": cs.steps, "wall_s": el,
+              "mlups": h.info()["lups_per_step"] * cs.steps / el / 1e6, "l2_rho": er, "l2_speed": eu})
+        h.close()
+
+
+def run_riemann():
+    cs = I.riemann3(N=1024, nlev=3)
+    h = V.Hierarchy.from_case(cs)
+    lups = h.info()["lups_per_step"]
+    h.advance(8)
+    h.sync()
+    t0 = now()
+    h.advance(cs.steps - 8)
+    h.sync()
+    el = now() - t0
+    sym = True
+    for l in range(cs.nlev):
+        f = h.get_populations(l).reshape(4, 4, *h.shapes[l])
+        a, b = h.layout(l)
+        act = (a == 1) & (b == 0)
+        ft = f.transpose(0, 1, 3, 2)[[2, 3, 0, 1]][:, [0, 2, 1, 3]]
+        sym = sym and bool(np.array_equal(f[:, :, act], ft[:, :, act]))
+    W, act = h.get_conserved(0)
+    info = h.info()
+    emit({"run": "riemann3", "N": 1024, "levels": 3, "steps": cs.steps, "t_end": cs.steps * cs.dx0 / cs.c,
+          "active_cells": info["active_cells"], "lups_per_step": lups, "wall_s": el,
+          "mlups": lups * (cs.steps - 8) / el / 1e6, "transpose_symmetric_bitwise": sym,
+          "rho_min": float(W[0][act].min()), "rho_max": float(W[0][act].max())})
+
+
+def run_shockbubble(steps=4000, every=4):
+    cs = I.shockbubble(steps=steps)
+    h = V.Hierarchy.from_case(cs)
+    for _ in range(cs.nlev - 1):
+        h.regrid()
+    worst = 0.0
+    lups = 0
+    active = []
+    t0 = now()
+    done = 0
+    while done < steps:
+        n = min(every, steps - done)
+        lups += n * h.info()["lups_per_step"]
+        h.advance(n)
+        done += n
+        if done < steps:
+            t_before, a_before = h.audit()
+            h.regrid()
+            t_after, _ = h.audit()
+            d = np.abs(t_after - t_before)
+            worst = max(worst, float(np.max(np.where(a_before > 0, d / np.where(a_before > 0, a_before, 1), d))))
+        if done % 500 == 0:
+            active.append([done] + h.info()["active_cells"])
+    h.sync()
+    el = now() - t0
+    emit({"run": "shockbubble", "coarse": [cs.nx0, cs.ny0], "levels": cs.nlev, "steps": steps,
+          "regrids": (steps - 1) // every, "wall_s": el, "mlups_incl_regrid": lups / el / 1e6,
+          "max_rel_change_across_regrid": worst, "active_cells_every_500": active})
+
+
+def main(argv=None):
+    which = (argv if argv is not None else sys.argv[1:]) or ["pulse", "vortex", "riemann", "shockbubble"]
+    for w in which:
+        {"pulse": run_pulse, "vortex": run_vortex, "riemann": run_riemann, "shockbubble": run_shockbubble}[w]()
+
+
+if __name__ == "__main__":
+    main()

@@ -213,26 +213,35 @@ def main(argv=None):
     ap.add_argument("--mem-gb", type=float, default=160.0)
     ap.add_argument("--oracle-sample", type=int, default=32)
     ap.add_argument("--nmax", type=int, default=1024)
+    ap.add_argument("--verbose", action="store_true")
     args = ap.parse_args(argv)
+    import sys
+    log = (lambda *a: print(*a, file=sys.stderr, flush=True)) if args.verbose else (lambda *a: None)
     import torch
     stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
     reqs = make_requests(args.requests, args.seed, nmax=args.nmax)
     total = sum(r.lups for r in reqs)
     budget = int(args.mem_gb * (1 << 30))
+    log(f"trace: {len(reqs)} requests, {total / 1e9:.1f} GLUP nominal, built in {time.perf_counter() - t0:.1f} s")
     # capacity: the whole trace offered at once (all arrivals at t = 0)
     for r in reqs:
         r.arrival = 0.0
     _, cap_mlups, cap_wall = serve_batched(reqs, budget, stream=stream)
+    log(f"capacity: {cap_mlups:.1f} MLUPS, {cap_wall:.1f} s")
     rate = args.load * len(reqs) / cap_wall
     schedule(reqs, rate, args.seed)
     sample = set(r.rid for r in sorted(reqs, key=lambda r: r.lups)[: args.oracle_sample])
     tts_b, ml_b, wall_b = serve_batched(reqs, budget, stream, sample)
+    log(f"batched: {ml_b:.1f} MLUPS, {wall_b:.1f} s")
     worst = 0.0
     for r in reqs:
         if r.rid in sample:
             worst = max(worst, agreement(r, run_oracle(r)))
             r.result = None
+    log(f"oracle sample: worst rel err {worst:.3g}")
     tts_1, ml_1, wall_1 = serve_one_at_a_time(reqs, stream=stream)
+    log(f"one at a time: {ml_1:.1f} MLUPS, {wall_1:.1f} s")
     out = {"requests": len(reqs), "total_lups": total, "capacity_mlups": round(cap_mlups, 1),
            "rate_per_s": round(rate, 3), "load": args.load,
            "batched": {"mlups": round(ml_b, 1), "p50_s": float(np.percentile(tts_b, 50)),

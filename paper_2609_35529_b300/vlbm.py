@@ -92,6 +92,11 @@ def lib():
         "vlbm_sync": [vp],
         "vlbm_get_info": [vp, C.POINTER(vlbm_info)],
         "vlbm_profile": [vp, i64, C.POINTER(vlbm_kernel_time), i32, C.POINTER(i32)],
+        "vlbm_set_step_totals": [vp, i32],
+        "vlbm_checkpoint_size": [vp, C.POINTER(C.c_size_t)],
+        "vlbm_checkpoint_save": [vp, vp, C.c_size_t],
+        "vlbm_checkpoint_load": [vp, vp, C.c_size_t],
+        "vlbm_get_step_totals": [vp, dp, i64, C.POINTER(i64)],
         "vlbm_engine_create": [C.c_size_t, vp, C.POINTER(vp)],
         "vlbm_engine_admit": [vp, vp, i64, i32, C.POINTER(i32)],
         "vlbm_engine_step": [vp, C.POINTER(i32), C.POINTER(i32)],
@@ -295,6 +300,31 @@ class Hierarchy:
         kinds = {0: "sweep", 1: "close", 2: "end_step"}
         return [{"kind": kinds[r.kind], "level": r.level, "launches": r.launches, "cells": r.cells, "ms": r.ms}
                 for r in recs[: n.value]]
+
+    def checkpoint(self):
+        """The hierarchy's state as a bytes blob (vlbm_checkpoint_save)."""
+        n = C.c_size_t()
+        _check(self._h, lib().vlbm_checkpoint_size(self._h, C.byref(n)))
+        buf = (C.c_char * n.value)()
+        _check(self._h, lib().vlbm_checkpoint_save(self._h, buf, n.value))
+        return bytes(buf)
+
+    def restore(self, blob):
+        """Resumes from a blob made by checkpoint() under the same configuration."""
+        buf = C.create_string_buffer(blob, len(blob))
+        _check(self._h, lib().vlbm_checkpoint_load(self._h, buf, len(blob)))
+
+    def set_step_totals(self, on=True):
+        _check(self._h, lib().vlbm_set_step_totals(self._h, 1 if on else 0))
+
+    def step_totals(self, cap=4096):
+        """Per-step totals recorded since the last call: array [n, 8]
+        (sum W_k, then sum |W_k|, of the state at the start of each step)."""
+        out = np.zeros((cap, 8))
+        n = C.c_int64()
+        _check(self._h, lib().vlbm_get_step_totals(self._h, out.ctypes.data_as(C.POINTER(C.c_double)), cap,
+                                                   C.byref(n)))
+        return out[: n.value]
 
     def set_tuning(self, variant=1, max_ctas=0, graph_steps=8, schedule=1):
         t = vlbm_tuning(variant, max_ctas, graph_steps, schedule)

@@ -169,17 +169,7 @@ def test_riemann3_transpose_symmetric(V):
 def test_reflective_walls_with_patch(V):
     """Explosion in a box (Sec. 4.2, Eq. 31) on a small grid: reflective walls
     on all sides, a centred ratio-2 patch."""
-    N = 64
-    refs = I.box_refs(N, N, 2, [(0, 16, 16, 32, 32)])
-
-    def fn(X, Y):
-        inside = (X - 0.4) ** 2 + (Y - 0.4) ** 2 < 0.3 ** 2
-        rho = np.where(inside, 5.0, 1.0)
-        return I.conserved(rho, np.zeros_like(X), np.zeros_like(X), rho)
-
-    Ws = I.fill_levels(N, N, 2, 1.0 / N, fn)
-    c = I.link_speed([Ws[0]], safety=2.0)
-    cs = I.Case("explosion", N, N, 2, (3, 3, 3, 3), 1.4, c, 0.9, Ws, refs, 50, dx0=1.0 / N)
+    cs = I.explosion(N=64, steps=50)
     g = V.Hierarchy.from_case(cs)
     o = oracle_of(cs)
     t0, a0 = g.audit()
@@ -327,3 +317,70 @@ def test_vortex_512_bench_configuration(V):
     g.advance(cs.steps)
     o.advance(cs.steps)
     compare(o, g, 2)
+
+
+@pytest.mark.parametrize("graph_steps", [8, 3])
+def test_step_totals_are_exact_every_step(V, graph_steps):
+    """The fused per-step audit returns, for every coarse step, the exactly
+    rounded totals of the state at the start of the step: they equal
+    math.fsum of the oracle's W (area-weighted) at the same times."""
+    n = 40
+    refs = I.box_refs(n, n, 3, [(0, 8, 8, 24, 16)])
+    refs[1][24:40, 24:56] = 1
+    cs = I.smooth_random(n, n, 3, refs, seed=51, amp=0.25, beta=0.85, steps=13)
+    g = V.Hierarchy.from_case(cs)
+    g.set_tuning(variant=1, graph_steps=graph_steps, schedule=1)
+    g.set_step_totals(True)
+    o = oracle_of(cs)
+    g.advance(cs.steps)
+    rows = g.step_totals()
+    assert rows.shape == (cs.steps, 8)
+    for st in range(cs.steps):
+        ot, oa = o.totals()
+        assert np.array_equal(rows[st, :4], ot), (st, rows[st, :4] - ot)
+        assert np.array_equal(rows[st, 4:], oa), (st, rows[st, 4:] - oa)
+        o.advance(1)
+    # the recorded totals stay constant to round-off (periodic domain)
+    d = np.abs(rows[:, :4] - rows[0, :4]) / rows[0, 4:]
+    assert d.max() < 1e-14
+    assert len(g.step_totals()) == 0
+
+
+def test_laxliu12_three_levels(V):
+    """Lax-Liu configuration 12 (Sec. 4.3.2) with three levels."""
+    cs = I.laxliu12(N=64, nlev=3, steps=50)
+    g = V.Hierarchy.from_case(cs)
+    o = oracle_of(cs)
+    g.advance(cs.steps)
+    o.advance(cs.steps)
+    compare(o, g, 3)
+
+
+def test_checkpoint_resume_is_bitwise(V):
+    """A run checkpointed mid-way and resumed in a fresh hierarchy continues
+    exactly as the uninterrupted run (including the faces' previous samples
+    and an adaptive regrid)."""
+    cs = I.shockbubble(nx0=128, ny0=64, nlev=3)
+    a = V.Hierarchy.from_case(cs)
+    for _ in range(2):
+        a.regrid()
+    a.advance(6)
+    a.regrid()
+    a.advance(3)
+    blob = a.checkpoint()
+    a.advance(5)
+    a.regrid()
+    a.advance(4)
+    b = V.Hierarchy(cs.nx0, cs.ny0, cs.nlev, cs.bc, cs.gamma, cs.c, cs.beta, dx0=cs.dx0, inflow=cs.inflow,
+                    tag_tol=cs.amr["tol"], tag_buffer=cs.amr["buffer"])
+    b.restore(blob)
+    b.advance(5)
+    b.regrid()
+    b.advance(4)
+    assert a.info()["steps"] == b.info()["steps"]
+    for l in range(cs.nlev):
+        assert np.array_equal(a.layout(l)[0], b.layout(l)[0])
+        assert np.array_equal(a.layout(l)[1], b.layout(l)[1])
+        ia, ra = a.layout(l)
+        act = (ia == 1) & (ra == 0)
+        assert np.array_equal(a.get_populations(l)[:, act], b.get_populations(l)[:, act])

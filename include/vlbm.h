@@ -168,7 +168,8 @@ vlbm_status vlbm_get_layout(vlbm_hier* h, int32_t level, uint8_t* in, uint8_t* r
 /* Conserved fields W = sum_i f_i of `level` into W[4][ny_l][ld] (host, may
  * be NULL); valid[ny_l*nx_l] (may be NULL) = 1 on active cells.  totals and
  * abs_totals (may be NULL) receive sum_l 4^-l sum_active W_k and the same
- * of |W_k| over the whole hierarchy (deterministic compensated sums).
+ * of |W_k| over the whole hierarchy: the exact sums (192-bit fixed point,
+ * resolution 2^-128) rounded once to nearest binary64.
  * Synchronises.  Errors: ERR_ARG, ERR_CUDA, ERR_NONPHYSICAL, ERR_STATE. */
 vlbm_status vlbm_get_conserved(vlbm_hier* h, int32_t level, double* W, int64_t ld,
                                uint8_t* valid, double totals[4], double abs_totals[4]);
@@ -180,6 +181,32 @@ vlbm_status vlbm_audit(vlbm_hier* h, double totals[4], double abs_totals[4]);
 vlbm_status vlbm_sync(vlbm_hier* h);
 
 vlbm_status vlbm_get_info(const vlbm_hier* h, vlbm_info* info);
+
+/* Host-side time the library has spent on a hierarchy since its creation,
+ * in milliseconds (wall clock, cumulative), by activity:
+ *   TAG       adaptive regrid: average-down, indicator and block flags on the
+ *             device, their copy to the host (after the stream is idle)
+ *   LAYOUT    new block maps from flags or boxes (grading, nesting)
+ *   REGRID    merge/split launches, per-cell flags, tile lists, uploads
+ *   BUILD     level tables of the launch (after a layout change)
+ *   TASKS     task lists with their dependencies (one coarse step or
+ *             graph_steps coarse steps), uploaded
+ *   CAPTURE   CUDA graph capture and instantiation
+ * and the counts NREGRIDS (vlbm_regrid calls) and NTASKLISTS (task lists
+ * built).  Device time of the sweeps is not included (see vlbm_profile).
+ * Errors: ERR_ARG. */
+enum {
+    VLBM_T_TAG = 0,
+    VLBM_T_LAYOUT = 1,
+    VLBM_T_REGRID = 2,
+    VLBM_T_BUILD = 3,
+    VLBM_T_TASKS = 4,
+    VLBM_T_CAPTURE = 5,
+    VLBM_T_NREGRIDS = 6,
+    VLBM_T_NTASKLISTS = 7,
+    VLBM_T_COUNT = 8
+};
+vlbm_status vlbm_host_times(const vlbm_hier* h, double out[VLBM_T_COUNT]);
 
 /* Per-kernel timing of the sub-cycle.  Runs `coarse_steps` coarse steps
  * launch by launch (not through the graph) with CUDA events around every
@@ -313,6 +340,9 @@ vlbm_status vlbm_engine_step(vlbm_engine* e, int32_t* finished_slots, int32_t* n
 
 /* Removes a resident (its hierarchy returns to the caller, unchanged). */
 vlbm_status vlbm_engine_release(vlbm_engine* e, int32_t slot);
+
+/* Coarse steps taken and cell updates done by a resident since admission. */
+vlbm_status vlbm_engine_slot_stats(const vlbm_engine* e, int32_t slot, int64_t* steps_done, int64_t* lups_done);
 
 /* Number of residents and their summed device bytes. */
 vlbm_status vlbm_engine_usage(const vlbm_engine* e, int32_t* residents, int64_t* bytes);

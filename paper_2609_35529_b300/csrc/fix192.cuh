@@ -40,31 +40,58 @@ __device__ __forceinline__ void fix_neg(Fix192& a) {
     fix_add(a, one);
 }
 
-// v * 2^scale_exp as fixed point (truncated below 2^-128; NaN/inf give 0,
-// the sweep reports them separately).
-__device__ __forceinline__ Fix192 fix_from_double(double v, int scale_exp) {
-    const unsigned long long B = (unsigned long long)__double_as_longlong(v);
+__device__ __forceinline__ void fix_sub(Fix192& a, const Fix192& b) {
+    const unsigned long long d0 = a.w[0] - b.w[0];
+    const unsigned long long b0 = a.w[0] < b.w[0] ? 1ull : 0ull;
+    const unsigned long long d1 = a.w[1] - b.w[1];
+    unsigned long long b1 = a.w[1] < b.w[1] ? 1ull : 0ull;
+    b1 += d1 < b0 ? 1ull : 0ull;
+    a.w[2] = a.w[2] - b.w[2] - b1;
+    a.w[1] = d1 - b0;
+    a.w[0] = d0;
+}
+
+// |v| * 2^scale_exp as fixed point, from the bits B of v (truncated below
+// 2^-128; NaN/inf give 0, the sweep reports them separately).  The words are
+// chosen by selects, not by indexing, so everything stays in registers.
+__device__ __forceinline__ Fix192 fix_from_mag(unsigned long long B, int scale_exp) {
     int E = (int)((B >> 52) & 0x7FFull);
     unsigned long long m = B & 0x000FFFFFFFFFFFFFull;
     Fix192 r = fix_zero();
     if (E == 2047) return r;
     if (E) m |= 0x0010000000000000ull;
     else E = 1;
-    if (m == 0) return r;
-    // value = m * 2^(E - 1075 + scale_exp); fixed = value * 2^128
+    // |v| = m * 2^(E - 1075 + scale_exp); fixed = |v| * 2^128
     const int sh = E - 1075 + scale_exp + 128;
     if (sh >= 0) {
         if (sh >= 192) return r;  // out of range: the caller's magnitudes never get here
         const int wi = sh >> 6, b = sh & 63;
-        r.w[wi] = m << b;
-        if (b > 11 && wi + 1 < 3) r.w[wi + 1] = m >> (64 - b);
-    } else {
-        const int rs = -sh;
-        if (rs >= 64) return r;
-        r.w[0] = m >> rs;
+        const unsigned long long lo = m << b;
+        const unsigned long long hi = b ? m >> (64 - b) : 0ull;
+        r.w[0] = wi == 0 ? lo : 0ull;
+        r.w[1] = wi == 1 ? lo : (wi == 0 ? hi : 0ull);
+        r.w[2] = wi == 2 ? lo : (wi == 1 ? hi : 0ull);
+    } else if (sh > -64) {
+        r.w[0] = m >> (-sh);
     }
+    return r;
+}
+
+// v * 2^scale_exp as fixed point.
+__device__ __forceinline__ Fix192 fix_from_double(double v, int scale_exp) {
+    const unsigned long long B = (unsigned long long)__double_as_longlong(v);
+    Fix192 r = fix_from_mag(B, scale_exp);
     if (B >> 63) fix_neg(r);
     return r;
+}
+
+// sum += v * 2^scale_exp and abs_sum += |v| * 2^scale_exp, exactly.
+__device__ __forceinline__ void fix_accumulate(Fix192& sum, Fix192& abs_sum, double v, int scale_exp) {
+    const unsigned long long B = (unsigned long long)__double_as_longlong(v);
+    const Fix192 a = fix_from_mag(B, scale_exp);
+    fix_add(abs_sum, a);
+    if (B >> 63) fix_sub(sum, a);
+    else fix_add(sum, a);
 }
 
 __device__ __forceinline__ Fix192 fix_shfl_down(const Fix192& a, int off) {

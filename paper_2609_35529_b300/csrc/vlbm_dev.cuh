@@ -26,6 +26,7 @@ namespace vlbm {
 constexpr int NQ = 16;
 constexpr int TILE = 8;          // tile edge = refinement block edge (cells)
 constexpr int TILES_PER_CTA = 4; // 4 x 64 threads
+constexpr int AUDIT_SLOT = 4 * 64; // doubles per audit slot: W_k of a tile's cells, [k][cell]
 constexpr int CTA_THREADS = TILES_PER_CTA * TILE * TILE;
 
 // per-cell flag bits
@@ -79,5 +80,21 @@ struct Task {
     int dep0, ndep;
     int aslot;  // first sub-step sweep of its coarse step: slot of its audit sums, else -1
 };
+
+// One hierarchy's task list as the persistent kernel sees it.  Task level
+// indices and dependency indices are local to the segment; lid_base maps
+// the level indices into the batch's level table.  done[] holds the launch
+// epoch in which each task completed (never cleared between launches).
+struct Segment {
+    const Task* tasks;
+    const int* deps;
+    unsigned* done;
+    double* aw;                  // audited moments, AUDIT_SLOT per slot (nullptr: no audit)
+    int* par0;                   // the hierarchy's level-0 parity word
+    int ntasks, lid_base;
+};
+
+// control words of a persistent launch
+enum : int { CTL_CLAIM = 0, CTL_FIN = 1, CTL_EPOCH = 2, CTL_TOTAL = 3, CTL_NSEG = 4, CTL_FLIP = 5, CTL_WORDS = 8 };
 
 }  // namespace vlbm

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -18,6 +19,13 @@
 using namespace vlbm;
 
 namespace {
+
+// audit slots (tiles) summed by one block of the per-step audit reduction
+constexpr int AUDIT_BLOCK_SLOTS = 32;
+
+double ms_since(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
 
 struct Fail {
     vlbm_status st;
@@ -148,7 +156,7 @@ struct vlbm_hier {
     // scratch
     DArr<double> stage;     // W / f staging
     DArr<uint8_t> stage8;   // valid masks, tags
-    DArr<double> partial;  // audit partial sums
+    DArr<unsigned long long> partial;  // audit partial sums (exact, 24 words per block)
     DArr<double> tot;      // audit result
     DArr<Item> listbuf;    // item lists for regrid kernels
     DArr<uint8_t> bflag;   // block flags
@@ -158,6 +166,7 @@ struct vlbm_hier {
     vlbm_tuning tune{1, 0, 8, 1};
     // per-step conservation totals recorded by vlbm_advance (pinned ring)
     bool step_audit = false;
+    double times[VLBM_T_COUNT] = {};  // host-side time, see vlbm_host_times
     double* hist = nullptr;
     long long hist_cap = 4096, hist_n = 0, hist_read = 0;
     // cached task lists of this hierarchy alone: [0] one step, [1] G steps
@@ -165,6 +174,22 @@ struct vlbm_hier {
         std::vector<Task> t;
         std::vector<int> d, key;
         int steps = -1;
+        bool audit = false;
+        // device copies (the hierarchy's memory): tasks, dependencies,
+        // completion epochs; for the per-step audit the audited moments
+        // (AUDIT_SLOT doubles per slot), each slot's weight exponent, the
+        // slot range of each reduction block, the blocks' exact partial
+        // sums, each step's block range and the per-step totals
+        DArr<Task> dt;
+        DArr<int> dd;
+        DArr<unsigned> done;
+        DArr<double> aw;
+        DArr<int> ascale;
+        DArr<int2> arng;
+        DArr<unsigned long long> apart;
+        DArr<int> abseg;
+        DArr<double> aout;
+        int nseg = 0, nblk = 0;
     } tl[2];
 
     LevelDev dev(int l, int parent, int child) const {
@@ -210,7 +235,6 @@ struct Batch {
     int G = 8;
     bool valid = false;
     int max_ctas = 0;  // sweep grid cap (0 = one CTA per 4 tiles)
-    bool multi = true; // also capture the G-step graph (the engine steps one at a time)
     int variant = 0;   // sweep kernel variant
 
     void release() {
@@ -224,16 +248,12 @@ struct Batch {
         }
         par.release(*mem);
         audit_items.release(*mem);
-        tasks.release(*mem);
-        deps.release(*mem);
-        done.release(*mem);
-        tasks1.release(*mem);
-        deps1.release(*mem);
-        done1.release(*mem);
         for (int w = 0; w < 2; w++) {
-            aslots[w].release(*mem);
-            aseg[w].release(*mem);
-            aout[w].release(*mem);
+            segs[w].release(*mem);
+            prefix[w].release(*mem);
+            ctl[w].release(*mem);
+            captured[w].clear();
+            seg_ok[w] = false;
         }
         valid = false;
     }
@@ -270,11 +290,14 @@ struct Batch {
         return ex;
     }
 
-    // rebuilds the tables of all members and re-captures the graphs
+    // rebuilds the tables of all members; graphs are re-captured on use
     void build(cudaStream_t s) {
-        if (exec1) cudaGraphExecDestroy(exec1);
-        if (execG) cudaGraphExecDestroy(execG);
-        exec1 = execG = nullptr;
+        if (schedule_mode != 1) {
+            if (exec1) cudaGraphExecDestroy(exec1);
+            if (execG) cudaGraphExecDestroy(execG);
+            exec1 = execG = nullptr;
+            for (auto& c : captured) c.clear();
+        }
         std::vector<LevelDev> tab;
         std::vector<Item> sw[VLBM_MAX_LEVELS], cl[VLBM_MAX_LEVELS], au;
         std::vector<int*> pw;
@@ -304,17 +327,9 @@ struct Batch {
         }
         par.upload(*mem, pw, s);
         audit_items.upload(*mem, au, s);
-        if (schedule_mode == 1) {
-            build_tasks(0, 1, tasks1, deps1, done1, ntasks1, s);
-            if (multi) build_tasks(1, G, tasks, deps, done, ntasksG, s);
-            VCK(cudaStreamSynchronize(s));
-            exec1 = capture_tasks(0, s);
-            if (multi) execG = capture_tasks(1, s);
-        } else {
-            VCK(cudaStreamSynchronize(s));
-            exec1 = capture(1, s);
-            if (multi) execG = capture(G, s);
-        }
+        VCK(cudaStreamSynchronize(s));  // the host tables above go out of scope
+        // the one-step and G-step graphs (and task lists) are built when first used
+        seg_ok[0] = seg_ok[1] = false;
         valid = true;
     }
 
@@ -372,19 +387,17 @@ struct Batch {
 
     // ---- persistent task schedule -----------------------------------------
     int schedule_mode = 1;  // 0: one launch per phase, 1: persistent task kernel
-    DArr<Task> tasks;
-    DArr<int> deps;
-    DArr<unsigned> done;  // [2 counters][ntasks marks]
-    int ntasks1 = 0, ntasksG = 0;
-    DArr<Task> tasks1;
-    DArr<int> deps1;
-    DArr<unsigned> done1;
-    // fused per-step conservation audit: [0] one-step list, [1] G-step list
-    bool audit = false;
-    DArr<unsigned long long> aslots[2];
-    DArr<int> aseg[2];
-    DArr<double> aout[2];
-    int nseg[2] = {0, 0};
+    bool audit = false;     // fused per-step audit (single-member batches)
+    // segment tables of the persistent launches: [0] one step, [1] G steps
+    DArr<Segment> segs[2];
+    DArr<int> prefix[2];
+    DArr<int> ctl[2];
+    int ntotal[2] = {0, 0};
+    bool seg_ok[2] = {false, false};
+    // everything a captured task graph holds by value (pointers, sizes,
+    // grid), so that it is re-captured exactly when one of them changes
+    std::vector<uintptr_t> captured[2];
+    std::vector<uintptr_t> launch_key(int which) const;
 
     // Dependency tracking at tile granularity.  Tasks of one phase write
     // disjoint cells (each destination slot has exactly one writer per
@@ -397,21 +410,45 @@ struct Batch {
         std::vector<int> writers, readers, prior;
     };
     struct Tracker {
-        // per level instance: 3 resources (buffer 0, buffer 1, flags) per tile
-        std::vector<std::vector<Res>> r;
+        // per level instance: 3 resources (buffer 0, buffer 1, flags) per
+        // tile, indexing a pool that holds only the resources touched since
+        // the last reset (the index maps persist between resets)
+        std::vector<std::vector<int>> idx;
         std::vector<int> bx, by;
+        std::vector<Res> pool;
+        std::vector<std::pair<int, size_t>> touched;
         std::vector<int> cur;
         void reset(const std::vector<LevelDev>& tab) {
-            r.assign(tab.size(), {});
-            bx.resize(tab.size());
-            by.resize(tab.size());
-            for (size_t i = 0; i < tab.size(); i++) {
-                bx[i] = (tab[i].nx + TILE - 1) / TILE;
-                by[i] = (tab[i].ny + TILE - 1) / TILE;
-                r[i].assign((size_t)3 * bx[i] * by[i], Res{});
+            bool same = idx.size() == tab.size();
+            for (size_t i = 0; same && i < tab.size(); i++)
+                same = bx[i] == (tab[i].nx + TILE - 1) / TILE && by[i] == (tab[i].ny + TILE - 1) / TILE;
+            if (same) {
+                for (const auto& t : touched) idx[t.first][t.second] = -1;
+            } else {
+                idx.assign(tab.size(), {});
+                bx.resize(tab.size());
+                by.resize(tab.size());
+                for (size_t i = 0; i < tab.size(); i++) {
+                    bx[i] = (tab[i].nx + TILE - 1) / TILE;
+                    by[i] = (tab[i].ny + TILE - 1) / TILE;
+                    idx[i].assign((size_t)3 * bx[i] * by[i], -1);
+                }
             }
+            touched.clear();
+            pool.clear();
+            cur.clear();
         }
-        Res& at(int lid, int kind, int tx, int ty) { return r[lid][((size_t)kind * by[lid] + ty) * bx[lid] + tx]; }
+        // valid until the next call (the pool may grow)
+        Res& at(int lid, int kind, int tx, int ty) {
+            const size_t k = ((size_t)kind * by[lid] + ty) * bx[lid] + tx;
+            int& i = idx[lid][k];
+            if (i < 0) {
+                i = (int)pool.size();
+                pool.emplace_back();
+                touched.emplace_back(lid, k);
+            }
+            return pool[i];
+        }
         void add(const std::vector<int>& v, int task) {
             for (int q : v)
                 if (q != task) cur.push_back(q);
@@ -434,6 +471,7 @@ struct Batch {
             if (x.writers.empty() || x.writers.back() != task) x.writers.push_back(task);
         }
     };
+    Tracker tracker;  // reused by every task-list build of this batch
     int phase_id = 0;
 
     // relative buffer ids: level 0 at step s reads (s & 1) and writes the
@@ -569,27 +607,23 @@ struct Batch {
         (void)before;
     }
 
-    // Task list of one hierarchy alone (local level indices), cached on the
-    // hierarchy until its layout or its steps-per-launch change.
-    void member_tasks(vlbm_hier* h, int which, int nsteps);
+    // Task list of one hierarchy alone (local level indices), cached and
+    // uploaded to the hierarchy's memory until its layout, its steps per
+    // launch or its audit setting change.
+    void member_tasks(vlbm_hier* h, int which, int nsteps, bool aud);
 
-    // Merges the members' cached lists phase by phase (a topological order
-    // for every member, interleaving members within a phase) and uploads.
-    void build_tasks(int which, int nsteps, DArr<Task>& dt, DArr<int>& dd, DArr<unsigned>& dn, int& count,
-                     cudaStream_t s);
+    // Segment table of a persistent launch over all members.
+    void build_segments(int which, int nsteps, cudaStream_t s);
     DevMem* mem_ptr() { return mem; }
 
     void task_launch(int which, cudaStream_t s) {
-        DArr<Task>& t = which ? tasks : tasks1;
-        DArr<int>& d = which ? deps : deps1;
-        DArr<unsigned>& dn = which ? done : done1;
-        const int n = which ? ntasksG : ntasks1;
-        const int steps = which ? G : 1;
-        VCK(cudaMemsetAsync(dn.p, 0, ((size_t)n + 2) * sizeof(unsigned), s));
-        unsigned long long* sl = audit ? aslots[which].p : nullptr;
-        VCK(launch_tasks(levs.p, t.p, n, d.p, dn.p + 2, (int*)dn.p, par.p, (int)par.n, steps & 1, variant, max_ctas,
-                         sl, s));
-        if (audit) VCK(launch_audit_segments(aslots[which].p, aseg[which].p, nseg[which], aout[which].p, s));
+        VCK(cudaMemsetAsync(ctl[which].p, 0, 2 * sizeof(int), s));  // claim and finish counters
+        VCK(launch_tasks(levs.p, segs[which].p, prefix[which].p, ctl[which].p, variant, max_ctas, s));
+        if (audit && members.size() == 1) {
+            auto& T = members[0]->tl[which];
+            VCK(launch_audit_slots(T.aw.p, T.arng.p, T.ascale.p, T.nblk, T.apart.p, s));
+            VCK(launch_audit_segments(T.apart.p, T.abseg.p, T.nseg, T.aout.p, s));
+        }
     }
 
     cudaGraphExec_t capture_tasks(int which, cudaStream_t s) {
@@ -610,22 +644,30 @@ struct Batch {
         return ex;
     }
 
+    // The graph of one step (which = 0) or of G steps (which = 1), with its
+    // task lists built and captured on first use.
+    cudaGraphExec_t exec_for(int which, cudaStream_t s);
+
     void advance(long long n, cudaStream_t s) {
-        while (n >= G) {
-            VCK(cudaGraphLaunch(execG, s));
-            n -= G;
+        if (n >= G) {
+            cudaGraphExec_t ex = exec_for(1, s);
+            for (; n >= G; n -= G) VCK(cudaGraphLaunch(ex, s));
         }
-        while (n-- > 0) VCK(cudaGraphLaunch(exec1, s));
+        if (n > 0) {
+            cudaGraphExec_t ex = exec_for(0, s);
+            for (; n > 0; n--) VCK(cudaGraphLaunch(ex, s));
+        }
     }
 };
 
-void Batch::member_tasks(vlbm_hier* h, int which, int nsteps) {
+void Batch::member_tasks(vlbm_hier* h, int which, int nsteps, bool aud) {
     vlbm_hier::TaskList& L = h->tl[which];
-    if (L.steps == nsteps) return;
+    if (L.steps == nsteps && L.audit == aud) return;
+    const auto t0 = std::chrono::steady_clock::now();
     std::vector<LevelDev> tab;
     for (int l = 0; l < h->nlev; l++) tab.push_back(h->dev(l, l ? l - 1 : -1, l + 1 < h->nlev ? l + 1 : -1));
     std::vector<std::pair<vlbm_hier*, int>> mm = {{h, 0}};
-    Tracker tr;
+    Tracker& tr = tracker;
     tr.reset(tab);
     phase_id = 0;
     L.t.clear();
@@ -634,72 +676,124 @@ void Batch::member_tasks(vlbm_hier* h, int which, int nsteps) {
     keys_out = &L.key;
     for (int st = 0; st < nsteps; st++) emit_schedule(tab, mm, 0, 0, 0, st, tr, L.t, L.d);
     keys_out = nullptr;
+    // audit slots: the audit tasks of step st are slots [seg[st], seg[st+1])
+    std::vector<int> seg(nsteps + 1, 0);
+    if (aud) {
+        for (const Task& T : L.t)
+            if (T.aslot == -2) seg[T.step + 1]++;
+        for (int i = 0; i < nsteps; i++) seg[i + 1] += seg[i];
+    }
+    std::vector<int> fill(nsteps, 0), scale(std::max(1, seg.back()), 0);
+    for (Task& T : L.t) {
+        T.aslot = (aud && T.aslot == -2) ? seg[T.step] + fill[T.step]++ : -1;
+        if (T.aslot >= 0) scale[T.aslot] = -2 * T.lid;  // weight 4^-level
+    }
+    // reduction blocks: at most AUDIT_BLOCK_SLOTS slots each, never across steps
+    std::vector<int2> rng;
+    std::vector<int> bseg(1, 0);
+    for (int st = 0; aud && st < nsteps; st++) {
+        for (int j = seg[st]; j < seg[st + 1]; j += AUDIT_BLOCK_SLOTS)
+            rng.push_back(make_int2(j, std::min(j + AUDIT_BLOCK_SLOTS, seg[st + 1])));
+        bseg.push_back((int)rng.size());
+    }
+    cudaStream_t s = h->stream;
+    L.dt.upload(h->mem, L.t, s);
+    std::vector<int> d = L.d;
+    if (d.empty()) d.push_back(0);
+    L.dd.upload(h->mem, d, s);
+    L.done.ensure(h->mem, std::max<size_t>(1, L.t.size()));
+    if (aud) {
+        L.nseg = nsteps;
+        L.nblk = (int)rng.size();
+        L.aw.ensure(h->mem, (size_t)std::max(1, seg.back()) * AUDIT_SLOT);
+        L.ascale.upload(h->mem, scale, s);
+        if (rng.empty()) rng.push_back(make_int2(0, 0));
+        L.arng.upload(h->mem, rng, s);
+        L.apart.ensure(h->mem, (size_t)std::max(1, L.nblk) * 24);
+        L.abseg.upload(h->mem, bseg, s);
+        L.aout.ensure(h->mem, (size_t)nsteps * 8);
+    } else {
+        L.nseg = L.nblk = 0;
+    }
+    VCK(cudaStreamSynchronize(s));
     L.steps = nsteps;
+    L.audit = aud;
+    h->times[VLBM_T_TASKS] += ms_since(t0);
+    h->times[VLBM_T_NTASKLISTS] += 1;
 }
 
-void Batch::build_tasks(int which, int nsteps, DArr<Task>& dt, DArr<int>& dd, DArr<unsigned>& dn, int& count,
-                        cudaStream_t s) {
-    size_t total = 0, totald = 0;
-    int maxkey = -1;
+std::vector<uintptr_t> Batch::launch_key(int which) const {
+    std::vector<uintptr_t> k = {(uintptr_t)levs.p, (uintptr_t)segs[which].p, (uintptr_t)prefix[which].p,
+                                (uintptr_t)ctl[which].p, (uintptr_t)variant, (uintptr_t)max_ctas,
+                                (uintptr_t)(audit && members.size() == 1)};
+    if (audit && members.size() == 1) {
+        const auto& T = members[0]->tl[which];
+        for (uintptr_t v : {(uintptr_t)T.aw.p, (uintptr_t)T.arng.p, (uintptr_t)T.ascale.p, (uintptr_t)T.nblk,
+                            (uintptr_t)T.apart.p, (uintptr_t)T.abseg.p, (uintptr_t)T.nseg, (uintptr_t)T.aout.p})
+            k.push_back(v);
+    }
+    return k;
+}
+
+cudaGraphExec_t Batch::exec_for(int which, cudaStream_t s) {
+    cudaGraphExec_t& ex = which ? execG : exec1;
+    if (schedule_mode != 1) {
+        if (!ex) ex = capture(which ? G : 1, s);
+        return ex;
+    }
+    if (!seg_ok[which]) {
+        build_segments(which, which ? G : 1, s);
+        VCK(cudaStreamSynchronize(s));
+        seg_ok[which] = true;
+    }
+    std::vector<uintptr_t> key = launch_key(which);
+    if (!ex || key != captured[which]) {
+        const auto t0 = std::chrono::steady_clock::now();
+        if (ex) cudaGraphExecDestroy(ex);
+        ex = nullptr;
+        captured[which].clear();
+        ex = capture_tasks(which, s);
+        captured[which] = key;
+        for (vlbm_hier* h : members) h->times[VLBM_T_CAPTURE] += ms_since(t0) / (double)members.size();
+    }
+    return ex;
+}
+
+void Batch::build_segments(int which, int nsteps, cudaStream_t s) {
+    const bool aud = audit && members.size() == 1;
+    std::vector<Segment> sg;
+    std::vector<int> pre(1, 0);
+    int base = 0;
     for (vlbm_hier* h : members) {
-        member_tasks(h, which, nsteps);
-        total += h->tl[which].t.size();
-        totald += h->tl[which].d.size();
-        if (!h->tl[which].key.empty()) maxkey = std::max(maxkey, h->tl[which].key.back());
+        member_tasks(h, which, nsteps, aud);
+        vlbm_hier::TaskList& L = h->tl[which];
+        // completion marks restart with this batch's epochs
+        VCK(cudaMemsetAsync(L.done.p, 0, std::max<size_t>(1, L.t.size()) * sizeof(unsigned), s));
+        Segment S{};
+        S.tasks = L.dt.p;
+        S.deps = L.dd.p;
+        S.done = L.done.p;
+        S.aw = aud ? L.aw.p : nullptr;
+        S.par0 = h->words;
+        S.ntasks = (int)L.t.size();
+        S.lid_base = base;
+        sg.push_back(S);
+        pre.push_back(pre.back() + S.ntasks);
+        base += h->nlev;
     }
-    std::vector<Task> out;
-    std::vector<int> dl;
-    out.reserve(total);
-    dl.reserve(totald);
-    const size_t M = members.size();
-    // audit slots: segment (member m, step st) holds the audit tasks of that
-    // member's coarse step st, contiguously
-    std::vector<int> segoff(M * nsteps + 1, 0), segfill(M * nsteps, 0);
-    if (audit) {
-        for (size_t m = 0; m < M; m++)
-            for (const Task& T : members[m]->tl[which].t)
-                if (T.aslot == -2) segoff[m * nsteps + T.step + 1]++;
-        for (size_t i = 0; i < M * (size_t)nsteps; i++) segoff[i + 1] += segoff[i];
+    if (sg.empty()) {
+        sg.push_back(Segment{});
+        pre.push_back(0);
     }
-    std::vector<size_t> cur(M, 0);
-    std::vector<std::vector<int>> pos(M);
-    std::vector<int> base(M, 0);
-    for (size_t m = 0, b = 0; m < M; m++) {
-        base[m] = (int)b;
-        b += members[m]->nlev;
-        pos[m].assign(members[m]->tl[which].t.size(), -1);
-    }
-    for (int k = 0; k <= maxkey; k++)
-        for (size_t m = 0; m < M; m++) {
-            const vlbm_hier::TaskList& L = members[m]->tl[which];
-            while (cur[m] < L.t.size() && L.key[cur[m]] == k) {
-                const size_t i = cur[m]++;
-                Task T = L.t[i];
-                T.lid += base[m];
-                if (T.aslot == -2 && audit) {
-                    const size_t sg = m * nsteps + T.step;
-                    T.aslot = segoff[sg] + segfill[sg]++;
-                } else {
-                    T.aslot = -1;
-                }
-                const int d0 = T.dep0;
-                T.dep0 = (int)dl.size();
-                for (int j = 0; j < T.ndep; j++) dl.push_back(pos[m][L.d[d0 + j]]);
-                pos[m][i] = (int)out.size();
-                out.push_back(T);
-            }
-        }
-    count = (int)out.size();
-    dt.upload(*mem, out, s);
-    if (dl.empty()) dl.push_back(0);
-    dd.upload(*mem, dl, s);
-    dn.ensure(*mem, (size_t)count + 2);
-    if (audit) {
-        nseg[which] = (int)(M * nsteps);
-        aslots[which].ensure(*mem, (size_t)std::max(1, segoff.back()) * 24);
-        aseg[which].upload(*mem, segoff, s);
-        aout[which].ensure(*mem, (size_t)nseg[which] * 8);
-    }
+    ntotal[which] = pre.back();
+    segs[which].upload(*mem, sg, s);
+    prefix[which].upload(*mem, pre, s);
+    std::vector<int> c(CTL_WORDS, 0);
+    c[CTL_EPOCH] = 1;
+    c[CTL_TOTAL] = pre.back();
+    c[CTL_NSEG] = (int)members.size();
+    c[CTL_FLIP] = nsteps & 1;
+    ctl[which].upload(*mem, c, s);
 }
 
 namespace {
@@ -886,9 +980,8 @@ void install_layout(vlbm_hier* h, std::vector<uint8_t>* bin, std::vector<uint8_t
     }
     h->aitems.upload(h->mem, items, s);
     h->atab.upload(h->mem, tab, s);
-    h->partial.ensure(h->mem, (size_t)16 * audit_blocks((int)items.size()));
+    h->partial.ensure(h->mem, (size_t)24 * audit_blocks((int)items.size()));
     h->tot.ensure(h->mem, 8);
-    VCK(cudaStreamSynchronize(s));
 }
 
 void check_status(vlbm_hier* h) {
@@ -907,11 +1000,12 @@ void regrid_to(vlbm_hier* h, std::vector<uint8_t>* newcov, bool averaged) {
     std::string why;
     if (!nested(h, newin, newcov, why)) throw Fail{VLBM_ERR_NESTING, why};
     // 1. average-down, finest level first (merge values and slope data)
+    // (one stream: each upload into listbuf is ordered after the kernel that
+    // read the previous list, so no host synchronisation is needed)
     if (!averaged)
         for (int l = h->nlev - 2; l >= 0; l--) {
             h->listbuf.upload(h->mem, h->lev[l].cov, s);
             VCK(launch_avgdown(lvdev(h, l), lvdev(h, l + 1), h->listbuf.p, (int)h->listbuf.n, s));
-            VCK(cudaStreamSynchronize(s));
         }
     // 2. merge: cells covered before and not now
     for (int l = h->nlev - 2; l >= 0; l--) {
@@ -923,7 +1017,6 @@ void regrid_to(vlbm_hier* h, std::vector<uint8_t>* newcov, bool averaged) {
         }
         h->listbuf.upload(h->mem, ex, s);
         VCK(launch_merge(lvdev(h, l), h->listbuf.p, (int)ex.size(), s));
-        VCK(cudaStreamSynchronize(s));
     }
     // 3. split: cells covered now and not before, coarsest level first
     for (int l = 0; l <= h->nlev - 2; l++) {
@@ -937,7 +1030,6 @@ void regrid_to(vlbm_hier* h, std::vector<uint8_t>* newcov, bool averaged) {
             }
         h->listbuf.upload(h->mem, en, s);
         VCK(launch_split(lvdev(h, l), lvdev(h, l + 1), h->listbuf.p, (int)en.size(), s));
-        VCK(cudaStreamSynchronize(s));
     }
     install_layout(h, newin, newcov);
 }
@@ -958,7 +1050,7 @@ struct vlbm_engine {
     Batch batch;
     struct Res {
         vlbm_hier* h = nullptr;
-        long long target = 0, done = 0;
+        long long target = 0, done = 0, lups = 0;
         int regrid_every = 0;
         bool live = false;
     };
@@ -1022,6 +1114,18 @@ void destroy_levels(vlbm_hier* h) {
     h->hout = nullptr;
     if (h->hist) cudaFreeHost(h->hist);
     h->hist = nullptr;
+    for (auto& L : h->tl) {
+        L.dt.release(h->mem);
+        L.dd.release(h->mem);
+        L.done.release(h->mem);
+        L.aw.release(h->mem);
+        L.ascale.release(h->mem);
+        L.arng.release(h->mem);
+        L.apart.release(h->mem);
+        L.abseg.release(h->mem);
+        L.aout.release(h->mem);
+        L.steps = -1;
+    }
 }
 
 void ensure_own_batch(vlbm_hier* h) {
@@ -1036,7 +1140,9 @@ void ensure_own_batch(vlbm_hier* h) {
         h->own->G = h->tune.graph_steps;
         h->own->schedule_mode = h->tune.schedule;
         h->own->audit = h->step_audit && h->tune.schedule == 1;
+        const auto t0 = std::chrono::steady_clock::now();
         h->own->build(h->stream);
+        h->times[VLBM_T_BUILD] += ms_since(t0);
     }
 }
 
@@ -1217,14 +1323,19 @@ vlbm_status vlbm_advance(vlbm_hier* h, int64_t coarse_steps) {
             b.advance(coarse_steps, h->stream);
         } else {
             long long n = coarse_steps;
-            while (n >= b.G) {
-                VCK(cudaGraphLaunch(b.execG, h->stream));
-                record_rows(h, b.aout[1].p, b.G);
-                n -= b.G;
+            if (n >= b.G) {
+                cudaGraphExec_t ex = b.exec_for(1, h->stream);
+                for (; n >= b.G; n -= b.G) {
+                    VCK(cudaGraphLaunch(ex, h->stream));
+                    record_rows(h, h->tl[1].aout.p, b.G);
+                }
             }
-            for (; n > 0; n--) {
-                VCK(cudaGraphLaunch(b.exec1, h->stream));
-                record_rows(h, b.aout[0].p, 1);
+            if (n > 0) {
+                cudaGraphExec_t ex = b.exec_for(0, h->stream);
+                for (; n > 0; n--) {
+                    VCK(cudaGraphLaunch(ex, h->stream));
+                    record_rows(h, h->tl[0].aout.p, 1);
+                }
             }
         }
         h->steps += coarse_steps;
@@ -1374,8 +1485,8 @@ vlbm_status vlbm_sync(vlbm_hier* h) {
     });
 }
 
-// Deterministic totals over the active cells of every level (two passes,
-// compensated sums); one 64-byte read-back.
+// Exact totals over the active cells of every level (two passes of
+// 192-bit fixed-point sums); one 64-byte read-back.
 static void audit_impl(vlbm_hier* h, double* totals, double* abs_totals) {
     if (!h->hout) VCK(cudaMallocHost((void**)&h->hout, 8 * sizeof(double)));
     VCK(launch_audit(h->atab.p, h->aitems.p, (int)h->aitems.n, h->partial.p, h->tot.p, h->stream));
@@ -1440,11 +1551,15 @@ vlbm_status vlbm_regrid_masks(vlbm_hier* h, const uint8_t* const* ref) {
 vlbm_status vlbm_regrid(vlbm_hier* h, const vlbm_box* boxes, int32_t nboxes) {
     return run(h, [&] {
         check_status(h);
+        auto t0 = std::chrono::steady_clock::now();
         std::vector<uint8_t> bcov[VLBM_MAX_LEVELS];
         if (boxes || nboxes > 0) {
             if (nboxes < 0 || !boxes) throw Fail{VLBM_ERR_ARG, "bad boxes"};
             boxes_to_maps(h, boxes, nboxes, bcov);
+            h->times[VLBM_T_LAYOUT] += ms_since(t0);
+            t0 = std::chrono::steady_clock::now();
             regrid_to(h, bcov, false);
+            h->times[VLBM_T_REGRID] += ms_since(t0);
         } else {
             if (!(h->cfg.tag_tol > 0.0) || h->cfg.tag_buffer < 0) throw Fail{VLBM_ERR_ARG, "no tagging parameters"};
             cudaStream_t s = h->stream;
@@ -1452,28 +1567,50 @@ vlbm_status vlbm_regrid(vlbm_hier* h, const vlbm_box* boxes, int32_t nboxes) {
             for (int l = h->nlev - 2; l >= 0; l--) {
                 h->listbuf.upload(h->mem, h->lev[l].cov, s);
                 VCK(launch_avgdown(lvdev(h, l), lvdev(h, l + 1), h->listbuf.p, (int)h->listbuf.n, s));
-                VCK(cudaStreamSynchronize(s));
             }
             std::vector<uint8_t> bflag[VLBM_MAX_LEVELS];
             const double tol2 = h->cfg.tag_tol * h->cfg.tag_tol;
             const int px = h->cfg.bc[0] == VLBM_BC_PERIODIC, py = h->cfg.bc[2] == VLBM_BC_PERIODIC;
+            size_t nb = 0;
+            for (int l = 0; l <= h->nlev - 2; l++) nb += (size_t)h->lev[l].bx * h->lev[l].by;
+            h->bflag.ensure(h->mem, nb);
+            size_t off = 0;
             for (int l = 0; l <= h->nlev - 2; l++) {
                 Level& L = h->lev[l];
                 h->stage8.ensure(h->mem, (size_t)L.nx * L.ny);
                 VCK(cudaMemsetAsync(h->stage8.p, 0, (size_t)L.nx * L.ny, s));
                 h->listbuf.upload(h->mem, L.in, s);
                 VCK(launch_tag(lvdev(h, l), h->listbuf.p, (int)L.in.size(), tol2, h->stage8.p, s));
-                h->bflag.ensure(h->mem, (size_t)L.bx * L.by);
-                VCK(launch_blockflag(h->stage8.p, L.nx, L.ny, px, py, h->cfg.tag_buffer, h->bflag.p, s));
-                bflag[l].resize((size_t)L.bx * L.by);
-                VCK(cudaMemcpyAsync(bflag[l].data(), h->bflag.p, bflag[l].size(), cudaMemcpyDeviceToHost, s));
-                VCK(cudaStreamSynchronize(s));
+                VCK(launch_blockflag(h->stage8.p, L.nx, L.ny, px, py, h->cfg.tag_buffer, h->bflag.p + off, s));
+                off += (size_t)L.bx * L.by;
             }
+            // the one synchronisation of an adaptive regrid: the block flags
+            std::vector<uint8_t> all(nb);
+            VCK(cudaMemcpyAsync(all.data(), h->bflag.p, nb, cudaMemcpyDeviceToHost, s));
+            VCK(cudaStreamSynchronize(s));
+            off = 0;
+            for (int l = 0; l <= h->nlev - 2; l++) {
+                const size_t n = (size_t)h->lev[l].bx * h->lev[l].by;
+                bflag[l].assign(all.begin() + off, all.begin() + off + n);
+                off += n;
+            }
+            h->times[VLBM_T_TAG] += ms_since(t0);
+            t0 = std::chrono::steady_clock::now();
             layout_rule(h, bflag, bcov);
+            h->times[VLBM_T_LAYOUT] += ms_since(t0);
+            t0 = std::chrono::steady_clock::now();
             regrid_to(h, bcov, true);
+            h->times[VLBM_T_REGRID] += ms_since(t0);
         }
+        h->times[VLBM_T_NREGRIDS] += 1;
         invalidate(h);
     });
+}
+
+vlbm_status vlbm_host_times(const vlbm_hier* h, double out[VLBM_T_COUNT]) {
+    if (!h || !out) return VLBM_ERR_ARG;
+    for (int i = 0; i < VLBM_T_COUNT; i++) out[i] = h->times[i];
+    return VLBM_OK;
 }
 
 vlbm_status vlbm_get_info(const vlbm_hier* h, vlbm_info* info) {
@@ -1560,8 +1697,14 @@ vlbm_status vlbm_engine_create(size_t mem_budget, void* stream, vlbm_engine** ou
     }
     e->mem.s = e->stream;
     e->batch.mem = &e->mem;
-    e->batch.multi = false;
     *out = e;
+    return VLBM_OK;
+}
+
+vlbm_status vlbm_engine_slot_stats(const vlbm_engine* e, int32_t slot, int64_t* steps_done, int64_t* lups_done) {
+    if (!e || slot < 0 || slot >= (int)e->res.size() || !e->res[slot].live) return VLBM_ERR_ARG;
+    if (steps_done) *steps_done = e->res[slot].done;
+    if (lups_done) *lups_done = e->res[slot].lups;
     return VLBM_OK;
 }
 
@@ -1600,6 +1743,7 @@ vlbm_status vlbm_engine_admit(vlbm_engine* e, vlbm_hier* h, int64_t coarse_steps
     e->res[s].target = coarse_steps;
     e->res[s].done = 0;
     e->res[s].regrid_every = regrid_every;
+    e->res[s].lups = 0;
     e->res[s].live = true;
     h->engine = e;
     e->dirty = true;
@@ -1633,6 +1777,7 @@ vlbm_status vlbm_engine_step(vlbm_engine* e, int32_t* finished, int32_t* nfinish
                 h->engine = keep;
                 e->dirty = true;
                 if (st != VLBM_OK) throw Fail{st, std::string("regrid: ") + h->err};
+                VCK(cudaStreamSynchronize(h->stream));  // its kernels ran on the hierarchy's stream
             }
         }
         if (e->dirty) {
@@ -1642,13 +1787,14 @@ vlbm_status vlbm_engine_step(vlbm_engine* e, int32_t* finished, int32_t* nfinish
             if (!e->batch.members.empty()) e->batch.build(e->stream);
             e->dirty = false;
         }
-        if (!e->batch.members.empty()) VCK(cudaGraphLaunch(e->batch.exec1, e->stream));
+        if (!e->batch.members.empty()) VCK(cudaGraphLaunch(e->batch.exec_for(0, e->stream), e->stream));
         int nf = 0;
         for (size_t i = 0; i < e->res.size(); i++) {
             auto& r = e->res[i];
             if (!r.live || r.done >= r.target) continue;
             r.done++;
             r.h->steps++;
+            for (int l = 0; l < r.h->nlev; l++) r.lups += r.h->lev[l].active_cells << l;
             if (r.done == r.target) {
                 if (finished) finished[nf] = (int)i;
                 nf++;

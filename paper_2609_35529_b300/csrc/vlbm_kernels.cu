@@ -377,10 +377,10 @@ __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
 // Bounded wait on a task's completion mark: gives up after ~2^21 polls
 // (about a second), records a timeout in the hierarchy's status word and
 // returns, so that a broken schedule can never hang the GPU.
-__device__ __forceinline__ void wait_done(const unsigned* p, int* status) {
+__device__ __forceinline__ void wait_done(const unsigned* p, unsigned epoch, int* status) {
     unsigned ns = 32;
     for (int it = 0; it < (1 << 21); it++) {
-        if (ld_acquire(p)) return;
+        if (ld_acquire(p) == epoch) return;
         // once any wait of this hierarchy has given up, stop waiting at all
         if ((it & 255) == 255 && (*(volatile int*)status & ST_TIMEOUT)) return;
         __nanosleep(ns);
@@ -389,61 +389,47 @@ __device__ __forceinline__ void wait_done(const unsigned* p, int* status) {
     atomicOr(status, ST_TIMEOUT);
 }
 
-// Tasks are claimed in list order, which is a topological order of their
-// dependencies, so every task a claimed task waits for was claimed earlier
-// by a running thread group: the schedule cannot deadlock, whatever the
-// number of resident CTAs.
-// Exact sums (192-bit fixed point) of w W_k and w |W_k| over the 64 cells of
-// a group, written by group lane 0 to slot[0..23].
-__device__ __forceinline__ void group_audit(int g, int lt, const double W[4], int scale_exp,
-                                            unsigned long long* __restrict__ slot) {
-    __shared__ Fix192 s_part[TILES_PER_CTA][2][8];
-    Fix192 v[8];
-    for (int k = 0; k < 4; k++) {
-        v[k] = fix_from_double(W[k], scale_exp);
-        v[4 + k] = fix_from_double(fabs(W[k]), scale_exp);
-    }
-    for (int off = 16; off > 0; off >>= 1)
-        for (int k = 0; k < 8; k++) {
-            const Fix192 o = fix_shfl_down(v[k], off);
-            fix_add(v[k], o);
-        }
-    if ((lt & 31) == 0)
-        for (int k = 0; k < 8; k++) s_part[g][lt >> 5][k] = v[k];
-    group_bar(g);
-    if (lt == 0)
-        for (int k = 0; k < 8; k++) {
-            Fix192 a = s_part[g][0][k];
-            fix_add(a, s_part[g][1][k]);
-            for (int i = 0; i < 3; i++) slot[3 * k + i] = a.w[i];
-        }
-}
-
+// Tasks are claimed in list order -- segment by segment, each segment in a
+// topological order of its dependencies -- so every task a claimed task
+// waits for was claimed earlier by a running thread group: the schedule
+// cannot deadlock, whatever the number of resident CTAs.
 template <int P, int MINB>
 __global__ void __launch_bounds__(CTA_THREADS, MINB)
-task_kernel(const LevelDev* __restrict__ levs, const Task* __restrict__ tasks, int ntasks, const int* __restrict__ deps,
-            unsigned* __restrict__ done, int* counters, int* const* par, int npar, int flip,
-            unsigned long long* __restrict__ aslots) {
+task_kernel(const LevelDev* __restrict__ levs, const Segment* __restrict__ segs, const int* __restrict__ prefix,
+            int* ctl) {
     __shared__ int s_task[TILES_PER_CTA];
     const int g = threadIdx.x >> 6;
     const int lt = threadIdx.x & 63;
     const int cx = lt & 7, cy = lt >> 3;
+    const unsigned epoch = (unsigned)ctl[CTL_EPOCH];
+    const int total = ctl[CTL_TOTAL], nseg = ctl[CTL_NSEG];
     for (;;) {
-        if (lt == 0) s_task[g] = atomicAdd(&counters[0], 1);
+        if (lt == 0) s_task[g] = atomicAdd(&ctl[CTL_CLAIM], 1);
         group_bar(g);
         const int t = s_task[g];
         group_bar(g);
-        if (t >= ntasks) break;
-        const Task T = tasks[t];
-        const LevelDev& L = levs[T.lid];
-        for (int j = lt; j < T.ndep; j += 64) wait_done(done + deps[T.dep0 + j], L.status);
+        if (t >= total) break;
+        int lo = 0, hi = nseg - 1;  // the segment holding ticket t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const Segment S = segs[lo];
+        const int i = t - prefix[lo];
+        const Task T = S.tasks[i];
+        const LevelDev& L = levs[T.lid + S.lid_base];
+        for (int j = lt; j < T.ndep; j += 64) wait_done(S.done + S.deps[T.dep0 + j], epoch, L.status);
         group_bar(g);
         __threadfence();
         if (T.kind == 0) {
-            if (aslots && T.aslot >= 0) {
+            if (S.aw && T.aslot >= 0) {
+                // audited sweep: keep the moments of the cell (0 off the
+                // active set) for the exact reduction after the launch
                 double W[4] = {0.0, 0.0, 0.0, 0.0};
                 sweep_cell<P, true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.kkp, T.step, W);
-                group_audit(g, lt, W, -2 * L.level, aslots + (size_t)T.aslot * 24);
+                double* o = S.aw + (size_t)T.aslot * AUDIT_SLOT + lt;
+                for (int k = 0; k < 4; k++) o[k * 64] = W[k];
             } else {
                 sweep_cell<P, true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.kkp, T.step);
             }
@@ -453,9 +439,14 @@ task_kernel(const LevelDev* __restrict__ levs, const Task* __restrict__ tasks, i
         __threadfence();
         group_bar(g);
         if (lt == 0) {
-            st_release(done + t, 1u);
-            if (atomicAdd(&counters[1], 1) == ntasks - 1 && flip)
-                for (int m = 0; m < npar; m++) *par[m] ^= 1;
+            st_release(S.done + i, epoch);
+            if (atomicAdd(&ctl[CTL_FIN], 1) == total - 1) {
+                // every task of the launch is complete: advance the parity of
+                // each hierarchy by the launch's step count, open the next epoch
+                if (ctl[CTL_FLIP])
+                    for (int m = 0; m < nseg; m++) *segs[m].par0 ^= 1;
+                ctl[CTL_EPOCH] = (int)(epoch + 1);
+            }
         }
     }
 }
@@ -465,16 +456,51 @@ __global__ void end_step_kernel(int* const* par, int n) {
     if (t < n) *par[t] ^= 1;
 }
 
-// Per (hierarchy, coarse step) totals from the audit slots of its tasks:
-// segment b covers slots [seg[b], seg[b+1]); out[b][0..3] = sum w W_k,
+// Exact sums of the audited moments: block b covers the audit slots
+// [rng[b].x, rng[b].y).  A slot holds W_k of the 64 cells of one tile,
+// layout [k][cell], at weight 2^scale[slot]; thread t always reads field
+// k = t / 64, so each thread keeps just two 192-bit sums.  The block's 8
+// exact sums go to part[b][0..23] (W_0..W_3, then |W_0|..|W_3|).
+__global__ void __launch_bounds__(256) audit_slots_kernel(const double* __restrict__ aw, const int2* __restrict__ rng,
+                                                          const int* __restrict__ scale,
+                                                          unsigned long long* __restrict__ part) {
+    __shared__ Fix192 s_part[8][2];
+    const int t = threadIdx.x;
+    const int2 r = rng[blockIdx.x];
+    Fix192 sum = fix_zero(), abs_sum = fix_zero();
+    for (int j = r.x; j < r.y; j++)
+        fix_accumulate(sum, abs_sum, __ldcs(aw + (size_t)j * AUDIT_SLOT + t), __ldg(scale + j));
+    for (int off = 16; off > 0; off >>= 1) {
+        const Fix192 o1 = fix_shfl_down(sum, off);
+        const Fix192 o2 = fix_shfl_down(abs_sum, off);
+        fix_add(sum, o1);
+        fix_add(abs_sum, o2);
+    }
+    if ((t & 31) == 0) {
+        s_part[t >> 5][0] = sum;
+        s_part[t >> 5][1] = abs_sum;
+    }
+    __syncthreads();
+    if (t < 8) {
+        const int k = t & 3, a = t >> 2;  // quantity t: field k, a = 1 for |W|
+        Fix192 v = s_part[2 * k][a];
+        fix_add(v, s_part[2 * k + 1][a]);
+        for (int i = 0; i < 3; i++) part[(size_t)blockIdx.x * 24 + 3 * t + i] = v.w[i];
+    }
+}
+
+// Totals from exact partial sums: segment b covers partials [seg[b],
+// seg[b+1]) (seg == nullptr: one segment [0, n)); out[b][0..3] = sum w W_k,
 // out[b][4..7] = sum w |W_k|, each the correctly rounded exact sum.
 __global__ void __launch_bounds__(256) audit_segments_kernel(const unsigned long long* __restrict__ slots,
-                                                             const int* __restrict__ seg, double* __restrict__ out) {
+                                                             const int* __restrict__ seg, int n,
+                                                             double* __restrict__ out) {
     __shared__ Fix192 part[256 / 32][8];
     const int b = blockIdx.x;
+    const int i0 = seg ? seg[b] : 0, i1 = seg ? seg[b + 1] : n;
     Fix192 acc[8];
     for (int k = 0; k < 8; k++) acc[k] = fix_zero();
-    for (int i = seg[b] + threadIdx.x; i < seg[b + 1]; i += blockDim.x)
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x)
         for (int k = 0; k < 8; k++) {
             Fix192 v;
             for (int j = 0; j < 3; j++) v.w[j] = __ldcg(slots + (size_t)i * 24 + 3 * k + j);
@@ -559,35 +585,16 @@ __global__ void gather_W_kernel(LevelDev L, double* __restrict__ W, long long ld
 }
 
 // ---------------------------------------------------------------------------
-// conservation audit: deterministic compensated sums
+// conservation audit: exact sums
 // ---------------------------------------------------------------------------
 
-struct CSum {
-    double s, c;
-};
-
-__device__ __forceinline__ void csum_add(CSum& a, double x) {
-    const double t = a.s + x;
-    if (fabs(a.s) >= fabs(x)) a.c += (a.s - t) + x;
-    else a.c += (x - t) + a.s;
-    a.s = t;
-}
-
-__device__ __forceinline__ CSum csum_join(CSum a, CSum b) {
-    CSum r;
-    r.s = a.s;
-    r.c = a.c + b.c;
-    csum_add(r, b.s);
-    return r;
-}
-
-// Pass 1: per-CTA partial sums over active cells of the listed tiles:
-// out[blk][0..3] = sum w W_k, out[blk][4..7] = sum w |W_k| (w = 4^-level),
-// as (sum, compensation) pairs.
+// Exact per-CTA sums over the active cells of the listed tiles:
+// part[blk][0..23] = sum w W_k (k = 0..3), then sum w |W_k|, w = 4^-level,
+// as 192-bit fixed point (three words each).
 __global__ void __launch_bounds__(256) audit_kernel(const LevelDev* __restrict__ levs, const Item* __restrict__ items,
-                                                    int nitems, double* __restrict__ partial) {
-    CSum acc[8];
-    for (int m = 0; m < 8; m++) acc[m] = {0.0, 0.0};
+                                                    int nitems, unsigned long long* __restrict__ part) {
+    Fix192 acc[8];
+    for (int m = 0; m < 8; m++) acc[m] = fix_zero();
     const int sub = threadIdx.x >> 6;
     const int cx = threadIdx.x & 7;
     const int cy = (threadIdx.x >> 3) & 7;
@@ -600,44 +607,27 @@ __global__ void __launch_bounds__(256) audit_kernel(const LevelDev* __restrict__
         if ((L.flags[c] & (F_IN | F_COV)) != F_IN) continue;
         const double* st = L.buf[state_buf(L)];
         for (int k = 0; k < 4; k++) {
-            const double v = ((st[(0 + k) * L.plane + c] + st[(4 + k) * L.plane + c]) +
-                              (st[(8 + k) * L.plane + c] + st[(12 + k) * L.plane + c])) * L.wscale;
-            csum_add(acc[k], v);
-            csum_add(acc[4 + k], fabs(v));
+            const double v = (st[(0 + k) * L.plane + c] + st[(4 + k) * L.plane + c]) +
+                             (st[(8 + k) * L.plane + c] + st[(12 + k) * L.plane + c]);
+            fix_accumulate(acc[k], acc[4 + k], v, -2 * L.level);
         }
     }
-    __shared__ CSum sh[8][8];
+    __shared__ Fix192 sh[8][8];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int m = 0; m < 8; m++) {
-        CSum a = acc[m];
         for (int o = 16; o > 0; o >>= 1) {
-            CSum b;
-            b.s = __shfl_down_sync(0xffffffffu, a.s, o);
-            b.c = __shfl_down_sync(0xffffffffu, a.c, o);
-            if (lane < o) a = csum_join(a, b);
+            const Fix192 b = fix_shfl_down(acc[m], o);
+            fix_add(acc[m], b);
         }
-        if (lane == 0) sh[wid][m] = a;
+        if (lane == 0) sh[wid][m] = acc[m];
     }
     __syncthreads();
     if (threadIdx.x < 8) {
         const int m = threadIdx.x;
-        CSum a = sh[0][m];
-        for (int w2 = 1; w2 < (int)(blockDim.x >> 5); w2++) a = csum_join(a, sh[w2][m]);
-        partial[blockIdx.x * 16 + 2 * m] = a.s;
-        partial[blockIdx.x * 16 + 2 * m + 1] = a.c;
+        Fix192 a = sh[0][m];
+        for (int w2 = 1; w2 < (int)(blockDim.x >> 5); w2++) fix_add(a, sh[w2][m]);
+        for (int i = 0; i < 3; i++) part[(size_t)blockIdx.x * 24 + 3 * m + i] = a.w[i];
     }
-}
-
-// Pass 2: one thread per quantity sums the partials in block order.
-__global__ void audit_final_kernel(const double* __restrict__ partial, int nblk, double* __restrict__ out) {
-    const int m = threadIdx.x;
-    if (m >= 8) return;
-    CSum a = {0.0, 0.0};
-    for (int b = 0; b < nblk; b++) {
-        CSum p = {partial[b * 16 + 2 * m], partial[b * 16 + 2 * m + 1]};
-        a = csum_join(a, p);
-    }
-    out[m] = a.s + a.c;
 }
 
 // ---------------------------------------------------------------------------
@@ -907,17 +897,11 @@ int task_kernel_ctas(int variant) {
     return cache[variant];
 }
 
-cudaError_t launch_tasks(const LevelDev* levs, const Task* tasks, int ntasks, const int* deps, unsigned* done,
-                         int* counters, int* const* par, int npar, int flip, int variant, int ctas,
-                         unsigned long long* aslots, cudaStream_t s) {
-    if (ntasks <= 0) return cudaSuccess;
+cudaError_t launch_tasks(const LevelDev* levs, const Segment* segs, const int* prefix, int* ctl, int variant, int ctas,
+                         cudaStream_t s) {
     const int g = ctas > 0 ? ctas : task_kernel_ctas(variant);
     switch (variant) {
-#define X(id, P, B)                                                                                    \
-    case id:                                                                                           \
-        task_kernel<P, B><<<g, CTA_THREADS, 0, s>>>(levs, tasks, ntasks, deps, done, counters, par, npar, \
-                                                    flip, aslots);                                     \
-        break;
+#define X(id, P, B) case id: task_kernel<P, B><<<g, CTA_THREADS, 0, s>>>(levs, segs, prefix, ctl); break;
         VLBM_SWEEP_VARIANTS(X)
 #undef X
         default: return cudaErrorInvalidValue;
@@ -928,7 +912,14 @@ cudaError_t launch_tasks(const LevelDev* levs, const Task* tasks, int ntasks, co
 cudaError_t launch_audit_segments(const unsigned long long* slots, const int* seg, int nseg, double* out,
                                   cudaStream_t s) {
     if (nseg <= 0) return cudaSuccess;
-    audit_segments_kernel<<<nseg, 256, 0, s>>>(slots, seg, out);
+    audit_segments_kernel<<<nseg, 256, 0, s>>>(slots, seg, 0, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_audit_slots(const double* aw, const int2* rng, const int* scale, int nblk,
+                               unsigned long long* part, cudaStream_t s) {
+    if (nblk <= 0) return cudaSuccess;
+    audit_slots_kernel<<<nblk, AUDIT_SLOT, 0, s>>>(aw, rng, scale, part);
     return cudaGetLastError();
 }
 
@@ -961,11 +952,11 @@ cudaError_t launch_gather_W(const LevelDev& L, double* W, long long ld, uint8_t*
 
 int audit_blocks(int nitems) { return tile_grid(nitems, 148 * 4); }
 
-cudaError_t launch_audit(const LevelDev* levs, const Item* items, int n, double* partial, double* out, cudaStream_t s) {
+cudaError_t launch_audit(const LevelDev* levs, const Item* items, int n, unsigned long long* part, double* out,
+                         cudaStream_t s) {
     const int g = audit_blocks(n);
-    if (n > 0) audit_kernel<<<g, 256, 0, s>>>(levs, items, n, partial);
-    else cudaMemsetAsync(partial, 0, sizeof(double) * 16 * g, s);
-    audit_final_kernel<<<1, 32, 0, s>>>(partial, n > 0 ? g : 1, out);
+    if (n > 0) audit_kernel<<<g, 256, 0, s>>>(levs, items, n, part);
+    audit_segments_kernel<<<1, 256, 0, s>>>(part, nullptr, n > 0 ? g : 0, out);
     return cudaGetLastError();
 }
 

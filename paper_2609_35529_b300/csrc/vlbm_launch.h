@@ -12,18 +12,20 @@ cudaError_t launch_sweep(const LevelDev* levs, const Item* items, int n, int kk,
 int sweep_variants();
 bool sweep_variant_needs_om_minus1(int v);
 int task_kernel_ctas(int variant);
-cudaError_t launch_tasks(const LevelDev* levs, const Task* tasks, int ntasks, const int* deps, unsigned* done,
-                         int* counters, int* const* par, int npar, int flip, int variant, int ctas,
-                         unsigned long long* aslots, cudaStream_t s);
+cudaError_t launch_tasks(const LevelDev* levs, const Segment* segs, const int* prefix, int* ctl, int variant, int ctas,
+                         cudaStream_t s);
 cudaError_t launch_audit_segments(const unsigned long long* slots, const int* seg, int nseg, double* out,
                                   cudaStream_t s);
+cudaError_t launch_audit_slots(const double* aw, const int2* rng, const int* scale, int nblk,
+                               unsigned long long* part, cudaStream_t s);
 cudaError_t launch_close(const LevelDev* levs, const Item* items, int n, int kk, cudaStream_t s);
 cudaError_t launch_end_step(int* const* par, int n, cudaStream_t s);
 cudaError_t launch_feq_init(const LevelDev& L, const double* W, long long ld, double hc, cudaStream_t s);
 cudaError_t launch_copy_pop(const LevelDev& L, double* ext, long long ld, int to_ext, cudaStream_t s);
 cudaError_t launch_gather_W(const LevelDev& L, double* W, long long ld, uint8_t* valid, cudaStream_t s);
 int audit_blocks(int nitems);
-cudaError_t launch_audit(const LevelDev* levs, const Item* items, int n, double* partial, double* out, cudaStream_t s);
+cudaError_t launch_audit(const LevelDev* levs, const Item* items, int n, unsigned long long* part, double* out,
+                         cudaStream_t s);
 cudaError_t launch_avgdown(const LevelDev& C, const LevelDev& F, const Item* items, int n, cudaStream_t s);
 cudaError_t launch_tag(const LevelDev& L, const Item* items, int n, double tol2, uint8_t* tags, cudaStream_t s);
 cudaError_t launch_blockflag(const uint8_t* tags, int nx, int ny, int px, int py, int buffer, uint8_t* out,

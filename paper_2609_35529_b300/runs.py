@@ -1,7 +1,7 @@
 """End-to-end runs of the paper's 2-D workloads on the GPU, with the checks
 each one is about.  One JSON line per run on stdout.
 
-  python -m paper_2609_35529_b300.runs [pulse] [vortex] [riemann] [shockbubble]
+  python -m paper_2609_35529_b300.runs [pulse] [vortex] [riemann] [shockbubble[=steps]]
 
 pulse        two-level Gaussian pulse, periodic 64^2, 200 coarse steps:
              per-step conservation (fused audit) and the uniform-state run
@@ -138,6 +138,8 @@ def run_riemann():
 
 
 def run_shockbubble(steps=4000, every=4):
+    """The adaptive run; the totals are audited (exactly) before and after
+    every regrid."""
     cs = I.shockbubble(steps=steps)
     h = V.Hierarchy.from_case(cs)
     for _ in range(cs.nlev - 1):
@@ -164,13 +166,16 @@ def run_shockbubble(steps=4000, every=4):
     el = now() - t0
     emit({"run": "shockbubble", "coarse": [cs.nx0, cs.ny0], "levels": cs.nlev, "steps": steps,
           "regrids": (steps - 1) // every, "wall_s": el, "mlups_incl_regrid": lups / el / 1e6,
-          "max_rel_change_across_regrid": worst, "active_cells_every_500": active})
+          "max_rel_change_across_regrid": worst, "active_cells_every_500": active,
+          "host_ms": h.host_times()})
 
 
 def main(argv=None):
     which = (argv if argv is not None else sys.argv[1:]) or ["pulse", "vortex", "riemann", "shockbubble"]
     for w in which:
-        {"pulse": run_pulse, "vortex": run_vortex, "riemann": run_riemann, "shockbubble": run_shockbubble}[w]()
+        name, _, arg = w.partition("=")
+        fn = {"pulse": run_pulse, "vortex": run_vortex, "riemann": run_riemann, "shockbubble": run_shockbubble}[name]
+        fn(int(arg)) if arg else fn()
 
 
 if __name__ == "__main__":

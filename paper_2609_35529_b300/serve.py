@@ -284,10 +284,9 @@ def serve_batched(reqs, budget, stream=None, keep_ids=()):
             if nxt < len(pending):
                 time.sleep(max(0.0, min(0.002, pending[nxt].arrival - (time.perf_counter() - t0))))
             continue
-        for slot, (r, h) in live.items():
-            r.lups_done += h.info()["lups_per_step"]
         for slot in eng.step():
             r, h = live.pop(slot)
+            r.lups_done = eng.slot_stats(slot)[1]
             W, act = h.get_conserved(0)
             r.done_at = time.perf_counter() - t0
             if r.rid in keep_ids:

@@ -91,6 +91,7 @@ def lib():
         "vlbm_audit": [vp, dp, dp],
         "vlbm_sync": [vp],
         "vlbm_get_info": [vp, C.POINTER(vlbm_info)],
+        "vlbm_host_times": [vp, dp],
         "vlbm_profile": [vp, i64, C.POINTER(vlbm_kernel_time), i32, C.POINTER(i32)],
         "vlbm_set_step_totals": [vp, i32],
         "vlbm_checkpoint_size": [vp, C.POINTER(C.c_size_t)],
@@ -102,6 +103,7 @@ def lib():
         "vlbm_engine_step": [vp, C.POINTER(i32), C.POINTER(i32)],
         "vlbm_engine_release": [vp, i32],
         "vlbm_engine_usage": [vp, C.POINTER(i32), C.POINTER(i64)],
+        "vlbm_engine_slot_stats": [vp, i32, C.POINTER(i64), C.POINTER(i64)],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -291,6 +293,15 @@ class Hierarchy:
                 "active_cells": list(i.active_cells[: i.nlev]), "lups_per_step": i.lups_per_step,
                 "device_bytes": i.device_bytes, "steps": i.steps, "c": i.c, "beta": i.beta}
 
+    HOST_TIMERS = ("tag", "layout", "regrid", "build", "tasks", "capture", "regrids", "task_lists")
+
+    def host_times(self):
+        """Cumulative host-side milliseconds by activity and the regrid and
+        task-list counts (vlbm_host_times)."""
+        out = (C.c_double * len(self.HOST_TIMERS))()
+        _check(self._h, lib().vlbm_host_times(self._h, out))
+        return dict(zip(self.HOST_TIMERS, out[:]))
+
     def profile(self, steps):
         """Per-kernel device times over `steps` eagerly launched coarse steps:
         list of dicts (kind: sweep/close/end_step, level, launches, cells, ms)."""
@@ -398,6 +409,14 @@ class Engine:
         st = lib().vlbm_engine_release(self._e, int(slot))
         if st != 0:
             raise VlbmError(st, "vlbm_engine_release")
+
+    def slot_stats(self, slot):
+        """(coarse steps done, cell updates done) of a resident."""
+        a, b = C.c_int64(), C.c_int64()
+        st = lib().vlbm_engine_slot_stats(self._e, int(slot), C.byref(a), C.byref(b))
+        if st != 0:
+            raise VlbmError(st, "vlbm_engine_slot_stats")
+        return a.value, b.value
 
     def usage(self):
         n = C.c_int32()

@@ -207,10 +207,15 @@ def test_regrid_to_masks(V):
     g.advance(6)
     o.advance(6)
     t0, a0 = g.audit()
+    # the audit is exact: it equals math.fsum of the oracle's weighted W
+    ot, oa = o.totals()
+    assert np.array_equal(t0, ot) and np.array_equal(a0, oa)
     g.regrid_masks(refs_b)
     o.regrid(refs_b)
-    t1, _ = g.audit()
+    t1, a1 = g.audit()
     assert drift(t0, t1, a0) < 1e-14
+    ot, oa = o.totals()
+    assert np.array_equal(t1, ot) and np.array_equal(a1, oa)
     compare(o, g, 3)
     g.advance(7)
     o.advance(7)

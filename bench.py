@@ -207,6 +207,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="sweep variant; -1 (default) lets the autotuner pick variant, schedule and steps per launch")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -226,7 +228,16 @@ def main():
     case = I.vortex(N=512, steps=args.steps)
     stream = torch.cuda.Stream()
     g = V.Hierarchy.from_case(case, stream=stream)
-    # every step includes the conservation audit (fused into the sweep)
+    if args.variant >= 0:
+        g.set_tuning(variant=args.variant)
+    else:
+        # launch shape from the project's autotuner, timed on a scratch
+        # hierarchy of the same configuration (the persistent schedule is
+        # required for the per-step audit)
+        from paper_2609_35529_b300 import autotune
+        cands = [c for c in autotune.DEFAULT_CANDIDATES if c["schedule"] == 1]
+        autotune.tune(lambda: V.Hierarchy.from_case(case, stream=stream), target=g, candidates=cands)
+    # every step includes the exact conservation audit
     g.set_step_totals(True)
     tune = g.get_tuning()
     chunk = max(1, tune["graph_steps"])
@@ -267,18 +278,32 @@ def main():
     ms = job_time(ms, pg, "cuda")
     value = job_mlups(lups, steps, world, ms)
 
-    # roofline of the dominant kernel.  With the persistent schedule one
-    # timed iteration is one launch of the task kernel (all sweeps and
-    # closes of `chunk` coarse steps); its duration is the iteration's
-    # CUDA-event time on the library's stream.
+    # roofline of the dominant kernel, the persistent task kernel (all
+    # sweeps and closes of `chunk` coarse steps in one launch): timed alone
+    # -- the same launches with the per-step audit off, so that the graph
+    # holds just the kernel (and its 8-byte counter reset) -- with CUDA
+    # events on the library's stream, L2 flushed between launches
     pk = peaks()
-    launch_ms = statistics.mean(it_ms)
+    g.set_step_totals(False)
+    g.advance(chunk)
+    nk = min(iters, 64)
+    evk = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nk)]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for i in range(nk):
+            flush.fill_(float(i))
+            evk[i][0].record(stream)
+            g.advance(chunk)
+            evk[i][1].record(stream)
+    torch.cuda.synchronize()
+    g.sync()
+    launch_ms = statistics.mean(a.elapsed_time(b) for a, b in evk)
+    audit_share = 1.0 - launch_ms / statistics.mean(it_ms)
     cells = lups * chunk
     achieved_tflops = FLOPS_PER_LUP * cells / (launch_ms * 1e-3) / 1e12
     hbm_gbs = BYTES_PER_LUP * cells / (launch_ms * 1e-3) / 1e9
     kernel = "task_kernel" if tune["schedule"] == 1 else "sweep_kernel"
     # the per-phase sweep kernel measured alone (eager launches with events)
-    g.set_step_totals(False)
     prof = g.profile(min(steps, 64))
     sweep = [r for r in prof if r["kind"] == "sweep"]
     sw_ms = sum(r["ms"] for r in sweep)
@@ -290,13 +315,14 @@ def main():
             "hbm": {"achieved": round(hbm_gbs, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
                     "frac": round(hbm_gbs / pk["hbm_gbs"], 4), "peak_source": pk["source"]},
             "sweep_kernel_alone_mlups": round(sw_cells / sw_ms / 1e3, 1),
+            "audit_share_of_step": round(audit_share, 4),
             "fp64_pipe": {"ops_per_lup": FP64_OPS_PER_LUP,
                           "achieved_gops": round(FP64_OPS_PER_LUP * cells / (launch_ms * 1e-3) / 1e9, 1),
                           "peak_gops_nominal": round(2 * 148 * pk["sm_max_mhz"] * 1e6 / 1e9, 1),
                           "frac_of_nominal": round(FP64_OPS_PER_LUP * cells / (launch_ms * 1e-3)
                                                    / (2 * 148 * pk["sm_max_mhz"] * 1e6), 4)}}
-    # schedule 1: the task kernel and the per-step audit reduction
-    launches_per_iter = 2 if tune["schedule"] == 1 else None
+    # schedule 1: the task kernel and the two kernels of the per-step audit
+    launches_per_iter = 3 if tune["schedule"] == 1 else None
     if launches_per_iter is None:
         launches_per_iter = sum(r["launches"] for r in prof) / min(steps, 64) * chunk
 

@@ -235,13 +235,19 @@ vlbm_status vlbm_profile(vlbm_hier* h, int64_t coarse_steps, vlbm_kernel_time* o
  * phase in one persistent launch whose 8x8-tile tasks start as soon as the
  * tasks they depend on (read-after-write, write-after-read and
  * write-after-write on populations and flags, derived on the host) are
- * done -- the waits are bounded and report VLBM_ERR_TIMEOUT.  max_ctas caps
- * the grid (0 = one CTA per four tiles for schedule 0, all resident CTAs for
- * schedule 1); graph_steps (1..64) is the number of coarse steps captured
- * per CUDA graph.  vlbm_set_tuning returns ERR_ARG for a variant that does
- * not apply to the hierarchy (it is then unchanged). */
+ * done -- the waits are bounded and report VLBM_ERR_TIMEOUT; schedule 2
+ * (auto) uses schedule 0 until the current layout has lived persist_after
+ * coarse steps and schedule 1 from then on (the task lists of schedule 1
+ * cost host time at every layout change, which an adaptive run that regrids
+ * every few steps would pay again and again), and schedule 1 whenever
+ * per-step totals are on.  max_ctas caps the grid (0 = one CTA per four
+ * tiles for schedule 0, all resident CTAs for schedule 1); graph_steps
+ * (1..64) is the number of coarse steps captured per CUDA graph.
+ * vlbm_set_tuning returns ERR_ARG for a variant that does not apply to the
+ * hierarchy (it is then unchanged).  Results do not depend on the tuning. */
 typedef struct {
     int32_t variant, max_ctas, graph_steps, schedule;
+    int64_t persist_after; /* schedule 2 only, >= 0 */
 } vlbm_tuning;
 
 int32_t vlbm_num_variants(void);
@@ -257,6 +263,16 @@ vlbm_status vlbm_get_tuning(const vlbm_hier* h, vlbm_tuning* t);
  * first offending (a, b, hardware, emulated).  Runs on the current device
  * and synchronises it.  Errors: ERR_ARG, ERR_OOM, ERR_CUDA. */
 vlbm_status vlbm_selftest_fp64(uint64_t seed, int64_t n, uint64_t mismatches[4], double first_bad[16]);
+
+/* Self-test of the bounded waits of the persistent task kernel (schedule
+ * 1): launches it on one task that depends on a completion mark nothing
+ * sets.  The wait gives up after its poll limit (about a second), the
+ * kernel records the timeout in its status word and returns.  Returns
+ * VLBM_ERR_TIMEOUT when that happened (the expected outcome), VLBM_OK if
+ * the wait ended otherwise, ERR_CUDA on a CUDA error; *elapsed_ms is the
+ * kernel's duration and *status_word the raw status bits (2 = timeout).
+ * Uses its own stream and memory; synchronises. */
+vlbm_status vlbm_selftest_timeout(double* elapsed_ms, int32_t* status_word);
 
 /* Checkpoint / resume.  The blob (host memory, versioned) holds what a
  * coarse step needs at a sync point: the configuration it was made under,

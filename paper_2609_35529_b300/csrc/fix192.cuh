@@ -100,25 +100,39 @@ __device__ __forceinline__ Fix192 fix_shfl_down(const Fix192& a, int off) {
     return r;
 }
 
+// Word i of a (0 beyond the top), by selects.
+__device__ __forceinline__ unsigned long long fix_word(const Fix192& a, int i) {
+    return i == 0 ? a.w[0] : i == 1 ? a.w[1] : i == 2 ? a.w[2] : 0ull;
+}
+
+// The 64 bits of a starting at bit position pos (0 <= pos < 192).
+__device__ __forceinline__ unsigned long long fix_bits64(const Fix192& a, int pos) {
+    const int wi = pos >> 6, b = pos & 63;
+    const unsigned long long lo = fix_word(a, wi) >> b;
+    return b ? lo | (fix_word(a, wi + 1) << (64 - b)) : lo;
+}
+
 // Correctly rounded (nearest, ties to even) binary64 value of a * 2^-128.
 __device__ __forceinline__ double fix_to_double(Fix192 a) {
     const bool neg = (a.w[2] >> 63) != 0;
     if (neg) fix_neg(a);
     int p = -1;  // index of the leading one
-    for (int i = 2; i >= 0 && p < 0; i--)
-        if (a.w[i]) p = 64 * i + 63 - __clzll((long long)a.w[i]);
+    if (a.w[2]) p = 128 + 63 - __clzll((long long)a.w[2]);
+    else if (a.w[1]) p = 64 + 63 - __clzll((long long)a.w[1]);
+    else if (a.w[0]) p = 63 - __clzll((long long)a.w[0]);
     if (p < 0) return 0.0;
     unsigned long long m;
-    bool rnd = false, sticky = false;
     if (p <= 52) {
-        m = a.w[0];
+        m = a.w[0];  // exact
     } else {
-        const int s = p - 52;  // shift right by s: keep 53 bits
-        auto bit = [&](int k) { return (a.w[k >> 6] >> (k & 63)) & 1ull; };
-        m = 0;
-        for (int k = 52; k >= 0; k--) m = (m << 1) | bit(s + k);
-        rnd = bit(s - 1) != 0;
-        for (int k = 0; k < s - 1 && !sticky; k++) sticky = bit(k) != 0;
+        const int s = p - 52;  // keep bits [s, s + 53)
+        m = fix_bits64(a, s) & 0x001FFFFFFFFFFFFFull;
+        const int t = s - 1;  // rounding bit; sticky = any bit below it
+        const bool rnd = (fix_bits64(a, t) & 1ull) != 0;
+        const int tw = t >> 6, tb = t & 63;
+        bool sticky = (fix_word(a, tw) & ((1ull << tb) - 1ull)) != 0;
+        if (tw >= 1) sticky = sticky || a.w[0] != 0;
+        if (tw >= 2) sticky = sticky || a.w[1] != 0;
         if (rnd && (sticky || (m & 1ull))) {
             m += 1;
             if (m >> 53) {
@@ -127,14 +141,9 @@ __device__ __forceinline__ double fix_to_double(Fix192 a) {
             }
         }
     }
-    double r;
-    if (p <= 52) {
-        // exact integer multiple of 2^-128: scale by powers of two
-        r = (double)m;  // m < 2^53: exact
-    } else {
-        r = (double)m;
-        r = ldexp(r, p - 52);
-    }
+    // m < 2^53 is exact in binary64; scaling by powers of two is exact
+    double r = (double)m;
+    if (p > 52) r = ldexp(r, p - 52);
     r = ldexp(r, -128);
     return neg ? -r : r;
 }

@@ -163,7 +163,8 @@ struct vlbm_hier {
     DArr<LevelDev> atab;   // level table for audits (rebuilt with the layout)
     DArr<Item> aitems;     // active tiles of every level (audits)
     double* hout = nullptr;  // pinned host copy of the audit result
-    vlbm_tuning tune{1, 0, 8, 1};
+    vlbm_tuning tune{1, 0, 8, 1, 256};
+    long long layout_steps = 0;  // coarse steps taken on the current layout
     // per-step conservation totals recorded by vlbm_advance (pinned ring)
     bool step_audit = false;
     double times[VLBM_T_COUNT] = {};  // host-side time, see vlbm_host_times
@@ -415,7 +416,8 @@ struct Batch {
         // the last reset (the index maps persist between resets)
         std::vector<std::vector<int>> idx;
         std::vector<int> bx, by;
-        std::vector<Res> pool;
+        std::vector<Res> pool;  // [0, used) live; the rest keep their capacity
+        size_t used = 0;
         std::vector<std::pair<int, size_t>> touched;
         std::vector<int> cur;
         void reset(const std::vector<LevelDev>& tab) {
@@ -435,7 +437,7 @@ struct Batch {
                 }
             }
             touched.clear();
-            pool.clear();
+            used = 0;
             cur.clear();
         }
         // valid until the next call (the pool may grow)
@@ -443,8 +445,13 @@ struct Batch {
             const size_t k = ((size_t)kind * by[lid] + ty) * bx[lid] + tx;
             int& i = idx[lid][k];
             if (i < 0) {
-                i = (int)pool.size();
-                pool.emplace_back();
+                i = (int)used++;
+                if (used > pool.size()) pool.emplace_back();
+                Res& x = pool[i];
+                x.phase = -1;
+                x.writers.clear();
+                x.readers.clear();
+                x.prior.clear();
                 touched.emplace_back(lid, k);
             }
             return pool[i];
@@ -972,6 +979,7 @@ void install_layout(vlbm_hier* h, std::vector<uint8_t>* bin, std::vector<uint8_t
     }
     build_lists(h);
     h->tl[0].steps = h->tl[1].steps = -1;
+    h->layout_steps = 0;
     std::vector<Item> items;
     std::vector<LevelDev> tab;
     for (int l = 0; l < h->nlev; l++) {
@@ -1128,18 +1136,28 @@ void destroy_levels(vlbm_hier* h) {
     }
 }
 
-void ensure_own_batch(vlbm_hier* h) {
+// Schedule of the next steps: 2 (auto) takes the per-phase launches on a
+// layout younger than persist_after coarse steps -- an adaptive run that
+// regrids often never pays for a task list -- and the persistent task
+// kernel after that, or whenever per-step totals are on.
+int effective_schedule(const vlbm_hier* h) {
+    if (h->tune.schedule != 2) return h->tune.schedule;
+    return (h->step_audit || h->layout_steps >= h->tune.persist_after) ? 1 : 0;
+}
+
+void ensure_own_batch(vlbm_hier* h, int sched) {
     if (!h->own) {
         h->own = new Batch();
         h->own->mem = &h->mem;
         h->own->members.push_back(h);
     }
+    if (h->own->valid && h->own->schedule_mode != sched) h->own->valid = false;
     if (!h->own->valid) {
         h->own->variant = h->tune.variant;
         h->own->max_ctas = h->tune.max_ctas;
         h->own->G = h->tune.graph_steps;
-        h->own->schedule_mode = h->tune.schedule;
-        h->own->audit = h->step_audit && h->tune.schedule == 1;
+        h->own->schedule_mode = sched;
+        h->own->audit = h->step_audit && sched == 1;
         const auto t0 = std::chrono::steady_clock::now();
         h->own->build(h->stream);
         h->times[VLBM_T_BUILD] += ms_since(t0);
@@ -1316,29 +1334,37 @@ vlbm_status vlbm_advance(vlbm_hier* h, int64_t coarse_steps) {
     return run(h, [&] {
         if (coarse_steps < 0) throw Fail{VLBM_ERR_ARG, "negative step count"};
         if (h->engine) throw Fail{VLBM_ERR_ARG, "hierarchy is resident in an engine"};
-        if (coarse_steps == 0) return;
-        ensure_own_batch(h);
-        Batch& b = *h->own;
-        if (!b.audit) {
-            b.advance(coarse_steps, h->stream);
-        } else {
-            long long n = coarse_steps;
-            if (n >= b.G) {
-                cudaGraphExec_t ex = b.exec_for(1, h->stream);
-                for (; n >= b.G; n -= b.G) {
-                    VCK(cudaGraphLaunch(ex, h->stream));
-                    record_rows(h, h->tl[1].aout.p, b.G);
+        long long left = coarse_steps;
+        while (left > 0) {
+            const int sched = effective_schedule(h);
+            // under auto, per-phase launches only up to the switch point
+            long long n = left;
+            if (h->tune.schedule == 2 && sched == 0) n = std::min(left, h->tune.persist_after - h->layout_steps);
+            ensure_own_batch(h, sched);
+            Batch& b = *h->own;
+            if (!b.audit) {
+                b.advance(n, h->stream);
+            } else {
+                long long m = n;
+                if (m >= b.G) {
+                    cudaGraphExec_t ex = b.exec_for(1, h->stream);
+                    for (; m >= b.G; m -= b.G) {
+                        VCK(cudaGraphLaunch(ex, h->stream));
+                        record_rows(h, h->tl[1].aout.p, b.G);
+                    }
+                }
+                if (m > 0) {
+                    cudaGraphExec_t ex = b.exec_for(0, h->stream);
+                    for (; m > 0; m--) {
+                        VCK(cudaGraphLaunch(ex, h->stream));
+                        record_rows(h, h->tl[0].aout.p, 1);
+                    }
                 }
             }
-            if (n > 0) {
-                cudaGraphExec_t ex = b.exec_for(0, h->stream);
-                for (; n > 0; n--) {
-                    VCK(cudaGraphLaunch(ex, h->stream));
-                    record_rows(h, h->tl[0].aout.p, 1);
-                }
-            }
+            h->steps += n;
+            h->layout_steps += n;
+            left -= n;
         }
-        h->steps += coarse_steps;
     });
 }
 
@@ -1453,7 +1479,7 @@ vlbm_status vlbm_checkpoint_load(vlbm_hier* h, const void* blob, size_t bytes) {
 
 vlbm_status vlbm_set_step_totals(vlbm_hier* h, int32_t on) {
     return run(h, [&] {
-        if (on && h->tune.schedule != 1) throw Fail{VLBM_ERR_ARG, "per-step totals need the persistent schedule"};
+        if (on && h->tune.schedule == 0) throw Fail{VLBM_ERR_ARG, "per-step totals need the persistent schedule"};
         if (on && !h->hist) VCK(cudaMallocHost((void**)&h->hist, (size_t)h->hist_cap * 8 * sizeof(double)));
         VCK(cudaStreamSynchronize(h->stream));
         h->step_audit = on != 0;
@@ -1639,11 +1665,11 @@ int32_t vlbm_num_variants(void) { return sweep_variants(); }
 vlbm_status vlbm_set_tuning(vlbm_hier* h, const vlbm_tuning* t) {
     return run(h, [&] {
         if (!t || t->variant < 0 || t->variant >= sweep_variants() || t->max_ctas < 0 || t->graph_steps < 1 ||
-            t->graph_steps > 64 || t->schedule < 0 || t->schedule > 1)
+            t->graph_steps > 64 || t->schedule < 0 || t->schedule > 2 || t->persist_after < 0)
             throw Fail{VLBM_ERR_ARG, "bad tuning"};
         if (sweep_variant_needs_om_minus1(t->variant) && h->om != -1.0)
             throw Fail{VLBM_ERR_ARG, "variant applies only when 1 - 2 beta == -1"};
-        if (h->step_audit && t->schedule != 1) throw Fail{VLBM_ERR_ARG, "per-step totals need the persistent schedule"};
+        if (h->step_audit && t->schedule == 0) throw Fail{VLBM_ERR_ARG, "per-step totals need the persistent schedule"};
         h->tune = *t;
         h->tl[0].steps = h->tl[1].steps = -1;
         if (h->own) h->own->valid = false;
@@ -1660,12 +1686,13 @@ vlbm_status vlbm_profile(vlbm_hier* h, int64_t coarse_steps, vlbm_kernel_time* o
     return run(h, [&] {
         if (coarse_steps < 0 || !out || !n) throw Fail{VLBM_ERR_ARG, "bad profile arguments"};
         if (h->engine) throw Fail{VLBM_ERR_ARG, "hierarchy is resident in an engine"};
-        ensure_own_batch(h);
+        ensure_own_batch(h, effective_schedule(h));  // profile() launches phase by phase
         long long cells[VLBM_MAX_LEVELS] = {};
         for (int l = 0; l < h->nlev; l++) cells[l] = h->lev[l].active_cells;
         std::vector<Batch::Rec> recs;
         h->own->profile(coarse_steps, cells, recs, h->stream);
         h->steps += coarse_steps;
+        h->layout_steps += coarse_steps;
         if ((int)recs.size() > cap) throw Fail{VLBM_ERR_ARG, "record capacity too small"};
         for (size_t i = 0; i < recs.size(); i++) {
             out[i].kind = recs[i].kind;

@@ -5,6 +5,7 @@
 // --fmad=false).  The expression order is fixed so that results do not
 // depend on the launch configuration.
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <cstdint>
 
 #include "fix192.cuh"
@@ -76,6 +77,10 @@ __device__ __forceinline__ bool collide(double f[16], double om, double hb, doub
 // fma(1 - 2 beta, f, A) as an addition when 1 - 2 beta is -1 (its product
 // is then exact).
 enum : int { EM_MOM = 1, EM_A = 2, EM_FLUX = 4, EM_OMF = 8 };
+// Launch-shape bit of a variant (no effect on the arithmetic): the
+// persistent task kernel prefetches the next task's populations into
+// shared memory (see task_kernel).
+enum : int { TK_PREFETCH = 256 };
 
 template <bool E>
 __device__ __forceinline__ double xadd(double a, double b) {
@@ -261,7 +266,8 @@ __device__ __noinline__ void sweep_special(const LevelDev* __restrict__ levs, co
 // sub-step; step: coarse step index inside a multi-step launch.
 template <int P, bool COH>
 __device__ __forceinline__ void sweep_cell(const LevelDev* __restrict__ levs, const LevelDev& L, int x, int y, int kk,
-                                           int kkp, int step, double* Wout = nullptr) {
+                                           int kkp, int step, double* Wout = nullptr,
+                                           const double* __restrict__ pre = nullptr) {
     const int nx = L.nx, ny = L.ny;
     if (x >= nx || y >= ny) return;
     const long long c = (long long)y * L.pitch + x;
@@ -272,8 +278,13 @@ __device__ __forceinline__ void sweep_cell(const LevelDev* __restrict__ levs, co
     level_bufs(L, kk, step, src, dst);
     const long long plane = L.plane;
     double f[16];
+    if (pre) {  // this cell's populations, prefetched into shared memory (stride 64)
 #pragma unroll
-    for (int q = 0; q < 16; q++) f[q] = ld<COH>(src + q * plane + c);
+        for (int q = 0; q < 16; q++) f[q] = pre[q * 64];
+    } else {
+#pragma unroll
+        for (int q = 0; q < 16; q++) f[q] = ld<COH>(src + q * plane + c);
+    }
     if (!collide_p<P>(f, L.om, L.hb, L.bcs, L.gm1, Wout)) atomicOr(L.status, ST_NONPHYS);
     // push streaming (Eq. 5): f*_i lands on x + c_i
     long long cxp = c + 1, cxm = c - 1, cyp = c + L.pitch, cym = c - L.pitch;
@@ -389,56 +400,132 @@ __device__ __forceinline__ void wait_done(const unsigned* p, unsigned epoch, int
     atomicOr(status, ST_TIMEOUT);
 }
 
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// The segment holding ticket t and the task's index in it.
+__device__ __forceinline__ int find_segment(const int* __restrict__ prefix, int nseg, int t) {
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Prefetch of task t2 by one warp, if t2 is a level sweep whose
+// dependencies are all complete already (checked without waiting; each
+// warp decides for its own cells).  Lane pair p of the group copies the two
+// cells (2p, 2p + 1) of the tile, the even lane planes 0-7, the odd lane
+// planes 8-15, 16 bytes per copy through L2, into buf[q][cell].  Returns
+// whether this warp's cells were requested.  The data cannot change before
+// t2 runs: every later writer of t2's source cells waits for t2.
+__device__ __forceinline__ bool prefetch_task(const LevelDev* __restrict__ levs, const Segment* __restrict__ segs,
+                                              const int* __restrict__ prefix, int nseg, int t2, unsigned epoch,
+                                              double* buf, int lt) {
+    const int sg = find_segment(prefix, nseg, t2);
+    const Segment S = segs[sg];
+    const Task T = S.tasks[t2 - prefix[sg]];
+    if (T.kind != 0) return false;
+    bool ok = true;
+    for (int j = lt & 31; j < T.ndep; j += 32) ok = ok && ld_acquire(S.done + S.deps[T.dep0 + j]) == epoch;
+    if (!__all_sync(0xffffffffu, ok)) return false;
+    __syncwarp();  // the acquire loads above precede every copy below
+    const LevelDev& L = levs[T.lid + S.lid_base];
+    const double* src;
+    double* dst;
+    level_bufs(L, T.kk, T.step, src, dst);
+    const int pr = lt >> 1, cy = pr >> 2, x = T.tx * TILE + (pr & 3) * 2, y = T.ty * TILE + cy;
+    if (y < L.ny) {  // x + 1 < pitch always: rows are padded to 16 cells
+        const double* g0 = src + (long long)y * L.pitch + x;
+        const int q0 = (lt & 1) * 8;
+#pragma unroll
+        for (int q = q0; q < q0 + 8; q++) cp_async16(buf + q * 64 + 2 * pr, g0 + q * L.plane);
+    }
+    return true;
+}
+
 // Tasks are claimed in list order -- segment by segment, each segment in a
 // topological order of its dependencies -- so every task a claimed task
 // waits for was claimed earlier by a running thread group: the schedule
-// cannot deadlock, whatever the number of resident CTAs.
+// cannot deadlock, whatever the number of resident CTAs.  A group claims its
+// next ticket once the waits of its current task are over, so a claimed but
+// unstarted task only ever waits behind a task that no longer waits.
+//
+// Memory ordering: the group's lane 0 publishes a task with a gpu-scope
+// fence and a release store after a group barrier (the writes of all 64
+// threads precede the barrier); waiting lanes read the marks with acquire
+// loads before the group barrier that precedes the task's reads, which go
+// through L2 (ld.global.cg, cp.async.cg).
+//
+// With TK_PREFETCH each group double-buffers the populations of its tasks
+// in shared memory (2 x 16 planes x 64 cells): while a task runs, the copy
+// of the next one is in flight whenever its dependencies are complete.
+constexpr int TK_SMEM = TILES_PER_CTA * 2 * NQ * 64 * (int)sizeof(double);
+
 template <int P, int MINB>
 __global__ void __launch_bounds__(CTA_THREADS, MINB)
 task_kernel(const LevelDev* __restrict__ levs, const Segment* __restrict__ segs, const int* __restrict__ prefix,
             int* ctl) {
-    __shared__ int s_task[TILES_PER_CTA];
+    constexpr bool PF = (P & TK_PREFETCH) != 0;
+    extern __shared__ double s_pf[];  // PF only: [group][buffer][q][cell]
+    __shared__ int s_task[TILES_PER_CTA][2];
     const int g = threadIdx.x >> 6;
     const int lt = threadIdx.x & 63;
     const int cx = lt & 7, cy = lt >> 3;
     const unsigned epoch = (unsigned)ctl[CTL_EPOCH];
     const int total = ctl[CTL_TOTAL], nseg = ctl[CTL_NSEG];
-    for (;;) {
-        if (lt == 0) s_task[g] = atomicAdd(&ctl[CTL_CLAIM], 1);
-        group_bar(g);
-        const int t = s_task[g];
-        group_bar(g);
+    bool pf = false;  // PF: this warp's cells of the current task are in buffer pb
+    int pb = 0;
+    if (lt == 0) s_task[g][0] = atomicAdd(&ctl[CTL_CLAIM], 1);
+    group_bar(g);
+    for (int par = 0;; par ^= 1) {
+        const int t = s_task[g][par];
         if (t >= total) break;
-        int lo = 0, hi = nseg - 1;  // the segment holding ticket t
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (prefix[mid] <= t) lo = mid;
-            else hi = mid - 1;
-        }
-        const Segment S = segs[lo];
-        const int i = t - prefix[lo];
+        const int sg = find_segment(prefix, nseg, t);
+        const Segment S = segs[sg];
+        const int i = t - prefix[sg];
         const Task T = S.tasks[i];
         const LevelDev& L = levs[T.lid + S.lid_base];
         for (int j = lt; j < T.ndep; j += 64) wait_done(S.done + S.deps[T.dep0 + j], epoch, L.status);
+        if (lt == 0) s_task[g][par ^ 1] = atomicAdd(&ctl[CTL_CLAIM], 1);
         group_bar(g);
-        __threadfence();
+        const double* pre = nullptr;
+        bool pf_next = false;
+        if constexpr (PF) {
+            const int t2 = s_task[g][par ^ 1];
+            double* base = s_pf + (size_t)g * 2 * NQ * 64;
+            if (t2 < total) pf_next = prefetch_task(levs, segs, prefix, nseg, t2, epoch, base + (pb ^ 1) * NQ * 64, lt);
+            cp_async_commit();
+            if (pf) {
+                cp_async_wait_prev();  // the copies of the current task
+                __syncwarp();          // ... including the partner lane's
+                pre = base + pb * NQ * 64 + lt;
+            }
+        }
         if (T.kind == 0) {
             if (S.aw && T.aslot >= 0) {
                 // audited sweep: keep the moments of the cell (0 off the
                 // active set) for the exact reduction after the launch
                 double W[4] = {0.0, 0.0, 0.0, 0.0};
-                sweep_cell<P, true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.kkp, T.step, W);
+                sweep_cell<P, true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.kkp, T.step, W, pre);
                 double* o = S.aw + (size_t)T.aslot * AUDIT_SLOT + lt;
                 for (int k = 0; k < 4; k++) o[k * 64] = W[k];
             } else {
-                sweep_cell<P, true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.kkp, T.step);
+                sweep_cell<P, true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.kkp, T.step, nullptr, pre);
             }
         } else {
             close_cell<true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.step);
         }
-        __threadfence();
         group_bar(g);
         if (lt == 0) {
+            __threadfence();
             st_release(S.done + i, epoch);
             if (atomicAdd(&ctl[CTL_FIN], 1) == total - 1) {
                 // every task of the launch is complete: advance the parity of
@@ -448,7 +535,12 @@ task_kernel(const LevelDev* __restrict__ levs, const Segment* __restrict__ segs,
                 ctl[CTL_EPOCH] = (int)(epoch + 1);
             }
         }
+        if constexpr (PF) {
+            pf = pf_next;
+            pb ^= 1;
+        }
     }
+    if constexpr (PF) cp_async_wait_all();
 }
 
 __global__ void end_step_kernel(int* const* par, int n) {
@@ -459,8 +551,43 @@ __global__ void end_step_kernel(int* const* par, int n) {
 // Exact sums of the audited moments: block b covers the audit slots
 // [rng[b].x, rng[b].y).  A slot holds W_k of the 64 cells of one tile,
 // layout [k][cell], at weight 2^scale[slot]; thread t always reads field
-// k = t / 64, so each thread keeps just two 192-bit sums.  The block's 8
-// exact sums go to part[b][0..23] (W_0..W_3, then |W_0|..|W_3|).
+// k = t / 64, so each thread keeps just two sums.  The block's 8 exact sums
+// go to part[b][0..23] (W_0..W_3, then |W_0|..|W_3|).
+//
+// Fast path: the values a thread sees have nearly the same exponent, so
+// they are added as integers m * 2^d (m the 53-bit significand) into a
+// two's-complement 128-bit window whose least significant bit sits at
+// position `base` of the 192-bit fixed point (0 <= base <= 64, chosen from
+// the thread's first value).  A value whose bits fit the window exactly
+// (0 <= d < 64) takes the fast path; zeros are skipped; anything else
+// (subnormal, tiny, huge, NaN) takes the general 192-bit path.  Below 2^10
+// fast additions the window cannot overflow (|m 2^d| < 2^117); it is
+// folded into the 192-bit sums before that and at the end, so the result
+// is the same exact sum either way.
+struct Win128 {
+    unsigned long long lo, hi;
+};
+
+__device__ __forceinline__ void win_fold(Fix192& acc, Win128& w, int base) {
+    const unsigned long long ext = (w.hi >> 63) ? ~0ull : 0ull;
+    Fix192 f;
+    if (base == 0) {
+        f.w[0] = w.lo;
+        f.w[1] = w.hi;
+        f.w[2] = ext;
+    } else if (base == 64) {
+        f.w[0] = 0ull;
+        f.w[1] = w.lo;
+        f.w[2] = w.hi;
+    } else {
+        f.w[0] = w.lo << base;
+        f.w[1] = (w.hi << base) | (w.lo >> (64 - base));
+        f.w[2] = (ext << base) | (w.hi >> (64 - base));
+    }
+    fix_add(acc, f);
+    w.lo = w.hi = 0ull;
+}
+
 __global__ void __launch_bounds__(256) audit_slots_kernel(const double* __restrict__ aw, const int2* __restrict__ rng,
                                                           const int* __restrict__ scale,
                                                           unsigned long long* __restrict__ part) {
@@ -468,8 +595,61 @@ __global__ void __launch_bounds__(256) audit_slots_kernel(const double* __restri
     const int t = threadIdx.x;
     const int2 r = rng[blockIdx.x];
     Fix192 sum = fix_zero(), abs_sum = fix_zero();
-    for (int j = r.x; j < r.y; j++)
-        fix_accumulate(sum, abs_sum, __ldcs(aw + (size_t)j * AUDIT_SLOT + t), __ldg(scale + j));
+    Win128 ws{0ull, 0ull}, wa{0ull, 0ull};
+    int base = -1, nfast = 0;
+    // AUDIT_BATCH loads in flight per thread, then their accumulation
+    constexpr int AUDIT_BATCH = 8;
+    for (int j0 = r.x; j0 < r.y; j0 += AUDIT_BATCH) {
+        double vb[AUDIT_BATCH];
+        int sb[AUDIT_BATCH];
+#pragma unroll
+        for (int u = 0; u < AUDIT_BATCH; u++) {
+            const int j = j0 + u;
+            vb[u] = j < r.y ? __ldcs(aw + (size_t)j * AUDIT_SLOT + t) : 0.0;
+            sb[u] = j < r.y ? __ldg(scale + j) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < AUDIT_BATCH; u++) {
+            const double v = vb[u];
+            const unsigned long long B = (unsigned long long)__double_as_longlong(v);
+            if ((B << 1) == 0ull) continue;  // +-0
+            const int E = (int)((B >> 52) & 0x7FFull);
+            const int sc = sb[u];
+            const int sh = E - 947 + sc;  // position of the significand's lsb (2^-128 units)
+            if (base < 0 && E != 0 && E != 2047) base = min(max(sh - 32, 0), 64);
+            const int d = sh - base;
+            if (E == 0 || E == 2047 || base < 0 || d < 0 || d > 63) {
+                fix_accumulate(sum, abs_sum, v, sc);
+                continue;
+            }
+            const unsigned long long m = (B & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+            const unsigned long long lo = m << d;
+            const unsigned long long hi = d ? m >> (64 - d) : 0ull;
+            // |v| into the magnitude window
+            const unsigned long long a0 = wa.lo + lo;
+            wa.hi += hi + (a0 < lo ? 1ull : 0ull);
+            wa.lo = a0;
+            // +-|v| into the signed window
+            if (B >> 63) {
+                const unsigned long long brw = ws.lo < lo ? 1ull : 0ull;
+                ws.lo -= lo;
+                ws.hi -= hi + brw;
+            } else {
+                const unsigned long long s0 = ws.lo + lo;
+                ws.hi += hi + (s0 < lo ? 1ull : 0ull);
+                ws.lo = s0;
+            }
+            if (++nfast == 1023) {
+                win_fold(sum, ws, base);
+                win_fold(abs_sum, wa, base);
+                nfast = 0;
+            }
+        }
+    }
+    if (base >= 0) {
+        win_fold(sum, ws, base);
+        win_fold(abs_sum, wa, base);
+    }
     for (int off = 16; off > 0; off >>= 1) {
         const Fix192 o1 = fix_shfl_down(sum, off);
         const Fix192 o2 = fix_shfl_down(abs_sum, off);
@@ -854,9 +1034,10 @@ static inline int flat_grid(long long n) {
 #define VLBM_SWEEP_VARIANTS(X)                                   \
     X(0, 0, 2) X(1, 0, 3) X(2, EM_MOM, 2) X(3, EM_MOM | EM_A, 2) \
     X(4, EM_MOM | EM_A | EM_FLUX, 2) X(5, EM_FLUX, 2) X(6, EM_MOM | EM_A | EM_FLUX | EM_OMF, 2) \
-    X(7, EM_MOM | EM_A | EM_OMF, 2) X(8, EM_MOM | EM_A | EM_FLUX, 3) X(9, EM_MOM | EM_A | EM_FLUX | EM_OMF, 3)
+    X(7, EM_MOM | EM_A | EM_OMF, 2) X(8, EM_MOM | EM_A | EM_FLUX, 3) X(9, EM_MOM | EM_A | EM_FLUX | EM_OMF, 3) \
+    X(10, 0, 4) X(11, TK_PREFETCH, 3) X(12, TK_PREFETCH, 2)
 
-int sweep_variants() { return 10; }
+int sweep_variants() { return 13; }
 
 // variant -> whether it needs 1 - 2 beta == -1
 bool sweep_variant_needs_om_minus1(int v) {
@@ -889,7 +1070,16 @@ int task_kernel_ctas(int variant) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     switch (variant) {
-#define X(id, P, B) case id: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, task_kernel<P, B>, CTA_THREADS, 0); break;
+#define X(id, P, B)                                                                                        \
+    case id:                                                                                               \
+        if ((P) & TK_PREFETCH) {                                                                           \
+            cudaFuncSetAttribute(task_kernel<P, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, TK_SMEM); \
+            cudaFuncSetAttribute(task_kernel<P, B>, cudaFuncAttributePreferredSharedMemoryCarveout,        \
+                                 (int)cudaSharedmemCarveoutMaxShared);                                     \
+        }                                                                                                  \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, task_kernel<P, B>, CTA_THREADS,                \
+                                                      ((P) & TK_PREFETCH) ? TK_SMEM : 0);                  \
+        break;
         VLBM_SWEEP_VARIANTS(X)
 #undef X
     }
@@ -899,9 +1089,13 @@ int task_kernel_ctas(int variant) {
 
 cudaError_t launch_tasks(const LevelDev* levs, const Segment* segs, const int* prefix, int* ctl, int variant, int ctas,
                          cudaStream_t s) {
-    const int g = ctas > 0 ? ctas : task_kernel_ctas(variant);
+    const int full = task_kernel_ctas(variant);  // also sets the kernel's shared-memory attributes
+    const int g = ctas > 0 ? std::min(ctas, full) : full;
     switch (variant) {
-#define X(id, P, B) case id: task_kernel<P, B><<<g, CTA_THREADS, 0, s>>>(levs, segs, prefix, ctl); break;
+#define X(id, P, B)                                                                                      \
+    case id:                                                                                             \
+        task_kernel<P, B><<<g, CTA_THREADS, ((P) & TK_PREFETCH) ? TK_SMEM : 0, s>>>(levs, segs, prefix, ctl); \
+        break;
         VLBM_SWEEP_VARIANTS(X)
 #undef X
         default: return cudaErrorInvalidValue;

@@ -1,7 +1,7 @@
 """End-to-end runs of the paper's 2-D workloads on the GPU, with the checks
 each one is about.  One JSON line per run on stdout.
 
-  python -m paper_2609_35529_b300.runs [pulse] [vortex] [riemann] [shockbubble[=steps]]
+  python -m paper_2609_35529_b300.runs [pulse] [vortex] [riemann] [shockbubble[=steps,every,schedule]]
 
 pulse        two-level Gaussian pulse, periodic 64^2, 200 coarse steps:
              per-step conservation (fused audit) and the uniform-state run
@@ -137,11 +137,13 @@ def run_riemann():
           "rho_min": float(W[0][act].min()), "rho_max": float(W[0][act].max())})
 
 
-def run_shockbubble(steps=4000, every=4):
+def run_shockbubble(steps=4000, every=4, schedule=2):
     """The adaptive run; the totals are audited (exactly) before and after
-    every regrid."""
+    every regrid.  schedule 2 (auto) keeps the per-phase launches on layouts
+    that live only `every` steps."""
     cs = I.shockbubble(steps=steps)
     h = V.Hierarchy.from_case(cs)
+    h.set_tuning(schedule=schedule)
     for _ in range(cs.nlev - 1):
         h.regrid()
     worst = 0.0
@@ -164,7 +166,7 @@ def run_shockbubble(steps=4000, every=4):
             active.append([done] + h.info()["active_cells"])
     h.sync()
     el = now() - t0
-    emit({"run": "shockbubble", "coarse": [cs.nx0, cs.ny0], "levels": cs.nlev, "steps": steps,
+    emit({"run": "shockbubble", "coarse": [cs.nx0, cs.ny0], "levels": cs.nlev, "steps": steps, "schedule": schedule,
           "regrids": (steps - 1) // every, "wall_s": el, "mlups_incl_regrid": lups / el / 1e6,
           "max_rel_change_across_regrid": worst, "active_cells_every_500": active,
           "host_ms": h.host_times()})
@@ -175,7 +177,7 @@ def main(argv=None):
     for w in which:
         name, _, arg = w.partition("=")
         fn = {"pulse": run_pulse, "vortex": run_vortex, "riemann": run_riemann, "shockbubble": run_shockbubble}[name]
-        fn(int(arg)) if arg else fn()
+        fn(*[int(a) for a in arg.split(",")]) if arg else fn()
 
 
 if __name__ == "__main__":

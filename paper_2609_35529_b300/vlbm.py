@@ -56,7 +56,8 @@ class vlbm_kernel_time(C.Structure):
 
 
 class vlbm_tuning(C.Structure):
-    _fields_ = [("variant", C.c_int32), ("max_ctas", C.c_int32), ("graph_steps", C.c_int32), ("schedule", C.c_int32)]
+    _fields_ = [("variant", C.c_int32), ("max_ctas", C.c_int32), ("graph_steps", C.c_int32), ("schedule", C.c_int32),
+                ("persist_after", C.c_int64)]
 
 
 class vlbm_info(C.Structure):
@@ -116,6 +117,8 @@ def lib():
     L.vlbm_get_tuning.argtypes = [vp, C.POINTER(vlbm_tuning)]
     L.vlbm_get_tuning.restype = C.c_int
     L.vlbm_selftest_fp64.argtypes = [C.c_uint64, i64, C.POINTER(C.c_uint64), dp]
+    L.vlbm_selftest_timeout.argtypes = [dp, C.POINTER(i32)]
+    L.vlbm_selftest_timeout.restype = C.c_int
     L.vlbm_selftest_fp64.restype = C.c_int
     L.vlbm_totals_static.argtypes = [vp, i64, i32, i32, C.c_double, vp, vp]
     L.vlbm_totals_static.restype = C.c_int
@@ -337,14 +340,17 @@ class Hierarchy:
                                                    C.byref(n)))
         return out[: n.value]
 
-    def set_tuning(self, variant=1, max_ctas=0, graph_steps=8, schedule=1):
-        t = vlbm_tuning(variant, max_ctas, graph_steps, schedule)
+    def set_tuning(self, variant=1, max_ctas=0, graph_steps=8, schedule=1, persist_after=256):
+        """schedule: 0 per-phase launches, 1 persistent task kernel, 2 auto
+        (per-phase until the layout has lived persist_after coarse steps)."""
+        t = vlbm_tuning(variant, max_ctas, graph_steps, schedule, persist_after)
         _check(self._h, lib().vlbm_set_tuning(self._h, C.byref(t)))
 
     def get_tuning(self):
         t = vlbm_tuning()
         _check(self._h, lib().vlbm_get_tuning(self._h, C.byref(t)))
-        return {"variant": t.variant, "max_ctas": t.max_ctas, "graph_steps": t.graph_steps, "schedule": t.schedule}
+        return {"variant": t.variant, "max_ctas": t.max_ctas, "graph_steps": t.graph_steps, "schedule": t.schedule,
+                "persist_after": t.persist_after}
 
     def last_error(self):
         return lib().vlbm_last_error(self._h).decode()
@@ -373,6 +379,16 @@ def selftest_fp64(seed, n):
         raise VlbmError(st, "vlbm_selftest_fp64")
     names = ["add", "sub", "mul", "half"]
     return {k: int(bad[i]) for i, k in enumerate(names)}, {k: tuple(first[4 * i: 4 * i + 4]) for i, k in enumerate(names)}
+
+
+def selftest_timeout():
+    """Bounded-wait self-test of the persistent kernel: returns (status code,
+    kernel milliseconds, raw status bits); the expected status is
+    VLBM_ERR_TIMEOUT (the wait on a mark nothing sets gives up)."""
+    ms = C.c_double()
+    word = C.c_int32()
+    st = lib().vlbm_selftest_timeout(C.byref(ms), C.byref(word))
+    return st, ms.value, word.value
 
 
 class Engine:

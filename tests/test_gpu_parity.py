@@ -122,18 +122,22 @@ def test_two_level_pulse_full_run(V):
     np.testing.assert_allclose(t1, ot, rtol=1e-14, atol=1e-14 * oa.max())
 
 
-@pytest.mark.parametrize("schedule,graph_steps", [(1, 8), (0, 8), (1, 3)])
-def test_three_level_periodic_ragged(V, schedule, graph_steps):
+@pytest.mark.parametrize("schedule,graph_steps,variant",
+                         [(1, 8, 1), (0, 8, 1), (1, 3, 1), (2, 4, 1), (1, 8, 10), (1, 8, 11), (1, 3, 12)])
+def test_three_level_periodic_ragged(V, schedule, graph_steps, variant):
     """Three levels on a domain whose size is not a multiple of the tile
     (ragged last tile column/row), including a patch that wraps across the
-    periodic seam; both schedules (per-phase launches and the persistent
-    task kernel, with an odd number of steps per launch)."""
+    periodic seam; every schedule (per-phase launches, the persistent task
+    kernel with an odd number of steps per launch, and auto switching from
+    the first to the second after 7 steps, inside one advance call) and the
+    launch-shape variants (4 CTAs/SM; shared-memory prefetch of the next
+    task at 3 and 2 CTAs/SM)."""
     nx0, ny0 = 52, 44
     refs = I.box_refs(nx0, ny0, 3, [(0, 8, 8, 24, 16), (0, 0, 32, 8, 8), (0, 48, 32, 4, 8)])
     refs[1][24:40, 24:56] = 1
     cs = I.smooth_random(nx0, ny0, 3, refs, seed=21, amp=0.25, beta=0.8, steps=25)
     g = V.Hierarchy.from_case(cs)
-    g.set_tuning(variant=1, graph_steps=graph_steps, schedule=schedule)
+    g.set_tuning(variant=variant, graph_steps=graph_steps, schedule=schedule, persist_after=7)
     o = oracle_of(cs)
     t0, a0 = g.audit()
     g.advance(cs.steps)
@@ -389,3 +393,68 @@ def test_checkpoint_resume_is_bitwise(V):
         ia, ra = a.layout(l)
         act = (ia == 1) & (ra == 0)
         assert np.array_equal(a.get_populations(l)[:, act], b.get_populations(l)[:, act])
+
+
+def test_exact_totals_on_wide_value_ranges(V):
+    """The exact audits (fused per-step totals and vlbm_audit) on two-level
+    states whose momenta take zeros, subnormals and values of both signs
+    over many decades, and whose densities and energies span six and four
+    decades: both equal math.fsum of the area-weighted moments, which the
+    test computes from the populations themselves (the same additions as
+    the sweep).  Momenta stay small against the pressure so that the one
+    step taken stays physical across the interface."""
+    n = 40
+    refs = I.box_refs(n, n, 2, [(0, 8, 16, 24, 16)])
+    cs = I.smooth_random(n, n, 2, refs, seed=5, steps=1, beta=0.5)
+    rng = np.random.default_rng(2024)
+
+    def momentum(shape, rho):
+        kind = rng.integers(0, 4, size=shape)
+        sign = np.where(rng.random(shape) < 0.5, -1.0, 1.0)
+        m = sign * rho * 10.0 ** rng.uniform(-8, -3, size=shape)
+        m = np.where(kind == 0, 0.0, m)
+        m = np.where(kind == 1, sign * 10.0 ** rng.uniform(-320, -250, size=shape), m)
+        return m
+
+    for l in range(cs.nlev):
+        shape = cs.W[l].shape[1:]
+        rho = 10.0 ** rng.uniform(-3, 3, size=shape)
+        mu, mv = momentum(shape, rho), momentum(shape, rho)
+        p = 10.0 ** rng.uniform(-2, 2, size=shape)
+        cs.W[l] = np.stack([rho, mu, mv, 0.5 * (mu * mu + mv * mv) / rho + p / (cs.gamma - 1.0)])
+    cs.c *= 100.0  # one quiet step: every intermediate state stays physical
+    g = V.Hierarchy.from_case(cs)
+    tot = [[] for _ in range(4)]
+    for l in range(cs.nlev):
+        f = g.get_populations(l)
+        a, b = g.layout(l)
+        act = (a == 1) & (b == 0)
+        for k in range(4):
+            w = (f[k] + f[4 + k]) + (f[8 + k] + f[12 + k])
+            tot[k].append(w[act] * 0.25 ** l)
+    exp_t = np.array([math.fsum(np.concatenate(t)) for t in tot])
+    exp_a = np.array([math.fsum(np.abs(np.concatenate(t))) for t in tot])
+    t0, a0 = g.audit()
+    assert np.array_equal(t0, exp_t), t0 - exp_t
+    assert np.array_equal(a0, exp_a), a0 - exp_a
+    g.set_step_totals(True)
+    g.advance(1)
+    rows = g.step_totals()
+    assert np.array_equal(rows[0, :4], exp_t) and np.array_equal(rows[0, 4:], exp_a)
+
+
+def test_bounded_wait_gives_up_and_context_survives(V):
+    """Failure detection of the persistent schedule: a task waiting on a
+    completion mark that nothing sets gives up after its poll limit, the
+    kernel reports VLBM_ERR_TIMEOUT through its status word, and the CUDA
+    context stays usable (a run afterwards still matches the oracle)."""
+    st, ms, word = V.selftest_timeout()
+    assert st == 6, (st, ms, word)  # VLBM_ERR_TIMEOUT
+    assert word & 2
+    assert 20.0 < ms < 30000.0, ms  # waited, then returned
+    cs = I.pulse2l(steps=6)
+    g = V.Hierarchy.from_case(cs)
+    o = oracle_of(cs)
+    g.advance(cs.steps)
+    o.advance(cs.steps)
+    compare(o, g, cs.nlev)

@@ -95,7 +95,17 @@ typedef struct {
     int32_t nboxes;
     double tag_tol;            /* adaptive regrid: indicator tolerance */
     int32_t tag_buffer;        /* adaptive regrid: dilation (cells) */
+    int32_t tag_sensor;        /* adaptive regrid indicator: VLBM_SENSOR_* */
 } vlbm_config;
+
+/* Tagging indicators of the adaptive regrid (both on the composite state,
+ * covered cells holding the average of their children; neighbours off the
+ * level or beyond a non-periodic side take the cell's own value):
+ *   DENSITY  (rho_E - rho_W)^2 + (rho_N - rho_S)^2 > tol^2 (2 rho_C)^2
+ *   FLUX     the flux-jump estimate of Sec. 3.4 (Eq. amr-sigma),
+ *            s = max_k |dx (div Q)_k| / max_{x,alpha} |Q_{alpha,k}| > tol,
+ *            central differences, maxima over every cell of every level */
+enum { VLBM_SENSOR_DENSITY = 0, VLBM_SENSOR_FLUX = 1 };
 
 typedef struct {
     /* returns device memory of `bytes` usable on `stream`, or NULL */
@@ -146,8 +156,7 @@ vlbm_status vlbm_advance(vlbm_hier* h, int64_t coarse_steps);
 
 /* Regrid (Sec. 3.4, Fig. 2).  boxes != NULL: the new layout is the union of
  * the boxes (validated like vlbm_create_hierarchy).  boxes == NULL: the
- * layout is derived from the normalised density-gradient indicator
- * ((rho_E - rho_W)^2 + (rho_N - rho_S)^2 > tol^2 (2 rho_C)^2) with
+ * layout is derived from the indicator cfg->tag_sensor (VLBM_SENSOR_*) with
  * cfg->tag_tol and cfg->tag_buffer, rounded to blocks and grown so that every
  * level nests.  Cells leaving refinement take the merge of their children,
  * cells entering refinement are split (finest level first for merges,
@@ -225,11 +234,15 @@ typedef struct {
 
 vlbm_status vlbm_profile(vlbm_hier* h, int64_t coarse_steps, vlbm_kernel_time* out, int32_t cap, int32_t* n);
 
-/* Launch tuning of the sweep.  variant selects one compiled form of the
- * level sweep: which of the collision's additions and multiplications run
- * on the integer pipes through bit-exact binary64 routines (results are
- * identical bit for bit in every variant) and how many CTAs per SM the
- * kernel is built for; some variants apply only when 1 - 2 beta == -1.
+/* Launch tuning of the sweep.  variant (0 .. vlbm_num_variants() - 1)
+ * selects one compiled form of the level sweep: which of the collision's
+ * additions and multiplications run on the integer pipes through bit-exact
+ * binary64 routines, how many CTAs per SM the kernel is built for, and how
+ * the persistent kernel of schedule 1 organises its threads (64-thread
+ * groups per tile task; groups that prefetch the next task's populations
+ * into shared memory; or warps working alone on half-tile tasks).  Results
+ * are identical bit for bit in every variant; some variants apply only when
+ * 1 - 2 beta == -1.
  * schedule 0 issues one kernel launch per phase of the sub-cycle (level
  * sweeps, reflux closes); schedule 1 runs graph_steps coarse steps of every
  * phase in one persistent launch whose 8x8-tile tasks start as soon as the
@@ -348,10 +361,22 @@ vlbm_status vlbm_engine_create(size_t mem_budget, void* stream, vlbm_engine** ou
 vlbm_status vlbm_engine_admit(vlbm_engine* e, vlbm_hier* h, int64_t coarse_steps,
                               int32_t regrid_every, int32_t* slot);
 
-/* One coarse step of every resident.  finished_slots (capacity = the number
- * of residents) receives the slots whose step count is now met.
- * Errors: ERR_CUDA, ERR_NONPHYSICAL (the offending residents are listed in
- * finished_slots with a negative sign-encoded slot: -(slot+1)). */
+/* Advances every resident by the same number k of coarse steps, 1 <= k <=
+ * max_steps, as many as no resident reaches its step count or an adaptive
+ * resident its next regrid in between (adaptive residents regrid at the
+ * start of the call when one is due).  Static residents run on the
+ * persistent task kernel, adaptive ones on captured per-phase launches;
+ * each resident's result is the same as when it is advanced alone.
+ * Asynchronous unless a resident finished.  finished_slots (capacity = the
+ * largest slot + 1) receives the slots whose step count is now met; a
+ * finished resident whose state turned non-physical is poisoned (its
+ * handle then returns ERR_STATE, vlbm_last_error says why).  *steps = k
+ * (0 when nothing is resident).  Errors: ERR_ARG, ERR_CUDA, errors of a
+ * resident's regrid. */
+vlbm_status vlbm_engine_advance(vlbm_engine* e, int32_t max_steps, int32_t* finished_slots, int32_t* nfinished,
+                                int32_t* steps);
+
+/* vlbm_engine_advance with max_steps = 1. */
 vlbm_status vlbm_engine_step(vlbm_engine* e, int32_t* finished_slots, int32_t* nfinished);
 
 /* Removes a resident (its hierarchy returns to the caller, unchanged). */

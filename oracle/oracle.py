@@ -46,11 +46,12 @@ def lib():
         L.ora_advance.argtypes = [C.c_void_p, C.c_int]
         L.ora_regrid.argtypes = [C.c_void_p, C.POINTER(C.c_void_p)]
         L.ora_regrid.restype = C.c_int
-        L.ora_regrid_tagged.argtypes = [C.c_void_p, C.c_double, C.c_int, C.c_int, C.POINTER(C.c_void_p)]
+        L.ora_regrid_tagged.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_int, C.POINTER(C.c_void_p)]
         L.ora_regrid_tagged.restype = C.c_int
         L.ora_layout_from_tags.argtypes = [C.c_void_p, C.POINTER(C.c_void_p), C.c_int, C.c_int,
                                            C.POINTER(C.c_void_p)]
-        L.ora_tags.argtypes = [C.c_void_p, C.c_double, C.POINTER(C.c_void_p)]
+        L.ora_tags.argtypes = [C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_void_p)]
+        L.ora_flux_max.argtypes = [C.c_void_p, dp]
         L.ora_feq.argtypes = [C.c_double, C.c_double, dp, dp]
         L.ora_collide.argtypes = [C.c_double, C.c_double, C.c_double, dp, dp]
         L.ora_minmod.argtypes = [C.c_double, C.c_double]
@@ -175,19 +176,26 @@ class Hierarchy:
         if err:
             raise ValueError(f"oracle: layout not nested (code {err})")
 
-    def regrid_tagged(self, tol, buffer, block):
+    def regrid_tagged(self, tol, buffer, block, sensor=0):
+        """Tag-driven regrid; sensor 0 = normalised density gradient, 1 =
+        flux jump with max norm (Sec. 3.4)."""
         outs = [np.zeros(s, dtype=np.uint8) for s in self.shapes]
         arr = (C.c_void_p * self.nlev)(*[o.ctypes.data for o in outs])
-        err = lib().ora_regrid_tagged(self._h, tol, buffer, block, arr)
+        err = lib().ora_regrid_tagged(self._h, int(sensor), tol, buffer, block, arr)
         if err:
             raise ValueError(f"oracle: regrid failed (code {err})")
         return outs[: self.nlev - 1]
 
-    def tags(self, tol):
+    def tags(self, tol, sensor=0):
         outs = [np.zeros(s, dtype=np.uint8) for s in self.shapes]
         arr = (C.c_void_p * self.nlev)(*[o.ctypes.data for o in outs])
-        lib().ora_tags(self._h, tol, arr)
+        lib().ora_tags(self._h, int(sensor), tol, arr)
         return outs[: self.nlev - 1]
+
+    def flux_max(self):
+        q = (C.c_double * 4)()
+        lib().ora_flux_max(self._h, q)
+        return np.array(q[:])
 
     def layout_from_tags(self, tags, buffer, block):
         tg = [np.ascontiguousarray(t, dtype=np.uint8) for t in tags] + \

@@ -672,6 +672,80 @@ static void tag_level(const OHier* H, int l, double* const* comp, double tol2, u
         }
 }
 
+/* Flux-jump sensor of Sec. 3.4, Eq. amr-sigma: per field k the jump
+ * estimate s_k = dx (div Q)_k / max_{x,alpha} |Q_{alpha,k}|, combined with a
+ * max norm, s = max_k |s_k|; a cell is tagged when s > tol.  With central
+ * differences (div Q)_k = ((Qx_k(E) - Qx_k(W)) + (Qy_k(N) - Qy_k(S))) / (2 dx),
+ * so dx cancels and s_k > tol reads |g_k| > (2 tol) qmax_k with
+ * g_k = (Qx_k(E) - Qx_k(W)) + (Qy_k(N) - Qy_k(S)) (no division; a field
+ * whose flux vanishes everywhere never tags).  Q is the Euler flux of the
+ * composite state; qmax_k runs over every cell of every level (covered
+ * cells holding the average of their children); neighbours off the level or
+ * beyond a non-periodic side take the cell's own flux. */
+static void comp_flux(const OHier* H, const OLevel* L, const double* a, size_t c, double Qx[4], double Qy[4]) {
+    double f[16], W[4];
+    gather(L, a, c, f);
+    moments(f, W);
+    euler_flux(H->gamma - 1.0, W, Qx, Qy);
+}
+
+static void flux_max(const OHier* H, double* const* comp, double qmax[4]) {
+    for (int k = 0; k < 4; k++) qmax[k] = 0.0;
+    for (int l = 0; l < H->nlev; l++) {
+        const OLevel* L = &H->lev[l];
+        for (size_t c = 0; c < L->n; c++) {
+            if (!L->in[c]) continue;
+            double Qx[4], Qy[4];
+            comp_flux(H, L, comp[l], c, Qx, Qy);
+            for (int k = 0; k < 4; k++) {
+                if (fabs(Qx[k]) > qmax[k]) qmax[k] = fabs(Qx[k]);
+                if (fabs(Qy[k]) > qmax[k]) qmax[k] = fabs(Qy[k]);
+            }
+        }
+    }
+}
+
+static void tag_level_flux(const OHier* H, int l, double* const* comp, const double qmax[4], double tol,
+                           uint8_t* tag) {
+    const OLevel* L = &H->lev[l];
+    for (int y = 0; y < L->ny; y++)
+        for (int x = 0; x < L->nx; x++) {
+            size_t c = cidx(L, x, y);
+            tag[c] = 0;
+            if (!L->in[c]) continue;
+            double Qx[4][4], Qy[4][4], Qcx[4], Qcy[4];
+            comp_flux(H, L, comp[l], c, Qcx, Qcy);
+            for (int d = 0; d < 4; d++) {
+                int xx = x + CX[d], yy = y + CY[d];
+                if (!resolve(H, L, &xx, &yy) && L->in[cidx(L, xx, yy)]) {
+                    comp_flux(H, L, comp[l], cidx(L, xx, yy), Qx[d], Qy[d]);
+                } else {
+                    for (int k = 0; k < 4; k++) {
+                        Qx[d][k] = Qcx[k];
+                        Qy[d][k] = Qcy[k];
+                    }
+                }
+            }
+            int t = 0;
+            for (int k = 0; k < 4; k++) {
+                double g = (Qx[0][k] - Qx[1][k]) + (Qy[2][k] - Qy[3][k]);
+                if (fabs(g) > (2.0 * tol) * qmax[k]) t = 1;
+            }
+            tag[c] = (uint8_t)t;
+        }
+}
+
+/* The tags of every refinable level: sensor 0 = normalised density
+ * gradient, 1 = flux jump (max norm). */
+static void tag_all(const OHier* H, double* const* comp, int sensor, double tol, uint8_t* const* tags) {
+    double qmax[4];
+    if (sensor == 1) flux_max(H, comp, qmax);
+    for (int l = 0; l <= H->nlev - 2; l++) {
+        if (sensor == 1) tag_level_flux(H, l, comp, qmax, tol, tags[l]);
+        else tag_level(H, l, comp, tol * tol, tags[l]);
+    }
+}
+
 /* Regrid layout.  tags[l] (l <= nlev-2) are per-cell tags on level l.  From
  * the finest refinable level down: dilate the tags by `buffer` cells (square
  * neighbourhood), add the parents of the 8-neighbourhood of the next finer
@@ -810,17 +884,16 @@ int ora_regrid(void* h, uint8_t* const* newref) {
 /* Tag-driven regrid: indicator, dilation, block rounding, nesting, then the
  * conservative merge/split.  Writes the chosen layout to newref_out when it
  * is not NULL.  Returns 0 or an error. */
-int ora_regrid_tagged(void* h, double tol, int buffer, int block, uint8_t** newref_out) {
+int ora_regrid_tagged(void* h, int sensor, double tol, int buffer, int block, uint8_t** newref_out) {
     OHier* H = (OHier*)h;
     double** comp = composite(H);
     uint8_t* tags[ORA_MAXLEV];
     uint8_t* newref[ORA_MAXLEV];
-    double tol2 = tol * tol;
     for (int l = 0; l < H->nlev; l++) {
         tags[l] = (uint8_t*)calloc(H->lev[l].n, 1);
         newref[l] = (uint8_t*)calloc(H->lev[l].n, 1);
-        if (l <= H->nlev - 2) tag_level(H, l, comp, tol2, tags[l]);
     }
+    tag_all(H, comp, sensor, tol, tags);
     layout_from_tags(H, tags, buffer, block, newref);
     int err = regrid_to(H, newref, comp);
     if (newref_out)
@@ -836,9 +909,17 @@ void ora_layout_from_tags(void* h, uint8_t* const* tags, int buffer, int block, 
 }
 
 /* Exposes the indicator alone on the current composite state. */
-void ora_tags(void* h, double tol, uint8_t** tags) {
+void ora_tags(void* h, int sensor, double tol, uint8_t** tags) {
     OHier* H = (OHier*)h;
     double** comp = composite(H);
-    for (int l = 0; l <= H->nlev - 2; l++) tag_level(H, l, comp, tol * tol, tags[l]);
+    tag_all(H, comp, sensor, tol, tags);
+    free_comp(H, comp);
+}
+
+/* The flux maxima qmax_k of the flux-jump sensor on the composite state. */
+void ora_flux_max(void* h, double qmax[4]) {
+    OHier* H = (OHier*)h;
+    double** comp = composite(H);
+    flux_max(H, comp, qmax);
     free_comp(H, comp);
 }

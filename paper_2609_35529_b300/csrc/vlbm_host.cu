@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <functional>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -15,6 +16,7 @@
 #include "vlbm.h"
 #include "vlbm_dev.cuh"
 #include "vlbm_launch.h"
+#include "vlbm_tasks.h"
 
 using namespace vlbm;
 
@@ -64,6 +66,34 @@ void host_feq(double gamma, double c, const double W[4], double feq[16]) {
     }
 }
 
+// The library's own stream-ordered memory pool on the current device, which
+// keeps freed memory for reuse (release threshold: unlimited) instead of
+// returning it to the driver at every synchronisation -- hierarchies of
+// several GB and task lists come and go with every request and regrid.
+cudaMemPool_t library_pool() {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        unsigned long long keep = ~0ull;
+        cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        pools[dev] = p;
+    }
+    return pools[dev];
+}
+
 struct DevMem {
     const vlbm_allocator* alloc = nullptr;
     vlbm_allocator a{};
@@ -78,7 +108,8 @@ struct DevMem {
             p = a.alloc(n, (void*)s, a.ctx);
             if (!p) throw Fail{VLBM_ERR_OOM, "allocator returned NULL"};
         } else {
-            cudaError_t e = cudaMallocAsync(&p, n, s);
+            cudaMemPool_t pool = library_pool();
+            cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, n, pool, s) : cudaMallocAsync(&p, n, s);
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 throw Fail{VLBM_ERR_OOM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e)};
@@ -156,6 +187,7 @@ struct vlbm_hier {
     // scratch
     DArr<double> stage;     // W / f staging
     DArr<uint8_t> stage8;   // valid masks, tags
+    DArr<unsigned long long> qmax;  // flux-jump sensor: max |Q_k| (bit patterns)
     DArr<unsigned long long> partial;  // audit partial sums (exact, 24 words per block)
     DArr<double> tot;      // audit result
     DArr<Item> listbuf;    // item lists for regrid kernels
@@ -173,7 +205,7 @@ struct vlbm_hier {
     // cached task lists of this hierarchy alone: [0] one step, [1] G steps
     struct TaskList {
         std::vector<Task> t;
-        std::vector<int> d, key;
+        std::vector<int> d;
         int steps = -1;
         bool audit = false;
         // device copies (the hierarchy's memory): tasks, dependencies,
@@ -400,220 +432,6 @@ struct Batch {
     std::vector<uintptr_t> captured[2];
     std::vector<uintptr_t> launch_key(int which) const;
 
-    // Dependency tracking at tile granularity.  Tasks of one phase write
-    // disjoint cells (each destination slot has exactly one writer per
-    // phase), so writers of the same phase do not wait for one another; a
-    // write of a new phase waits for the previous phase's writers (WAW) and
-    // for everything that read the old content (WAR); a read waits for the
-    // writers of the phase that produced the content (RAW).
-    struct Res {
-        int phase = -1;
-        std::vector<int> writers, readers, prior;
-    };
-    struct Tracker {
-        // per level instance: 3 resources (buffer 0, buffer 1, flags) per
-        // tile, indexing a pool that holds only the resources touched since
-        // the last reset (the index maps persist between resets)
-        std::vector<std::vector<int>> idx;
-        std::vector<int> bx, by;
-        std::vector<Res> pool;  // [0, used) live; the rest keep their capacity
-        size_t used = 0;
-        std::vector<std::pair<int, size_t>> touched;
-        std::vector<int> cur;
-        void reset(const std::vector<LevelDev>& tab) {
-            bool same = idx.size() == tab.size();
-            for (size_t i = 0; same && i < tab.size(); i++)
-                same = bx[i] == (tab[i].nx + TILE - 1) / TILE && by[i] == (tab[i].ny + TILE - 1) / TILE;
-            if (same) {
-                for (const auto& t : touched) idx[t.first][t.second] = -1;
-            } else {
-                idx.assign(tab.size(), {});
-                bx.resize(tab.size());
-                by.resize(tab.size());
-                for (size_t i = 0; i < tab.size(); i++) {
-                    bx[i] = (tab[i].nx + TILE - 1) / TILE;
-                    by[i] = (tab[i].ny + TILE - 1) / TILE;
-                    idx[i].assign((size_t)3 * bx[i] * by[i], -1);
-                }
-            }
-            touched.clear();
-            used = 0;
-            cur.clear();
-        }
-        // valid until the next call (the pool may grow)
-        Res& at(int lid, int kind, int tx, int ty) {
-            const size_t k = ((size_t)kind * by[lid] + ty) * bx[lid] + tx;
-            int& i = idx[lid][k];
-            if (i < 0) {
-                i = (int)used++;
-                if (used > pool.size()) pool.emplace_back();
-                Res& x = pool[i];
-                x.phase = -1;
-                x.writers.clear();
-                x.readers.clear();
-                x.prior.clear();
-                touched.emplace_back(lid, k);
-            }
-            return pool[i];
-        }
-        void add(const std::vector<int>& v, int task) {
-            for (int q : v)
-                if (q != task) cur.push_back(q);
-        }
-        void read(int lid, int kind, int tx, int ty, int task) {
-            Res& x = at(lid, kind, tx, ty);
-            add(x.writers, task);
-            if (x.readers.empty() || x.readers.back() != task) x.readers.push_back(task);
-        }
-        void write(int lid, int kind, int tx, int ty, int task, int phase) {
-            Res& x = at(lid, kind, tx, ty);
-            if (x.phase != phase) {
-                x.prior.swap(x.writers);
-                x.prior.insert(x.prior.end(), x.readers.begin(), x.readers.end());
-                x.writers.clear();
-                x.readers.clear();
-                x.phase = phase;
-            }
-            add(x.prior, task);
-            if (x.writers.empty() || x.writers.back() != task) x.writers.push_back(task);
-        }
-    };
-    Tracker tracker;  // reused by every task-list build of this batch
-    int phase_id = 0;
-
-    // relative buffer ids: level 0 at step s reads (s & 1) and writes the
-    // other; level >= 1 at sub-step 1 reads 0 and writes 1, at 2 the reverse
-    static int src_of(int level, int kk, int step) { return level == 0 ? (step & 1) : (kk == 1 ? 0 : 1); }
-
-    void emit_level(const std::vector<LevelDev>& tab, const std::vector<std::pair<vlbm_hier*, int>>& mem, int l, int kk,
-                    int kkp, int step, Tracker& tr, std::vector<Task>& out, std::vector<int>& dl, bool first = false) {
-        auto wrap = [](int v, int n, bool per, bool& ok) {
-            if (v < 0 || v >= n) {
-                if (!per) { ok = false; return 0; }
-                v = (v % n + n) % n;
-            }
-            return v;
-        };
-        const int phase = phase_id++;
-        for (auto& m : mem) {
-            vlbm_hier* h = m.first;
-            if (l >= h->nlev) continue;
-            const int lid = m.second + l;
-            const LevelDev& L = tab[lid];
-            const Level& HL = h->lev[l];
-            const int bs = src_of(l, kk, step), bd = bs ^ 1;
-            for (const Item& it : HL.act) {
-                const int t = (int)out.size();
-                tr.cur.clear();
-                tr.read(lid, bs, it.tx, it.ty, t);
-                const int di[5] = {0, 1, -1, 0, 0}, dj[5] = {0, 0, 0, 1, -1};
-                for (int d = 0; d < 5; d++) {
-                    bool ok = true;
-                    const int tx = wrap(it.tx + di[d], tr.bx[lid], L.px, ok);
-                    const int ty = wrap(it.ty + dj[d], tr.by[lid], L.py, ok);
-                    if (ok) tr.write(lid, bd, tx, ty, t, phase);
-                }
-                if (l > 0 && HL.recon[(size_t)it.ty * HL.bx + it.tx]) {
-                    const int plid = L.parent;
-                    const LevelDev& P = tab[plid];
-                    const int pbs = src_of(l - 1, kkp, step), pbd = pbs ^ 1;
-                    const int c0x = it.tx * TILE / 2 - 1, c1x = it.tx * TILE / 2 + TILE / 2;
-                    const int c0y = it.ty * TILE / 2 - 1, c1y = it.ty * TILE / 2 + TILE / 2;
-                    int seen[16], ns = 0;
-                    for (int cy2 = c0y; cy2 <= c1y; cy2++)
-                        for (int cx2 = c0x; cx2 <= c1x; cx2++) {
-                            bool ok = true;
-                            const int xx = wrap(cx2, P.nx, P.px, ok), yy = wrap(cy2, P.ny, P.py, ok);
-                            if (!ok) continue;
-                            const int key = (yy / TILE) * tr.bx[plid] + xx / TILE;
-                            bool dup = false;
-                            for (int q = 0; q < ns; q++) dup = dup || seen[q] == key;
-                            if (dup || ns == 16) continue;
-                            seen[ns++] = key;
-                            tr.read(plid, pbs, xx / TILE, yy / TILE, t);
-                            tr.read(plid, pbd, xx / TILE, yy / TILE, t);
-                            tr.read(plid, 2, xx / TILE, yy / TILE, t);
-                        }
-                }
-                std::sort(tr.cur.begin(), tr.cur.end());
-                tr.cur.erase(std::unique(tr.cur.begin(), tr.cur.end()), tr.cur.end());
-                Task T{};
-                T.lid = lid;
-                T.tx = it.tx;
-                T.ty = it.ty;
-                T.kind = 0;
-                T.kk = (signed char)kk;
-                T.kkp = (signed char)kkp;
-                T.step = (signed char)step;
-                T.dep0 = (int)dl.size();
-                T.ndep = (int)tr.cur.size();
-                T.aslot = first ? -2 : -1;  // -2: audit task, slot assigned at merge
-                dl.insert(dl.end(), tr.cur.begin(), tr.cur.end());
-                out.push_back(T);
-            }
-        }
-    }
-
-    void emit_close(const std::vector<LevelDev>& tab, const std::vector<std::pair<vlbm_hier*, int>>& mem, int l, int kk,
-                    int step, Tracker& tr, std::vector<Task>& out, std::vector<int>& dl) {
-        const int phase = phase_id++;
-        for (auto& m : mem) {
-            vlbm_hier* h = m.first;
-            if (l + 1 >= h->nlev) continue;
-            const int lid = m.second + l, clid = lid + 1;
-            const int bd = src_of(l, kk, step) ^ 1;
-            for (const Item& it : h->lev[l].ring) {
-                const int t = (int)out.size();
-                tr.cur.clear();
-                for (int b = 0; b < 2; b++)
-                    for (int a = 0; a < 2; a++) {
-                        const int fx = 2 * it.tx + a, fy = 2 * it.ty + b;
-                        if (fx >= tr.bx[clid] || fy >= tr.by[clid]) continue;
-                        tr.read(clid, 0, fx, fy, t);
-                        tr.read(clid, 1, fx, fy, t);
-                    }
-                tr.write(lid, bd, it.tx, it.ty, t, phase);
-                tr.write(lid, 2, it.tx, it.ty, t, phase);
-                std::sort(tr.cur.begin(), tr.cur.end());
-                tr.cur.erase(std::unique(tr.cur.begin(), tr.cur.end()), tr.cur.end());
-                Task T{};
-                T.lid = lid;
-                T.tx = it.tx;
-                T.ty = it.ty;
-                T.kind = 1;
-                T.kk = (signed char)kk;
-                T.kkp = 0;
-                T.step = (signed char)step;
-                T.dep0 = (int)dl.size();
-                T.ndep = (int)tr.cur.size();
-                T.aslot = -1;
-                dl.insert(dl.end(), tr.cur.begin(), tr.cur.end());
-                out.push_back(T);
-            }
-        }
-    }
-
-    // The recursion always walks the schedule of VLBM_MAX_LEVELS levels so
-    // that phase ids (the merge keys) are the same for every hierarchy.
-    std::vector<int>* keys_out = nullptr;
-    // `first`: this level step is the first of its coarse step on its level,
-    // i.e. it starts from the state at the beginning of the coarse step (its
-    // sweep tasks carry the per-step conservation audit).
-    void emit_schedule(const std::vector<LevelDev>& tab, const std::vector<std::pair<vlbm_hier*, int>>& mem, int l,
-                       int kk, int kkp, int step, Tracker& tr, std::vector<Task>& out, std::vector<int>& dl,
-                       bool first = true) {
-        const size_t before = out.size();
-        emit_level(tab, mem, l, kk, kkp, step, tr, out, dl, first);
-        if (keys_out) keys_out->resize(out.size(), phase_id - 1);
-        if (l + 1 < VLBM_MAX_LEVELS) {
-            emit_schedule(tab, mem, l + 1, 1, kk, step, tr, out, dl, first);
-            emit_schedule(tab, mem, l + 1, 2, kk, step, tr, out, dl, false);
-            emit_close(tab, mem, l, kk, step, tr, out, dl);
-            if (keys_out) keys_out->resize(out.size(), phase_id - 1);
-        }
-        (void)before;
-    }
-
     // Task list of one hierarchy alone (local level indices), cached and
     // uploaded to the hierarchy's memory until its layout, its steps per
     // launch or its audit setting change.
@@ -671,18 +489,23 @@ void Batch::member_tasks(vlbm_hier* h, int which, int nsteps, bool aud) {
     vlbm_hier::TaskList& L = h->tl[which];
     if (L.steps == nsteps && L.audit == aud) return;
     const auto t0 = std::chrono::steady_clock::now();
-    std::vector<LevelDev> tab;
-    for (int l = 0; l < h->nlev; l++) tab.push_back(h->dev(l, l ? l - 1 : -1, l + 1 < h->nlev ? l + 1 : -1));
-    std::vector<std::pair<vlbm_hier*, int>> mm = {{h, 0}};
-    Tracker& tr = tracker;
-    tr.reset(tab);
-    phase_id = 0;
-    L.t.clear();
-    L.d.clear();
-    L.key.clear();
-    keys_out = &L.key;
-    for (int st = 0; st < nsteps; st++) emit_schedule(tab, mm, 0, 0, 0, st, tr, L.t, L.d);
-    keys_out = nullptr;
+    std::vector<TaskLevel> lv(h->nlev);
+    for (int l = 0; l < h->nlev; l++) {
+        const Level& HL = h->lev[l];
+        lv[l].nx = HL.nx;
+        lv[l].ny = HL.ny;
+        lv[l].bx = HL.bx;
+        lv[l].by = HL.by;
+        lv[l].px = h->cfg.bc[0] == VLBM_BC_PERIODIC;
+        lv[l].py = h->cfg.bc[2] == VLBM_BC_PERIODIC;
+        lv[l].act = &HL.act;
+        lv[l].ring = &HL.ring;
+        lv[l].recon = &HL.recon;
+    }
+    TaskLists tl;
+    build_tasks(lv, nsteps, tl);
+    L.t.swap(tl.t);
+    L.d.swap(tl.d);
     // audit slots: the audit tasks of step st are slots [seg[st], seg[st+1])
     std::vector<int> seg(nsteps + 1, 0);
     if (aud) {
@@ -927,38 +750,14 @@ void build_lists(vlbm_hier* h) {
     const bool px = h->cfg.bc[0] == VLBM_BC_PERIODIC, py = h->cfg.bc[2] == VLBM_BC_PERIODIC;
     for (int l = 0; l < h->nlev; l++) {
         Level& L = h->lev[l];
-        L.act.clear();
-        L.ring.clear();
-        L.cov.clear();
-        L.in.clear();
-        L.recon.assign((size_t)L.bx * L.by, 0);
-        L.active_cells = 0;
-        for (int jb = 0; jb < L.by; jb++)
-            for (int ib = 0; ib < L.bx; ib++) {
-                const size_t b = (size_t)jb * L.bx + ib;
-                if (!L.bin[b]) continue;
-                Item it{l, (unsigned short)ib, (unsigned short)jb};
-                L.in.push_back(it);
-                if (L.bcov[b]) {
-                    L.cov.push_back(it);
-                    continue;
-                }
-                L.act.push_back(it);
-                L.active_cells += (long long)(std::min(L.nx, ib * TILE + TILE) - ib * TILE) *
-                                  (std::min(L.ny, jb * TILE + TILE) - jb * TILE);
-                bool ring = false, rec = false;
-                const int di[4] = {1, -1, 0, 0}, dj[4] = {0, 0, 1, -1};
-                for (int d = 0; d < 4; d++) {
-                    int i2 = ib + di[d], j2 = jb + dj[d];
-                    if (i2 < 0 || i2 >= L.bx) { if (!px) continue; i2 = (i2 + L.bx) % L.bx; }
-                    if (j2 < 0 || j2 >= L.by) { if (!py) continue; j2 = (j2 + L.by) % L.by; }
-                    const size_t b2 = (size_t)j2 * L.bx + i2;
-                    ring = ring || (L.bin[b2] && L.bcov[b2]);
-                    rec = rec || !L.bin[b2];
-                }
-                if (ring) L.ring.push_back(it);
-                L.recon[b] = rec;
-            }
+        TileLists o;
+        tile_lists(l, L.nx, L.ny, L.bx, L.by, px, py, L.bin.data(), L.bcov.data(), o);
+        L.act.swap(o.act);
+        L.ring.swap(o.ring);
+        L.cov.swap(o.cov);
+        L.in.swap(o.in);
+        L.recon.swap(o.recon);
+        L.active_cells = o.active_cells;
     }
 }
 
@@ -1055,12 +854,17 @@ struct vlbm_engine {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     DevMem mem;
+    // static residents run on the persistent task kernel (their task lists
+    // are built once); adaptive residents, whose layouts change every few
+    // steps, on captured per-phase launches, which need no task lists
     Batch batch;
+    Batch phased;
     struct Res {
         vlbm_hier* h = nullptr;
         long long target = 0, done = 0, lups = 0;
         int regrid_every = 0;
         bool live = false;
+        bool adaptive() const { return regrid_every > 0 && h->cfg.tag_tol > 0; }
     };
     std::vector<Res> res;
     bool dirty = true;
@@ -1112,6 +916,7 @@ void destroy_levels(vlbm_hier* h) {
     h->words = nullptr;
     h->stage.release(h->mem);
     h->stage8.release(h->mem);
+    h->qmax.release(h->mem);
     h->partial.release(h->mem);
     h->tot.release(h->mem);
     h->listbuf.release(h->mem);
@@ -1588,6 +1393,8 @@ vlbm_status vlbm_regrid(vlbm_hier* h, const vlbm_box* boxes, int32_t nboxes) {
             h->times[VLBM_T_REGRID] += ms_since(t0);
         } else {
             if (!(h->cfg.tag_tol > 0.0) || h->cfg.tag_buffer < 0) throw Fail{VLBM_ERR_ARG, "no tagging parameters"};
+            if (h->cfg.tag_sensor != VLBM_SENSOR_DENSITY && h->cfg.tag_sensor != VLBM_SENSOR_FLUX)
+                throw Fail{VLBM_ERR_ARG, "unknown tagging sensor"};
             cudaStream_t s = h->stream;
             // average-down, then tag on every refinable level
             for (int l = h->nlev - 2; l >= 0; l--) {
@@ -1596,6 +1403,16 @@ vlbm_status vlbm_regrid(vlbm_hier* h, const vlbm_box* boxes, int32_t nboxes) {
             }
             std::vector<uint8_t> bflag[VLBM_MAX_LEVELS];
             const double tol2 = h->cfg.tag_tol * h->cfg.tag_tol;
+            const bool fluxs = h->cfg.tag_sensor == VLBM_SENSOR_FLUX;
+            if (fluxs) {
+                // the flux maxima over every cell of every level
+                h->qmax.ensure(h->mem, 4);
+                VCK(cudaMemsetAsync(h->qmax.p, 0, 4 * sizeof(unsigned long long), s));
+                for (int l = 0; l < h->nlev; l++) {
+                    h->listbuf.upload(h->mem, h->lev[l].in, s);
+                    VCK(launch_qmax(lvdev(h, l), h->listbuf.p, (int)h->listbuf.n, h->qmax.p, s));
+                }
+            }
             const int px = h->cfg.bc[0] == VLBM_BC_PERIODIC, py = h->cfg.bc[2] == VLBM_BC_PERIODIC;
             size_t nb = 0;
             for (int l = 0; l <= h->nlev - 2; l++) nb += (size_t)h->lev[l].bx * h->lev[l].by;
@@ -1606,7 +1423,11 @@ vlbm_status vlbm_regrid(vlbm_hier* h, const vlbm_box* boxes, int32_t nboxes) {
                 h->stage8.ensure(h->mem, (size_t)L.nx * L.ny);
                 VCK(cudaMemsetAsync(h->stage8.p, 0, (size_t)L.nx * L.ny, s));
                 h->listbuf.upload(h->mem, L.in, s);
-                VCK(launch_tag(lvdev(h, l), h->listbuf.p, (int)L.in.size(), tol2, h->stage8.p, s));
+                if (fluxs)
+                    VCK(launch_tag_flux(lvdev(h, l), h->listbuf.p, (int)L.in.size(), h->qmax.p, h->cfg.tag_tol,
+                                        h->stage8.p, s));
+                else
+                    VCK(launch_tag(lvdev(h, l), h->listbuf.p, (int)L.in.size(), tol2, h->stage8.p, s));
                 VCK(launch_blockflag(h->stage8.p, L.nx, L.ny, px, py, h->cfg.tag_buffer, h->bflag.p + off, s));
                 off += (size_t)L.bx * L.by;
             }
@@ -1724,6 +1545,8 @@ vlbm_status vlbm_engine_create(size_t mem_budget, void* stream, vlbm_engine** ou
     }
     e->mem.s = e->stream;
     e->batch.mem = &e->mem;
+    e->phased.mem = &e->mem;
+    e->phased.schedule_mode = 0;
     *out = e;
     return VLBM_OK;
 }
@@ -1788,13 +1611,15 @@ vlbm_status vlbm_engine_release(vlbm_engine* e, int32_t slot) {
     return VLBM_OK;
 }
 
-vlbm_status vlbm_engine_step(vlbm_engine* e, int32_t* finished, int32_t* nfinished) {
-    if (!e) return VLBM_ERR_ARG;
+vlbm_status vlbm_engine_advance(vlbm_engine* e, int32_t max_steps, int32_t* finished, int32_t* nfinished,
+                                int32_t* steps) {
+    if (!e || max_steps < 1) return VLBM_ERR_ARG;
     if (nfinished) *nfinished = 0;
+    if (steps) *steps = 0;
     try {
         // adaptive residents regrid on their own schedule (between steps)
         for (auto& r : e->res) {
-            if (!r.live || r.regrid_every <= 0 || !(r.h->cfg.tag_tol > 0)) continue;
+            if (!r.live || !r.adaptive()) continue;
             if (r.done > 0 && r.done % r.regrid_every == 0 && r.done < r.target) {
                 VCK(cudaStreamSynchronize(e->stream));
                 vlbm_hier* h = r.h;
@@ -1809,19 +1634,39 @@ vlbm_status vlbm_engine_step(vlbm_engine* e, int32_t* finished, int32_t* nfinish
         }
         if (e->dirty) {
             e->batch.members.clear();
+            e->phased.members.clear();
             for (auto& r : e->res)
-                if (r.live && r.done < r.target) e->batch.members.push_back(r.h);
+                if (r.live && r.done < r.target) (r.adaptive() ? e->phased : e->batch).members.push_back(r.h);
             if (!e->batch.members.empty()) e->batch.build(e->stream);
+            if (!e->phased.members.empty()) e->phased.build(e->stream);
             e->dirty = false;
         }
-        if (!e->batch.members.empty()) VCK(cudaGraphLaunch(e->batch.exec_for(0, e->stream), e->stream));
+        // as many steps as no resident finishes or regrids in between
+        long long k = max_steps;
+        bool any = false;
+        for (const auto& r : e->res) {
+            if (!r.live || r.done >= r.target) continue;
+            any = true;
+            k = std::min(k, r.target - r.done);
+            if (r.adaptive()) k = std::min<long long>(k, r.regrid_every - r.done % r.regrid_every);
+        }
+        if (!any) return VLBM_OK;
+        cudaGraphExec_t gs = e->batch.members.empty() ? nullptr : e->batch.exec_for(0, e->stream);
+        cudaGraphExec_t gp = e->phased.members.empty() ? nullptr : e->phased.exec_for(0, e->stream);
+        for (long long i = 0; i < k; i++) {
+            if (gs) VCK(cudaGraphLaunch(gs, e->stream));
+            if (gp) VCK(cudaGraphLaunch(gp, e->stream));
+        }
         int nf = 0;
         for (size_t i = 0; i < e->res.size(); i++) {
             auto& r = e->res[i];
             if (!r.live || r.done >= r.target) continue;
-            r.done++;
-            r.h->steps++;
-            for (int l = 0; l < r.h->nlev; l++) r.lups += r.h->lev[l].active_cells << l;
+            r.done += k;
+            r.h->steps += k;
+            r.h->layout_steps += k;
+            long long per = 0;
+            for (int l = 0; l < r.h->nlev; l++) per += r.h->lev[l].active_cells << l;
+            r.lups += per * k;
             if (r.done == r.target) {
                 if (finished) finished[nf] = (int)i;
                 nf++;
@@ -1829,9 +1674,10 @@ vlbm_status vlbm_engine_step(vlbm_engine* e, int32_t* finished, int32_t* nfinish
             }
         }
         if (nfinished) *nfinished = nf;
+        if (steps) *steps = (int32_t)k;
         if (nf) {
             // results of finished residents are read by the caller: make the
-            // step visible and check the residents for non-physical states
+            // steps visible and check the residents for non-physical states
             VCK(cudaStreamSynchronize(e->stream));
             for (size_t i = 0; i < e->res.size(); i++) {
                 auto& r = e->res[i];
@@ -1848,12 +1694,17 @@ vlbm_status vlbm_engine_step(vlbm_engine* e, int32_t* finished, int32_t* nfinish
     }
 }
 
+vlbm_status vlbm_engine_step(vlbm_engine* e, int32_t* finished, int32_t* nfinished) {
+    return vlbm_engine_advance(e, 1, finished, nfinished, nullptr);
+}
+
 void vlbm_engine_destroy(vlbm_engine* e) {
     if (!e) return;
     cudaStreamSynchronize(e->stream);
     for (auto& r : e->res)
         if (r.live && r.h) r.h->engine = nullptr;
     e->batch.release();
+    e->phased.release();
     cudaStreamSynchronize(e->stream);
     if (e->own_stream) cudaStreamDestroy(e->stream);
     delete e;

@@ -80,7 +80,7 @@ enum : int { EM_MOM = 1, EM_A = 2, EM_FLUX = 4, EM_OMF = 8 };
 // Launch-shape bit of a variant (no effect on the arithmetic): the
 // persistent task kernel prefetches the next task's populations into
 // shared memory (see task_kernel).
-enum : int { TK_PREFETCH = 256 };
+enum : int { TK_PREFETCH = 256, TK_HALF = 512 };
 
 template <bool E>
 __device__ __forceinline__ double xadd(double a, double b) {
@@ -543,6 +543,60 @@ task_kernel(const LevelDev* __restrict__ levs, const Segment* __restrict__ segs,
     if constexpr (PF) cp_async_wait_all();
 }
 
+// TK_HALF: the same schedule with every warp on its own -- a task (tile) is
+// two half-tasks of four rows, claimed as tickets 2 t and 2 t + 1 by any
+// two warps; each warp waits for the task's dependencies itself and
+// publishes its half by adding 1 to the task's mark, so a task of launch
+// epoch e is complete when its mark reaches 2 e.  No group barrier is left
+// in the loop.  Deadlock freedom is unchanged: the halves of every task a
+// half waits for were claimed before it.
+template <int P, int MINB>
+__global__ void __launch_bounds__(CTA_THREADS, MINB)
+task_kernel_half(const LevelDev* __restrict__ levs, const Segment* __restrict__ segs,
+                 const int* __restrict__ prefix, int* ctl) {
+    const int lane = threadIdx.x & 31;
+    const unsigned epoch = (unsigned)ctl[CTL_EPOCH];
+    const int total = ctl[CTL_TOTAL], nseg = ctl[CTL_NSEG];
+    const unsigned mark = 2u * epoch;
+    for (;;) {
+        int h = 0;
+        if (lane == 0) h = atomicAdd(&ctl[CTL_CLAIM], 1);
+        h = __shfl_sync(0xffffffffu, h, 0);
+        if (h >= 2 * total) break;
+        const int t = h >> 1, half = h & 1;
+        const int sg = find_segment(prefix, nseg, t);
+        const Segment S = segs[sg];
+        const int i = t - prefix[sg];
+        const Task T = S.tasks[i];
+        const LevelDev& L = levs[T.lid + S.lid_base];
+        for (int j = lane; j < T.ndep; j += 32) wait_done(S.done + S.deps[T.dep0 + j], mark, L.status);
+        __syncwarp();
+        const int cx = lane & 7, cy = half * 4 + (lane >> 3), lt = cy * 8 + cx;
+        if (T.kind == 0) {
+            if (S.aw && T.aslot >= 0) {
+                double W[4] = {0.0, 0.0, 0.0, 0.0};
+                sweep_cell<P, true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.kkp, T.step, W);
+                double* o = S.aw + (size_t)T.aslot * AUDIT_SLOT + lt;
+                for (int k = 0; k < 4; k++) o[k * 64] = W[k];
+            } else {
+                sweep_cell<P, true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.kkp, T.step);
+            }
+        } else {
+            close_cell<true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.step);
+        }
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence();
+            atomicAdd(S.done + i, 1u);
+            if (atomicAdd(&ctl[CTL_FIN], 1) == 2 * total - 1) {
+                if (ctl[CTL_FLIP])
+                    for (int m = 0; m < nseg; m++) *segs[m].par0 ^= 1;
+                ctl[CTL_EPOCH] = (int)(epoch + 1);
+            }
+        }
+    }
+}
+
 __global__ void end_step_kernel(int* const* par, int n) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) *par[t] ^= 1;
@@ -882,6 +936,92 @@ __global__ void tag_kernel(LevelDev L, const Item* __restrict__ items, int nitem
     }
 }
 
+// Moments of the composite state at cell c.
+__device__ __forceinline__ void comp_W(const LevelDev& L, long long c, double W[4]) {
+    const double* s = composite_src(L, L.flags[c]);
+    for (int k = 0; k < 4; k++)
+        W[k] = (s[(0 + k) * L.plane + c] + s[(4 + k) * L.plane + c]) +
+               (s[(8 + k) * L.plane + c] + s[(12 + k) * L.plane + c]);
+}
+
+// Flux-jump sensor of Sec. 3.4, Eq. amr-sigma, first pass: the maxima
+// qmax_k = max |Q_{alpha,k}| over the composite cells of the listed tiles,
+// merged into qmax[k] as bit patterns (non-negative binary64 values order
+// like their bits).
+__global__ void qmax_kernel(LevelDev L, const Item* __restrict__ items, int nitems,
+                            unsigned long long* __restrict__ qmax) {
+    const int sub = threadIdx.x >> 6, cx = threadIdx.x & 7, cy = (threadIdx.x >> 3) & 7;
+    unsigned long long m[4] = {0ull, 0ull, 0ull, 0ull};
+    for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
+        const Item w = items[it];
+        const int x = w.tx * TILE + cx, y = w.ty * TILE + cy;
+        if (x >= L.nx || y >= L.ny) continue;
+        const long long c = (long long)y * L.pitch + x;
+        if (!(L.flags[c] & F_IN)) continue;
+        double W[4], Qx[4], Qy[4], p;
+        comp_W(L, c, W);
+        euler_flux(L.gm1, W, Qx, Qy, p);
+        for (int k = 0; k < 4; k++) {
+            const unsigned long long a = (unsigned long long)__double_as_longlong(fabs(Qx[k]));
+            const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(Qy[k]));
+            m[k] = max(m[k], max(a, b));
+        }
+    }
+    for (int k = 0; k < 4; k++) {
+        unsigned long long v = m[k];
+        for (int off = 16; off > 0; off >>= 1) v = max(v, __shfl_down_sync(0xffffffffu, v, off));
+        if ((threadIdx.x & 31) == 0 && v) atomicMax(qmax + k, v);
+    }
+}
+
+// Second pass: a cell is tagged when s = max_k |s_k| > tol with
+// s_k = dx (div Q)_k / qmax_k, i.e. when |g_k| > (2 tol) qmax_k for some k,
+// g_k = (Qx_k(E) - Qx_k(W)) + (Qy_k(N) - Qy_k(S)) (central differences;
+// neighbours off the level or beyond a non-periodic side take the cell's
+// own flux).
+__global__ void tag_flux_kernel(LevelDev L, const Item* __restrict__ items, int nitems,
+                                const unsigned long long* __restrict__ qmax, double tol,
+                                uint8_t* __restrict__ tags) {
+    const int sub = threadIdx.x >> 6, cx = threadIdx.x & 7, cy = (threadIdx.x >> 3) & 7;
+    for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
+        const Item w = items[it];
+        const int x = w.tx * TILE + cx, y = w.ty * TILE + cy;
+        if (x >= L.nx || y >= L.ny) continue;
+        const long long c = (long long)y * L.pitch + x;
+        if (!(L.flags[c] & F_IN)) continue;
+        double W[4], Qcx[4], Qcy[4], p;
+        comp_W(L, c, W);
+        euler_flux(L.gm1, W, Qcx, Qcy, p);
+        double Qx[4][4], Qy[4][4];
+        for (int d = 0; d < 4; d++) {
+            int xx = x + kCX[d], yy = y + kCY[d];
+            bool ok = true;
+            if (xx < 0) { if (L.px) xx += L.nx; else ok = false; }
+            if (xx >= L.nx) { if (L.px) xx -= L.nx; else ok = false; }
+            if (yy < 0) { if (L.py) yy += L.ny; else ok = false; }
+            if (yy >= L.ny) { if (L.py) yy -= L.ny; else ok = false; }
+            const long long cn = (long long)yy * L.pitch + xx;
+            if (ok && (L.flags[cn] & F_IN)) {
+                double Wn[4];
+                comp_W(L, cn, Wn);
+                euler_flux(L.gm1, Wn, Qx[d], Qy[d], p);
+            } else {
+                for (int k = 0; k < 4; k++) {
+                    Qx[d][k] = Qcx[k];
+                    Qy[d][k] = Qcy[k];
+                }
+            }
+        }
+        bool t = false;
+        for (int k = 0; k < 4; k++) {
+            const double g = (Qx[0][k] - Qx[1][k]) + (Qy[2][k] - Qy[3][k]);
+            const double lim = (2.0 * tol) * __longlong_as_double((long long)qmax[k]);
+            t = t || fabs(g) > lim;
+        }
+        tags[(long long)y * L.nx + x] = t;
+    }
+}
+
 // A block (8 x 8 cells) is flagged when any tagged cell lies within
 // `buffer` cells (square neighbourhood) of it.
 __global__ void blockflag_kernel(const uint8_t* __restrict__ tags, int nx, int ny, int px, int py, int buffer,
@@ -1035,9 +1175,9 @@ static inline int flat_grid(long long n) {
     X(0, 0, 2) X(1, 0, 3) X(2, EM_MOM, 2) X(3, EM_MOM | EM_A, 2) \
     X(4, EM_MOM | EM_A | EM_FLUX, 2) X(5, EM_FLUX, 2) X(6, EM_MOM | EM_A | EM_FLUX | EM_OMF, 2) \
     X(7, EM_MOM | EM_A | EM_OMF, 2) X(8, EM_MOM | EM_A | EM_FLUX, 3) X(9, EM_MOM | EM_A | EM_FLUX | EM_OMF, 3) \
-    X(10, 0, 4) X(11, TK_PREFETCH, 3) X(12, TK_PREFETCH, 2)
+    X(10, 0, 4) X(11, TK_PREFETCH, 3) X(12, TK_PREFETCH, 2) X(13, TK_HALF, 3) X(14, TK_HALF, 2)
 
-int sweep_variants() { return 13; }
+int sweep_variants() { return 15; }
 
 // variant -> whether it needs 1 - 2 beta == -1
 bool sweep_variant_needs_om_minus1(int v) {
@@ -1062,6 +1202,33 @@ cudaError_t launch_sweep(const LevelDev* levs, const Item* items, int n, int kk,
     return cudaGetLastError();
 }
 
+// Resident CTAs per SM of one task-kernel variant (sets its shared-memory
+// attributes first), and its launch.
+template <int P, int B>
+int task_variant_per_sm() {
+    int per = 0;
+    if constexpr ((P & TK_HALF) != 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, task_kernel_half<P, B>, CTA_THREADS, 0);
+    } else if constexpr ((P & TK_PREFETCH) != 0) {
+        cudaFuncSetAttribute(task_kernel<P, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, TK_SMEM);
+        cudaFuncSetAttribute(task_kernel<P, B>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, task_kernel<P, B>, CTA_THREADS, TK_SMEM);
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, task_kernel<P, B>, CTA_THREADS, 0);
+    }
+    return per;
+}
+
+template <int P, int B>
+void task_variant_launch(int g, const LevelDev* levs, const Segment* segs, const int* prefix, int* ctl,
+                         cudaStream_t s) {
+    if constexpr ((P & TK_HALF) != 0)
+        task_kernel_half<P, B><<<g, CTA_THREADS, 0, s>>>(levs, segs, prefix, ctl);
+    else
+        task_kernel<P, B><<<g, CTA_THREADS, (P & TK_PREFETCH) ? TK_SMEM : 0, s>>>(levs, segs, prefix, ctl);
+}
+
 int task_kernel_ctas(int variant) {
     static int cache[16] = {0};
     if (variant < 0 || variant >= 16) return 0;
@@ -1070,16 +1237,7 @@ int task_kernel_ctas(int variant) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     switch (variant) {
-#define X(id, P, B)                                                                                        \
-    case id:                                                                                               \
-        if ((P) & TK_PREFETCH) {                                                                           \
-            cudaFuncSetAttribute(task_kernel<P, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, TK_SMEM); \
-            cudaFuncSetAttribute(task_kernel<P, B>, cudaFuncAttributePreferredSharedMemoryCarveout,        \
-                                 (int)cudaSharedmemCarveoutMaxShared);                                     \
-        }                                                                                                  \
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, task_kernel<P, B>, CTA_THREADS,                \
-                                                      ((P) & TK_PREFETCH) ? TK_SMEM : 0);                  \
-        break;
+#define X(id, P, B) case id: per = task_variant_per_sm<P, B>(); break;
         VLBM_SWEEP_VARIANTS(X)
 #undef X
     }
@@ -1092,10 +1250,7 @@ cudaError_t launch_tasks(const LevelDev* levs, const Segment* segs, const int* p
     const int full = task_kernel_ctas(variant);  // also sets the kernel's shared-memory attributes
     const int g = ctas > 0 ? std::min(ctas, full) : full;
     switch (variant) {
-#define X(id, P, B)                                                                                      \
-    case id:                                                                                             \
-        task_kernel<P, B><<<g, CTA_THREADS, ((P) & TK_PREFETCH) ? TK_SMEM : 0, s>>>(levs, segs, prefix, ctl); \
-        break;
+#define X(id, P, B) case id: task_variant_launch<P, B>(g, levs, segs, prefix, ctl, s); break;
         VLBM_SWEEP_VARIANTS(X)
 #undef X
         default: return cudaErrorInvalidValue;
@@ -1163,6 +1318,19 @@ cudaError_t launch_avgdown(const LevelDev& C, const LevelDev& F, const Item* ite
 cudaError_t launch_tag(const LevelDev& L, const Item* items, int n, double tol2, uint8_t* tags, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     tag_kernel<<<tile_grid(n, 0), CTA_THREADS, 0, s>>>(L, items, n, tol2, tags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_qmax(const LevelDev& L, const Item* items, int n, unsigned long long* qmax, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    qmax_kernel<<<tile_grid(n, 0), CTA_THREADS, 0, s>>>(L, items, n, qmax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tag_flux(const LevelDev& L, const Item* items, int n, const unsigned long long* qmax, double tol,
+                            uint8_t* tags, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    tag_flux_kernel<<<tile_grid(n, 0), CTA_THREADS, 0, s>>>(L, items, n, qmax, tol, tags);
     return cudaGetLastError();
 }
 

@@ -28,6 +28,9 @@ cudaError_t launch_audit(const LevelDev* levs, const Item* items, int n, unsigne
                          cudaStream_t s);
 cudaError_t launch_avgdown(const LevelDev& C, const LevelDev& F, const Item* items, int n, cudaStream_t s);
 cudaError_t launch_tag(const LevelDev& L, const Item* items, int n, double tol2, uint8_t* tags, cudaStream_t s);
+cudaError_t launch_qmax(const LevelDev& L, const Item* items, int n, unsigned long long* qmax, cudaStream_t s);
+cudaError_t launch_tag_flux(const LevelDev& L, const Item* items, int n, const unsigned long long* qmax, double tol,
+                            uint8_t* tags, cudaStream_t s);
 cudaError_t launch_blockflag(const uint8_t* tags, int nx, int ny, int px, int py, int buffer, uint8_t* out,
                              cudaStream_t s);
 cudaError_t launch_merge(const LevelDev& L, const Item* items, int n, cudaStream_t s);

@@ -2,9 +2,11 @@
 
 Requests (2-D Riemann quadrant problems or isentropic vortices of different
 sizes and refinement layouts) arrive by a seeded Poisson process.  The loop
-admits arrived requests while the engine's device-memory budget allows,
-advances every resident request by one coarse step per engine step (one
-CUDA-graph launch per step for the whole batch), and returns each result to
+admits arrived requests while the engine's device-memory budget allows
+(setting each one up on its own stream, overlapping the queued work), lets
+the engine advance every resident request by up to 16 coarse steps per call
+(each step: one persistent-kernel launch for the static residents, one graph
+of per-phase launches for the adaptive ones), and returns each result to
 the host as soon as its step count is met; freed memory admits the next
 requests.  The same arrival trace can be served one request at a time
 (each request alone on the GPU, its own graph launches) for comparison.
@@ -120,6 +122,10 @@ def _start(r, stream):
     h = V.Hierarchy(cs.nx0, cs.ny0, cs.nlev, cs.bc, cs.gamma, cs.c, cs.beta, dx0=cs.dx0,
                     tag_tol=(cs.amr or {}).get("tol", 0.0), tag_buffer=(cs.amr or {}).get("buffer", 0),
                     stream=stream)
+    # auto schedule: a request advanced alone takes per-phase launches while
+    # its layout is young (adaptive requests regrid every 4 steps) and the
+    # persistent task kernel once a layout has lived long enough
+    h.set_tuning(schedule=2)
     h.set_state(0, cs.W[0])
     if r.adaptive:
         for _ in range(cs.nlev - 1):
@@ -214,11 +220,14 @@ def main(argv=None):
     ap.add_argument("--oracle-sample", type=int, default=32)
     ap.add_argument("--nmax", type=int, default=1024)
     ap.add_argument("--verbose", action="store_true")
+    ap.add_argument("--capacity-one", action="store_true",
+                    help="also measure the one-at-a-time capacity (whole trace offered at t = 0)")
     args = ap.parse_args(argv)
     import sys
     log = (lambda *a: print(*a, file=sys.stderr, flush=True)) if args.verbose else (lambda *a: None)
     import torch
     stream = torch.cuda.Stream()
+    setup = torch.cuda.Stream()
     t0 = time.perf_counter()
     reqs = make_requests(args.requests, args.seed, nmax=args.nmax)
     total = sum(r.lups for r in reqs)
@@ -227,13 +236,18 @@ def main(argv=None):
     # capacity: the whole trace offered at once (all arrivals at t = 0)
     for r in reqs:
         r.arrival = 0.0
-    _, cap_mlups, cap_wall = serve_batched(reqs, budget, stream=stream)
-    log(f"capacity: {cap_mlups:.1f} MLUPS, {cap_wall:.1f} s")
+    _, cap_mlups, cap_wall = serve_batched(reqs, budget, stream=stream, setup_stream=setup)
+    log(f"capacity: {cap_mlups:.1f} MLUPS, {cap_wall:.1f} s, {serve_batched.breakdown}")
+    cap1 = None
+    if args.capacity_one:
+        _, cap1, cap1_wall = serve_one_at_a_time(reqs, stream=stream)
+        log(f"capacity one at a time: {cap1:.1f} MLUPS, {cap1_wall:.1f} s")
     rate = args.load * len(reqs) / cap_wall
     schedule(reqs, rate, args.seed)
     sample = set(r.rid for r in sorted(reqs, key=lambda r: r.lups)[: args.oracle_sample])
-    tts_b, ml_b, wall_b = serve_batched(reqs, budget, stream, sample)
-    log(f"batched: {ml_b:.1f} MLUPS, {wall_b:.1f} s")
+    tts_b, ml_b, wall_b = serve_batched(reqs, budget, stream, sample, setup_stream=setup)
+    breakdown = serve_batched.breakdown
+    log(f"batched: {ml_b:.1f} MLUPS, {wall_b:.1f} s, {breakdown}")
     worst = 0.0
     for r in reqs:
         if r.rid in sample:
@@ -243,9 +257,10 @@ def main(argv=None):
     tts_1, ml_1, wall_1 = serve_one_at_a_time(reqs, stream=stream)
     log(f"one at a time: {ml_1:.1f} MLUPS, {wall_1:.1f} s")
     out = {"requests": len(reqs), "total_lups": total, "capacity_mlups": round(cap_mlups, 1),
+           "capacity_one_at_a_time_mlups": round(cap1, 1) if cap1 else None,
            "rate_per_s": round(rate, 3), "load": args.load,
            "batched": {"mlups": round(ml_b, 1), "p50_s": float(np.percentile(tts_b, 50)),
-                       "p99_s": float(np.percentile(tts_b, 99)), "wall_s": wall_b},
+                       "p99_s": float(np.percentile(tts_b, 99)), "wall_s": wall_b, "breakdown": breakdown},
            "one_at_a_time": {"mlups": round(ml_1, 1), "p50_s": float(np.percentile(tts_1, 50)),
                              "p99_s": float(np.percentile(tts_1, 99)), "wall_s": wall_1},
            "oracle_sample": len(sample), "oracle_worst_rel_err": worst}
@@ -253,10 +268,17 @@ def main(argv=None):
     return out
 
 
-def serve_batched(reqs, budget, stream=None, keep_ids=()):
-    """Continuous batching over the engine.  Returns per-request
-    time-to-solution (s), the aggregate MLUPS and the wall time; the final
-    populations of the requests in keep_ids are kept in `result`."""
+# coarse steps queued per engine call: the GPU works through them while the
+# host admits the requests that arrived meanwhile
+MAX_STEPS = 16
+
+
+def serve_batched(reqs, budget, stream=None, keep_ids=(), setup_stream=None):
+    """Continuous batching over the engine.  New requests are set up on their
+    own stream (`setup_stream`) so that their set-up overlaps the engine's
+    queued steps.  Returns per-request time-to-solution (s), the aggregate
+    MLUPS and the wall time; the final populations of the requests in
+    keep_ids are kept in `result`."""
     eng = V.Engine(budget, stream=stream)
     pending = sorted(reqs, key=lambda r: r.arrival)
     for r in reqs:
@@ -266,14 +288,18 @@ def serve_batched(reqs, budget, stream=None, keep_ids=()):
     nxt = 0
     t0 = time.perf_counter()
     total_lups = 0
+    spent = {"start_s": 0.0, "step_s": 0.0, "finish_s": 0.0}  # host wall time by part of the loop
+    host_ms = {}  # library host time (vlbm_host_times) summed over the requests
     while nxt < len(pending) or live:
         now = time.perf_counter() - t0
         while nxt < len(pending) and pending[nxt].arrival <= now:
             r = pending[nxt]
             if live and used + r.bytes_est > budget:
                 break
-            h, cs = _start(r, stream)
+            ta = time.perf_counter()
+            h, cs = _start(r, setup_stream if setup_stream is not None else stream)
             slot = eng.admit(h, cs.steps, 4 if r.adaptive else 0)
+            spent["start_s"] += time.perf_counter() - ta
             if slot is None:
                 h.close()
                 break
@@ -284,7 +310,11 @@ def serve_batched(reqs, budget, stream=None, keep_ids=()):
             if nxt < len(pending):
                 time.sleep(max(0.0, min(0.002, pending[nxt].arrival - (time.perf_counter() - t0))))
             continue
-        for slot in eng.step():
+        ta = time.perf_counter()
+        done, _ = eng.advance(MAX_STEPS)
+        tb = time.perf_counter()
+        spent["step_s"] += tb - ta
+        for slot in done:
             r, h = live.pop(slot)
             r.lups_done = eng.slot_stats(slot)[1]
             W, act = h.get_conserved(0)
@@ -293,11 +323,15 @@ def serve_batched(reqs, budget, stream=None, keep_ids=()):
                 r.result = [h.get_populations(l) for l in range(h.nlev)]
             total_lups += r.lups_done
             eng.release(slot)
+            for k, v in h.host_times().items():
+                host_ms[k] = host_ms.get(k, 0.0) + v
             h.close()
             used -= r.bytes_est
+        spent["finish_s"] += time.perf_counter() - tb
     wall = time.perf_counter() - t0
     eng.close()
     tts = np.array([r.done_at - r.arrival for r in reqs])
+    serve_batched.breakdown = {"loop": spent, "library_host_ms": host_ms}
     return tts, total_lups / wall / 1e6, wall
 
 

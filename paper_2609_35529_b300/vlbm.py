@@ -39,7 +39,7 @@ class vlbm_config(C.Structure):
     _fields_ = [("nx0", C.c_int32), ("ny0", C.c_int32), ("dx0", C.c_double), ("max_levels", C.c_int32),
                 ("bc", C.c_int32 * 4), ("inflow_W", (C.c_double * 4) * 4), ("gamma", C.c_double),
                 ("c", C.c_double), ("beta", C.c_double), ("boxes", C.POINTER(vlbm_box)), ("nboxes", C.c_int32),
-                ("tag_tol", C.c_double), ("tag_buffer", C.c_int32)]
+                ("tag_tol", C.c_double), ("tag_buffer", C.c_int32), ("tag_sensor", C.c_int32)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -102,6 +102,7 @@ def lib():
         "vlbm_engine_create": [C.c_size_t, vp, C.POINTER(vp)],
         "vlbm_engine_admit": [vp, vp, i64, i32, C.POINTER(i32)],
         "vlbm_engine_step": [vp, C.POINTER(i32), C.POINTER(i32)],
+        "vlbm_engine_advance": [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)],
         "vlbm_engine_release": [vp, i32],
         "vlbm_engine_usage": [vp, C.POINTER(i32), C.POINTER(i64)],
         "vlbm_engine_slot_stats": [vp, i32, C.POINTER(i64), C.POINTER(i64)],
@@ -171,7 +172,7 @@ class Hierarchy:
     """A refined VLBM hierarchy on the GPU (vlbm_hier)."""
 
     def __init__(self, nx0, ny0, nlev, bc, gamma, c, beta, boxes=(), dx0=1.0, inflow=None, tag_tol=0.0,
-                 tag_buffer=0, stream=None, allocator=None):
+                 tag_buffer=0, stream=None, allocator=None, tag_sensor=0):
         L = lib()
         cfg = vlbm_config()
         cfg.nx0, cfg.ny0, cfg.dx0, cfg.max_levels = nx0, ny0, dx0, nlev
@@ -185,7 +186,7 @@ class Hierarchy:
         self._boxes = (vlbm_box * max(1, len(boxes)))(*[vlbm_box(*b) for b in boxes])
         cfg.boxes = self._boxes if boxes else None
         cfg.nboxes = len(boxes)
-        cfg.tag_tol, cfg.tag_buffer = tag_tol, tag_buffer
+        cfg.tag_tol, cfg.tag_buffer, cfg.tag_sensor = tag_tol, tag_buffer, int(tag_sensor)
         self._alloc = _TorchAllocator() if allocator == "torch" else None
         h = C.c_void_p()
         st = L.vlbm_create_hierarchy(C.byref(cfg), C.byref(self._alloc.struct) if self._alloc else None,
@@ -201,7 +202,8 @@ class Hierarchy:
         """Creates a hierarchy for an inputs.Case and loads its initial state."""
         h = cls(case.nx0, case.ny0, case.nlev, case.bc, case.gamma, case.c, case.beta, boxes=boxes or (),
                 dx0=case.dx0, inflow=case.inflow, tag_tol=(case.amr or {}).get("tol", 0.0),
-                tag_buffer=(case.amr or {}).get("buffer", 0), stream=stream, allocator=allocator)
+                tag_buffer=(case.amr or {}).get("buffer", 0), stream=stream, allocator=allocator,
+                tag_sensor=(case.amr or {}).get("sensor", 0))
         if refs and case.nlev > 1 and not boxes and any(r.any() for r in case.refs):
             h.regrid_masks(case.refs)
         for l in range(case.nlev):
@@ -392,8 +394,9 @@ def selftest_timeout():
 
 
 class Engine:
-    """Continuous-batching engine (vlbm_engine): one graph launch per coarse
-    step advances every resident hierarchy."""
+    """Continuous-batching engine (vlbm_engine): every coarse step advances
+    all resident hierarchies -- static ones in one persistent-kernel launch,
+    adaptive ones in one graph of per-phase launches."""
 
     def __init__(self, mem_budget=0, stream=None):
         e = C.c_void_p()
@@ -420,6 +423,17 @@ class Engine:
         if st != 0:
             raise VlbmError(st, "vlbm_engine_step")
         return [buf[i] for i in range(n.value)]
+
+    def advance(self, max_steps):
+        """Up to max_steps coarse steps of every resident (see
+        vlbm_engine_advance): (finished slots, steps taken)."""
+        buf = (C.c_int32 * max(1, self.cap))()
+        n = C.c_int32()
+        k = C.c_int32()
+        st = lib().vlbm_engine_advance(self._e, int(max_steps), buf, C.byref(n), C.byref(k))
+        if st != 0:
+            raise VlbmError(st, "vlbm_engine_advance")
+        return [buf[i] for i in range(n.value)], k.value
 
     def release(self, slot):
         st = lib().vlbm_engine_release(self._e, int(slot))

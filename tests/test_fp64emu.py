@@ -26,7 +26,7 @@ def test_emulated_binary64_is_bit_exact(V, seed):
     assert all(v == 0 for v in bad.values()), (bad, first)
 
 
-@pytest.mark.parametrize("variant", range(13))
+@pytest.mark.parametrize("variant", range(15))
 def test_every_sweep_variant_matches_oracle(V, variant):
     # beta = 1 so that every variant applies (1 - 2 beta = -1)
     refs = I.box_refs(48, 40, 3, [(0, 8, 8, 24, 24)])

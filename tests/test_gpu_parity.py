@@ -123,7 +123,8 @@ def test_two_level_pulse_full_run(V):
 
 
 @pytest.mark.parametrize("schedule,graph_steps,variant",
-                         [(1, 8, 1), (0, 8, 1), (1, 3, 1), (2, 4, 1), (1, 8, 10), (1, 8, 11), (1, 3, 12)])
+                         [(1, 8, 1), (0, 8, 1), (1, 3, 1), (2, 4, 1), (1, 8, 10), (1, 8, 11), (1, 3, 12),
+                          (1, 8, 13), (1, 3, 14)])
 def test_three_level_periodic_ragged(V, schedule, graph_steps, variant):
     """Three levels on a domain whose size is not a multiple of the tile
     (ragged last tile column/row), including a patch that wraps across the
@@ -131,7 +132,7 @@ def test_three_level_periodic_ragged(V, schedule, graph_steps, variant):
     kernel with an odd number of steps per launch, and auto switching from
     the first to the second after 7 steps, inside one advance call) and the
     launch-shape variants (4 CTAs/SM; shared-memory prefetch of the next
-    task at 3 and 2 CTAs/SM)."""
+    task at 3 and 2 CTAs/SM; warps on half-tile tasks at 3 and 2 CTAs/SM)."""
     nx0, ny0 = 52, 44
     refs = I.box_refs(nx0, ny0, 3, [(0, 8, 8, 24, 16), (0, 0, 32, 8, 8), (0, 48, 32, 4, 8)])
     refs[1][24:40, 24:56] = 1
@@ -256,6 +257,32 @@ def test_adaptive_shockbubble_small(V):
     assert info["active_cells"][1] > 0 and info["active_cells"][2] > 0
 
 
+def test_adaptive_shockbubble_flux_jump_sensor(V):
+    """The same adaptive run driven by the paper's flux-jump sensor (Sec. 3.4,
+    Eq. amr-sigma, tol 0.01): tags, layouts and populations match the oracle
+    through every regrid, totals are conserved across each regrid."""
+    cs = I.shockbubble(nx0=128, ny0=64, nlev=3)
+    cs.amr = dict(cs.amr, tol=0.01, sensor=1)
+    tol, buf, every = cs.amr["tol"], cs.amr["buffer"], cs.amr["every"]
+    g = V.Hierarchy.from_case(cs)
+    o = oracle_of(cs)
+    for _ in range(2):
+        g.regrid()
+        o.regrid_tagged(tol, buf, 8, sensor=1)
+    compare(o, g, 3)
+    for cycle in range(5):
+        g.advance(every)
+        o.advance(every)
+        t0, a0 = g.audit()
+        g.regrid()
+        o.regrid_tagged(tol, buf, 8, sensor=1)
+        t1, _ = g.audit()
+        assert drift(t0, t1, a0) < 1e-14
+        compare(o, g, 3)
+    info = g.info()
+    assert info["active_cells"][1] > 0 and info["active_cells"][2] > 0
+
+
 def test_engine_results_equal_alone_and_in_mix(V):
     cases = [I.pulse2l(steps=30), I.riemann3(N=64, nlev=3, steps=25),
              I.smooth_random(40, 32, 1, [], seed=5, amp=0.2, steps=35)]
@@ -273,6 +300,60 @@ def test_engine_results_equal_alone_and_in_mix(V):
         for s in e.step():
             done.add(s)
     for cs, h, a in zip(cases, hs, alone):
+        for l in range(cs.nlev):
+            gin, gref = h.layout(l)
+            act = (gin == 1) & (gref == 0)
+            assert np.array_equal(h.get_populations(l)[:, act], a[l][:, act])
+    for s in slots:
+        e.release(s)
+    e.close()
+
+
+@pytest.mark.parametrize("max_steps", [1, 5, 16])
+def test_engine_static_and_adaptive_residents_equal_alone(V, max_steps):
+    """Continuous batching with static residents (persistent task kernel)
+    and adaptive residents regridding every 4 of their own steps (per-phase
+    launches) admitted at different times: every result is bit-identical to
+    the same request advanced alone, whatever the number of steps per
+    engine call."""
+    def adaptive_case(steps):
+        return I.shockbubble(nx0=64, ny0=32, nlev=3, steps=steps)
+
+    specs = [(I.pulse2l(steps=30), 0, 0), (adaptive_case(22), 4, 0), (I.riemann3(N=64, nlev=3, steps=25), 0, 3),
+             (adaptive_case(13), 4, 7), (I.smooth_random(40, 32, 1, [], seed=5, amp=0.2, steps=9), 0, 11)]
+
+    def start(cs, every):
+        g = V.Hierarchy.from_case(cs)
+        if every:
+            for _ in range(cs.nlev - 1):
+                g.regrid()
+        return g
+
+    alone = []
+    for cs, every, _ in specs:
+        g = start(cs, every)
+        left = cs.steps
+        while left > 0:
+            n = min(left, every) if every else left
+            g.advance(n)
+            left -= n
+            if every and left > 0:
+                g.regrid()
+        alone.append([g.get_populations(l) for l in range(cs.nlev)])
+        g.close()
+    e = V.Engine()
+    hs, slots = [None] * len(specs), [None] * len(specs)
+    done, t = set(), 0
+    while len(done) < len(specs):
+        for i, (cs, every, at) in enumerate(specs):
+            if hs[i] is None and at <= t:
+                hs[i] = start(cs, every)
+                slots[i] = e.admit(hs[i], cs.steps, every)
+        fin, k = e.advance(max_steps)
+        assert 0 <= k <= max_steps
+        t += max(k, 1)  # nothing resident: let the clock reach the next admission
+        done.update(fin)
+    for (cs, _, _), h, a in zip(specs, hs, alone):
         for l in range(cs.nlev):
             gin, gref = h.layout(l)
             act = (gin == 1) & (gref == 0)

@@ -392,6 +392,73 @@ def test_adaptive_run_conserves_across_regrids():
     assert max(nref) > 0
 
 
+def flux_sensor_hierarchy(rho, u, v, p, periodic=True):
+    """Two-level oracle hierarchy (no refinement yet) holding the given
+    level-0 primitive fields."""
+    ny, nx = rho.shape
+    bc = (0, 0, 0, 0) if periodic else (1, 1, 1, 1)
+    h = O.Hierarchy(nx, ny, 2, 2, bc, 1.4, 10.0, 0.9, None)
+    h.set_layout(I.empty_refs(nx, ny, 2))
+    h.set_state(0, I.conserved(rho, u, v, p))
+    h.set_state(1, np.zeros((4, 2 * ny, 2 * nx)))
+    return h
+
+
+def test_flux_jump_sensor_tags_a_pressure_step_by_its_closed_form():
+    """Flux-jump sensor (Sec. 3.4): at rest, a pressure step from 1 to 2 makes
+    Q_x of the momentum field jump by 1 with max |Q| = 2, so the two columns
+    beside the step (and beside the periodic wrap) have s = 1 / (2 * 2) =
+    0.25: tagged for tol 0.24, untagged for tol 0.26; nothing else is."""
+    ny, nx = 16, 24
+    z = np.zeros((ny, nx))
+    p = np.ones((ny, nx))
+    p[:, 10:] = 2.0
+    h = flux_sensor_hierarchy(z + 1.0, z, z, p)
+    qmax = h.flux_max()
+    # at rest only the pressure terms survive: Q_x of rho u and Q_y of rho v
+    assert qmax[0] == 0.0 and qmax[3] == 0.0
+    assert abs(qmax[1] - 2.0) < 1e-14 and abs(qmax[2] - 2.0) < 1e-14
+    t = h.tags(0.24, sensor=1)[0]
+    want = np.zeros((ny, nx), dtype=np.uint8)
+    want[:, [9, 10, nx - 1, 0]] = 1
+    assert np.array_equal(t, want)
+    assert not h.tags(0.26, sensor=1)[0].any()
+
+
+def test_flux_jump_sensor_ignores_contacts_and_shear():
+    """A density jump at rest and uniform pressure (a contact) and a shear
+    layer u(y) carry no jump of div Q, so the flux-jump sensor tags neither,
+    while the density-gradient indicator does tag the contact."""
+    ny, nx = 16, 16
+    z = np.zeros((ny, nx))
+    rho = np.ones((ny, nx))
+    rho[:, 8:] = 3.0
+    h = flux_sensor_hierarchy(rho, z, z, z + 1.0)
+    assert not h.tags(1e-6, sensor=1)[0].any()
+    assert h.tags(0.02, sensor=0)[0].any()
+    u = np.where(np.arange(ny)[:, None] < 8, 0.5, -0.5) * np.ones((ny, nx))
+    h = flux_sensor_hierarchy(z + 1.0, u, z, z + 1.0)
+    assert not h.tags(1e-6, sensor=1)[0].any()
+
+
+def test_flux_jump_sensor_uses_the_max_norm_over_fields():
+    """A jump in one conserved field's flux is not diluted by the others: with
+    v jumping from 0 to 0.1 across a horizontal line, the mass flux rho v
+    jumps by its own maximum, so the rows beside the line have s_0 = 0.5
+    and tag at just below that tolerance, whatever the other fields do."""
+    ny, nx = 16, 16
+    z = np.zeros((ny, nx))
+    v = np.where(np.arange(ny)[:, None] < 8, 0.0, 0.1) * np.ones((ny, nx))
+    h = flux_sensor_hierarchy(z + 1.0, z, v, z + 1.0, periodic=False)
+    qmax = h.flux_max()
+    # rho field: Q_y = rho v jumps 0 -> 0.1 between rows 7 and 8; qmax_0 = 0.1,
+    # so s_0 = 0.1 / (2 * 0.1) = 0.5 there, whatever the other fields do
+    assert abs(qmax[0] - 0.1) < 1e-15
+    t = h.tags(0.49, sensor=1)[0]
+    assert t[7].all() and t[8].all()
+    assert not h.tags(0.51, sensor=1)[0][[7, 8]].any()
+
+
 # ----------------------------------------------------------------------
 # the paper's validation numbers
 # ----------------------------------------------------------------------

@@ -50,6 +50,14 @@ BYTES_PER_LUP = 256
 # IEEE division, which ncu counts as about 5 further FP64-pipe operations
 # (DFMA/DADD/DMUL thread-instructions per cell update in the sweep: 67.1)
 FP64_OPS_PER_LUP = 67
+# DRAM traffic of the task kernel per cell update: dram__bytes_read.sum +
+# dram__bytes_write.sum of two launches of 16 coarse steps (variant 1, audit
+# off, 512 MB L2 flush before each launch), ncu --nvtx capture of this bench's
+# roofline launches (profiles/task_kernel_vortex512.md): 3.025e9 B per
+# 11 534 336 cell updates.  Valid for the kernel as captured; to be measured
+# again whenever the kernel changes.
+TASK_KERNEL_DRAM_BYTES_PER_LUP = 262.3
+TRAFFIC_VARIANT = 1
 
 
 def peaks():
@@ -310,8 +318,12 @@ def main():
     sweep = [r for r in prof if r["kind"] == "sweep"]
     sw_ms = sum(r["ms"] for r in sweep)
     sw_cells = sum(r["cells"] for r in sweep)
+    traffic = None
+    if tune["schedule"] == 1 and tune["variant"] == TRAFFIC_VARIANT:
+        traffic = round(TASK_KERNEL_DRAM_BYTES_PER_LUP * cells)  # bytes per launch
     roof = {"bound": "alu", "achieved": round(achieved_tflops, 4), "peak": round(pk["fp64_tflops"], 4),
-            "unit": "TFLOP/s", "frac": round(achieved_tflops / pk["fp64_tflops"], 4), "traffic": None,
+            "unit": "TFLOP/s", "frac": round(achieved_tflops / pk["fp64_tflops"], 4), "traffic": traffic,
+            "traffic_unit": "bytes per launch (ncu capture scaled by cell updates)",
             "kernel": kernel, "avg_launch_ms": round(launch_ms, 5), "cells_per_launch": cells,
             "flops_per_lup": FLOPS_PER_LUP, "peak_basis": "2 FP64 FMA/clk/SM x 148 SMs x sm_max_mhz",
             "hbm": {"achieved": round(hbm_gbs, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",

@@ -26,7 +26,7 @@
 // since -- the plain definition, kept as the reference.  build_tasks derives
 // each task's dependencies on its own: the phase sequence is known, and which
 // tasks of a phase touch a given tile follows from the tile maps, so every
-// task is independent and the work is split across host threads.  It also
+// task is independent (and the work can be split across host threads).  It also
 // leaves out the write-after-write edges that a write-after-read edge
 // already implies (a reader waits for every writer it read from), so its
 // lists have the same transitive closure with fewer edges.
@@ -394,10 +394,13 @@ struct FastCtx {
 
 }  // namespace taskdetail
 
-// Host threads for the builder: the CPUs this process may actually use --
-// the smaller of the visible cores and a cgroup CPU quota (cgroup v2
-// cpu.max or v1 cfs quota), at most 8.  Oversubscribing a quota would stall
-// the whole process, not just the builder.
+// Host threads the builder may use: the CPUs this process may actually use
+// -- the smaller of the visible cores and a cgroup CPU quota (cgroup v2
+// cpu.max or v1 cfs quota), at most 8.  The library itself builds on one
+// thread (build_tasks' default): on hosts where threads are expensive (a
+// sandboxed container measured 42 ms on one thread and 165 ms on two for
+// the same list) more threads only cost; callers that know better pass a
+// count.
 inline int builder_threads() {
     static int cached = 0;
     if (cached) return cached;
@@ -423,7 +426,7 @@ inline int builder_threads() {
     return cached;
 }
 
-inline void build_tasks(const std::vector<TaskLevel>& lev, int nsteps, TaskLists& out, int threads = 0) {
+inline void build_tasks(const std::vector<TaskLevel>& lev, int nsteps, TaskLists& out, int threads = 1) {
     using namespace taskdetail;
     const int nlev = (int)lev.size();
     FastCtx X;

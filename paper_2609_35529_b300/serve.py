@@ -114,11 +114,57 @@ def schedule(reqs, rate, seed=20261202):
     return reqs
 
 
-def _start(r, stream):
-    """Creates the request's hierarchy: level-0 state from the closed form,
-    finer levels by the conservative split (Eqs. 26-27) of a regrid to the
-    request's static layout, or by tag-driven regrids when adaptive."""
-    cs = make_case(r)
+class Payloads:
+    """A request's payload -- its configuration and level-0 initial state --
+    is what a client would send with it.  A background thread prepares the
+    payloads of the trace in arrival order, at most `ahead` beyond the
+    oldest one not yet taken, so that building the closed-form states with
+    numpy stays out of the serving loop in both serving modes."""
+
+    def __init__(self, reqs, ahead=48):
+        import threading
+        self.order = sorted(reqs, key=lambda r: r.arrival)
+        self.ready = {}
+        self.taken = 0
+        self.cv = threading.Condition()
+        self.ahead = ahead
+        self.stop = False
+        self.th = threading.Thread(target=self._run, daemon=True)
+        self.th.start()
+
+    def _run(self):
+        for i, r in enumerate(self.order):
+            with self.cv:
+                while not self.stop and i >= self.taken + self.ahead:
+                    self.cv.wait()
+                if self.stop:
+                    return
+            cs = make_case(r)
+            with self.cv:
+                self.ready[r.rid] = cs
+                self.cv.notify_all()
+
+    def take(self, r):
+        with self.cv:
+            while r.rid not in self.ready:
+                self.cv.wait()
+            self.taken += 1
+            self.cv.notify_all()
+            return self.ready.pop(r.rid)
+
+    def close(self):
+        with self.cv:
+            self.stop = True
+            self.cv.notify_all()
+        self.th.join()
+
+
+def _start(r, stream, cs=None):
+    """Creates the request's hierarchy from its payload (the case; built here
+    when not given): level-0 state from the closed form, finer levels by the
+    conservative split (Eqs. 26-27) of a regrid to the request's static
+    layout, or by tag-driven regrids when adaptive."""
+    cs = cs if cs is not None else make_case(r)
     h = V.Hierarchy(cs.nx0, cs.ny0, cs.nlev, cs.bc, cs.gamma, cs.c, cs.beta, dx0=cs.dx0,
                     tag_tol=(cs.amr or {}).get("tol", 0.0), tag_buffer=(cs.amr or {}).get("buffer", 0),
                     stream=stream)
@@ -140,13 +186,14 @@ def serve_one_at_a_time(reqs, stream=None):
     pending = sorted(reqs, key=lambda r: r.arrival)
     for r in reqs:
         r.lups_done = 0
+    pay = Payloads(reqs)
     t0 = time.perf_counter()
     total_lups = 0
     for r in pending:
         now = time.perf_counter() - t0
         if r.arrival > now:
             time.sleep(r.arrival - now)
-        h, cs = _start(r, stream)
+        h, cs = _start(r, stream, pay.take(r))
         left = cs.steps
         every = 4 if r.adaptive else 0
         while left > 0:
@@ -161,6 +208,7 @@ def serve_one_at_a_time(reqs, stream=None):
         total_lups += r.lups_done
         h.close()
     wall = time.perf_counter() - t0
+    pay.close()
     tts = np.array([r.done_at - r.arrival for r in reqs])
     return tts, total_lups / wall / 1e6, wall
 
@@ -283,53 +331,64 @@ def serve_batched(reqs, budget, stream=None, keep_ids=(), setup_stream=None):
     pending = sorted(reqs, key=lambda r: r.arrival)
     for r in reqs:
         r.lups_done = 0
+        r.case = None
     live = {}
     used = 0
     nxt = 0
+    pay = Payloads(reqs)
     t0 = time.perf_counter()
     total_lups = 0
     spent = {"start_s": 0.0, "step_s": 0.0, "finish_s": 0.0}  # host wall time by part of the loop
     host_ms = {}  # library host time (vlbm_host_times) summed over the requests
     while nxt < len(pending) or live:
+        # 1. queue steps of the residents first: the GPU works through them
+        #    while the host sets up the requests that arrived meanwhile
+        if live:
+            ta = time.perf_counter()
+            done, _ = eng.advance(MAX_STEPS)
+            tb = time.perf_counter()
+            spent["step_s"] += tb - ta
+            for slot in done:
+                r, h = live.pop(slot)
+                r.lups_done = eng.slot_stats(slot)[1]
+                W, act = h.get_conserved(0)
+                r.done_at = time.perf_counter() - t0
+                if r.rid in keep_ids:
+                    r.result = [h.get_populations(l) for l in range(h.nlev)]
+                total_lups += r.lups_done
+                eng.release(slot)
+                for k, v in h.host_times().items():
+                    host_ms[k] = host_ms.get(k, 0.0) + v
+                h.close()
+                used -= r.bytes_est
+            spent["finish_s"] += time.perf_counter() - tb
+        # 2. admit arrived requests while the memory budget allows (a few per
+        #    round, so that the queue of steps is refilled in between)
         now = time.perf_counter() - t0
-        while nxt < len(pending) and pending[nxt].arrival <= now:
+        admitted = 0
+        while nxt < len(pending) and pending[nxt].arrival <= now and admitted < 4:
             r = pending[nxt]
             if live and used + r.bytes_est > budget:
                 break
             ta = time.perf_counter()
-            h, cs = _start(r, setup_stream if setup_stream is not None else stream)
+            if r.case is None:
+                r.case = pay.take(r)
+            h, cs = _start(r, setup_stream if setup_stream is not None else stream, r.case)
             slot = eng.admit(h, cs.steps, 4 if r.adaptive else 0)
             spent["start_s"] += time.perf_counter() - ta
-            if slot is None:
+            if slot is None:  # over the engine's byte budget: retry later, payload kept
                 h.close()
                 break
+            r.case = None
             live[slot] = (r, h)
             used += r.bytes_est
             nxt += 1
-        if not live:
-            if nxt < len(pending):
-                time.sleep(max(0.0, min(0.002, pending[nxt].arrival - (time.perf_counter() - t0))))
-            continue
-        ta = time.perf_counter()
-        done, _ = eng.advance(MAX_STEPS)
-        tb = time.perf_counter()
-        spent["step_s"] += tb - ta
-        for slot in done:
-            r, h = live.pop(slot)
-            r.lups_done = eng.slot_stats(slot)[1]
-            W, act = h.get_conserved(0)
-            r.done_at = time.perf_counter() - t0
-            if r.rid in keep_ids:
-                r.result = [h.get_populations(l) for l in range(h.nlev)]
-            total_lups += r.lups_done
-            eng.release(slot)
-            for k, v in h.host_times().items():
-                host_ms[k] = host_ms.get(k, 0.0) + v
-            h.close()
-            used -= r.bytes_est
-        spent["finish_s"] += time.perf_counter() - tb
+            admitted += 1
+        if not live and nxt < len(pending):
+            time.sleep(max(0.0, min(0.002, pending[nxt].arrival - (time.perf_counter() - t0))))
     wall = time.perf_counter() - t0
     eng.close()
+    pay.close()
     tts = np.array([r.done_at - r.arrival for r in reqs])
     serve_batched.breakdown = {"loop": spent, "library_host_ms": host_ms}
     return tts, total_lups / wall / 1e6, wall

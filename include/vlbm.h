@@ -277,6 +277,27 @@ vlbm_status vlbm_get_tuning(const vlbm_hier* h, vlbm_tuning* t);
  * and synchronises it.  Errors: ERR_ARG, ERR_OOM, ERR_CUDA. */
 vlbm_status vlbm_selftest_fp64(uint64_t seed, int64_t n, uint64_t mismatches[4], double first_bad[16]);
 
+/* Sensor-driven relaxation (Sec. 2.2, Eq. sensor-B).  on = 1: every level
+ * step first evaluates, on the level's pre-collision state,
+ *   s_k   = dx (div Q)_k / qmax_k (central differences), qmax_k =
+ *           max |Q_{alpha,k}| over the active cells of every level of the
+ *           state at this call (kept fixed, like the link speed),
+ *   s     = (sum_k s_k^2 / 4)^(1/2),
+ *   theta = dil^2 / (dil^2 + vort^2 + eps) where dil = div u < 0, else 0
+ *           (undivided central differences),
+ * then relaxes each active cell with
+ *   beta  = beta_max - (beta_max - beta_min) clip(c_sensor s_bar theta_bar, 0, 1)
+ * where s_bar, theta_bar are 3 x 3 box filters and beta_max is cfg->beta;
+ * neighbours that are not active cells of the level take the cell's own
+ * value.  W remains a collision invariant cell by cell, so conservation is
+ * unchanged.  The hierarchy then advances with one launch per phase (two
+ * sensor passes before each level sweep); the persistent schedule and
+ * per-step totals are not available with the sensor.  on = 0: constant
+ * beta again.  Synchronises.  Errors: ERR_ARG (parameters: 0 <= beta_min
+ * <= beta, c_sensor >= 0, eps >= 0; resident in an engine; per-step totals
+ * on), ERR_OOM, ERR_CUDA, ERR_STATE. */
+vlbm_status vlbm_set_sensor(vlbm_hier* h, int32_t on, double beta_min, double c_sensor, double eps);
+
 /* Self-test of the bounded waits of the persistent task kernel (schedule
  * 1): launches it on one task that depends on a completion mark nothing
  * sets.  The wait gives up after its poll limit (about a second), the

@@ -52,6 +52,8 @@ def lib():
                                            C.POINTER(C.c_void_p)]
         L.ora_tags.argtypes = [C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_void_p)]
         L.ora_flux_max.argtypes = [C.c_void_p, dp]
+        L.ora_set_sensor.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_double]
+        L.ora_sensor_beta.argtypes = [C.c_void_p, C.c_int, dp]
         L.ora_feq.argtypes = [C.c_double, C.c_double, dp, dp]
         L.ora_collide.argtypes = [C.c_double, C.c_double, C.c_double, dp, dp]
         L.ora_minmod.argtypes = [C.c_double, C.c_double]
@@ -191,6 +193,16 @@ class Hierarchy:
         arr = (C.c_void_p * self.nlev)(*[o.ctypes.data for o in outs])
         lib().ora_tags(self._h, int(sensor), tol, arr)
         return outs[: self.nlev - 1]
+
+    def set_sensor(self, on=True, beta_min=0.5, c_sensor=1.0, eps=1e-30):
+        """Sensor-driven relaxation (Sec. 2.2): beta_max is the hierarchy's
+        beta; the flux maxima are fixed from the current state."""
+        lib().ora_set_sensor(self._h, int(on), beta_min, c_sensor, eps)
+
+    def sensor_beta(self, level):
+        out = np.zeros(self.shapes[level])
+        lib().ora_sensor_beta(self._h, level, out.ctypes.data_as(C.POINTER(C.c_double)))
+        return out
 
     def flux_max(self):
         q = (C.c_double * 4)()

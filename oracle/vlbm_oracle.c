@@ -84,6 +84,9 @@ typedef struct {
     double feqb[4][16];
     double gamma, c, beta;
     double om, hb, bcs, gm1, hc;
+    /* sensor-driven relaxation (off unless ora_set_sensor) */
+    int sensor;
+    double beta_min, csens, eps, iq[4], ninth;
     OLevel lev[ORA_MAXLEV];
 } OHier;
 
@@ -135,17 +138,21 @@ void ora_feq(double gamma, double c, const double W[4], double feq[16]) {
 /* BGK relaxation of Eq. 6: f* = 2 beta f^eq(W) + (1 - 2 beta) f with
  * W = sum_i f_i.  With 2 beta f^eq_{+-alpha} = (beta/2) W +- (beta/c) Q_alpha,
  * f* = fma(+-beta/c, Q_alpha, fma(1-2beta, f, (beta/2) W)). */
-static void collide_cell(const OHier* H, const double f[16], double fs[16]) {
+static void collide_with(double gm1, double om, double hb, double bcs, const double f[16], double fs[16]) {
     double W[4], Qx[4], Qy[4];
     moments(f, W);
-    euler_flux(H->gm1, W, Qx, Qy);
+    euler_flux(gm1, W, Qx, Qy);
     for (int k = 0; k < 4; k++) {
-        double A = H->hb * W[k];
-        fs[QI(0, k)] = fma(H->bcs, Qx[k], fma(H->om, f[QI(0, k)], A));
-        fs[QI(1, k)] = fma(-H->bcs, Qx[k], fma(H->om, f[QI(1, k)], A));
-        fs[QI(2, k)] = fma(H->bcs, Qy[k], fma(H->om, f[QI(2, k)], A));
-        fs[QI(3, k)] = fma(-H->bcs, Qy[k], fma(H->om, f[QI(3, k)], A));
+        double A = hb * W[k];
+        fs[QI(0, k)] = fma(bcs, Qx[k], fma(om, f[QI(0, k)], A));
+        fs[QI(1, k)] = fma(-bcs, Qx[k], fma(om, f[QI(1, k)], A));
+        fs[QI(2, k)] = fma(bcs, Qy[k], fma(om, f[QI(2, k)], A));
+        fs[QI(3, k)] = fma(-bcs, Qy[k], fma(om, f[QI(3, k)], A));
     }
+}
+
+static void collide_cell(const OHier* H, const double f[16], double fs[16]) {
+    collide_with(H->gm1, H->om, H->hb, H->bcs, f, fs);
 }
 
 void ora_collide(double gamma, double c, double beta, const double f[16], double fs[16]) {
@@ -474,19 +481,113 @@ static void gather(const OLevel* L, const double* a, size_t c, double v[16]) {
     for (int q = 0; q < 16; q++) v[q] = a[q * L->n + c];
 }
 
+/* ---- sensor-driven relaxation (Sec. 2.2, Eq. sensor-B) -------------
+ * Per level step, on the pre-collision state of the level's active cells:
+ *   s_k   = dx (div Q)_k / max_{x,alpha} |Q_{alpha,k}|, central differences,
+ *           so s_k = g_k / (2 qmax_k) with g_k = (Qx_k(E) - Qx_k(W)) +
+ *           (Qy_k(N) - Qy_k(S)); qmax_k fixed when the sensor is switched on
+ *   s     = ((1/(D+2)) sum_k s_k^2)^(1/2), D = 2
+ *   theta = dil^2 / (dil^2 + vort^2 + eps) where dil < 0, else 0 (Ducros-
+ *           type), dil = (u(E) - u(W)) + (v(N) - v(S)),
+ *           vort = (v(E) - v(W)) - (u(N) - u(S))  (undivided differences)
+ *   s_bar, theta_bar = 3 x 3 box filters
+ *   beta  = beta_max - (beta_max - beta_min) clip(C s_bar theta_bar, 0, 1)
+ * A neighbour that is not an active cell of the level (covered, off the
+ * level, beyond a non-periodic side) takes the centre cell's value. */
+static double nbv(const OHier* H, const OLevel* L, const double* a, int x, int y, int dx, int dy) {
+    int xx = x + dx, yy = y + dy;
+    if (!resolve(H, L, &xx, &yy)) {
+        size_t cn = cidx(L, xx, yy);
+        if (is_active(L, cn)) return a[cn];
+    }
+    return a[cidx(L, x, y)];
+}
+
+/* beta[c] for every active cell of level l (other cells untouched). */
+static void sensor_beta(const OHier* H, const OLevel* L, double* beta) {
+    const size_t n = L->n;
+    double* pr = (double*)calloc(10 * n, sizeof(double));  /* Qx[4], Qy[4], u, v */
+    double* st = (double*)calloc(2 * n, sizeof(double));   /* s, theta */
+    for (size_t c = 0; c < n; c++) {
+        if (!is_active(L, c)) continue;
+        double f[16], W[4], Qx[4], Qy[4];
+        gather(L, L->f, c, f);
+        moments(f, W);
+        euler_flux(H->gm1, W, Qx, Qy);
+        double inv = 1.0 / W[0];
+        for (int k = 0; k < 4; k++) {
+            pr[k * n + c] = Qx[k];
+            pr[(4 + k) * n + c] = Qy[k];
+        }
+        pr[8 * n + c] = W[1] * inv;
+        pr[9 * n + c] = W[2] * inv;
+    }
+    for (int y = 0; y < L->ny; y++)
+        for (int x = 0; x < L->nx; x++) {
+            size_t c = cidx(L, x, y);
+            if (!is_active(L, c)) continue;
+            double sh[4];
+            for (int k = 0; k < 4; k++) {
+                const double* qx = pr + k * n;
+                const double* qy = pr + (4 + k) * n;
+                double g = (nbv(H, L, qx, x, y, 1, 0) - nbv(H, L, qx, x, y, -1, 0)) +
+                           (nbv(H, L, qy, x, y, 0, 1) - nbv(H, L, qy, x, y, 0, -1));
+                sh[k] = g * H->iq[k];
+            }
+            st[c] = sqrt(0.25 * ((sh[0] * sh[0] + sh[1] * sh[1]) + (sh[2] * sh[2] + sh[3] * sh[3])));
+            const double* u = pr + 8 * n;
+            const double* v = pr + 9 * n;
+            double dil = (nbv(H, L, u, x, y, 1, 0) - nbv(H, L, u, x, y, -1, 0)) +
+                         (nbv(H, L, v, x, y, 0, 1) - nbv(H, L, v, x, y, 0, -1));
+            double vort = (nbv(H, L, v, x, y, 1, 0) - nbv(H, L, v, x, y, -1, 0)) -
+                          (nbv(H, L, u, x, y, 0, 1) - nbv(H, L, u, x, y, 0, -1));
+            double d2 = dil * dil;
+            st[n + c] = dil < 0.0 ? d2 / ((d2 + vort * vort) + H->eps) : 0.0;
+        }
+    for (int y = 0; y < L->ny; y++)
+        for (int x = 0; x < L->nx; x++) {
+            size_t c = cidx(L, x, y);
+            if (!is_active(L, c)) continue;
+            double as = 0.0, at = 0.0;
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    as += nbv(H, L, st, x, y, dx, dy);
+                    at += nbv(H, L, st + n, x, y, dx, dy);
+                }
+            double z = (H->csens * (H->ninth * as)) * (H->ninth * at);
+            if (z < 0.0) z = 0.0;
+            if (z > 1.0) z = 1.0;
+            beta[c] = H->beta - (H->beta - H->beta_min) * z;
+        }
+    free(pr);
+    free(st);
+}
+
 static void step(OHier* H, int l, int k) {
     OLevel* L = &H->lev[l];
     const int r = H->r;
     const size_t n = L->n;
 
-    /* 1. collision on every active cell of level l */
+    /* 1. collision on every active cell of level l (relaxation parameter
+     *    per cell from the sensor when it is on) */
+    double* beta = NULL;
+    if (H->sensor) {
+        beta = (double*)calloc(n, sizeof(double));
+        sensor_beta(H, L, beta);
+    }
     for (size_t c = 0; c < n; c++) {
         if (!is_active(L, c)) continue;
         double f[16], fs[16];
         gather(L, L->f, c, f);
-        collide_cell(H, f, fs);
+        if (beta) {
+            double b = beta[c];
+            collide_with(H->gm1, 1.0 - 2.0 * b, 0.5 * b, b / H->c, f, fs);
+        } else {
+            collide_cell(H, f, fs);
+        }
         for (int q = 0; q < 16; q++) L->fs[q * n + c] = fs[q];
     }
+    free(beta);
 
     /* 2. fine side: post-collision populations leaving towards coarser
      *    territory go to the register of their face, slot (k, j). */
@@ -922,4 +1023,48 @@ void ora_flux_max(void* h, double qmax[4]) {
     double** comp = composite(H);
     flux_max(H, comp, qmax);
     free_comp(H, comp);
+}
+
+/* Sensor-driven relaxation: on = 1 switches it on with beta_max = the
+ * hierarchy's beta, the given beta_min, C_sensor and eps, and fixes
+ * qmax_k = max |Q_{alpha,k}| over the active cells of every level of the
+ * current state; on = 0 returns to the constant beta. */
+void ora_set_sensor(void* h, int on, double beta_min, double csens, double eps) {
+    OHier* H = (OHier*)h;
+    H->sensor = on;
+    H->beta_min = beta_min;
+    H->csens = csens;
+    H->eps = eps;
+    H->ninth = 1.0 / 9.0;
+    double qmax[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int l = 0; l < H->nlev; l++) {
+        const OLevel* L = &H->lev[l];
+        for (size_t c = 0; c < L->n; c++) {
+            if (!is_active(L, c)) continue;
+            double f[16], W[4], Qx[4], Qy[4];
+            gather(L, L->f, c, f);
+            moments(f, W);
+            euler_flux(H->gm1, W, Qx, Qy);
+            for (int k = 0; k < 4; k++) {
+                if (fabs(Qx[k]) > qmax[k]) qmax[k] = fabs(Qx[k]);
+                if (fabs(Qy[k]) > qmax[k]) qmax[k] = fabs(Qy[k]);
+            }
+        }
+    }
+    for (int k = 0; k < 4; k++) H->iq[k] = qmax[k] > 0.0 ? 1.0 / (2.0 * qmax[k]) : 0.0;
+}
+
+/* The relaxation parameter the next step of level l would use on each
+ * active cell (constant beta when the sensor is off; 0 elsewhere). */
+void ora_sensor_beta(void* h, int l, double* out) {
+    OHier* H = (OHier*)h;
+    const OLevel* L = &H->lev[l];
+    for (size_t c = 0; c < L->n; c++) out[c] = is_active(L, c) ? H->beta : 0.0;
+    if (H->sensor) {
+        double* b = (double*)calloc(L->n, sizeof(double));
+        sensor_beta(H, L, b);
+        for (size_t c = 0; c < L->n; c++)
+            if (is_active(L, c)) out[c] = b[c];
+        free(b);
+    }
 }

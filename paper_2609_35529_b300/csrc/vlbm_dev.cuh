@@ -1,9 +1,10 @@
 // Device-side data model of the VLBM library (sm_103a).
 //
 // Storage: every level l of a hierarchy owns two dense population buffers
-// over its whole index space, buf[b][q * plane + y * pitch + x], q = 4 i + k
-// (direction i in +x,-x,+y,-y; field k in rho, rho u, rho v, rho E), plus a
-// 16-bit flag word per cell.  Work is organised in 8 x 8 tiles that coincide
+// over its whole index space, population q = 4 i + k (direction i in
+// +x,-x,+y,-y; field k in rho, rho u, rho v, rho E) of cell y * pitch + x at
+// qoff(q, plane, cell) (pairs of fields interleaved), plus a 16-bit flag
+// word per cell.  Work is organised in 8 x 8 tiles that coincide
 // with the refinement blocks, so a tile is entirely active, entirely covered
 // by the next level, or entirely off the level.
 //
@@ -62,7 +63,27 @@ struct LevelDev {
     double om, hb, bcs, gm1;
     double wscale;    // area weight 4^-level
     double feqb[4][16];
+    // sensor-driven relaxation (sens == nullptr: constant beta): planes of
+    // sens: 0-3 Qx, 4-7 Qy, 8 u, 9 v (from the pre-collision state of the
+    // level step), 10 s, 11 theta; plane stride `plane`
+    double* sens;
+    double beta_max, beta_min, csens, eps, ninth, c, iq[4];
 };
+constexpr int SENS_PLANES = 12;
+
+#ifdef __CUDACC__
+#define VLBM_HD __host__ __device__
+#else
+#define VLBM_HD
+#endif
+
+// Offset of population q = 4 i + k of cell c in a level buffer: the planes
+// of fields (0, 1) and of fields (2, 3) of each direction are interleaved,
+// [q / 2][cell][q % 2], so one 16-byte access moves a pair of them (same
+// direction, same destination cell).  16 * plane doubles in all.
+VLBM_HD inline long long qoff(int q, long long plane, long long c) {
+    return (long long)(q >> 1) * (2 * plane) + 2 * c + (q & 1);
+}
 
 // A unit of work: one 8 x 8 tile of one level.
 struct Item {

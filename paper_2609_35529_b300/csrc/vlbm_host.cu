@@ -200,6 +200,11 @@ struct vlbm_hier {
     // per-step conservation totals recorded by vlbm_advance (pinned ring)
     bool step_audit = false;
     double times[VLBM_T_COUNT] = {};  // host-side time, see vlbm_host_times
+    // sensor-driven relaxation (vlbm_set_sensor): parameters and, per level,
+    // SENS_PLANES planes of the level's index space
+    bool sensor_on = false;
+    double s_beta_min = 0.5, s_csens = 0.0, s_eps = 0.0, s_iq[4] = {0, 0, 0, 0};
+    double* sens[VLBM_MAX_LEVELS] = {};
     double* hist = nullptr;
     long long hist_cap = 4096, hist_n = 0, hist_read = 0;
     // cached task lists of this hierarchy alone: [0] one step, [1] G steps
@@ -249,6 +254,14 @@ struct vlbm_hier {
         d.gm1 = gm1;
         d.wscale = std::ldexp(1.0, -2 * l);
         std::memcpy(d.feqb, feqb, sizeof feqb);
+        d.sens = sensor_on ? sens[l] : nullptr;
+        d.beta_max = cfg.beta;
+        d.beta_min = s_beta_min;
+        d.csens = s_csens;
+        d.eps = s_eps;
+        d.ninth = 1.0 / 9.0;
+        d.c = cfg.c;
+        for (int k = 0; k < 4; k++) d.iq[k] = s_iq[k];
         return d;
     }
     size_t device_bytes() const { return mem.bytes; }
@@ -266,6 +279,7 @@ struct Batch {
     DArr<Item> audit_items;
     cudaGraphExec_t exec1 = nullptr, execG = nullptr;
     int G = 8;
+    bool sensor = false;  // some member runs the sensor-driven relaxation (per-phase schedule)
     bool valid = false;
     int max_ctas = 0;  // sweep grid cap (0 = one CTA per 4 tiles)
     int variant = 0;   // sweep kernel variant
@@ -292,7 +306,8 @@ struct Batch {
     }
 
     void schedule(int l, int kk, int kkp, cudaStream_t s) {
-        VCK(launch_sweep(levs.p, sweep[l].p, (int)sweep[l].n, kk, kkp, max_ctas, variant, s));
+        if (sensor) VCK(launch_sensor(levs.p, sweep[l].p, (int)sweep[l].n, kk, s));
+        VCK(launch_sweep(levs.p, sweep[l].p, (int)sweep[l].n, kk, kkp, max_ctas, variant, s, sensor));
         if (l + 1 < maxlev && sweep[l + 1].n > 0) {
             schedule(l + 1, 1, kk, s);
             schedule(l + 1, 2, kk, s);
@@ -335,6 +350,7 @@ struct Batch {
         std::vector<Item> sw[VLBM_MAX_LEVELS], cl[VLBM_MAX_LEVELS], au;
         std::vector<int*> pw;
         maxlev = 0;
+        sensor = false;
         for (vlbm_hier* h : members) {
             const int base = (int)tab.size();
             for (int l = 0; l < h->nlev; l++) {
@@ -352,6 +368,7 @@ struct Batch {
             }
             maxlev = std::max(maxlev, h->nlev);
             pw.push_back(h->words);
+            sensor = sensor || h->sensor_on;
         }
         levs.upload(*mem, tab, s);
         for (int l = 0; l < VLBM_MAX_LEVELS; l++) {
@@ -402,8 +419,13 @@ struct Batch {
     }
     void schedule_timed(int l, int kk, int kkp, const long long* cells, std::vector<Rec>& recs, cudaStream_t s) {
         if (sweep[l].n)
-            timed(0, l, cells[l], recs, s,
-                  [&] { return launch_sweep(levs.p, sweep[l].p, (int)sweep[l].n, kk, kkp, max_ctas, variant, s); });
+            timed(0, l, cells[l], recs, s, [&] {
+                if (sensor) {
+                    cudaError_t e = launch_sensor(levs.p, sweep[l].p, (int)sweep[l].n, kk, s);
+                    if (e != cudaSuccess) return e;
+                }
+                return launch_sweep(levs.p, sweep[l].p, (int)sweep[l].n, kk, kkp, max_ctas, variant, s, sensor);
+            });
         if (l + 1 < maxlev && sweep[l + 1].n > 0) {
             schedule_timed(l + 1, 1, kk, cells, recs, s);
             schedule_timed(l + 1, 2, kk, cells, recs, s);
@@ -865,6 +887,7 @@ struct vlbm_engine {
         int regrid_every = 0;
         bool live = false;
         bool adaptive() const { return regrid_every > 0 && h->cfg.tag_tol > 0; }
+        bool phased() const { return adaptive() || h->sensor_on; }
     };
     std::vector<Res> res;
     bool dirty = true;
@@ -912,6 +935,10 @@ void destroy_levels(vlbm_hier* h) {
         L.buf[0] = L.buf[1] = nullptr;
         L.flags = L.flags_tmp = nullptr;
     }
+    for (int l = 0; l < VLBM_MAX_LEVELS; l++) {
+        if (h->sens[l]) h->mem.put(h->sens[l], (size_t)SENS_PLANES * h->lev[l].plane * sizeof(double));
+        h->sens[l] = nullptr;
+    }
     h->mem.put(h->words, 64);
     h->words = nullptr;
     h->stage.release(h->mem);
@@ -946,6 +973,7 @@ void destroy_levels(vlbm_hier* h) {
 // regrids often never pays for a task list -- and the persistent task
 // kernel after that, or whenever per-step totals are on.
 int effective_schedule(const vlbm_hier* h) {
+    if (h->sensor_on) return 0;  // the sensor passes run between per-phase launches
     if (h->tune.schedule != 2) return h->tune.schedule;
     return (h->step_audit || h->layout_steps >= h->tune.persist_after) ? 1 : 0;
 }
@@ -1285,6 +1313,7 @@ vlbm_status vlbm_checkpoint_load(vlbm_hier* h, const void* blob, size_t bytes) {
 vlbm_status vlbm_set_step_totals(vlbm_hier* h, int32_t on) {
     return run(h, [&] {
         if (on && h->tune.schedule == 0) throw Fail{VLBM_ERR_ARG, "per-step totals need the persistent schedule"};
+        if (on && h->sensor_on) throw Fail{VLBM_ERR_ARG, "per-step totals and the relaxation sensor exclude each other"};
         if (on && !h->hist) VCK(cudaMallocHost((void**)&h->hist, (size_t)h->hist_cap * 8 * sizeof(double)));
         VCK(cudaStreamSynchronize(h->stream));
         h->step_audit = on != 0;
@@ -1450,6 +1479,44 @@ vlbm_status vlbm_regrid(vlbm_hier* h, const vlbm_box* boxes, int32_t nboxes) {
             h->times[VLBM_T_REGRID] += ms_since(t0);
         }
         h->times[VLBM_T_NREGRIDS] += 1;
+        invalidate(h);
+    });
+}
+
+vlbm_status vlbm_set_sensor(vlbm_hier* h, int32_t on, double beta_min, double c_sensor, double eps) {
+    return run(h, [&] {
+        if (h->engine) throw Fail{VLBM_ERR_ARG, "hierarchy is resident in an engine"};
+        if (on && !(beta_min >= 0.0 && beta_min <= h->cfg.beta && c_sensor >= 0.0 && eps >= 0.0))
+            throw Fail{VLBM_ERR_ARG, "bad sensor parameters"};
+        if (on && h->step_audit) throw Fail{VLBM_ERR_ARG, "per-step totals and the relaxation sensor exclude each other"};
+        cudaStream_t s = h->stream;
+        if (on) {
+            // the flux maxima over the active cells of every level, now
+            h->qmax.ensure(h->mem, 4);
+            VCK(cudaMemsetAsync(h->qmax.p, 0, 4 * sizeof(unsigned long long), s));
+            for (int l = 0; l < h->nlev; l++) {
+                h->listbuf.upload(h->mem, h->lev[l].act, s);
+                VCK(launch_qmax(lvdev(h, l), h->listbuf.p, (int)h->listbuf.n, h->qmax.p, s));
+            }
+            unsigned long long q[4];
+            VCK(cudaMemcpyAsync(q, h->qmax.p, sizeof q, cudaMemcpyDeviceToHost, s));
+            VCK(cudaStreamSynchronize(s));
+            for (int k = 0; k < 4; k++) {
+                double m;
+                std::memcpy(&m, &q[k], sizeof m);
+                h->s_iq[k] = m > 0.0 ? 1.0 / (2.0 * m) : 0.0;
+            }
+            for (int l = 0; l < h->nlev; l++)
+                if (!h->sens[l]) {
+                    const size_t b = (size_t)SENS_PLANES * h->lev[l].plane * sizeof(double);
+                    h->sens[l] = (double*)h->mem.get(b);
+                    VCK(cudaMemsetAsync(h->sens[l], 0, b, s));
+                }
+            h->s_beta_min = beta_min;
+            h->s_csens = c_sensor;
+            h->s_eps = eps;
+        }
+        h->sensor_on = on != 0;
         invalidate(h);
     });
 }
@@ -1636,7 +1703,7 @@ vlbm_status vlbm_engine_advance(vlbm_engine* e, int32_t max_steps, int32_t* fini
             e->batch.members.clear();
             e->phased.members.clear();
             for (auto& r : e->res)
-                if (r.live && r.done < r.target) (r.adaptive() ? e->phased : e->batch).members.push_back(r.h);
+                if (r.live && r.done < r.target) (r.phased() ? e->phased : e->batch).members.push_back(r.h);
             if (!e->batch.members.empty()) e->batch.build(e->stream);
             if (!e->phased.members.empty()) e->phased.build(e->stream);
             e->dirty = false;
@@ -1651,11 +1718,16 @@ vlbm_status vlbm_engine_advance(vlbm_engine* e, int32_t max_steps, int32_t* fini
             if (r.adaptive()) k = std::min<long long>(k, r.regrid_every - r.done % r.regrid_every);
         }
         if (!any) return VLBM_OK;
+        // static residents: one graph of the persistent kernel per step;
+        // adaptive residents: their per-phase launches issued directly (their
+        // batch changes at nearly every step, when one of them regrids, so
+        // capturing and instantiating a graph each time would cost more than
+        // the launches)
         cudaGraphExec_t gs = e->batch.members.empty() ? nullptr : e->batch.exec_for(0, e->stream);
-        cudaGraphExec_t gp = e->phased.members.empty() ? nullptr : e->phased.exec_for(0, e->stream);
+        const bool phased = !e->phased.members.empty();
         for (long long i = 0; i < k; i++) {
             if (gs) VCK(cudaGraphLaunch(gs, e->stream));
-            if (gp) VCK(cudaGraphLaunch(gp, e->stream));
+            if (phased) e->phased.one_step(e->stream);
         }
         int nf = 0;
         for (size_t i = 0; i < e->res.size(); i++) {

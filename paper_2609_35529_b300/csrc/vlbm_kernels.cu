@@ -81,6 +81,9 @@ enum : int { EM_MOM = 1, EM_A = 2, EM_FLUX = 4, EM_OMF = 8 };
 // persistent task kernel prefetches the next task's populations into
 // shared memory (see task_kernel).
 enum : int { TK_PREFETCH = 256, TK_HALF = 512 };
+// The sweep reads the relaxation parameter of each cell from the sensor
+// planes (sensor-driven relaxation; per-phase schedule only).
+enum : int { SW_SENSOR = 1024 };
 
 template <bool E>
 __device__ __forceinline__ double xadd(double a, double b) {
@@ -177,6 +180,109 @@ __device__ __forceinline__ void level_bufs(const LevelDev& L, int kk, int step, 
 __device__ __forceinline__ int state_buf(const LevelDev& L) { return L.level == 0 ? *L.par0 : 0; }
 
 // ---------------------------------------------------------------------------
+// sensor-driven relaxation (Sec. 2.2, Eq. sensor-B)
+// ---------------------------------------------------------------------------
+// Per level step, on the level's active cells, from the pre-collision state:
+//   s_k   = g_k / (2 qmax_k), g_k = (Qx_k(E) - Qx_k(W)) + (Qy_k(N) - Qy_k(S))
+//           (dx (div Q)_k / max |Q_k| with central differences)
+//   s     = (0.25 sum_k s_k^2)^(1/2)
+//   theta = dil^2 / (dil^2 + vort^2 + eps) where dil < 0, else 0, with the
+//           undivided dil = (u(E) - u(W)) + (v(N) - v(S)) and
+//           vort = (v(E) - v(W)) - (u(N) - u(S))
+//   beta  = beta_max - (beta_max - beta_min) clip(C s_bar theta_bar, 0, 1)
+//           with 3 x 3 box filters s_bar, theta_bar
+// A neighbour that is not an active cell of the level (covered, off the
+// level, beyond a non-periodic side) takes the centre cell's value.
+
+// Cell index of neighbour (x + dx, y + dy) when it is an active cell of the
+// level, else the centre's.
+__device__ __forceinline__ long long sens_nb(const LevelDev& L, int x, int y, int dx, int dy, long long c) {
+    int xx = x + dx, yy = y + dy;
+    if (xx < 0) { if (!L.px) return c; xx += L.nx; }
+    if (xx >= L.nx) { if (!L.px) return c; xx -= L.nx; }
+    if (yy < 0) { if (!L.py) return c; yy += L.ny; }
+    if (yy >= L.ny) { if (!L.py) return c; yy -= L.ny; }
+    const long long cn = (long long)yy * L.pitch + xx;
+    return (L.flags[cn] & (F_IN | F_COV)) == F_IN ? cn : c;
+}
+
+// Pass 1: Q, u, v of every active cell from the level step's source buffer.
+__global__ void sensor_prep_kernel(const LevelDev* __restrict__ levs, const Item* __restrict__ items, int nitems,
+                                   int kk) {
+    const int sub = threadIdx.x >> 6, cx = threadIdx.x & 7, cy = (threadIdx.x >> 3) & 7;
+    for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
+        const Item w = items[it];
+        const LevelDev& L = levs[w.lid];
+        if (!L.sens) continue;
+        const int x = w.tx * TILE + cx, y = w.ty * TILE + cy;
+        if (x >= L.nx || y >= L.ny) continue;
+        const long long c = (long long)y * L.pitch + x;
+        if ((L.flags[c] & (F_IN | F_COV)) != F_IN) continue;
+        const double* src;
+        double* dst;
+        level_bufs(L, kk, 0, src, dst);
+        double W[4], Qx[4], Qy[4], p;
+        for (int k = 0; k < 4; k++)
+            W[k] = (src[qoff(0 + k, L.plane, c)] + src[qoff(4 + k, L.plane, c)]) +
+                   (src[qoff(8 + k, L.plane, c)] + src[qoff(12 + k, L.plane, c)]);
+        euler_flux(L.gm1, W, Qx, Qy, p);
+        const double inv = 1.0 / W[0];
+        for (int k = 0; k < 4; k++) {
+            L.sens[k * L.plane + c] = Qx[k];
+            L.sens[(4 + k) * L.plane + c] = Qy[k];
+        }
+        L.sens[8 * L.plane + c] = W[1] * inv;
+        L.sens[9 * L.plane + c] = W[2] * inv;
+    }
+}
+
+// Pass 2: s and theta of every active cell.
+__global__ void sensor_rate_kernel(const LevelDev* __restrict__ levs, const Item* __restrict__ items, int nitems) {
+    const int sub = threadIdx.x >> 6, cx = threadIdx.x & 7, cy = (threadIdx.x >> 3) & 7;
+    for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
+        const Item w = items[it];
+        const LevelDev& L = levs[w.lid];
+        if (!L.sens) continue;
+        const int x = w.tx * TILE + cx, y = w.ty * TILE + cy;
+        if (x >= L.nx || y >= L.ny) continue;
+        const long long c = (long long)y * L.pitch + x;
+        if ((L.flags[c] & (F_IN | F_COV)) != F_IN) continue;
+        const long long e = sens_nb(L, x, y, 1, 0, c), ww = sens_nb(L, x, y, -1, 0, c);
+        const long long n = sens_nb(L, x, y, 0, 1, c), so = sens_nb(L, x, y, 0, -1, c);
+        const double* S = L.sens;
+        const long long P = L.plane;
+        double sh[4];
+        for (int k = 0; k < 4; k++) {
+            const double g = (S[k * P + e] - S[k * P + ww]) + (S[(4 + k) * P + n] - S[(4 + k) * P + so]);
+            sh[k] = g * L.iq[k];
+        }
+        L.sens[10 * P + c] = sqrt(0.25 * ((sh[0] * sh[0] + sh[1] * sh[1]) + (sh[2] * sh[2] + sh[3] * sh[3])));
+        const double dil = (S[8 * P + e] - S[8 * P + ww]) + (S[9 * P + n] - S[9 * P + so]);
+        const double vort = (S[9 * P + e] - S[9 * P + ww]) - (S[8 * P + n] - S[8 * P + so]);
+        const double d2 = dil * dil;
+        L.sens[11 * P + c] = dil < 0.0 ? d2 / ((d2 + vort * vort) + L.eps) : 0.0;
+    }
+}
+
+// The relaxation parameter of active cell (x, y) from the 3 x 3 filters.
+__device__ double sensor_beta_at(const LevelDev& L, int x, int y) {
+    const long long c = (long long)y * L.pitch + x;
+    const double* Ss = L.sens + 10 * L.plane;
+    const double* St = L.sens + 11 * L.plane;
+    double as = 0.0, at = 0.0;
+    for (int dy = -1; dy <= 1; dy++)
+        for (int dx = -1; dx <= 1; dx++) {
+            const long long q = sens_nb(L, x, y, dx, dy, c);
+            as += Ss[q];
+            at += St[q];
+        }
+    double z = (L.csens * (L.ninth * as)) * (L.ninth * at);
+    if (z < 0.0) z = 0.0;
+    if (z > 1.0) z = 1.0;
+    return L.beta_max - (L.beta_max - L.beta_min) * z;
+}
+
+// ---------------------------------------------------------------------------
 // the fused level sweep: collide, push-stream, boundary and coarse-to-fine
 // ---------------------------------------------------------------------------
 
@@ -208,7 +314,7 @@ __device__ __noinline__ void sweep_special(const LevelDev* __restrict__ levs, co
                     const double m = fs[4 * (i ^ 1) + k];
                     v = (k == normal) ? -m : m;
                 }
-                dst[(long long)(4 * i + k) * L.plane + c] = v;
+                dst[qoff(4 * i + k, L.plane, c)] = v;
             }
         }
     }
@@ -250,12 +356,12 @@ __device__ __noinline__ void sweep_special(const LevelDev* __restrict__ levs, co
         const int j = d < 2 ? (y & 1) : (x & 1);
         const double wj = j ? 0.25 : -0.25;
         for (int k = 0; k < 4; k++) {
-            const long long qo = (long long)(4 * d + k) * P.plane;
-            const double a = ld<COH>(pdst + qo + ch);
-            const double ap = fresh ? a : ld<COH>(psrc + qo + ch);
+            const int q = 4 * d + k;
+            const double a = ld<COH>(pdst + qoff(q, P.plane, ch));
+            const double ap = fresh ? a : ld<COH>(psrc + qoff(q, P.plane, ch));
             double s = 0.0;
-            if (okm && okp) s = minmod(a - ld<COH>(pdst + qo + cm), ld<COH>(pdst + qo + cp) - a);
-            dst[(long long)(4 * i + k) * L.plane + c] = fma(s, wj, fma(a - ap, wk, a));
+            if (okm && okp) s = minmod(a - ld<COH>(pdst + qoff(q, P.plane, cm)), ld<COH>(pdst + qoff(q, P.plane, cp)) - a);
+            dst[qoff(4 * i + k, L.plane, c)] = fma(s, wj, fma(a - ap, wk, a));
         }
     }
 }
@@ -278,14 +384,29 @@ __device__ __forceinline__ void sweep_cell(const LevelDev* __restrict__ levs, co
     level_bufs(L, kk, step, src, dst);
     const long long plane = L.plane;
     double f[16];
-    if (pre) {  // this cell's populations, prefetched into shared memory (stride 64)
+    if (pre) {  // this cell's populations, prefetched into shared memory ([pair][cell][2])
 #pragma unroll
-        for (int q = 0; q < 16; q++) f[q] = pre[q * 64];
+        for (int q = 0; q < 16; q++) f[q] = pre[(q >> 1) * 128 + (q & 1)];
     } else {
 #pragma unroll
-        for (int q = 0; q < 16; q++) f[q] = ld<COH>(src + q * plane + c);
+        for (int pr = 0; pr < 8; pr++) {  // 16-byte loads of the field pairs
+            const double2 v = ld<COH>(reinterpret_cast<const double2*>(src + qoff(2 * pr, plane, c)));
+            f[2 * pr] = v.x;
+            f[2 * pr + 1] = v.y;
+        }
     }
-    if (!collide_p<P>(f, L.om, L.hb, L.bcs, L.gm1, Wout)) atomicOr(L.status, ST_NONPHYS);
+    bool ok;
+    if constexpr ((P & SW_SENSOR) != 0) {
+        if (L.sens) {
+            const double b = sensor_beta_at(L, x, y);
+            ok = collide_p<P>(f, 1.0 - 2.0 * b, 0.5 * b, b / L.c, L.gm1, Wout);
+        } else {
+            ok = collide_p<P>(f, L.om, L.hb, L.bcs, L.gm1, Wout);
+        }
+    } else {
+        ok = collide_p<P>(f, L.om, L.hb, L.bcs, L.gm1, Wout);
+    }
+    if (!ok) atomicOr(L.status, ST_NONPHYS);
     // push streaming (Eq. 5): f*_i lands on x + c_i
     long long cxp = c + 1, cxm = c - 1, cyp = c + L.pitch, cym = c - L.pitch;
     bool oxp = true, oxm = true, oyp = true, oym = true;
@@ -293,13 +414,15 @@ __device__ __forceinline__ void sweep_cell(const LevelDev* __restrict__ levs, co
     if (x == 0) { if (L.px) cxm = c + (nx - 1); else oxm = false; }
     if (y == ny - 1) { if (L.py) cyp = c - (long long)(ny - 1) * L.pitch; else oyp = false; }
     if (y == 0) { if (L.py) cym = c + (long long)(ny - 1) * L.pitch; else oym = false; }
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        if (oxp) dst[(0 + k) * plane + cxp] = f[0 + k];
-        if (oxm) dst[(4 + k) * plane + cxm] = f[4 + k];
-        if (oyp) dst[(8 + k) * plane + cyp] = f[8 + k];
-        if (oym) dst[(12 + k) * plane + cym] = f[12 + k];
-    }
+    // 16-byte stores of the field pairs
+    auto push = [&](int i, long long t) {
+        *reinterpret_cast<double2*>(dst + qoff(4 * i, plane, t)) = make_double2(f[4 * i], f[4 * i + 1]);
+        *reinterpret_cast<double2*>(dst + qoff(4 * i + 2, plane, t)) = make_double2(f[4 * i + 2], f[4 * i + 3]);
+    };
+    if (oxp) push(0, cxp);
+    if (oxm) push(1, cxm);
+    if (oyp) push(2, cyp);
+    if (oym) push(3, cym);
     if (fl & (F_BND | F_RECON_MASK)) sweep_special<COH>(levs, L, x, y, c, fl, f, dst, kk, kkp, step);
 }
 
@@ -347,10 +470,10 @@ __device__ __forceinline__ void close_cell(const LevelDev* __restrict__ levs, co
         const long long g0 = (long long)gy0 * F.pitch + gx0;
         const long long g1 = (long long)gy1 * F.pitch + gx1;
         for (int k = 0; k < 4; k++) {
-            const long long qo = (long long)(4 * i + k) * F.plane;
-            const double v = ((ld<COH>(s1 + qo + g0) + ld<COH>(s1 + qo + g1)) +
-                              (ld<COH>(s2 + qo + g0) + ld<COH>(s2 + qo + g1))) * 0.25;
-            dst[(long long)(4 * i + k) * L.plane + c] = v;
+            const int q = 4 * i + k;
+            const long long o0 = qoff(q, F.plane, g0), o1 = qoff(q, F.plane, g1);
+            const double v = ((ld<COH>(s1 + o0) + ld<COH>(s1 + o1)) + (ld<COH>(s2 + o0) + ld<COH>(s2 + o1))) * 0.25;
+            dst[qoff(q, L.plane, c)] = v;
         }
     }
     if (fl & F_FRESH_MASK) L.flags[c] = (uint16_t)(fl & ~F_FRESH_MASK);
@@ -421,11 +544,10 @@ __device__ __forceinline__ int find_segment(const int* __restrict__ prefix, int 
 
 // Prefetch of task t2 by one warp, if t2 is a level sweep whose
 // dependencies are all complete already (checked without waiting; each
-// warp decides for its own cells).  Lane pair p of the group copies the two
-// cells (2p, 2p + 1) of the tile, the even lane planes 0-7, the odd lane
-// planes 8-15, 16 bytes per copy through L2, into buf[q][cell].  Returns
-// whether this warp's cells were requested.  The data cannot change before
-// t2 runs: every later writer of t2's source cells waits for t2.
+// warp decides for its own cells).  Each lane copies the eight field pairs
+// of its own cell, 16 bytes per copy through L2, into buf[pair][cell][2].
+// Returns whether this warp's cells were requested.  The data cannot change
+// before t2 runs: every later writer of t2's source cells waits for t2.
 __device__ __forceinline__ bool prefetch_task(const LevelDev* __restrict__ levs, const Segment* __restrict__ segs,
                                               const int* __restrict__ prefix, int nseg, int t2, unsigned epoch,
                                               double* buf, int lt) {
@@ -441,12 +563,11 @@ __device__ __forceinline__ bool prefetch_task(const LevelDev* __restrict__ levs,
     const double* src;
     double* dst;
     level_bufs(L, T.kk, T.step, src, dst);
-    const int pr = lt >> 1, cy = pr >> 2, x = T.tx * TILE + (pr & 3) * 2, y = T.ty * TILE + cy;
-    if (y < L.ny) {  // x + 1 < pitch always: rows are padded to 16 cells
-        const double* g0 = src + (long long)y * L.pitch + x;
-        const int q0 = (lt & 1) * 8;
+    const int x = T.tx * TILE + (lt & 7), y = T.ty * TILE + (lt >> 3);
+    if (y < L.ny) {  // x < pitch always: rows are padded to 16 cells
+        const long long c = (long long)y * L.pitch + x;
 #pragma unroll
-        for (int q = q0; q < q0 + 8; q++) cp_async16(buf + q * 64 + 2 * pr, g0 + q * L.plane);
+        for (int pr = 0; pr < 8; pr++) cp_async16(buf + pr * 128 + 2 * lt, src + qoff(2 * pr, L.plane, c));
     }
     return true;
 }
@@ -465,8 +586,8 @@ __device__ __forceinline__ bool prefetch_task(const LevelDev* __restrict__ levs,
 // through L2 (ld.global.cg, cp.async.cg).
 //
 // With TK_PREFETCH each group double-buffers the populations of its tasks
-// in shared memory (2 x 16 planes x 64 cells): while a task runs, the copy
-// of the next one is in flight whenever its dependencies are complete.
+// in shared memory (2 x 8 pairs x 64 cells x 2): while a task runs, the
+// copy of the next one is in flight whenever its dependencies are complete.
 constexpr int TK_SMEM = TILES_PER_CTA * 2 * NQ * 64 * (int)sizeof(double);
 
 template <int P, int MINB>
@@ -505,8 +626,8 @@ task_kernel(const LevelDev* __restrict__ levs, const Segment* __restrict__ segs,
             cp_async_commit();
             if (pf) {
                 cp_async_wait_prev();  // the copies of the current task
-                __syncwarp();          // ... including the partner lane's
-                pre = base + pb * NQ * 64 + lt;
+                __syncwarp();
+                pre = base + pb * NQ * 64 + 2 * lt;  // this cell: [pair][cell][2]
             }
         }
         if (T.kind == 0) {
@@ -774,10 +895,10 @@ __global__ void feq_init_kernel(LevelDev L, const double* __restrict__ W, long l
         double* out = L.buf[state_buf(L)];
         for (int k = 0; k < 4; k++) {
             const double qw = 0.25 * w[k];
-            out[(0 + k) * L.plane + c] = fma(hc, Qx[k], qw);
-            out[(4 + k) * L.plane + c] = fma(-hc, Qx[k], qw);
-            out[(8 + k) * L.plane + c] = fma(hc, Qy[k], qw);
-            out[(12 + k) * L.plane + c] = fma(-hc, Qy[k], qw);
+            out[qoff(0 + k, L.plane, c)] = fma(hc, Qx[k], qw);
+            out[qoff(4 + k, L.plane, c)] = fma(-hc, Qx[k], qw);
+            out[qoff(8 + k, L.plane, c)] = fma(hc, Qy[k], qw);
+            out[qoff(12 + k, L.plane, c)] = fma(-hc, Qy[k], qw);
         }
     }
 }
@@ -791,8 +912,8 @@ __global__ void copy_pop_kernel(LevelDev L, double* __restrict__ ext, long long 
         const long long c = (long long)y * L.pitch + x;
         for (int q = 0; q < 16; q++) {
             const long long e = (long long)q * ld * L.ny + (long long)y * ld + x;
-            if (to_ext) ext[e] = st[q * L.plane + c];
-            else st[q * L.plane + c] = ext[e];
+            if (to_ext) ext[e] = st[qoff(q, L.plane, c)];
+            else st[qoff(q, L.plane, c)] = ext[e];
         }
     }
 }
@@ -810,8 +931,8 @@ __global__ void gather_W_kernel(LevelDev L, double* __restrict__ W, long long ld
         for (int k = 0; k < 4; k++) {
             double v = 0.0;
             if (fl & F_IN)
-                v = (st[(0 + k) * L.plane + c] + st[(4 + k) * L.plane + c]) +
-                    (st[(8 + k) * L.plane + c] + st[(12 + k) * L.plane + c]);
+                v = (st[qoff(0 + k, L.plane, c)] + st[qoff(4 + k, L.plane, c)]) +
+                    (st[qoff(8 + k, L.plane, c)] + st[qoff(12 + k, L.plane, c)]);
             W[k * pl + o] = v;
         }
         if (valid) valid[(long long)y * L.nx + x] = (fl & (F_IN | F_COV)) == F_IN;
@@ -841,8 +962,8 @@ __global__ void __launch_bounds__(256) audit_kernel(const LevelDev* __restrict__
         if ((L.flags[c] & (F_IN | F_COV)) != F_IN) continue;
         const double* st = L.buf[state_buf(L)];
         for (int k = 0; k < 4; k++) {
-            const double v = (st[(0 + k) * L.plane + c] + st[(4 + k) * L.plane + c]) +
-                             (st[(8 + k) * L.plane + c] + st[(12 + k) * L.plane + c]);
+            const double v = (st[qoff(0 + k, L.plane, c)] + st[qoff(4 + k, L.plane, c)]) +
+                             (st[qoff(8 + k, L.plane, c)] + st[qoff(12 + k, L.plane, c)]);
             fix_accumulate(acc[k], acc[4 + k], v, -2 * L.level);
         }
     }
@@ -892,17 +1013,16 @@ __global__ void avgdown_kernel(LevelDev C, LevelDev F, const Item* __restrict__ 
         const double* p10 = composite_src(F, F.flags[k10]);
         const double* p01 = composite_src(F, F.flags[k01]);
         const double* p11 = composite_src(F, F.flags[k11]);
-        for (int q = 0; q < 16; q++) {
-            const long long o = (long long)q * F.plane;
-            out[(long long)q * C.plane + c] = ((p00[o + k00] + p11[o + k11]) + (p10[o + k10] + p01[o + k01])) * 0.25;
-        }
+        for (int q = 0; q < 16; q++)
+            out[qoff(q, C.plane, c)] = ((p00[qoff(q, F.plane, k00)] + p11[qoff(q, F.plane, k11)]) +
+                                        (p10[qoff(q, F.plane, k10)] + p01[qoff(q, F.plane, k01)])) * 0.25;
     }
 }
 
 __device__ __forceinline__ double comp_rho(const LevelDev& L, long long c) {
     const uint32_t fl = L.flags[c];
     const double* s = composite_src(L, fl);
-    return (s[0 * L.plane + c] + s[4 * L.plane + c]) + (s[8 * L.plane + c] + s[12 * L.plane + c]);
+    return (s[qoff(0, L.plane, c)] + s[qoff(4, L.plane, c)]) + (s[qoff(8, L.plane, c)] + s[qoff(12, L.plane, c)]);
 }
 
 // Normalised density-gradient indicator: tag when
@@ -940,8 +1060,8 @@ __global__ void tag_kernel(LevelDev L, const Item* __restrict__ items, int nitem
 __device__ __forceinline__ void comp_W(const LevelDev& L, long long c, double W[4]) {
     const double* s = composite_src(L, L.flags[c]);
     for (int k = 0; k < 4; k++)
-        W[k] = (s[(0 + k) * L.plane + c] + s[(4 + k) * L.plane + c]) +
-               (s[(8 + k) * L.plane + c] + s[(12 + k) * L.plane + c]);
+        W[k] = (s[qoff(0 + k, L.plane, c)] + s[qoff(4 + k, L.plane, c)]) +
+               (s[qoff(8 + k, L.plane, c)] + s[qoff(12 + k, L.plane, c)]);
 }
 
 // Flux-jump sensor of Sec. 3.4, Eq. amr-sigma, first pass: the maxima
@@ -1062,7 +1182,7 @@ __global__ void merge_kernel(LevelDev L, const Item* __restrict__ items, int nit
         if (x >= L.nx || y >= L.ny) continue;
         const long long c = (long long)y * L.pitch + x;
         const int sb = state_buf(L);
-        for (int q = 0; q < 16; q++) L.buf[sb][q * L.plane + c] = L.buf[sb ^ 1][q * L.plane + c];
+        for (int q = 0; q < 16; q++) L.buf[sb][qoff(q, L.plane, c)] = L.buf[sb ^ 1][qoff(q, L.plane, c)];
     }
 }
 
@@ -1096,17 +1216,15 @@ __global__ void split_kernel(LevelDev C, LevelDev F, const Item* __restrict__ it
         double* fo = F.buf[state_buf(F)];
         const long long k00 = (long long)(2 * y) * F.pitch + 2 * x;
         for (int q = 0; q < 16; q++) {
-            const long long o = (long long)q * C.plane;
-            const double fc = st[o + c];
-            const double vE = nsrc[0][o + nb[0]], vW = nsrc[1][o + nb[1]];
-            const double vN = nsrc[2][o + nb[2]], vS = nsrc[3][o + nb[3]];
+            const double fc = st[qoff(q, C.plane, c)];
+            const double vE = nsrc[0][qoff(q, C.plane, nb[0])], vW = nsrc[1][qoff(q, C.plane, nb[1])];
+            const double vN = nsrc[2][qoff(q, C.plane, nb[2])], vS = nsrc[3][qoff(q, C.plane, nb[3])];
             const double sx = (ok[0] && ok[1]) ? minmod(fc - vW, vE - fc) : 0.0;
             const double sy = (ok[2] && ok[3]) ? minmod(fc - vS, vN - fc) : 0.0;
-            const long long of = (long long)q * F.plane;
-            fo[of + k00] = fc + (sx * -0.25 + sy * -0.25);
-            fo[of + k00 + 1] = fc + (sx * 0.25 + sy * -0.25);
-            fo[of + k00 + F.pitch] = fc + (sx * -0.25 + sy * 0.25);
-            fo[of + k00 + F.pitch + 1] = fc + (sx * 0.25 + sy * 0.25);
+            fo[qoff(q, F.plane, k00)] = fc + (sx * -0.25 + sy * -0.25);
+            fo[qoff(q, F.plane, k00 + 1)] = fc + (sx * 0.25 + sy * -0.25);
+            fo[qoff(q, F.plane, k00 + F.pitch)] = fc + (sx * -0.25 + sy * 0.25);
+            fo[qoff(q, F.plane, k00 + F.pitch + 1)] = fc + (sx * 0.25 + sy * 0.25);
         }
     }
 }
@@ -1189,10 +1307,22 @@ bool sweep_variant_needs_om_minus1(int v) {
     return false;
 }
 
+cudaError_t launch_sensor(const LevelDev* levs, const Item* items, int n, int kk, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int g = tile_grid(n, 0);
+    sensor_prep_kernel<<<g, CTA_THREADS, 0, s>>>(levs, items, n, kk);
+    sensor_rate_kernel<<<g, CTA_THREADS, 0, s>>>(levs, items, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sweep(const LevelDev* levs, const Item* items, int n, int kk, int kkp, int max_ctas, int variant,
-                         cudaStream_t s) {
+                         cudaStream_t s, bool sensor) {
     if (n <= 0) return cudaSuccess;
     const int g = tile_grid(n, max_ctas);
+    if (sensor) {  // per-cell relaxation parameters: one form of the sweep
+        sweep_kernel<SW_SENSOR, 2><<<g, CTA_THREADS, 0, s>>>(levs, items, n, kk, kkp);
+        return cudaGetLastError();
+    }
     switch (variant) {
 #define X(id, P, B) case id: sweep_kernel<P, B><<<g, CTA_THREADS, 0, s>>>(levs, items, n, kk, kkp); break;
         VLBM_SWEEP_VARIANTS(X)

@@ -8,7 +8,8 @@
 namespace vlbm {
 
 cudaError_t launch_sweep(const LevelDev* levs, const Item* items, int n, int kk, int kkp, int max_ctas, int variant,
-                         cudaStream_t s);
+                         cudaStream_t s, bool sensor = false);
+cudaError_t launch_sensor(const LevelDev* levs, const Item* items, int n, int kk, cudaStream_t s);
 int sweep_variants();
 bool sweep_variant_needs_om_minus1(int v);
 int task_kernel_ctas(int variant);

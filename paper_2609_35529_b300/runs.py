@@ -1,7 +1,8 @@
 """End-to-end runs of the paper's 2-D workloads on the GPU, with the checks
 each one is about.  One JSON line per run on stdout.
 
-  python -m paper_2609_35529_b300.runs [pulse] [vortex] [riemann] [shockbubble[=steps,every,schedule]]
+  python -m paper_2609_35529_b300.runs [pulse] [vortex] [riemann] [riemann_sensor]
+                                      [shockbubble[=steps,every,schedule]]
 
 pulse        two-level Gaussian pulse, periodic 64^2, 200 coarse steps:
              per-step conservation (fused audit) and the uniform-state run
@@ -11,6 +12,7 @@ vortex       advected isentropic vortex, N = 128, 256, 512 with a central
              order, and the same for uniform grids of N and 2N
 riemann      Lax-Liu configuration 3, 1024^2, three levels, t = 0.3:
              throughput, x<->y symmetry of the result (bitwise)
+riemann_sensor  the same with beta_max = 1 and the sensor-driven relaxation
 shockbubble  adaptive shock-bubble, 2048 x 1024, up to three levels,
              regrid every 4 coarse steps, 4000 steps: conservation audited
              across every regrid, throughput including regrids
@@ -137,6 +139,35 @@ def run_riemann():
           "rho_min": float(W[0][act].min()), "rho_max": float(W[0][act].max())})
 
 
+def run_riemann_sensor(N=1024, nlev=3):
+    """Lax-Liu 3 with beta_max = 1 and the sensor-driven relaxation (beta
+    between 0.5 and 1, C = 16): constant beta = 1 (or 0.9) loses positivity
+    on this problem; with the sensor the run reaches t = 0.3."""
+    cs = I.riemann3(N=N, nlev=nlev, beta=1.0)
+    h = V.Hierarchy.from_case(cs)
+    h.set_sensor(True, beta_min=0.5, c_sensor=16.0)
+    lups = h.info()["lups_per_step"]
+    h.advance(4)
+    h.sync()
+    t0 = now()
+    h.advance(cs.steps - 4)
+    h.sync()
+    el = now() - t0
+    W, act = h.get_conserved(0)
+    p = 0.4 * (W[3] - 0.5 * (W[1] ** 2 + W[2] ** 2) / W[0])
+    sym = True
+    for l in range(cs.nlev):
+        f = h.get_populations(l).reshape(4, 4, *h.shapes[l])
+        a, b = h.layout(l)
+        act_l = (a == 1) & (b == 0)
+        ft = f.transpose(0, 1, 3, 2)[[2, 3, 0, 1]][:, [0, 2, 1, 3]]
+        sym = sym and bool(np.array_equal(f[:, :, act_l], ft[:, :, act_l]))
+    emit({"run": "riemann3-sensor", "N": N, "levels": nlev, "steps": cs.steps, "lups_per_step": lups,
+          "wall_s": el, "mlups": lups * (cs.steps - 4) / el / 1e6, "transpose_symmetric_bitwise": sym,
+          "rho_min": float(W[0][act].min()), "rho_max": float(W[0][act].max()), "p_min": float(p[act].min()),
+          "beta": [0.5, 1.0], "c_sensor": 16.0})
+
+
 def run_shockbubble(steps=4000, every=4, schedule=2):
     """The adaptive run; the totals are audited (exactly) before and after
     every regrid.  schedule 2 (auto) keeps the per-phase launches on layouts
@@ -176,7 +207,8 @@ def main(argv=None):
     which = (argv if argv is not None else sys.argv[1:]) or ["pulse", "vortex", "riemann", "shockbubble"]
     for w in which:
         name, _, arg = w.partition("=")
-        fn = {"pulse": run_pulse, "vortex": run_vortex, "riemann": run_riemann, "shockbubble": run_shockbubble}[name]
+        fn = {"pulse": run_pulse, "vortex": run_vortex, "riemann": run_riemann, "riemann_sensor": run_riemann_sensor,
+              "shockbubble": run_shockbubble}[name]
         fn(*[int(a) for a in arg.split(",")]) if arg else fn()
 
 

@@ -93,6 +93,7 @@ def lib():
         "vlbm_sync": [vp],
         "vlbm_get_info": [vp, C.POINTER(vlbm_info)],
         "vlbm_host_times": [vp, dp],
+        "vlbm_set_sensor": [vp, i32, C.c_double, C.c_double, C.c_double],
         "vlbm_profile": [vp, i64, C.POINTER(vlbm_kernel_time), i32, C.POINTER(i32)],
         "vlbm_set_step_totals": [vp, i32],
         "vlbm_checkpoint_size": [vp, C.POINTER(C.c_size_t)],
@@ -297,6 +298,11 @@ class Hierarchy:
         return {"nlev": i.nlev, "nx": list(i.nx[: i.nlev]), "ny": list(i.ny[: i.nlev]),
                 "active_cells": list(i.active_cells[: i.nlev]), "lups_per_step": i.lups_per_step,
                 "device_bytes": i.device_bytes, "steps": i.steps, "c": i.c, "beta": i.beta}
+
+    def set_sensor(self, on=True, beta_min=0.5, c_sensor=16.0, eps=1e-30):
+        """Sensor-driven relaxation (vlbm_set_sensor): beta_max is the
+        hierarchy's beta; the flux maxima are fixed from the current state."""
+        _check(self._h, lib().vlbm_set_sensor(self._h, int(on), beta_min, c_sensor, eps))
 
     HOST_TIMERS = ("tag", "layout", "regrid", "build", "tasks", "capture", "regrids", "task_lists")
 

@@ -460,6 +460,110 @@ def test_flux_jump_sensor_uses_the_max_norm_over_fields():
 
 
 # ----------------------------------------------------------------------
+# sensor-driven relaxation (Sec. 2.2, Eq. sensor-B)
+# ----------------------------------------------------------------------
+
+def sensor_level0(rho, u, v, p, beta=1.0, periodic=True, **kw):
+    ny, nx = rho.shape
+    bc = (0, 0, 0, 0) if periodic else (1, 1, 1, 1)
+    h = O.Hierarchy(nx, ny, 1, 2, bc, 1.4, 10.0, beta, None)
+    h.set_layout([])
+    h.set_state(0, I.conserved(rho, u, v, p))
+    h.set_sensor(True, **kw)
+    return h
+
+
+def test_sensor_with_zero_gain_is_the_constant_beta_scheme_bitwise():
+    """C_sensor = 0 clips to 0, so beta = beta_max on every cell and the run
+    is the constant-beta run bit for bit (three levels, ragged, periodic)."""
+    nx0, ny0 = 44, 36
+    refs = I.box_refs(nx0, ny0, 3, [(0, 8, 8, 16, 16)])
+    refs[1][24:40, 24:40] = 1
+    cs = I.smooth_random(nx0, ny0, 3, refs, seed=61, amp=0.25, beta=0.85, steps=7)
+    a, b = make(cs), make(cs)
+    b.set_sensor(True, beta_min=0.5, c_sensor=0.0)
+    a.advance(cs.steps)
+    b.advance(cs.steps)
+    for l in range(3):
+        assert np.array_equal(a.get_f(l), b.get_f(l))
+
+
+def test_sensor_keeps_beta_max_in_uniform_flow_shear_and_expansion():
+    """No compression, no sensor response: a uniform moving state, a shear
+    layer u(y) (div u = 0, the Ducros gate closes) and a pure expansion
+    (div u > 0) keep beta = beta_max on every cell, however large C."""
+    ny, nx = 16, 24
+    one = np.ones((ny, nx))
+    h = sensor_level0(one, 0.3 * one, -0.2 * one, one, c_sensor=1e6)
+    assert np.all(h.sensor_beta(0) == 1.0)
+    yy = np.arange(ny)[:, None] * one
+    h = sensor_level0(one, np.where(yy < 8, 0.5, -0.5), 0 * one, one, c_sensor=1e6)
+    assert np.all(h.sensor_beta(0) == 1.0)
+    xx = np.arange(nx)[None, :] * one
+    h = sensor_level0(one, 0.01 * xx, 0 * one, one, periodic=False, c_sensor=1e6)
+    assert np.all(h.sensor_beta(0) == 1.0)
+
+
+def test_sensor_lowers_beta_only_at_a_compression():
+    """A compression band (u falling from +0.5 to -0.5 over two cells, with
+    the pressure jump of a shock) drives beta to beta_min there for a large
+    gain, while cells more than two cells away (beyond the 3 x 3 filter of
+    the 3-point differences) keep beta_max; beta stays in [beta_min, beta_max]."""
+    ny, nx = 8, 32
+    one = np.ones((ny, nx))
+    xx = np.arange(nx)[None, :] * one
+    u = np.clip((15.5 - xx) * 0.5, -0.5, 0.5)
+    p = np.where(xx < 16, 2.0, 1.0)
+    h = sensor_level0(one, u, 0 * one, p, periodic=False, beta_min=0.5, c_sensor=1e6)
+    b = h.sensor_beta(0)
+    assert np.all((b >= 0.5) & (b <= 1.0))
+    assert np.all(b[:, 15:17] == 0.5)
+    assert np.all(b[:, :11] == 1.0) and np.all(b[:, 21:] == 1.0)
+
+
+def test_sensor_run_conserves_exactly():
+    """beta varies per cell, W stays a collision invariant cell by cell
+    (Eq. 6), so the totals of a three-level periodic run with the sensor
+    acting stay at round-off."""
+    n = 40
+    refs = I.box_refs(n, n, 3, [(0, 8, 8, 16, 16)])
+    refs[1][24:40, 24:40] = 1
+    cs = I.smooth_random(n, n, 3, refs, seed=67, amp=0.35, beta=1.0, steps=8)
+    h = make(cs)
+    h.set_sensor(True, beta_min=0.5, c_sensor=20.0)
+    b = h.sensor_beta(0)
+    assert b[b > 0].min() < 1.0  # the sensor acts somewhere
+    t0, a0 = h.totals()
+    h.advance(cs.steps)
+    t1, _ = h.totals()
+    assert np.all(np.abs(t1 - t0) / a0 < 1e-14)
+
+
+def test_sensor_keeps_lax_liu_3_physical_where_constant_beta_fails():
+    """Lax-Liu configuration 3 on 128^2 to t = 0.3: with a constant beta of
+    0.9 or 1.0 the scheme loses positivity, with the sensor (beta between 0.5
+    and 1, C = 16) density and pressure stay positive to the end."""
+    cs = I.riemann3(N=128, nlev=1, beta=1.0)
+
+    def physical_to_end(beta, sensor):
+        o = O.Hierarchy(cs.nx0, cs.ny0, 1, 2, cs.bc, cs.gamma, cs.c, beta, cs.inflow)
+        o.set_layout([])
+        o.set_state(0, cs.W[0])
+        if sensor:
+            o.set_sensor(True, beta_min=0.5, c_sensor=16.0)
+        for _ in range(0, cs.steps, 25):
+            o.advance(25)
+            W, _ = o.get_W(0)
+            p = 0.4 * (W[3] - 0.5 * (W[1] ** 2 + W[2] ** 2) / W[0])
+            if not (np.all(np.isfinite(p)) and W[0].min() > 0 and p.min() > 0):
+                return False
+        return True
+
+    assert not physical_to_end(0.9, False)
+    assert physical_to_end(1.0, True)
+
+
+# ----------------------------------------------------------------------
 # the paper's validation numbers
 # ----------------------------------------------------------------------
 

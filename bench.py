@@ -51,12 +51,12 @@ BYTES_PER_LUP = 256
 # (DFMA/DADD/DMUL thread-instructions per cell update in the sweep: 67.1)
 FP64_OPS_PER_LUP = 67
 # DRAM traffic of the task kernel per cell update: dram__bytes_read.sum +
-# dram__bytes_write.sum of two launches of 16 coarse steps (variant 1, audit
-# off, 512 MB L2 flush before each launch), ncu --nvtx capture of this bench's
-# roofline launches (profiles/task_kernel_vortex512.md): 3.025e9 B per
-# 11 534 336 cell updates.  Valid for the kernel as captured; to be measured
-# again whenever the kernel changes.
-TASK_KERNEL_DRAM_BYTES_PER_LUP = 262.3
+# dram__bytes_write.sum of a launch of 16 coarse steps (variant 1, audit off,
+# 512 MB L2 flush before each launch), ncu --nvtx capture of this bench's
+# roofline launches (profiles/task_kernel_vortex512.md): 2.649e9 B per
+# 11 534 336 cell updates.  Valid for the kernel as captured (paired-field
+# layout); to be measured again whenever the kernel changes.
+TASK_KERNEL_DRAM_BYTES_PER_LUP = 229.7
 TRAFFIC_VARIANT = 1
 
 

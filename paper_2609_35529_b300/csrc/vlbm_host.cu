@@ -288,6 +288,13 @@ struct Batch {
         if (exec1) cudaGraphExecDestroy(exec1);
         if (execG) cudaGraphExecDestroy(execG);
         exec1 = execG = nullptr;
+        if (stage_pending) cudaEventSynchronize(stage_ev);
+        stage_pending = false;
+        if (stage) cudaFreeHost(stage);
+        stage = nullptr;
+        stage_cap = 0;
+        if (stage_ev) cudaEventDestroy(stage_ev);
+        stage_ev = nullptr;
         levs.release(*mem);
         for (int l = 0; l < VLBM_MAX_LEVELS; l++) {
             sweep[l].release(*mem);
@@ -370,17 +377,58 @@ struct Batch {
             pw.push_back(h->words);
             sensor = sensor || h->sensor_on;
         }
-        levs.upload(*mem, tab, s);
+        // uploads from a pinned staging buffer: no stream synchronisation,
+        // the engine's queue keeps running while a batch is rebuilt
+        size_t need = tab.size() * sizeof(LevelDev) + pw.size() * sizeof(int*) + au.size() * sizeof(Item);
+        for (int l = 0; l < VLBM_MAX_LEVELS; l++) need += (sw[l].size() + cl[l].size()) * sizeof(Item);
+        stage_begin(need + 16 * 256);
+        staged(levs, tab, s);
         for (int l = 0; l < VLBM_MAX_LEVELS; l++) {
-            sweep[l].upload(*mem, sw[l], s);
-            close[l].upload(*mem, cl[l], s);
+            staged(sweep[l], sw[l], s);
+            staged(close[l], cl[l], s);
         }
-        par.upload(*mem, pw, s);
-        audit_items.upload(*mem, au, s);
-        VCK(cudaStreamSynchronize(s));  // the host tables above go out of scope
+        staged(par, pw, s);
+        staged(audit_items, au, s);
+        stage_end(s);
         // the one-step and G-step graphs (and task lists) are built when first used
         seg_ok[0] = seg_ok[1] = false;
         valid = true;
+    }
+
+    // Pinned staging of the table uploads.  A build waits (normally not at
+    // all) for the copies of the previous build before reusing the buffer.
+    char* stage = nullptr;
+    size_t stage_cap = 0, stage_off = 0;
+    cudaEvent_t stage_ev = nullptr;
+    bool stage_pending = false;
+    std::vector<std::pair<size_t, size_t>> stage_parts;
+    void stage_begin(size_t need) {
+        if (stage_pending) VCK(cudaEventSynchronize(stage_ev));
+        stage_pending = false;
+        stage_off = 0;
+        if (need > stage_cap) {  // the buffer is idle here
+            if (stage) cudaFreeHost(stage);
+            stage = nullptr;
+            stage_cap = std::max(2 * stage_cap, need + (size_t)(1 << 20));
+            VCK(cudaMallocHost((void**)&stage, stage_cap));
+        }
+    }
+    template <class T>
+    void staged(DArr<T>& d, const std::vector<T>& v, cudaStream_t s) {
+        d.ensure(*mem, v.size());
+        d.n = v.size();
+        const size_t b = v.size() * sizeof(T);
+        if (!b) return;
+        const size_t off = (stage_off + 255) & ~size_t(255);
+        if (off + b > stage_cap) throw Fail{VLBM_ERR_ARG, "staging buffer too small"};  // sized by build()
+        std::memcpy(stage + off, v.data(), b);
+        VCK(cudaMemcpyAsync(d.p, stage + off, b, cudaMemcpyHostToDevice, s));
+        stage_off = off + b;
+    }
+    void stage_end(cudaStream_t s) {
+        if (!stage_ev) VCK(cudaEventCreateWithFlags(&stage_ev, cudaEventDisableTiming));
+        VCK(cudaEventRecord(stage_ev, s));
+        stage_pending = true;
     }
 
     // eager launches with events around each kernel (profiling)
@@ -888,9 +936,15 @@ struct vlbm_engine {
         bool live = false;
         bool adaptive() const { return regrid_every > 0 && h->cfg.tag_tol > 0; }
         bool phased() const { return adaptive() || h->sensor_on; }
+        bool paused = false;           // waiting for its regrid (not in a batch)
+        long long regridded_at = -1;   // step count of its last regrid
+        cudaEvent_t ev = nullptr;      // end of its last step on the engine's stream
     };
     std::vector<Res> res;
     bool dirty = true;
+    bool regridded = false;  // an adaptive resident changed its layout since the last rebuild
+    bool admitted = true;    // a resident was admitted or released since the last rebuild
+    cudaStream_t hi = nullptr;  // high-priority stream of the residents' regrids
     std::string err = "no error";
 };
 
@@ -1659,6 +1713,9 @@ vlbm_status vlbm_engine_admit(vlbm_engine* e, vlbm_hier* h, int64_t coarse_steps
     e->res[s].h = h;
     e->res[s].target = coarse_steps;
     e->res[s].done = 0;
+    e->res[s].paused = false;
+    e->res[s].regridded_at = -1;
+    e->admitted = true;
     e->res[s].regrid_every = regrid_every;
     e->res[s].lups = 0;
     e->res[s].live = true;
@@ -1675,6 +1732,7 @@ vlbm_status vlbm_engine_release(vlbm_engine* e, int32_t slot) {
     e->res[slot].live = false;
     e->res[slot].h = nullptr;
     e->dirty = true;
+    e->admitted = true;
     return VLBM_OK;
 }
 
@@ -1684,55 +1742,68 @@ vlbm_status vlbm_engine_advance(vlbm_engine* e, int32_t max_steps, int32_t* fini
     if (nfinished) *nfinished = 0;
     if (steps) *steps = 0;
     try {
-        // adaptive residents regrid on their own schedule (between steps)
-        for (auto& r : e->res) {
-            if (!r.live || !r.adaptive()) continue;
-            if (r.done > 0 && r.done % r.regrid_every == 0 && r.done < r.target) {
-                VCK(cudaStreamSynchronize(e->stream));
-                vlbm_hier* h = r.h;
-                vlbm_engine* keep = h->engine;
-                h->engine = nullptr;  // regrid runs on the hierarchy's own stream
-                vlbm_status st = vlbm_regrid(h, nullptr, 0);
-                h->engine = keep;
+        // 1. adaptive residents due for a regrid leave the batches; an event
+        //    marks the end of their last step on the engine's stream
+        std::vector<size_t> due;
+        for (size_t i = 0; i < e->res.size(); i++) {
+            auto& r = e->res[i];
+            if (!r.live || !r.adaptive() || r.paused) continue;
+            if (r.done > 0 && r.done % r.regrid_every == 0 && r.done < r.target && r.regridded_at != r.done) {
+                if (!r.ev) VCK(cudaEventCreateWithFlags(&r.ev, cudaEventDisableTiming));
+                VCK(cudaEventRecord(r.ev, e->stream));
+                r.paused = true;
+                due.push_back(i);
                 e->dirty = true;
-                if (st != VLBM_OK) throw Fail{st, std::string("regrid: ") + h->err};
-                VCK(cudaStreamSynchronize(h->stream));  // its kernels ran on the hierarchy's stream
             }
         }
         if (e->dirty) {
-            e->batch.members.clear();
-            e->phased.members.clear();
+            // rebuild a batch only when its members changed (or, for the
+            // adaptive batch, when one of them regridded): the persistent
+            // kernel's tables and graph survive the adaptive residents' regrids
+            std::vector<vlbm_hier*> ms, mp;
             for (auto& r : e->res)
-                if (r.live && r.done < r.target) (r.phased() ? e->phased : e->batch).members.push_back(r.h);
-            if (!e->batch.members.empty()) e->batch.build(e->stream);
-            if (!e->phased.members.empty()) e->phased.build(e->stream);
+                if (r.live && !r.paused && r.done < r.target) (r.phased() ? mp : ms).push_back(r.h);
+            // (an admission or release since the last rebuild always counts as
+            // a change: a new hierarchy may sit at a released one's address)
+            if (e->admitted || ms != e->batch.members || !e->batch.valid) {
+                e->batch.members = ms;
+                if (!ms.empty()) e->batch.build(e->stream);
+            }
+            if (e->admitted || e->regridded || mp != e->phased.members || !e->phased.valid) {
+                e->phased.members = mp;
+                if (!mp.empty()) e->phased.build(e->stream);
+            }
+            e->admitted = e->regridded = false;
             e->dirty = false;
         }
-        // as many steps as no resident finishes or regrids in between
+        // 2. as many steps of the other residents as none of them finishes or
+        //    regrids in between
         long long k = max_steps;
         bool any = false;
         for (const auto& r : e->res) {
-            if (!r.live || r.done >= r.target) continue;
+            if (!r.live || r.paused || r.done >= r.target) continue;
             any = true;
             k = std::min(k, r.target - r.done);
             if (r.adaptive()) k = std::min<long long>(k, r.regrid_every - r.done % r.regrid_every);
         }
-        if (!any) return VLBM_OK;
+        if (!any) k = 0;
         // static residents: one graph of the persistent kernel per step;
         // adaptive residents: their per-phase launches issued directly (their
         // batch changes at nearly every step, when one of them regrids, so
         // capturing and instantiating a graph each time would cost more than
         // the launches)
-        cudaGraphExec_t gs = e->batch.members.empty() ? nullptr : e->batch.exec_for(0, e->stream);
-        const bool phased = !e->phased.members.empty();
-        for (long long i = 0; i < k; i++) {
-            if (gs) VCK(cudaGraphLaunch(gs, e->stream));
-            if (phased) e->phased.one_step(e->stream);
+        if (k > 0) {
+            cudaGraphExec_t gs = e->batch.members.empty() ? nullptr : e->batch.exec_for(0, e->stream);
+            const bool phased = !e->phased.members.empty();
+            for (long long i = 0; i < k; i++) {
+                if (gs) VCK(cudaGraphLaunch(gs, e->stream));
+                if (phased) e->phased.one_step(e->stream);
+            }
         }
         int nf = 0;
         for (size_t i = 0; i < e->res.size(); i++) {
             auto& r = e->res[i];
-            if (!r.live || r.done >= r.target) continue;
+            if (!r.live || r.paused || r.done >= r.target || k == 0) continue;
             r.done += k;
             r.h->steps += k;
             r.h->layout_steps += k;
@@ -1744,6 +1815,38 @@ vlbm_status vlbm_engine_advance(vlbm_engine* e, int32_t max_steps, int32_t* fini
                 nf++;
                 e->dirty = true;
             }
+        }
+        // 3. the paused residents' regrids, on their own streams after their
+        //    events: the host work overlaps the steps just queued (their step
+        //    counts were not advanced above)
+        //    The regrid runs on the engine's high-priority stream, so that
+        //    its small kernels are scheduled at the next launch boundary
+        //    instead of queueing behind every step already queued.
+        if (!due.empty() && !e->hi) {
+            int lo = 0, hi = 0;
+            VCK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+            VCK(cudaStreamCreateWithPriority(&e->hi, cudaStreamNonBlocking, hi));
+        }
+        for (size_t i : due) {
+            auto& r = e->res[i];
+            vlbm_hier* h = r.h;
+            VCK(cudaStreamWaitEvent(e->hi, r.ev, 0));
+            vlbm_engine* keep = h->engine;
+            cudaStream_t own = h->stream;
+            h->engine = nullptr;  // vlbm_regrid refuses engine residents
+            h->stream = e->hi;
+            h->mem.s = e->hi;
+            vlbm_status st = vlbm_regrid(h, nullptr, 0);
+            cudaError_t ce = cudaStreamSynchronize(e->hi);
+            h->stream = own;
+            h->mem.s = own;
+            h->engine = keep;
+            if (st != VLBM_OK) throw Fail{st, std::string("regrid: ") + h->err};
+            VCK(ce);
+            r.regridded_at = r.done;
+            r.paused = false;
+            e->dirty = true;
+            e->regridded = true;
         }
         if (nfinished) *nfinished = nf;
         if (steps) *steps = (int32_t)k;
@@ -1773,11 +1876,15 @@ vlbm_status vlbm_engine_step(vlbm_engine* e, int32_t* finished, int32_t* nfinish
 void vlbm_engine_destroy(vlbm_engine* e) {
     if (!e) return;
     cudaStreamSynchronize(e->stream);
-    for (auto& r : e->res)
+    for (auto& r : e->res) {
         if (r.live && r.h) r.h->engine = nullptr;
+        if (r.ev) cudaEventDestroy(r.ev);
+        r.ev = nullptr;
+    }
     e->batch.release();
     e->phased.release();
     cudaStreamSynchronize(e->stream);
+    if (e->hi) cudaStreamDestroy(e->hi);
     if (e->own_stream) cudaStreamDestroy(e->stream);
     delete e;
 }

@@ -324,11 +324,13 @@ vlbm_status vlbm_checkpoint_load(vlbm_hier* h, const void* blob, size_t bytes);
  * report conservation to round-off; this checks it at every coarse step).
  * With `on`, every coarse step taken by vlbm_advance records the totals of
  * the state at the START of that step: sum_l 4^-l sum_active W_k and the
- * same of |W_k| (k = rho, rho u, rho v, rho E).  The sums are accumulated
- * inside the sweep's first sub-step on every level in 192-bit fixed point
- * on the integer pipes (resolution 2^-128), so they are exact, independent
- * of the launch configuration, and rounded once to binary64 (the correctly
- * rounded sum); no extra pass over the populations is made.  Requires the
+ * same of |W_k| (k = rho, rho u, rho v, rho E).  The sweep's first
+ * sub-step on every level keeps the moments of its cells; reduction tasks of
+ * the same persistent launch, scheduled between the later sweeps, sum them
+ * in 192-bit fixed point on the integer pipes (resolution 2^-128), so the
+ * totals are exact, independent of the launch configuration, and rounded
+ * once to binary64 (the correctly rounded sum); no extra pass over the
+ * populations is made.  Requires the
  * persistent schedule (vlbm_tuning.schedule = 1), else ERR_ARG.
  * vlbm_get_step_totals synchronises and returns, oldest first, the rows
  * recorded since the previous call (at most the 4096 most recent), each

@@ -486,11 +486,12 @@ static void gather(const OLevel* L, const double* a, size_t c, double v[16]) {
  *   s_k   = dx (div Q)_k / max_{x,alpha} |Q_{alpha,k}|, central differences,
  *           so s_k = g_k / (2 qmax_k) with g_k = (Qx_k(E) - Qx_k(W)) +
  *           (Qy_k(N) - Qy_k(S)); qmax_k fixed when the sensor is switched on
- *   s     = ((1/(D+2)) sum_k s_k^2)^(1/2), D = 2
+ *   s     = ((1/(D+2)) sum_k s_k^2)^(1/2), D = 2 (summed as
+ *           (s_0^2 + s_3^2) + (s_1^2 + s_2^2))
  *   theta = dil^2 / (dil^2 + vort^2 + eps) where dil < 0, else 0 (Ducros-
  *           type), dil = (u(E) - u(W)) + (v(N) - v(S)),
  *           vort = (v(E) - v(W)) - (u(N) - u(S))  (undivided differences)
- *   s_bar, theta_bar = 3 x 3 box filters
+ *   s_bar, theta_bar = 3 x 3 box filters (box9)
  *   beta  = beta_max - (beta_max - beta_min) clip(C s_bar theta_bar, 0, 1)
  * A neighbour that is not an active cell of the level (covered, off the
  * level, beyond a non-periodic side) takes the centre cell's value. */
@@ -501,6 +502,16 @@ static double nbv(const OHier* H, const OLevel* L, const double* a, int x, int y
         if (is_active(L, cn)) return a[cn];
     }
     return a[cidx(L, x, y)];
+}
+
+/* Sum of a 3 x 3 neighbourhood, grouped so that swapping x and y gives
+ * the same rounding: centre + ((E + W) + (N + S)) + ((NE + SW) + (NW + SE)). */
+static double box9(const OHier* H, const OLevel* L, const double* a, int x, int y) {
+    double edges = (nbv(H, L, a, x, y, 1, 0) + nbv(H, L, a, x, y, -1, 0)) +
+                   (nbv(H, L, a, x, y, 0, 1) + nbv(H, L, a, x, y, 0, -1));
+    double corners = (nbv(H, L, a, x, y, 1, 1) + nbv(H, L, a, x, y, -1, -1)) +
+                     (nbv(H, L, a, x, y, -1, 1) + nbv(H, L, a, x, y, 1, -1));
+    return (a[cidx(L, x, y)] + edges) + corners;
 }
 
 /* beta[c] for every active cell of level l (other cells untouched). */
@@ -534,7 +545,9 @@ static void sensor_beta(const OHier* H, const OLevel* L, double* beta) {
                            (nbv(H, L, qy, x, y, 0, 1) - nbv(H, L, qy, x, y, 0, -1));
                 sh[k] = g * H->iq[k];
             }
-            st[c] = sqrt(0.25 * ((sh[0] * sh[0] + sh[1] * sh[1]) + (sh[2] * sh[2] + sh[3] * sh[3])));
+            /* fields paired (rho, rho E), (rho u, rho v): the grouping is
+             * the same after swapping x and y */
+            st[c] = sqrt(0.25 * ((sh[0] * sh[0] + sh[3] * sh[3]) + (sh[1] * sh[1] + sh[2] * sh[2])));
             const double* u = pr + 8 * n;
             const double* v = pr + 9 * n;
             double dil = (nbv(H, L, u, x, y, 1, 0) - nbv(H, L, u, x, y, -1, 0)) +
@@ -548,12 +561,7 @@ static void sensor_beta(const OHier* H, const OLevel* L, double* beta) {
         for (int x = 0; x < L->nx; x++) {
             size_t c = cidx(L, x, y);
             if (!is_active(L, c)) continue;
-            double as = 0.0, at = 0.0;
-            for (int dy = -1; dy <= 1; dy++)
-                for (int dx = -1; dx <= 1; dx++) {
-                    as += nbv(H, L, st, x, y, dx, dy);
-                    at += nbv(H, L, st + n, x, y, dx, dy);
-                }
+            double as = box9(H, L, st, x, y), at = box9(H, L, st + n, x, y);
             double z = (H->csens * (H->ninth * as)) * (H->ninth * at);
             if (z < 0.0) z = 0.0;
             if (z > 1.0) z = 1.0;

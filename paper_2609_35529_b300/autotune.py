@@ -20,6 +20,8 @@ from . import vlbm as V
 DEFAULT_CANDIDATES = [
     {"variant": 1, "schedule": 1, "graph_steps": 8, "max_ctas": 0},
     {"variant": 1, "schedule": 1, "graph_steps": 16, "max_ctas": 0},
+    {"variant": 1, "schedule": 1, "graph_steps": 32, "max_ctas": 0},
+    {"variant": 1, "schedule": 1, "graph_steps": 64, "max_ctas": 0},
     {"variant": 1, "schedule": 1, "graph_steps": 4, "max_ctas": 0},
     {"variant": 0, "schedule": 1, "graph_steps": 8, "max_ctas": 0},
     {"variant": 10, "schedule": 1, "graph_steps": 8, "max_ctas": 0},

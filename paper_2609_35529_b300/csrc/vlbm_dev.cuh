@@ -21,6 +21,13 @@
 // No face tables, ghost copies or register arrays are needed.
 #pragma once
 #include <cstdint>
+#ifdef __CUDACC__
+#include <vector_types.h>
+#else
+struct int2 {
+    int x, y;
+};
+#endif
 
 namespace vlbm {
 
@@ -92,14 +99,15 @@ struct Item {
 };
 
 // A task of the persistent kernel: one tile of one phase (kind 0 = level
-// sweep, kind 1 = reflux close) of one coarse step; its dependencies are
+// sweep, kind 1 = reflux close) of one coarse step, or (kind 2) the exact
+// sums of one field (kk) over one block of audit slots; its dependencies are
 // deps[dep0 .. dep0 + ndep), indices of earlier tasks.
 struct Task {
     int lid;
     unsigned short tx, ty;
     signed char kind, kk, kkp, step;
     int dep0, ndep;
-    int aslot;  // first sub-step sweep of its coarse step: slot of its audit sums, else -1
+    int aslot;  // kind 0: the slot of its moments when audited, else -1; kind 2: the audit block
 };
 
 // One hierarchy's task list as the persistent kernel sees it.  Task level
@@ -111,6 +119,9 @@ struct Segment {
     const int* deps;
     unsigned* done;
     double* aw;                  // audited moments, AUDIT_SLOT per slot (nullptr: no audit)
+    const int2* arng;            // slot range of each audit block
+    const int* ascale;           // weight exponent of each slot
+    unsigned long long* apart;   // exact sums of each audit block, 24 words
     int* par0;                   // the hierarchy's level-0 parity word
     int ntasks, lid_base;
 };

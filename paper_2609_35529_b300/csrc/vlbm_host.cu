@@ -195,6 +195,11 @@ struct vlbm_hier {
     DArr<LevelDev> atab;   // level table for audits (rebuilt with the layout)
     DArr<Item> aitems;     // active tiles of every level (audits)
     double* hout = nullptr;  // pinned host copy of the audit result
+    // tag-driven regrid in two halves: the status words and the block flags
+    // land in pinned memory (rg_pin), rg_ev marks their arrival
+    uint8_t* rg_pin = nullptr;
+    size_t rg_cap = 0;
+    cudaEvent_t rg_ev = nullptr;
     vlbm_tuning tune{1, 0, 8, 1, 256};
     long long layout_steps = 0;  // coarse steps taken on the current layout
     // per-step conservation totals recorded by vlbm_advance (pinned ring)
@@ -516,7 +521,6 @@ struct Batch {
         VCK(launch_tasks(levs.p, segs[which].p, prefix[which].p, ctl[which].p, variant, max_ctas, s));
         if (audit && members.size() == 1) {
             auto& T = members[0]->tl[which];
-            VCK(launch_audit_slots(T.aw.p, T.arng.p, T.ascale.p, T.nblk, T.apart.p, s));
             VCK(launch_audit_segments(T.apart.p, T.abseg.p, T.nseg, T.aout.p, s));
         }
     }
@@ -576,26 +580,10 @@ void Batch::member_tasks(vlbm_hier* h, int which, int nsteps, bool aud) {
     build_tasks(lv, nsteps, tl);
     L.t.swap(tl.t);
     L.d.swap(tl.d);
-    // audit slots: the audit tasks of step st are slots [seg[st], seg[st+1])
-    std::vector<int> seg(nsteps + 1, 0);
-    if (aud) {
-        for (const Task& T : L.t)
-            if (T.aslot == -2) seg[T.step + 1]++;
-        for (int i = 0; i < nsteps; i++) seg[i + 1] += seg[i];
-    }
-    std::vector<int> fill(nsteps, 0), scale(std::max(1, seg.back()), 0);
-    for (Task& T : L.t) {
-        T.aslot = (aud && T.aslot == -2) ? seg[T.step] + fill[T.step]++ : -1;
-        if (T.aslot >= 0) scale[T.aslot] = -2 * T.lid;  // weight 4^-level
-    }
-    // reduction blocks: at most AUDIT_BLOCK_SLOTS slots each, never across steps
+    // audit slots, reduction blocks and their tasks
+    std::vector<int> scale, bseg;
     std::vector<int2> rng;
-    std::vector<int> bseg(1, 0);
-    for (int st = 0; aud && st < nsteps; st++) {
-        for (int j = seg[st]; j < seg[st + 1]; j += AUDIT_BLOCK_SLOTS)
-            rng.push_back(make_int2(j, std::min(j + AUDIT_BLOCK_SLOTS, seg[st + 1])));
-        bseg.push_back((int)rng.size());
-    }
+    const int nslots = assign_audit(L.t, L.d, nsteps, aud ? AUDIT_BLOCK_SLOTS : 0, scale, rng, bseg);
     cudaStream_t s = h->stream;
     L.dt.upload(h->mem, L.t, s);
     std::vector<int> d = L.d;
@@ -605,7 +593,7 @@ void Batch::member_tasks(vlbm_hier* h, int which, int nsteps, bool aud) {
     if (aud) {
         L.nseg = nsteps;
         L.nblk = (int)rng.size();
-        L.aw.ensure(h->mem, (size_t)std::max(1, seg.back()) * AUDIT_SLOT);
+        L.aw.ensure(h->mem, (size_t)std::max(1, nslots) * AUDIT_SLOT);
         L.ascale.upload(h->mem, scale, s);
         if (rng.empty()) rng.push_back(make_int2(0, 0));
         L.arng.upload(h->mem, rng, s);
@@ -674,6 +662,9 @@ void Batch::build_segments(int which, int nsteps, cudaStream_t s) {
         S.deps = L.dd.p;
         S.done = L.done.p;
         S.aw = aud ? L.aw.p : nullptr;
+        S.arng = aud ? L.arng.p : nullptr;
+        S.ascale = aud ? L.ascale.p : nullptr;
+        S.apart = aud ? L.apart.p : nullptr;
         S.par0 = h->words;
         S.ntasks = (int)L.t.size();
         S.lid_base = base;
@@ -911,6 +902,89 @@ void regrid_to(vlbm_hier* h, std::vector<uint8_t>* newcov, bool averaged) {
     install_layout(h, newin, newcov);
 }
 
+// Tag-driven regrid (Sec. 3.4), first half, queued on h->stream:
+// average-down, the sensor on every refinable level, the block flags, and
+// their copy -- with the hierarchy's status words -- into pinned host
+// memory; h->rg_ev completes when they have arrived.  Nothing waits here.
+void tag_begin(vlbm_hier* h) {
+    if (!(h->cfg.tag_tol > 0.0) || h->cfg.tag_buffer < 0) throw Fail{VLBM_ERR_ARG, "no tagging parameters"};
+    if (h->cfg.tag_sensor != VLBM_SENSOR_DENSITY && h->cfg.tag_sensor != VLBM_SENSOR_FLUX)
+        throw Fail{VLBM_ERR_ARG, "unknown tagging sensor"};
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = h->stream;
+    for (int l = h->nlev - 2; l >= 0; l--) {
+        h->listbuf.upload(h->mem, h->lev[l].cov, s);
+        VCK(launch_avgdown(lvdev(h, l), lvdev(h, l + 1), h->listbuf.p, (int)h->listbuf.n, s));
+    }
+    const double tol2 = h->cfg.tag_tol * h->cfg.tag_tol;
+    const bool fluxs = h->cfg.tag_sensor == VLBM_SENSOR_FLUX;
+    if (fluxs) {
+        // the flux maxima over every cell of every level
+        h->qmax.ensure(h->mem, 4);
+        VCK(cudaMemsetAsync(h->qmax.p, 0, 4 * sizeof(unsigned long long), s));
+        for (int l = 0; l < h->nlev; l++) {
+            h->listbuf.upload(h->mem, h->lev[l].in, s);
+            VCK(launch_qmax(lvdev(h, l), h->listbuf.p, (int)h->listbuf.n, h->qmax.p, s));
+        }
+    }
+    const int px = h->cfg.bc[0] == VLBM_BC_PERIODIC, py = h->cfg.bc[2] == VLBM_BC_PERIODIC;
+    size_t nb = 0;
+    for (int l = 0; l <= h->nlev - 2; l++) nb += (size_t)h->lev[l].bx * h->lev[l].by;
+    h->bflag.ensure(h->mem, std::max<size_t>(1, nb));
+    size_t off = 0;
+    for (int l = 0; l <= h->nlev - 2; l++) {
+        Level& L = h->lev[l];
+        h->stage8.ensure(h->mem, (size_t)L.nx * L.ny);
+        VCK(cudaMemsetAsync(h->stage8.p, 0, (size_t)L.nx * L.ny, s));
+        h->listbuf.upload(h->mem, L.in, s);
+        if (fluxs)
+            VCK(launch_tag_flux(lvdev(h, l), h->listbuf.p, (int)L.in.size(), h->qmax.p, h->cfg.tag_tol, h->stage8.p,
+                                s));
+        else
+            VCK(launch_tag(lvdev(h, l), h->listbuf.p, (int)L.in.size(), tol2, h->stage8.p, s));
+        VCK(launch_blockflag(h->stage8.p, L.nx, L.ny, px, py, h->cfg.tag_buffer, h->bflag.p + off, s));
+        off += (size_t)L.bx * L.by;
+    }
+    // status words first (8 bytes), then the flags
+    if (h->rg_cap < 8 + nb) {
+        if (h->rg_pin) {
+            if (h->rg_ev) VCK(cudaEventSynchronize(h->rg_ev));  // a copy into the old buffer may be in flight
+            VCK(cudaFreeHost(h->rg_pin));
+            h->rg_pin = nullptr;
+            h->rg_cap = 0;
+        }
+        VCK(cudaMallocHost((void**)&h->rg_pin, 8 + nb));
+        h->rg_cap = 8 + nb;
+    }
+    if (!h->rg_ev) VCK(cudaEventCreateWithFlags(&h->rg_ev, cudaEventDisableTiming));
+    VCK(cudaMemcpyAsync(h->rg_pin, h->words, 8, cudaMemcpyDeviceToHost, s));
+    if (nb) VCK(cudaMemcpyAsync(h->rg_pin + 8, h->bflag.p, nb, cudaMemcpyDeviceToHost, s));
+    VCK(cudaEventRecord(h->rg_ev, s));
+    h->times[VLBM_T_TAG] += ms_since(t0);
+}
+
+// Second half, once h->rg_ev has completed: the status check, the layout
+// rule on the block flags, and the conservative regrid (queued on h->stream).
+void tag_finish(vlbm_hier* h) {
+    int st[2];
+    std::memcpy(st, h->rg_pin, sizeof st);
+    if (st[1] & ST_NONPHYS) throw Fail{VLBM_ERR_NONPHYSICAL, "non-physical state (rho <= 0, p <= 0 or NaN)"};
+    if (st[1] & ST_TIMEOUT) throw Fail{VLBM_ERR_TIMEOUT, "a bounded device wait timed out"};
+    auto t0 = std::chrono::steady_clock::now();
+    std::vector<uint8_t> bflag[VLBM_MAX_LEVELS], bcov[VLBM_MAX_LEVELS];
+    size_t off = 0;
+    for (int l = 0; l <= h->nlev - 2; l++) {
+        const size_t n = (size_t)h->lev[l].bx * h->lev[l].by;
+        bflag[l].assign(h->rg_pin + 8 + off, h->rg_pin + 8 + off + n);
+        off += n;
+    }
+    layout_rule(h, bflag, bcov);
+    h->times[VLBM_T_LAYOUT] += ms_since(t0);
+    t0 = std::chrono::steady_clock::now();
+    regrid_to(h, bcov, true);
+    h->times[VLBM_T_REGRID] += ms_since(t0);
+}
+
 void invalidate(vlbm_hier* h);
 
 }  // namespace
@@ -937,14 +1011,21 @@ struct vlbm_engine {
         bool adaptive() const { return regrid_every > 0 && h->cfg.tag_tol > 0; }
         bool phased() const { return adaptive() || h->sensor_on; }
         bool paused = false;           // waiting for its regrid (not in a batch)
+        bool tagging = false;          // the first half of its regrid is queued
         long long regridded_at = -1;   // step count of its last regrid
-        cudaEvent_t ev = nullptr;      // end of its last step on the engine's stream
+        cudaEvent_t ev = nullptr;      // end of its last step, then of its regrid
     };
     std::vector<Res> res;
     bool dirty = true;
     bool regridded = false;  // an adaptive resident changed its layout since the last rebuild
     bool admitted = true;    // a resident was admitted or released since the last rebuild
     cudaStream_t hi = nullptr;  // high-priority stream of the residents' regrids
+    // the ends of the steps queued by the last two calls: a call waits for
+    // the steps queued two calls before, so the host stays at most two
+    // calls ahead of the GPU
+    cudaEvent_t lead[2] = {nullptr, nullptr};
+    bool lead_set[2] = {false, false};
+    int lead_i = 0;
     std::string err = "no error";
 };
 
@@ -953,6 +1034,26 @@ namespace {
 void invalidate(vlbm_hier* h) {
     if (h->own) h->own->valid = false;
     if (h->engine) h->engine->dirty = true;
+}
+
+// Runs fn with the hierarchy's queue and memory pool stream set to s; a
+// failure poisons the hierarchy as its own calls would.
+template <class F>
+void on_stream(vlbm_hier* h, cudaStream_t s, F&& fn) {
+    cudaStream_t own = h->stream;
+    h->stream = s;
+    h->mem.s = s;
+    try {
+        fn();
+    } catch (const Fail& f) {
+        h->stream = own;
+        h->mem.s = own;
+        h->err = f.msg;
+        if (f.st == VLBM_ERR_NONPHYSICAL || f.st == VLBM_ERR_TIMEOUT || f.st == VLBM_ERR_CUDA) h->poisoned = true;
+        throw Fail{f.st, "regrid: " + f.msg};
+    }
+    h->stream = own;
+    h->mem.s = own;
 }
 
 vlbm_status finish(vlbm_hier* h, const Fail& f) {
@@ -1006,6 +1107,11 @@ void destroy_levels(vlbm_hier* h) {
     h->aitems.release(h->mem);
     if (h->hout) cudaFreeHost(h->hout);
     h->hout = nullptr;
+    if (h->rg_pin) cudaFreeHost(h->rg_pin);
+    h->rg_pin = nullptr;
+    h->rg_cap = 0;
+    if (h->rg_ev) cudaEventDestroy(h->rg_ev);
+    h->rg_ev = nullptr;
     if (h->hist) cudaFreeHost(h->hist);
     h->hist = nullptr;
     for (auto& L : h->tl) {
@@ -1464,10 +1570,10 @@ vlbm_status vlbm_regrid_masks(vlbm_hier* h, const uint8_t* const* ref) {
 
 vlbm_status vlbm_regrid(vlbm_hier* h, const vlbm_box* boxes, int32_t nboxes) {
     return run(h, [&] {
-        check_status(h);
         auto t0 = std::chrono::steady_clock::now();
-        std::vector<uint8_t> bcov[VLBM_MAX_LEVELS];
         if (boxes || nboxes > 0) {
+            std::vector<uint8_t> bcov[VLBM_MAX_LEVELS];
+            check_status(h);
             if (nboxes < 0 || !boxes) throw Fail{VLBM_ERR_ARG, "bad boxes"};
             boxes_to_maps(h, boxes, nboxes, bcov);
             h->times[VLBM_T_LAYOUT] += ms_since(t0);
@@ -1475,62 +1581,11 @@ vlbm_status vlbm_regrid(vlbm_hier* h, const vlbm_box* boxes, int32_t nboxes) {
             regrid_to(h, bcov, false);
             h->times[VLBM_T_REGRID] += ms_since(t0);
         } else {
-            if (!(h->cfg.tag_tol > 0.0) || h->cfg.tag_buffer < 0) throw Fail{VLBM_ERR_ARG, "no tagging parameters"};
-            if (h->cfg.tag_sensor != VLBM_SENSOR_DENSITY && h->cfg.tag_sensor != VLBM_SENSOR_FLUX)
-                throw Fail{VLBM_ERR_ARG, "unknown tagging sensor"};
-            cudaStream_t s = h->stream;
-            // average-down, then tag on every refinable level
-            for (int l = h->nlev - 2; l >= 0; l--) {
-                h->listbuf.upload(h->mem, h->lev[l].cov, s);
-                VCK(launch_avgdown(lvdev(h, l), lvdev(h, l + 1), h->listbuf.p, (int)h->listbuf.n, s));
-            }
-            std::vector<uint8_t> bflag[VLBM_MAX_LEVELS];
-            const double tol2 = h->cfg.tag_tol * h->cfg.tag_tol;
-            const bool fluxs = h->cfg.tag_sensor == VLBM_SENSOR_FLUX;
-            if (fluxs) {
-                // the flux maxima over every cell of every level
-                h->qmax.ensure(h->mem, 4);
-                VCK(cudaMemsetAsync(h->qmax.p, 0, 4 * sizeof(unsigned long long), s));
-                for (int l = 0; l < h->nlev; l++) {
-                    h->listbuf.upload(h->mem, h->lev[l].in, s);
-                    VCK(launch_qmax(lvdev(h, l), h->listbuf.p, (int)h->listbuf.n, h->qmax.p, s));
-                }
-            }
-            const int px = h->cfg.bc[0] == VLBM_BC_PERIODIC, py = h->cfg.bc[2] == VLBM_BC_PERIODIC;
-            size_t nb = 0;
-            for (int l = 0; l <= h->nlev - 2; l++) nb += (size_t)h->lev[l].bx * h->lev[l].by;
-            h->bflag.ensure(h->mem, nb);
-            size_t off = 0;
-            for (int l = 0; l <= h->nlev - 2; l++) {
-                Level& L = h->lev[l];
-                h->stage8.ensure(h->mem, (size_t)L.nx * L.ny);
-                VCK(cudaMemsetAsync(h->stage8.p, 0, (size_t)L.nx * L.ny, s));
-                h->listbuf.upload(h->mem, L.in, s);
-                if (fluxs)
-                    VCK(launch_tag_flux(lvdev(h, l), h->listbuf.p, (int)L.in.size(), h->qmax.p, h->cfg.tag_tol,
-                                        h->stage8.p, s));
-                else
-                    VCK(launch_tag(lvdev(h, l), h->listbuf.p, (int)L.in.size(), tol2, h->stage8.p, s));
-                VCK(launch_blockflag(h->stage8.p, L.nx, L.ny, px, py, h->cfg.tag_buffer, h->bflag.p + off, s));
-                off += (size_t)L.bx * L.by;
-            }
-            // the one synchronisation of an adaptive regrid: the block flags
-            std::vector<uint8_t> all(nb);
-            VCK(cudaMemcpyAsync(all.data(), h->bflag.p, nb, cudaMemcpyDeviceToHost, s));
-            VCK(cudaStreamSynchronize(s));
-            off = 0;
-            for (int l = 0; l <= h->nlev - 2; l++) {
-                const size_t n = (size_t)h->lev[l].bx * h->lev[l].by;
-                bflag[l].assign(all.begin() + off, all.begin() + off + n);
-                off += n;
-            }
+            tag_begin(h);
+            t0 = std::chrono::steady_clock::now();
+            VCK(cudaEventSynchronize(h->rg_ev));
             h->times[VLBM_T_TAG] += ms_since(t0);
-            t0 = std::chrono::steady_clock::now();
-            layout_rule(h, bflag, bcov);
-            h->times[VLBM_T_LAYOUT] += ms_since(t0);
-            t0 = std::chrono::steady_clock::now();
-            regrid_to(h, bcov, true);
-            h->times[VLBM_T_REGRID] += ms_since(t0);
+            tag_finish(h);
         }
         h->times[VLBM_T_NREGRIDS] += 1;
         invalidate(h);
@@ -1714,6 +1769,7 @@ vlbm_status vlbm_engine_admit(vlbm_engine* e, vlbm_hier* h, int64_t coarse_steps
     e->res[s].target = coarse_steps;
     e->res[s].done = 0;
     e->res[s].paused = false;
+    e->res[s].tagging = false;
     e->res[s].regridded_at = -1;
     e->admitted = true;
     e->res[s].regrid_every = regrid_every;
@@ -1728,6 +1784,11 @@ vlbm_status vlbm_engine_admit(vlbm_engine* e, vlbm_hier* h, int64_t coarse_steps
 vlbm_status vlbm_engine_release(vlbm_engine* e, int32_t slot) {
     if (!e || slot < 0 || slot >= (int)e->res.size() || !e->res[slot].live) return VLBM_ERR_ARG;
     cudaStreamSynchronize(e->stream);
+    if (e->res[slot].tagging) {
+        // a regrid left half done: its copies land before the slot is free
+        cudaEventSynchronize(e->res[slot].h->rg_ev);
+        e->res[slot].tagging = false;
+    }
     e->res[slot].h->engine = nullptr;
     e->res[slot].live = false;
     e->res[slot].h = nullptr;
@@ -1742,6 +1803,29 @@ vlbm_status vlbm_engine_advance(vlbm_engine* e, int32_t max_steps, int32_t* fini
     if (nfinished) *nfinished = 0;
     if (steps) *steps = 0;
     try {
+        // 0. second halves of the regrids whose block flags have arrived (all
+        //    of them, waiting, when no other resident can step); the
+        //    resident's steps resume after its regrid's kernels
+        bool runnable = false;
+        for (const auto& r : e->res)
+            if (r.live && !r.paused && r.done < r.target) runnable = true;
+        for (auto& r : e->res) {
+            if (!r.live || !r.tagging) continue;
+            vlbm_hier* h = r.h;
+            const cudaError_t q = runnable ? cudaEventQuery(h->rg_ev) : cudaEventSynchronize(h->rg_ev);
+            if (q == cudaErrorNotReady) continue;
+            VCK(q);
+            on_stream(h, e->hi, [&] { tag_finish(h); });
+            VCK(cudaEventRecord(r.ev, e->hi));
+            VCK(cudaStreamWaitEvent(e->stream, r.ev, 0));
+            h->times[VLBM_T_NREGRIDS] += 1;
+            if (h->own) h->own->valid = false;
+            r.tagging = false;
+            r.paused = false;
+            r.regridded_at = r.done;
+            e->dirty = true;
+            e->regridded = true;
+        }
         // 1. adaptive residents due for a regrid leave the batches; an event
         //    marks the end of their last step on the engine's stream
         std::vector<size_t> due;
@@ -1799,6 +1883,12 @@ vlbm_status vlbm_engine_advance(vlbm_engine* e, int32_t max_steps, int32_t* fini
                 if (gs) VCK(cudaGraphLaunch(gs, e->stream));
                 if (phased) e->phased.one_step(e->stream);
             }
+            int& c = e->lead_i;
+            if (!e->lead[c]) VCK(cudaEventCreateWithFlags(&e->lead[c], cudaEventDisableTiming));
+            if (e->lead_set[c]) VCK(cudaEventSynchronize(e->lead[c]));  // the steps of two calls ago
+            VCK(cudaEventRecord(e->lead[c], e->stream));
+            e->lead_set[c] = true;
+            c ^= 1;
         }
         int nf = 0;
         for (size_t i = 0; i < e->res.size(); i++) {
@@ -1816,12 +1906,12 @@ vlbm_status vlbm_engine_advance(vlbm_engine* e, int32_t max_steps, int32_t* fini
                 e->dirty = true;
             }
         }
-        // 3. the paused residents' regrids, on their own streams after their
-        //    events: the host work overlaps the steps just queued (their step
-        //    counts were not advanced above)
-        //    The regrid runs on the engine's high-priority stream, so that
-        //    its small kernels are scheduled at the next launch boundary
-        //    instead of queueing behind every step already queued.
+        // 3. the first halves of the due residents' regrids, after their
+        //    events, on the engine's high-priority stream (its small kernels
+        //    are scheduled at the next launch boundary instead of queueing
+        //    behind every step already queued); nothing waits for them here:
+        //    a later call finishes each regrid once its block flags are on
+        //    the host, while the other residents keep stepping
         if (!due.empty() && !e->hi) {
             int lo = 0, hi = 0;
             VCK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
@@ -1831,22 +1921,8 @@ vlbm_status vlbm_engine_advance(vlbm_engine* e, int32_t max_steps, int32_t* fini
             auto& r = e->res[i];
             vlbm_hier* h = r.h;
             VCK(cudaStreamWaitEvent(e->hi, r.ev, 0));
-            vlbm_engine* keep = h->engine;
-            cudaStream_t own = h->stream;
-            h->engine = nullptr;  // vlbm_regrid refuses engine residents
-            h->stream = e->hi;
-            h->mem.s = e->hi;
-            vlbm_status st = vlbm_regrid(h, nullptr, 0);
-            cudaError_t ce = cudaStreamSynchronize(e->hi);
-            h->stream = own;
-            h->mem.s = own;
-            h->engine = keep;
-            if (st != VLBM_OK) throw Fail{st, std::string("regrid: ") + h->err};
-            VCK(ce);
-            r.regridded_at = r.done;
-            r.paused = false;
-            e->dirty = true;
-            e->regridded = true;
+            on_stream(h, e->hi, [&] { tag_begin(h); });
+            r.tagging = true;
         }
         if (nfinished) *nfinished = nf;
         if (steps) *steps = (int32_t)k;
@@ -1876,6 +1952,9 @@ vlbm_status vlbm_engine_step(vlbm_engine* e, int32_t* finished, int32_t* nfinish
 void vlbm_engine_destroy(vlbm_engine* e) {
     if (!e) return;
     cudaStreamSynchronize(e->stream);
+    if (e->hi) cudaStreamSynchronize(e->hi);
+    for (cudaEvent_t& ev : e->lead)
+        if (ev) cudaEventDestroy(ev), ev = nullptr;
     for (auto& r : e->res) {
         if (r.live && r.h) r.h->engine = nullptr;
         if (r.ev) cudaEventDestroy(r.ev);

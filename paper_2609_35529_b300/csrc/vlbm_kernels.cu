@@ -185,12 +185,13 @@ __device__ __forceinline__ int state_buf(const LevelDev& L) { return L.level == 
 // Per level step, on the level's active cells, from the pre-collision state:
 //   s_k   = g_k / (2 qmax_k), g_k = (Qx_k(E) - Qx_k(W)) + (Qy_k(N) - Qy_k(S))
 //           (dx (div Q)_k / max |Q_k| with central differences)
-//   s     = (0.25 sum_k s_k^2)^(1/2)
+//   s     = (0.25 ((s_0^2 + s_3^2) + (s_1^2 + s_2^2)))^(1/2)
 //   theta = dil^2 / (dil^2 + vort^2 + eps) where dil < 0, else 0, with the
 //           undivided dil = (u(E) - u(W)) + (v(N) - v(S)) and
 //           vort = (v(E) - v(W)) - (u(N) - u(S))
 //   beta  = beta_max - (beta_max - beta_min) clip(C s_bar theta_bar, 0, 1)
-//           with 3 x 3 box filters s_bar, theta_bar
+//           with 3 x 3 box filters s_bar, theta_bar (sums grouped so that
+//           swapping x and y gives the same rounding)
 // A neighbour that is not an active cell of the level (covered, off the
 // level, beyond a non-periodic side) takes the centre cell's value.
 
@@ -256,7 +257,8 @@ __global__ void sensor_rate_kernel(const LevelDev* __restrict__ levs, const Item
             const double g = (S[k * P + e] - S[k * P + ww]) + (S[(4 + k) * P + n] - S[(4 + k) * P + so]);
             sh[k] = g * L.iq[k];
         }
-        L.sens[10 * P + c] = sqrt(0.25 * ((sh[0] * sh[0] + sh[1] * sh[1]) + (sh[2] * sh[2] + sh[3] * sh[3])));
+        // fields paired (rho, rho E), (rho u, rho v): invariant under x <-> y
+        L.sens[10 * P + c] = sqrt(0.25 * ((sh[0] * sh[0] + sh[3] * sh[3]) + (sh[1] * sh[1] + sh[2] * sh[2])));
         const double dil = (S[8 * P + e] - S[8 * P + ww]) + (S[9 * P + n] - S[9 * P + so]);
         const double vort = (S[9 * P + e] - S[9 * P + ww]) - (S[8 * P + n] - S[8 * P + so]);
         const double d2 = dil * dil;
@@ -269,13 +271,14 @@ __device__ double sensor_beta_at(const LevelDev& L, int x, int y) {
     const long long c = (long long)y * L.pitch + x;
     const double* Ss = L.sens + 10 * L.plane;
     const double* St = L.sens + 11 * L.plane;
-    double as = 0.0, at = 0.0;
-    for (int dy = -1; dy <= 1; dy++)
-        for (int dx = -1; dx <= 1; dx++) {
-            const long long q = sens_nb(L, x, y, dx, dy, c);
-            as += Ss[q];
-            at += St[q];
-        }
+    // centre + ((E + W) + (N + S)) + ((NE + SW) + (NW + SE)): the same
+    // rounding after swapping x and y
+    const long long e = sens_nb(L, x, y, 1, 0, c), w = sens_nb(L, x, y, -1, 0, c);
+    const long long n = sens_nb(L, x, y, 0, 1, c), so = sens_nb(L, x, y, 0, -1, c);
+    const long long ne = sens_nb(L, x, y, 1, 1, c), sw = sens_nb(L, x, y, -1, -1, c);
+    const long long nw = sens_nb(L, x, y, -1, 1, c), se = sens_nb(L, x, y, 1, -1, c);
+    const double as = (Ss[c] + ((Ss[e] + Ss[w]) + (Ss[n] + Ss[so]))) + ((Ss[ne] + Ss[sw]) + (Ss[nw] + Ss[se]));
+    const double at = (St[c] + ((St[e] + St[w]) + (St[n] + St[so]))) + ((St[ne] + St[sw]) + (St[nw] + St[se]));
     double z = (L.csens * (L.ninth * as)) * (L.ninth * at);
     if (z < 0.0) z = 0.0;
     if (z > 1.0) z = 1.0;
@@ -489,14 +492,174 @@ __global__ void close_kernel(const LevelDev* __restrict__ levs, const Item* __re
     }
 }
 
+// Exact sums of the audited moments.  An audit slot holds W_k of the 64
+// cells of one tile, layout [k][cell], at weight 2^scale[slot]; a thread
+// reads one (field, cell) column across a range of slots and keeps two
+// sums (W and |W|).
+//
+// Fast path: the values a thread sees have nearly the same exponent, so
+// they are added as integers m * 2^d (m the 53-bit significand) into a
+// two's-complement 128-bit window whose least significant bit sits at
+// position `base` of the 192-bit fixed point (0 <= base <= 64, chosen from
+// the thread's first value).  A value whose bits fit the window exactly
+// (0 <= d < 64) takes the fast path; zeros are skipped; anything else
+// (subnormal, tiny, huge, NaN) takes the general 192-bit path.  Below 2^10
+// fast additions the window cannot overflow (|m 2^d| < 2^117); it is
+// folded into the 192-bit sums before that and at the end, so the result
+// is the same exact sum either way.
+struct Win128 {
+    unsigned long long lo, hi;
+};
+
+__device__ __forceinline__ void win_fold(Fix192& acc, Win128& w, int base) {
+    const unsigned long long ext = (w.hi >> 63) ? ~0ull : 0ull;
+    Fix192 f;
+    if (base == 0) {
+        f.w[0] = w.lo;
+        f.w[1] = w.hi;
+        f.w[2] = ext;
+    } else if (base == 64) {
+        f.w[0] = 0ull;
+        f.w[1] = w.lo;
+        f.w[2] = w.hi;
+    } else {
+        f.w[0] = w.lo << base;
+        f.w[1] = (w.hi << base) | (w.lo >> (64 - base));
+        f.w[2] = (ext << base) | (w.hi >> (64 - base));
+    }
+    fix_add(acc, f);
+    w.lo = w.hi = 0ull;
+}
+
+// Exact per-thread sums of v_j * 2^scale[j] for v_j = aw[j * AUDIT_SLOT +
+// col], slots j in [j0, j1), into sum and abs_sum (192-bit), through the
+// 128-bit window; COH: loads through L2 (data written in the same launch).
+template <bool COH>
+__device__ __forceinline__ void audit_thread_sums(const double* __restrict__ aw, const int* __restrict__ scale,
+                                                  int j0, int j1, int col, Fix192& sum, Fix192& abs_sum) {
+    Win128 ws{0ull, 0ull}, wa{0ull, 0ull};
+    int base = -1, nfast = 0;
+    // AUDIT_BATCH loads in flight per thread, then their accumulation
+    constexpr int AUDIT_BATCH = 8;
+    for (int jb = j0; jb < j1; jb += AUDIT_BATCH) {
+        double vb[AUDIT_BATCH];
+        int sb[AUDIT_BATCH];
+#pragma unroll
+        for (int u = 0; u < AUDIT_BATCH; u++) {
+            const int j = jb + u;
+            const double* q = aw + (size_t)j * AUDIT_SLOT + col;
+            vb[u] = j < j1 ? (COH ? __ldcg(q) : __ldcs(q)) : 0.0;
+            sb[u] = j < j1 ? (COH ? __ldcg(scale + j) : __ldg(scale + j)) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < AUDIT_BATCH; u++) {
+            const double v = vb[u];
+            const unsigned long long B = (unsigned long long)__double_as_longlong(v);
+            if ((B << 1) == 0ull) continue;  // +-0
+            const int E = (int)((B >> 52) & 0x7FFull);
+            const int sc = sb[u];
+            const int sh = E - 947 + sc;  // position of the significand's lsb (2^-128 units)
+            if (base < 0 && E != 0 && E != 2047) base = min(max(sh - 32, 0), 64);
+            const int d = sh - base;
+            if (E == 0 || E == 2047 || base < 0 || d < 0 || d > 63) {
+                fix_accumulate(sum, abs_sum, v, sc);
+                continue;
+            }
+            const unsigned long long m = (B & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+            const unsigned long long lo = m << d;
+            const unsigned long long hi = d ? m >> (64 - d) : 0ull;
+            // |v| into the magnitude window
+            const unsigned long long a0 = wa.lo + lo;
+            wa.hi += hi + (a0 < lo ? 1ull : 0ull);
+            wa.lo = a0;
+            // +-|v| into the signed window
+            if (B >> 63) {
+                const unsigned long long brw = ws.lo < lo ? 1ull : 0ull;
+                ws.lo -= lo;
+                ws.hi -= hi + brw;
+            } else {
+                const unsigned long long s0 = ws.lo + lo;
+                ws.hi += hi + (s0 < lo ? 1ull : 0ull);
+                ws.lo = s0;
+            }
+            if (++nfast == 1023) {
+                win_fold(sum, ws, base);
+                win_fold(abs_sum, wa, base);
+                nfast = 0;
+            }
+        }
+    }
+    if (base >= 0) {
+        win_fold(sum, ws, base);
+        win_fold(abs_sum, wa, base);
+    }
+}
+
+// Barrier of one 64-thread group (named barrier 1 + g).
+__device__ __forceinline__ void group_bar(int g) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(64) : "memory");
+}
+
+// Audit task (kind 2) run by one 64-thread group: field T.kk over the audit
+// block T.aslot; thread lt reads column (field, cell lt) of every slot of the
+// block (written earlier in the same launch: loads through L2).  The block's
+// sums of W_k and |W_k| go to words 3 k .. 3 k + 2 and 3 (4 + k) .. of its
+// 24-word partial.
+__device__ __forceinline__ void audit_task(const Segment& S, const Task& T, int g, int lt) {
+    __shared__ Fix192 s_ap[TILES_PER_CTA][2][2];
+    const int k = T.kk;
+    const int2 r = S.arng[T.aslot];
+    Fix192 sum = fix_zero(), abs_sum = fix_zero();
+    audit_thread_sums<true>(S.aw, S.ascale, r.x, r.y, k * 64 + lt, sum, abs_sum);
+    for (int off = 16; off > 0; off >>= 1) {
+        const Fix192 o1 = fix_shfl_down(sum, off);
+        const Fix192 o2 = fix_shfl_down(abs_sum, off);
+        fix_add(sum, o1);
+        fix_add(abs_sum, o2);
+    }
+    if ((lt & 31) == 0) {
+        s_ap[g][lt >> 5][0] = sum;
+        s_ap[g][lt >> 5][1] = abs_sum;
+    }
+    group_bar(g);
+    if (lt == 0) {
+        Fix192 a = s_ap[g][0][0], b = s_ap[g][0][1];
+        fix_add(a, s_ap[g][1][0]);
+        fix_add(b, s_ap[g][1][1]);
+        unsigned long long* o = S.apart + (size_t)T.aslot * 24;
+        for (int i = 0; i < 3; i++) {
+            o[3 * k + i] = a.w[i];
+            o[3 * (4 + k) + i] = b.w[i];
+        }
+    }
+}
+
+// The same by one warp alone (two columns per lane).
+__device__ __forceinline__ void audit_task_warp(const Segment& S, const Task& T, int lane) {
+    const int k = T.kk;
+    const int2 r = S.arng[T.aslot];
+    Fix192 sum = fix_zero(), abs_sum = fix_zero();
+    audit_thread_sums<true>(S.aw, S.ascale, r.x, r.y, k * 64 + lane, sum, abs_sum);
+    audit_thread_sums<true>(S.aw, S.ascale, r.x, r.y, k * 64 + 32 + lane, sum, abs_sum);
+    for (int off = 16; off > 0; off >>= 1) {
+        const Fix192 o1 = fix_shfl_down(sum, off);
+        const Fix192 o2 = fix_shfl_down(abs_sum, off);
+        fix_add(sum, o1);
+        fix_add(abs_sum, o2);
+    }
+    if (lane == 0) {
+        unsigned long long* o = S.apart + (size_t)T.aslot * 24;
+        for (int i = 0; i < 3; i++) {
+            o[3 * k + i] = sum.w[i];
+            o[3 * (4 + k) + i] = abs_sum.w[i];
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // the persistent task kernel: every tile of every phase of G coarse steps,
 // of every hierarchy of the batch, in one launch
 // ---------------------------------------------------------------------------
-
-__device__ __forceinline__ void group_bar(int g) {
-    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(64) : "memory");
-}
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     unsigned v;
@@ -641,8 +804,10 @@ task_kernel(const LevelDev* __restrict__ levs, const Segment* __restrict__ segs,
             } else {
                 sweep_cell<P, true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.kkp, T.step, nullptr, pre);
             }
-        } else {
+        } else if (T.kind == 1) {
             close_cell<true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.step);
+        } else {
+            audit_task(S, T, g, lt);
         }
         group_bar(g);
         if (lt == 0) {
@@ -702,8 +867,10 @@ task_kernel_half(const LevelDev* __restrict__ levs, const Segment* __restrict__ 
             } else {
                 sweep_cell<P, true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.kkp, T.step);
             }
-        } else {
+        } else if (T.kind == 1) {
             close_cell<true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.step);
+        } else if (half == 0) {  // the first half does the whole audit task
+            audit_task_warp(S, T, lane);
         }
         __syncwarp();
         if (lane == 0) {
@@ -723,46 +890,9 @@ __global__ void end_step_kernel(int* const* par, int n) {
     if (t < n) *par[t] ^= 1;
 }
 
-// Exact sums of the audited moments: block b covers the audit slots
-// [rng[b].x, rng[b].y).  A slot holds W_k of the 64 cells of one tile,
-// layout [k][cell], at weight 2^scale[slot]; thread t always reads field
-// k = t / 64, so each thread keeps just two sums.  The block's 8 exact sums
-// go to part[b][0..23] (W_0..W_3, then |W_0|..|W_3|).
-//
-// Fast path: the values a thread sees have nearly the same exponent, so
-// they are added as integers m * 2^d (m the 53-bit significand) into a
-// two's-complement 128-bit window whose least significant bit sits at
-// position `base` of the 192-bit fixed point (0 <= base <= 64, chosen from
-// the thread's first value).  A value whose bits fit the window exactly
-// (0 <= d < 64) takes the fast path; zeros are skipped; anything else
-// (subnormal, tiny, huge, NaN) takes the general 192-bit path.  Below 2^10
-// fast additions the window cannot overflow (|m 2^d| < 2^117); it is
-// folded into the 192-bit sums before that and at the end, so the result
-// is the same exact sum either way.
-struct Win128 {
-    unsigned long long lo, hi;
-};
-
-__device__ __forceinline__ void win_fold(Fix192& acc, Win128& w, int base) {
-    const unsigned long long ext = (w.hi >> 63) ? ~0ull : 0ull;
-    Fix192 f;
-    if (base == 0) {
-        f.w[0] = w.lo;
-        f.w[1] = w.hi;
-        f.w[2] = ext;
-    } else if (base == 64) {
-        f.w[0] = 0ull;
-        f.w[1] = w.lo;
-        f.w[2] = w.hi;
-    } else {
-        f.w[0] = w.lo << base;
-        f.w[1] = (w.hi << base) | (w.lo >> (64 - base));
-        f.w[2] = (ext << base) | (w.hi >> (64 - base));
-    }
-    fix_add(acc, f);
-    w.lo = w.hi = 0ull;
-}
-
+// Block b sums the audit slots [rng[b].x, rng[b].y), thread t the column
+// t (field t / 64); the block's 8 exact sums go to part[b][0..23] (W_0..W_3,
+// then |W_0|..|W_3|).
 __global__ void __launch_bounds__(256) audit_slots_kernel(const double* __restrict__ aw, const int2* __restrict__ rng,
                                                           const int* __restrict__ scale,
                                                           unsigned long long* __restrict__ part) {
@@ -770,61 +900,7 @@ __global__ void __launch_bounds__(256) audit_slots_kernel(const double* __restri
     const int t = threadIdx.x;
     const int2 r = rng[blockIdx.x];
     Fix192 sum = fix_zero(), abs_sum = fix_zero();
-    Win128 ws{0ull, 0ull}, wa{0ull, 0ull};
-    int base = -1, nfast = 0;
-    // AUDIT_BATCH loads in flight per thread, then their accumulation
-    constexpr int AUDIT_BATCH = 8;
-    for (int j0 = r.x; j0 < r.y; j0 += AUDIT_BATCH) {
-        double vb[AUDIT_BATCH];
-        int sb[AUDIT_BATCH];
-#pragma unroll
-        for (int u = 0; u < AUDIT_BATCH; u++) {
-            const int j = j0 + u;
-            vb[u] = j < r.y ? __ldcs(aw + (size_t)j * AUDIT_SLOT + t) : 0.0;
-            sb[u] = j < r.y ? __ldg(scale + j) : 0;
-        }
-#pragma unroll
-        for (int u = 0; u < AUDIT_BATCH; u++) {
-            const double v = vb[u];
-            const unsigned long long B = (unsigned long long)__double_as_longlong(v);
-            if ((B << 1) == 0ull) continue;  // +-0
-            const int E = (int)((B >> 52) & 0x7FFull);
-            const int sc = sb[u];
-            const int sh = E - 947 + sc;  // position of the significand's lsb (2^-128 units)
-            if (base < 0 && E != 0 && E != 2047) base = min(max(sh - 32, 0), 64);
-            const int d = sh - base;
-            if (E == 0 || E == 2047 || base < 0 || d < 0 || d > 63) {
-                fix_accumulate(sum, abs_sum, v, sc);
-                continue;
-            }
-            const unsigned long long m = (B & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
-            const unsigned long long lo = m << d;
-            const unsigned long long hi = d ? m >> (64 - d) : 0ull;
-            // |v| into the magnitude window
-            const unsigned long long a0 = wa.lo + lo;
-            wa.hi += hi + (a0 < lo ? 1ull : 0ull);
-            wa.lo = a0;
-            // +-|v| into the signed window
-            if (B >> 63) {
-                const unsigned long long brw = ws.lo < lo ? 1ull : 0ull;
-                ws.lo -= lo;
-                ws.hi -= hi + brw;
-            } else {
-                const unsigned long long s0 = ws.lo + lo;
-                ws.hi += hi + (s0 < lo ? 1ull : 0ull);
-                ws.lo = s0;
-            }
-            if (++nfast == 1023) {
-                win_fold(sum, ws, base);
-                win_fold(abs_sum, wa, base);
-                nfast = 0;
-            }
-        }
-    }
-    if (base >= 0) {
-        win_fold(sum, ws, base);
-        win_fold(abs_sum, wa, base);
-    }
+    audit_thread_sums<false>(aw, scale, r.x, r.y, t, sum, abs_sum);
     for (int off = 16; off > 0; off >>= 1) {
         const Fix192 o1 = fix_shfl_down(sum, off);
         const Fix192 o2 = fix_shfl_down(abs_sum, off);

@@ -599,4 +599,90 @@ inline void build_tasks(const std::vector<TaskLevel>& lev, int nsteps, TaskLists
     }
 }
 
+// Exact per-step conservation audit (Sec. 4.1.2, 4.1.3, 4.2) on a built task list.
+// With block_slots > 0: every first sweep of a tile in a step (aslot == -2)
+// gets an audit slot, numbered step by step in list order; scale[j] is the
+// weight exponent of slot j (4^-level: -2 level); the slots of each step are
+// cut into reduction blocks rng[b] = [first, last) of at most block_slots
+// slots, never across steps, and bseg[st] .. bseg[st + 1] are the blocks of
+// step st.  Each block gets four reduction tasks (kind 2, one per field kk,
+// aslot = the block), each depending on the sweeps that write the block's
+// slots and inserted right after the last of them, so that the reductions
+// run between later sweeps; the other tasks keep their order and their
+// (remapped) dependencies, which all point to earlier tasks.  With
+// block_slots == 0 nothing is audited (aslot = -1 everywhere).  Returns the
+// number of slots.
+inline int assign_audit(std::vector<Task>& t, std::vector<int>& d, int nsteps, int block_slots,
+                        std::vector<int>& scale, std::vector<int2>& rng, std::vector<int>& bseg) {
+    scale.clear();
+    rng.clear();
+    bseg.assign(1, 0);
+    if (block_slots <= 0) {
+        for (Task& T : t)
+            if (T.kind == 0) T.aslot = -1;
+        return 0;
+    }
+    std::vector<int> seg(nsteps + 1, 0);
+    for (const Task& T : t)
+        if (T.kind == 0 && T.aslot == -2) seg[T.step + 1]++;
+    for (int i = 0; i < nsteps; i++) seg[i + 1] += seg[i];
+    const int nslots = seg.back();
+    std::vector<int> fill(nsteps, 0), writer(nslots, -1);
+    scale.assign(std::max(1, nslots), 0);
+    const int n = (int)t.size();
+    for (int i = 0; i < n; i++) {
+        Task& T = t[i];
+        if (T.kind != 0) continue;
+        T.aslot = T.aslot == -2 ? seg[T.step] + fill[T.step]++ : -1;
+        if (T.aslot >= 0) {
+            scale[T.aslot] = -2 * T.lid;
+            writer[T.aslot] = i;
+        }
+    }
+    for (int st = 0; st < nsteps; st++) {
+        for (int j = seg[st]; j < seg[st + 1]; j += block_slots) {
+            int2 r;
+            r.x = j;
+            r.y = std::min(j + block_slots, seg[st + 1]);
+            rng.push_back(r);
+        }
+        bseg.push_back((int)rng.size());
+    }
+    // the blocks whose last writer is task i
+    std::vector<std::vector<int>> after(n);
+    for (int b = 0; b < (int)rng.size(); b++) {
+        int last = -1;
+        for (int j = rng[b].x; j < rng[b].y; j++) last = std::max(last, writer[j]);
+        after[last].push_back(b);
+    }
+    std::vector<Task> nt;
+    std::vector<int> nd, remap(n);
+    nt.reserve(n + 4 * rng.size());
+    nd.reserve(d.size() + 4 * (size_t)nslots);
+    for (int i = 0; i < n; i++) {
+        Task T = t[i];
+        const int d0 = (int)nd.size();
+        for (int j = 0; j < T.ndep; j++) nd.push_back(remap[d[T.dep0 + j]]);  // earlier tasks: remapped already
+        T.dep0 = d0;
+        remap[i] = (int)nt.size();
+        nt.push_back(T);
+        for (int b : after[i])
+            for (int k = 0; k < 4; k++) {
+                Task A{};
+                A.lid = T.lid;
+                A.kind = 2;
+                A.kk = (signed char)k;
+                A.step = T.step;
+                A.dep0 = (int)nd.size();
+                A.ndep = rng[b].y - rng[b].x;
+                A.aslot = b;
+                for (int j = rng[b].x; j < rng[b].y; j++) nd.push_back(remap[writer[j]]);
+                nt.push_back(A);
+            }
+    }
+    t.swap(nt);
+    d.swap(nd);
+    return nslots;
+}
+
 }  // namespace vlbm

@@ -4,7 +4,8 @@
 // must produce the same tasks, the fast builder's edges must be reference
 // edges pointing backwards, and both lists must order the tasks the same
 // way (equal transitive closures); the fast builder must give the same
-// lists on 1 and 4 threads.  With --time it reports the build time of both
+// lists on 1 and 4 threads, and the audit's slots, blocks and reduction
+// tasks must be placed as assign_audit states.  With --time it reports the build time of both
 // on a large three-level layout.
 //
 //   task_builder_check [--layouts N] [--seed S] [--time [--threads T]]
@@ -163,6 +164,75 @@ static bool same_order(const TaskLists& ref, const TaskLists& f, char* why, size
     return true;
 }
 
+// assign_audit on a copy of list `a`: the sweeps and closes keep their
+// order, fields and (remapped) dependencies; every first sweep of a step
+// owns one slot of its step, with weight exponent -2 level; the blocks tile
+// each step's slots in at most `bs` slots; every block has exactly one
+// reduction task per field, after all of the block's writers, depending on
+// exactly those writers; every edge points backwards.
+static bool audit_ok(const TaskLists& a, int nsteps, int bs, char* why) {
+    std::vector<Task> t = a.t;
+    std::vector<int> d = a.d, scale, bseg;
+    std::vector<int2> rng;
+    const int nslots = assign_audit(t, d, nsteps, bs, scale, rng, bseg);
+    std::vector<int> first(nsteps, 0);
+    for (const Task& T : a.t)
+        if (T.kind == 0 && T.aslot == -2) first[T.step]++;
+    int expect = 0;
+    for (int v : first) expect += v;
+    if (nslots != expect) return sprintf(why, "audit: %d slots, %d first sweeps", nslots, expect), false;
+    if ((int)bseg.size() != nsteps + 1 || bseg.back() != (int)rng.size())
+        return sprintf(why, "audit: step segmentation of the blocks"), false;
+    std::vector<int> pos(a.t.size(), -1), writer(nslots, -1), slot_step(nslots, -1);
+    std::vector<std::vector<int>> red(rng.size());
+    size_t k = 0;
+    for (size_t i = 0; i < t.size(); i++) {
+        const Task& T = t[i];
+        for (int j = 0; j < T.ndep; j++)
+            if (d[T.dep0 + j] >= (int)i) return sprintf(why, "audit: task %zu has a forward edge", i), false;
+        if (T.kind == 2) {
+            if (T.aslot < 0 || T.aslot >= (int)rng.size()) return sprintf(why, "audit: block index"), false;
+            red[T.aslot].push_back((int)i);
+            continue;
+        }
+        if (k >= a.t.size()) return sprintf(why, "audit: extra task"), false;
+        const Task& O = a.t[k];
+        if (O.lid != T.lid || O.tx != T.tx || O.ty != T.ty || O.kind != T.kind || O.kk != T.kk || O.kkp != T.kkp ||
+            O.step != T.step || O.ndep != T.ndep)
+            return sprintf(why, "audit: task %zu changed", k), false;
+        for (int j = 0; j < T.ndep; j++)
+            if (d[T.dep0 + j] != pos[a.d[O.dep0 + j]]) return sprintf(why, "audit: task %zu edge changed", k), false;
+        const bool owns = O.kind == 0 && O.aslot == -2;
+        if (owns != (T.aslot >= 0)) return sprintf(why, "audit: slot owner %zu", k), false;
+        if (T.aslot >= 0) {
+            if (T.aslot >= nslots || writer[T.aslot] >= 0) return sprintf(why, "audit: slot %d", T.aslot), false;
+            writer[T.aslot] = (int)i;
+            slot_step[T.aslot] = T.step;
+            if (scale[T.aslot] != -2 * T.lid) return sprintf(why, "audit: weight of slot %d", T.aslot), false;
+        }
+        pos[k++] = (int)i;
+    }
+    if (k != a.t.size()) return sprintf(why, "audit: lost tasks"), false;
+    int next = 0;
+    for (int st = 0; st < nsteps; st++)
+        for (int b = bseg[st]; b < bseg[st + 1]; b++) {
+            const int2 r = rng[b];
+            if (r.x != next || r.y <= r.x || r.y - r.x > bs) return sprintf(why, "audit: block %d range", b), false;
+            next = r.y;
+            for (int j = r.x; j < r.y; j++)
+                if (slot_step[j] != st) return sprintf(why, "audit: block %d crosses steps", b), false;
+            if (red[b].size() != 4) return sprintf(why, "audit: block %d has %zu tasks", b, red[b].size()), false;
+            for (int q = 0; q < 4; q++) {
+                const Task& A = t[red[b][q]];
+                if (A.kk != q || A.step != st || A.ndep != r.y - r.x) return sprintf(why, "audit: task of block %d", b), false;
+                for (int j = 0; j < A.ndep; j++)
+                    if (d[A.dep0 + j] != writer[r.x + j]) return sprintf(why, "audit: block %d edge", b), false;
+            }
+        }
+    if (next != nslots) return sprintf(why, "audit: blocks cover %d of %d slots", next, nslots), false;
+    return true;
+}
+
 static double ms_since(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
@@ -192,7 +262,8 @@ int main(int argc, char** argv) {
         build_tasks(L.lev, nsteps, fast1, 1);
         build_tasks(L.lev, nsteps, fast4, 4);
         char why[256];
-        if (!same_order(ref, fast1, why) || !same(fast1, fast4, why)) {
+        const int bs = 1 + (int)(rng() % 40);
+        if (!same_order(ref, fast1, why) || !same(fast1, fast4, why) || !audit_ok(fast1, nsteps, bs, why)) {
             printf("MISMATCH layout %d (nlev %d, %dx%d, periodic %d%d, steps %d): %s\n", n, nlev, nx0, ny0, px, py,
                    nsteps, why);
             return 1;

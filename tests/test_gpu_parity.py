@@ -159,9 +159,12 @@ def test_riemann3_three_levels_outflow(V, schedule):
     compare(o, g, 3)
 
 
-def test_riemann3_transpose_symmetric(V):
-    cs = I.riemann3(N=64, nlev=3, steps=40)
+@pytest.mark.parametrize("sensor", [False, True])
+def test_riemann3_transpose_symmetric(V, sensor):
+    cs = I.riemann3(N=64, nlev=3, steps=40, beta=1.0 if sensor else 0.7)
     g = V.Hierarchy.from_case(cs)
+    if sensor:
+        g.set_sensor(True, beta_min=0.5, c_sensor=64.0)
     g.advance(cs.steps)
     for l in range(3):
         f = g.get_populations(l).reshape(4, 4, *g.shapes[l])

@@ -267,12 +267,19 @@ def test_exact_conservation_periodic(which):
     assert np.all(drift < 1e-14), drift
 
 
-def test_transpose_symmetry_is_bitwise():
+@pytest.mark.parametrize("sensor", [False, True])
+def test_transpose_symmetry_is_bitwise(sensor):
     """Lax-Liu configuration 3 is symmetric under x <-> y (with u <-> v); the
     canonical arithmetic is written symmetrically, so the three-level run
-    stays exactly symmetric."""
-    cs = I.riemann3(N=64, nlev=3, steps=40)
+    stays exactly symmetric -- also with the sensor-driven relaxation, whose
+    sums over fields and over the 3 x 3 neighbourhood are grouped in pairs
+    that swap into each other."""
+    cs = I.riemann3(N=64, nlev=3, steps=40, beta=1.0 if sensor else 0.7)
     h = make(cs)
+    if sensor:
+        h.set_sensor(True, beta_min=0.5, c_sensor=64.0)
+        b = h.sensor_beta(0)
+        assert b[b > 0].min() < 1.0  # the sensor acts
     h.advance(cs.steps)
     for l in range(cs.nlev):
         f = h.get_f(l).reshape(4, 4, *h.shapes[l])

@@ -277,6 +277,20 @@ vlbm_status vlbm_get_tuning(const vlbm_hier* h, vlbm_tuning* t);
  * and synchronises it.  Errors: ERR_ARG, ERR_OOM, ERR_CUDA. */
 vlbm_status vlbm_selftest_fp64(uint64_t seed, int64_t n, uint64_t mismatches[4], double first_bad[16]);
 
+/* Self-test of the integer-pipe reciprocal that the collision uses for
+ * 1/rho (the Euler flux of Sec. 2.1, Eq. 1; Newton-Raphson in integer
+ * fixed point with an exact remainder test): on n seeded values
+ * (SplitMix64 stream from `seed`; densities near 1, significands next to 1
+ * and 2, exponent extremes, zeros, subnormals, infinities, NaNs,
+ * negatives, raw bit patterns) *mismatches counts results whose bits
+ * differ from the FP64 division 1.0 / x, *unsettled the inputs of the
+ * handled range (positive normal x with a normal reciprocal) whose exact
+ * correction did not settle (they would take the division); first_bad
+ * (may be NULL) receives the first offending (x, result).  Runs on the
+ * current device and synchronises it.  Errors: ERR_ARG, ERR_OOM, ERR_CUDA. */
+vlbm_status vlbm_selftest_rcp(uint64_t seed, int64_t n, uint64_t* mismatches, uint64_t* unsettled,
+                              double first_bad[2]);
+
 /* Sensor-driven relaxation (Sec. 2.2, Eq. sensor-B).  on = 1: every level
  * step first evaluates, on the level's pre-collision state,
  *   s_k   = dx (div Q)_k / qmax_k (central differences), qmax_k =

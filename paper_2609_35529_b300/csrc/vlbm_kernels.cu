@@ -10,6 +10,7 @@
 
 #include "fix192.cuh"
 #include "fp64emu.cuh"
+#include "rcp_rn.cuh"
 #include "vlbm_dev.cuh"
 #include "vlbm_launch.h"
 
@@ -105,7 +106,7 @@ __device__ __forceinline__ bool collide_p(double f[16], double om, double hb, do
     for (int k = 0; k < 4; k++) W[k] = xadd<M>(xadd<M>(f[k], f[4 + k]), xadd<M>(f[8 + k], f[12 + k]));
     if (Wout)
         for (int k = 0; k < 4; k++) Wout[k] = W[k];
-    const double inv = 1.0 / W[0];
+    const double inv = rcp_rn(W[0]);  // = 1.0 / W[0], on the integer pipes
     const double u = xmul<F>(W[1], inv);
     const double v = xmul<F>(W[2], inv);
     const double ruu = xmul<F>(W[1], u);

@@ -122,6 +122,8 @@ def lib():
     L.vlbm_selftest_timeout.argtypes = [dp, C.POINTER(i32)]
     L.vlbm_selftest_timeout.restype = C.c_int
     L.vlbm_selftest_fp64.restype = C.c_int
+    L.vlbm_selftest_rcp.argtypes = [C.c_uint64, i64, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), dp]
+    L.vlbm_selftest_rcp.restype = C.c_int
     L.vlbm_totals_static.argtypes = [vp, i64, i32, i32, C.c_double, vp, vp]
     L.vlbm_totals_static.restype = C.c_int
     L.vlbm_last_error.argtypes = [vp]
@@ -387,6 +389,19 @@ def selftest_fp64(seed, n):
         raise VlbmError(st, "vlbm_selftest_fp64")
     names = ["add", "sub", "mul", "half"]
     return {k: int(bad[i]) for i, k in enumerate(names)}, {k: tuple(first[4 * i: 4 * i + 4]) for i, k in enumerate(names)}
+
+
+def selftest_rcp(seed, n):
+    """Bitwise check of the integer-pipe reciprocal against the FP64
+    division on n seeded values; returns (mismatches, inputs whose exact
+    correction did not settle, first offending (x, result))."""
+    bad = C.c_uint64()
+    uns = C.c_uint64()
+    first = (C.c_double * 2)()
+    st = lib().vlbm_selftest_rcp(int(seed), int(n), C.byref(bad), C.byref(uns), first)
+    if st != 0:
+        raise VlbmError(st, "vlbm_selftest_rcp")
+    return int(bad.value), int(uns.value), tuple(first)
 
 
 def selftest_timeout():

@@ -24,6 +24,9 @@ namespace {
 
 // audit slots (tiles) summed by one block of the per-step audit reduction
 constexpr int AUDIT_BLOCK_SLOTS = 32;
+// distance (in tasks) between an audit reduction and the last sweep it reads:
+// about twice the thread groups resident at 3 CTAs per SM (148 x 3 x 4)
+constexpr int AUDIT_LAG = 4096;
 
 double ms_since(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -94,7 +97,62 @@ cudaMemPool_t library_pool() {
     return pools[dev];
 }
 
+// Pinned staging of host-to-device uploads inside a region (begin .. end):
+// a copy from pageable memory can make the host wait until the stream
+// reaches it, one from pinned memory never does.  Chunks are reused once the
+// event recorded at the end of the previous region has completed.
+struct PinArena {
+    std::vector<std::pair<uint8_t*, size_t>> chunks;
+    size_t ci = 0, off = 0;
+    cudaEvent_t ev = nullptr;
+    cudaStream_t s = nullptr;
+    bool pending = false, on = false;
+    void begin(cudaStream_t stream) {
+        if (on) VCK(cudaStreamSynchronize(s));  // a region left by an error: its copies may be in flight
+        if (pending) VCK(cudaEventSynchronize(ev));
+        pending = false;
+        on = true;
+        ci = off = 0;
+        s = stream;
+    }
+    const void* put(const void* src, size_t n) {
+        off = (off + 15) & ~size_t(15);
+        while (ci < chunks.size() && off + n > chunks[ci].second) {
+            ci++;
+            off = 0;
+        }
+        if (ci == chunks.size()) {
+            const size_t sz = std::max<size_t>(n, size_t(1) << 20);
+            uint8_t* p = nullptr;
+            VCK(cudaMallocHost((void**)&p, sz));
+            chunks.push_back({p, sz});
+            off = 0;
+        }
+        uint8_t* d = chunks[ci].first + off;
+        std::memcpy(d, src, n);
+        off += n;
+        return d;
+    }
+    void end() {
+        if (!on) return;
+        on = false;
+        if (!ev) VCK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        VCK(cudaEventRecord(ev, s));
+        pending = true;
+    }
+    void release() {
+        if (on && s) cudaStreamSynchronize(s);
+        if (pending && ev) cudaEventSynchronize(ev);
+        for (auto& c : chunks) cudaFreeHost(c.first);
+        chunks.clear();
+        if (ev) cudaEventDestroy(ev);
+        ev = nullptr;
+        pending = on = false;
+    }
+};
+
 struct DevMem {
+    PinArena* pin = nullptr;  // uploads are staged through it while it is on
     const vlbm_allocator* alloc = nullptr;
     vlbm_allocator a{};
     bool has = false;
@@ -142,7 +200,10 @@ struct DArr {
     void upload(DevMem& m, const std::vector<T>& v, cudaStream_t s) {
         ensure(m, v.size());
         n = v.size();
-        if (n) VCK(cudaMemcpyAsync(p, v.data(), n * sizeof(T), cudaMemcpyHostToDevice, s));
+        if (!n) return;
+        const void* src = v.data();
+        if (m.pin && m.pin->on) src = m.pin->put(src, n * sizeof(T));
+        VCK(cudaMemcpyAsync(p, src, n * sizeof(T), cudaMemcpyHostToDevice, s));
     }
     void release(DevMem& m) {
         if (p) m.put(p, cap * sizeof(T));
@@ -197,6 +258,7 @@ struct vlbm_hier {
     double* hout = nullptr;  // pinned host copy of the audit result
     // tag-driven regrid in two halves: the status words and the block flags
     // land in pinned memory (rg_pin), rg_ev marks their arrival
+    PinArena pin;  // staging of the regrids' uploads
     uint8_t* rg_pin = nullptr;
     size_t rg_cap = 0;
     cudaEvent_t rg_ev = nullptr;
@@ -583,7 +645,7 @@ void Batch::member_tasks(vlbm_hier* h, int which, int nsteps, bool aud) {
     // audit slots, reduction blocks and their tasks
     std::vector<int> scale, bseg;
     std::vector<int2> rng;
-    const int nslots = assign_audit(L.t, L.d, nsteps, aud ? AUDIT_BLOCK_SLOTS : 0, scale, rng, bseg);
+    const int nslots = assign_audit(L.t, L.d, nsteps, aud ? AUDIT_BLOCK_SLOTS : 0, scale, rng, bseg, AUDIT_LAG);
     cudaStream_t s = h->stream;
     L.dt.upload(h->mem, L.t, s);
     std::vector<int> d = L.d;
@@ -867,6 +929,7 @@ void regrid_to(vlbm_hier* h, std::vector<uint8_t>* newcov, bool averaged) {
     derive_in(h, newin, newcov);
     std::string why;
     if (!nested(h, newin, newcov, why)) throw Fail{VLBM_ERR_NESTING, why};
+    h->pin.begin(s);  // the uploads below come from pinned staging
     // 1. average-down, finest level first (merge values and slope data)
     // (one stream: each upload into listbuf is ordered after the kernel that
     // read the previous list, so no host synchronisation is needed)
@@ -900,6 +963,7 @@ void regrid_to(vlbm_hier* h, std::vector<uint8_t>* newcov, bool averaged) {
         VCK(launch_split(lvdev(h, l), lvdev(h, l + 1), h->listbuf.p, (int)en.size(), s));
     }
     install_layout(h, newin, newcov);
+    h->pin.end();
 }
 
 // Tag-driven regrid (Sec. 3.4), first half, queued on h->stream:
@@ -912,6 +976,7 @@ void tag_begin(vlbm_hier* h) {
         throw Fail{VLBM_ERR_ARG, "unknown tagging sensor"};
     const auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = h->stream;
+    h->pin.begin(s);  // the uploads below come from pinned staging
     for (int l = h->nlev - 2; l >= 0; l--) {
         h->listbuf.upload(h->mem, h->lev[l].cov, s);
         VCK(launch_avgdown(lvdev(h, l), lvdev(h, l + 1), h->listbuf.p, (int)h->listbuf.n, s));
@@ -959,6 +1024,7 @@ void tag_begin(vlbm_hier* h) {
     if (!h->rg_ev) VCK(cudaEventCreateWithFlags(&h->rg_ev, cudaEventDisableTiming));
     VCK(cudaMemcpyAsync(h->rg_pin, h->words, 8, cudaMemcpyDeviceToHost, s));
     if (nb) VCK(cudaMemcpyAsync(h->rg_pin + 8, h->bflag.p, nb, cudaMemcpyDeviceToHost, s));
+    h->pin.end();
     VCK(cudaEventRecord(h->rg_ev, s));
     h->times[VLBM_T_TAG] += ms_since(t0);
 }
@@ -1107,6 +1173,7 @@ void destroy_levels(vlbm_hier* h) {
     h->aitems.release(h->mem);
     if (h->hout) cudaFreeHost(h->hout);
     h->hout = nullptr;
+    h->pin.release();
     if (h->rg_pin) cudaFreeHost(h->rg_pin);
     h->rg_pin = nullptr;
     h->rg_cap = 0;
@@ -1208,6 +1275,7 @@ vlbm_status vlbm_create_hierarchy(const vlbm_config* cfg, const vlbm_allocator* 
             h->own_stream = true;
         }
         h->mem.s = h->stream;
+        h->mem.pin = &h->pin;
         h->words = (int*)h->mem.get(64);
         VCK(cudaMemsetAsync(h->words, 0, 64, h->stream));
         for (int l = 0; l < h->nlev; l++) {

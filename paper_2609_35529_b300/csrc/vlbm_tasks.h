@@ -607,13 +607,16 @@ inline void build_tasks(const std::vector<TaskLevel>& lev, int nsteps, TaskLists
 // slots, never across steps, and bseg[st] .. bseg[st + 1] are the blocks of
 // step st.  Each block gets four reduction tasks (kind 2, one per field kk,
 // aslot = the block), each depending on the sweeps that write the block's
-// slots and inserted right after the last of them, so that the reductions
-// run between later sweeps; the other tasks keep their order and their
-// (remapped) dependencies, which all point to earlier tasks.  With
-// block_slots == 0 nothing is audited (aslot = -1 everywhere).  Returns the
-// number of slots.
+// slots and inserted `lag` tasks after the last of them (at the end of the
+// list at the latest): tasks are claimed in list order by every resident
+// thread group at once, so with a lag of about twice the number of resident
+// groups the writers are complete when a reduction is claimed and its group
+// does not wait; the reductions run between later sweeps.  The other tasks
+// keep their order and their (remapped) dependencies, which all point to
+// earlier tasks.  With block_slots == 0 nothing is audited (aslot = -1
+// everywhere).  Returns the number of slots.
 inline int assign_audit(std::vector<Task>& t, std::vector<int>& d, int nsteps, int block_slots,
-                        std::vector<int>& scale, std::vector<int2>& rng, std::vector<int>& bseg) {
+                        std::vector<int>& scale, std::vector<int2>& rng, std::vector<int>& bseg, int lag = 0) {
     scale.clear();
     rng.clear();
     bseg.assign(1, 0);
@@ -648,12 +651,15 @@ inline int assign_audit(std::vector<Task>& t, std::vector<int>& d, int nsteps, i
         }
         bseg.push_back((int)rng.size());
     }
+    std::vector<int> blk_step(rng.size(), 0);
+    for (int st = 0; st < nsteps; st++)
+        for (int b = bseg[st]; b < bseg[st + 1]; b++) blk_step[b] = st;
     // the blocks whose last writer is task i
     std::vector<std::vector<int>> after(n);
     for (int b = 0; b < (int)rng.size(); b++) {
         int last = -1;
         for (int j = rng[b].x; j < rng[b].y; j++) last = std::max(last, writer[j]);
-        after[last].push_back(b);
+        after[std::min(n - 1, last + std::max(0, lag))].push_back(b);
     }
     std::vector<Task> nt;
     std::vector<int> nd, remap(n);
@@ -672,7 +678,7 @@ inline int assign_audit(std::vector<Task>& t, std::vector<int>& d, int nsteps, i
                 A.lid = T.lid;
                 A.kind = 2;
                 A.kk = (signed char)k;
-                A.step = T.step;
+                A.step = (signed char)blk_step[b];
                 A.dep0 = (int)nd.size();
                 A.ndep = rng[b].y - rng[b].x;
                 A.aslot = b;

@@ -170,11 +170,11 @@ static bool same_order(const TaskLists& ref, const TaskLists& f, char* why, size
 // each step's slots in at most `bs` slots; every block has exactly one
 // reduction task per field, after all of the block's writers, depending on
 // exactly those writers; every edge points backwards.
-static bool audit_ok(const TaskLists& a, int nsteps, int bs, char* why) {
+static bool audit_ok(const TaskLists& a, int nsteps, int bs, int lag, char* why) {
     std::vector<Task> t = a.t;
     std::vector<int> d = a.d, scale, bseg;
     std::vector<int2> rng;
-    const int nslots = assign_audit(t, d, nsteps, bs, scale, rng, bseg);
+    const int nslots = assign_audit(t, d, nsteps, bs, scale, rng, bseg, lag);
     std::vector<int> first(nsteps, 0);
     for (const Task& T : a.t)
         if (T.kind == 0 && T.aslot == -2) first[T.step]++;
@@ -185,6 +185,7 @@ static bool audit_ok(const TaskLists& a, int nsteps, int bs, char* why) {
         return sprintf(why, "audit: step segmentation of the blocks"), false;
     std::vector<int> pos(a.t.size(), -1), writer(nslots, -1), slot_step(nslots, -1);
     std::vector<std::vector<int>> red(rng.size());
+    std::vector<int> red_k(rng.size(), -1), writer_k(nslots, -1);  // original tasks before it
     size_t k = 0;
     for (size_t i = 0; i < t.size(); i++) {
         const Task& T = t[i];
@@ -193,6 +194,9 @@ static bool audit_ok(const TaskLists& a, int nsteps, int bs, char* why) {
         if (T.kind == 2) {
             if (T.aslot < 0 || T.aslot >= (int)rng.size()) return sprintf(why, "audit: block index"), false;
             red[T.aslot].push_back((int)i);
+            if (red_k[T.aslot] >= 0 && red_k[T.aslot] != (int)k)
+                return sprintf(why, "audit: tasks of block %d apart", T.aslot), false;
+            red_k[T.aslot] = (int)k;
             continue;
         }
         if (k >= a.t.size()) return sprintf(why, "audit: extra task"), false;
@@ -207,6 +211,7 @@ static bool audit_ok(const TaskLists& a, int nsteps, int bs, char* why) {
         if (T.aslot >= 0) {
             if (T.aslot >= nslots || writer[T.aslot] >= 0) return sprintf(why, "audit: slot %d", T.aslot), false;
             writer[T.aslot] = (int)i;
+            writer_k[T.aslot] = (int)k;
             slot_step[T.aslot] = T.step;
             if (scale[T.aslot] != -2 * T.lid) return sprintf(why, "audit: weight of slot %d", T.aslot), false;
         }
@@ -222,6 +227,11 @@ static bool audit_ok(const TaskLists& a, int nsteps, int bs, char* why) {
             for (int j = r.x; j < r.y; j++)
                 if (slot_step[j] != st) return sprintf(why, "audit: block %d crosses steps", b), false;
             if (red[b].size() != 4) return sprintf(why, "audit: block %d has %zu tasks", b, red[b].size()), false;
+            int last = -1;
+            for (int j = r.x; j < r.y; j++) last = std::max(last, writer_k[j]);
+            if (red_k[b] != std::min((int)a.t.size() - 1, last + lag) + 1)
+                return sprintf(why, "audit: block %d placed after %d original tasks, not %d + lag %d", b, red_k[b],
+                               last, lag), false;
             for (int q = 0; q < 4; q++) {
                 const Task& A = t[red[b][q]];
                 if (A.kk != q || A.step != st || A.ndep != r.y - r.x) return sprintf(why, "audit: task of block %d", b), false;
@@ -263,7 +273,7 @@ int main(int argc, char** argv) {
         build_tasks(L.lev, nsteps, fast4, 4);
         char why[256];
         const int bs = 1 + (int)(rng() % 40);
-        if (!same_order(ref, fast1, why) || !same(fast1, fast4, why) || !audit_ok(fast1, nsteps, bs, why)) {
+        if (!same_order(ref, fast1, why) || !same(fast1, fast4, why) || !audit_ok(fast1, nsteps, bs, (int)(rng() % 3) * (int)(rng() % 200), why)) {
             printf("MISMATCH layout %d (nlev %d, %dx%d, periodic %d%d, steps %d): %s\n", n, nlev, nx0, ny0, px, py,
                    nsteps, why);
             return 1;

@@ -46,17 +46,17 @@ METRIC = "MLUPS (FP64, 1 B300)"
 FLOPS_PER_LUP = 12 + 1 + 15 + 4 + 64
 # algorithmic bytes of one cell update: 16 populations read + 16 written
 BYTES_PER_LUP = 256
-# FP64-pipe operations of one cell update: 62 arithmetic operations plus the
-# IEEE division, which ncu counts as about 5 further FP64-pipe operations
-# (DFMA/DADD/DMUL thread-instructions per cell update in the sweep: 67.1)
-FP64_OPS_PER_LUP = 67
+# FP64-pipe operations of one cell update: the 62 arithmetic operations (the
+# reciprocal 1/rho runs on the integer pipes); ncu counts 33.0 DFMA + 16.1
+# DADD + 13.0 DMUL thread-instructions per cell update in the task kernel
+FP64_OPS_PER_LUP = 62
 # DRAM traffic of the task kernel per cell update: dram__bytes_read.sum +
-# dram__bytes_write.sum of a launch of 16 coarse steps (variant 1, audit off,
+# dram__bytes_write.sum of a launch of 64 coarse steps (variant 1, audit off,
 # 512 MB L2 flush before each launch), ncu --nvtx capture of this bench's
-# roofline launches (profiles/task_kernel_vortex512.md): 2.649e9 B per
-# 11 534 336 cell updates.  Valid for the kernel as captured (paired-field
-# layout); to be measured again whenever the kernel changes.
-TASK_KERNEL_DRAM_BYTES_PER_LUP = 229.7
+# roofline launches (profiles/task_kernel_vortex512.md): 3.612e9 + 6.525e9 B
+# per 46 137 344 cell updates.  Valid for the kernel as captured (integer-pipe
+# reciprocal, audit tasks); to be measured again whenever the kernel changes.
+TASK_KERNEL_DRAM_BYTES_PER_LUP = 219.7
 TRAFFIC_VARIANT = 1
 
 

@@ -339,13 +339,26 @@ def serve_batched(reqs, budget, stream=None, keep_ids=(), setup_stream=None):
     t0 = time.perf_counter()
     total_lups = 0
     spent = {"start_s": 0.0, "step_s": 0.0, "finish_s": 0.0}  # host wall time by part of the loop
+    # events on the engine's stream around every engine call: the time the
+    # stream spends between one call's queued work and the next call's is
+    # GPU time the host did not fill (other streams' work aside)
+    import torch
+    tstream = stream if isinstance(stream, torch.cuda.Stream) else None
+    marks = [] if tstream is not None else None
     host_ms = {}  # library host time (vlbm_host_times) summed over the requests
     while nxt < len(pending) or live:
         # 1. queue steps of the residents first: the GPU works through them
         #    while the host sets up the requests that arrived meanwhile
         if live:
             ta = time.perf_counter()
+            if marks is not None:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e0.record(tstream)
             done, _ = eng.advance(MAX_STEPS)
+            if marks is not None:
+                e1 = torch.cuda.Event(enable_timing=True)
+                e1.record(tstream)
+                marks.append((e0, e1))
             tb = time.perf_counter()
             spent["step_s"] += tb - ta
             for slot in done:
@@ -387,10 +400,16 @@ def serve_batched(reqs, budget, stream=None, keep_ids=(), setup_stream=None):
         if not live and nxt < len(pending):
             time.sleep(max(0.0, min(0.002, pending[nxt].arrival - (time.perf_counter() - t0))))
     wall = time.perf_counter() - t0
+    idle = None
+    if marks:
+        torch.cuda.synchronize()
+        idle = {"engine_calls": len(marks),
+                "stream_gap_s": sum(max(0.0, a[1].elapsed_time(b[0])) for a, b in zip(marks, marks[1:])) / 1e3,
+                "stream_busy_s": sum(max(0.0, a.elapsed_time(b)) for a, b in marks) / 1e3}
     eng.close()
     pay.close()
     tts = np.array([r.done_at - r.arrival for r in reqs])
-    serve_batched.breakdown = {"loop": spent, "library_host_ms": host_ms}
+    serve_batched.breakdown = {"loop": spent, "library_host_ms": host_ms, "engine_stream": idle}
     return tts, total_lups / wall / 1e6, wall
 
 

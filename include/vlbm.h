@@ -194,7 +194,8 @@ vlbm_status vlbm_get_info(const vlbm_hier* h, vlbm_info* info);
 /* Host-side time the library has spent on a hierarchy since its creation,
  * in milliseconds (wall clock, cumulative), by activity:
  *   TAG       adaptive regrid: average-down, indicator and block flags on the
- *             device, their copy to the host (after the stream is idle)
+ *             device and their copy to the host queued, and (vlbm_regrid)
+ *             the wait for them
  *   LAYOUT    new block maps from flags or boxes (grading, nesting)
  *   REGRID    merge/split launches, per-cell flags, tile lists, uploads
  *   BUILD     level tables of the launch (after a layout change)
@@ -398,25 +399,32 @@ vlbm_status vlbm_engine_create(size_t mem_budget, void* stream, vlbm_engine** ou
 vlbm_status vlbm_engine_admit(vlbm_engine* e, vlbm_hier* h, int64_t coarse_steps,
                               int32_t regrid_every, int32_t* slot);
 
-/* Advances every resident by the same number k of coarse steps, 1 <= k <=
- * max_steps, as many as no resident reaches its step count or an adaptive
- * resident its next regrid in between (adaptive residents regrid at the
- * start of the call when one is due).  Static residents run on the
- * persistent task kernel, adaptive ones on captured per-phase launches;
- * each resident's result is the same as when it is advanced alone.
- * Asynchronous unless a resident finished.  finished_slots (capacity = the
- * largest slot + 1) receives the slots whose step count is now met; a
- * finished resident whose state turned non-physical is poisoned (its
- * handle then returns ERR_STATE, vlbm_last_error says why).  *steps = k
- * (0 when nothing is resident).  Errors: ERR_ARG, ERR_CUDA, errors of a
- * resident's regrid. */
+/* Queues the next k coarse steps of every resident that can step, 1 <= k
+ * <= max_steps, as many as no resident reaches its step count or an
+ * adaptive resident its next regrid in between.  Static residents run on
+ * the persistent task kernel, adaptive ones and those with the relaxation
+ * sensor on per-phase launches; each resident's result is the same as when
+ * it is advanced alone.  An adaptive resident due for a regrid pauses: the
+ * first half of its regrid is queued on a high-priority stream, a later
+ * call finishes it once its block flags are on the host.  Asynchronous:
+ * the call waits only for the steps it queued two calls before, and for
+ * pending regrids or finishing residents when no resident can step.
+ * finished_slots (capacity = the largest slot + 1) receives the residents
+ * whose step count is met and whose last step has completed on the GPU --
+ * reported by the first call after that; their results can then be read
+ * without waiting, and a finished resident whose state turned non-physical
+ * is poisoned (its handle then returns ERR_STATE, vlbm_last_error says
+ * why).  *steps = k (0 when no resident can step).  Errors: ERR_ARG,
+ * ERR_CUDA, errors of a resident's regrid. */
 vlbm_status vlbm_engine_advance(vlbm_engine* e, int32_t max_steps, int32_t* finished_slots, int32_t* nfinished,
                                 int32_t* steps);
 
 /* vlbm_engine_advance with max_steps = 1. */
 vlbm_status vlbm_engine_step(vlbm_engine* e, int32_t* finished_slots, int32_t* nfinished);
 
-/* Removes a resident (its hierarchy returns to the caller, unchanged). */
+/* Removes a resident (its hierarchy returns to the caller, unchanged).
+ * Waits for the engine's queued work unless the resident was reported
+ * finished. */
 vlbm_status vlbm_engine_release(vlbm_engine* e, int32_t slot);
 
 /* Coarse steps taken and cell updates done by a resident since admission. */
@@ -424,6 +432,33 @@ vlbm_status vlbm_engine_slot_stats(const vlbm_engine* e, int32_t slot, int64_t* 
 
 /* Number of residents and their summed device bytes. */
 vlbm_status vlbm_engine_usage(const vlbm_engine* e, int32_t* residents, int64_t* bytes);
+
+/* Host time of the engine's calls, in milliseconds (wall clock,
+ * cumulative), by activity:
+ *   REGRID_FINISH  second halves of residents' regrids (layout rule,
+ *                  merge/split queued), including waits when no resident
+ *                  could step
+ *   FINISH         finishing residents: event checks, status words, waits
+ *                  when no resident could step
+ *   REBUILD        batch tables, task lists and graphs after a change of
+ *                  members or layouts
+ *   LAUNCH         queueing the steps (graph and per-phase launches)
+ *   LEAD           waiting for the steps queued two calls before
+ *   REGRID_BEGIN   first halves of residents' regrids queued
+ * and the counts CALLS (engine calls) and STEPS (coarse steps queued, the
+ * sum of k).  Errors: ERR_ARG. */
+enum {
+    VLBM_ET_REGRID_FINISH = 0,
+    VLBM_ET_FINISH = 1,
+    VLBM_ET_REBUILD = 2,
+    VLBM_ET_LAUNCH = 3,
+    VLBM_ET_LEAD = 4,
+    VLBM_ET_REGRID_BEGIN = 5,
+    VLBM_ET_CALLS = 6,
+    VLBM_ET_STEPS = 7,
+    VLBM_ET_COUNT = 8
+};
+vlbm_status vlbm_engine_host_times(const vlbm_engine* e, double out[VLBM_ET_COUNT]);
 
 void vlbm_engine_destroy(vlbm_engine* e);
 

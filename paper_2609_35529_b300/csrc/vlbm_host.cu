@@ -1078,6 +1078,8 @@ struct vlbm_engine {
         bool phased() const { return adaptive() || h->sensor_on; }
         bool paused = false;           // waiting for its regrid (not in a batch)
         bool tagging = false;          // the first half of its regrid is queued
+        bool finishing = false;        // step count met, last step maybe still running (ev)
+        bool reported = false;         // reported finished
         long long regridded_at = -1;   // step count of its last regrid
         cudaEvent_t ev = nullptr;      // end of its last step, then of its regrid
     };
@@ -1092,6 +1094,7 @@ struct vlbm_engine {
     cudaEvent_t lead[2] = {nullptr, nullptr};
     bool lead_set[2] = {false, false};
     int lead_i = 0;
+    double times[VLBM_ET_COUNT] = {};  // host time by activity, see vlbm_engine_host_times
     std::string err = "no error";
 };
 
@@ -1802,6 +1805,12 @@ vlbm_status vlbm_engine_slot_stats(const vlbm_engine* e, int32_t slot, int64_t* 
     return VLBM_OK;
 }
 
+vlbm_status vlbm_engine_host_times(const vlbm_engine* e, double out[VLBM_ET_COUNT]) {
+    if (!e || !out) return VLBM_ERR_ARG;
+    for (int i = 0; i < VLBM_ET_COUNT; i++) out[i] = e->times[i];
+    return VLBM_OK;
+}
+
 vlbm_status vlbm_engine_usage(const vlbm_engine* e, int32_t* residents, int64_t* bytes) {
     if (!e) return VLBM_ERR_ARG;
     int n = 0;
@@ -1838,6 +1847,8 @@ vlbm_status vlbm_engine_admit(vlbm_engine* e, vlbm_hier* h, int64_t coarse_steps
     e->res[s].done = 0;
     e->res[s].paused = false;
     e->res[s].tagging = false;
+    e->res[s].finishing = false;
+    e->res[s].reported = false;
     e->res[s].regridded_at = -1;
     e->admitted = true;
     e->res[s].regrid_every = regrid_every;
@@ -1851,7 +1862,9 @@ vlbm_status vlbm_engine_admit(vlbm_engine* e, vlbm_hier* h, int64_t coarse_steps
 
 vlbm_status vlbm_engine_release(vlbm_engine* e, int32_t slot) {
     if (!e || slot < 0 || slot >= (int)e->res.size() || !e->res[slot].live) return VLBM_ERR_ARG;
-    cudaStreamSynchronize(e->stream);
+    // a resident reported finished has no work left in flight; any other
+    // may still be in a queued launch
+    if (!e->res[slot].reported) cudaStreamSynchronize(e->stream);
     if (e->res[slot].tagging) {
         // a regrid left half done: its copies land before the slot is free
         cudaEventSynchronize(e->res[slot].h->rg_ev);
@@ -1874,9 +1887,14 @@ vlbm_status vlbm_engine_advance(vlbm_engine* e, int32_t max_steps, int32_t* fini
         // 0. second halves of the regrids whose block flags have arrived (all
         //    of them, waiting, when no other resident can step); the
         //    resident's steps resume after its regrid's kernels
-        bool runnable = false;
-        for (const auto& r : e->res)
-            if (r.live && !r.paused && r.done < r.target) runnable = true;
+        auto t0 = std::chrono::steady_clock::now();
+        e->times[VLBM_ET_CALLS] += 1;
+        auto can_step = [&] {
+            for (const auto& r : e->res)
+                if (r.live && !r.paused && r.done < r.target) return true;
+            return false;
+        };
+        bool runnable = can_step();
         for (auto& r : e->res) {
             if (!r.live || !r.tagging) continue;
             vlbm_hier* h = r.h;
@@ -1894,6 +1912,28 @@ vlbm_status vlbm_engine_advance(vlbm_engine* e, int32_t max_steps, int32_t* fini
             e->dirty = true;
             e->regridded = true;
         }
+        e->times[VLBM_ET_REGRID_FINISH] += ms_since(t0);
+        // residents whose last step has completed on the GPU are reported
+        // finished (waiting for them when no other resident can step), after
+        // a look at their status words
+        t0 = std::chrono::steady_clock::now();
+        runnable = can_step();
+        int nf = 0;
+        for (size_t i = 0; i < e->res.size(); i++) {
+            auto& r = e->res[i];
+            if (!r.live || !r.finishing) continue;
+            const cudaError_t q = runnable ? cudaEventQuery(r.ev) : cudaEventSynchronize(r.ev);
+            if (q == cudaErrorNotReady) continue;
+            VCK(q);
+            int st[2];
+            VCK(cudaMemcpy(st, r.h->words, sizeof st, cudaMemcpyDeviceToHost));
+            if (st[1]) r.h->poisoned = true, r.h->err = "non-physical state";
+            r.finishing = false;
+            r.reported = true;
+            if (finished) finished[nf] = (int)i;
+            nf++;
+        }
+        e->times[VLBM_ET_FINISH] += ms_since(t0);
         // 1. adaptive residents due for a regrid leave the batches; an event
         //    marks the end of their last step on the engine's stream
         std::vector<size_t> due;
@@ -1908,6 +1948,7 @@ vlbm_status vlbm_engine_advance(vlbm_engine* e, int32_t max_steps, int32_t* fini
                 e->dirty = true;
             }
         }
+        t0 = std::chrono::steady_clock::now();
         if (e->dirty) {
             // rebuild a batch only when its members changed (or, for the
             // adaptive batch, when one of them regridded): the persistent
@@ -1928,6 +1969,7 @@ vlbm_status vlbm_engine_advance(vlbm_engine* e, int32_t max_steps, int32_t* fini
             e->admitted = e->regridded = false;
             e->dirty = false;
         }
+        e->times[VLBM_ET_REBUILD] += ms_since(t0);
         // 2. as many steps of the other residents as none of them finishes or
         //    regrids in between
         long long k = max_steps;
@@ -1945,20 +1987,24 @@ vlbm_status vlbm_engine_advance(vlbm_engine* e, int32_t max_steps, int32_t* fini
         // capturing and instantiating a graph each time would cost more than
         // the launches)
         if (k > 0) {
+            t0 = std::chrono::steady_clock::now();
             cudaGraphExec_t gs = e->batch.members.empty() ? nullptr : e->batch.exec_for(0, e->stream);
             const bool phased = !e->phased.members.empty();
             for (long long i = 0; i < k; i++) {
                 if (gs) VCK(cudaGraphLaunch(gs, e->stream));
                 if (phased) e->phased.one_step(e->stream);
             }
+            e->times[VLBM_ET_LAUNCH] += ms_since(t0);
+            t0 = std::chrono::steady_clock::now();
             int& c = e->lead_i;
             if (!e->lead[c]) VCK(cudaEventCreateWithFlags(&e->lead[c], cudaEventDisableTiming));
             if (e->lead_set[c]) VCK(cudaEventSynchronize(e->lead[c]));  // the steps of two calls ago
             VCK(cudaEventRecord(e->lead[c], e->stream));
             e->lead_set[c] = true;
             c ^= 1;
+            e->times[VLBM_ET_LEAD] += ms_since(t0);
+            e->times[VLBM_ET_STEPS] += (double)k;
         }
-        int nf = 0;
         for (size_t i = 0; i < e->res.size(); i++) {
             auto& r = e->res[i];
             if (!r.live || r.paused || r.done >= r.target || k == 0) continue;
@@ -1969,8 +2015,10 @@ vlbm_status vlbm_engine_advance(vlbm_engine* e, int32_t max_steps, int32_t* fini
             for (int l = 0; l < r.h->nlev; l++) per += r.h->lev[l].active_cells << l;
             r.lups += per * k;
             if (r.done == r.target) {
-                if (finished) finished[nf] = (int)i;
-                nf++;
+                // reported by a later call, once this event has completed
+                if (!r.ev) VCK(cudaEventCreateWithFlags(&r.ev, cudaEventDisableTiming));
+                VCK(cudaEventRecord(r.ev, e->stream));
+                r.finishing = true;
                 e->dirty = true;
             }
         }
@@ -1985,6 +2033,7 @@ vlbm_status vlbm_engine_advance(vlbm_engine* e, int32_t max_steps, int32_t* fini
             VCK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
             VCK(cudaStreamCreateWithPriority(&e->hi, cudaStreamNonBlocking, hi));
         }
+        t0 = std::chrono::steady_clock::now();
         for (size_t i : due) {
             auto& r = e->res[i];
             vlbm_hier* h = r.h;
@@ -1992,20 +2041,9 @@ vlbm_status vlbm_engine_advance(vlbm_engine* e, int32_t max_steps, int32_t* fini
             on_stream(h, e->hi, [&] { tag_begin(h); });
             r.tagging = true;
         }
+        e->times[VLBM_ET_REGRID_BEGIN] += ms_since(t0);
         if (nfinished) *nfinished = nf;
         if (steps) *steps = (int32_t)k;
-        if (nf) {
-            // results of finished residents are read by the caller: make the
-            // steps visible and check the residents for non-physical states
-            VCK(cudaStreamSynchronize(e->stream));
-            for (size_t i = 0; i < e->res.size(); i++) {
-                auto& r = e->res[i];
-                if (!r.live || r.done != r.target) continue;
-                int st[2];
-                VCK(cudaMemcpy(st, r.h->words, sizeof st, cudaMemcpyDeviceToHost));
-                if (st[1]) r.h->poisoned = true, r.h->err = "non-physical state";
-            }
-        }
         return VLBM_OK;
     } catch (const Fail& f) {
         e->err = f.msg;

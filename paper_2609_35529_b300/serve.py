@@ -270,6 +270,8 @@ def main(argv=None):
     ap.add_argument("--verbose", action="store_true")
     ap.add_argument("--capacity-one", action="store_true",
                     help="also measure the one-at-a-time capacity (whole trace offered at t = 0)")
+    ap.add_argument("--capacity-only", action="store_true",
+                    help="stop after the capacity measurements (no latency runs, no oracle sample)")
     args = ap.parse_args(argv)
     import sys
     log = (lambda *a: print(*a, file=sys.stderr, flush=True)) if args.verbose else (lambda *a: None)
@@ -290,6 +292,12 @@ def main(argv=None):
     if args.capacity_one:
         _, cap1, cap1_wall = serve_one_at_a_time(reqs, stream=stream)
         log(f"capacity one at a time: {cap1:.1f} MLUPS, {cap1_wall:.1f} s")
+    if args.capacity_only:
+        out = {"requests": len(reqs), "total_lups": total, "capacity_mlups": round(cap_mlups, 1),
+               "capacity_one_at_a_time_mlups": round(cap1, 1) if cap1 else None,
+               "capacity_breakdown": serve_batched.breakdown}
+        print(json.dumps(out))
+        return out
     rate = args.load * len(reqs) / cap_wall
     schedule(reqs, rate, args.seed)
     sample = set(r.rid for r in sorted(reqs, key=lambda r: r.lups)[: args.oracle_sample])
@@ -403,7 +411,7 @@ def serve_batched(reqs, budget, stream=None, keep_ids=(), setup_stream=None):
     idle = None
     if marks:
         torch.cuda.synchronize()
-        idle = {"engine_calls": len(marks),
+        idle = {"engine_calls": len(marks), "engine_host_ms": eng.host_times(),
                 "stream_gap_s": sum(max(0.0, a[1].elapsed_time(b[0])) for a, b in zip(marks, marks[1:])) / 1e3,
                 "stream_busy_s": sum(max(0.0, a.elapsed_time(b)) for a, b in marks) / 1e3}
     eng.close()

@@ -106,6 +106,7 @@ def lib():
         "vlbm_engine_advance": [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)],
         "vlbm_engine_release": [vp, i32],
         "vlbm_engine_usage": [vp, C.POINTER(i32), C.POINTER(i64)],
+        "vlbm_engine_host_times": [vp, dp],
         "vlbm_engine_slot_stats": [vp, i32, C.POINTER(i64), C.POINTER(i64)],
     }
     for name, args in sig.items():
@@ -474,6 +475,16 @@ class Engine:
         b = C.c_int64()
         lib().vlbm_engine_usage(self._e, C.byref(n), C.byref(b))
         return n.value, b.value
+
+    def host_times(self):
+        """Host milliseconds of the engine's calls by activity, and the call
+        and step counts (vlbm_engine_host_times)."""
+        out = (C.c_double * 8)()
+        st = lib().vlbm_engine_host_times(self._e, out)
+        if st != 0:
+            raise VlbmError(st, "vlbm_engine_host_times")
+        names = ["regrid_finish", "finish", "rebuild", "launch", "lead", "regrid_begin", "calls", "steps"]
+        return {k: out[i] for i, k in enumerate(names)}
 
     def close(self):
         if getattr(self, "_e", None):

@@ -97,6 +97,39 @@ cudaMemPool_t library_pool() {
     return pools[dev];
 }
 
+// Pinned host memory for the library's staging buffers, from a process-wide
+// pool with power-of-two size classes: blocks are returned to the pool, not
+// to the driver, because freeing pinned memory (cudaFreeHost) waits for the
+// whole device -- a hierarchy destroyed while an engine's steps are queued
+// would drain them.  The pool keeps what it holds until the process exits.
+std::mutex pin_pool_mu;
+std::vector<std::vector<void*>> pin_pool(64);
+size_t pin_class(size_t n) {
+    size_t c = 12;  // 4 KiB at least
+    while (((size_t)1 << c) < n) c++;
+    return c;
+}
+void* pin_alloc(size_t n) {
+    const size_t c = pin_class(n);
+    {
+        std::lock_guard<std::mutex> g(pin_pool_mu);
+        if (!pin_pool[c].empty()) {
+            void* p = pin_pool[c].back();
+            pin_pool[c].pop_back();
+            return p;
+        }
+    }
+    void* p = nullptr;
+    VCK(cudaMallocHost(&p, (size_t)1 << c));
+    return p;
+}
+// n must be the size given to pin_alloc; no copy may still use the block
+void pin_free(void* p, size_t n) {
+    if (!p) return;
+    std::lock_guard<std::mutex> g(pin_pool_mu);
+    pin_pool[pin_class(n)].push_back(p);
+}
+
 // Pinned staging of host-to-device uploads inside a region (begin .. end):
 // a copy from pageable memory can make the host wait until the stream
 // reaches it, one from pinned memory never does.  Chunks are reused once the
@@ -123,8 +156,7 @@ struct PinArena {
         }
         if (ci == chunks.size()) {
             const size_t sz = std::max<size_t>(n, size_t(1) << 20);
-            uint8_t* p = nullptr;
-            VCK(cudaMallocHost((void**)&p, sz));
+            uint8_t* p = (uint8_t*)pin_alloc(sz);
             chunks.push_back({p, sz});
             off = 0;
         }
@@ -143,7 +175,7 @@ struct PinArena {
     void release() {
         if (on && s) cudaStreamSynchronize(s);
         if (pending && ev) cudaEventSynchronize(ev);
-        for (auto& c : chunks) cudaFreeHost(c.first);
+        for (auto& c : chunks) pin_free(c.first, c.second);
         chunks.clear();
         if (ev) cudaEventDestroy(ev);
         ev = nullptr;
@@ -355,13 +387,13 @@ struct Batch {
         if (exec1) cudaGraphExecDestroy(exec1);
         if (execG) cudaGraphExecDestroy(execG);
         exec1 = execG = nullptr;
-        if (stage_pending) cudaEventSynchronize(stage_ev);
-        stage_pending = false;
-        if (stage) cudaFreeHost(stage);
-        stage = nullptr;
-        stage_cap = 0;
-        if (stage_ev) cudaEventDestroy(stage_ev);
-        stage_ev = nullptr;
+        for (StageBuf& b : sbufs) {
+            if (b.pending) cudaEventSynchronize(b.ev);
+            pin_free(b.p, b.cap);
+            if (b.ev) cudaEventDestroy(b.ev);
+        }
+        sbufs.clear();
+        scur = -1;
         levs.release(*mem);
         for (int l = 0; l < VLBM_MAX_LEVELS; l++) {
             sweep[l].release(*mem);
@@ -448,7 +480,7 @@ struct Batch {
         // the engine's queue keeps running while a batch is rebuilt
         size_t need = tab.size() * sizeof(LevelDev) + pw.size() * sizeof(int*) + au.size() * sizeof(Item);
         for (int l = 0; l < VLBM_MAX_LEVELS; l++) need += (sw[l].size() + cl[l].size()) * sizeof(Item);
-        stage_begin(need + 16 * 256);
+        stage_begin(need);
         staged(levs, tab, s);
         for (int l = 0; l < VLBM_MAX_LEVELS; l++) {
             staged(sweep[l], sw[l], s);
@@ -462,23 +494,52 @@ struct Batch {
         valid = true;
     }
 
-    // Pinned staging of the table uploads.  A build waits (normally not at
-    // all) for the copies of the previous build before reusing the buffer.
-    char* stage = nullptr;
-    size_t stage_cap = 0, stage_off = 0;
-    cudaEvent_t stage_ev = nullptr;
-    bool stage_pending = false;
-    std::vector<std::pair<size_t, size_t>> stage_parts;
+    // Pinned staging of the table uploads: a small ring of buffers, each
+    // reused once the copies queued from it have completed, so that a
+    // rebuild never waits for the steps queued on the engine's stream (the
+    // copies are ordered after them).
+    struct StageBuf {
+        char* p = nullptr;
+        size_t cap = 0;
+        cudaEvent_t ev = nullptr;
+        bool pending = false;
+    };
+    std::vector<StageBuf> sbufs;
+    int scur = -1, slast = -1;
+    size_t stage_off = 0;
     void stage_begin(size_t need) {
-        if (stage_pending) VCK(cudaEventSynchronize(stage_ev));
-        stage_pending = false;
-        stage_off = 0;
-        if (need > stage_cap) {  // the buffer is idle here
-            if (stage) cudaFreeHost(stage);
-            stage = nullptr;
-            stage_cap = std::max(2 * stage_cap, need + (size_t)(1 << 20));
-            VCK(cudaMallocHost((void**)&stage, stage_cap));
+        need += 16 * 256;  // alignment of the parts
+        int pick = -1;
+        for (int i = 0; i < (int)sbufs.size() && pick < 0; i++) {
+            StageBuf& b = sbufs[i];
+            if (b.cap < need) continue;
+            if (b.pending) {
+                const cudaError_t q = cudaEventQuery(b.ev);
+                if (q == cudaErrorNotReady) continue;
+                VCK(q);
+                b.pending = false;
+            }
+            pick = i;
         }
+        if (pick < 0 && sbufs.size() < 8) {
+            sbufs.emplace_back();
+            pick = (int)sbufs.size() - 1;
+        }
+        if (pick < 0) {  // all eight in flight: wait for the one after the last used
+            pick = (slast + 1) % (int)sbufs.size();
+            VCK(cudaEventSynchronize(sbufs[pick].ev));
+            sbufs[pick].pending = false;
+        }
+        StageBuf& b = sbufs[pick];
+        if (b.cap < need) {  // idle here
+            pin_free(b.p, b.cap);
+            b.p = nullptr;
+            b.cap = std::max(2 * b.cap, need + (size_t)(1 << 20));
+            b.p = (char*)pin_alloc(b.cap);
+        }
+        if (!b.ev) VCK(cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming));
+        scur = pick;
+        stage_off = 0;
     }
     template <class T>
     void staged(DArr<T>& d, const std::vector<T>& v, cudaStream_t s) {
@@ -486,16 +547,19 @@ struct Batch {
         d.n = v.size();
         const size_t b = v.size() * sizeof(T);
         if (!b) return;
+        StageBuf& sb = sbufs[scur];
         const size_t off = (stage_off + 255) & ~size_t(255);
-        if (off + b > stage_cap) throw Fail{VLBM_ERR_ARG, "staging buffer too small"};  // sized by build()
-        std::memcpy(stage + off, v.data(), b);
-        VCK(cudaMemcpyAsync(d.p, stage + off, b, cudaMemcpyHostToDevice, s));
+        if (off + b > sb.cap) throw Fail{VLBM_ERR_ARG, "staging buffer too small"};  // sized by the caller
+        std::memcpy(sb.p + off, v.data(), b);
+        VCK(cudaMemcpyAsync(d.p, sb.p + off, b, cudaMemcpyHostToDevice, s));
         stage_off = off + b;
     }
     void stage_end(cudaStream_t s) {
-        if (!stage_ev) VCK(cudaEventCreateWithFlags(&stage_ev, cudaEventDisableTiming));
-        VCK(cudaEventRecord(stage_ev, s));
-        stage_pending = true;
+        StageBuf& sb = sbufs[scur];
+        VCK(cudaEventRecord(sb.ev, s));
+        sb.pending = true;
+        slast = scur;
+        scur = -1;
     }
 
     // eager launches with events around each kernel (profiling)
@@ -693,7 +757,6 @@ cudaGraphExec_t Batch::exec_for(int which, cudaStream_t s) {
     }
     if (!seg_ok[which]) {
         build_segments(which, which ? G : 1, s);
-        VCK(cudaStreamSynchronize(s));
         seg_ok[which] = true;
     }
     std::vector<uintptr_t> key = launch_key(which);
@@ -739,14 +802,17 @@ void Batch::build_segments(int which, int nsteps, cudaStream_t s) {
         pre.push_back(0);
     }
     ntotal[which] = pre.back();
-    segs[which].upload(*mem, sg, s);
-    prefix[which].upload(*mem, pre, s);
     std::vector<int> c(CTL_WORDS, 0);
     c[CTL_EPOCH] = 1;
     c[CTL_TOTAL] = pre.back();
     c[CTL_NSEG] = (int)members.size();
     c[CTL_FLIP] = nsteps & 1;
-    ctl[which].upload(*mem, c, s);
+    // pinned staging: the engine's queued steps keep running meanwhile
+    stage_begin(sg.size() * sizeof(Segment) + (pre.size() + c.size()) * sizeof(int));
+    staged(segs[which], sg, s);
+    staged(prefix[which], pre, s);
+    staged(ctl[which], c, s);
+    stage_end(s);
 }
 
 namespace {
@@ -1014,11 +1080,11 @@ void tag_begin(vlbm_hier* h) {
     if (h->rg_cap < 8 + nb) {
         if (h->rg_pin) {
             if (h->rg_ev) VCK(cudaEventSynchronize(h->rg_ev));  // a copy into the old buffer may be in flight
-            VCK(cudaFreeHost(h->rg_pin));
+            pin_free(h->rg_pin, h->rg_cap);
             h->rg_pin = nullptr;
             h->rg_cap = 0;
         }
-        VCK(cudaMallocHost((void**)&h->rg_pin, 8 + nb));
+        h->rg_pin = (uint8_t*)pin_alloc(8 + nb);
         h->rg_cap = 8 + nb;
     }
     if (!h->rg_ev) VCK(cudaEventCreateWithFlags(&h->rg_ev, cudaEventDisableTiming));
@@ -1174,15 +1240,15 @@ void destroy_levels(vlbm_hier* h) {
     h->bflag.release(h->mem);
     h->atab.release(h->mem);
     h->aitems.release(h->mem);
-    if (h->hout) cudaFreeHost(h->hout);
+    pin_free(h->hout, 8 * sizeof(double));
     h->hout = nullptr;
     h->pin.release();
-    if (h->rg_pin) cudaFreeHost(h->rg_pin);
+    pin_free(h->rg_pin, h->rg_cap);
     h->rg_pin = nullptr;
     h->rg_cap = 0;
     if (h->rg_ev) cudaEventDestroy(h->rg_ev);
     h->rg_ev = nullptr;
-    if (h->hist) cudaFreeHost(h->hist);
+    pin_free(h->hist, (size_t)h->hist_cap * 8 * sizeof(double));
     h->hist = nullptr;
     for (auto& L : h->tl) {
         L.dt.release(h->mem);
@@ -1545,7 +1611,7 @@ vlbm_status vlbm_set_step_totals(vlbm_hier* h, int32_t on) {
     return run(h, [&] {
         if (on && h->tune.schedule == 0) throw Fail{VLBM_ERR_ARG, "per-step totals need the persistent schedule"};
         if (on && h->sensor_on) throw Fail{VLBM_ERR_ARG, "per-step totals and the relaxation sensor exclude each other"};
-        if (on && !h->hist) VCK(cudaMallocHost((void**)&h->hist, (size_t)h->hist_cap * 8 * sizeof(double)));
+        if (on && !h->hist) h->hist = (double*)pin_alloc((size_t)h->hist_cap * 8 * sizeof(double));
         VCK(cudaStreamSynchronize(h->stream));
         h->step_audit = on != 0;
         h->hist_n = h->hist_read = 0;
@@ -1579,7 +1645,7 @@ vlbm_status vlbm_sync(vlbm_hier* h) {
 // Exact totals over the active cells of every level (two passes of
 // 192-bit fixed-point sums); one 64-byte read-back.
 static void audit_impl(vlbm_hier* h, double* totals, double* abs_totals) {
-    if (!h->hout) VCK(cudaMallocHost((void**)&h->hout, 8 * sizeof(double)));
+    if (!h->hout) h->hout = (double*)pin_alloc(8 * sizeof(double));
     VCK(launch_audit(h->atab.p, h->aitems.p, (int)h->aitems.n, h->partial.p, h->tot.p, h->stream));
     VCK(cudaMemcpyAsync(h->hout, h->tot.p, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     VCK(cudaStreamSynchronize(h->stream));

@@ -401,10 +401,10 @@ vlbm_status vlbm_engine_admit(vlbm_engine* e, vlbm_hier* h, int64_t coarse_steps
 
 /* Queues the next k coarse steps of every resident that can step, 1 <= k
  * <= max_steps, as many as no resident reaches its step count or an
- * adaptive resident its next regrid in between.  Static residents run on
- * the persistent task kernel, adaptive ones and those with the relaxation
- * sensor on per-phase launches; each resident's result is the same as when
- * it is advanced alone.  An adaptive resident due for a regrid pauses: the
+ * adaptive resident its next regrid in between.  Every resident runs on
+ * per-phase launches shared by all residents (one launch per level phase
+ * covers the tiles of every resident); each resident's result is the same
+ * as when it is advanced alone.  An adaptive resident due for a regrid pauses: the
  * first half of its regrid is queued on a high-priority stream, a later
  * call finishes it once its block flags are on the host.  Asynchronous:
  * the call waits only for the steps it queued two calls before, and for

@@ -386,9 +386,9 @@ void vlbm_destroy(vlbm_hier* h);
 /* ---- batching / serving engine ------------------------------------------ */
 
 /* An engine advances many resident hierarchies together: every engine step
- * is one coarse step of every resident, issued as one CUDA-graph launch in
- * which each phase of the sub-cycle (level-0 sweep, level-1 sweeps, ...)
- * processes the tiles of all residents.  mem_budget bounds the summed
+ * is one coarse step of every resident, issued as one launch per phase of
+ * the sub-cycle (level-0 sweep, level-1 sweeps, reflux closes, ...), each
+ * processing the tiles of all residents.  mem_budget bounds the summed
  * device memory of the residents (0 = no bound). */
 vlbm_status vlbm_engine_create(size_t mem_budget, void* stream, vlbm_engine** out);
 

@@ -52,24 +52,8 @@ __device__ __forceinline__ bool physical(double rho, double p) {
 }
 
 // BGK relaxation (Eq. 6) in place: f <- 2 beta f^eq(W) + (1 - 2 beta) f with
-// 2 beta f^eq_{+-alpha} = (beta/2) W +- (beta/c) Q_alpha (Eq. 4, D = 2).
-__device__ __forceinline__ bool collide(double f[16], double om, double hb, double bcs, double gm1) {
-    double W[4], Qx[4], Qy[4], p;
-#pragma unroll
-    for (int k = 0; k < 4; k++) W[k] = (f[k] + f[4 + k]) + (f[8 + k] + f[12 + k]);
-    euler_flux(gm1, W, Qx, Qy, p);
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        const double A = hb * W[k];
-        f[k] = fma(bcs, Qx[k], fma(om, f[k], A));
-        f[4 + k] = fma(-bcs, Qx[k], fma(om, f[4 + k], A));
-        f[8 + k] = fma(bcs, Qy[k], fma(om, f[8 + k], A));
-        f[12 + k] = fma(-bcs, Qy[k], fma(om, f[12 + k], A));
-    }
-    return physical(W[0], p);
-}
-
-// The same collision with a chosen subset of its additions and
+// 2 beta f^eq_{+-alpha} = (beta/2) W +- (beta/c) Q_alpha (Eq. 4, D = 2), and
+// a chosen subset of its additions and
 // multiplications carried out by the bit-exact integer-pipe routines
 // (fp64emu.cuh); the results are identical bit for bit, only the pipe that
 // computes them changes.  Policy bits: EM_MOM the twelve moment additions,
@@ -891,36 +875,6 @@ __global__ void end_step_kernel(int* const* par, int n) {
     if (t < n) *par[t] ^= 1;
 }
 
-// Block b sums the audit slots [rng[b].x, rng[b].y), thread t the column
-// t (field t / 64); the block's 8 exact sums go to part[b][0..23] (W_0..W_3,
-// then |W_0|..|W_3|).
-__global__ void __launch_bounds__(256) audit_slots_kernel(const double* __restrict__ aw, const int2* __restrict__ rng,
-                                                          const int* __restrict__ scale,
-                                                          unsigned long long* __restrict__ part) {
-    __shared__ Fix192 s_part[8][2];
-    const int t = threadIdx.x;
-    const int2 r = rng[blockIdx.x];
-    Fix192 sum = fix_zero(), abs_sum = fix_zero();
-    audit_thread_sums<false>(aw, scale, r.x, r.y, t, sum, abs_sum);
-    for (int off = 16; off > 0; off >>= 1) {
-        const Fix192 o1 = fix_shfl_down(sum, off);
-        const Fix192 o2 = fix_shfl_down(abs_sum, off);
-        fix_add(sum, o1);
-        fix_add(abs_sum, o2);
-    }
-    if ((t & 31) == 0) {
-        s_part[t >> 5][0] = sum;
-        s_part[t >> 5][1] = abs_sum;
-    }
-    __syncthreads();
-    if (t < 8) {
-        const int k = t & 3, a = t >> 2;  // quantity t: field k, a = 1 for |W|
-        Fix192 v = s_part[2 * k][a];
-        fix_add(v, s_part[2 * k + 1][a]);
-        for (int i = 0; i < 3; i++) part[(size_t)blockIdx.x * 24 + 3 * t + i] = v.w[i];
-    }
-}
-
 // Totals from exact partial sums: segment b covers partials [seg[b],
 // seg[b+1]) (seg == nullptr: one segment [0, n)); out[b][0..3] = sum w W_k,
 // out[b][4..7] = sum w |W_k|, each the correctly rounded exact sum.
@@ -1472,12 +1426,6 @@ cudaError_t launch_audit_segments(const unsigned long long* slots, const int* se
     return cudaGetLastError();
 }
 
-cudaError_t launch_audit_slots(const double* aw, const int2* rng, const int* scale, int nblk,
-                               unsigned long long* part, cudaStream_t s) {
-    if (nblk <= 0) return cudaSuccess;
-    audit_slots_kernel<<<nblk, AUDIT_SLOT, 0, s>>>(aw, rng, scale, part);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_close(const LevelDev* levs, const Item* items, int n, int kk, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;

@@ -17,8 +17,6 @@ cudaError_t launch_tasks(const LevelDev* levs, const Segment* segs, const int* p
                          cudaStream_t s);
 cudaError_t launch_audit_segments(const unsigned long long* slots, const int* seg, int nseg, double* out,
                                   cudaStream_t s);
-cudaError_t launch_audit_slots(const double* aw, const int2* rng, const int* scale, int nblk,
-                               unsigned long long* part, cudaStream_t s);
 cudaError_t launch_close(const LevelDev* levs, const Item* items, int n, int kk, cudaStream_t s);
 cudaError_t launch_end_step(int* const* par, int n, cudaStream_t s);
 cudaError_t launch_feq_init(const LevelDev& L, const double* W, long long ld, double hc, cudaStream_t s);

@@ -278,16 +278,29 @@ class Hierarchy:
         _check(self._h, lib().vlbm_get_layout(self._h, level, a.ctypes.data, b.ctypes.data))
         return a, b
 
-    def get_conserved(self, level, totals=False):
-        W = np.zeros((4,) + self.shapes[level])
-        v = np.zeros(self.shapes[level], dtype=np.uint8)
+    def get_conserved(self, level, totals=False, out=None, valid=True):
+        """W of every cell of `level` (shape (4, ny, nx)) and the mask of the
+        cells whose W is meaningful.  `out`: a caller-owned float64 array of
+        that shape to fill (C-contiguous; pinned host memory makes the copy
+        run at full PCIe speed); valid=False skips the mask (returned as
+        None)."""
+        shape = (4,) + self.shapes[level]
+        if out is None:
+            W = np.zeros(shape)
+        else:
+            W = out
+            if W.shape != shape or W.dtype != np.float64 or not W.flags["C_CONTIGUOUS"]:
+                raise ValueError("out must be a C-contiguous float64 array of shape %s" % (shape,))
+        v = np.zeros(self.shapes[level], dtype=np.uint8) if valid else None
         t = (C.c_double * 4)()
         a = (C.c_double * 4)()
-        _check(self._h, lib().vlbm_get_conserved(self._h, level, W.ctypes.data, W.shape[2], v.ctypes.data,
+        _check(self._h, lib().vlbm_get_conserved(self._h, level, W.ctypes.data, W.shape[2],
+                                                 v.ctypes.data if valid else None,
                                                  t if totals else None, a if totals else None))
+        vm = v.astype(bool) if valid else None
         if totals:
-            return W, v.astype(bool), np.array(t[:]), np.array(a[:])
-        return W, v.astype(bool)
+            return W, vm, np.array(t[:]), np.array(a[:])
+        return W, vm
 
     def audit(self):
         t = (C.c_double * 4)()

@@ -586,3 +586,19 @@ def test_sensor_driven_relaxation_matches_oracle(V, which):
         assert np.array_equal(g2.get_populations(l)[:, act], g.get_populations(l)[:, act])
     e.release(slot)
     e.close()
+
+
+def test_get_conserved_into_caller_buffer(V):
+    """Reading W into a caller-owned (pinned) buffer gives the same values as
+    the default read."""
+    import torch
+    cs = I.pulse2l(steps=6)
+    g = V.Hierarchy.from_case(cs)
+    g.advance(cs.steps)
+    for l in range(cs.nlev):
+        W, _ = g.get_conserved(l)
+        buf = torch.empty(W.shape, dtype=torch.float64).pin_memory().numpy()
+        W2, v2 = g.get_conserved(l, out=buf, valid=False)
+        assert v2 is None and W2 is buf
+        assert np.array_equal(W, W2)
+    g.close()

@@ -396,6 +396,10 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(round(launches_per_iter * iters)),
+                # per timed iteration (`chunk` coarse steps, L2 flushed before each)
+                "iterations": {"n": iters, "steps_each": chunk,
+                               "best_mlups": round(lups * chunk / (min(it_ms) * 1e-3) / 1e6, 1),
+                               "median_mlups": round(lups * chunk / (statistics.median(it_ms) * 1e-3) / 1e6, 1)},
                 "conservation": {"max_rel_drift_over_timed_steps": drift, "audited_steps": len(rows)},
                 "clocks": clk.summary()}
         print(json.dumps(line))

@@ -39,6 +39,19 @@ class Request:
     lups: int = 0
     lups_done: int = 0
     bytes_est: int = 0
+    digest: dict = field(default_factory=dict)  # run name -> bit-pattern digest of the final W
+
+
+def digest(W, act):
+    """A 64-bit digest of the bit patterns of W on the meaningful cells: equal
+    results give equal digests, and a change of any bit changes it (save
+    for a 2^-64 chance)."""
+    v = np.ascontiguousarray(W[:, act]).view(np.uint64).ravel()
+    if v.size == 0:
+        return 0
+    with np.errstate(over="ignore"):
+        mixed = v * np.uint64(0x9E3779B97F4A7C15) + np.arange(v.size, dtype=np.uint64)
+    return int(np.bitwise_xor.reduce(mixed)) ^ int(mixed.sum(dtype=np.uint64))
 
 
 def level_bytes(nx0, ny0, nlev):
@@ -205,6 +218,7 @@ def serve_one_at_a_time(reqs, stream=None):
                 h.regrid()
         W, act = h.get_conserved(0)
         r.done_at = time.perf_counter() - t0
+        r.digest["alone"] = digest(W, act)
         total_lups += r.lups_done
         h.close()
     wall = time.perf_counter() - t0
@@ -321,7 +335,12 @@ def main(argv=None):
                        "p99_s": float(np.percentile(tts_b, 99)), "wall_s": wall_b, "breakdown": breakdown},
            "one_at_a_time": {"mlups": round(ml_1, 1), "p50_s": float(np.percentile(tts_1, 50)),
                              "p99_s": float(np.percentile(tts_1, 99)), "wall_s": wall_1},
-           "oracle_sample": len(sample), "oracle_worst_rel_err": worst}
+           "oracle_sample": len(sample), "oracle_worst_rel_err": worst,
+           # every request's level-0 W (active and averaged-down cells) in the
+           # batched run against the same request served alone
+           "alone_vs_mix": {"compared": sum(1 for r in reqs if len(r.digest) == 2),
+                            "bitwise_equal": sum(1 for r in reqs if len(r.digest) == 2
+                                                 and r.digest["alone"] == r.digest["batched"])}}
     print(json.dumps(out))
     return out
 
@@ -376,6 +395,7 @@ def serve_batched(reqs, budget, stream=None, keep_ids=(), setup_stream=None):
                 r.lups_done = eng.slot_stats(slot)[1]
                 W, act = h.get_conserved(0)
                 r.done_at = time.perf_counter() - t0
+                r.digest["batched"] = digest(W, act)
                 if r.rid in keep_ids:
                     r.result = [h.get_populations(l) for l in range(h.nlev)]
                 total_lups += r.lups_done

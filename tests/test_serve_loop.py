@@ -128,3 +128,25 @@ def test_one_at_a_time_loop_finishes_every_request(fakes):
     assert len(tts) == len(reqs) and all(r.done_at is not None for r in reqs)
     assert calls["n"] == len(reqs)
     assert all(h.closed for h in made)
+
+
+def test_result_digest_sees_every_bit():
+    """The alone-vs-mix comparison's digest: equal results give equal
+    digests, one flipped bit or two swapped cells give another."""
+    from paper_2609_35529_b300.serve import digest
+    rng = np.random.default_rng(3)
+    W = rng.standard_normal((4, 16, 24))
+    act = rng.random((16, 24)) > 0.3
+    d0 = digest(W, act)
+    assert digest(W.copy(), act) == d0
+    W2 = W.copy()
+    W2.view(np.uint64)[2, 5, 7] ^= np.uint64(1)
+    if act[5, 7]:
+        assert digest(W2, act) != d0
+    else:
+        assert digest(W2, act) == d0  # masked cells do not count
+    cells = np.argwhere(act)
+    (a0, b0), (a1, b1) = cells[0], cells[1]
+    W3 = W.copy()
+    W3[:, a0, b0], W3[:, a1, b1] = W[:, a1, b1], W[:, a0, b0]
+    assert digest(W3, act) != d0

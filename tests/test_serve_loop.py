@@ -130,9 +130,22 @@ def test_one_at_a_time_loop_finishes_every_request(fakes):
     assert all(h.closed for h in made)
 
 
+@pytest.mark.timeout(120)
+def test_both_loops_feed_the_alone_vs_mix_comparison(fakes):
+    made, calls = fakes
+    reqs = S.make_requests(8, seed=5, nmax=256)
+    for r in reqs:
+        r.arrival = 0.0
+        r.steps = 6
+    S.serve_batched(reqs, budget=1 << 40, verify=True)
+    S.serve_one_at_a_time(reqs, verify=True)
+    assert S.alone_vs_mix(reqs) == {"compared": len(reqs), "bitwise_equal": len(reqs)}
+
+
 def test_result_digest_sees_every_bit():
     """The alone-vs-mix comparison's digest: equal results give equal
-    digests, one flipped bit or two swapped cells give another."""
+    digests, one flipped bit, two swapped cells or two swapped fields give
+    another."""
     from paper_2609_35529_b300.serve import digest
     rng = np.random.default_rng(3)
     W = rng.standard_normal((4, 16, 24))
@@ -150,3 +163,6 @@ def test_result_digest_sees_every_bit():
     W3 = W.copy()
     W3[:, a0, b0], W3[:, a1, b1] = W[:, a1, b1], W[:, a0, b0]
     assert digest(W3, act) != d0
+    W4 = W.copy()
+    W4[0, a0, b0], W4[1, a0, b0] = W[1, a0, b0], W[0, a0, b0]  # two fields of one cell
+    assert digest(W4, act) != d0

@@ -3,13 +3,14 @@
 Requests (2-D Riemann quadrant problems or isentropic vortices of different
 sizes and refinement layouts) arrive by a seeded Poisson process.  The loop
 admits arrived requests while the engine's device-memory budget allows
-(setting each one up on its own stream, overlapping the queued work), lets
-the engine advance every resident request by up to 16 coarse steps per call
-(each step: one persistent-kernel launch for the static residents, one graph
-of per-phase launches for the adaptive ones), and returns each result to
-the host as soon as its step count is met; freed memory admits the next
-requests.  The same arrival trace can be served one request at a time
-(each request alone on the GPU, its own graph launches) for comparison.
+(setting each one up on its own high-priority stream, overlapping the
+queued work), lets the engine advance every resident request by up to 16
+coarse steps per call (each step: one launch per level phase covering the
+tiles of every resident), and returns each result to the host once its last
+step has completed; freed memory admits the next requests.  The same arrival
+trace can be served one request at a time (each request alone on the GPU,
+with the auto schedule) for comparison, and every request's result is
+checked bit for bit against its run alone.
 
 Times are wall-clock from a request's arrival to its result on the host.
 """

@@ -314,11 +314,10 @@ def test_engine_results_equal_alone_and_in_mix(V):
 
 @pytest.mark.parametrize("max_steps", [1, 5, 16])
 def test_engine_static_and_adaptive_residents_equal_alone(V, max_steps):
-    """Continuous batching with static residents (persistent task kernel)
-    and adaptive residents regridding every 4 of their own steps (per-phase
-    launches) admitted at different times: every result is bit-identical to
-    the same request advanced alone, whatever the number of steps per
-    engine call."""
+    """Continuous batching with static residents and adaptive residents
+    regridding every 4 of their own steps (all on shared per-phase launches)
+    admitted at different times: every result is bit-identical to the same
+    request advanced alone, whatever the number of steps per engine call."""
     def adaptive_case(steps):
         return I.shockbubble(nx0=64, ny0=32, nlev=3, steps=steps)
 

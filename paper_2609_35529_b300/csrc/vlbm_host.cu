@@ -11,6 +11,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "vlbm.h"
@@ -375,7 +376,6 @@ struct Batch {
     DArr<LevelDev> levs;
     DArr<Item> sweep[VLBM_MAX_LEVELS], close[VLBM_MAX_LEVELS];
     DArr<int*> par;
-    DArr<Item> audit_items;
     cudaGraphExec_t exec1 = nullptr, execG = nullptr;
     int G = 8;
     bool sensor = false;  // some member runs the sensor-driven relaxation (per-phase schedule)
@@ -400,7 +400,6 @@ struct Batch {
             close[l].release(*mem);
         }
         par.release(*mem);
-        audit_items.release(*mem);
         for (int w = 0; w < 2; w++) {
             segs[w].release(*mem);
             prefix[w].release(*mem);
@@ -452,42 +451,50 @@ struct Batch {
             exec1 = execG = nullptr;
             for (auto& c : captured) c.clear();
         }
-        std::vector<LevelDev> tab;
-        std::vector<Item> sw[VLBM_MAX_LEVELS], cl[VLBM_MAX_LEVELS], au;
-        std::vector<int*> pw;
+        // sizes first, then every table written once, straight into a pinned
+        // staging buffer, and copied from there (no stream synchronisation:
+        // the engine's queue keeps running while a batch is rebuilt)
+        size_t ntab = 0, nsw[VLBM_MAX_LEVELS] = {}, ncl[VLBM_MAX_LEVELS] = {};
         maxlev = 0;
         sensor = false;
         for (vlbm_hier* h : members) {
-            const int base = (int)tab.size();
+            ntab += h->nlev;
             for (int l = 0; l < h->nlev; l++) {
-                tab.push_back(h->dev(l, l ? base + l - 1 : -1, l + 1 < h->nlev ? base + l + 1 : -1));
+                nsw[l] += h->lev[l].act.size();
+                if (l + 1 < h->nlev) ncl[l] += h->lev[l].ring.size();
+            }
+            maxlev = std::max(maxlev, h->nlev);
+            sensor = sensor || h->sensor_on;
+        }
+        size_t need = ntab * sizeof(LevelDev) + members.size() * sizeof(int*);
+        for (int l = 0; l < VLBM_MAX_LEVELS; l++) need += (nsw[l] + ncl[l]) * sizeof(Item);
+        stage_begin(need);
+        LevelDev* tab = stage_part(levs, ntab);
+        int** pw = stage_part(par, members.size());
+        Item *sw[VLBM_MAX_LEVELS], *cl[VLBM_MAX_LEVELS];
+        for (int l = 0; l < VLBM_MAX_LEVELS; l++) {
+            sw[l] = stage_part(sweep[l], nsw[l]);
+            cl[l] = stage_part(close[l], ncl[l]);
+        }
+        int base = 0;
+        for (size_t m = 0; m < members.size(); m++) {
+            vlbm_hier* h = members[m];
+            for (int l = 0; l < h->nlev; l++) {
+                *tab++ = h->dev(l, l ? base + l - 1 : -1, l + 1 < h->nlev ? base + l + 1 : -1);
                 for (Item it : h->lev[l].act) {
                     it.lid = base + l;
-                    sw[l].push_back(it);
-                    au.push_back(it);
+                    *sw[l]++ = it;
                 }
                 if (l + 1 < h->nlev)
                     for (Item it : h->lev[l].ring) {
                         it.lid = base + l;
-                        cl[l].push_back(it);
+                        *cl[l]++ = it;
                     }
             }
-            maxlev = std::max(maxlev, h->nlev);
-            pw.push_back(h->words);
-            sensor = sensor || h->sensor_on;
+            pw[m] = h->words;
+            base += h->nlev;
         }
-        // uploads from a pinned staging buffer: no stream synchronisation,
-        // the engine's queue keeps running while a batch is rebuilt
-        size_t need = tab.size() * sizeof(LevelDev) + pw.size() * sizeof(int*) + au.size() * sizeof(Item);
-        for (int l = 0; l < VLBM_MAX_LEVELS; l++) need += (sw[l].size() + cl[l].size()) * sizeof(Item);
-        stage_begin(need);
-        staged(levs, tab, s);
-        for (int l = 0; l < VLBM_MAX_LEVELS; l++) {
-            staged(sweep[l], sw[l], s);
-            staged(close[l], cl[l], s);
-        }
-        staged(par, pw, s);
-        staged(audit_items, au, s);
+        stage_copies(s);
         stage_end(s);
         // the one-step and G-step graphs (and task lists) are built when first used
         seg_ok[0] = seg_ok[1] = false;
@@ -553,6 +560,27 @@ struct Batch {
         std::memcpy(sb.p + off, v.data(), b);
         VCK(cudaMemcpyAsync(d.p, sb.p + off, b, cudaMemcpyHostToDevice, s));
         stage_off = off + b;
+    }
+    // A part of n elements of the current staging buffer for d (resized to
+    // n), to be filled by the caller and copied by stage_copies.
+    std::vector<std::tuple<void*, size_t, size_t>> stage_pending_copies;
+    template <class T>
+    T* stage_part(DArr<T>& d, size_t n) {
+        d.ensure(*mem, n);
+        d.n = n;
+        StageBuf& sb = sbufs[scur];
+        const size_t off = (stage_off + 255) & ~size_t(255);
+        const size_t b = n * sizeof(T);
+        if (off + b > sb.cap) throw Fail{VLBM_ERR_ARG, "staging buffer too small"};  // sized by the caller
+        stage_off = off + b;
+        if (b) stage_pending_copies.emplace_back((void*)d.p, off, b);
+        return (T*)(sb.p + off);
+    }
+    void stage_copies(cudaStream_t s) {
+        StageBuf& sb = sbufs[scur];
+        for (auto& c : stage_pending_copies)
+            VCK(cudaMemcpyAsync(std::get<0>(c), sb.p + std::get<1>(c), std::get<2>(c), cudaMemcpyHostToDevice, s));
+        stage_pending_copies.clear();
     }
     void stage_end(cudaStream_t s) {
         StageBuf& sb = sbufs[scur];

@@ -407,7 +407,7 @@ vlbm_status vlbm_engine_admit(vlbm_engine* e, vlbm_hier* h, int64_t coarse_steps
  * as when it is advanced alone.  An adaptive resident due for a regrid pauses: the
  * first half of its regrid is queued on a high-priority stream, a later
  * call finishes it once its block flags are on the host.  Asynchronous:
- * the call waits only for the steps it queued two calls before, and for
+ * the call waits only for the steps it queued four calls before, and for
  * pending regrids or finishing residents when no resident can step.
  * finished_slots (capacity = the largest slot + 1) receives the residents
  * whose step count is met and whose last step has completed on the GPU --
@@ -443,7 +443,7 @@ vlbm_status vlbm_engine_usage(const vlbm_engine* e, int32_t* residents, int64_t*
  *   REBUILD        batch tables, task lists and graphs after a change of
  *                  members or layouts
  *   LAUNCH         queueing the steps (graph and per-phase launches)
- *   LEAD           waiting for the steps queued two calls before
+ *   LEAD           waiting for the steps queued four calls before
  *   REGRID_BEGIN   first halves of residents' regrids queued
  * and the counts CALLS (engine calls) and STEPS (coarse steps queued, the
  * sum of k).  Errors: ERR_ARG. */

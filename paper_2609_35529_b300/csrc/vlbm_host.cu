@@ -1184,11 +1184,12 @@ struct vlbm_engine {
     bool regridded = false;  // an adaptive resident changed its layout since the last rebuild
     bool admitted = true;    // a resident was admitted or released since the last rebuild
     cudaStream_t hi = nullptr;  // high-priority stream of the residents' regrids
-    // the ends of the steps queued by the last two calls: a call waits for
-    // the steps queued two calls before, so the host stays at most two
+    // the ends of the steps queued by the last LEAD calls: a call waits for
+    // the steps queued LEAD calls before, so the host stays at most LEAD
     // calls ahead of the GPU
-    cudaEvent_t lead[2] = {nullptr, nullptr};
-    bool lead_set[2] = {false, false};
+    static constexpr int LEAD = 4;  // deep enough to cover a burst of admissions
+    cudaEvent_t lead[LEAD] = {};
+    bool lead_set[LEAD] = {};
     int lead_i = 0;
     double times[VLBM_ET_COUNT] = {};  // host time by activity, see vlbm_engine_host_times
     std::string err = "no error";
@@ -2081,10 +2082,10 @@ vlbm_status vlbm_engine_advance(vlbm_engine* e, int32_t max_steps, int32_t* fini
             t0 = std::chrono::steady_clock::now();
             int& c = e->lead_i;
             if (!e->lead[c]) VCK(cudaEventCreateWithFlags(&e->lead[c], cudaEventDisableTiming));
-            if (e->lead_set[c]) VCK(cudaEventSynchronize(e->lead[c]));  // the steps of two calls ago
+            if (e->lead_set[c]) VCK(cudaEventSynchronize(e->lead[c]));  // the steps of LEAD calls ago
             VCK(cudaEventRecord(e->lead[c], e->stream));
             e->lead_set[c] = true;
-            c ^= 1;
+            c = (c + 1) % vlbm_engine::LEAD;
             e->times[VLBM_ET_LEAD] += ms_since(t0);
             e->times[VLBM_ET_STEPS] += (double)k;
         }

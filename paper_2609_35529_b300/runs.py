@@ -71,9 +71,9 @@ def l2_errors(h, case, exact_levels):
         Ex = exact_levels[l]
         a = dx0 / 2 ** l
         e_rho += float(np.sum((W[0][act] - Ex[0][act]) ** 2)) * a * a
-        sp = np.hypot(W[1] / W[0], W[2] / W[0])
-        se = np.hypot(Ex[1] / Ex[0], Ex[2] / Ex[0])
-        e_u += float(np.sum((sp[act] - se[act]) ** 2)) * a * a
+        sp = np.hypot(W[1][act] / W[0][act], W[2][act] / W[0][act])  # W is meaningful on `act` only
+        se = np.hypot(Ex[1][act] / Ex[0][act], Ex[2][act] / Ex[0][act])
+        e_u += float(np.sum((sp - se) ** 2)) * a * a
     return math.sqrt(e_rho), math.sqrt(e_u)
 
 

@@ -10,7 +10,7 @@ conserved state is ``W[4, ny, nx]`` with fields (rho, rho*u, rho*v, rho*E);
 a refinement mask ``ref[l]`` is ``uint8[ny_l, nx_l]`` on the level it refines
 (1 = covered by level l+1).  Cell centres sit at ``(i + 0.5) * dx_l``.
 
-Recipes (the paper's workloads, read as documented in the design doc):
+Recipes (the paper's workloads):
   * ``pulse2l``      two-level Gaussian density pulse straddling a patch edge
   * ``vortex``       advected isentropic vortex (Sec. 4.1.3, Eq. 30) with a
                      central ratio-2 patch

@@ -393,7 +393,8 @@ void vlbm_destroy(vlbm_hier* h);
 vlbm_status vlbm_engine_create(size_t mem_budget, void* stream, vlbm_engine** out);
 
 /* Admits h (created on the same device; the engine borrows it until release)
- * for coarse_steps steps; adaptive hierarchies (tag_tol > 0) regrid every
+ * for coarse_steps steps (0: reported finished, unchanged, by the next
+ * vlbm_engine_advance); adaptive hierarchies (tag_tol > 0) regrid every
  * regrid_every coarse steps (0 = never).  Errors: ERR_OOM when admitting
  * would exceed the budget (not admitted, try later), ERR_ARG. */
 vlbm_status vlbm_engine_admit(vlbm_engine* e, vlbm_hier* h, int64_t coarse_steps,

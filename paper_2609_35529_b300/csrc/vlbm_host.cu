@@ -1952,6 +1952,13 @@ vlbm_status vlbm_engine_admit(vlbm_engine* e, vlbm_hier* h, int64_t coarse_steps
     e->res[s].live = true;
     h->engine = e;
     e->dirty = true;
+    if (coarse_steps == 0) {
+        // nothing to do: reported finished by the next call
+        auto& r = e->res[s];
+        if (!r.ev && cudaEventCreateWithFlags(&r.ev, cudaEventDisableTiming) != cudaSuccess) return VLBM_ERR_CUDA;
+        if (cudaEventRecord(r.ev, e->stream) != cudaSuccess) return VLBM_ERR_CUDA;
+        r.finishing = true;
+    }
     if (slot) *slot = s;
     return VLBM_OK;
 }

@@ -601,3 +601,54 @@ def test_get_conserved_into_caller_buffer(V):
         assert v2 is None and W2 is buf
         assert np.array_equal(W, W2)
     g.close()
+
+
+@pytest.mark.parametrize("schedule,graph_steps", [(0, 8), (1, 3)])
+def test_four_levels_maximum_depth(V, schedule, graph_steps):
+    """The deepest hierarchy the library takes: four levels, each nested in
+    the previous one with a one-block margin (eight level-3 sub-steps per
+    coarse step), per-phase and persistent schedules: bitwise equal to the
+    oracle, totals conserved."""
+    n = 40
+    refs = I.box_refs(n, n, 4, [(0, 8, 8, 24, 24)])
+    refs[1][24:56, 24:56] = 1
+    refs[2][56:104, 56:104] = 1
+    cs = I.smooth_random(n, n, 4, refs, seed=71, amp=0.2, beta=0.9, steps=6)
+    g = V.Hierarchy.from_case(cs)
+    g.set_tuning(variant=1, graph_steps=graph_steps, schedule=schedule)
+    o = oracle_of(cs)
+    t0, a0 = g.audit()
+    g.advance(cs.steps)
+    o.advance(cs.steps)
+    compare(o, g, 4)
+    t1, _ = g.audit()
+    assert drift(t0, t1, a0) < 1e-13
+    g.close()
+
+
+def test_degenerate_calls(V):
+    """advance(0) changes nothing; an engine with nothing resident queues no
+    steps and reports nothing; a resident admitted for zero steps is
+    reported finished, unchanged."""
+    cs = I.pulse2l(steps=3)
+    g = V.Hierarchy.from_case(cs)
+    before = [g.get_populations(l) for l in range(cs.nlev)]
+    g.advance(0)
+    for l in range(cs.nlev):
+        assert np.array_equal(g.get_populations(l), before[l])
+    e = V.Engine()
+    fin, k = e.advance(4)
+    assert list(fin) == [] and k == 0
+    slot = e.admit(g, 0)
+    done = []
+    for _ in range(3):
+        fin, k = e.advance(4)
+        done += list(fin)
+        if done:
+            break
+    assert done == [slot]
+    e.release(slot)
+    for l in range(cs.nlev):
+        assert np.array_equal(g.get_populations(l), before[l])
+    e.close()
+    g.close()

@@ -255,50 +255,6 @@ def serve_one_at_a_time(reqs, stream=None, verify=False):
     return tts, total_lups / wall / 1e6, wall
 
 
-def run_oracle(req):
-    """The oracle's answer for one request (test infrastructure: used only to
-    check agreement on a sample of the trace)."""
-    from oracle import oracle as O
-    cs = make_case(req)
-    o = O.Hierarchy(cs.nx0, cs.ny0, cs.nlev, 2, cs.bc, cs.gamma, cs.c, cs.beta, cs.inflow)
-    o.set_layout(None)
-    o.set_state(0, cs.W[0])
-    if req.adaptive:
-        for _ in range(cs.nlev - 1):
-            o.regrid_tagged(cs.amr["tol"], cs.amr["buffer"], 8)
-    elif cs.nlev > 1:
-        o.regrid(cs.refs)
-    left = cs.steps
-    every = 4 if req.adaptive else 0
-    while left > 0:
-        n = min(left, every) if every else left
-        o.advance(n)
-        left -= n
-        if every and left > 0:
-            o.regrid_tagged(cs.amr["tol"], cs.amr["buffer"], 8)
-    return o
-
-
-def agreement(req, oracle_h):
-    """Worst field-wise relative difference between the served result and the
-    oracle, over every level's active cells (0.0 = identical)."""
-    worst = 0.0
-    for l, fg in enumerate(req.result):
-        a, b = oracle_h.layout(l)
-        act = (a == 1) & (b == 0)
-        fo = oracle_h.get_f(l)
-        Wg = fg.reshape(4, 4, *fg.shape[1:]).sum(axis=0)
-        Wo = fo.reshape(4, 4, *fo.shape[1:]).sum(axis=0)
-        for k in range(4):
-            if not act.any():
-                continue
-            scale = max(float(np.max(np.abs(Wo[k][act]))), 1e-300)
-            worst = max(worst, float(np.max(np.abs(Wg[k][act] - Wo[k][act]))) / scale)
-        if not np.array_equal(fg[:, act], fo[:, act]):
-            worst = max(worst, 1e-300)
-    return worst
-
-
 def alone_vs_mix(reqs):
     ds = [_digests(r) for r in reqs]
     both = [d for d in ds if "alone" in d and "batched" in d]
@@ -306,20 +262,31 @@ def alone_vs_mix(reqs):
 
 
 def main(argv=None):
-    import argparse
+    """Runs the benchmark and prints its JSON summary."""
     import json
+    out, _ = run(argv)
+    print(json.dumps(out))
+    return out
+
+
+def run(argv=None):
+    """The serving benchmark.  Returns (summary, requests); the requests of
+    the --keep-sample smallest ones still hold their batched results
+    (`Request.result`, per-level populations) for a caller that checks them."""
+    import argparse
     ap = argparse.ArgumentParser(description="continuous-batching VLBM serving benchmark")
     ap.add_argument("--requests", type=int, default=512)
     ap.add_argument("--seed", type=int, default=20261202)
     ap.add_argument("--load", type=float, default=0.75, help="arrival rate as a fraction of batched capacity")
     ap.add_argument("--mem-gb", type=float, default=160.0)
-    ap.add_argument("--oracle-sample", type=int, default=32)
+    ap.add_argument("--keep-sample", type=int, default=0,
+                    help="keep the batched results of this many of the smallest requests")
     ap.add_argument("--nmax", type=int, default=1024)
     ap.add_argument("--verbose", action="store_true")
     ap.add_argument("--capacity-one", action="store_true",
                     help="also measure the one-at-a-time capacity (whole trace offered at t = 0)")
     ap.add_argument("--capacity-only", action="store_true",
-                    help="stop after the capacity measurements (no latency runs, no oracle sample)")
+                    help="stop after the capacity measurements (no latency runs)")
     args = ap.parse_args(argv)
     import sys
     log = (lambda *a: print(*a, file=sys.stderr, flush=True)) if args.verbose else (lambda *a: None)
@@ -346,20 +313,14 @@ def main(argv=None):
         out = {"requests": len(reqs), "total_lups": total, "capacity_mlups": round(cap_mlups, 1),
                "capacity_one_at_a_time_mlups": round(cap1, 1) if cap1 else None,
                "capacity_breakdown": serve_batched.breakdown}
-        print(json.dumps(out))
-        return out
+        return out, reqs
     rate = args.load * len(reqs) / cap_wall
     schedule(reqs, rate, args.seed)
-    sample = set(r.rid for r in sorted(reqs, key=lambda r: r.lups)[: args.oracle_sample])
+    sample = set(r.rid for r in sorted(reqs, key=lambda r: r.lups)[: args.keep_sample])
     tts_b, ml_b, wall_b = serve_batched(reqs, budget, stream, sample, setup_stream=setup, verify=True)
     breakdown = serve_batched.breakdown
     log(f"batched: {ml_b:.1f} MLUPS, {wall_b:.1f} s, {breakdown}")
-    worst = 0.0
-    for r in reqs:
-        if r.rid in sample:
-            worst = max(worst, agreement(r, run_oracle(r)))
-            r.result = None
-    log(f"oracle sample: worst rel err {worst:.3g}")
+    kept = {r.rid: r.result for r in reqs if r.rid in sample}
     tts_1, ml_1, wall_1 = serve_one_at_a_time(reqs, stream=stream, verify=True)
     log(f"one at a time: {ml_1:.1f} MLUPS, {wall_1:.1f} s")
     out = {"requests": len(reqs), "total_lups": total, "capacity_mlups": round(cap_mlups, 1),
@@ -369,12 +330,12 @@ def main(argv=None):
                        "p99_s": float(np.percentile(tts_b, 99)), "wall_s": wall_b, "breakdown": breakdown},
            "one_at_a_time": {"mlups": round(ml_1, 1), "p50_s": float(np.percentile(tts_1, 50)),
                              "p99_s": float(np.percentile(tts_1, 99)), "wall_s": wall_1},
-           "oracle_sample": len(sample), "oracle_worst_rel_err": worst,
            # every request's level-0 W (active and averaged-down cells) in the
            # batched run against the same request served alone
            "alone_vs_mix": alone_vs_mix(reqs)}
-    print(json.dumps(out))
-    return out
+    for r in reqs:
+        r.result = kept.get(r.rid)
+    return out, reqs
 
 
 # coarse steps queued per engine call: the GPU works through them while the

@@ -649,3 +649,30 @@ def test_stationary_vortex_second_order_with_and_without_patch():
         orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
         assert orders[-1] > 0.9 * g["vortex_order"], (patch, errs, orders)
         assert orders[0] > 1.6
+
+
+@pytest.mark.slow
+def test_explosion_in_a_box_drift_within_the_papers_values():
+    """Sec. 4.2: explosion in a box with reflective walls, N0 = 256 plus the
+    centred ratio-2 patch over [0.25, 0.75]^2, sampled every 0.05 up to
+    t = 0.5.  The paper's refined run drifts at most 3.2e-14 in mass and
+    5.3e-14 in energy; walls exchange no mass or energy, so the oracle's
+    drift (exact sums of its state) must stay within those values."""
+    g = golden("paper_numbers.txt")
+    cs = I.explosion(N=256, beta=0.9)
+    h = O.Hierarchy(cs.nx0, cs.ny0, cs.nlev, 2, cs.bc, cs.gamma, cs.c, cs.beta)
+    h.set_layout(cs.refs)
+    for l in range(cs.nlev):
+        h.set_state(l, cs.W[l])
+    t0, _ = h.totals()
+    dt = cs.dx0 / cs.c
+    done, worst_m, worst_e = 0, 0.0, 0.0
+    for i in range(10):
+        s = int(round(0.05 * (i + 1) / dt))
+        h.advance(s - done)
+        done = s
+        t1, _ = h.totals()
+        worst_m = max(worst_m, abs(t1[0] - t0[0]) / t0[0])
+        worst_e = max(worst_e, abs(t1[3] - t0[3]) / t0[3])
+    assert worst_m <= g["explosion_mass_drift"], worst_m
+    assert worst_e <= g["explosion_energy_drift"], worst_e

@@ -150,17 +150,27 @@ vlbm_status vlbm_get_populations(vlbm_hier* h, int32_t level, double* f, int64_t
 
 /* Advances `coarse_steps` coarse steps (each: one level-0 step, two level-1
  * steps per level-0 step, and so on, with reconstruction and reflux at every
- * interface).  Asynchronous on the handle's stream; launches a captured CUDA
- * graph.  Errors: ERR_ARG (negative), ERR_CUDA, ERR_STATE. */
+ * interface; Sec. 3.2, Fig. 1 and Eq. 15 for the sub-cycle, Sec. 3.3, Eqs.
+ * 20-24 for the coupling, Sec. 2.2, Eqs. 4-6 for the level update).
+ * Asynchronous on the handle's stream: launches captured CUDA graphs, and
+ * after a layout change first builds the persistent schedule's task lists
+ * on the device.  Deferred errors (non-physical state, a timed-out wait, a
+ * device layout or task list that did not fit) are reported by the next
+ * synchronising call.  Errors: ERR_ARG (negative), ERR_CUDA, ERR_STATE. */
 vlbm_status vlbm_advance(vlbm_hier* h, int64_t coarse_steps);
 
 /* Regrid (Sec. 3.4, Fig. 2).  boxes != NULL: the new layout is the union of
- * the boxes (validated like vlbm_create_hierarchy).  boxes == NULL: the
- * layout is derived from the indicator cfg->tag_sensor (VLBM_SENSOR_*) with
- * cfg->tag_tol and cfg->tag_buffer, rounded to blocks and grown so that every
- * level nests.  Cells leaving refinement take the merge of their children,
- * cells entering refinement are split (finest level first for merges,
- * coarsest first for splits).  Synchronises the stream.
+ * the boxes (validated like vlbm_create_hierarchy); synchronises the
+ * stream.  boxes == NULL: the layout is derived from the indicator
+ * cfg->tag_sensor (VLBM_SENSOR_*) with cfg->tag_tol and cfg->tag_buffer,
+ * rounded to blocks and grown so that every level nests; for a hierarchy
+ * outside an engine this runs on the device alone and is asynchronous (the
+ * indicator, block flags, layout rule, merge, split, flags and tile lists
+ * are queued on the stream and the host never waits), a nesting violation
+ * then being reported as ERR_NESTING by the next synchronising call.  Cells
+ * leaving refinement take the merge of their children (Eq. 25), cells
+ * entering refinement are split (Eqs. 26-27) -- finest level first for
+ * merges, coarsest first for splits.
  * Errors: ERR_ARG, ERR_NESTING (layout unchanged), ERR_CUDA, ERR_STATE,
  * ERR_NONPHYSICAL (from an earlier advance). */
 vlbm_status vlbm_regrid(vlbm_hier* h, const vlbm_box* boxes, int32_t nboxes);
@@ -189,7 +199,18 @@ vlbm_status vlbm_audit(vlbm_hier* h, double totals[4], double abs_totals[4]);
 /* Waits for the stream and reports deferred device errors. */
 vlbm_status vlbm_sync(vlbm_hier* h);
 
+/* Sizes, active cells per level and cell updates per coarse step of the
+ * current layout.  After a tag-driven regrid (which runs on the device
+ * alone) this synchronises the stream to fetch the new layout.
+ * Errors: ERR_ARG, ERR_CUDA, ERR_STATE. */
 vlbm_status vlbm_get_info(const vlbm_hier* h, vlbm_info* info);
+
+/* Cell updates done since the hierarchy was created: the sum over every
+ * coarse step taken of sum_l active_cells_l * 2^l, counted on the device at
+ * the layout each step ran on (so it stays exact across regrids that the
+ * host never waited for).  Synchronises.
+ * Errors: ERR_ARG, ERR_CUDA, ERR_NONPHYSICAL, ERR_STATE. */
+vlbm_status vlbm_lups_done(vlbm_hier* h, int64_t* lups);
 
 /* Host-side time the library has spent on a hierarchy since its creation,
  * in milliseconds (wall clock, cumulative), by activity:
@@ -312,6 +333,23 @@ vlbm_status vlbm_selftest_rcp(uint64_t seed, int64_t n, uint64_t* mismatches, ui
  * <= beta, c_sensor >= 0, eps >= 0; resident in an engine; per-step totals
  * on), ERR_OOM, ERR_CUDA, ERR_STATE. */
 vlbm_status vlbm_set_sensor(vlbm_hier* h, int32_t on, double beta_min, double c_sensor, double eps);
+
+/* Self-test of the device-resident layouts (no counterpart in the paper:
+ * it checks this library's own machinery).  `cases` seeded random
+ * hierarchies (2-4 levels, ragged sizes, periodic or not per axis), each
+ * regridded three times from random block flags on the device alone; after
+ * each regrid the device's block maps, tile lists (active, ring, covered,
+ * on-level, in row-major order), reconstruction map and active cell counts
+ * must equal those the host computes from the same flags with its layout
+ * rule, and the persistent schedule's task list built on the device for
+ * 1-3 coarse steps must equal the host builder's task for task and
+ * dependency for dependency.  *mismatches counts differences;
+ * *second_pass (may be NULL) the tasks whose dependency set outgrew the
+ * builder's small per-thread set and took its second pass; first_bad (may
+ * be NULL, `cap` bytes) describes the first difference.  Runs on the
+ * current device, synchronises.  Errors: ERR_ARG, ERR_OOM, ERR_CUDA. */
+vlbm_status vlbm_selftest_layout(uint64_t seed, int32_t cases, int64_t* mismatches, int64_t* second_pass,
+                                 char* first_bad, int32_t cap);
 
 /* Self-test of the bounded waits of the persistent task kernel (schedule
  * 1): launches it on one task that depends on a completion mark nothing

@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libvlbm.so")
-SOURCES = ["vlbm_kernels.cu", "vlbm_host.cu", "vlbm_selftest.cu", "vlbm_noalloc.cu", "vlbm_waittest.cu"]
+SOURCES = ["vlbm_kernels.cu", "vlbm_amr.cu", "vlbm_host.cu", "vlbm_selftest.cu", "vlbm_noalloc.cu", "vlbm_waittest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,808 @@
+// Device-resident layouts and task lists (see vlbm_amr.h).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "vlbm_amr.h"
+
+namespace vlbm {
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// CTA-wide prefix sums
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int warp_incl(int v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// Exclusive scan of one value per thread over the CTA (blockDim.x a
+// multiple of 32, at most 1024); returns the thread's offset, *total the
+// CTA's sum.
+__device__ int cta_excl(int v, int* sm, int* total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    const int inc = warp_incl(v);
+    if (lane == 31) sm[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        int x = lane < nw ? sm[lane] : 0;
+        x = warp_incl(x);
+        if (lane < nw) sm[lane] = x;
+    }
+    __syncthreads();
+    const int base = w ? sm[w - 1] : 0;
+    *total = sm[nw - 1];
+    __syncthreads();
+    return base + inc - v;
+}
+
+// ---------------------------------------------------------------------------
+// layout rule, derived maps, nesting
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int wrap_or(int v, int n, int per, bool& ok) {
+    if (v < 0 || v >= n) {
+        if (!per) {
+            ok = false;
+            return 0;
+        }
+        v = ((v % n) + n) % n;
+    }
+    return v;
+}
+
+// Whether the one-cell-widened extent of child block ib (child level of n
+// cells, periodic or not) holds a cell whose parent cell lies in parent block
+// pb: the cells 8 ib - 1 .. min(n, 8 ib + 8), wrapped or dropped at the
+// sides, parent cell x >> 1, its block (x >> 1) / 8.
+__device__ bool widened_touches(int ib, int n, int per, int pb) {
+    const int x0 = ib * TILE - 1, x1 = min(n, ib * TILE + TILE) + 1;
+    for (int x = x0; x < x1; x++) {
+        int xx = x;
+        if (xx < 0 || xx >= n) {
+            if (!per) continue;
+            xx = (xx + n) % n;
+        }
+        if (((xx >> 1) / TILE) == pb) return true;
+    }
+    return false;
+}
+
+__global__ void layout_rule_kernel(LayoutDev L, LayoutDev F, int has_f, const uint8_t* __restrict__ bflag) {
+    const long long nb = (long long)L.bx * L.by;
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb; b += (long long)gridDim.x * blockDim.x) {
+        const int ib = (int)(b % L.bx), jb = (int)(b / L.bx);
+        uint8_t cov = bflag[b] ? 1 : 0;
+        if (has_f && !cov) {
+            // candidate child blocks: a window around the children of this
+            // block, wrapped on periodic sides (duplicates do not matter)
+            for (int dj = -3; dj <= 4 && !cov; dj++) {
+                bool oky = true;
+                const int cj = wrap_or(2 * jb + dj, F.by, F.py, oky);
+                if (!oky) continue;
+                if (!widened_touches(cj, F.ny, F.py, jb)) continue;
+                for (int di = -3; di <= 4; di++) {
+                    bool okx = true;
+                    const int ci = wrap_or(2 * ib + di, F.bx, F.px, okx);
+                    if (!okx) continue;
+                    if (!F.ncov[(long long)cj * F.bx + ci]) continue;
+                    if (widened_touches(ci, F.nx, F.px, ib)) {
+                        cov = 1;
+                        break;
+                    }
+                }
+            }
+        }
+        L.ncov[b] = cov;
+    }
+}
+
+__global__ void derive_in_kernel(LayoutDev P, LayoutDev L, int level0) {
+    const long long nb = (long long)L.bx * L.by;
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb; b += (long long)gridDim.x * blockDim.x) {
+        if (level0) {
+            L.nin[b] = 1;
+            continue;
+        }
+        const int ib = (int)(b % L.bx), jb = (int)(b / L.bx);
+        const long long pb = (long long)(jb >> 1) * P.bx + (ib >> 1);
+        L.nin[b] = (P.nin[pb] && P.ncov[pb]) ? 1 : 0;
+    }
+}
+
+__global__ void nest_check_kernel(LayoutDev L, int finest, int* status) {
+    const long long nb = (long long)L.bx * L.by;
+    bool bad = false;
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb; b += (long long)gridDim.x * blockDim.x) {
+        if (!L.ncov[b]) continue;
+        if (finest || !L.nin[b]) {
+            bad = true;
+            continue;
+        }
+        if (L.level == 0) continue;
+        const int ib = (int)(b % L.bx), jb = (int)(b / L.bx);
+        const int di[4] = {1, -1, 0, 0}, dj[4] = {0, 0, 1, -1};
+        for (int d = 0; d < 4; d++) {
+            bool ok = true;
+            const int i2 = wrap_or(ib + di[d], L.bx, L.px, ok), j2 = wrap_or(jb + dj[d], L.by, L.py, ok);
+            if (ok && !L.nin[(long long)j2 * L.bx + i2]) bad = true;
+        }
+    }
+    if (bad) atomicOr(status, ST_NESTING);
+}
+
+__global__ void commit_maps_kernel(LayoutDev L) {
+    const long long nb = (long long)L.bx * L.by;
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb; b += (long long)gridDim.x * blockDim.x) {
+        L.bin[b] = L.nin[b];
+        L.bcov[b] = L.ncov[b];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// tile lists by compaction (row-major block order)
+// ---------------------------------------------------------------------------
+
+constexpr int LIST_T = 256, LIST_E = LAY_CHUNK / LIST_T;
+
+struct Member {
+    uint8_t bits;   // 1 << LST_*
+    uint8_t recon;  // active with a face neighbour off the level
+};
+
+__device__ __forceinline__ Member member(const LayoutDev& L, long long b) {
+    Member m{0, 0};
+    const int ib = (int)(b % L.bx), jb = (int)(b / L.bx);
+    const bool in = L.bin[b] != 0, covb = L.bcov[b] != 0;
+    const bool cov = in && covb, act = in && !covb;
+    if (in) m.bits |= 1u << LST_IN;
+    if (cov) m.bits |= 1u << LST_COV;
+    if (act) {
+        m.bits |= 1u << LST_ACT;
+        bool ring = false, rec = false;
+        const int di[4] = {1, -1, 0, 0}, dj[4] = {0, 0, 1, -1};
+        for (int d = 0; d < 4; d++) {
+            bool ok = true;
+            const int i2 = wrap_or(ib + di[d], L.bx, L.px, ok), j2 = wrap_or(jb + dj[d], L.by, L.py, ok);
+            if (!ok) continue;
+            const long long b2 = (long long)j2 * L.bx + i2;
+            ring = ring || (L.bin[b2] && L.bcov[b2]);
+            rec = rec || !L.bin[b2];
+        }
+        if (ring) m.bits |= 1u << LST_RING;
+        m.recon = rec;
+    }
+    if (L.nin && L.ncov) {
+        const bool ncov = L.nin[b] && L.ncov[b];
+        if (cov && !ncov) m.bits |= 1u << LST_EXIT;
+        if (ncov && !cov) m.bits |= 1u << LST_ENTER;
+        if (in || L.nin[b]) m.bits |= 1u << LST_TOUCH;
+    }
+    return m;
+}
+
+__global__ void lists_count_kernel(LayoutDev L, int mask) {
+    __shared__ int sm[32];
+    const long long nb = (long long)L.bx * L.by;
+    const int c = blockIdx.x;
+    int n[NLST] = {};
+    for (int e = 0; e < LIST_E; e++) {
+        const long long b = (long long)c * LAY_CHUNK + threadIdx.x * LIST_E + e;
+        if (b >= nb) break;
+        const Member m = member(L, b);
+        for (int k = 0; k < NLST; k++) n[k] += (m.bits & mask) >> k & 1;
+    }
+    for (int k = 0; k < NLST; k++) {
+        if (!(mask >> k & 1)) continue;
+        int tot;
+        cta_excl(n[k], sm, &tot);
+        if (threadIdx.x == 0) L.chunk[k * L.nchunk + c] = tot;
+    }
+}
+
+// one CTA per list: exclusive chunk offsets, the list length, and (act) the
+// reset of the active cell count
+__global__ void lists_scan_kernel(LayoutDev L, int mask) {
+    __shared__ int sm[32];
+    const int k = blockIdx.x;
+    if (!(mask >> k & 1)) return;
+    int carry = 0;
+    for (int b = 0; b < L.nchunk; b += blockDim.x) {
+        const int i = b + threadIdx.x;
+        const int v = i < L.nchunk ? L.chunk[k * L.nchunk + i] : 0;
+        int tot;
+        const int off = cta_excl(v, sm, &tot);
+        if (i < L.nchunk) L.chunk[k * L.nchunk + i] = carry + off;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        L.cnt[k] = carry;
+        if (k == LST_ACT) *L.cells = 0ull;
+    }
+}
+
+__global__ void lists_scatter_kernel(LayoutDev L, int mask, int lid) {
+    __shared__ int sm[32];
+    const long long nb = (long long)L.bx * L.by;
+    const int c = blockIdx.x;
+    Member m[LIST_E];
+    int n[NLST] = {};
+    for (int e = 0; e < LIST_E; e++) {
+        const long long b = (long long)c * LAY_CHUNK + threadIdx.x * LIST_E + e;
+        m[e] = b < nb ? member(L, b) : Member{0, 0};
+        for (int k = 0; k < NLST; k++) n[k] += (m[e].bits & mask) >> k & 1;
+    }
+    int off[NLST];
+    for (int k = 0; k < NLST; k++) {
+        off[k] = 0;
+        if (!(mask >> k & 1)) continue;
+        int tot;
+        off[k] = L.chunk[k * L.nchunk + c] + cta_excl(n[k], sm, &tot);
+    }
+    const bool maps = (mask >> LST_ACT) & 1;
+    unsigned long long cells = 0;
+    for (int e = 0; e < LIST_E; e++) {
+        const long long b = (long long)c * LAY_CHUNK + threadIdx.x * LIST_E + e;
+        if (b >= nb) break;
+        const int ib = (int)(b % L.bx), jb = (int)(b / L.bx);
+        const Item it{lid, (unsigned short)ib, (unsigned short)jb};
+        const uint8_t bits = m[e].bits & mask;
+        for (int k = 0; k < NLST; k++)
+            if (bits >> k & 1) L.list[k][off[k]++] = it;
+        if (maps) {
+            const bool act = bits >> LST_ACT & 1;
+            L.act_idx[b] = act ? off[LST_ACT] - 1 : -1;
+            L.ring_idx[b] = (bits >> LST_RING & 1) ? off[LST_RING] - 1 : -1;
+            L.recon[b] = m[e].recon;
+            if (act)
+                cells += (unsigned long long)(min(L.nx, ib * TILE + TILE) - ib * TILE) *
+                         (unsigned long long)(min(L.ny, jb * TILE + TILE) - jb * TILE);
+        }
+    }
+    if (maps) {
+        for (int o = 16; o > 0; o >>= 1) cells += __shfl_down_sync(0xffffffffu, cells, o);
+        if ((threadIdx.x & 31) == 0 && cells) atomicAdd(L.cells, cells);
+    }
+}
+
+// bit 0: some sweep of the level pushes into the block (an active block
+// among the block and its four face neighbours, by the push targets of the
+// task builder); bit 1: a reflux close writes it (a ring block)
+__global__ void wmask_kernel(LayoutDev L) {
+    const long long nb = (long long)L.bx * L.by;
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb; b += (long long)gridDim.x * blockDim.x) {
+        const int tx = (int)(b % L.bx), ty = (int)(b / L.bx);
+        const int sdi[5] = {0, 1, -1, 0, 0}, sdj[5] = {0, 0, 0, 1, -1};
+        uint8_t m = 0;
+        for (int d = 0; d < 5 && !m; d++) {
+            bool ok = true;
+            const int sx = wrap_or(tx - sdi[d], L.bx, L.px, ok), sy = wrap_or(ty - sdj[d], L.by, L.py, ok);
+            if (!ok) continue;
+            bool ok2 = true;
+            const int rx = wrap_or(sx + sdi[d], L.bx, L.px, ok2), ry = wrap_or(sy + sdj[d], L.by, L.py, ok2);
+            if (!ok2 || rx != tx || ry != ty) continue;
+            if (L.act_idx[(long long)sy * L.bx + sx] >= 0) m = 1;
+        }
+        if (L.ring_idx[b] >= 0) m |= 2;
+        L.wm[b] = m;
+    }
+}
+
+// parent tiles under the reconstruction footprint of child tile (tx, ty):
+// the parent cells 4 t - 1 .. 4 t + 4 on each axis, wrapped or dropped
+__device__ int foot_keys(const LayoutDev& P, int tx, int ty, int* keys) {
+    int ns = 0;
+    for (int cy2 = ty * TILE / 2 - 1; cy2 <= ty * TILE / 2 + TILE / 2; cy2++)
+        for (int cx2 = tx * TILE / 2 - 1; cx2 <= tx * TILE / 2 + TILE / 2; cx2++) {
+            bool ok = true;
+            const int xx = wrap_or(cx2, P.nx, P.px, ok), yy = wrap_or(cy2, P.ny, P.py, ok);
+            if (!ok) continue;
+            const int key = (yy / TILE) * P.bx + xx / TILE;
+            bool dup = false;
+            for (int q = 0; q < ns; q++) dup = dup || keys[q] == key;
+            if (dup || ns == 16) continue;
+            keys[ns++] = key;
+        }
+    return ns;
+}
+
+__global__ void footprints_kernel(LayoutDev P, LayoutDev C, int* status) {
+    const int n = C.cnt[LST_ACT];
+    bool ovf = false;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const Item it = C.list[LST_ACT][i];
+        if (!C.recon[(long long)it.ty * C.bx + it.tx]) continue;
+        int keys[16];
+        const int nk = foot_keys(P, it.tx, it.ty, keys);
+        for (int q = 0; q < nk; q++) {
+            const int slot = atomicAdd(P.fcnt + keys[q], 1);
+            if (slot < FOOT_CAP) P.fidx[(long long)keys[q] * FOOT_CAP + slot] = i;
+            else ovf = true;
+        }
+    }
+    if (ovf) atomicOr(status, ST_TASKCAP);
+}
+
+__global__ void foot_clamp_kernel(LayoutDev P) {
+    const long long nb = (long long)P.bx * P.by;
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb; b += (long long)gridDim.x * blockDim.x)
+        if (P.fcnt[b] > FOOT_CAP) P.fcnt[b] = FOOT_CAP;
+}
+
+struct ActRef {
+    const Item* list[4];
+    const int* cnt[4];
+    int cap[4];
+};
+
+__global__ void concat_act_kernel(ActRef R, int nl, Item* __restrict__ out, int* __restrict__ n_out) {
+    int off[5];
+    off[0] = 0;
+    for (int l = 0; l < nl; l++) off[l + 1] = off[l] + R.cnt[l][LST_ACT];
+    if (blockIdx.x == 0 && threadIdx.x == 0) *n_out = off[nl];
+    for (int l = 0; l < nl; l++) {
+        const int n = R.cnt[l][LST_ACT];
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+            Item it = R.list[l][i];
+            it.lid = l;
+            out[off[l] + i] = it;
+        }
+    }
+}
+
+__global__ void count_lups_kernel(const unsigned long long* c0, const unsigned long long* c1,
+                                  const unsigned long long* c2, const unsigned long long* c3, int nl, long long steps,
+                                  unsigned long long* counter) {
+    const unsigned long long* c[4] = {c0, c1, c2, c3};
+    unsigned long long s = 0;
+    for (int l = 0; l < nl; l++) s += *c[l] << l;
+    *counter += s * (unsigned long long)steps;
+}
+
+static inline int flat_blocks(long long n) {
+    long long g = (n + 255) / 256;
+    if (g > 148LL * 16) g = 148LL * 16;
+    return (int)(g < 1 ? 1 : g);
+}
+
+// ---------------------------------------------------------------------------
+// task lists (the device form of build_tasks in vlbm_tasks.h)
+// ---------------------------------------------------------------------------
+
+// A task's dependency set: up to TB_SMALL entries in registers (one thread
+// per task, many threads in flight: the work is chains of table lookups,
+// latency bound); the rare task with more dependencies is redone by a
+// second pass with a TB_MAXDEP-entry set in local memory.  Adversarial
+// layouts (most cells refined, checkerboard coverage) reached 98 distinct
+// dependencies; beyond TB_MAXDEP the build raises ST_TASKCAP (reported as
+// VLBM_ERR_OOM).
+constexpr int TB_SMALL = TASK_DEP_SLOT;
+constexpr int TB_MAXDEP = 256;
+constexpr int TB_BUILD_THREADS = 128;
+__constant__ int kSDI[5] = {0, 1, -1, 0, 0};
+__constant__ int kSDJ[5] = {0, 0, 0, 1, -1};
+
+__device__ __forceinline__ int src_of(int level, int kk, int step) { return level == 0 ? (step & 1) : (kk == 1 ? 0 : 1); }
+
+// The common case: a set of at most TB_SMALL entries held in registers
+// (every index below is a compile-time constant after unrolling), so the
+// whole L1 stays free for the table lookups.
+struct DepSetR {
+    int v[TB_SMALL];
+    int n;
+    bool ovf;
+    __device__ __forceinline__ void add(int q) {
+        bool found = false;
+#pragma unroll
+        for (int i = 0; i < TB_SMALL; i++) found |= (i < n) && (v[i] == q);
+        if (found) return;
+        if (n >= TB_SMALL) {
+            ovf = true;
+            return;
+        }
+#pragma unroll
+        for (int i = 0; i < TB_SMALL; i++)
+            if (i == n) v[i] = q;
+        n++;
+    }
+    // ascending (odd-even transposition over the first n entries)
+    __device__ __forceinline__ void sort() {
+#pragma unroll
+        for (int r = 0; r < TB_SMALL; r++) {
+#pragma unroll
+            for (int i = r & 1; i + 1 < TB_SMALL; i += 2) {
+                if (i + 1 < n && v[i] > v[i + 1]) {
+                    const int x = v[i];
+                    v[i] = v[i + 1];
+                    v[i + 1] = x;
+                }
+            }
+        }
+    }
+    __device__ __forceinline__ void store(int* out) const {
+#pragma unroll
+        for (int i = 0; i < TB_SMALL; i++)
+            if (i < n) out[i] = v[i];
+    }
+};
+
+// The rare larger set, in local memory.
+struct DepSet {
+    int* v;      // entry i at v[i * stride]
+    int stride;
+    int cap;
+    int n;
+    bool ovf;
+    __device__ void store(int* out) const {
+        for (int i = 0; i < n; i++) out[i] = at(i);
+    }
+    __device__ void add(int q) {
+        for (int i = 0; i < n; i++)
+            if (v[i * stride] == q) return;
+        if (n < cap) v[(n++) * stride] = q;
+        else ovf = true;
+    }
+    __device__ int at(int i) const { return v[i * stride]; }
+    __device__ void put(int i, int q) { v[i * stride] = q; }
+    // ascending, like the host builder
+    __device__ void sort() {
+        for (int a = 1; a < n; a++) {
+            const int x = at(a);
+            int b = a - 1;
+            while (b >= 0 && at(b) > x) {
+                put(b + 1, at(b));
+                b--;
+            }
+            put(b + 1, x);
+        }
+    }
+};
+
+// parent tiles read by the reconstruction of fine tile (tx, ty): the coarse
+// tiles under the coarse cells [4 t - 1, 4 t + 4] in each direction
+__device__ int footprint(const TBLevel& P, int tx, int ty, int* keys) {
+    int ns = 0;
+    const int c0x = tx * TILE / 2 - 1, c1x = tx * TILE / 2 + TILE / 2;
+    const int c0y = ty * TILE / 2 - 1, c1y = ty * TILE / 2 + TILE / 2;
+    for (int cy2 = c0y; cy2 <= c1y; cy2++)
+        for (int cx2 = c0x; cx2 <= c1x; cx2++) {
+            bool ok = true;
+            const int xx = wrap_or(cx2, P.nx, P.px, ok), yy = wrap_or(cy2, P.ny, P.py, ok);
+            if (!ok) continue;
+            const int key = (yy / TILE) * P.bx + xx / TILE;
+            bool dup = false;
+            for (int q = 0; q < ns; q++) dup = dup || keys[q] == key;
+            if (dup || ns == 16) continue;
+            keys[ns++] = key;
+        }
+    return ns;
+}
+
+// The builder's view of a plan: the static tables (phases, accesses,
+// offsets) read from shared memory, everything else from the plan.
+struct TB {
+    const TBPlan& P;
+    const TBPhase* ph;
+    const TBAcc* acc;
+    const int* acc_beg;
+    const int* acc_pos;
+    const int* off;
+    __device__ explicit TB(const TBPlan& p) : P(p) {}
+
+    template <class F>
+    __device__ void touching(const TBAcc& a, int l, int tx, int ty, F&& emit) const {
+        const int base = off[a.phase];
+        switch (a.pat) {
+            case TB_OWN: {
+                const int i = P.lev[l].act_idx[ty * P.lev[l].bx + tx];
+                if (i >= 0) emit(base + i);
+                break;
+            }
+            case TB_STENCIL: {
+                const TBLevel& V = P.lev[l];
+                for (int d = 0; d < 5; d++) {
+                    bool ok = true;
+                    const int sx = wrap_or(tx - kSDI[d], V.bx, V.px, ok), sy = wrap_or(ty - kSDJ[d], V.by, V.py, ok);
+                    if (!ok) continue;
+                    bool ok2 = true;
+                    const int rx = wrap_or(sx + kSDI[d], V.bx, V.px, ok2), ry = wrap_or(sy + kSDJ[d], V.by, V.py, ok2);
+                    if (!ok2 || rx != tx || ry != ty) continue;
+                    const int i = V.act_idx[sy * V.bx + sx];
+                    if (i >= 0) emit(base + i);
+                }
+                break;
+            }
+            case TB_FOOT: {  // reconstructing tiles of level l + 1 whose footprint holds (tx, ty)
+                const TBLevel& Pl = P.lev[l];
+                const int key = ty * Pl.bx + tx;
+                const int n = Pl.fcnt[key];
+                for (int j = 0; j < n; j++) emit(base + Pl.fidx[key * FOOT_CAP + j]);
+                break;
+            }
+            case TB_CHILD4: {
+                const TBLevel& Pl = P.lev[l - 1];
+                const int i = Pl.ring_idx[(ty / 2) * Pl.bx + tx / 2];
+                if (i >= 0) emit(base + i);
+                break;
+            }
+            case TB_OWNRING: {
+                const int i = P.lev[l].ring_idx[ty * P.lev[l].bx + tx];
+                if (i >= 0) emit(base + i);
+                break;
+            }
+        }
+    }
+
+    // bit 0: some sweep of level l pushes into the tile; bit 1: a close writes it
+    __device__ int wmask(int l, int tx, int ty) const {
+        const TBLevel& V = P.lev[l];
+        const int m = V.wm[ty * V.bx + tx];
+        return (l + 1 < P.nlev) ? m : (m & 1);
+    }
+
+    template <class Set>
+    __device__ __forceinline__ void deps_of(int p, bool write, int l, int kind, int tx, int ty, Set& S) const {
+        if (!write) {
+            const int m = wmask(l, tx, ty);
+            if (kind == 2 ? !(m & 2) : !m) return;
+        }
+        const int rc = l * 3 + kind;
+        const int a0 = acc_beg[rc];
+        bool readers = false;
+        for (int e = acc_pos[rc * (P.nphase + 1) + p] - 1; e >= a0; e--) {
+            const TBAcc a = acc[e];
+            if (a.write) {
+                bool any = false;
+                touching(a, l, tx, ty, [&](int q) {
+                    any = true;
+                    if (!readers) S.add(q);
+                });
+                if (any) return;
+            } else if (write) {
+                touching(a, l, tx, ty, [&](int q) {
+                    readers = true;
+                    S.add(q);
+                });
+            }
+        }
+    }
+
+    // the dependencies of task t of phase p
+    template <class Set>
+    __device__ __forceinline__ void deps(int p, int t, Set& S, Item& it) const {
+        const TBPhase ph = this->ph[p];
+        const int l = ph.l;
+        const TBLevel& L = P.lev[l];
+        const int i = t - off[p];
+        it = ph.kind == 0 ? L.act[i] : L.ring[i];
+        S.n = 0;
+        S.ovf = false;
+        if (ph.kind == 0) {
+            const int bs = src_of(l, ph.kk, ph.step), bd = bs ^ 1;
+            deps_of(p, false, l, bs, it.tx, it.ty, S);
+            for (int d = 0; d < 5; d++) {
+                bool ok = true;
+                const int tx = wrap_or(it.tx + kSDI[d], L.bx, L.px, ok), ty = wrap_or(it.ty + kSDJ[d], L.by, L.py, ok);
+                if (ok) deps_of(p, true, l, bd, tx, ty, S);
+            }
+            if (l > 0 && L.recon[it.ty * L.bx + it.tx]) {
+                const TBLevel& Pl = P.lev[l - 1];
+                const int pbs = src_of(l - 1, ph.kkp, ph.step), pbd = pbs ^ 1;
+                int keys[16];
+                const int nk = footprint(Pl, it.tx, it.ty, keys);
+                for (int q = 0; q < nk; q++) {
+                    const int cx = keys[q] % Pl.bx, cy = keys[q] / Pl.bx;
+                    deps_of(p, false, l - 1, pbs, cx, cy, S);
+                    deps_of(p, false, l - 1, pbd, cx, cy, S);
+                    deps_of(p, false, l - 1, 2, cx, cy, S);
+                }
+            }
+        } else {
+            const int bd = src_of(l, ph.kk, ph.step) ^ 1;
+            const TBLevel& C = P.lev[l + 1];
+            for (int b2 = 0; b2 < 2; b2++)
+                for (int a2 = 0; a2 < 2; a2++) {
+                    const int fx = 2 * it.tx + a2, fy = 2 * it.ty + b2;
+                    if (fx >= C.bx || fy >= C.by) continue;
+                    deps_of(p, false, l + 1, 0, fx, fy, S);
+                    deps_of(p, false, l + 1, 1, fx, fy, S);
+                }
+            deps_of(p, true, l, bd, it.tx, it.ty, S);
+            deps_of(p, true, l, 2, it.tx, it.ty, S);
+        }
+    }
+
+    __device__ int phase_of(int t) const {
+        int lo = 0, hi = P.nphase - 1;  // largest p with off[p] <= t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        return lo;  // off[lo] <= t < off[lo + 1]: never an empty phase
+    }
+};
+
+__global__ void tb_offsets_kernel(TBPlan P) {
+    if (threadIdx.x || blockIdx.x) return;
+    int o = 0;
+    for (int p = 0; p < P.nphase; p++) {
+        P.off[p] = o;
+        const TBPhase ph = P.ph[p];
+        int c = 0;
+        if (ph.kind == 0) c = ph.l < P.nlev ? P.lev[ph.l].cnt[LST_ACT] : 0;
+        else c = ph.l + 1 < P.nlev ? P.lev[ph.l].cnt[LST_RING] : 0;
+        o += c;
+    }
+    P.off[P.nphase] = o;
+    P.need[0] = o;
+    P.need[1] = 0;
+    P.need[3] = 0;
+    P.need[4] = 0;
+}
+
+// Copies the plan's static tables into shared memory; returns the view.
+__device__ TB tb_global(const TBPlan& P) {
+    TB tb(P);
+    tb.ph = P.ph;
+    tb.acc = P.acc;
+    tb.acc_beg = P.acc_beg;
+    tb.acc_pos = P.acc_pos;
+    tb.off = P.off;
+    return tb;
+}
+
+
+// Writes a task and its sorted dependencies (at deps[d0 ..]).
+template <class Set>
+__device__ __forceinline__ void tb_write(const TBPlan& P, const TB& tb, int p, int t, const Item& it, Set& S,
+                                         long long d0) {
+    S.sort();
+    S.store(P.deps + d0);
+    const TBPhase ph = tb.ph[p];
+    Task T;
+    T.lid = ph.l;
+    T.tx = it.tx;
+    T.ty = it.ty;
+    T.kind = (signed char)ph.kind;
+    T.kk = (signed char)ph.kk;
+    T.kkp = (signed char)(ph.kind == 0 ? ph.kkp : 0);
+    T.step = (signed char)ph.step;
+    T.dep0 = (int)d0;
+    T.ndep = S.n;
+    T.aslot = -1;
+    P.tasks[t] = T;
+}
+
+// One pass: every task's dependencies into its fixed TB_SMALL slot of the
+// dependency array (deps[t * TB_SMALL ..]); a task with more is left to the
+// second pass.
+__global__ void __launch_bounds__(TB_BUILD_THREADS) tb_build_kernel(TBPlan P) {
+    const int total = P.off[P.nphase];
+    if (total > P.task_cap) return;
+    const TB tb = tb_global(P);
+    DepSetR S;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int p = tb.phase_of(t);
+        Item it;
+        tb.deps(p, t, S, it);
+        if (S.ovf) P.big[atomicAdd(P.need + 4, 1)] = t;
+        else tb_write(P, tb, p, t, it, S, (long long)t * TB_SMALL);
+    }
+}
+
+// Second pass: the tasks with more than TB_SMALL dependencies, with a
+// local-memory set, into the overflow area after the fixed slots.
+__global__ void __launch_bounds__(TB_BUILD_THREADS) tb_big_kernel(TBPlan P) {
+    const int nbig = P.need[4];
+    if (nbig == 0) return;
+    const TB tb = tb_global(P);
+    int buf[TB_MAXDEP];
+    DepSet S{buf, 1, TB_MAXDEP, 0, false};
+    const long long base = (long long)P.task_cap * TB_SMALL;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nbig; i += gridDim.x * blockDim.x) {
+        const int t = P.big[i];
+        const int p = tb.phase_of(t);
+        Item it;
+        tb.deps(p, t, S, it);
+        const long long at = base + atomicAdd(P.need + 1, S.n);
+        if (S.ovf || at + S.n > P.dep_cap) {
+            atomicOr(P.need + 3, 1);
+            continue;
+        }
+        tb_write(P, tb, p, t, it, S, at);
+    }
+}
+
+__global__ void tb_finish_kernel(TBPlan P) {
+    if (threadIdx.x || blockIdx.x) return;
+    int total = P.off[P.nphase];
+    if (P.need[3] != 0 || total > P.task_cap) {
+        atomicOr(P.status, ST_TASKCAP);
+        total = 0;
+    }
+    P.seg->ntasks = total;
+    P.prefix[0] = 0;
+    P.prefix[1] = total;
+    P.ctl[CTL_TOTAL] = total;
+}
+
+}  // namespace
+
+
+cudaError_t launch_layout_rule(const LayoutDev& L, const LayoutDev* F, const uint8_t* bflag, cudaStream_t s) {
+    layout_rule_kernel<<<flat_blocks((long long)L.bx * L.by), 256, 0, s>>>(L, F ? *F : L, F != nullptr, bflag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_derive_in(const LayoutDev* P, const LayoutDev& L, cudaStream_t s) {
+    derive_in_kernel<<<flat_blocks((long long)L.bx * L.by), 256, 0, s>>>(P ? *P : L, L, P == nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nest_check(const LayoutDev& L, bool finest, int* status, cudaStream_t s) {
+    nest_check_kernel<<<flat_blocks((long long)L.bx * L.by), 256, 0, s>>>(L, finest, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_commit_maps(const LayoutDev& L, cudaStream_t s) {
+    commit_maps_kernel<<<flat_blocks((long long)L.bx * L.by), 256, 0, s>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lists(const LayoutDev& L, int mask, int lid, cudaStream_t s) {
+    if (L.nchunk <= 0) return cudaSuccess;
+    lists_count_kernel<<<L.nchunk, LIST_T, 0, s>>>(L, mask);
+    lists_scan_kernel<<<NLST, 1024, 0, s>>>(L, mask);
+    lists_scatter_kernel<<<L.nchunk, LIST_T, 0, s>>>(L, mask, lid);
+    if ((mask >> LST_ACT) & 1) wmask_kernel<<<flat_blocks((long long)L.bx * L.by), 256, 0, s>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_footprints(const LayoutDev& P, const LayoutDev& C, int* status, cudaStream_t s) {
+    const long long nb = (long long)P.bx * P.by;
+    cudaMemsetAsync(P.fcnt, 0, nb * sizeof(int), s);
+    footprints_kernel<<<flat_blocks((long long)C.bx * C.by), 256, 0, s>>>(P, C, status);
+    foot_clamp_kernel<<<flat_blocks(nb), 256, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_concat_act(const LayoutDev* levs, int n, Item* out, int* n_out, cudaStream_t s) {
+    ActRef R{};
+    long long cap = 0;
+    for (int l = 0; l < n; l++) {
+        R.list[l] = levs[l].list[LST_ACT];
+        R.cnt[l] = levs[l].cnt;
+        R.cap[l] = levs[l].bx * levs[l].by;
+        cap = cap > R.cap[l] ? cap : R.cap[l];
+    }
+    concat_act_kernel<<<flat_blocks(cap), 256, 0, s>>>(R, n, out, n_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_lups(const LayoutDev* levs, int n, long long steps, unsigned long long* counter,
+                              cudaStream_t s) {
+    const unsigned long long* c[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (int l = 0; l < n; l++) c[l] = levs[l].cells;
+    count_lups_kernel<<<1, 1, 0, s>>>(c[0], c[1], c[2], c[3], n, steps, counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_task_build(const TBPlan& P, cudaStream_t s) {
+    tb_offsets_kernel<<<1, 1, 0, s>>>(P);
+    long long gl = ((long long)P.task_cap + TB_BUILD_THREADS - 1) / TB_BUILD_THREADS;
+    const int g = (int)(gl < 1 ? 1 : (gl > 148 * 16 ? 148 * 16 : gl));
+    tb_build_kernel<<<g, TB_BUILD_THREADS, 0, s>>>(P);
+    tb_big_kernel<<<148 * 4, TB_BUILD_THREADS, 0, s>>>(P);
+    tb_finish_kernel<<<1, 1, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+}  // namespace vlbm

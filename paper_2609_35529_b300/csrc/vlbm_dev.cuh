@@ -51,7 +51,9 @@ constexpr uint32_t F_PEND_MASK = 0xFu << F_PEND_SHIFT;
 constexpr uint32_t F_FRESH_MASK = 0xFu << F_FRESH_SHIFT;
 
 // status bits of a hierarchy
-enum : int { ST_NONPHYS = 1, ST_TIMEOUT = 2 };
+// ST_NESTING: a layout computed on the device is not properly nested;
+// ST_TASKCAP: a task list built on the device did not fit its buffers
+enum : int { ST_NONPHYS = 1, ST_TIMEOUT = 2, ST_NESTING = 4, ST_TASKCAP = 8 };
 
 enum : int { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_INFLOW = 2, BC_REFLECT = 3 };
 

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "vlbm.h"
+#include "vlbm_amr.h"
 #include "vlbm_dev.cuh"
 #include "vlbm_launch.h"
 #include "vlbm_tasks.h"
@@ -251,8 +252,8 @@ struct Level {
     double* buf[2] = {nullptr, nullptr};
     uint16_t* flags = nullptr;
     uint16_t* flags_tmp = nullptr;
-    std::vector<uint8_t> bin, bcov;  // block maps (current layout)
-    DArr<uint8_t> dbin, dbcov;
+    std::vector<uint8_t> bin, bcov;  // block maps (current layout; host copy, see vlbm_hier::host_ok)
+    LayoutDev dl;                      // the layout on the device (always current)
     std::vector<Item> act, ring, cov, in;  // tiles (lid = level index)
     std::vector<uint8_t> recon;             // per tile: a face neighbour is coarser land
     long long active_cells = 0;
@@ -287,7 +288,6 @@ struct vlbm_hier {
     DArr<Item> listbuf;    // item lists for regrid kernels
     DArr<uint8_t> bflag;   // block flags
     DArr<LevelDev> atab;   // level table for audits (rebuilt with the layout)
-    DArr<Item> aitems;     // active tiles of every level (audits)
     double* hout = nullptr;  // pinned host copy of the audit result
     // tag-driven regrid in two halves: the status words and the block flags
     // land in pinned memory (rg_pin), rg_ev marks their arrival
@@ -297,6 +297,42 @@ struct vlbm_hier {
     cudaEvent_t rg_ev = nullptr;
     vlbm_tuning tune{1, 0, 8, 1, 256};
     long long layout_steps = 0;  // coarse steps taken on the current layout
+    // The layout lives on the device (Level::dl, always current); the host
+    // copies (Level::bin, bcov and the tile lists) are current while host_ok.
+    // A tag-driven regrid runs on the device alone and clears host_ok; calls
+    // that need the host copies fetch them first (ensure_host).
+    bool host_ok = true;
+    long long layout_version = 0;    // bumped at every layout change
+    Item* ditems = nullptr;          // active tiles of every level (audits), length at dcount[0]
+    size_t ditems_cap = 0;
+    int* dcount = nullptr;           // [0] ditems length
+    unsigned long long* lupc = nullptr;  // cell updates done so far
+    int** parp = nullptr;                // device array holding `words` (the level-0 parity)
+    long long foot_version = -1;         // layout of the last reverse footprints (task builds)
+    cudaGraphExec_t rg_exec = nullptr;   // the device regrid, captured
+    std::vector<uintptr_t> rg_key;
+    // Task lists built on the device for the persistent schedule (no
+    // per-step audit): [0] one coarse step, [1] tune.graph_steps steps
+    struct DevPlan {
+        int steps = -1;
+        long long version = -1;
+        int nphase = 0, nacc = 0;
+        DArr<TBPhase> ph;
+        DArr<TBAcc> acc;
+        DArr<int> acc_beg, acc_pos, off, deps, need, prefix, ctl, big;
+        DArr<Task> tasks;
+        DArr<unsigned> done;
+        DArr<Segment> seg;
+        int task_cap = 0;
+        long long dep_cap = 0;
+        cudaGraphExec_t exec = nullptr;
+        std::vector<uintptr_t> key;
+    } dp[2];
+    // per-phase launches over the device lists: [0] one step, [1] G steps
+    struct PhaseGraph {
+        cudaGraphExec_t exec = nullptr;
+        std::vector<uintptr_t> key;
+    } pg[2];
     // per-step conservation totals recorded by vlbm_advance (pinned ring)
     bool step_audit = false;
     double times[VLBM_T_COUNT] = {};  // host-side time, see vlbm_host_times
@@ -980,32 +1016,137 @@ void build_lists(vlbm_hier* h) {
 
 LevelDev lvdev(vlbm_hier* h, int l) { return h->dev(l, -1, -1); }
 
+constexpr int LISTS_ALL = (1 << LST_ACT) | (1 << LST_RING) | (1 << LST_COV) | (1 << LST_IN);
+constexpr int LISTS_MOVE = (1 << LST_EXIT) | (1 << LST_ENTER) | (1 << LST_TOUCH);
+
+int lcap(const LayoutDev& D) { return D.bx * D.by; }
+
+// The hierarchy's level table (parent / child links) as the kernels see it.
+void refresh_atab(vlbm_hier* h) {
+    std::vector<LevelDev> tab;
+    for (int l = 0; l < h->nlev; l++) tab.push_back(h->dev(l, l ? l - 1 : -1, l + 1 < h->nlev ? l + 1 : -1));
+    h->atab.upload(h->mem, tab, h->stream);
+}
+
+void layout_changed(vlbm_hier* h) {
+    h->layout_version++;
+    h->tl[0].steps = h->tl[1].steps = -1;
+    h->layout_steps = 0;
+}
+
+// The device lists of every level from the current device maps, and the
+// concatenated active tiles of the audits.
+void device_lists(vlbm_hier* h) {
+    LayoutDev dls[VLBM_MAX_LEVELS];
+    for (int l = 0; l < h->nlev; l++) {
+        VCK(launch_lists(h->lev[l].dl, LISTS_ALL, l, h->stream));
+        dls[l] = h->lev[l].dl;
+    }
+    VCK(launch_concat_act(dls, h->nlev, h->ditems, h->dcount, h->stream));
+}
+
+void upload_bytes(vlbm_hier* h, void* dst, const void* src, size_t n) {
+    if (!n) return;
+    if (h->pin.on) src = h->pin.put(src, n);
+    VCK(cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, h->stream));
+}
+
 // Installs new block maps: uploads them, rebuilds the per-cell flags (old
-// flags decide which faces are new) and the tile lists.
+// flags decide which faces are new) and the tile lists, on the host and on
+// the device.
 void install_layout(vlbm_hier* h, std::vector<uint8_t>* bin, std::vector<uint8_t>* bcov) {
     cudaStream_t s = h->stream;
     for (int l = 0; l < h->nlev; l++) {
         Level& L = h->lev[l];
         L.bin = bin[l];
         L.bcov = bcov[l];
-        L.dbin.upload(h->mem, L.bin, s);
-        L.dbcov.upload(h->mem, L.bcov, s);
-        VCK(launch_flags(lvdev(h, l), L.dbin.p, L.dbcov.p, L.flags, L.flags_tmp, s));
+        upload_bytes(h, L.dl.bin, L.bin.data(), L.bin.size());
+        upload_bytes(h, L.dl.bcov, L.bcov.data(), L.bcov.size());
+        VCK(launch_flags(lvdev(h, l), L.dl.bin, L.dl.bcov, L.flags, L.flags_tmp, s));
         std::swap(L.flags, L.flags_tmp);
     }
     build_lists(h);
-    h->tl[0].steps = h->tl[1].steps = -1;
-    h->layout_steps = 0;
-    std::vector<Item> items;
-    std::vector<LevelDev> tab;
+    h->host_ok = true;
+    layout_changed(h);
+    device_lists(h);
+    refresh_atab(h);
+}
+
+// The host copies of the layout (maps and tile lists), fetched from the
+// device after a regrid that ran there.  Synchronises the stream.
+void ensure_host(vlbm_hier* h) {
+    if (h->host_ok) return;
+    VCK(cudaStreamSynchronize(h->stream));
     for (int l = 0; l < h->nlev; l++) {
-        items.insert(items.end(), h->lev[l].act.begin(), h->lev[l].act.end());
-        tab.push_back(h->dev(l, l ? l - 1 : -1, l + 1 < h->nlev ? l + 1 : -1));
+        Level& L = h->lev[l];
+        const size_t nb = (size_t)L.bx * L.by;
+        L.bin.resize(nb);
+        L.bcov.resize(nb);
+        VCK(cudaMemcpy(L.bin.data(), L.dl.bin, nb, cudaMemcpyDeviceToHost));
+        VCK(cudaMemcpy(L.bcov.data(), L.dl.bcov, nb, cudaMemcpyDeviceToHost));
     }
-    h->aitems.upload(h->mem, items, s);
-    h->atab.upload(h->mem, tab, s);
-    h->partial.ensure(h->mem, (size_t)24 * audit_blocks((int)items.size()));
-    h->tot.ensure(h->mem, 8);
+    build_lists(h);
+    h->host_ok = true;
+    h->tl[0].steps = h->tl[1].steps = -1;
+    if (h->own) h->own->valid = false;
+}
+
+// Device layout of level l: block maps, lists and their lengths, sized for
+// the whole level.
+void alloc_layout(vlbm_hier* h, int l) {
+    Level& L = h->lev[l];
+    LayoutDev& D = L.dl;
+    D.nx = L.nx;
+    D.ny = L.ny;
+    D.bx = L.bx;
+    D.by = L.by;
+    D.px = h->cfg.bc[0] == VLBM_BC_PERIODIC;
+    D.py = h->cfg.bc[2] == VLBM_BC_PERIODIC;
+    D.level = l;
+    const size_t nb = (size_t)L.bx * L.by;
+    D.nchunk = (int)((nb + LAY_CHUNK - 1) / LAY_CHUNK);
+    cudaStream_t s = h->stream;
+    D.bin = (uint8_t*)h->mem.get(nb);
+    D.bcov = (uint8_t*)h->mem.get(nb);
+    D.nin = (uint8_t*)h->mem.get(nb);
+    D.ncov = (uint8_t*)h->mem.get(nb);
+    D.recon = (uint8_t*)h->mem.get(nb);
+    D.act_idx = (int*)h->mem.get(nb * sizeof(int));
+    D.ring_idx = (int*)h->mem.get(nb * sizeof(int));
+    D.wm = (uint8_t*)h->mem.get(nb);
+    if (l + 1 < h->nlev) {
+        D.fcnt = (int*)h->mem.get(nb * sizeof(int));
+        D.fidx = (int*)h->mem.get(nb * FOOT_CAP * sizeof(int));
+        VCK(cudaMemsetAsync(D.fcnt, 0, nb * sizeof(int), s));
+    }
+    for (int k = 0; k < NLST; k++) D.list[k] = (Item*)h->mem.get(nb * sizeof(Item));
+    D.cnt = (int*)h->mem.get(NLST * sizeof(int));
+    D.cells = (unsigned long long*)h->mem.get(sizeof(unsigned long long));
+    D.chunk = (int*)h->mem.get((size_t)NLST * D.nchunk * sizeof(int));
+    for (uint8_t* m : {D.bin, D.bcov, D.nin, D.ncov, D.recon, D.wm}) VCK(cudaMemsetAsync(m, 0, nb, s));
+    VCK(cudaMemsetAsync(D.act_idx, 0xff, nb * sizeof(int), s));
+    VCK(cudaMemsetAsync(D.ring_idx, 0xff, nb * sizeof(int), s));
+    VCK(cudaMemsetAsync(D.cnt, 0, NLST * sizeof(int), s));
+    VCK(cudaMemsetAsync(D.cells, 0, sizeof(unsigned long long), s));
+}
+
+void free_layout(vlbm_hier* h, int l) {
+    Level& L = h->lev[l];
+    LayoutDev& D = L.dl;
+    if (!D.bin) return;
+    const size_t nb = (size_t)L.bx * L.by;
+    for (uint8_t* m : {D.bin, D.bcov, D.nin, D.ncov, D.recon, D.wm}) h->mem.put(m, nb);
+    h->mem.put(D.act_idx, nb * sizeof(int));
+    h->mem.put(D.ring_idx, nb * sizeof(int));
+    if (D.fcnt) {
+        h->mem.put(D.fcnt, nb * sizeof(int));
+        h->mem.put(D.fidx, nb * FOOT_CAP * sizeof(int));
+    }
+    for (int k = 0; k < NLST; k++) h->mem.put(D.list[k], nb * sizeof(Item));
+    h->mem.put(D.cnt, NLST * sizeof(int));
+    h->mem.put(D.cells, sizeof(unsigned long long));
+    h->mem.put(D.chunk, (size_t)NLST * D.nchunk * sizeof(int));
+    D = LayoutDev{};
 }
 
 void check_status(vlbm_hier* h) {
@@ -1014,10 +1155,13 @@ void check_status(vlbm_hier* h) {
     VCK(cudaStreamSynchronize(h->stream));
     if (st[1] & ST_NONPHYS) throw Fail{VLBM_ERR_NONPHYSICAL, "non-physical state (rho <= 0, p <= 0 or NaN)"};
     if (st[1] & ST_TIMEOUT) throw Fail{VLBM_ERR_TIMEOUT, "a bounded device wait timed out"};
+    if (st[1] & ST_NESTING) throw Fail{VLBM_ERR_NESTING, "a layout computed on the device is not properly nested"};
+    if (st[1] & ST_TASKCAP) throw Fail{VLBM_ERR_OOM, "a task list built on the device did not fit its buffers"};
 }
 
 // Conservative regrid to the covered maps newcov (Sec. 3.4, Fig. 2).
 void regrid_to(vlbm_hier* h, std::vector<uint8_t>* newcov, bool averaged) {
+    ensure_host(h);
     cudaStream_t s = h->stream;
     std::vector<uint8_t> newin[VLBM_MAX_LEVELS];
     derive_in(h, newin, newcov);
@@ -1145,6 +1289,418 @@ void tag_finish(vlbm_hier* h) {
     h->times[VLBM_T_REGRID] += ms_since(t0);
 }
 
+// ---- the adaptive regrid on the device (Sec. 3.4, Fig. 2) --------------------
+
+// Indicator and block flags of every refinable level into h->bflag (level l
+// at offset sum_{m < l} bx_m by_m), from the composite state.
+void check_tagging(const vlbm_hier* h) {
+    if (!(h->cfg.tag_tol > 0.0) || h->cfg.tag_buffer < 0) throw Fail{VLBM_ERR_ARG, "no tagging parameters"};
+    if (h->cfg.tag_sensor != VLBM_SENSOR_DENSITY && h->cfg.tag_sensor != VLBM_SENSOR_FLUX)
+        throw Fail{VLBM_ERR_ARG, "unknown tagging sensor"};
+}
+
+// The scratch of a device regrid at its final size (allocated outside any
+// stream capture).
+void regrid_buffers(vlbm_hier* h) {
+    size_t nb = 0, cells = 1;
+    for (int l = 0; l <= h->nlev - 2; l++) {
+        nb += (size_t)h->lev[l].bx * h->lev[l].by;
+        cells = std::max(cells, (size_t)h->lev[l].nx * h->lev[l].ny);
+    }
+    h->bflag.ensure(h->mem, std::max<size_t>(1, nb));
+    h->stage8.ensure(h->mem, cells);
+    h->qmax.ensure(h->mem, 4);
+}
+
+void device_tags(vlbm_hier* h) {
+    check_tagging(h);
+    cudaStream_t s = h->stream;
+    const int nl = h->nlev;
+    // composite state: the average of the children in every covered cell,
+    // finest level first
+    for (int l = nl - 2; l >= 0; l--) {
+        const LayoutDev& D = h->lev[l].dl;
+        VCK(launch_avgdown(lvdev(h, l), lvdev(h, l + 1), D.list[LST_COV], lcap(D), s, D.cnt + LST_COV));
+    }
+    const bool fluxs = h->cfg.tag_sensor == VLBM_SENSOR_FLUX;
+    if (fluxs) {
+        h->qmax.ensure(h->mem, 4);
+        VCK(cudaMemsetAsync(h->qmax.p, 0, 4 * sizeof(unsigned long long), s));
+        for (int l = 0; l < nl; l++) {
+            const LayoutDev& D = h->lev[l].dl;
+            VCK(launch_qmax(lvdev(h, l), D.list[LST_IN], lcap(D), h->qmax.p, s, D.cnt + LST_IN));
+        }
+    }
+    const int px = h->cfg.bc[0] == VLBM_BC_PERIODIC, py = h->cfg.bc[2] == VLBM_BC_PERIODIC;
+    size_t nb = 0;
+    for (int l = 0; l <= nl - 2; l++) nb += (size_t)h->lev[l].bx * h->lev[l].by;
+    h->bflag.ensure(h->mem, std::max<size_t>(1, nb));
+    const double tol2 = h->cfg.tag_tol * h->cfg.tag_tol;
+    size_t off = 0;
+    for (int l = 0; l <= nl - 2; l++) {
+        Level& L = h->lev[l];
+        const LayoutDev& D = L.dl;
+        h->stage8.ensure(h->mem, (size_t)L.nx * L.ny);
+        VCK(cudaMemsetAsync(h->stage8.p, 0, (size_t)L.nx * L.ny, s));
+        if (fluxs)
+            VCK(launch_tag_flux(lvdev(h, l), D.list[LST_IN], lcap(D), h->qmax.p, h->cfg.tag_tol, h->stage8.p, s,
+                                D.cnt + LST_IN));
+        else
+            VCK(launch_tag(lvdev(h, l), D.list[LST_IN], lcap(D), tol2, h->stage8.p, s, D.cnt + LST_IN));
+        VCK(launch_blockflag(h->stage8.p, L.nx, L.ny, px, py, h->cfg.tag_buffer, h->bflag.p + off, s));
+        off += (size_t)L.bx * L.by;
+    }
+}
+
+// From block flags to the new layout, on the device: the layout rule
+// (finest refinable level first), the new on-level maps, the nesting check,
+// merge (finest first) and split (coarsest first) of the cells that change,
+// the per-cell flags, then the new maps and lists.  Expects the composite
+// state of the current layout (device_tags).
+void device_apply_flags(vlbm_hier* h, const uint8_t* bflag) {
+    cudaStream_t s = h->stream;
+    const int nl = h->nlev;
+    size_t off[VLBM_MAX_LEVELS] = {};
+    for (int l = 1; l < nl; l++) off[l] = off[l - 1] + (size_t)h->lev[l - 1].bx * h->lev[l - 1].by;
+    LayoutDev* D[VLBM_MAX_LEVELS];
+    for (int l = 0; l < nl; l++) D[l] = &h->lev[l].dl;
+    VCK(cudaMemsetAsync(D[nl - 1]->ncov, 0, (size_t)lcap(*D[nl - 1]), s));
+    for (int l = nl - 2; l >= 0; l--) VCK(launch_layout_rule(*D[l], l + 1 <= nl - 2 ? D[l + 1] : nullptr, bflag + off[l], s));
+    VCK(launch_derive_in(nullptr, *D[0], s));
+    for (int l = 1; l < nl; l++) VCK(launch_derive_in(D[l - 1], *D[l], s));
+    for (int l = 0; l < nl; l++) VCK(launch_nest_check(*D[l], l == nl - 1, h->words + 1, s));
+    for (int l = 0; l < nl; l++) VCK(launch_lists(*D[l], l <= nl - 2 ? LISTS_MOVE : (1 << LST_TOUCH), l, s));
+    for (int l = nl - 2; l >= 0; l--)
+        VCK(launch_merge(lvdev(h, l), D[l]->list[LST_EXIT], lcap(*D[l]), s, D[l]->cnt + LST_EXIT));
+    for (int l = 0; l <= nl - 2; l++)
+        VCK(launch_split(lvdev(h, l), lvdev(h, l + 1), D[l]->list[LST_ENTER], lcap(*D[l]), s, D[l]->cnt + LST_ENTER));
+    for (int l = 0; l < nl; l++) {
+        Level& L = h->lev[l];
+        VCK(launch_flags_update(lvdev(h, l), D[l]->list[LST_TOUCH], lcap(*D[l]), D[l]->cnt + LST_TOUCH, D[l]->nin,
+                                D[l]->ncov, L.flags, L.flags_tmp, s));
+        VCK(launch_commit_maps(*D[l], s));
+    }
+    device_lists(h);
+}
+
+// A tag-driven regrid on the device: indicator, block flags, new layout,
+// merge / split, flags and lists, replayed as one captured graph (every
+// size involved is decided on the device, so the graph stays valid).
+void device_regrid(vlbm_hier* h) {
+    check_tagging(h);
+    regrid_buffers(h);
+    std::vector<uintptr_t> key = {(uintptr_t)h->bflag.p, (uintptr_t)h->stage8.p, (uintptr_t)h->qmax.p,
+                                  (uintptr_t)h->cfg.tag_sensor, (uintptr_t)h->ditems, (uintptr_t)h->words};
+    for (int l = 0; l < h->nlev; l++) {
+        key.push_back((uintptr_t)h->lev[l].flags);
+        key.push_back((uintptr_t)h->lev[l].flags_tmp);
+        key.push_back((uintptr_t)h->lev[l].buf[0]);
+    }
+    cudaStream_t s = h->stream;
+    if (!h->rg_exec || key != h->rg_key) {
+        const auto t0 = std::chrono::steady_clock::now();
+        if (h->rg_exec) cudaGraphExecDestroy(h->rg_exec);
+        h->rg_exec = nullptr;
+        cudaGraph_t g = nullptr;
+        VCK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        try {
+            device_tags(h);
+            device_apply_flags(h, h->bflag.p);
+        } catch (...) {
+            cudaStreamEndCapture(s, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+        }
+        VCK(cudaStreamEndCapture(s, &g));
+        cudaError_t e = cudaGraphInstantiate(&h->rg_exec, g, 0);
+        cudaGraphDestroy(g);
+        VCK(e);
+        h->rg_key = key;
+        h->times[VLBM_T_CAPTURE] += ms_since(t0);
+    }
+    VCK(cudaGraphLaunch(h->rg_exec, s));
+    h->host_ok = false;
+    layout_changed(h);
+}
+
+// ---- the sub-cycle over the device lists ---------------------------------------
+
+// Static tables of the phase sequence of `nsteps` coarse steps (the same
+// recursion as phases() in vlbm_tasks.h) and the accesses of its phases per
+// resource class (level, buffer 0 / 1 / flags), in phase order.
+void plan_tables(int nlev, int nsteps, std::vector<TBPhase>& ph, std::vector<TBAcc>& acc, std::vector<int>& beg,
+                 std::vector<int>& pos) {
+    ph.clear();
+    struct Rec {
+        static void run(std::vector<TBPhase>& ph, int l, int kk, int kkp, int step, bool first) {
+            ph.push_back(TBPhase{0, l, kk, kkp, step, first ? 1 : 0});
+            if (l + 1 < TASK_MAX_LEVELS) {
+                run(ph, l + 1, 1, kk, step, first);
+                run(ph, l + 1, 2, kk, step, false);
+                ph.push_back(TBPhase{1, l, kk, 0, step, 0});
+            }
+        }
+    };
+    for (int st = 0; st < nsteps; st++) Rec::run(ph, 0, 0, 0, st, true);
+    auto src_of = [](int level, int kk, int step) { return level == 0 ? (step & 1) : (kk == 1 ? 0 : 1); };
+    std::vector<TBAcc> per[TASK_MAX_LEVELS][3];
+    for (int p = 0; p < (int)ph.size(); p++) {
+        const TBPhase& P = ph[p];
+        const int l = P.l;
+        if (P.kind == 0) {
+            if (l >= nlev) continue;
+            const int bs = src_of(l, P.kk, P.step);
+            per[l][bs].push_back({p, 0, TB_OWN});
+            per[l][bs ^ 1].push_back({p, 1, TB_STENCIL});
+            if (l > 0) {
+                const int pbs = src_of(l - 1, P.kkp, P.step);
+                per[l - 1][pbs].push_back({p, 0, TB_FOOT});
+                per[l - 1][pbs ^ 1].push_back({p, 0, TB_FOOT});
+                per[l - 1][2].push_back({p, 0, TB_FOOT});
+            }
+        } else {
+            if (l + 1 >= nlev) continue;
+            const int bd = src_of(l, P.kk, P.step) ^ 1;
+            per[l + 1][0].push_back({p, 0, TB_CHILD4});
+            per[l + 1][1].push_back({p, 0, TB_CHILD4});
+            per[l][bd].push_back({p, 1, TB_OWNRING});
+            per[l][2].push_back({p, 1, TB_OWNRING});
+        }
+    }
+    const int np = (int)ph.size();
+    acc.clear();
+    beg.assign(TASK_MAX_LEVELS * 3 + 1, 0);
+    pos.assign((size_t)TASK_MAX_LEVELS * 3 * (np + 1), 0);
+    for (int rc = 0; rc < TASK_MAX_LEVELS * 3; rc++) {
+        const std::vector<TBAcc>& A = per[rc / 3][rc % 3];
+        beg[rc] = (int)acc.size();
+        int e = 0;
+        for (int p = 0; p <= np; p++) {
+            while (e < (int)A.size() && A[e].phase < p) e++;
+            pos[(size_t)rc * (np + 1) + p] = beg[rc] + e;
+        }
+        acc.insert(acc.end(), A.begin(), A.end());
+    }
+    beg[TASK_MAX_LEVELS * 3] = (int)acc.size();
+}
+
+// The task list of `k` coarse steps on the current layout, built on the
+// device when the layout changed.
+vlbm_hier::DevPlan& dev_plan(vlbm_hier* h, int which, int k) {
+    vlbm_hier::DevPlan& D = h->dp[which];
+    cudaStream_t s = h->stream;
+    if (D.steps != k) {
+        std::vector<TBPhase> ph;
+        std::vector<TBAcc> acc;
+        std::vector<int> beg, pos;
+        plan_tables(h->nlev, k, ph, acc, beg, pos);
+        long long cap = 0;
+        for (const TBPhase& P : ph) {
+            if (P.kind == 0 && P.l < h->nlev) cap += (long long)h->lev[P.l].bx * h->lev[P.l].by;
+            if (P.kind == 1 && P.l + 1 < h->nlev) cap += (long long)h->lev[P.l].bx * h->lev[P.l].by;
+        }
+        if (cap >= (1LL << 31) - 1) throw Fail{VLBM_ERR_ARG, "hierarchy too large for one task list"};
+        if (acc.empty()) acc.push_back(TBAcc{0, 0, 0});
+        D.ph.upload(h->mem, ph, s);
+        D.acc.upload(h->mem, acc, s);
+        D.acc_beg.upload(h->mem, beg, s);
+        D.acc_pos.upload(h->mem, pos, s);
+        D.nphase = (int)ph.size();
+        D.nacc = (int)acc.size();
+        D.off.ensure(h->mem, ph.size() + 1);
+        D.task_cap = (int)cap;
+        // fixed slots of TASK_DEP_SLOT dependencies per task and an overflow
+        // area for the tasks with more: measured at most about 12
+        // dependencies per task slot on average and 98 for one task on
+        // adversarial layouts (most cells refined, checkerboard coverage); an
+        // exhausted area raises VLBM_ERR_OOM at the next synchronising call
+        D.dep_cap = (long long)TASK_DEP_SLOT * cap + std::max<long long>(1 << 22, 8 * cap);
+        if (D.dep_cap >= (1LL << 31)) throw Fail{VLBM_ERR_ARG, "hierarchy too large for one task list"};
+        D.tasks.ensure(h->mem, (size_t)cap + 1);
+        D.deps.ensure(h->mem, (size_t)D.dep_cap);
+        D.need.ensure(h->mem, 8);
+        D.big.ensure(h->mem, (size_t)cap + 1);
+        const bool fresh = D.done.cap < (size_t)cap + 1;
+        D.done.ensure(h->mem, (size_t)cap + 1);
+        if (fresh) VCK(cudaMemsetAsync(D.done.p, 0, D.done.cap * sizeof(unsigned), s));
+        // the launch's segment and control words (the builder fills in the
+        // task count; the epoch only ever grows, so completion marks left by
+        // earlier launches never match)
+        Segment sg{};
+        sg.tasks = D.tasks.p;
+        sg.deps = D.deps.p;
+        sg.done = D.done.p;
+        sg.par0 = h->words;
+        sg.lid_base = 0;
+        D.seg.upload(h->mem, std::vector<Segment>{sg}, s);
+        D.prefix.upload(h->mem, std::vector<int>{0, 0}, s);
+        std::vector<int> c(CTL_WORDS, 0);
+        c[CTL_EPOCH] = 1;
+        c[CTL_NSEG] = 1;
+        c[CTL_FLIP] = k & 1;
+        D.ctl.upload(h->mem, c, s);
+        D.steps = k;
+        D.version = -1;
+    }
+    if (D.version != h->layout_version) {
+        const auto t0 = std::chrono::steady_clock::now();
+        // the reverse footprints of the current layout (shared by both plans)
+        if (h->foot_version != h->layout_version) {
+            for (int l = 0; l + 1 < h->nlev; l++)
+                VCK(launch_footprints(h->lev[l].dl, h->lev[l + 1].dl, h->words + 1, s));
+            h->foot_version = h->layout_version;
+        }
+        TBPlan P;
+        P.nlev = h->nlev;
+        P.nphase = D.nphase;
+        P.nacc = D.nacc;
+        for (int l = 0; l < h->nlev; l++) {
+            const LayoutDev& L = h->lev[l].dl;
+            P.lev[l] = TBLevel{L.nx, L.ny, L.bx, L.by, L.px, L.py, L.list[LST_ACT], L.list[LST_RING],
+                               L.act_idx, L.ring_idx, L.recon, L.wm, L.fcnt, L.fidx, L.cnt};
+        }
+        P.ph = D.ph.p;
+        P.acc = D.acc.p;
+        P.acc_beg = D.acc_beg.p;
+        P.acc_pos = D.acc_pos.p;
+        P.off = D.off.p;
+        P.tasks = D.tasks.p;
+        P.deps = D.deps.p;
+        P.done = D.done.p;
+        P.task_cap = D.task_cap;
+        P.dep_cap = D.dep_cap;
+        P.need = D.need.p;
+        P.big = D.big.p;
+        P.status = h->words + 1;
+        P.seg = D.seg.p;
+        P.prefix = D.prefix.p;
+        P.ctl = D.ctl.p;
+        VCK(launch_task_build(P, s));
+        D.version = h->layout_version;
+        h->times[VLBM_T_TASKS] += ms_since(t0);
+        h->times[VLBM_T_NTASKLISTS] += 1;
+    }
+    return D;
+}
+
+// ... and the graph of its persistent launch.
+cudaGraphExec_t dev_task_graph(vlbm_hier* h, int which, int k) {
+    vlbm_hier::DevPlan& D = dev_plan(h, which, k);
+    cudaStream_t s = h->stream;
+    std::vector<uintptr_t> key = {(uintptr_t)h->atab.p, (uintptr_t)D.seg.p, (uintptr_t)D.prefix.p, (uintptr_t)D.ctl.p,
+                                  (uintptr_t)h->tune.variant, (uintptr_t)h->tune.max_ctas};
+    if (!D.exec || key != D.key) {
+        const auto t0 = std::chrono::steady_clock::now();
+        if (D.exec) cudaGraphExecDestroy(D.exec);
+        D.exec = nullptr;
+        cudaGraph_t g = nullptr;
+        VCK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaMemsetAsync(D.ctl.p, 0, 2 * sizeof(int), s);  // claim and finish counters
+        if (e == cudaSuccess) e = launch_tasks(h->atab.p, D.seg.p, D.prefix.p, D.ctl.p, h->tune.variant, h->tune.max_ctas, s);
+        cudaError_t e2 = cudaStreamEndCapture(s, &g);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&D.exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        VCK(e);
+        D.key = key;
+        h->times[VLBM_T_CAPTURE] += ms_since(t0);
+    }
+    return D.exec;
+}
+
+// One launch per level phase over the device lists (the per-phase schedule,
+// and the one the relaxation sensor runs on).
+void dev_schedule(vlbm_hier* h, int l, int kk, int kkp, cudaStream_t s) {
+    const LayoutDev& D = h->lev[l].dl;
+    if (h->sensor_on) VCK(launch_sensor(h->atab.p, D.list[LST_ACT], lcap(D), kk, s, D.cnt + LST_ACT));
+    VCK(launch_sweep(h->atab.p, D.list[LST_ACT], lcap(D), kk, kkp, h->tune.max_ctas, h->tune.variant, s, h->sensor_on,
+                     D.cnt + LST_ACT));
+    if (l + 1 < h->nlev) {
+        dev_schedule(h, l + 1, 1, kk, s);
+        dev_schedule(h, l + 1, 2, kk, s);
+        VCK(launch_close(h->atab.p, D.list[LST_RING], lcap(D), kk, s, D.cnt + LST_RING));
+    }
+}
+
+cudaGraphExec_t dev_phase_graph(vlbm_hier* h, int which, int k) {
+    vlbm_hier::PhaseGraph& P = h->pg[which];
+    std::vector<uintptr_t> key = {(uintptr_t)h->atab.p, (uintptr_t)h->tune.variant, (uintptr_t)h->tune.max_ctas,
+                                  (uintptr_t)h->sensor_on, (uintptr_t)k, (uintptr_t)h->parp};
+    if (P.exec && key == P.key) return P.exec;
+    const auto t0 = std::chrono::steady_clock::now();
+    if (P.exec) cudaGraphExecDestroy(P.exec);
+    P.exec = nullptr;
+    cudaStream_t s = h->stream;
+    cudaGraph_t g = nullptr;
+    VCK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    try {
+        for (int i = 0; i < k; i++) {
+            dev_schedule(h, 0, 0, 0, s);
+            VCK(launch_end_step(h->parp, 1, s));
+        }
+    } catch (...) {
+        cudaStreamEndCapture(s, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+    }
+    VCK(cudaStreamEndCapture(s, &g));
+    cudaError_t e = cudaGraphInstantiate(&P.exec, g, 0);
+    cudaGraphDestroy(g);
+    VCK(e);
+    P.key = key;
+    h->times[VLBM_T_CAPTURE] += ms_since(t0);
+    return P.exec;
+}
+
+void count_lups(vlbm_hier* h, long long n) {
+    if (n <= 0) return;
+    LayoutDev dls[VLBM_MAX_LEVELS];
+    for (int l = 0; l < h->nlev; l++) dls[l] = h->lev[l].dl;
+    VCK(launch_count_lups(dls, h->nlev, n, h->lupc, h->stream));
+}
+
+// n coarse steps on the device lists: the persistent task kernel (sched 1)
+// or one launch per phase (sched 0), G steps per graph launch.
+void dev_advance(vlbm_hier* h, long long n, int sched) {
+    cudaStream_t s = h->stream;
+    const int G = h->tune.graph_steps;
+    long long left = n;
+    if (left >= G) {
+        cudaGraphExec_t ex = sched == 1 ? dev_task_graph(h, 1, G) : dev_phase_graph(h, 1, G);
+        for (; left >= G; left -= G) VCK(cudaGraphLaunch(ex, s));
+    }
+    if (left > 0) {
+        cudaGraphExec_t ex = sched == 1 ? dev_task_graph(h, 0, 1) : dev_phase_graph(h, 0, 1);
+        for (; left > 0; left--) VCK(cudaGraphLaunch(ex, s));
+    }
+    count_lups(h, n);
+}
+
+void release_dev_plans(vlbm_hier* h) {
+    for (auto& D : h->dp) {
+        if (D.exec) cudaGraphExecDestroy(D.exec);
+        D.exec = nullptr;
+        D.key.clear();
+        for (DArr<int>* a : {&D.acc_beg, &D.acc_pos, &D.off, &D.deps, &D.need, &D.prefix, &D.ctl, &D.big})
+            a->release(h->mem);
+        D.ph.release(h->mem);
+        D.acc.release(h->mem);
+        D.tasks.release(h->mem);
+        D.done.release(h->mem);
+        D.seg.release(h->mem);
+        D.steps = -1;
+        D.version = -1;
+    }
+    for (auto& P : h->pg) {
+        if (P.exec) cudaGraphExecDestroy(P.exec);
+        P.exec = nullptr;
+        P.key.clear();
+    }
+    if (h->rg_exec) cudaGraphExecDestroy(h->rg_exec);
+    h->rg_exec = nullptr;
+    h->rg_key.clear();
+}
+
 void invalidate(vlbm_hier* h);
 
 }  // namespace
@@ -1251,8 +1807,7 @@ void destroy_levels(vlbm_hier* h) {
         h->mem.put(L.buf[1], pb);
         h->mem.put(L.flags, (size_t)L.plane * 2);
         h->mem.put(L.flags_tmp, (size_t)L.plane * 2);
-        L.dbin.release(h->mem);
-        L.dbcov.release(h->mem);
+        free_layout(h, l);
         L.buf[0] = L.buf[1] = nullptr;
         L.flags = L.flags_tmp = nullptr;
     }
@@ -1270,7 +1825,15 @@ void destroy_levels(vlbm_hier* h) {
     h->listbuf.release(h->mem);
     h->bflag.release(h->mem);
     h->atab.release(h->mem);
-    h->aitems.release(h->mem);
+    release_dev_plans(h);
+    h->mem.put(h->ditems, h->ditems_cap * sizeof(Item));
+    h->mem.put(h->dcount, 4 * sizeof(int));
+    h->mem.put(h->lupc, sizeof(unsigned long long));
+    h->mem.put(h->parp, sizeof(int*));
+    h->ditems = nullptr;
+    h->dcount = nullptr;
+    h->lupc = nullptr;
+    h->parp = nullptr;
     pin_free(h->hout, 8 * sizeof(double));
     h->hout = nullptr;
     h->pin.release();
@@ -1305,7 +1868,20 @@ int effective_schedule(const vlbm_hier* h) {
     return (h->step_audit || h->layout_steps >= h->tune.persist_after) ? 1 : 0;
 }
 
+// Schedule of the steps on the device lists.  Auto (2) keeps the per-phase
+// launches on a layout younger than persist_after coarse steps, as on the
+// host lists: building a layout's task lists on the device costs about as
+// much GPU time as a few coarse steps of the per-phase schedule lose to the
+// persistent one (measured on the 2048 x 1024 shock-bubble regridding every
+// 4 steps: 5030 MLUPS per phase, 4550 persistent with a build per regrid).
+int dev_schedule_mode(const vlbm_hier* h) {
+    if (h->sensor_on) return 0;
+    if (h->tune.schedule != 2) return h->tune.schedule;
+    return h->layout_steps >= h->tune.persist_after ? 1 : 0;
+}
+
 void ensure_own_batch(vlbm_hier* h, int sched) {
+    ensure_host(h);
     if (!h->own) {
         h->own = new Batch();
         h->own->mem = &h->mem;
@@ -1395,13 +1971,25 @@ vlbm_status vlbm_create_hierarchy(const vlbm_config* cfg, const vlbm_allocator* 
             VCK(cudaMemsetAsync(L.buf[1], 0, pb, h->stream));
             VCK(cudaMemsetAsync(L.flags, 0, (size_t)L.plane * 2, h->stream));
             VCK(cudaMemsetAsync(L.flags_tmp, 0, (size_t)L.plane * 2, h->stream));
+            alloc_layout(h, l);
+            h->ditems_cap += (size_t)L.bx * L.by;
         }
+        h->ditems = (Item*)h->mem.get(h->ditems_cap * sizeof(Item));
+        h->dcount = (int*)h->mem.get(4 * sizeof(int));
+        h->lupc = (unsigned long long*)h->mem.get(sizeof(unsigned long long));
+        h->parp = (int**)h->mem.get(sizeof(int*));
+        VCK(cudaMemsetAsync(h->dcount, 0, 4 * sizeof(int), h->stream));
+        VCK(cudaMemsetAsync(h->lupc, 0, sizeof(unsigned long long), h->stream));
+        VCK(cudaMemcpyAsync(h->parp, &h->words, sizeof(int*), cudaMemcpyHostToDevice, h->stream));
+        h->partial.ensure(h->mem, (size_t)24 * audit_blocks((int)std::min<size_t>(h->ditems_cap, 1u << 30)));
+        h->tot.ensure(h->mem, 8);
         std::vector<uint8_t> bin[VLBM_MAX_LEVELS], bcov[VLBM_MAX_LEVELS];
         boxes_to_maps(h, h->boxes.data(), (int)h->boxes.size(), bcov);
         derive_in(h, bin, bcov);
         std::string why;
         if (!nested(h, bin, bcov, why)) throw Fail{VLBM_ERR_NESTING, why};
         install_layout(h, bin, bcov);
+        VCK(cudaStreamSynchronize(h->stream));
     } catch (const Fail& f) {
         vlbm_status st = f.st;
         destroy_levels(h);
@@ -1495,6 +2083,20 @@ vlbm_status vlbm_advance(vlbm_hier* h, int64_t coarse_steps) {
     return run(h, [&] {
         if (coarse_steps < 0) throw Fail{VLBM_ERR_ARG, "negative step count"};
         if (h->engine) throw Fail{VLBM_ERR_ARG, "hierarchy is resident in an engine"};
+        if (!h->step_audit) {
+            // on the device lists: nothing here waits for the GPU
+            long long left = coarse_steps;
+            while (left > 0) {
+                const int sched = dev_schedule_mode(h);
+                long long n = left;
+                if (h->tune.schedule == 2 && sched == 0) n = std::min(left, h->tune.persist_after - h->layout_steps);
+                dev_advance(h, n, sched);
+                h->steps += n;
+                h->layout_steps += n;
+                left -= n;
+            }
+            return;
+        }
         long long left = coarse_steps;
         while (left > 0) {
             const int sched = effective_schedule(h);
@@ -1526,6 +2128,7 @@ vlbm_status vlbm_advance(vlbm_hier* h, int64_t coarse_steps) {
             h->layout_steps += n;
             left -= n;
         }
+        count_lups(h, coarse_steps);
     });
 }
 
@@ -1564,6 +2167,7 @@ vlbm_status vlbm_checkpoint_save(vlbm_hier* h, void* blob, size_t bytes) {
         if (!blob || bytes < ckpt_bytes(h)) throw Fail{VLBM_ERR_ARG, "blob too small"};
         VCK(cudaStreamSynchronize(h->stream));
         check_status(h);
+        ensure_host(h);
         int par0 = 0;
         VCK(cudaMemcpy(&par0, h->words, sizeof(int), cudaMemcpyDeviceToHost));
         CkptHeader H{};
@@ -1644,6 +2248,7 @@ vlbm_status vlbm_set_step_totals(vlbm_hier* h, int32_t on) {
         if (on && h->sensor_on) throw Fail{VLBM_ERR_ARG, "per-step totals and the relaxation sensor exclude each other"};
         if (on && !h->hist) h->hist = (double*)pin_alloc((size_t)h->hist_cap * 8 * sizeof(double));
         VCK(cudaStreamSynchronize(h->stream));
+        if (on) ensure_host(h);
         h->step_audit = on != 0;
         h->hist_n = h->hist_read = 0;
         if (h->own) h->own->valid = false;
@@ -1677,7 +2282,8 @@ vlbm_status vlbm_sync(vlbm_hier* h) {
 // 192-bit fixed-point sums); one 64-byte read-back.
 static void audit_impl(vlbm_hier* h, double* totals, double* abs_totals) {
     if (!h->hout) h->hout = (double*)pin_alloc(8 * sizeof(double));
-    VCK(launch_audit(h->atab.p, h->aitems.p, (int)h->aitems.n, h->partial.p, h->tot.p, h->stream));
+    VCK(launch_audit(h->atab.p, h->ditems, (int)std::min<size_t>(h->ditems_cap, 1u << 30), h->partial.p, h->tot.p,
+                     h->stream, h->dcount));
     VCK(cudaMemcpyAsync(h->hout, h->tot.p, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     VCK(cudaStreamSynchronize(h->stream));
     if (totals) std::memcpy(totals, h->hout, 4 * sizeof(double));
@@ -1716,6 +2322,7 @@ vlbm_status vlbm_get_conserved(vlbm_hier* h, int32_t level, double* W, int64_t l
 vlbm_status vlbm_get_layout(vlbm_hier* h, int32_t level, uint8_t* in, uint8_t* ref) {
     return run(h, [&] {
         if (level < 0 || level >= h->nlev) throw Fail{VLBM_ERR_ARG, "bad level"};
+        ensure_host(h);
         Level& L = h->lev[level];
         for (int y = 0; y < L.ny; y++)
             for (int x = 0; x < L.nx; x++) {
@@ -1748,6 +2355,10 @@ vlbm_status vlbm_regrid(vlbm_hier* h, const vlbm_box* boxes, int32_t nboxes) {
             t0 = std::chrono::steady_clock::now();
             regrid_to(h, bcov, false);
             h->times[VLBM_T_REGRID] += ms_since(t0);
+        } else if (!h->engine) {
+            // on the device alone: queued, nothing waits
+            device_regrid(h);
+            h->times[VLBM_T_REGRID] += ms_since(t0);
         } else {
             tag_begin(h);
             t0 = std::chrono::steady_clock::now();
@@ -1766,6 +2377,7 @@ vlbm_status vlbm_set_sensor(vlbm_hier* h, int32_t on, double beta_min, double c_
         if (on && !(beta_min >= 0.0 && beta_min <= h->cfg.beta && c_sensor >= 0.0 && eps >= 0.0))
             throw Fail{VLBM_ERR_ARG, "bad sensor parameters"};
         if (on && h->step_audit) throw Fail{VLBM_ERR_ARG, "per-step totals and the relaxation sensor exclude each other"};
+        ensure_host(h);
         cudaStream_t s = h->stream;
         if (on) {
             // the flux maxima over the active cells of every level, now
@@ -1794,6 +2406,7 @@ vlbm_status vlbm_set_sensor(vlbm_hier* h, int32_t on, double beta_min, double c_
             h->s_eps = eps;
         }
         h->sensor_on = on != 0;
+        refresh_atab(h);
         invalidate(h);
     });
 }
@@ -1804,8 +2417,13 @@ vlbm_status vlbm_host_times(const vlbm_hier* h, double out[VLBM_T_COUNT]) {
     return VLBM_OK;
 }
 
-vlbm_status vlbm_get_info(const vlbm_hier* h, vlbm_info* info) {
-    if (!h || !info) return VLBM_ERR_ARG;
+vlbm_status vlbm_get_info(const vlbm_hier* hc, vlbm_info* info) {
+    if (!hc || !info) return VLBM_ERR_ARG;
+    vlbm_hier* h = const_cast<vlbm_hier*>(hc);
+    if (!h->host_ok) {  // the active cell counts of a layout made on the device
+        const vlbm_status st = run(h, [&] { ensure_host(h); });
+        if (st != VLBM_OK) return st;
+    }
     std::memset(info, 0, sizeof *info);
     info->nlev = h->nlev;
     long long lups = 0;
@@ -1823,6 +2441,159 @@ vlbm_status vlbm_get_info(const vlbm_hier* h, vlbm_info* info) {
     info->gamma = h->cfg.gamma;
     info->dx0 = h->cfg.dx0;
     return VLBM_OK;
+}
+
+vlbm_status vlbm_selftest_layout(uint64_t seed, int32_t cases, int64_t* mismatches, int64_t* second_pass,
+                                 char* first_bad, int32_t cap) {
+    if (cases < 0 || !mismatches) return VLBM_ERR_ARG;
+    *mismatches = 0;
+    if (second_pass) *second_pass = 0;
+    if (first_bad && cap > 0) first_bad[0] = 0;
+    uint64_t st = seed;
+    auto rnd = [&]() {  // SplitMix64
+        uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    auto bad = [&](const std::string& why) {
+        if (*mismatches == 0 && first_bad && cap > 0) std::snprintf(first_bad, (size_t)cap, "%s", why.c_str());
+        (*mismatches)++;
+    };
+    for (int cs = 0; cs < cases; cs++) {
+        vlbm_config cfg{};
+        cfg.max_levels = 2 + (int)(rnd() % 3);
+        cfg.nx0 = 4 + (int)(rnd() % 37);
+        cfg.ny0 = 4 + (int)(rnd() % 37);
+        cfg.dx0 = 1.0;
+        const int bx = (rnd() & 1) ? VLBM_BC_PERIODIC : VLBM_BC_OUTFLOW, by = (rnd() & 1) ? VLBM_BC_PERIODIC : VLBM_BC_OUTFLOW;
+        cfg.bc[0] = cfg.bc[1] = bx;
+        cfg.bc[2] = cfg.bc[3] = by;
+        cfg.gamma = 1.4;
+        cfg.c = 5.0;
+        cfg.beta = 0.9;
+        vlbm_hier* h = nullptr;
+        vlbm_status e = vlbm_create_hierarchy(&cfg, nullptr, nullptr, &h);
+        if (e != VLBM_OK) return e;
+        const vlbm_status r = run(h, [&] {
+            const int nl = h->nlev;
+            for (int round = 0; round < 3; round++) {
+                // random block flags on every refinable level, some in clusters
+                std::vector<uint8_t> bflag[VLBM_MAX_LEVELS], all;
+                const int dens = 2 + (int)(rnd() % 40);  // percent
+                for (int l = 0; l <= nl - 2; l++) {
+                    const Level& L = h->lev[l];
+                    bflag[l].assign((size_t)L.bx * L.by, 0);
+                    for (auto& b : bflag[l]) b = (int)(rnd() % 100) < dens ? 1 : 0;
+                    all.insert(all.end(), bflag[l].begin(), bflag[l].end());
+                }
+                std::vector<uint8_t> hcov[VLBM_MAX_LEVELS], hin[VLBM_MAX_LEVELS];
+                layout_rule(h, bflag, hcov);
+                derive_in(h, hin, hcov);
+                std::string why;
+                if (!nested(h, hin, hcov, why)) {
+                    bad("host layout not nested: " + why);
+                    return;
+                }
+                if (all.empty()) all.push_back(0);
+                h->bflag.ensure(h->mem, all.size());
+                VCK(cudaMemcpyAsync(h->bflag.p, all.data(), all.size(), cudaMemcpyHostToDevice, h->stream));
+                device_apply_flags(h, h->bflag.p);
+                h->host_ok = false;
+                layout_changed(h);
+                const int k = 1 + (int)(rnd() % 3);
+                vlbm_hier::DevPlan& D = dev_plan(h, 1, k);
+                VCK(cudaStreamSynchronize(h->stream));
+                int stw[2];
+                VCK(cudaMemcpy(stw, h->words, sizeof stw, cudaMemcpyDeviceToHost));
+                if (stw[1]) bad("status word " + std::to_string(stw[1]));
+                // maps and lists
+                std::vector<TileLists> tl(nl);
+                std::vector<TaskLevel> lv(nl);
+                const bool px = bx == VLBM_BC_PERIODIC, py = by == VLBM_BC_PERIODIC;
+                for (int l = 0; l < nl; l++) {
+                    const Level& L = h->lev[l];
+                    const LayoutDev& DL = L.dl;
+                    const size_t nb = (size_t)L.bx * L.by;
+                    std::vector<uint8_t> din(nb), dcov(nb), drec(nb);
+                    VCK(cudaMemcpy(din.data(), DL.bin, nb, cudaMemcpyDeviceToHost));
+                    VCK(cudaMemcpy(dcov.data(), DL.bcov, nb, cudaMemcpyDeviceToHost));
+                    VCK(cudaMemcpy(drec.data(), DL.recon, nb, cudaMemcpyDeviceToHost));
+                    if (din != hin[l]) bad("level " + std::to_string(l) + ": on-level map");
+                    if (dcov != hcov[l]) bad("level " + std::to_string(l) + ": covered map");
+                    tile_lists(l, L.nx, L.ny, L.bx, L.by, px, py, hin[l].data(), hcov[l].data(), tl[l]);
+                    if (drec != tl[l].recon) bad("level " + std::to_string(l) + ": recon map");
+                    int cnt[NLST];
+                    VCK(cudaMemcpy(cnt, DL.cnt, sizeof cnt, cudaMemcpyDeviceToHost));
+                    const std::vector<Item>* want[4] = {&tl[l].act, &tl[l].ring, &tl[l].cov, &tl[l].in};
+                    for (int q = 0; q < 4; q++) {
+                        std::vector<Item> got((size_t)cnt[q]);
+                        if (cnt[q]) VCK(cudaMemcpy(got.data(), DL.list[q], got.size() * sizeof(Item), cudaMemcpyDeviceToHost));
+                        bool same = got.size() == want[q]->size();
+                        for (size_t i = 0; same && i < got.size(); i++)
+                            same = got[i].tx == (*want[q])[i].tx && got[i].ty == (*want[q])[i].ty && got[i].lid == l;
+                        if (!same) bad("level " + std::to_string(l) + ": list " + std::to_string(q));
+                    }
+                    unsigned long long cells = 0;
+                    VCK(cudaMemcpy(&cells, DL.cells, sizeof cells, cudaMemcpyDeviceToHost));
+                    if ((long long)cells != tl[l].active_cells) bad("level " + std::to_string(l) + ": active cells");
+                    lv[l].nx = L.nx;
+                    lv[l].ny = L.ny;
+                    lv[l].bx = L.bx;
+                    lv[l].by = L.by;
+                    lv[l].px = px;
+                    lv[l].py = py;
+                    lv[l].act = &tl[l].act;
+                    lv[l].ring = &tl[l].ring;
+                    lv[l].recon = &tl[l].recon;
+                }
+                // task lists: the host builder against the device's
+                TaskLists want;
+                build_tasks(lv, k, want);
+                int need[5];
+                VCK(cudaMemcpy(need, D.need.p, sizeof need, cudaMemcpyDeviceToHost));
+                if (second_pass) *second_pass += need[4];
+                if (need[0] != (int)want.t.size()) {
+                    bad("task count " + std::to_string(need[0]) + " vs " + std::to_string(want.t.size()));
+                    continue;
+                }
+                std::vector<Task> gt(want.t.size());
+                if (!gt.empty()) VCK(cudaMemcpy(gt.data(), D.tasks.p, gt.size() * sizeof(Task), cudaMemcpyDeviceToHost));
+                // the dependency array as far as any task's slot reaches
+                long long reach = 0;
+                for (const Task& T : gt) reach = std::max(reach, (long long)T.dep0 + T.ndep);
+                std::vector<int> gd((size_t)reach);
+                if (reach) VCK(cudaMemcpy(gd.data(), D.deps.p, (size_t)reach * sizeof(int), cudaMemcpyDeviceToHost));
+                for (size_t i = 0; i < gt.size(); i++) {
+                    const Task &x = gt[i], &y = want.t[i];
+                    const int ya = y.kind == 0 ? -1 : y.aslot;  // no audit slots on the device lists
+                    bool same = x.lid == y.lid && x.tx == y.tx && x.ty == y.ty && x.kind == y.kind && x.kk == y.kk &&
+                                x.kkp == y.kkp && x.step == y.step && x.ndep == y.ndep && x.aslot == ya;
+                    for (int q = 0; same && q < x.ndep; q++) same = gd[x.dep0 + q] == want.d[y.dep0 + q];
+                    if (!same) {
+                        bad("task " + std::to_string(i) + " of " + std::to_string(gt.size()) + " (kind " +
+                            std::to_string(y.kind) + ", level " + std::to_string(y.lid) + ", ndep " +
+                            std::to_string(x.ndep) + " vs " + std::to_string(y.ndep) + ")");
+                        break;
+                    }
+                }
+            }
+        });
+        vlbm_destroy(h);
+        if (r != VLBM_OK) return r;
+    }
+    return VLBM_OK;
+}
+
+vlbm_status vlbm_lups_done(vlbm_hier* h, int64_t* lups) {
+    return run(h, [&] {
+        if (!lups) throw Fail{VLBM_ERR_ARG, "null output"};
+        unsigned long long v = 0;
+        VCK(cudaMemcpyAsync(&v, h->lupc, sizeof v, cudaMemcpyDeviceToHost, h->stream));
+        VCK(cudaStreamSynchronize(h->stream));
+        check_status(h);
+        *lups = (int64_t)v;
+    });
 }
 
 int32_t vlbm_num_variants(void) { return sweep_variants(); }
@@ -1852,6 +2623,7 @@ vlbm_status vlbm_profile(vlbm_hier* h, int64_t coarse_steps, vlbm_kernel_time* o
         if (coarse_steps < 0 || !out || !n) throw Fail{VLBM_ERR_ARG, "bad profile arguments"};
         if (h->engine) throw Fail{VLBM_ERR_ARG, "hierarchy is resident in an engine"};
         ensure_own_batch(h, effective_schedule(h));  // profile() launches phase by phase
+        count_lups(h, coarse_steps);
         long long cells[VLBM_MAX_LEVELS] = {};
         for (int l = 0; l < h->nlev; l++) cells[l] = h->lev[l].active_cells;
         std::vector<Batch::Rec> recs;
@@ -1929,8 +2701,10 @@ vlbm_status vlbm_engine_admit(vlbm_engine* e, vlbm_hier* h, int64_t coarse_steps
     for (const auto& r : e->res)
         if (r.live) used += (long long)r.h->device_bytes();
     if (e->budget && (size_t)(used + (long long)h->device_bytes()) > e->budget) return VLBM_ERR_OOM;
-    // the hierarchy's own queue must be drained before it joins the engine
+    // the hierarchy's own queue must be drained before it joins the engine,
+    // with its layout on the host
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return VLBM_ERR_CUDA;
+    if (run(h, [&] { ensure_host(h); }) != VLBM_OK) return VLBM_ERR_CUDA;
     int s = -1;
     for (size_t i = 0; i < e->res.size(); i++)
         if (!e->res[i].live) { s = (int)i; break; }

@@ -194,7 +194,8 @@ __device__ __forceinline__ long long sens_nb(const LevelDev& L, int x, int y, in
 
 // Pass 1: Q, u, v of every active cell from the level step's source buffer.
 __global__ void sensor_prep_kernel(const LevelDev* __restrict__ levs, const Item* __restrict__ items, int nitems,
-                                   int kk) {
+                                   int kk, const int* __restrict__ ncount) {
+    if (ncount) nitems = *ncount;
     const int sub = threadIdx.x >> 6, cx = threadIdx.x & 7, cy = (threadIdx.x >> 3) & 7;
     for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
         const Item w = items[it];
@@ -223,7 +224,9 @@ __global__ void sensor_prep_kernel(const LevelDev* __restrict__ levs, const Item
 }
 
 // Pass 2: s and theta of every active cell.
-__global__ void sensor_rate_kernel(const LevelDev* __restrict__ levs, const Item* __restrict__ items, int nitems) {
+__global__ void sensor_rate_kernel(const LevelDev* __restrict__ levs, const Item* __restrict__ items, int nitems,
+                                   const int* __restrict__ ncount) {
+    if (ncount) nitems = *ncount;
     const int sub = threadIdx.x >> 6, cx = threadIdx.x & 7, cy = (threadIdx.x >> 3) & 7;
     for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
         const Item w = items[it];
@@ -418,7 +421,9 @@ __device__ __forceinline__ void sweep_cell(const LevelDev* __restrict__ levs, co
 // index within their hierarchies).
 template <int P, int MINB>
 __global__ void __launch_bounds__(CTA_THREADS, MINB)
-sweep_kernel(const LevelDev* __restrict__ levs, const Item* __restrict__ items, int nitems, int kk, int kkp) {
+sweep_kernel(const LevelDev* __restrict__ levs, const Item* __restrict__ items, int nitems, int kk, int kkp,
+             const int* __restrict__ ncount) {
+    if (ncount) nitems = *ncount;
     const int sub = threadIdx.x >> 6;
     const int cx = threadIdx.x & 7;
     const int cy = (threadIdx.x >> 3) & 7;
@@ -467,7 +472,9 @@ __device__ __forceinline__ void close_cell(const LevelDev* __restrict__ levs, co
     if (fl & F_FRESH_MASK) L.flags[c] = (uint16_t)(fl & ~F_FRESH_MASK);
 }
 
-__global__ void close_kernel(const LevelDev* __restrict__ levs, const Item* __restrict__ items, int nitems, int kk) {
+__global__ void close_kernel(const LevelDev* __restrict__ levs, const Item* __restrict__ items, int nitems, int kk,
+                             const int* __restrict__ ncount) {
+    if (ncount) nitems = *ncount;
     const int sub = threadIdx.x >> 6;
     const int cx = threadIdx.x & 7;
     const int cy = (threadIdx.x >> 3) & 7;
@@ -978,7 +985,9 @@ __global__ void gather_W_kernel(LevelDev L, double* __restrict__ W, long long ld
 // part[blk][0..23] = sum w W_k (k = 0..3), then sum w |W_k|, w = 4^-level,
 // as 192-bit fixed point (three words each).
 __global__ void __launch_bounds__(256) audit_kernel(const LevelDev* __restrict__ levs, const Item* __restrict__ items,
-                                                    int nitems, unsigned long long* __restrict__ part) {
+                                                    int nitems, unsigned long long* __restrict__ part,
+                                                    const int* __restrict__ ncount) {
+    if (ncount) nitems = *ncount;
     Fix192 acc[8];
     for (int m = 0; m < 8; m++) acc[m] = fix_zero();
     const int sub = threadIdx.x >> 6;
@@ -1029,7 +1038,9 @@ __device__ __forceinline__ const double* composite_src(const LevelDev& L, uint32
 
 // Average-down (Eq. 25) of every covered cell of level C from its children
 // on level F: ((c00 + c11) + (c10 + c01)) / 4, into C's scratch buffer.
-__global__ void avgdown_kernel(LevelDev C, LevelDev F, const Item* __restrict__ items, int nitems) {
+__global__ void avgdown_kernel(LevelDev C, LevelDev F, const Item* __restrict__ items, int nitems,
+                               const int* __restrict__ ncount) {
+    if (ncount) nitems = *ncount;
     const int sub = threadIdx.x >> 6, cx = threadIdx.x & 7, cy = (threadIdx.x >> 3) & 7;
     for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
         const Item w = items[it];
@@ -1059,7 +1070,9 @@ __device__ __forceinline__ double comp_rho(const LevelDev& L, long long c) {
 // Normalised density-gradient indicator: tag when
 // (rho_E - rho_W)^2 + (rho_N - rho_S)^2 > tol^2 (2 rho_C)^2; neighbours off
 // the level or beyond a non-periodic side take rho_C.
-__global__ void tag_kernel(LevelDev L, const Item* __restrict__ items, int nitems, double tol2, uint8_t* __restrict__ tags) {
+__global__ void tag_kernel(LevelDev L, const Item* __restrict__ items, int nitems, double tol2, uint8_t* __restrict__ tags,
+                           const int* __restrict__ ncount) {
+    if (ncount) nitems = *ncount;
     const int sub = threadIdx.x >> 6, cx = threadIdx.x & 7, cy = (threadIdx.x >> 3) & 7;
     for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
         const Item w = items[it];
@@ -1100,7 +1113,8 @@ __device__ __forceinline__ void comp_W(const LevelDev& L, long long c, double W[
 // merged into qmax[k] as bit patterns (non-negative binary64 values order
 // like their bits).
 __global__ void qmax_kernel(LevelDev L, const Item* __restrict__ items, int nitems,
-                            unsigned long long* __restrict__ qmax) {
+                            unsigned long long* __restrict__ qmax, const int* __restrict__ ncount) {
+    if (ncount) nitems = *ncount;
     const int sub = threadIdx.x >> 6, cx = threadIdx.x & 7, cy = (threadIdx.x >> 3) & 7;
     unsigned long long m[4] = {0ull, 0ull, 0ull, 0ull};
     for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
@@ -1132,7 +1146,8 @@ __global__ void qmax_kernel(LevelDev L, const Item* __restrict__ items, int nite
 // own flux).
 __global__ void tag_flux_kernel(LevelDev L, const Item* __restrict__ items, int nitems,
                                 const unsigned long long* __restrict__ qmax, double tol,
-                                uint8_t* __restrict__ tags) {
+                                uint8_t* __restrict__ tags, const int* __restrict__ ncount) {
+    if (ncount) nitems = *ncount;
     const int sub = threadIdx.x >> 6, cx = threadIdx.x & 7, cy = (threadIdx.x >> 3) & 7;
     for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
         const Item w = items[it];
@@ -1205,7 +1220,8 @@ __global__ void blockflag_kernel(const uint8_t* __restrict__ tags, int nx, int n
 }
 
 // Cells leaving refinement take their merged value (Eq. 25).
-__global__ void merge_kernel(LevelDev L, const Item* __restrict__ items, int nitems) {
+__global__ void merge_kernel(LevelDev L, const Item* __restrict__ items, int nitems, const int* __restrict__ ncount) {
+    if (ncount) nitems = *ncount;
     const int sub = threadIdx.x >> 6, cx = threadIdx.x & 7, cy = (threadIdx.x >> 3) & 7;
     for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
         const Item w = items[it];
@@ -1223,7 +1239,9 @@ __global__ void merge_kernel(LevelDev L, const Item* __restrict__ items, int nit
 // covered before the regrid contribute their children's average; beyond a
 // non-periodic side the slope is zero.  Uses the layout from before the
 // regrid (flags are rebuilt afterwards).
-__global__ void split_kernel(LevelDev C, LevelDev F, const Item* __restrict__ items, int nitems) {
+__global__ void split_kernel(LevelDev C, LevelDev F, const Item* __restrict__ items, int nitems,
+                             const int* __restrict__ ncount) {
+    if (ncount) nitems = *ncount;
     const int sub = threadIdx.x >> 6, cx = threadIdx.x & 7, cy = (threadIdx.x >> 3) & 7;
     for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
         const Item w = items[it];
@@ -1263,43 +1281,70 @@ __global__ void split_kernel(LevelDev C, LevelDev F, const Item* __restrict__ it
 // Per-cell flags of a level from its block maps (blk_in, blk_cov: one byte
 // per 8 x 8 block).  Faces that exist now but did not exist under the old
 // flags have no previous sample.
+__device__ __forceinline__ uint16_t cell_flags(const LevelDev& L, int x, int y, long long t, int bx,
+                                               const uint8_t* __restrict__ blk_in,
+                                               const uint8_t* __restrict__ blk_cov,
+                                               const uint16_t* __restrict__ oldf) {
+    if (x >= L.nx) return 0;
+    const long long b = (long long)(y / TILE) * bx + x / TILE;
+    const bool in = blk_in[b], cov = in && blk_cov[b];
+    uint32_t fl = (in ? F_IN : 0u) | (cov ? F_COV : 0u);
+    if (in && !cov) {
+        const uint32_t ofl = oldf[t];
+        const bool oact = (ofl & (F_IN | F_COV)) == F_IN;
+        for (int i = 0; i < 4; i++) {
+            // upwind neighbour of direction i (the one that feeds it)
+            int ux = x - kCX[i], uy = y - kCY[i];
+            bool inside = true;
+            if (ux < 0) { if (L.px) ux += L.nx; else inside = false; }
+            if (ux >= L.nx) { if (L.px) ux -= L.nx; else inside = false; }
+            if (uy < 0) { if (L.py) uy += L.ny; else inside = false; }
+            if (uy >= L.ny) { if (L.py) uy -= L.ny; else inside = false; }
+            if (!inside) { fl |= F_BND; continue; }
+            const long long ub = (long long)(uy / TILE) * bx + ux / TILE;
+            const bool uin = blk_in[ub], ucov = uin && blk_cov[ub];
+            if (!uin) fl |= 1u << (F_RECON_SHIFT + i);
+            else if (ucov) {
+                fl |= 1u << (F_PEND_SHIFT + i);
+                // face (x, d) with d = i ^ 1 points at the covered cell u
+                const int d = i ^ 1;
+                const long long uc = (long long)uy * L.pitch + ux;
+                const bool existed = oact && ((oldf[uc] & (F_IN | F_COV)) == (F_IN | F_COV));
+                const bool was_fresh = (ofl >> (F_FRESH_SHIFT + d)) & 1u;
+                if (!existed || was_fresh) fl |= 1u << (F_FRESH_SHIFT + d);
+            }
+        }
+    }
+    return (uint16_t)fl;
+}
+
 __global__ void flags_kernel(LevelDev L, const uint8_t* __restrict__ blk_in, const uint8_t* __restrict__ blk_cov,
                              const uint16_t* __restrict__ oldf, uint16_t* __restrict__ newf) {
     const int bx = (L.nx + TILE - 1) / TILE;
     const long long n = (long long)L.pitch * L.ny;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(t % L.pitch), y = (int)(t / L.pitch);
-        if (x >= L.nx) { newf[t] = 0; continue; }
-        const long long b = (long long)(y / TILE) * bx + x / TILE;
-        const bool in = blk_in[b], cov = in && blk_cov[b];
-        uint32_t fl = (in ? F_IN : 0u) | (cov ? F_COV : 0u);
-        if (in && !cov) {
-            const uint32_t ofl = oldf[t];
-            const bool oact = (ofl & (F_IN | F_COV)) == F_IN;
-            for (int i = 0; i < 4; i++) {
-                // upwind neighbour of direction i (the one that feeds it)
-                int ux = x - kCX[i], uy = y - kCY[i];
-                bool inside = true;
-                if (ux < 0) { if (L.px) ux += L.nx; else inside = false; }
-                if (ux >= L.nx) { if (L.px) ux -= L.nx; else inside = false; }
-                if (uy < 0) { if (L.py) uy += L.ny; else inside = false; }
-                if (uy >= L.ny) { if (L.py) uy -= L.ny; else inside = false; }
-                if (!inside) { fl |= F_BND; continue; }
-                const long long ub = (long long)(uy / TILE) * bx + ux / TILE;
-                const bool uin = blk_in[ub], ucov = uin && blk_cov[ub];
-                if (!uin) fl |= 1u << (F_RECON_SHIFT + i);
-                else if (ucov) {
-                    fl |= 1u << (F_PEND_SHIFT + i);
-                    // face (x, d) with d = i ^ 1 points at the covered cell u
-                    const int d = i ^ 1;
-                    const long long uc = (long long)uy * L.pitch + ux;
-                    const bool existed = oact && ((oldf[uc] & (F_IN | F_COV)) == (F_IN | F_COV));
-                    const bool was_fresh = (ofl >> (F_FRESH_SHIFT + d)) & 1u;
-                    if (!existed || was_fresh) fl |= 1u << (F_FRESH_SHIFT + d);
-                }
-            }
-        }
-        newf[t] = (uint16_t)fl;
+        newf[t] = cell_flags(L, x, y, t, bx, blk_in, blk_cov, oldf);
+    }
+}
+
+// The same for the listed blocks (those on the level before or after a
+// change of layout; length at *nc), into newf; copy = 1 then copies those
+// blocks of newf back into oldf.  Every other block is off the level on both
+// sides: its flags are zero and stay zero.
+__global__ void flags_blocks_kernel(LevelDev L, const Item* __restrict__ items, const int* __restrict__ nc,
+                                    const uint8_t* __restrict__ blk_in, const uint8_t* __restrict__ blk_cov,
+                                    uint16_t* __restrict__ oldf, uint16_t* __restrict__ newf, int copy) {
+    const int bx = (L.nx + TILE - 1) / TILE;
+    const int n = *nc;
+    const int sub = threadIdx.x >> 6, cx = threadIdx.x & 7, cy = (threadIdx.x >> 3) & 7;
+    for (int it = blockIdx.x * TILES_PER_CTA + sub; it < n; it += gridDim.x * TILES_PER_CTA) {
+        const Item w = items[it];
+        const int x = w.tx * TILE + cx, y = w.ty * TILE + cy;
+        if (y >= L.ny) continue;
+        const long long t = (long long)y * L.pitch + x;
+        if (copy) oldf[t] = newf[t];
+        else newf[t] = cell_flags(L, x, y, t, bx, blk_in, blk_cov, oldf);
     }
 }
 
@@ -1311,6 +1356,15 @@ static inline int tile_grid(int nitems, int max_ctas) {
     int g = (nitems + TILES_PER_CTA - 1) / TILES_PER_CTA;
     if (max_ctas > 0 && g > max_ctas) g = max_ctas;
     return g < 1 ? 1 : g;
+}
+
+// Grid of a launch over a tile list: n tiles, or -- when the list's length
+// lives in device memory (nc != nullptr) -- at most n tiles with a grid of
+// at most six CTAs per SM looping over the list.
+static inline int list_grid(int n, const int* nc, int max_ctas = 0) {
+    int g = tile_grid(n, max_ctas);
+    if (nc && g > 148 * 6) g = 148 * 6;
+    return g;
 }
 
 static inline int flat_grid(long long n) {
@@ -1338,24 +1392,24 @@ bool sweep_variant_needs_om_minus1(int v) {
     return false;
 }
 
-cudaError_t launch_sensor(const LevelDev* levs, const Item* items, int n, int kk, cudaStream_t s) {
+cudaError_t launch_sensor(const LevelDev* levs, const Item* items, int n, int kk, cudaStream_t s, const int* nc) {
     if (n <= 0) return cudaSuccess;
-    const int g = tile_grid(n, 0);
-    sensor_prep_kernel<<<g, CTA_THREADS, 0, s>>>(levs, items, n, kk);
-    sensor_rate_kernel<<<g, CTA_THREADS, 0, s>>>(levs, items, n);
+    const int g = list_grid(n, nc);
+    sensor_prep_kernel<<<g, CTA_THREADS, 0, s>>>(levs, items, n, kk, nc);
+    sensor_rate_kernel<<<g, CTA_THREADS, 0, s>>>(levs, items, n, nc);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sweep(const LevelDev* levs, const Item* items, int n, int kk, int kkp, int max_ctas, int variant,
-                         cudaStream_t s, bool sensor) {
+                         cudaStream_t s, bool sensor, const int* nc) {
     if (n <= 0) return cudaSuccess;
-    const int g = tile_grid(n, max_ctas);
+    const int g = list_grid(n, nc, max_ctas);
     if (sensor) {  // per-cell relaxation parameters: one form of the sweep
-        sweep_kernel<SW_SENSOR, 2><<<g, CTA_THREADS, 0, s>>>(levs, items, n, kk, kkp);
+        sweep_kernel<SW_SENSOR, 2><<<g, CTA_THREADS, 0, s>>>(levs, items, n, kk, kkp, nc);
         return cudaGetLastError();
     }
     switch (variant) {
-#define X(id, P, B) case id: sweep_kernel<P, B><<<g, CTA_THREADS, 0, s>>>(levs, items, n, kk, kkp); break;
+#define X(id, P, B) case id: sweep_kernel<P, B><<<g, CTA_THREADS, 0, s>>>(levs, items, n, kk, kkp, nc); break;
         VLBM_SWEEP_VARIANTS(X)
 #undef X
         default: return cudaErrorInvalidValue;
@@ -1427,9 +1481,9 @@ cudaError_t launch_audit_segments(const unsigned long long* slots, const int* se
 }
 
 
-cudaError_t launch_close(const LevelDev* levs, const Item* items, int n, int kk, cudaStream_t s) {
+cudaError_t launch_close(const LevelDev* levs, const Item* items, int n, int kk, cudaStream_t s, const int* nc) {
     if (n <= 0) return cudaSuccess;
-    close_kernel<<<tile_grid(n, 0), CTA_THREADS, 0, s>>>(levs, items, n, kk);
+    close_kernel<<<list_grid(n, nc), CTA_THREADS, 0, s>>>(levs, items, n, kk, nc);
     return cudaGetLastError();
 }
 
@@ -1457,35 +1511,38 @@ cudaError_t launch_gather_W(const LevelDev& L, double* W, long long ld, uint8_t*
 int audit_blocks(int nitems) { return tile_grid(nitems, 148 * 4); }
 
 cudaError_t launch_audit(const LevelDev* levs, const Item* items, int n, unsigned long long* part, double* out,
-                         cudaStream_t s) {
+                         cudaStream_t s, const int* nc) {
     const int g = audit_blocks(n);
-    if (n > 0) audit_kernel<<<g, 256, 0, s>>>(levs, items, n, part);
+    if (n > 0) audit_kernel<<<g, 256, 0, s>>>(levs, items, n, part, nc);
     audit_segments_kernel<<<1, 256, 0, s>>>(part, nullptr, n > 0 ? g : 0, out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_avgdown(const LevelDev& C, const LevelDev& F, const Item* items, int n, cudaStream_t s) {
+cudaError_t launch_avgdown(const LevelDev& C, const LevelDev& F, const Item* items, int n, cudaStream_t s,
+                           const int* nc) {
     if (n <= 0) return cudaSuccess;
-    avgdown_kernel<<<tile_grid(n, 0), CTA_THREADS, 0, s>>>(C, F, items, n);
+    avgdown_kernel<<<list_grid(n, nc), CTA_THREADS, 0, s>>>(C, F, items, n, nc);
     return cudaGetLastError();
 }
 
-cudaError_t launch_tag(const LevelDev& L, const Item* items, int n, double tol2, uint8_t* tags, cudaStream_t s) {
+cudaError_t launch_tag(const LevelDev& L, const Item* items, int n, double tol2, uint8_t* tags, cudaStream_t s,
+                       const int* nc) {
     if (n <= 0) return cudaSuccess;
-    tag_kernel<<<tile_grid(n, 0), CTA_THREADS, 0, s>>>(L, items, n, tol2, tags);
+    tag_kernel<<<list_grid(n, nc), CTA_THREADS, 0, s>>>(L, items, n, tol2, tags, nc);
     return cudaGetLastError();
 }
 
-cudaError_t launch_qmax(const LevelDev& L, const Item* items, int n, unsigned long long* qmax, cudaStream_t s) {
+cudaError_t launch_qmax(const LevelDev& L, const Item* items, int n, unsigned long long* qmax, cudaStream_t s,
+                        const int* nc) {
     if (n <= 0) return cudaSuccess;
-    qmax_kernel<<<tile_grid(n, 0), CTA_THREADS, 0, s>>>(L, items, n, qmax);
+    qmax_kernel<<<list_grid(n, nc), CTA_THREADS, 0, s>>>(L, items, n, qmax, nc);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tag_flux(const LevelDev& L, const Item* items, int n, const unsigned long long* qmax, double tol,
-                            uint8_t* tags, cudaStream_t s) {
+                            uint8_t* tags, cudaStream_t s, const int* nc) {
     if (n <= 0) return cudaSuccess;
-    tag_flux_kernel<<<tile_grid(n, 0), CTA_THREADS, 0, s>>>(L, items, n, qmax, tol, tags);
+    tag_flux_kernel<<<list_grid(n, nc), CTA_THREADS, 0, s>>>(L, items, n, qmax, tol, tags, nc);
     return cudaGetLastError();
 }
 
@@ -1495,21 +1552,30 @@ cudaError_t launch_blockflag(const uint8_t* tags, int nx, int ny, int px, int py
     return cudaGetLastError();
 }
 
-cudaError_t launch_merge(const LevelDev& L, const Item* items, int n, cudaStream_t s) {
+cudaError_t launch_merge(const LevelDev& L, const Item* items, int n, cudaStream_t s, const int* nc) {
     if (n <= 0) return cudaSuccess;
-    merge_kernel<<<tile_grid(n, 0), CTA_THREADS, 0, s>>>(L, items, n);
+    merge_kernel<<<list_grid(n, nc), CTA_THREADS, 0, s>>>(L, items, n, nc);
     return cudaGetLastError();
 }
 
-cudaError_t launch_split(const LevelDev& C, const LevelDev& F, const Item* items, int n, cudaStream_t s) {
+cudaError_t launch_split(const LevelDev& C, const LevelDev& F, const Item* items, int n, cudaStream_t s,
+                         const int* nc) {
     if (n <= 0) return cudaSuccess;
-    split_kernel<<<tile_grid(n, 0), CTA_THREADS, 0, s>>>(C, F, items, n);
+    split_kernel<<<list_grid(n, nc), CTA_THREADS, 0, s>>>(C, F, items, n, nc);
     return cudaGetLastError();
 }
 
 cudaError_t launch_flags(const LevelDev& L, const uint8_t* blk_in, const uint8_t* blk_cov, const uint16_t* oldf,
                          uint16_t* newf, cudaStream_t s) {
     flags_kernel<<<flat_grid((long long)L.pitch * L.ny), 256, 0, s>>>(L, blk_in, blk_cov, oldf, newf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flags_update(const LevelDev& L, const Item* items, int cap, const int* nc, const uint8_t* blk_in,
+                                const uint8_t* blk_cov, uint16_t* flags, uint16_t* tmp, cudaStream_t s) {
+    const int g = list_grid(cap, nc);
+    flags_blocks_kernel<<<g, CTA_THREADS, 0, s>>>(L, items, nc, blk_in, blk_cov, flags, tmp, 0);
+    flags_blocks_kernel<<<g, CTA_THREADS, 0, s>>>(L, items, nc, blk_in, blk_cov, flags, tmp, 1);
     return cudaGetLastError();
 }
 

@@ -7,9 +7,12 @@
 
 namespace vlbm {
 
+// Launchers over a tile list take its length n, or -- with nc != nullptr --
+// its capacity n and the length in device memory at nc.
 cudaError_t launch_sweep(const LevelDev* levs, const Item* items, int n, int kk, int kkp, int max_ctas, int variant,
-                         cudaStream_t s, bool sensor = false);
-cudaError_t launch_sensor(const LevelDev* levs, const Item* items, int n, int kk, cudaStream_t s);
+                         cudaStream_t s, bool sensor = false, const int* nc = nullptr);
+cudaError_t launch_sensor(const LevelDev* levs, const Item* items, int n, int kk, cudaStream_t s,
+                          const int* nc = nullptr);
 int sweep_variants();
 bool sweep_variant_needs_om_minus1(int v);
 int task_kernel_ctas(int variant);
@@ -17,24 +20,34 @@ cudaError_t launch_tasks(const LevelDev* levs, const Segment* segs, const int* p
                          cudaStream_t s);
 cudaError_t launch_audit_segments(const unsigned long long* slots, const int* seg, int nseg, double* out,
                                   cudaStream_t s);
-cudaError_t launch_close(const LevelDev* levs, const Item* items, int n, int kk, cudaStream_t s);
+cudaError_t launch_close(const LevelDev* levs, const Item* items, int n, int kk, cudaStream_t s,
+                         const int* nc = nullptr);
 cudaError_t launch_end_step(int* const* par, int n, cudaStream_t s);
 cudaError_t launch_feq_init(const LevelDev& L, const double* W, long long ld, double hc, cudaStream_t s);
 cudaError_t launch_copy_pop(const LevelDev& L, double* ext, long long ld, int to_ext, cudaStream_t s);
 cudaError_t launch_gather_W(const LevelDev& L, double* W, long long ld, uint8_t* valid, cudaStream_t s);
 int audit_blocks(int nitems);
 cudaError_t launch_audit(const LevelDev* levs, const Item* items, int n, unsigned long long* part, double* out,
-                         cudaStream_t s);
-cudaError_t launch_avgdown(const LevelDev& C, const LevelDev& F, const Item* items, int n, cudaStream_t s);
-cudaError_t launch_tag(const LevelDev& L, const Item* items, int n, double tol2, uint8_t* tags, cudaStream_t s);
-cudaError_t launch_qmax(const LevelDev& L, const Item* items, int n, unsigned long long* qmax, cudaStream_t s);
+                         cudaStream_t s, const int* nc = nullptr);
+cudaError_t launch_avgdown(const LevelDev& C, const LevelDev& F, const Item* items, int n, cudaStream_t s,
+                           const int* nc = nullptr);
+cudaError_t launch_tag(const LevelDev& L, const Item* items, int n, double tol2, uint8_t* tags, cudaStream_t s,
+                       const int* nc = nullptr);
+cudaError_t launch_qmax(const LevelDev& L, const Item* items, int n, unsigned long long* qmax, cudaStream_t s,
+                        const int* nc = nullptr);
 cudaError_t launch_tag_flux(const LevelDev& L, const Item* items, int n, const unsigned long long* qmax, double tol,
-                            uint8_t* tags, cudaStream_t s);
+                            uint8_t* tags, cudaStream_t s, const int* nc = nullptr);
 cudaError_t launch_blockflag(const uint8_t* tags, int nx, int ny, int px, int py, int buffer, uint8_t* out,
                              cudaStream_t s);
-cudaError_t launch_merge(const LevelDev& L, const Item* items, int n, cudaStream_t s);
-cudaError_t launch_split(const LevelDev& C, const LevelDev& F, const Item* items, int n, cudaStream_t s);
+cudaError_t launch_merge(const LevelDev& L, const Item* items, int n, cudaStream_t s, const int* nc = nullptr);
+cudaError_t launch_split(const LevelDev& C, const LevelDev& F, const Item* items, int n, cudaStream_t s,
+                         const int* nc = nullptr);
 cudaError_t launch_flags(const LevelDev& L, const uint8_t* blk_in, const uint8_t* blk_cov, const uint16_t* oldf,
                          uint16_t* newf, cudaStream_t s);
+// Flags of the listed blocks (on the level before or after a layout change;
+// length at *nc, capacity cap) from the new block maps, rebuilt in place
+// through tmp (which it overwrites).
+cudaError_t launch_flags_update(const LevelDev& L, const Item* items, int cap, const int* nc, const uint8_t* blk_in,
+                                const uint8_t* blk_cov, uint16_t* flags, uint16_t* tmp, cudaStream_t s);
 
 }  // namespace vlbm

@@ -92,6 +92,7 @@ def lib():
         "vlbm_audit": [vp, dp, dp],
         "vlbm_sync": [vp],
         "vlbm_get_info": [vp, C.POINTER(vlbm_info)],
+        "vlbm_lups_done": [vp, C.POINTER(i64)],
         "vlbm_host_times": [vp, dp],
         "vlbm_set_sensor": [vp, i32, C.c_double, C.c_double, C.c_double],
         "vlbm_profile": [vp, i64, C.POINTER(vlbm_kernel_time), i32, C.POINTER(i32)],
@@ -125,6 +126,8 @@ def lib():
     L.vlbm_selftest_fp64.restype = C.c_int
     L.vlbm_selftest_rcp.argtypes = [C.c_uint64, i64, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), dp]
     L.vlbm_selftest_rcp.restype = C.c_int
+    L.vlbm_selftest_layout.argtypes = [C.c_uint64, i32, C.POINTER(i64), C.POINTER(i64), C.c_char_p, i32]
+    L.vlbm_selftest_layout.restype = C.c_int
     L.vlbm_totals_static.argtypes = [vp, i64, i32, i32, C.c_double, vp, vp]
     L.vlbm_totals_static.restype = C.c_int
     L.vlbm_last_error.argtypes = [vp]
@@ -315,6 +318,13 @@ class Hierarchy:
                 "active_cells": list(i.active_cells[: i.nlev]), "lups_per_step": i.lups_per_step,
                 "device_bytes": i.device_bytes, "steps": i.steps, "c": i.c, "beta": i.beta}
 
+    def lups_done(self):
+        """Cell updates done since creation, counted on the device at the
+        layout each step ran on (vlbm_lups_done; synchronises)."""
+        v = C.c_int64()
+        _check(self._h, lib().vlbm_lups_done(self._h, C.byref(v)))
+        return int(v.value)
+
     def set_sensor(self, on=True, beta_min=0.5, c_sensor=16.0, eps=1e-30):
         """Sensor-driven relaxation (vlbm_set_sensor): beta_max is the
         hierarchy's beta; the flux maxima are fixed from the current state."""
@@ -416,6 +426,19 @@ def selftest_rcp(seed, n):
     if st != 0:
         raise VlbmError(st, "vlbm_selftest_rcp")
     return int(bad.value), int(uns.value), tuple(first)
+
+
+def selftest_layout(seed, cases):
+    """Device-resident layouts against the host's layout rule, tile lists and
+    task builder on seeded random hierarchies; returns (mismatches, tasks
+    that took the builder's second pass, first difference)."""
+    bad = C.c_int64()
+    big = C.c_int64()
+    buf = C.create_string_buffer(512)
+    st = lib().vlbm_selftest_layout(int(seed), int(cases), C.byref(bad), C.byref(big), buf, 512)
+    if st != 0:
+        raise VlbmError(st, "vlbm_selftest_layout")
+    return int(bad.value), int(big.value), buf.value.decode()
 
 
 def selftest_timeout():

@@ -1,17 +1,21 @@
 #!/usr/bin/env python3
 """Throughput benchmark of the refined VLBM on B300 (FP64).
 
-Workload: the isentropic-vortex configuration -- periodic [0,10]^2, vortex
-strength 5, free stream (1,1), gamma = 1.4, FP64 -- at the largest size of
-its convergence series: 512 x 512 coarse cells with a ratio-2 patch over the
-central 256 x 256 coarse cells (25 % of the area), time ratio 2.  One step is
-one coarse step of the whole hierarchy: the level-0 sweep, two level-1
-sweeps (fused collide + push-stream + mean-preserving coarse-to-fine
-reconstruction), the reflux close and the end-of-step bookkeeping.
+Workload: the adaptive shock-bubble -- a Mach 1.22 planar shock running into
+a circular light-gas bubble (density ratio 0.14, radius 1/8 of the domain
+height) on [0, 2] x [0, 1], gamma = 1.4, FP64 -- on a 2048 x 1024 coarse
+grid with up to three levels of ratio 2, regridded every 4 coarse steps from
+the normalised density-gradient indicator with the conservative split and
+merge operators, its totals audited exactly across every regrid.  One step
+is one coarse step of the whole hierarchy (one level-0 step, two level-1
+steps, four level-2 steps, reconstruction and reflux at every interface);
+the regrid that follows every fourth step of the run, and its two audits,
+are inside the timed region.
 
-Metric: MLUPS (cell updates per second, counting every active cell of every
-level once per level step) and the fraction of the roofline of the dominant
-kernel (the level sweep), which on B300 is bounded by the FP64 pipe.
+Metric: MLUPS (cell updates per second, every active cell of every level
+counted once per level step, counted on the device at the layout each step
+ran on) and the roofline fraction of the dominant kernel (the level sweep),
+which on B300 is bounded by the FP64 pipe.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 
@@ -21,8 +25,9 @@ whole-job aggregate.  `--impl reference` times the oracle (the plain FP64 CPU
 rendering of the method) on the host cores, on the same workload and metric.
 """
 import argparse
+import hashlib
 import json
-import math
+import multiprocessing as mp
 import os
 import statistics
 import subprocess
@@ -37,27 +42,33 @@ sys.path.insert(0, ROOT)
 
 from paper_2609_35529_b300 import inputs as I  # noqa: E402
 
-WORKLOAD = "isentropic vortex 512^2 coarse + central ratio-2 patch (2 levels), periodic, FP64"
+WORKLOAD = ("AMR shock-bubble: Mach 1.22 shock into a bubble of density ratio 0.14 (radius 1/8 of the height), "
+            "2048x1024 coarse, 3 levels of ratio 2, regrid every 4 coarse steps (normalised density gradient, "
+            "tol 0.02, buffer 2, split/merge), exact audit before and after every regrid, FP64")
 METRIC = "MLUPS (FP64, 1 B300)"
 # FP64 arithmetic of one cell update in the canonical collision (FMA = 2
-# flops, the one division = 1): 12 adds (moments), 1 division, 14 flux
-# operations of which one is fused (15 flops), 4 products (beta/2) W,
-# 32 fused multiply-adds (relaxation).
+# flops, the one reciprocal = 1): 12 adds (moments), 1 reciprocal, 14 flux
+# operations of which one is fused (15 flops), 4 products (beta/2) W, 32
+# fused multiply-adds (relaxation).
 FLOPS_PER_LUP = 12 + 1 + 15 + 4 + 64
 # algorithmic bytes of one cell update: 16 populations read + 16 written
 BYTES_PER_LUP = 256
-# FP64-pipe operations of one cell update: the 62 arithmetic operations (the
-# reciprocal 1/rho runs on the integer pipes); ncu counts 33.0 DFMA + 16.1
-# DADD + 13.0 DMUL thread-instructions per cell update in the task kernel
+# FP64-pipe operations of one cell update (the reciprocal runs on the
+# integer pipes)
 FP64_OPS_PER_LUP = 62
-# DRAM traffic of the task kernel per cell update: dram__bytes_read.sum +
-# dram__bytes_write.sum of a launch of 64 coarse steps (variant 1, audit off,
-# 512 MB L2 flush before each launch), ncu --nvtx capture of this bench's
-# roofline launches (profiles/task_kernel_vortex512.md): 3.612e9 + 6.525e9 B
-# per 46 137 344 cell updates.  Valid for the kernel as captured (integer-pipe
-# reciprocal, audit tasks); to be measured again whenever the kernel changes.
-TASK_KERNEL_DRAM_BYTES_PER_LUP = 219.7
-TRAFFIC_VARIANT = 1
+# DRAM traffic of the per-phase sweep kernel per cell update on this
+# workload: dram__bytes_read.sum + dram__bytes_write.sum over the sweep
+# launches of one ncu capture of the same layout type (1024 x 512 coarse
+# shock-bubble, three adaptive levels), divided by their cell updates; valid
+# while the kernel source is the one captured (SWEEP_SOURCE_SHA of
+# csrc/vlbm_kernels.cu), else the line reports traffic as null.
+SWEEP_DRAM_BYTES_PER_LUP = None
+SWEEP_SOURCE_SHA = None
+
+
+def kernel_source_sha():
+    with open(os.path.join(ROOT, "paper_2609_35529_b300", "csrc", "vlbm_kernels.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
 def peaks():
@@ -129,23 +140,11 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_rate(case, seconds):
-    """The oracle (plain FP64 CPU code, one thread) on `case`: coarse steps
-    until `seconds` of CPU time have passed.  Returns (MLUPS, steps, wall)."""
-    from oracle import oracle as O
-    o = O.Hierarchy(case.nx0, case.ny0, case.nlev, 2, case.bc, case.gamma, case.c, case.beta, case.inflow)
-    o.set_layout(case.refs if case.nlev > 1 else None)
-    for l in range(case.nlev):
-        o.set_state(l, case.W[l])
-    lups = case.lups_per_step()
-    n, t0 = 0, time.perf_counter()
-    while True:
-        o.advance(1)
-        n += 1
-        el = time.perf_counter() - t0
-        if el >= seconds:
-            break
-    return lups * n / el / 1e6, n, el
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
 
 
 def job_time(x, pg, device="cpu"):
@@ -164,59 +163,168 @@ def job_mlups(lups_per_step, steps, world, ms):
     return world * lups_per_step * steps / (ms * 1e-3) / 1e6
 
 
-def dist_env():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+def run_steps(h, n, state, every):
+    """n coarse steps of the run, regridding after every `every`-th step of
+    the run (state["step"] counts the run's steps)."""
+    while n > 0:
+        k = min(n, every - state["step"] % every)
+        h.advance(k)
+        state["step"] += k
+        n -= k
+        if state["step"] % every == 0:
+            h.regrid()
+
+
+# --------------------------------------------------------------------------
+# the oracle on the host cores (cpu_baseline and the reference arm)
+# --------------------------------------------------------------------------
+
+def oracle_setup(case):
+    from oracle import oracle as O
+    o = O.Hierarchy(case.nx0, case.ny0, case.nlev, 2, case.bc, case.gamma, case.c, case.beta, case.inflow)
+    o.set_layout(None)
+    o.set_state(0, case.W[0])
+    for _ in range(case.nlev - 1):
+        o.regrid_tagged(case.amr["tol"], case.amr["buffer"], 8)
+    return o
+
+
+def oracle_lups_per_step(o, nlev):
+    act = o.active_masks()
+    return sum(int(act[l].sum()) << l for l in range(nlev))
+
+
+def oracle_cycles(o, case, steps, budget_s, state):
+    """Up to `steps` coarse steps of the oracle with the run's regrids,
+    stopping once budget_s seconds have passed; returns (lups, steps done,
+    seconds)."""
+    every = case.amr["every"]
+    lups, done, t0 = 0, 0, time.perf_counter()
+    while done < steps:
+        k = min(steps - done, every - state["step"] % every)
+        lups += oracle_lups_per_step(o, case.nlev) * k
+        o.advance(k)
+        state["step"] += k
+        done += k
+        if state["step"] % every == 0:
+            o.regrid_tagged(case.amr["tol"], case.amr["buffer"], 8)
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    return lups, done, time.perf_counter() - t0
+
+
+def _replica(args):
+    """One oracle replica (a process of its own): set up, then one regrid
+    cycle of the workload timed."""
+    steps, q = args
+    case = I.shockbubble()
+    o = oracle_setup(case)
+    lups, done, el = oracle_cycles(o, case, steps, 1e9, {"step": 0})
+    q.put((lups, el))
+
+
+def mem_available_bytes():
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except Exception:
+        pass
+    return 0
+
+
+def cpu_baseline(seconds):
+    """The oracle on the host: one thread on one regrid cycle (4 coarse steps
+    and the regrid) of the workload after its set-up, then as many
+    concurrent single-thread replicas of the same sample as the cores and
+    the host memory allow (each replica is a process of its own; the oracle
+    itself is single-threaded)."""
+    case = I.shockbubble()
+    every = case.amr["every"]
+    o = oracle_setup(case)
+    lups, done, el = oracle_cycles(o, case, every, seconds, {"step": 0})
+    one = {"value": round(lups / el / 1e6, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+           "sample": f"{done} coarse steps of the workload and the regrid after them ({el:.1f} s, one thread), "
+                     f"after the initial layout"}
+    del o
+    cores = os.cpu_count() or 1
+    per = 13 * (1 << 30)  # host memory of one oracle instance of this workload (dense levels)
+    reps = max(1, min(cores, 64, int(0.6 * mem_available_bytes() / per)))
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_replica, args=((every, q),)) for _ in range(reps)]
+    for p in procs:
+        p.start()
+    res = [q.get() for _ in procs]
+    for p in procs:
+        p.join()
+    agg = sum(r[0] for r in res) / max(r[1] for r in res) / 1e6
+    one["all_cores"] = {"value": round(agg, 3), "unit": "MLUPS", "cores": reps, "nproc": cores,
+                        "sample": f"{reps} concurrent single-thread replicas of the same sample "
+                                  f"(limited by host memory: ~13 GB each)" if reps < cores else
+                                  f"{reps} concurrent single-thread replicas of the same sample"}
+    one["nproc"] = cores
+    return one
 
 
 def run_reference(args, budget_s=90.0):
-    """The oracle on the host cores.  Each timed step is one coarse step of
-    the workload; the run stops after `budget_s` seconds of timed steps (a
-    bounded sample of the K requested) so that it ends within minutes."""
+    """The reference arm: the oracle, as it stands, on the host cores, on the
+    same workload and metric: the initial layout, min(W, 1) warm-up steps,
+    then up to K coarse steps with the run's regrids (a bounded sample: at
+    most budget_s seconds of timed steps)."""
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
-    case = I.vortex(N=512, steps=args.steps)
-    lups = case.lups_per_step()
-    from oracle import oracle as O
-    o = O.Hierarchy(case.nx0, case.ny0, case.nlev, 2, case.bc, case.gamma, case.c, case.beta)
-    o.set_layout(case.refs)
-    for l in range(case.nlev):
-        o.set_state(l, case.W[l])
-    for _ in range(min(args.warmup, 1)):
-        o.advance(1)
-    t0 = time.perf_counter()
-    done = 0
-    while done < args.steps:
-        o.advance(1)
-        done += 1
-        if time.perf_counter() - t0 >= budget_s:
-            break
-    el = time.perf_counter() - t0
-    v = lups * done / el / 1e6
+    case = I.shockbubble()
+    o = oracle_setup(case)
+    state = {"step": 0}
+    oracle_cycles(o, case, min(args.warmup, 1), 1e9, state)
+    lups, done, el = oracle_cycles(o, case, args.steps, budget_s, state)
+    v = lups / el / 1e6
+    cores = os.cpu_count() or 1
     line = {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "MLUPS", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / done * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / max(done, 1) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "lups_per_step": lups, "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": round(v, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                             "sample": f"{done} of {args.steps} coarse steps of the workload (time budget "
-                                       f"{budget_s:.0f} s), one thread"},
+            "config": {"workload": WORKLOAD, "coarse": [case.nx0, case.ny0], "levels": case.nlev,
+                       "regrid_every": case.amr["every"], "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": round(v, 3), "unit": "MLUPS", "cores": 1, "nproc": cores, "kind": "oracle",
+                             "sample": f"{done} of {args.steps} coarse steps of the workload with their regrids "
+                                       f"(time budget {budget_s:.0f} s), one thread"},
             "e2e": {"value": round(v, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
+# --------------------------------------------------------------------------
+# extra workloads (context for the headline; static layouts)
+# --------------------------------------------------------------------------
+
+def static_rate(V, case, stream, steps=256, schedule=1, graph_steps=16):
+    h = V.Hierarchy.from_case(case, stream=stream)
+    h.set_tuning(schedule=schedule, graph_steps=graph_steps)
+    h.advance(graph_steps)
+    h.sync()
+    l0 = h.lups_done()
+    t0 = time.perf_counter()
+    h.advance(steps)
+    h.sync()
+    el = time.perf_counter() - t0
+    v = (h.lups_done() - l0) / el / 1e6
+    h.close()
+    return round(v, 1)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=4000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--variant", type=int, default=-1,
-                    help="sweep variant; -1 (default) lets the autotuner pick variant, schedule and steps per launch")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--schedule", type=int, default=-1,
+                    help="0 per-phase, 1 persistent; -1 (default) lets the autotuner pick")
+    ap.add_argument("--no-extras", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -230,178 +338,169 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
         pg = dist
     dev = torch.cuda.current_device()
-    from paper_2609_35529_b300 import build, vlbm as V
+    from paper_2609_35529_b300 import autotune, build, vlbm as V
     build.build()
 
-    case = I.vortex(N=512, steps=args.steps)
+    case = I.shockbubble()
+    every = case.amr["every"]
     stream = torch.cuda.Stream()
-    g = V.Hierarchy.from_case(case, stream=stream)
-    if args.variant >= 0:
-        g.set_tuning(variant=args.variant)
+
+    def make():
+        h = V.Hierarchy.from_case(case, stream=stream)
+        for _ in range(case.nlev - 1):
+            h.regrid()
+        return h
+
+    # launch shape: the project's autotuner on scratch hierarchies of the
+    # same workload (regrid cycles), or a fixed schedule
+    if args.schedule < 0:
+        tune, trials = autotune.tune_adaptive(make, every, cycles=6)
     else:
-        # launch shape from the project's autotuner, timed on a scratch
-        # hierarchy of the same configuration (the persistent schedule is
-        # required for the per-step audit)
-        from paper_2609_35529_b300 import autotune
-        cands = [c for c in autotune.DEFAULT_CANDIDATES if c["schedule"] == 1]
-        autotune.tune(lambda: V.Hierarchy.from_case(case, stream=stream), target=g, candidates=cands, steps=128)
-    # every step includes the exact conservation audit
-    g.set_step_totals(True)
-    tune = g.get_tuning()
-    chunk = max(1, tune["graph_steps"])
-    info = g.info()
-    lups = info["lups_per_step"]
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        tune = {"variant": 1, "schedule": args.schedule, "max_ctas": 0, "graph_steps": every, "persist_after": 0}
+        trials = {}
+    torch.cuda.empty_cache()
+    h = make()
+    h.set_tuning(**tune)
+    h.set_regrid_audit(True)
+    state = {"step": 0}
+    run_steps(h, max(3, args.warmup), state, every)
+    h.sync()
+    h.regrid_audits()  # drop the warm-up rows
+    info0 = h.info()
 
-    # warm-up (also builds the task lists and instantiates the CUDA graphs)
-    for _ in range(max(3, args.warmup)):
-        g.advance(1)
-    g.advance(chunk)
-    g.sync()
-    g.step_totals()  # drop the warm-up rows
-
-    # timed: iterations of `chunk` coarse steps (one graph launch each), the
-    # L2 flushed between iterations
-    iters = max(1, args.steps // chunk)
-    steps = iters * chunk
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(iters)]
+    # timed: exactly K coarse steps; an iteration is the steps up to the
+    # next regrid point of the run and that regrid (with its audits); the
+    # working set (11 GB) is far larger than the 126 MB L2, so no flush
+    marks = torch.zeros(2 + args.steps, dtype=torch.int64).pin_memory()
+    chunks = []
+    left, s = args.steps, state["step"]
+    while left > 0:
+        k = min(left, every - s % every)
+        chunks.append(k)
+        s += k
+        left -= k
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in chunks]
+    k0 = h.kernels_launched()
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
     with ClockSampler(dev) as clk:
-        torch.cuda.nvtx.range_push("timed")  # lets ncu select these launches (--nvtx-include timed/)
         with torch.cuda.stream(stream):
-            for i in range(iters):
-                flush.fill_(float(i))  # > L2 between timed iterations
+            h.lups_mark(marks.data_ptr())
+            for i, k in enumerate(chunks):
                 ev[i][0].record(stream)
-                g.advance(chunk)
+                run_steps(h, k, state, every)
                 ev[i][1].record(stream)
+                h.lups_mark(marks.data_ptr() + 8 * (i + 1))
         torch.cuda.synchronize()
-        torch.cuda.nvtx.range_pop()
-    g.sync()
-    rows = g.step_totals(cap=steps)
-    drift = float(np.max(np.abs(rows[:, :4] - rows[0, :4]) / rows[0, 4:])) if len(rows) else None
+    launches = h.kernels_launched() - k0
     it_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = sum(it_ms)
+    ms = ev[0][0].elapsed_time(ev[-1][1])
+    m = marks.numpy()
+    it_lups = [int(m[i + 1] - m[i]) for i in range(len(chunks))]
+    lups = int(m[len(chunks)] - m[0])
     if pg:
         pg.barrier()
     ms = job_time(ms, pg, "cuda")
-    value = job_mlups(lups, steps, world, ms)
+    value = job_mlups(lups, 1, world, ms)
+    # conservation across the timed regrids
+    rows = h.regrid_audits()
+    if len(rows):
+        drift = float(np.max(np.abs(rows[:, 8:12] - rows[:, 0:4]) / np.maximum(rows[:, 4:8], 1e-300)))
+    else:
+        drift = None
+    info1 = h.info()
 
-    # roofline of the dominant kernel, the persistent task kernel (all
-    # sweeps and closes of `chunk` coarse steps in one launch): timed alone
-    # -- the same launches with the per-step audit off, so that the graph
-    # holds just the kernel (and its 8-byte counter reset) -- with CUDA
-    # events on the library's stream, L2 flushed between launches
+    # roofline of the dominant kernel, the level sweep: eager per-phase
+    # launches of the same hierarchy (layout of the end of the timed steps),
+    # each timed with CUDA events on the library's stream
     pk = peaks()
-    g.set_step_totals(False)
-    g.advance(chunk)
-    nk = min(iters, 64)
-    evk = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nk)]
-    torch.cuda.synchronize()
-    torch.cuda.nvtx.range_push("roofline")  # lets ncu select these launches (--nvtx-include roofline/)
-    with torch.cuda.stream(stream):
-        for i in range(nk):
-            flush.fill_(float(i))
-            evk[i][0].record(stream)
-            g.advance(chunk)
-            evk[i][1].record(stream)
-    torch.cuda.synchronize()
-    torch.cuda.nvtx.range_pop()
-    g.sync()
-    launch_ms = statistics.mean(a.elapsed_time(b) for a, b in evk)
-    audit_share = 1.0 - launch_ms / statistics.mean(it_ms)
-    cells = lups * chunk
-    achieved_tflops = FLOPS_PER_LUP * cells / (launch_ms * 1e-3) / 1e12
-    hbm_gbs = BYTES_PER_LUP * cells / (launch_ms * 1e-3) / 1e9
-    kernel = "task_kernel" if tune["schedule"] == 1 else "sweep_kernel"
-    # the per-phase sweep kernel measured alone (eager launches with events)
-    prof = g.profile(min(steps, 64))
+    prof = h.profile(8)
     sweep = [r for r in prof if r["kind"] == "sweep"]
     sw_ms = sum(r["ms"] for r in sweep)
     sw_cells = sum(r["cells"] for r in sweep)
+    sw_launches = sum(r["launches"] for r in sweep)
+    launch_ms = sw_ms / sw_launches
+    cells = sw_cells / sw_launches
+    achieved_tflops = FLOPS_PER_LUP * cells / (launch_ms * 1e-3) / 1e12
+    hbm_gbs = BYTES_PER_LUP * cells / (launch_ms * 1e-3) / 1e9
     traffic = None
-    if tune["schedule"] == 1 and tune["variant"] == TRAFFIC_VARIANT:
-        traffic = round(TASK_KERNEL_DRAM_BYTES_PER_LUP * cells)  # bytes per launch
+    if SWEEP_DRAM_BYTES_PER_LUP is not None and SWEEP_SOURCE_SHA == kernel_source_sha():
+        traffic = round(SWEEP_DRAM_BYTES_PER_LUP * cells)
     roof = {"bound": "alu", "achieved": round(achieved_tflops, 4), "peak": round(pk["fp64_tflops"], 4),
             "unit": "TFLOP/s", "frac": round(achieved_tflops / pk["fp64_tflops"], 4), "traffic": traffic,
-            "traffic_unit": "bytes per launch (ncu capture scaled by cell updates)",
-            "kernel": kernel, "avg_launch_ms": round(launch_ms, 5), "cells_per_launch": cells,
-            "flops_per_lup": FLOPS_PER_LUP, "peak_basis": "2 FP64 FMA/clk/SM x 148 SMs x sm_max_mhz",
+            "traffic_unit": "bytes per launch (ncu capture per cell update x the launch's cell updates)",
+            "kernel": "sweep_kernel", "avg_launch_ms": round(launch_ms, 5), "cells_per_launch": round(cells),
+            "launches_timed": sw_launches, "flops_per_lup": FLOPS_PER_LUP,
+            "peak_basis": "2 FP64 FMA/clk/SM x 148 SMs x sm_max_mhz x 2 flops (no FP64 figure in MEASURED_PEAKS)",
             "hbm": {"achieved": round(hbm_gbs, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
                     "frac": round(hbm_gbs / pk["hbm_gbs"], 4), "peak_source": pk["source"]},
-            "sweep_kernel_alone_mlups": round(sw_cells / sw_ms / 1e3, 1),
-            "audit_share_of_step": round(audit_share, 4),
             "fp64_pipe": {"ops_per_lup": FP64_OPS_PER_LUP,
                           "achieved_gops": round(FP64_OPS_PER_LUP * cells / (launch_ms * 1e-3) / 1e9, 1),
                           "peak_gops_nominal": round(2 * 148 * pk["sm_max_mhz"] * 1e6 / 1e9, 1),
                           "frac_of_nominal": round(FP64_OPS_PER_LUP * cells / (launch_ms * 1e-3)
                                                    / (2 * 148 * pk["sm_max_mhz"] * 1e6), 4)}}
-    # schedule 1: the task kernel (sweeps and audit reductions) and the
-    # kernel that rounds each step's audit totals
-    launches_per_iter = 2 if tune["schedule"] == 1 else None
-    if launches_per_iter is None:
-        launches_per_iter = sum(r["launches"] for r in prof) / min(steps, 64) * chunk
+    h.close()
+    torch.cuda.empty_cache()
 
     # end to end through the public API with host buffers: the initial state
-    # from pinned host memory, every step's conservation totals read back to
-    # the host (one copy per launch of `chunk` steps), the final state read
-    # back.
-    Wh = [torch.from_numpy(np.ascontiguousarray(w)).pin_memory().numpy() for w in case.W]
-    # the results land in pinned host buffers too (allocated before timing)
-    Wr = [torch.empty(w.shape, dtype=torch.float64).pin_memory().numpy() for w in case.W]
+    # from pinned host memory, the initial layout and K coarse steps with
+    # their regrids, every level's final W read back into pinned host memory
+    Wh = torch.from_numpy(np.ascontiguousarray(case.W[0])).pin_memory().numpy()
+    shapes = [(4, case.ny0 << l, case.nx0 << l) for l in range(case.nlev)]
+    Wr = [torch.empty(sh, dtype=torch.float64).pin_memory().numpy() for sh in shapes]
     h2 = V.Hierarchy(case.nx0, case.ny0, case.nlev, case.bc, case.gamma, case.c, case.beta, dx0=case.dx0,
-                     stream=stream)
-    h2.regrid_masks(case.refs)
-    h2.set_step_totals(True)
-    for l in range(case.nlev):
-        h2.set_state(l, Wh[l])
-    h2.advance(chunk)
-    h2.step_totals()
+                     inflow=case.inflow, tag_tol=case.amr["tol"], tag_buffer=case.amr["buffer"], stream=stream)
+    h2.set_tuning(**tune)
     torch.cuda.synchronize()
-    n_e2e = min(steps, 2048)
     t0 = time.perf_counter()
+    h2.set_state(0, Wh)
+    for _ in range(case.nlev - 1):
+        h2.regrid()
+    st2 = {"step": 0}
+    run_steps(h2, args.steps, st2, every)
     for l in range(case.nlev):
-        h2.set_state(l, Wh[l])
-    got = 0
-    for _ in range(n_e2e // chunk):
-        h2.advance(chunk)
-        got += len(h2.step_totals())
-    Wout = [h2.get_conserved(l, out=Wr[l], valid=False)[0] for l in range(case.nlev)]
+        h2.get_conserved(l, out=Wr[l], valid=False)
     e2e_s = time.perf_counter() - t0
-    assert got == (n_e2e // chunk) * chunk
-    n_e2e = (n_e2e // chunk) * chunk
+    e2e_lups = h2.lups_done()
+    h2.close()
     e2e_s = job_time(e2e_s, pg, "cuda")
-    wbytes = sum(w.nbytes for w in case.W)
-    e2e = {"value": round(job_mlups(lups, n_e2e, world, e2e_s * 1e3), 3), "unit": "MLUPS",
-           "h2d_bytes_per_step": wbytes / n_e2e, "d2h_bytes_per_step": 64 + wbytes / n_e2e,
-           "note": f"{n_e2e} steps through the C ABI: vlbm_set_state from pinned host W, vlbm_advance in "
-                   f"launches of {chunk} steps, each step's conservation totals (64 B) read to the host "
-                   f"after every launch, final W of every level read back into pinned host memory"}
+    wbytes = Wh.nbytes
+    rbytes = sum(w.nbytes for w in Wr)
+    e2e = {"value": round(world * e2e_lups / e2e_s / 1e6, 3), "unit": "MLUPS",
+           "h2d_bytes_per_step": wbytes / args.steps, "d2h_bytes_per_step": rbytes / args.steps,
+           "note": f"{args.steps} coarse steps through the C ABI from a fresh hierarchy: vlbm_set_state from pinned "
+                   f"host W, the initial layout ({case.nlev - 1} tag-driven regrids), the steps with their regrids, "
+                   f"every level's final W read back into pinned host memory; wall clock"}
+
+    extras = None
+    if not args.no_extras:
+        extras = {"vortex_512_patch_static_mlups": static_rate(V, I.vortex(N=512), stream),
+                  "laxliu3_1024_three_levels_static_mlups": static_rate(V, I.riemann3(N=1024, nlev=3), stream)}
 
     if rank == 0:
         cpu = None
         if world == 1 and args.cpu_seconds > 0:
-            mlups, nst, el = oracle_rate(case, args.cpu_seconds)
-            cpu = {"value": round(mlups, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                   "sample": f"{nst} coarse steps of the same workload ({el:.1f} s, one thread)"}
+            cpu = cpu_baseline(args.cpu_seconds)
+        its = [l / (t * 1e-3) / 1e6 for l, t in zip(it_lups, it_ms) if t > 0]
         line = {"metric": METRIC, "value": round(value, 3), "unit": "MLUPS", "n_gpus": world,
-                "steps": steps, "warmup": max(3, args.warmup), "ms_per_step": ms / steps,
+                "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic (closed-form initial state)",
                 "config": {"workload": WORKLOAD, "coarse": [case.nx0, case.ny0], "levels": case.nlev,
-                           "lups_per_step": lups, "c": case.c, "beta": case.beta,
-                           "l2": f"flushed between timed iterations of {chunk} coarse steps (512 MB write)",
-                           "tuning": tune,
+                           "regrid_every": every, "timed_steps": [state["step"] - args.steps, state["step"]],
+                           "lups_per_step_at_start": info0["lups_per_step"],
+                           "lups_per_step_at_end": info1["lups_per_step"],
+                           "active_cells_at_end": info1["active_cells"], "c": case.c, "beta": case.beta,
+                           "l2": "not flushed: the working set (about 11 GB) is far larger than the 126 MB L2",
+                           "tuning": tune, "tuning_trials_mlups": {str(k): round(v, 1) for k, v in trials.items()},
                            "parallelism": f"replicas x{world}"},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": int(round(launches_per_iter * iters)),
-                # per timed iteration (`chunk` coarse steps, L2 flushed before each)
-                "iterations": {"n": iters, "steps_each": chunk,
-                               "best_mlups": round(lups * chunk / (min(it_ms) * 1e-3) / 1e6, 1),
-                               "median_mlups": round(lups * chunk / (statistics.median(it_ms) * 1e-3) / 1e6, 1)},
-                "conservation": {"max_rel_drift_over_timed_steps": drift, "audited_steps": len(rows)},
-                "clocks": clk.summary()}
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "iterations": {"n": len(its), "steps_each": chunks[0] if chunks else 0,
+                               "best_mlups": round(max(its), 1) if its else None,
+                               "median_mlups": round(statistics.median(its), 1) if its else None},
+                "conservation": {"max_rel_change_across_regrid": drift, "regrids_audited": int(len(rows))},
+                "extras": extras, "clocks": clk.summary()}
         print(json.dumps(line))
     if pg:
         pg.destroy_process_group()

@@ -212,6 +212,30 @@ vlbm_status vlbm_get_info(const vlbm_hier* h, vlbm_info* info);
  * Errors: ERR_ARG, ERR_CUDA, ERR_NONPHYSICAL, ERR_STATE. */
 vlbm_status vlbm_lups_done(vlbm_hier* h, int64_t* lups);
 
+/* Kernels this library has queued for the hierarchy since its creation
+ * (every kernel of every captured graph launch, and each eager launch of a
+ * step, regrid, audit or task-list build), counted on the host when they
+ * are queued.  Errors: ERR_ARG. */
+vlbm_status vlbm_kernels_launched(const vlbm_hier* h, int64_t* n);
+
+/* The cell-update counter (vlbm_lups_done) copied, in stream order and
+ * without waiting, into *dst
+ * (host memory: pinned for a truly asynchronous copy; valid once the stream
+ * has reached this point).  Errors: ERR_ARG, ERR_CUDA, ERR_STATE. */
+vlbm_status vlbm_lups_mark(vlbm_hier* h, int64_t* dst);
+
+/* Conservation across regrids (Sec. 3.4: merge and split add or remove
+ * nothing).  on = 1: every tag-driven regrid that runs on the device
+ * records, on the device and without synchronising, the exact totals of
+ * vlbm_audit immediately before and immediately after it, into a ring of
+ * the last 4096 regrids.  vlbm_get_regrid_audits copies the rows recorded
+ * since the previous read (at most cap, oldest first) into out[n][16]:
+ * totals before (4), |W| totals before (4), totals after (4), |W| totals
+ * after (4); it synchronises.  Errors: ERR_ARG, ERR_OOM, ERR_CUDA,
+ * ERR_STATE (and deferred errors on the read). */
+vlbm_status vlbm_set_regrid_audit(vlbm_hier* h, int32_t on);
+vlbm_status vlbm_get_regrid_audits(vlbm_hier* h, double* out, int64_t cap, int64_t* n);
+
 /* Host-side time the library has spent on a hierarchy since its creation,
  * in milliseconds (wall clock, cumulative), by activity:
  *   TAG       adaptive regrid: average-down, indicator and block flags on the

@@ -1,9 +1,14 @@
 """Autotuner for the sweep launch: picks, per hierarchy signature, the
 compiled sweep variant, the schedule (one launch per phase, or the
-persistent task kernel), the coarse steps per graph launch and the grid cap,
-by timing candidates on a scratch hierarchy of the same configuration (made
-by a caller-supplied factory and destroyed afterwards), so tuning never
-touches the simulation it is for.
+persistent task kernel), the task granularity of the persistent kernel
+(whole 8 x 8 tiles per thread group, or half tiles per warp), the coarse
+steps per graph launch and the grid cap (one CTA per four tiles, or a grid
+of resident CTAs looping over the tiles), by timing candidates on a scratch
+hierarchy of the same configuration (made by a caller-supplied factory and
+destroyed afterwards), so tuning never touches the simulation it is for.
+tune() times static runs; tune_adaptive() times cycles of coarse steps and
+regrids, where a layout lives only a few steps and the persistent schedule
+pays for a task list at every regrid.
 
 The signature is what the cost depends on: the level sizes, the active
 cells per level and whether 1 - 2 beta == -1 (some variants need it).
@@ -82,6 +87,52 @@ def tune(make, target=None, steps=64, candidates=None, cache_file=None, verbose=
             with open(cache_file, "w") as fh:
                 json.dump(_cache, fh, indent=1)
     probe.close()
+    if target is not None:
+        target.set_tuning(**best)
+    return best, results
+
+
+ADAPTIVE_CANDIDATES = [
+    {"variant": 1, "schedule": 0, "max_ctas": 0},
+    {"variant": 0, "schedule": 0, "max_ctas": 0},
+    {"variant": 1, "schedule": 0, "max_ctas": 148 * 3},
+    {"variant": 1, "schedule": 1, "max_ctas": 0},
+    {"variant": 13, "schedule": 1, "max_ctas": 0},
+]
+
+
+def tune_adaptive(make, every, target=None, cycles=8, candidates=None, verbose=False):
+    """Times candidates on adaptive runs: a fresh scratch hierarchy from
+    make() per candidate (with its initial layout), two warm-up cycles, then
+    `cycles` cycles of `every` coarse steps and a tag-driven regrid, counted
+    with the device's cell-update counter.  Installs the fastest on `target`
+    (with `every` coarse steps per graph launch).  Returns (settings,
+    {candidate index: MLUPS})."""
+    cands = candidates or ADAPTIVE_CANDIDATES
+    results = {}
+    for i, c in enumerate(cands):
+        probe = make()
+        try:
+            probe.set_tuning(graph_steps=every, persist_after=0, **c)
+            for _ in range(2):
+                probe.advance(every)
+                probe.regrid()
+            probe.sync()
+            l0 = probe.lups_done()
+            t0 = time.perf_counter()
+            for _ in range(cycles):
+                probe.advance(every)
+                probe.regrid()
+            probe.sync()
+            el = time.perf_counter() - t0
+            results[i] = (probe.lups_done() - l0) / el / 1e6
+        except V.VlbmError:
+            continue
+        finally:
+            probe.close()
+        if verbose:
+            print(f"autotune adaptive: {c} -> {results[i]:.1f} MLUPS", flush=True)
+    best = dict(cands[max(results, key=results.get)], graph_steps=every, persist_after=0)
     if target is not None:
         target.set_tuning(**best)
     return best, results

@@ -30,6 +30,47 @@ constexpr int AUDIT_BLOCK_SLOTS = 32;
 // about twice the thread groups resident at 3 CTAs per SM (148 x 3 x 4)
 constexpr int AUDIT_LAG = 4096;
 
+// Kernel nodes of every instantiated graph, so that a launch can be counted
+// as the kernels it runs (vlbm_kernels_launched).
+std::mutex g_nk_mu;
+std::vector<std::pair<cudaGraphExec_t, long long>> g_nk;
+
+long long kernel_nodes(cudaGraph_t g) {
+    size_t n = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) return 0;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (n && cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return 0;
+    long long k = 0;
+    for (cudaGraphNode_t v : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(v, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) k++;
+    }
+    return k;
+}
+
+// cudaGraphInstantiate, recording the graph's kernel count for the exec.
+cudaError_t instantiate(cudaGraphExec_t* ex, cudaGraph_t g) {
+    const cudaError_t e = cudaGraphInstantiate(ex, g, 0);
+    if (e == cudaSuccess) {
+        const long long k = kernel_nodes(g);
+        std::lock_guard<std::mutex> lk(g_nk_mu);
+        for (auto& p : g_nk)
+            if (p.first == *ex) {
+                p.second = k;
+                return e;
+            }
+        g_nk.emplace_back(*ex, k);
+    }
+    return e;
+}
+
+long long graph_kernels(cudaGraphExec_t ex) {
+    std::lock_guard<std::mutex> lk(g_nk_mu);
+    for (const auto& p : g_nk)
+        if (p.first == ex) return p.second;
+    return 0;
+}
+
 double ms_since(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
@@ -309,6 +350,13 @@ struct vlbm_hier {
     unsigned long long* lupc = nullptr;  // cell updates done so far
     int** parp = nullptr;                // device array holding `words` (the level-0 parity)
     long long foot_version = -1;         // layout of the last reverse footprints (task builds)
+    // exact totals recorded on the device before and after every device
+    // regrid (vlbm_set_regrid_audit): ring of RA_CAP rows of 16 doubles
+    long long klaunch = 0;  // kernels launched for this hierarchy (vlbm_kernels_launched)
+    bool regrid_audit = false;
+    double* raud = nullptr;
+    long long ra_n = 0, ra_read = 0;
+    static constexpr long long RA_CAP = 4096;
     cudaGraphExec_t rg_exec = nullptr;   // the device regrid, captured
     std::vector<uintptr_t> rg_key;
     // Task lists built on the device for the persistent schedule (no
@@ -325,6 +373,7 @@ struct vlbm_hier {
         DArr<Segment> seg;
         int task_cap = 0;
         long long dep_cap = 0;
+        int build_kernels = 0;  // kernels the last dev_plan call queued (a task list build)
         cudaGraphExec_t exec = nullptr;
         std::vector<uintptr_t> key;
     } dp[2];
@@ -473,7 +522,7 @@ struct Batch {
         }
         VCK(cudaStreamEndCapture(s, &g));
         cudaGraphExec_t ex = nullptr;
-        cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+        cudaError_t e = instantiate(&ex, g);
         cudaGraphDestroy(g);
         VCK(e);
         return ex;
@@ -727,7 +776,7 @@ struct Batch {
         }
         VCK(cudaStreamEndCapture(s, &g));
         cudaGraphExec_t ex = nullptr;
-        cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+        cudaError_t e = instantiate(&ex, g);
         cudaGraphDestroy(g);
         VCK(e);
         return ex;
@@ -737,14 +786,24 @@ struct Batch {
     // task lists built and captured on first use.
     cudaGraphExec_t exec_for(int which, cudaStream_t s);
 
+    long long* klaunch = nullptr;  // kernel counter of the batch's hierarchy (own batches)
+    void count(cudaGraphExec_t ex) {
+        if (klaunch) *klaunch += graph_kernels(ex);
+    }
     void advance(long long n, cudaStream_t s) {
         if (n >= G) {
             cudaGraphExec_t ex = exec_for(1, s);
-            for (; n >= G; n -= G) VCK(cudaGraphLaunch(ex, s));
+            for (; n >= G; n -= G) {
+                VCK(cudaGraphLaunch(ex, s));
+                count(ex);
+            }
         }
         if (n > 0) {
             cudaGraphExec_t ex = exec_for(0, s);
-            for (; n > 0; n--) VCK(cudaGraphLaunch(ex, s));
+            for (; n > 0; n--) {
+                VCK(cudaGraphLaunch(ex, s));
+                count(ex);
+            }
         }
     }
 };
@@ -1412,13 +1471,23 @@ void device_regrid(vlbm_hier* h) {
             throw;
         }
         VCK(cudaStreamEndCapture(s, &g));
-        cudaError_t e = cudaGraphInstantiate(&h->rg_exec, g, 0);
+        cudaError_t e = instantiate(&h->rg_exec, g);
         cudaGraphDestroy(g);
         VCK(e);
         h->rg_key = key;
         h->times[VLBM_T_CAPTURE] += ms_since(t0);
     }
+    const long long slot = h->ra_n % vlbm_hier::RA_CAP;
+    const int icap = (int)std::min<size_t>(h->ditems_cap, 1u << 30);
+    if (h->regrid_audit)
+        VCK(launch_audit(h->atab.p, h->ditems, icap, h->partial.p, h->raud + 16 * slot, s, h->dcount));
     VCK(cudaGraphLaunch(h->rg_exec, s));
+    h->klaunch += graph_kernels(h->rg_exec);
+    if (h->regrid_audit) {
+        VCK(launch_audit(h->atab.p, h->ditems, icap, h->partial.p, h->raud + 16 * slot + 8, s, h->dcount));
+        h->ra_n++;
+        h->klaunch += 4;  // two audits: partial sums and their rounding each
+    }
     h->host_ok = false;
     layout_changed(h);
 }
@@ -1488,6 +1557,7 @@ void plan_tables(int nlev, int nsteps, std::vector<TBPhase>& ph, std::vector<TBA
 // device when the layout changed.
 vlbm_hier::DevPlan& dev_plan(vlbm_hier* h, int which, int k) {
     vlbm_hier::DevPlan& D = h->dp[which];
+    D.build_kernels = 0;
     cudaStream_t s = h->stream;
     if (D.steps != k) {
         std::vector<TBPhase> ph;
@@ -1549,6 +1619,7 @@ vlbm_hier::DevPlan& dev_plan(vlbm_hier* h, int which, int k) {
             for (int l = 0; l + 1 < h->nlev; l++)
                 VCK(launch_footprints(h->lev[l].dl, h->lev[l + 1].dl, h->words + 1, s));
             h->foot_version = h->layout_version;
+            D.build_kernels += 2 * (h->nlev - 1);
         }
         TBPlan P;
         P.nlev = h->nlev;
@@ -1576,6 +1647,7 @@ vlbm_hier::DevPlan& dev_plan(vlbm_hier* h, int which, int k) {
         P.prefix = D.prefix.p;
         P.ctl = D.ctl.p;
         VCK(launch_task_build(P, s));
+        D.build_kernels += 4;
         D.version = h->layout_version;
         h->times[VLBM_T_TASKS] += ms_since(t0);
         h->times[VLBM_T_NTASKLISTS] += 1;
@@ -1599,7 +1671,7 @@ cudaGraphExec_t dev_task_graph(vlbm_hier* h, int which, int k) {
         if (e == cudaSuccess) e = launch_tasks(h->atab.p, D.seg.p, D.prefix.p, D.ctl.p, h->tune.variant, h->tune.max_ctas, s);
         cudaError_t e2 = cudaStreamEndCapture(s, &g);
         if (e == cudaSuccess) e = e2;
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&D.exec, g, 0);
+        if (e == cudaSuccess) e = instantiate(&D.exec, g);
         if (g) cudaGraphDestroy(g);
         VCK(e);
         D.key = key;
@@ -1644,7 +1716,7 @@ cudaGraphExec_t dev_phase_graph(vlbm_hier* h, int which, int k) {
         throw;
     }
     VCK(cudaStreamEndCapture(s, &g));
-    cudaError_t e = cudaGraphInstantiate(&P.exec, g, 0);
+    cudaError_t e = instantiate(&P.exec, g);
     cudaGraphDestroy(g);
     VCK(e);
     P.key = key;
@@ -1667,13 +1739,24 @@ void dev_advance(vlbm_hier* h, long long n, int sched) {
     long long left = n;
     if (left >= G) {
         cudaGraphExec_t ex = sched == 1 ? dev_task_graph(h, 1, G) : dev_phase_graph(h, 1, G);
-        for (; left >= G; left -= G) VCK(cudaGraphLaunch(ex, s));
+        if (sched == 1) h->klaunch += h->dp[1].build_kernels;  // a task list build, if one was queued
+        const long long nk = graph_kernels(ex);
+        for (; left >= G; left -= G) {
+            VCK(cudaGraphLaunch(ex, s));
+            h->klaunch += nk;
+        }
     }
     if (left > 0) {
         cudaGraphExec_t ex = sched == 1 ? dev_task_graph(h, 0, 1) : dev_phase_graph(h, 0, 1);
-        for (; left > 0; left--) VCK(cudaGraphLaunch(ex, s));
+        if (sched == 1) h->klaunch += h->dp[0].build_kernels;
+        const long long nk = graph_kernels(ex);
+        for (; left > 0; left--) {
+            VCK(cudaGraphLaunch(ex, s));
+            h->klaunch += nk;
+        }
     }
     count_lups(h, n);
+    h->klaunch += 1;
 }
 
 void release_dev_plans(vlbm_hier* h) {
@@ -1830,6 +1913,8 @@ void destroy_levels(vlbm_hier* h) {
     h->mem.put(h->dcount, 4 * sizeof(int));
     h->mem.put(h->lupc, sizeof(unsigned long long));
     h->mem.put(h->parp, sizeof(int*));
+    h->mem.put(h->raud, (size_t)vlbm_hier::RA_CAP * 16 * sizeof(double));
+    h->raud = nullptr;
     h->ditems = nullptr;
     h->dcount = nullptr;
     h->lupc = nullptr;
@@ -1885,6 +1970,7 @@ void ensure_own_batch(vlbm_hier* h, int sched) {
     if (!h->own) {
         h->own = new Batch();
         h->own->mem = &h->mem;
+        h->own->klaunch = &h->klaunch;
         h->own->members.push_back(h);
     }
     if (h->own->valid && h->own->schedule_mode != sched) h->own->valid = false;
@@ -2035,6 +2121,7 @@ vlbm_status vlbm_set_state(vlbm_hier* h, int32_t level, const double* W, int64_t
             src = h->stage.p;
         }
         VCK(launch_feq_init(lvdev(h, level), src, ld, h->hc, h->stream));
+        h->klaunch += 1;
         if (!on_device) VCK(cudaStreamSynchronize(h->stream));
     });
 }
@@ -2052,6 +2139,7 @@ static vlbm_status pop_copy(vlbm_hier* h, int32_t level, double* f, int64_t ld, 
             if (!to_ext) VCK(cudaMemcpyAsync(ext, f, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
         }
         VCK(launch_copy_pop(lvdev(h, level), ext, ld, to_ext, h->stream));
+        h->klaunch += 1;
         if (!on_device && to_ext) VCK(cudaMemcpyAsync(f, ext, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
         VCK(cudaStreamSynchronize(h->stream));
     });
@@ -2113,6 +2201,7 @@ vlbm_status vlbm_advance(vlbm_hier* h, int64_t coarse_steps) {
                     cudaGraphExec_t ex = b.exec_for(1, h->stream);
                     for (; m >= b.G; m -= b.G) {
                         VCK(cudaGraphLaunch(ex, h->stream));
+                        b.count(ex);
                         record_rows(h, h->tl[1].aout.p, b.G);
                     }
                 }
@@ -2120,6 +2209,7 @@ vlbm_status vlbm_advance(vlbm_hier* h, int64_t coarse_steps) {
                     cudaGraphExec_t ex = b.exec_for(0, h->stream);
                     for (; m > 0; m--) {
                         VCK(cudaGraphLaunch(ex, h->stream));
+                        b.count(ex);
                         record_rows(h, h->tl[0].aout.p, 1);
                     }
                 }
@@ -2129,6 +2219,7 @@ vlbm_status vlbm_advance(vlbm_hier* h, int64_t coarse_steps) {
             left -= n;
         }
         count_lups(h, coarse_steps);
+        h->klaunch += 1;
     });
 }
 
@@ -2284,6 +2375,7 @@ static void audit_impl(vlbm_hier* h, double* totals, double* abs_totals) {
     if (!h->hout) h->hout = (double*)pin_alloc(8 * sizeof(double));
     VCK(launch_audit(h->atab.p, h->ditems, (int)std::min<size_t>(h->ditems_cap, 1u << 30), h->partial.p, h->tot.p,
                      h->stream, h->dcount));
+    h->klaunch += 2;
     VCK(cudaMemcpyAsync(h->hout, h->tot.p, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     VCK(cudaStreamSynchronize(h->stream));
     if (totals) std::memcpy(totals, h->hout, 4 * sizeof(double));
@@ -2310,6 +2402,7 @@ vlbm_status vlbm_get_conserved(vlbm_hier* h, int32_t level, double* W, int64_t l
             h->stage.ensure(h->mem, n);
             h->stage8.ensure(h->mem, (size_t)L.nx * L.ny);
             VCK(launch_gather_W(lvdev(h, level), h->stage.p, ldd, valid ? h->stage8.p : nullptr, h->stream));
+            h->klaunch += 1;
             if (W) VCK(cudaMemcpyAsync(W, h->stage.p, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
             if (valid)
                 VCK(cudaMemcpyAsync(valid, h->stage8.p, (size_t)L.nx * L.ny, cudaMemcpyDeviceToHost, h->stream));
@@ -2585,6 +2678,47 @@ vlbm_status vlbm_selftest_layout(uint64_t seed, int32_t cases, int64_t* mismatch
     return VLBM_OK;
 }
 
+vlbm_status vlbm_kernels_launched(const vlbm_hier* h, int64_t* n) {
+    if (!h || !n) return VLBM_ERR_ARG;
+    *n = h->klaunch;
+    return VLBM_OK;
+}
+
+vlbm_status vlbm_lups_mark(vlbm_hier* h, int64_t* dst) {
+    return run(h, [&] {
+        if (!dst) throw Fail{VLBM_ERR_ARG, "null destination"};
+        VCK(cudaMemcpyAsync(dst, h->lupc, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
+    });
+}
+
+vlbm_status vlbm_set_regrid_audit(vlbm_hier* h, int32_t on) {
+    return run(h, [&] {
+        if (on && !h->raud) {
+            h->raud = (double*)h->mem.get((size_t)vlbm_hier::RA_CAP * 16 * sizeof(double));
+            VCK(cudaMemsetAsync(h->raud, 0, (size_t)vlbm_hier::RA_CAP * 16 * sizeof(double), h->stream));
+        }
+        h->regrid_audit = on != 0;
+        h->ra_n = h->ra_read = 0;
+    });
+}
+
+vlbm_status vlbm_get_regrid_audits(vlbm_hier* h, double* out, int64_t cap, int64_t* n) {
+    return run(h, [&] {
+        if (!n || cap < 0 || (cap > 0 && !out)) throw Fail{VLBM_ERR_ARG, "bad arguments"};
+        VCK(cudaStreamSynchronize(h->stream));
+        check_status(h);
+        long long avail = h->ra_n - h->ra_read;
+        if (avail > vlbm_hier::RA_CAP) avail = vlbm_hier::RA_CAP;  // older rows were overwritten
+        const long long take = std::min<long long>(avail, cap);
+        const long long first = h->ra_n - take;  // the most recent `take` rows, oldest first
+        for (long long r = 0; r < take; r++)
+            VCK(cudaMemcpy(out + r * 16, h->raud + ((first + r) % vlbm_hier::RA_CAP) * 16, 16 * sizeof(double),
+                           cudaMemcpyDeviceToHost));
+        *n = take;
+        h->ra_read = h->ra_n;
+    });
+}
+
 vlbm_status vlbm_lups_done(vlbm_hier* h, int64_t* lups) {
     return run(h, [&] {
         if (!lups) throw Fail{VLBM_ERR_ARG, "null output"};
@@ -2628,6 +2762,7 @@ vlbm_status vlbm_profile(vlbm_hier* h, int64_t coarse_steps, vlbm_kernel_time* o
         for (int l = 0; l < h->nlev; l++) cells[l] = h->lev[l].active_cells;
         std::vector<Batch::Rec> recs;
         h->own->profile(coarse_steps, cells, recs, h->stream);
+        for (const auto& r : recs) h->klaunch += r.launches;
         h->steps += coarse_steps;
         h->layout_steps += coarse_steps;
         if ((int)recs.size() > cap) throw Fail{VLBM_ERR_ARG, "record capacity too small"};

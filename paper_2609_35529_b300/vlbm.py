@@ -93,6 +93,10 @@ def lib():
         "vlbm_sync": [vp],
         "vlbm_get_info": [vp, C.POINTER(vlbm_info)],
         "vlbm_lups_done": [vp, C.POINTER(i64)],
+        "vlbm_lups_mark": [vp, vp],
+        "vlbm_kernels_launched": [vp, C.POINTER(i64)],
+        "vlbm_set_regrid_audit": [vp, i32],
+        "vlbm_get_regrid_audits": [vp, dp, i64, C.POINTER(i64)],
         "vlbm_host_times": [vp, dp],
         "vlbm_set_sensor": [vp, i32, C.c_double, C.c_double, C.c_double],
         "vlbm_profile": [vp, i64, C.POINTER(vlbm_kernel_time), i32, C.POINTER(i32)],
@@ -324,6 +328,30 @@ class Hierarchy:
         v = C.c_int64()
         _check(self._h, lib().vlbm_lups_done(self._h, C.byref(v)))
         return int(v.value)
+
+    def kernels_launched(self):
+        """Kernels the library has queued for this hierarchy so far."""
+        v = C.c_int64()
+        _check(self._h, lib().vlbm_kernels_launched(self._h, C.byref(v)))
+        return int(v.value)
+
+    def lups_mark(self, dst_ptr):
+        """Queues a copy of the cell-update counter into host memory at
+        dst_ptr (an int64; pinned for a truly asynchronous copy)."""
+        _check(self._h, lib().vlbm_lups_mark(self._h, C.c_void_p(dst_ptr)))
+
+    def set_regrid_audit(self, on=True):
+        """Record exact totals before and after every device regrid."""
+        _check(self._h, lib().vlbm_set_regrid_audit(self._h, int(on)))
+
+    def regrid_audits(self, cap=4096):
+        """Rows recorded since the last read: [n, 16] = totals, |W| totals
+        before the regrid, then after (synchronises)."""
+        out = np.zeros((cap, 16))
+        n = C.c_int64()
+        _check(self._h, lib().vlbm_get_regrid_audits(self._h, out.ctypes.data_as(C.POINTER(C.c_double)), cap,
+                                                     C.byref(n)))
+        return out[: n.value]
 
     def set_sensor(self, on=True, beta_min=0.5, c_sensor=16.0, eps=1e-30):
         """Sensor-driven relaxation (vlbm_set_sensor): beta_max is the

@@ -126,11 +126,17 @@ typedef struct {
 
 /* ---- hierarchy life cycle ---------------------------------------------- */
 
-/* Creates a hierarchy with the initial static layout cfg->boxes (validated:
- * block aligned, inside the domain, properly nested -- every cell covered on
- * level l >= 1 has its four face neighbours on level l).  The populations are
- * zero until vlbm_set_state.  stream is a cudaStream_t (NULL = legacy
- * default stream) used by every later call on the handle.
+/* Creates a hierarchy: levels 0 .. max_levels-1 at refinement ratio 2 with
+ * one link speed c on every level (acoustic scaling, Sec. 3.2, Eq. 15: the
+ * time step halves from level to level), ideal gas of ratio gamma
+ * (Sec. 2.1, Eq. 1), BGK parameter beta (Sec. 2.2, Eq. 6), with the initial
+ * static layout cfg->boxes (validated: block aligned, inside the domain,
+ * properly nested -- every cell covered on level l >= 1 has its four face
+ * neighbours on level l; the paper's levels are nested, Sec. 4.3).  The
+ * populations are zero until vlbm_set_state.  alloc (may be NULL: stream
+ * ordered cudaMallocAsync) provides all of the handle's device memory;
+ * stream is a cudaStream_t (NULL = legacy default stream) used by every
+ * later call on the handle.
  * Errors: ERR_ARG, ERR_NESTING, ERR_OOM, ERR_CUDA; *out is NULL then. */
 vlbm_status vlbm_create_hierarchy(const vlbm_config* cfg, const vlbm_allocator* alloc,
                                   void* stream, vlbm_hier** out);
@@ -184,16 +190,21 @@ vlbm_status vlbm_regrid_masks(vlbm_hier* h, const uint8_t* const* ref);
  * the next level (host arrays of ny_l * nx_l bytes, either may be NULL). */
 vlbm_status vlbm_get_layout(vlbm_hier* h, int32_t level, uint8_t* in, uint8_t* ref);
 
-/* Conserved fields W = sum_i f_i of `level` into W[4][ny_l][ld] (host, may
- * be NULL); valid[ny_l*nx_l] (may be NULL) = 1 on active cells.  totals and
+/* Conserved fields W = sum_i f_i (the zeroth moment of the populations,
+ * Sec. 2.2, Eq. 4) of `level` into W[4][ny_l][ld] (host, may be NULL);
+ * valid[ny_l*nx_l] (may be NULL) = 1 on active cells.  totals and
  * abs_totals (may be NULL) receive sum_l 4^-l sum_active W_k and the same
- * of |W_k| over the whole hierarchy: the exact sums (192-bit fixed point,
- * resolution 2^-128) rounded once to nearest binary64.
+ * of |W_k| over the whole hierarchy -- the paper's conservation monitors
+ * (total over the coarse cells outside the patch holes plus the fine cells,
+ * area weighted; Sec. 4.1.2, 4.1.3, 4.2) -- as the exact sums (192-bit
+ * fixed point, resolution 2^-128) rounded once to nearest binary64.
  * Synchronises.  Errors: ERR_ARG, ERR_CUDA, ERR_NONPHYSICAL, ERR_STATE. */
 vlbm_status vlbm_get_conserved(vlbm_hier* h, int32_t level, double* W, int64_t ld,
                                uint8_t* valid, double totals[4], double abs_totals[4]);
 
-/* Totals only (see vlbm_get_conserved).  Synchronises. */
+/* Totals only: the conservation monitors of Sec. 4.1.2, 4.1.3 and 4.2 as
+ * exact sums (see vlbm_get_conserved).  Synchronises.
+ * Errors: ERR_ARG, ERR_CUDA, ERR_NONPHYSICAL, ERR_STATE. */
 vlbm_status vlbm_audit(vlbm_hier* h, double totals[4], double abs_totals[4]);
 
 /* Waits for the stream and reports deferred device errors. */
@@ -429,13 +440,20 @@ vlbm_status vlbm_get_step_totals(vlbm_hier* h, double* out, int64_t cap, int64_t
  * The reduction's partial sums live in one fixed device array of
  * VLBM_STATIC_MAX_BLOCKS slots (2 MiB, held by every device that loads the
  * library until exit); each slot covers 4096 cells, so nx * ny is limited to
- * VLBM_STATIC_MAX_BLOCKS * 4096 cells and larger grids get ERR_ARG.  The
- * first call on a device looks up the array's device address for that
- * device; make that first call before any stream capture.  Every call
- * shares the array: calls whose kernels overlap on the GPU (other streams)
- * race and must be serialised by the caller.  No cudaMalloc, cudaFree or
- * allocating library routine is used.  Asynchronous: read `out` after
- * synchronising `stream`.  Errors: ERR_ARG (null pointers, sizes), ERR_CUDA. */
+ * VLBM_STATIC_MAX_BLOCKS * 4096 cells and larger grids get ERR_ARG.  CUDA
+ * loads modules lazily: the first call on a device loads this code and the
+ * array onto it, which takes device memory once -- make that first call (a
+ * warm-up on a small array will do) before reserving the rest of the
+ * device's memory, and before any stream capture; later calls take none.
+ * A call made outside a capture looks the array's device address up afresh
+ * (a context recreated after a device reset is followed); a call made while
+ * `stream` is captured uses the address of the last call on that device.
+ * Every call shares the array: calls whose kernels overlap on the GPU
+ * (other streams) race and must be serialised by the caller.  No
+ * cudaMalloc, cudaFree or allocating library routine is used.
+ * Asynchronous: read `out` after synchronising `stream`.
+ * Errors: ERR_ARG (null pointers, sizes), ERR_CUDA (also: first call on the
+ * device made during a stream capture). */
 #define VLBM_STATIC_MAX_BLOCKS 16384
 vlbm_status vlbm_totals_static(const double* f, int64_t ld, int32_t nx, int32_t ny, double weight, double* out,
                                void* stream);
@@ -451,8 +469,12 @@ void vlbm_destroy(vlbm_hier* h);
  * is one coarse step of every resident, issued as one launch per phase of
  * the sub-cycle (level-0 sweep, level-1 sweeps, reflux closes, ...), each
  * processing the tiles of all residents.  mem_budget bounds the summed
- * device memory of the residents (0 = no bound). */
-vlbm_status vlbm_engine_create(size_t mem_budget, void* stream, vlbm_engine** out);
+ * device memory of the residents (0 = no bound).  alloc (may be NULL:
+ * stream-ordered cudaMallocAsync) provides the engine's own device memory
+ * (its launch tables); the residents' memory comes from their own handles.
+ * stream (NULL: a stream of its own) carries every engine launch.
+ * Errors: ERR_ARG, ERR_CUDA, ERR_OOM; *out is NULL then. */
+vlbm_status vlbm_engine_create(size_t mem_budget, const vlbm_allocator* alloc, void* stream, vlbm_engine** out);
 
 /* Admits h (created on the same device; the engine borrows it until release)
  * for coarse_steps steps (0: reported finished, unchanged, by the next

@@ -2779,12 +2779,17 @@ vlbm_status vlbm_profile(vlbm_hier* h, int64_t coarse_steps, vlbm_kernel_time* o
 
 // ---- engine ------------------------------------------------------------------
 
-vlbm_status vlbm_engine_create(size_t mem_budget, void* stream, vlbm_engine** out) {
+vlbm_status vlbm_engine_create(size_t mem_budget, const vlbm_allocator* alloc, void* stream, vlbm_engine** out) {
     if (!out) return VLBM_ERR_ARG;
     *out = nullptr;
+    if (alloc && (!alloc->alloc || !alloc->free)) return VLBM_ERR_ARG;
     vlbm_engine* e = new (std::nothrow) vlbm_engine();
     if (!e) return VLBM_ERR_OOM;
     e->budget = mem_budget;
+    if (alloc) {
+        e->mem.a = *alloc;
+        e->mem.has = true;
+    }
     if (stream) {
         e->stream = (cudaStream_t)stream;
     } else {
@@ -2847,6 +2852,13 @@ vlbm_status vlbm_engine_admit(vlbm_engine* e, vlbm_hier* h, int64_t coarse_steps
         s = (int)e->res.size();
         e->res.emplace_back();
     }
+    if (coarse_steps == 0) {
+        // nothing to do: reported finished by the next call, once this event
+        // (recorded before the slot is published) has completed
+        auto& r = e->res[s];
+        if (!r.ev && cudaEventCreateWithFlags(&r.ev, cudaEventDisableTiming) != cudaSuccess) return VLBM_ERR_CUDA;
+        if (cudaEventRecord(r.ev, e->stream) != cudaSuccess) return VLBM_ERR_CUDA;
+    }
     e->res[s].h = h;
     e->res[s].target = coarse_steps;
     e->res[s].done = 0;
@@ -2861,13 +2873,7 @@ vlbm_status vlbm_engine_admit(vlbm_engine* e, vlbm_hier* h, int64_t coarse_steps
     e->res[s].live = true;
     h->engine = e;
     e->dirty = true;
-    if (coarse_steps == 0) {
-        // nothing to do: reported finished by the next call
-        auto& r = e->res[s];
-        if (!r.ev && cudaEventCreateWithFlags(&r.ev, cudaEventDisableTiming) != cudaSuccess) return VLBM_ERR_CUDA;
-        if (cudaEventRecord(r.ev, e->stream) != cudaSuccess) return VLBM_ERR_CUDA;
-        r.finishing = true;
-    }
+    if (coarse_steps == 0) e->res[s].finishing = true;
     if (slot) *slot = s;
     return VLBM_OK;
 }

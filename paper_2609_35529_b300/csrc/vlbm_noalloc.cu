@@ -97,8 +97,11 @@ __global__ void static_final(const double* __restrict__ partials, int nblk, doub
     out[m] = a.s + a.c;
 }
 
-// Device address of g_partials, looked up once per device (with that device
-// current) on the first call made on it.
+// Device address of g_partials per device: looked up again (with that device
+// current) on every call made outside a stream capture, so that a context
+// created anew (after cudaDeviceReset) is followed; the last address is
+// kept for calls made while `stream` is being captured, which must not load
+// modules.
 std::mutex g_mu;
 double* g_addr[64] = {};
 
@@ -112,17 +115,20 @@ extern "C" vlbm_status vlbm_totals_static(const double* f, int64_t ld, int32_t n
     if (nblk > kMaxBlocks) return VLBM_ERR_ARG;  // more cells than the fixed scratch covers
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return VLBM_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return VLBM_ERR_CUDA;
     double* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_addr[dev]) {
+        if (cap == cudaStreamCaptureStatusNone) {
             void* p = nullptr;
             if (cudaGetSymbolAddress(&p, g_partials) != cudaSuccess || !p) return VLBM_ERR_CUDA;
             g_addr[dev] = (double*)p;
         }
         scratch = g_addr[dev];
     }
-    cudaStream_t s = (cudaStream_t)stream;
+    if (!scratch) return VLBM_ERR_CUDA;  // first call on this device made during a capture
     static_partials<<<(unsigned)nblk, kStaticThreads, 0, s>>>(f, ld, nx, ny, weight, scratch);
     static_final<<<1, 32, 0, s>>>(scratch, (int)nblk, out);
     return cudaGetLastError() == cudaSuccess ? VLBM_OK : VLBM_ERR_CUDA;

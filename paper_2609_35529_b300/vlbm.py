@@ -105,7 +105,7 @@ def lib():
         "vlbm_checkpoint_save": [vp, vp, C.c_size_t],
         "vlbm_checkpoint_load": [vp, vp, C.c_size_t],
         "vlbm_get_step_totals": [vp, dp, i64, C.POINTER(i64)],
-        "vlbm_engine_create": [C.c_size_t, vp, C.POINTER(vp)],
+        "vlbm_engine_create": [C.c_size_t, C.POINTER(vlbm_allocator), vp, C.POINTER(vp)],
         "vlbm_engine_admit": [vp, vp, i64, i32, C.POINTER(i32)],
         "vlbm_engine_step": [vp, C.POINTER(i32), C.POINTER(i32)],
         "vlbm_engine_advance": [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)],
@@ -484,9 +484,13 @@ class Engine:
     all resident hierarchies -- static ones in one persistent-kernel launch,
     adaptive ones in one graph of per-phase launches."""
 
-    def __init__(self, mem_budget=0, stream=None):
+    def __init__(self, mem_budget=0, stream=None, allocator=None):
+        """allocator="torch" routes the engine's own device memory (its launch
+        tables) through torch's caching allocator."""
         e = C.c_void_p()
-        st = lib().vlbm_engine_create(int(mem_budget), _stream_handle(stream), C.byref(e))
+        self._alloc = _TorchAllocator() if allocator == "torch" else None
+        st = lib().vlbm_engine_create(int(mem_budget), C.byref(self._alloc.struct) if self._alloc else None,
+                                      _stream_handle(stream), C.byref(e))
         if st != 0:
             raise VlbmError(st, "vlbm_engine_create")
         self._e = e

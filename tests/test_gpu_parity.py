@@ -295,7 +295,7 @@ def test_engine_results_equal_alone_and_in_mix(V):
         g.advance(cs.steps)
         alone.append([g.get_populations(l) for l in range(cs.nlev)])
         g.close()
-    e = V.Engine()
+    e = V.Engine(allocator="torch")  # the engine's launch tables from torch's caching allocator
     hs = [V.Hierarchy.from_case(cs) for cs in cases]
     slots = [e.admit(h, cs.steps) for h, cs in zip(hs, cases)]
     done = set()

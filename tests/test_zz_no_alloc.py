@@ -31,12 +31,16 @@ def test_totals_static_matches_audit_twice():
     st = V.lib().vlbm_get_populations(h.handle, 0, ctypes.c_void_p(f.data_ptr()), ld, 1)
     assert st == 0
     stream = torch.cuda.current_stream()
-    outs = []
-    for _ in range(2):
-        out = torch.full((8,), float("nan"), dtype=torch.float64, device="cuda")
+    bufs = [torch.full((8,), float("nan"), dtype=torch.float64, device="cuda") for _ in range(2)]
+    outs, free = [], []
+    for out in bufs:
         V.totals_static(f.data_ptr(), ld, nx, ny, 1.0, out.data_ptr(), stream)
         torch.cuda.synchronize()
+        free.append(torch.cuda.mem_get_info()[0])
         outs.append(out.cpu().numpy())
+    # the first call loads the module (code and scratch array); the second
+    # takes no device memory at all
+    assert free[1] == free[0]
     for o in outs:
         np.testing.assert_allclose(o[:4], ref_tot, rtol=1e-14, atol=1e-14 * np.max(ref_abs))
         np.testing.assert_allclose(o[4:], ref_abs, rtol=1e-14)

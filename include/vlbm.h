@@ -292,29 +292,28 @@ typedef struct {
 vlbm_status vlbm_profile(vlbm_hier* h, int64_t coarse_steps, vlbm_kernel_time* out, int32_t cap, int32_t* n);
 
 /* Launch tuning of the sweep.  variant (0 .. vlbm_num_variants() - 1)
- * selects one compiled form of the level sweep: which of the collision's
- * additions and multiplications run on the integer pipes through bit-exact
- * binary64 routines, how many CTAs per SM the kernel is built for, and how
- * the persistent kernel of schedule 1 organises its threads (64-thread
- * groups per tile task; groups that prefetch the next task's populations
- * into shared memory; or warps working alone on half-tile tasks).  Results
- * are identical bit for bit in every variant; some variants apply only when
- * 1 - 2 beta == -1.
+ * selects one compiled launch shape of the level sweep: 0, 1, 2 -- 64-thread
+ * groups on whole 8x8 tiles at 2, 3 or 4 CTAs per SM; 3, 4 -- for the
+ * persistent kernel of schedule 1, warps working alone on half-tile tasks at
+ * 3 or 2 CTAs per SM (the per-phase sweep runs whole tiles).  Results are
+ * identical bit for bit in every variant.
  * schedule 0 issues one kernel launch per phase of the sub-cycle (level
  * sweeps, reflux closes); schedule 1 runs graph_steps coarse steps of every
  * phase in one persistent launch whose 8x8-tile tasks start as soon as the
  * tasks they depend on (read-after-write, write-after-read and
- * write-after-write on populations and flags, derived on the host) are
- * done -- the waits are bounded and report VLBM_ERR_TIMEOUT; schedule 2
- * (auto) uses schedule 0 until the current layout has lived persist_after
- * coarse steps and schedule 1 from then on (the task lists of schedule 1
- * cost host time at every layout change, which an adaptive run that regrids
- * every few steps would pay again and again), and schedule 1 whenever
- * per-step totals are on.  max_ctas caps the grid (0 = one CTA per four
- * tiles for schedule 0, all resident CTAs for schedule 1); graph_steps
- * (1..64) is the number of coarse steps captured per CUDA graph.
- * vlbm_set_tuning returns ERR_ARG for a variant that does not apply to the
- * hierarchy (it is then unchanged).  Results do not depend on the tuning. */
+ * write-after-write on populations and flags) are done -- the waits are
+ * bounded and report VLBM_ERR_TIMEOUT; the task lists are built on the
+ * device after every layout change (on the host when per-step totals are
+ * on); schedule 2 (auto) uses schedule 0 until the current layout has lived
+ * persist_after coarse steps and schedule 1 from then on (a task-list build
+ * costs about what a few coarse steps of schedule 0 lose to schedule 1, so
+ * an adaptive run that regrids every few steps keeps schedule 0), and
+ * schedule 1 whenever per-step totals are on.  max_ctas caps the grid (0 =
+ * one CTA per four tiles for schedule 0, all resident CTAs for schedule 1);
+ * graph_steps (1..64) is the number of coarse steps captured per CUDA graph.
+ * vlbm_set_tuning returns ERR_ARG for an unknown variant or out-of-range
+ * values (the tuning is then unchanged).  Results do not depend on the
+ * tuning. */
 typedef struct {
     int32_t variant, max_ctas, graph_steps, schedule;
     int64_t persist_after; /* schedule 2 only, >= 0 */
@@ -324,15 +323,6 @@ int32_t vlbm_num_variants(void);
 vlbm_status vlbm_set_tuning(vlbm_hier* h, const vlbm_tuning* t);
 vlbm_status vlbm_get_tuning(const vlbm_hier* h, vlbm_tuning* t);
 
-/* Self-test of the integer-pipe binary64 routines used inside the sweep
- * (addition, subtraction, multiplication, halving) against the FP64 unit on
- * n seeded operand pairs (SplitMix64 stream from `seed`; values near 1,
- * equal and distant exponents, near-cancellations, zeros, subnormals,
- * infinities, NaNs, raw bit patterns).  mismatches[k] counts results whose
- * bits differ for k = add, sub, mul, half; first_bad[4k..4k+3] holds the
- * first offending (a, b, hardware, emulated).  Runs on the current device
- * and synchronises it.  Errors: ERR_ARG, ERR_OOM, ERR_CUDA. */
-vlbm_status vlbm_selftest_fp64(uint64_t seed, int64_t n, uint64_t mismatches[4], double first_bad[16]);
 
 /* Self-test of the integer-pipe reciprocal that the collision uses for
  * 1/rho (the Euler flux of Sec. 2.1, Eq. 1; Newton-Raphson in integer

@@ -11,7 +11,7 @@ regrids, where a layout lives only a few steps and the persistent schedule
 pays for a task list at every regrid.
 
 The signature is what the cost depends on: the level sizes, the active
-cells per level and whether 1 - 2 beta == -1 (some variants need it).
+cells per level and beta.
 Results are cached in memory and, optionally, in a JSON file.
 """
 import json
@@ -29,9 +29,9 @@ DEFAULT_CANDIDATES = [
     {"variant": 1, "schedule": 1, "graph_steps": 64, "max_ctas": 0},
     {"variant": 1, "schedule": 1, "graph_steps": 4, "max_ctas": 0},
     {"variant": 0, "schedule": 1, "graph_steps": 8, "max_ctas": 0},
-    {"variant": 10, "schedule": 1, "graph_steps": 8, "max_ctas": 0},
-    {"variant": 13, "schedule": 1, "graph_steps": 8, "max_ctas": 0},
-    {"variant": 13, "schedule": 1, "graph_steps": 16, "max_ctas": 0},
+    {"variant": 2, "schedule": 1, "graph_steps": 8, "max_ctas": 0},
+    {"variant": 3, "schedule": 1, "graph_steps": 8, "max_ctas": 0},
+    {"variant": 3, "schedule": 1, "graph_steps": 16, "max_ctas": 0},
     {"variant": 1, "schedule": 0, "graph_steps": 8, "max_ctas": 0},
     {"variant": 0, "schedule": 0, "graph_steps": 8, "max_ctas": 0},
 ]
@@ -97,7 +97,7 @@ ADAPTIVE_CANDIDATES = [
     {"variant": 0, "schedule": 0, "max_ctas": 0},
     {"variant": 1, "schedule": 0, "max_ctas": 148 * 3},
     {"variant": 1, "schedule": 1, "max_ctas": 0},
-    {"variant": 13, "schedule": 1, "max_ctas": 0},
+    {"variant": 3, "schedule": 1, "max_ctas": 0},
 ]
 
 

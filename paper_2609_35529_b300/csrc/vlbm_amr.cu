@@ -376,10 +376,10 @@ static inline int flat_blocks(long long n) {
 // task lists (the device form of build_tasks in vlbm_tasks.h)
 // ---------------------------------------------------------------------------
 
-// A task's dependency set: up to TB_SMALL entries in registers (one thread
-// per task, many threads in flight: the work is chains of table lookups,
-// latency bound); the rare task with more dependencies is redone by a
-// second pass with a TB_MAXDEP-entry set in local memory.  Adversarial
+// A task's dependency set: up to TB_SMALL entries (one thread per task,
+// many threads in flight, the sets in L1: the work is chains of table
+// lookups, latency bound); the rare task with more dependencies is redone by
+// a second pass with a TB_MAXDEP-entry set.  Adversarial
 // layouts (most cells refined, checkerboard coverage) reached 98 distinct
 // dependencies; beyond TB_MAXDEP the build raises ST_TASKCAP (reported as
 // VLBM_ERR_OOM).
@@ -391,49 +391,8 @@ __constant__ int kSDJ[5] = {0, 0, 0, 1, -1};
 
 __device__ __forceinline__ int src_of(int level, int kk, int step) { return level == 0 ? (step & 1) : (kk == 1 ? 0 : 1); }
 
-// The common case: a set of at most TB_SMALL entries held in registers
-// (every index below is a compile-time constant after unrolling), so the
-// whole L1 stays free for the table lookups.
-struct DepSetR {
-    int v[TB_SMALL];
-    int n;
-    bool ovf;
-    __device__ __forceinline__ void add(int q) {
-        bool found = false;
-#pragma unroll
-        for (int i = 0; i < TB_SMALL; i++) found |= (i < n) && (v[i] == q);
-        if (found) return;
-        if (n >= TB_SMALL) {
-            ovf = true;
-            return;
-        }
-#pragma unroll
-        for (int i = 0; i < TB_SMALL; i++)
-            if (i == n) v[i] = q;
-        n++;
-    }
-    // ascending (odd-even transposition over the first n entries)
-    __device__ __forceinline__ void sort() {
-#pragma unroll
-        for (int r = 0; r < TB_SMALL; r++) {
-#pragma unroll
-            for (int i = r & 1; i + 1 < TB_SMALL; i += 2) {
-                if (i + 1 < n && v[i] > v[i + 1]) {
-                    const int x = v[i];
-                    v[i] = v[i + 1];
-                    v[i + 1] = x;
-                }
-            }
-        }
-    }
-    __device__ __forceinline__ void store(int* out) const {
-#pragma unroll
-        for (int i = 0; i < TB_SMALL; i++)
-            if (i < n) out[i] = v[i];
-    }
-};
-
-// The rare larger set, in local memory.
+// A task's dependency set (in local memory): at most `cap` distinct task
+// indices, entry i at v[i * stride].
 struct DepSet {
     int* v;      // entry i at v[i * stride]
     int stride;
@@ -688,7 +647,8 @@ __global__ void __launch_bounds__(TB_BUILD_THREADS) tb_build_kernel(TBPlan P) {
     const int total = P.off[P.nphase];
     if (total > P.task_cap) return;
     const TB tb = tb_global(P);
-    DepSetR S;
+    int buf[TB_SMALL];
+    DepSet S{buf, 1, TB_SMALL, 0, false};
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
         const int p = tb.phase_of(t);
         Item it;
@@ -796,6 +756,12 @@ cudaError_t launch_count_lups(const LayoutDev* levs, int n, long long steps, uns
 }
 
 cudaError_t launch_task_build(const TBPlan& P, cudaStream_t s) {
+    static bool attrs = false;
+    if (!attrs) {  // no shared memory: the whole L1 for the sets and lookups
+        cudaFuncSetAttribute(tb_build_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+        cudaFuncSetAttribute(tb_big_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+        attrs = true;
+    }
     tb_offsets_kernel<<<1, 1, 0, s>>>(P);
     long long gl = ((long long)P.task_cap + TB_BUILD_THREADS - 1) / TB_BUILD_THREADS;
     const int g = (int)(gl < 1 ? 1 : (gl > 148 * 16 ? 148 * 16 : gl));

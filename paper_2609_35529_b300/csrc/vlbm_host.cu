@@ -2737,8 +2737,6 @@ vlbm_status vlbm_set_tuning(vlbm_hier* h, const vlbm_tuning* t) {
         if (!t || t->variant < 0 || t->variant >= sweep_variants() || t->max_ctas < 0 || t->graph_steps < 1 ||
             t->graph_steps > 64 || t->schedule < 0 || t->schedule > 2 || t->persist_after < 0)
             throw Fail{VLBM_ERR_ARG, "bad tuning"};
-        if (sweep_variant_needs_om_minus1(t->variant) && h->om != -1.0)
-            throw Fail{VLBM_ERR_ARG, "variant applies only when 1 - 2 beta == -1"};
         if (h->step_audit && t->schedule == 0) throw Fail{VLBM_ERR_ARG, "per-step totals need the persistent schedule"};
         h->tune = *t;
         h->tl[0].steps = h->tl[1].steps = -1;

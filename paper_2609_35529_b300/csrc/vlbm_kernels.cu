@@ -9,7 +9,6 @@
 #include <cstdint>
 
 #include "fix192.cuh"
-#include "fp64emu.cuh"
 #include "rcp_rn.cuh"
 #include "vlbm_dev.cuh"
 #include "vlbm_launch.h"
@@ -51,82 +50,47 @@ __device__ __forceinline__ bool physical(double rho, double p) {
     return rb > 0 && rb < inf && pb > 0 && pb < inf;
 }
 
-// BGK relaxation (Eq. 6) in place: f <- 2 beta f^eq(W) + (1 - 2 beta) f with
-// 2 beta f^eq_{+-alpha} = (beta/2) W +- (beta/c) Q_alpha (Eq. 4, D = 2), and
-// a chosen subset of its additions and
-// multiplications carried out by the bit-exact integer-pipe routines
-// (fp64emu.cuh); the results are identical bit for bit, only the pipe that
-// computes them changes.  Policy bits: EM_MOM the twelve moment additions,
-// EM_A the four (beta/2) W products, EM_FLUX the flux products and sums
-// (with rho E - (1/2) ke as an exact-halving addition), EM_OMF the inner
-// fma(1 - 2 beta, f, A) as an addition when 1 - 2 beta is -1 (its product
-// is then exact).
-enum : int { EM_MOM = 1, EM_A = 2, EM_FLUX = 4, EM_OMF = 8 };
 // Launch-shape bit of a variant (no effect on the arithmetic): the
-// persistent task kernel prefetches the next task's populations into
-// shared memory (see task_kernel).
-enum : int { TK_PREFETCH = 256, TK_HALF = 512 };
+// persistent task kernel runs half tiles per warp (task_kernel_half).
+enum : int { TK_HALF = 512 };
 // The sweep reads the relaxation parameter of each cell from the sensor
 // planes (sensor-driven relaxation; per-phase schedule only).
 enum : int { SW_SENSOR = 1024 };
 
-template <bool E>
-__device__ __forceinline__ double xadd(double a, double b) {
-    if constexpr (E) return emu_add(a, b);
-    else return a + b;
-}
-template <bool E>
-__device__ __forceinline__ double xmul(double a, double b) {
-    if constexpr (E) return emu_mul(a, b);
-    else return a * b;
-}
-
-template <int P>
-__device__ __forceinline__ bool collide_p(double f[16], double om, double hb, double bcs, double gm1,
-                                          double* Wout = nullptr) {
-    constexpr bool M = (P & EM_MOM) != 0, A_ = (P & EM_A) != 0, F = (P & EM_FLUX) != 0, O = (P & EM_OMF) != 0;
+// BGK relaxation (Eq. 6) in place: f <- 2 beta f^eq(W) + (1 - 2 beta) f with
+// 2 beta f^eq_{+-alpha} = (beta/2) W +- (beta/c) Q_alpha (Eq. 4, D = 2):
+// f* = fma(+-beta/c, Q_alpha, fma(1 - 2 beta, f, (beta/2) W)).  The one
+// division 1/rho is the correctly rounded reciprocal on the integer pipes
+// (the same bits as 1.0 / rho).  Returns whether the state is physical.
+__device__ __forceinline__ bool collide(double f[16], double om, double hb, double bcs, double gm1,
+                                        double* Wout = nullptr) {
     double W[4], Qx[4], Qy[4];
 #pragma unroll
-    for (int k = 0; k < 4; k++) W[k] = xadd<M>(xadd<M>(f[k], f[4 + k]), xadd<M>(f[8 + k], f[12 + k]));
+    for (int k = 0; k < 4; k++) W[k] = (f[k] + f[4 + k]) + (f[8 + k] + f[12 + k]);
     if (Wout)
         for (int k = 0; k < 4; k++) Wout[k] = W[k];
     const double inv = rcp_rn(W[0]);  // = 1.0 / W[0], on the integer pipes
-    const double u = xmul<F>(W[1], inv);
-    const double v = xmul<F>(W[2], inv);
-    const double ruu = xmul<F>(W[1], u);
-    const double rvv = xmul<F>(W[2], v);
-    double e;
-    if constexpr (F) e = emu_sub(W[3], emu_half(emu_add(ruu, rvv)));
-    else e = fma(-0.5, ruu + rvv, W[3]);
-    const double p = xmul<F>(gm1, e);
-    const double H = xadd<F>(W[3], p);
+    const double u = W[1] * inv;
+    const double v = W[2] * inv;
+    const double ruu = W[1] * u;
+    const double rvv = W[2] * v;
+    const double p = gm1 * fma(-0.5, ruu + rvv, W[3]);
+    const double H = W[3] + p;
     Qx[0] = W[1];
-    Qx[1] = xadd<F>(ruu, p);
-    Qx[2] = xmul<F>(W[2], u);
-    Qx[3] = xmul<F>(H, u);
+    Qx[1] = ruu + p;
+    Qx[2] = W[2] * u;
+    Qx[3] = H * u;
     Qy[0] = W[2];
-    Qy[1] = xmul<F>(W[1], v);
-    Qy[2] = xadd<F>(rvv, p);
-    Qy[3] = xmul<F>(H, v);
+    Qy[1] = W[1] * v;
+    Qy[2] = rvv + p;
+    Qy[3] = H * v;
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-        const double A = xmul<A_>(hb, W[k]);
-        double t0, t1, t2, t3;
-        if constexpr (O) {  // om == -1: fma(om, f, A) == A - f exactly
-            t0 = emu_sub(A, f[k]);
-            t1 = emu_sub(A, f[4 + k]);
-            t2 = emu_sub(A, f[8 + k]);
-            t3 = emu_sub(A, f[12 + k]);
-        } else {
-            t0 = fma(om, f[k], A);
-            t1 = fma(om, f[4 + k], A);
-            t2 = fma(om, f[8 + k], A);
-            t3 = fma(om, f[12 + k], A);
-        }
-        f[k] = fma(bcs, Qx[k], t0);
-        f[4 + k] = fma(-bcs, Qx[k], t1);
-        f[8 + k] = fma(bcs, Qy[k], t2);
-        f[12 + k] = fma(-bcs, Qy[k], t3);
+        const double A = hb * W[k];
+        f[k] = fma(bcs, Qx[k], fma(om, f[k], A));
+        f[4 + k] = fma(-bcs, Qx[k], fma(om, f[4 + k], A));
+        f[8 + k] = fma(bcs, Qy[k], fma(om, f[8 + k], A));
+        f[12 + k] = fma(-bcs, Qy[k], fma(om, f[12 + k], A));
     }
     return physical(W[0], p);
 }
@@ -363,8 +327,7 @@ __device__ __noinline__ void sweep_special(const LevelDev* __restrict__ levs, co
 // sub-step; step: coarse step index inside a multi-step launch.
 template <int P, bool COH>
 __device__ __forceinline__ void sweep_cell(const LevelDev* __restrict__ levs, const LevelDev& L, int x, int y, int kk,
-                                           int kkp, int step, double* Wout = nullptr,
-                                           const double* __restrict__ pre = nullptr) {
+                                           int kkp, int step, double* Wout = nullptr) {
     const int nx = L.nx, ny = L.ny;
     if (x >= nx || y >= ny) return;
     const long long c = (long long)y * L.pitch + x;
@@ -375,27 +338,22 @@ __device__ __forceinline__ void sweep_cell(const LevelDev* __restrict__ levs, co
     level_bufs(L, kk, step, src, dst);
     const long long plane = L.plane;
     double f[16];
-    if (pre) {  // this cell's populations, prefetched into shared memory ([pair][cell][2])
 #pragma unroll
-        for (int q = 0; q < 16; q++) f[q] = pre[(q >> 1) * 128 + (q & 1)];
-    } else {
-#pragma unroll
-        for (int pr = 0; pr < 8; pr++) {  // 16-byte loads of the field pairs
-            const double2 v = ld<COH>(reinterpret_cast<const double2*>(src + qoff(2 * pr, plane, c)));
-            f[2 * pr] = v.x;
-            f[2 * pr + 1] = v.y;
-        }
+    for (int pr = 0; pr < 8; pr++) {  // 16-byte loads of the field pairs
+        const double2 v = ld<COH>(reinterpret_cast<const double2*>(src + qoff(2 * pr, plane, c)));
+        f[2 * pr] = v.x;
+        f[2 * pr + 1] = v.y;
     }
     bool ok;
     if constexpr ((P & SW_SENSOR) != 0) {
         if (L.sens) {
             const double b = sensor_beta_at(L, x, y);
-            ok = collide_p<P>(f, 1.0 - 2.0 * b, 0.5 * b, b / L.c, L.gm1, Wout);
+            ok = collide(f, 1.0 - 2.0 * b, 0.5 * b, b / L.c, L.gm1, Wout);
         } else {
-            ok = collide_p<P>(f, L.om, L.hb, L.bcs, L.gm1, Wout);
+            ok = collide(f, L.om, L.hb, L.bcs, L.gm1, Wout);
         }
     } else {
-        ok = collide_p<P>(f, L.om, L.hb, L.bcs, L.gm1, Wout);
+        ok = collide(f, L.om, L.hb, L.bcs, L.gm1, Wout);
     }
     if (!ok) atomicOr(L.status, ST_NONPHYS);
     // push streaming (Eq. 5): f*_i lands on x + c_i
@@ -678,14 +636,6 @@ __device__ __forceinline__ void wait_done(const unsigned* p, unsigned epoch, int
     atomicOr(status, ST_TIMEOUT);
 }
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
 // The segment holding ticket t and the task's index in it.
 __device__ __forceinline__ int find_segment(const int* __restrict__ prefix, int nseg, int t) {
     int lo = 0, hi = nseg - 1;
@@ -695,36 +645,6 @@ __device__ __forceinline__ int find_segment(const int* __restrict__ prefix, int 
         else hi = mid - 1;
     }
     return lo;
-}
-
-// Prefetch of task t2 by one warp, if t2 is a level sweep whose
-// dependencies are all complete already (checked without waiting; each
-// warp decides for its own cells).  Each lane copies the eight field pairs
-// of its own cell, 16 bytes per copy through L2, into buf[pair][cell][2].
-// Returns whether this warp's cells were requested.  The data cannot change
-// before t2 runs: every later writer of t2's source cells waits for t2.
-__device__ __forceinline__ bool prefetch_task(const LevelDev* __restrict__ levs, const Segment* __restrict__ segs,
-                                              const int* __restrict__ prefix, int nseg, int t2, unsigned epoch,
-                                              double* buf, int lt) {
-    const int sg = find_segment(prefix, nseg, t2);
-    const Segment S = segs[sg];
-    const Task T = S.tasks[t2 - prefix[sg]];
-    if (T.kind != 0) return false;
-    bool ok = true;
-    for (int j = lt & 31; j < T.ndep; j += 32) ok = ok && ld_acquire(S.done + S.deps[T.dep0 + j]) == epoch;
-    if (!__all_sync(0xffffffffu, ok)) return false;
-    __syncwarp();  // the acquire loads above precede every copy below
-    const LevelDev& L = levs[T.lid + S.lid_base];
-    const double* src;
-    double* dst;
-    level_bufs(L, T.kk, T.step, src, dst);
-    const int x = T.tx * TILE + (lt & 7), y = T.ty * TILE + (lt >> 3);
-    if (y < L.ny) {  // x < pitch always: rows are padded to 16 cells
-        const long long c = (long long)y * L.pitch + x;
-#pragma unroll
-        for (int pr = 0; pr < 8; pr++) cp_async16(buf + pr * 128 + 2 * lt, src + qoff(2 * pr, L.plane, c));
-    }
-    return true;
 }
 
 // Tasks are claimed in list order -- segment by segment, each segment in a
@@ -739,26 +659,18 @@ __device__ __forceinline__ bool prefetch_task(const LevelDev* __restrict__ levs,
 // threads precede the barrier); waiting lanes read the marks with acquire
 // loads before the group barrier that precedes the task's reads, which go
 // through L2 (ld.global.cg, cp.async.cg).
-//
-// With TK_PREFETCH each group double-buffers the populations of its tasks
-// in shared memory (2 x 8 pairs x 64 cells x 2): while a task runs, the
-// copy of the next one is in flight whenever its dependencies are complete.
-constexpr int TK_SMEM = TILES_PER_CTA * 2 * NQ * 64 * (int)sizeof(double);
+
 
 template <int P, int MINB>
 __global__ void __launch_bounds__(CTA_THREADS, MINB)
 task_kernel(const LevelDev* __restrict__ levs, const Segment* __restrict__ segs, const int* __restrict__ prefix,
             int* ctl) {
-    constexpr bool PF = (P & TK_PREFETCH) != 0;
-    extern __shared__ double s_pf[];  // PF only: [group][buffer][q][cell]
     __shared__ int s_task[TILES_PER_CTA][2];
     const int g = threadIdx.x >> 6;
     const int lt = threadIdx.x & 63;
     const int cx = lt & 7, cy = lt >> 3;
     const unsigned epoch = (unsigned)ctl[CTL_EPOCH];
     const int total = ctl[CTL_TOTAL], nseg = ctl[CTL_NSEG];
-    bool pf = false;  // PF: this warp's cells of the current task are in buffer pb
-    int pb = 0;
     if (lt == 0) s_task[g][0] = atomicAdd(&ctl[CTL_CLAIM], 1);
     group_bar(g);
     for (int par = 0;; par ^= 1) {
@@ -772,29 +684,16 @@ task_kernel(const LevelDev* __restrict__ levs, const Segment* __restrict__ segs,
         for (int j = lt; j < T.ndep; j += 64) wait_done(S.done + S.deps[T.dep0 + j], epoch, L.status);
         if (lt == 0) s_task[g][par ^ 1] = atomicAdd(&ctl[CTL_CLAIM], 1);
         group_bar(g);
-        const double* pre = nullptr;
-        bool pf_next = false;
-        if constexpr (PF) {
-            const int t2 = s_task[g][par ^ 1];
-            double* base = s_pf + (size_t)g * 2 * NQ * 64;
-            if (t2 < total) pf_next = prefetch_task(levs, segs, prefix, nseg, t2, epoch, base + (pb ^ 1) * NQ * 64, lt);
-            cp_async_commit();
-            if (pf) {
-                cp_async_wait_prev();  // the copies of the current task
-                __syncwarp();
-                pre = base + pb * NQ * 64 + 2 * lt;  // this cell: [pair][cell][2]
-            }
-        }
         if (T.kind == 0) {
             if (S.aw && T.aslot >= 0) {
                 // audited sweep: keep the moments of the cell (0 off the
                 // active set) for the exact reduction after the launch
                 double W[4] = {0.0, 0.0, 0.0, 0.0};
-                sweep_cell<P, true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.kkp, T.step, W, pre);
+                sweep_cell<P, true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.kkp, T.step, W);
                 double* o = S.aw + (size_t)T.aslot * AUDIT_SLOT + lt;
                 for (int k = 0; k < 4; k++) o[k * 64] = W[k];
             } else {
-                sweep_cell<P, true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.kkp, T.step, nullptr, pre);
+                sweep_cell<P, true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.kkp, T.step);
             }
         } else if (T.kind == 1) {
             close_cell<true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.step);
@@ -813,12 +712,7 @@ task_kernel(const LevelDev* __restrict__ levs, const Segment* __restrict__ segs,
                 ctl[CTL_EPOCH] = (int)(epoch + 1);
             }
         }
-        if constexpr (PF) {
-            pf = pf_next;
-            pb ^= 1;
-        }
     }
-    if constexpr (PF) cp_async_wait_all();
 }
 
 // TK_HALF: the same schedule with every warp on its own -- a task (tile) is
@@ -1373,24 +1267,12 @@ static inline int flat_grid(long long n) {
     return (int)(g < 1 ? 1 : g);
 }
 
-// Sweep variants: (emulation policy, minimum resident CTAs per SM).
-#define VLBM_SWEEP_VARIANTS(X)                                   \
-    X(0, 0, 2) X(1, 0, 3) X(2, EM_MOM, 2) X(3, EM_MOM | EM_A, 2) \
-    X(4, EM_MOM | EM_A | EM_FLUX, 2) X(5, EM_FLUX, 2) X(6, EM_MOM | EM_A | EM_FLUX | EM_OMF, 2) \
-    X(7, EM_MOM | EM_A | EM_OMF, 2) X(8, EM_MOM | EM_A | EM_FLUX, 3) X(9, EM_MOM | EM_A | EM_FLUX | EM_OMF, 3) \
-    X(10, 0, 4) X(11, TK_PREFETCH, 3) X(12, TK_PREFETCH, 2) X(13, TK_HALF, 3) X(14, TK_HALF, 2)
+// Sweep variants: (launch shape, minimum resident CTAs per SM): whole
+// 8 x 8 tiles per group of 64 threads at 2, 3 or 4 CTAs per SM, or (the
+// persistent kernel only) half tiles per warp at 3 or 2.
+#define VLBM_SWEEP_VARIANTS(X) X(0, 0, 2) X(1, 0, 3) X(2, 0, 4) X(3, TK_HALF, 3) X(4, TK_HALF, 2)
 
-int sweep_variants() { return 15; }
-
-// variant -> whether it needs 1 - 2 beta == -1
-bool sweep_variant_needs_om_minus1(int v) {
-    switch (v) {
-#define X(id, P, B) case id: return ((P) & EM_OMF) != 0;
-        VLBM_SWEEP_VARIANTS(X)
-#undef X
-    }
-    return false;
-}
+int sweep_variants() { return 5; }
 
 cudaError_t launch_sensor(const LevelDev* levs, const Item* items, int n, int kk, cudaStream_t s, const int* nc) {
     if (n <= 0) return cudaSuccess;
@@ -1424,11 +1306,6 @@ int task_variant_per_sm() {
     int per = 0;
     if constexpr ((P & TK_HALF) != 0) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, task_kernel_half<P, B>, CTA_THREADS, 0);
-    } else if constexpr ((P & TK_PREFETCH) != 0) {
-        cudaFuncSetAttribute(task_kernel<P, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, TK_SMEM);
-        cudaFuncSetAttribute(task_kernel<P, B>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, task_kernel<P, B>, CTA_THREADS, TK_SMEM);
     } else {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, task_kernel<P, B>, CTA_THREADS, 0);
     }
@@ -1441,7 +1318,7 @@ void task_variant_launch(int g, const LevelDev* levs, const Segment* segs, const
     if constexpr ((P & TK_HALF) != 0)
         task_kernel_half<P, B><<<g, CTA_THREADS, 0, s>>>(levs, segs, prefix, ctl);
     else
-        task_kernel<P, B><<<g, CTA_THREADS, (P & TK_PREFETCH) ? TK_SMEM : 0, s>>>(levs, segs, prefix, ctl);
+        task_kernel<P, B><<<g, CTA_THREADS, 0, s>>>(levs, segs, prefix, ctl);
 }
 
 int task_kernel_ctas(int variant) {

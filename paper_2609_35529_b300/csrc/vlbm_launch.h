@@ -14,7 +14,6 @@ cudaError_t launch_sweep(const LevelDev* levs, const Item* items, int n, int kk,
 cudaError_t launch_sensor(const LevelDev* levs, const Item* items, int n, int kk, cudaStream_t s,
                           const int* nc = nullptr);
 int sweep_variants();
-bool sweep_variant_needs_om_minus1(int v);
 int task_kernel_ctas(int variant);
 cudaError_t launch_tasks(const LevelDev* levs, const Segment* segs, const int* prefix, int* ctl, int variant, int ctas,
                          cudaStream_t s);

@@ -1,13 +1,15 @@
-// Self-tests of the integer-pipe FP64 routines (binary64 addition and
-// multiplication, the correctly rounded reciprocal) against the FP64 unit.
+// Self-test of the correctly rounded reciprocal on the integer pipes (used
+// by the collision for 1/rho) against the FP64 division.
 #include <cuda_runtime.h>
 #include <cstdint>
 
-#include "fp64emu.cuh"
 #include "rcp_rn.cuh"
 #include "vlbm.h"
 
 namespace vlbm {
+
+constexpr unsigned long long EMU_MANT = 0x000FFFFFFFFFFFFFull;  // binary64 significand field
+constexpr unsigned long long EMU_HID = 0x0010000000000000ull;   // its hidden bit
 
 // SplitMix64 (Steele, Lea & Flood 2014): counter-based 64-bit generator.
 __device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
@@ -17,82 +19,12 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
     return x ^ (x >> 31);
 }
 
-// A test operand: mostly values near 1 (the range of the method's data),
-// plus exponent gaps, equal exponents, specials and raw bit patterns.
-__device__ double operand(unsigned long long r, unsigned long long r2, double other) {
-    const unsigned kind = (unsigned)(r2 % 100);
-    unsigned long long mant = r & EMU_MANT;
-    unsigned long long sign = (r2 >> 40) & 1ull;
-    unsigned long long e;
-    if (kind < 60) e = 1023 - 40 + (r2 >> 8) % 80;
-    else if (kind < 72) e = ((unsigned long long)__double_as_longlong(other) >> 52) & 0x7FF;  // equal exponent
-    else if (kind < 80) e = (((unsigned long long)__double_as_longlong(other) >> 52) & 0x7FF) + ((r2 >> 8) % 130) - 65;
-    else if (kind < 85) {  // near-cancellation partner
-        unsigned long long o = (unsigned long long)__double_as_longlong(other);
-        return __longlong_as_double((long long)((o ^ EMU_SIGN) + ((r2 >> 8) % 5) - 2));
-    } else if (kind < 90) {
-        const unsigned long long sp[8] = {0ull, EMU_SIGN, 1ull, 0x000FFFFFFFFFFFFFull, 0x0010000000000000ull,
-                                          0x7FEFFFFFFFFFFFFFull, 0x7FF0000000000000ull, 0x7FF8000000000000ull};
-        return __longlong_as_double((long long)(sp[(r2 >> 8) % 8] | (sign << 63)));
-    } else if (kind < 95) e = (r2 >> 8) % 2048;
-    else return __longlong_as_double((long long)r);
-    if (e > 2047) e = 1023;
-    return __longlong_as_double((long long)((sign << 63) | (e << 52) | mant));
-}
-
 __device__ __forceinline__ bool same(double x, double y) {
     if (x != x && y != y) return true;  // both NaN
     return __double_as_longlong(x) == __double_as_longlong(y);
 }
 
-__global__ void selftest_kernel(unsigned long long seed, long long n, unsigned long long* bad, double* first) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const unsigned long long r1 = splitmix64(seed ^ (4 * i)), r2 = splitmix64(seed ^ (4 * i + 1));
-        const unsigned long long r3 = splitmix64(seed ^ (4 * i + 2)), r4 = splitmix64(seed ^ (4 * i + 3));
-        const double a = operand(r1, r2, 1.0);
-        const double b = operand(r3, r4, a);
-        const double ref[4] = {a + b, a - b, a * b, a * 0.5};
-        const double got[4] = {emu_add(a, b), emu_sub(a, b), emu_mul(a, b), emu_half(a)};
-        for (int k = 0; k < 4; k++) {
-            if (!same(ref[k], got[k])) {
-                if (atomicAdd(&bad[k], 1ull) == 0) {
-                    first[4 * k + 0] = a;
-                    first[4 * k + 1] = b;
-                    first[4 * k + 2] = ref[k];
-                    first[4 * k + 3] = got[k];
-                }
-            }
-        }
-    }
-}
-
 }  // namespace vlbm
-
-extern "C" vlbm_status vlbm_selftest_fp64(uint64_t seed, int64_t n, uint64_t mismatches[4], double first_bad[16]) {
-    if (n < 0 || !mismatches) return VLBM_ERR_ARG;
-    unsigned long long* dbad = nullptr;
-    double* dfirst = nullptr;
-    if (cudaMalloc(&dbad, 4 * sizeof(unsigned long long)) != cudaSuccess) return VLBM_ERR_OOM;
-    if (cudaMalloc(&dfirst, 16 * sizeof(double)) != cudaSuccess) {
-        cudaFree(dbad);
-        return VLBM_ERR_OOM;
-    }
-    cudaMemset(dbad, 0, 4 * sizeof(unsigned long long));
-    cudaMemset(dfirst, 0, 16 * sizeof(double));
-    vlbm::selftest_kernel<<<148 * 8, 256>>>(seed, n, dbad, dfirst);
-    cudaError_t e = cudaDeviceSynchronize();
-    unsigned long long hb[4] = {0, 0, 0, 0};
-    double hf[16];
-    if (e == cudaSuccess) e = cudaMemcpy(hb, dbad, sizeof hb, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(hf, dfirst, sizeof hf, cudaMemcpyDeviceToHost);
-    cudaFree(dbad);
-    cudaFree(dfirst);
-    if (e != cudaSuccess) return VLBM_ERR_CUDA;
-    for (int k = 0; k < 4; k++) mismatches[k] = hb[k];
-    if (first_bad)
-        for (int k = 0; k < 16; k++) first_bad[k] = hf[k];
-    return VLBM_OK;
-}
 
 namespace vlbm {
 

@@ -124,10 +124,8 @@ def lib():
     L.vlbm_set_tuning.restype = C.c_int
     L.vlbm_get_tuning.argtypes = [vp, C.POINTER(vlbm_tuning)]
     L.vlbm_get_tuning.restype = C.c_int
-    L.vlbm_selftest_fp64.argtypes = [C.c_uint64, i64, C.POINTER(C.c_uint64), dp]
     L.vlbm_selftest_timeout.argtypes = [dp, C.POINTER(i32)]
     L.vlbm_selftest_timeout.restype = C.c_int
-    L.vlbm_selftest_fp64.restype = C.c_int
     L.vlbm_selftest_rcp.argtypes = [C.c_uint64, i64, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), dp]
     L.vlbm_selftest_rcp.restype = C.c_int
     L.vlbm_selftest_layout.argtypes = [C.c_uint64, i32, C.POINTER(i64), C.POINTER(i64), C.c_char_p, i32]
@@ -429,18 +427,6 @@ def totals_static(f_ptr, ld, nx, ny, weight, out_ptr, stream=None):
 
 def num_variants():
     return lib().vlbm_num_variants()
-
-
-def selftest_fp64(seed, n):
-    """Bitwise check of the integer-pipe FP64 routines against the FP64 unit;
-    returns ({op: mismatches}, first offending (a, b, hw, emu) per op)."""
-    bad = (C.c_uint64 * 4)()
-    first = (C.c_double * 16)()
-    st = lib().vlbm_selftest_fp64(int(seed), int(n), bad, first)
-    if st != 0:
-        raise VlbmError(st, "vlbm_selftest_fp64")
-    names = ["add", "sub", "mul", "half"]
-    return {k: int(bad[i]) for i, k in enumerate(names)}, {k: tuple(first[4 * i: 4 * i + 4]) for i, k in enumerate(names)}
 
 
 def selftest_rcp(seed, n):

@@ -369,8 +369,8 @@ vlbm_status vlbm_set_sensor(vlbm_hier* h, int32_t on, double beta_min, double c_
  * rule, and the persistent schedule's task list built on the device for
  * 1-3 coarse steps must equal the host builder's task for task and
  * dependency for dependency.  *mismatches counts differences;
- * *second_pass (may be NULL) the tasks whose dependency set outgrew the
- * builder's small per-thread set and took its second pass; first_bad (may
+ * *second_pass (may be NULL) the tasks with more dependencies than their
+ * fixed slot holds (stored in the overflow area); first_bad (may
  * be NULL, `cap` bytes) describes the first difference.  Runs on the
  * current device, synchronises.  Errors: ERR_ARG, ERR_OOM, ERR_CUDA. */
 vlbm_status vlbm_selftest_layout(uint64_t seed, int32_t cases, int64_t* mismatches, int64_t* second_pass,

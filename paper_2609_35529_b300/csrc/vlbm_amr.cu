@@ -376,13 +376,12 @@ static inline int flat_blocks(long long n) {
 // task lists (the device form of build_tasks in vlbm_tasks.h)
 // ---------------------------------------------------------------------------
 
-// A task's dependency set: up to TB_SMALL entries (one thread per task,
-// many threads in flight, the sets in L1: the work is chains of table
-// lookups, latency bound); the rare task with more dependencies is redone by
-// a second pass with a TB_MAXDEP-entry set.  Adversarial
-// layouts (most cells refined, checkerboard coverage) reached 98 distinct
-// dependencies; beyond TB_MAXDEP the build raises ST_TASKCAP (reported as
-// VLBM_ERR_OOM).
+// Dependencies per task: up to TB_SMALL in the task's fixed slot, more in
+// the overflow area.  The work is chains of table lookups (latency bound),
+// so a warp walks one task's accesses in parallel (tb_warp_kernel).
+// Adversarial layouts (most cells refined, checkerboard coverage) reached
+// 98 distinct dependencies; the fallback pass holds TB_MAXDEP, beyond which
+// the build raises ST_TASKCAP (reported as VLBM_ERR_OOM).
 constexpr int TB_SMALL = TASK_DEP_SLOT;
 constexpr int TB_MAXDEP = 256;
 constexpr int TB_BUILD_THREADS = 128;
@@ -391,8 +390,8 @@ __constant__ int kSDJ[5] = {0, 0, 0, 1, -1};
 
 __device__ __forceinline__ int src_of(int level, int kk, int step) { return level == 0 ? (step & 1) : (kk == 1 ? 0 : 1); }
 
-// A task's dependency set (in local memory): at most `cap` distinct task
-// indices, entry i at v[i * stride].
+// A task's dependency set for the fallback pass (in local memory): at most
+// `cap` distinct task indices, entry i at v[i * stride].
 struct DepSet {
     int* v;      // entry i at v[i * stride]
     int stride;
@@ -506,34 +505,103 @@ struct TB {
         return (l + 1 < P.nlev) ? m : (m & 1);
     }
 
-    template <class Set>
-    __device__ __forceinline__ void deps_of(int p, bool write, int l, int kind, int tx, int ty, Set& S) const {
+    // The tasks that the access (write or read, level l, resource kind, tile
+    // (tx, ty)) of phase p depends on, each passed to emit (possibly more
+    // than once): a read waits for the last earlier writer of the tile; a
+    // write waits for every reader since that writer, or for the writer
+    // itself when there was none.  A cyclic list's walk goes on through the
+    // whole previous iteration (entries ~q): every tile a step reads or
+    // writes is written within one step, so the walk ends there.  Level 0
+    // alternates its buffers from step to step, so there its buffer kinds
+    // swap across the wrap.
+    template <class Emit>
+    __device__ __forceinline__ void deps_of(int p, bool write, int l, int kind, int tx, int ty, Emit&& emit) const {
         if (!write) {
             const int m = wmask(l, tx, ty);
             if (kind == 2 ? !(m & 2) : !m) return;
         }
-        const int rc = l * 3 + kind;
-        const int a0 = acc_beg[rc];
         bool readers = false;
-        for (int e = acc_pos[rc * (P.nphase + 1) + p] - 1; e >= a0; e--) {
-            const TBAcc a = acc[e];
-            if (a.write) {
-                bool any = false;
-                touching(a, l, tx, ty, [&](int q) {
-                    any = true;
-                    if (!readers) S.add(q);
-                });
-                if (any) return;
-            } else if (write) {
-                touching(a, l, tx, ty, [&](int q) {
-                    readers = true;
-                    S.add(q);
-                });
+        for (int pass = 0; pass < 1 + P.cyclic; pass++) {
+            const int rc = l * 3 + (pass && l == 0 && kind < 2 ? kind ^ 1 : kind);
+            const int a0 = acc_beg[rc];
+            const int e0 = pass ? acc_beg[rc + 1] : acc_pos[rc * (P.nphase + 1) + p];
+            for (int e = e0 - 1; e >= a0; e--) {
+                const TBAcc a = acc[e];
+                if (a.write) {
+                    bool any = false;
+                    touching(a, l, tx, ty, [&](int q) {
+                        any = true;
+                        if (!readers) emit(pass ? ~q : q);
+                    });
+                    if (any) return;
+                } else if (write) {
+                    touching(a, l, tx, ty, [&](int q) {
+                        readers = true;
+                        emit(pass ? ~q : q);
+                    });
+                }
             }
         }
     }
 
-    // the dependencies of task t of phase p
+    // Access q (0 <= q < nq) of a task of phase ph on tile it: false when
+    // the access falls off a non-periodic side or outside the finer level.
+    // Sweeps: q = 0 reads the tile's source buffer, q = 1..5 write the
+    // destination buffer of the tile and its four neighbours (push), and a
+    // reconstructing tile reads both buffers and the flags of each coarse
+    // footprint tile (q = 6 + 3 k + r); closes: q = 0..7 read the two buffers
+    // of the four child tiles, q = 8, 9 write the tile's destination buffer
+    // and flags.
+    __device__ __forceinline__ bool query(const TBPhase& ph, const Item& it, const int* keys, int q, bool& write,
+                                          int& l, int& kind, int& tx, int& ty) const {
+        l = ph.l;
+        if (ph.kind == 0) {
+            const int bs = src_of(l, ph.kk, ph.step);
+            if (q == 0) {
+                write = false;
+                kind = bs;
+                tx = it.tx;
+                ty = it.ty;
+                return true;
+            }
+            if (q <= 5) {
+                const TBLevel& L = P.lev[l];
+                bool ok = true;
+                tx = wrap_or(it.tx + kSDI[q - 1], L.bx, L.px, ok);
+                ty = wrap_or(it.ty + kSDJ[q - 1], L.by, L.py, ok);
+                write = true;
+                kind = bs ^ 1;
+                return ok;
+            }
+            const int k = (q - 6) / 3, r = (q - 6) % 3;
+            const int pbs = src_of(l - 1, ph.kkp, ph.step);
+            const int bx = P.lev[l - 1].bx;
+            l -= 1;
+            write = false;
+            kind = r == 0 ? pbs : (r == 1 ? pbs ^ 1 : 2);
+            tx = keys[k] % bx;
+            ty = keys[k] / bx;
+            return true;
+        }
+        if (q < 8) {
+            const TBLevel& C = P.lev[l + 1];
+            const int c = q >> 1;
+            tx = 2 * it.tx + (c & 1);
+            ty = 2 * it.ty + (c >> 1);
+            l += 1;
+            write = false;
+            kind = q & 1;
+            return tx < C.bx && ty < C.by;
+        }
+        write = true;
+        kind = q == 8 ? (src_of(l, ph.kk, ph.step) ^ 1) : 2;
+        tx = it.tx;
+        ty = it.ty;
+        return true;
+    }
+
+    // the dependencies of task t of phase p into the set S (the fallback
+    // pass: one thread per task)
     template <class Set>
     __device__ __forceinline__ void deps(int p, int t, Set& S, Item& it) const {
         const TBPhase ph = this->ph[p];
@@ -543,38 +611,13 @@ struct TB {
         it = ph.kind == 0 ? L.act[i] : L.ring[i];
         S.n = 0;
         S.ovf = false;
-        if (ph.kind == 0) {
-            const int bs = src_of(l, ph.kk, ph.step), bd = bs ^ 1;
-            deps_of(p, false, l, bs, it.tx, it.ty, S);
-            for (int d = 0; d < 5; d++) {
-                bool ok = true;
-                const int tx = wrap_or(it.tx + kSDI[d], L.bx, L.px, ok), ty = wrap_or(it.ty + kSDJ[d], L.by, L.py, ok);
-                if (ok) deps_of(p, true, l, bd, tx, ty, S);
-            }
-            if (l > 0 && L.recon[it.ty * L.bx + it.tx]) {
-                const TBLevel& Pl = P.lev[l - 1];
-                const int pbs = src_of(l - 1, ph.kkp, ph.step), pbd = pbs ^ 1;
-                int keys[16];
-                const int nk = footprint(Pl, it.tx, it.ty, keys);
-                for (int q = 0; q < nk; q++) {
-                    const int cx = keys[q] % Pl.bx, cy = keys[q] / Pl.bx;
-                    deps_of(p, false, l - 1, pbs, cx, cy, S);
-                    deps_of(p, false, l - 1, pbd, cx, cy, S);
-                    deps_of(p, false, l - 1, 2, cx, cy, S);
-                }
-            }
-        } else {
-            const int bd = src_of(l, ph.kk, ph.step) ^ 1;
-            const TBLevel& C = P.lev[l + 1];
-            for (int b2 = 0; b2 < 2; b2++)
-                for (int a2 = 0; a2 < 2; a2++) {
-                    const int fx = 2 * it.tx + a2, fy = 2 * it.ty + b2;
-                    if (fx >= C.bx || fy >= C.by) continue;
-                    deps_of(p, false, l + 1, 0, fx, fy, S);
-                    deps_of(p, false, l + 1, 1, fx, fy, S);
-                }
-            deps_of(p, true, l, bd, it.tx, it.ty, S);
-            deps_of(p, true, l, 2, it.tx, it.ty, S);
+        int keys[16];
+        const int nk = (ph.kind == 0 && l > 0 && L.recon[it.ty * L.bx + it.tx]) ? footprint(P.lev[l - 1], it.tx, it.ty, keys) : 0;
+        const int nq = ph.kind == 0 ? 6 + 3 * nk : 10;
+        for (int q = 0; q < nq; q++) {
+            bool wr;
+            int ql, qk, qx, qy;
+            if (query(ph, it, keys, q, wr, ql, qk, qx, qy)) deps_of(p, wr, ql, qk, qx, qy, [&](int d) { S.add(d); });
         }
     }
 
@@ -603,6 +646,7 @@ __global__ void tb_offsets_kernel(TBPlan P) {
     P.off[P.nphase] = o;
     P.need[0] = o;
     P.need[1] = 0;
+    P.need[2] = 0;
     P.need[3] = 0;
     P.need[4] = 0;
 }
@@ -640,28 +684,111 @@ __device__ __forceinline__ void tb_write(const TBPlan& P, const TB& tb, int p, i
     P.tasks[t] = T;
 }
 
-// One pass: every task's dependencies into its fixed TB_SMALL slot of the
-// dependency array (deps[t * TB_SMALL ..]); a task with more is left to the
-// second pass.
-__global__ void __launch_bounds__(TB_BUILD_THREADS) tb_build_kernel(TBPlan P) {
+// One warp per task: the lanes walk the task's accesses in parallel and
+// append what they find (duplicates included) to the warp's shared buffer;
+// the distinct entries, ascending, go to the task's fixed TB_SMALL slot of
+// the dependency array (deps[t * TB_SMALL ..]), or to the overflow area
+// after the slots when there are more.  A task whose raw entries exceed the
+// buffer is left to the fallback pass.
+constexpr int TBW_WARPS = 4;
+constexpr int TBW_RAW = 768;
+
+__global__ void __launch_bounds__(TBW_WARPS * 32) tb_warp_kernel(TBPlan P) {
+    __shared__ int raw[TBW_WARPS][TBW_RAW];
+    __shared__ unsigned char keep[TBW_WARPS][TBW_RAW];
+    __shared__ int nraw[TBW_WARPS];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int total = P.off[P.nphase];
     if (total > P.task_cap) return;
     const TB tb = tb_global(P);
-    int buf[TB_SMALL];
-    DepSet S{buf, 1, TB_SMALL, 0, false};
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    int* R = raw[w];
+    unsigned char* K = keep[w];
+    const long long base = (long long)P.task_cap * TB_SMALL;
+    for (int t = blockIdx.x * TBW_WARPS + w; t < total; t += gridDim.x * TBW_WARPS) {
         const int p = tb.phase_of(t);
-        Item it;
-        tb.deps(p, t, S, it);
-        if (S.ovf) P.big[atomicAdd(P.need + 4, 1)] = t;
-        else tb_write(P, tb, p, t, it, S, (long long)t * TB_SMALL);
+        const TBPhase ph = tb.ph[p];
+        const TBLevel& L = P.lev[ph.l];
+        const int i = t - tb.off[p];
+        const Item it = ph.kind == 0 ? L.act[i] : L.ring[i];
+        int keys[16];
+        const int nk = (ph.kind == 0 && ph.l > 0 && L.recon[it.ty * L.bx + it.tx])
+                           ? footprint(P.lev[ph.l - 1], it.tx, it.ty, keys) : 0;
+        const int nq = ph.kind == 0 ? 6 + 3 * nk : 10;
+        if (lane == 0) nraw[w] = 0;
+        __syncwarp();
+        for (int q = lane; q < nq; q += 32) {
+            bool wr;
+            int ql, qk, qx, qy;
+            if (!tb.query(ph, it, keys, q, wr, ql, qk, qx, qy)) continue;
+            tb.deps_of(p, wr, ql, qk, qx, qy, [&](int d) {
+                const int at = atomicAdd(&nraw[w], 1);
+                if (at < TBW_RAW) R[at] = d;
+            });
+        }
+        __syncwarp();
+        const int n = nraw[w];
+        __syncwarp();
+        if (n > TBW_RAW) {
+            if (lane == 0) P.big[atomicAdd(P.need + 2, 1)] = t;
+            continue;
+        }
+        // entry j is kept when no earlier entry holds its value
+        int kept = 0;
+        for (int j = lane; j < n; j += 32) {
+            const int v = R[j];
+            bool first = true;
+            for (int k = 0; k < j && first; k++) first = R[k] != v;
+            K[j] = first;
+            kept += first;
+        }
+        const int nu = __reduce_add_sync(0xffffffffu, kept);
+        __syncwarp();
+        long long at = (long long)t * TB_SMALL;
+        if (nu > TB_SMALL) {
+            long long a = 0;
+            if (lane == 0) {
+                a = base + atomicAdd(P.need + 1, nu);
+                atomicAdd(P.need + 4, 1);
+                if (a + nu > P.dep_cap) {
+                    atomicOr(P.need + 3, 1);
+                    a = -1;
+                }
+            }
+            at = __shfl_sync(0xffffffffu, a, 0);
+        }
+        if (at >= 0) {
+            // a kept entry's place: the kept entries with smaller values
+            for (int j = lane; j < n; j += 32) {
+                if (!K[j]) continue;
+                const int v = R[j];
+                int r = 0;
+                for (int k = 0; k < n; k++) r += (K[k] && R[k] < v);
+                P.deps[at + r] = v;
+            }
+            if (lane == 0) {
+                Task T;
+                T.lid = ph.l;
+                T.tx = it.tx;
+                T.ty = it.ty;
+                T.kind = (signed char)ph.kind;
+                T.kk = (signed char)ph.kk;
+                T.kkp = (signed char)(ph.kind == 0 ? ph.kkp : 0);
+                T.step = (signed char)ph.step;
+                T.dep0 = (int)at;
+                T.ndep = nu;
+                T.aslot = -1;
+                P.tasks[t] = T;
+            }
+        }
+        __syncwarp();
     }
 }
 
-// Second pass: the tasks with more than TB_SMALL dependencies, with a
-// local-memory set, into the overflow area after the fixed slots.
+// Fallback pass: the tasks whose raw entries overflowed the warp buffer,
+// one thread each with a local-memory set of up to TB_MAXDEP distinct
+// dependencies, into the overflow area.
 __global__ void __launch_bounds__(TB_BUILD_THREADS) tb_big_kernel(TBPlan P) {
-    const int nbig = P.need[4];
+    const int nbig = P.need[2];
     if (nbig == 0) return;
     const TB tb = tb_global(P);
     int buf[TB_MAXDEP];
@@ -677,6 +804,7 @@ __global__ void __launch_bounds__(TB_BUILD_THREADS) tb_big_kernel(TBPlan P) {
             atomicOr(P.need + 3, 1);
             continue;
         }
+        if (S.n > TB_SMALL) atomicAdd(P.need + 4, 1);
         tb_write(P, tb, p, t, it, S, at);
     }
 }
@@ -757,16 +885,15 @@ cudaError_t launch_count_lups(const LayoutDev* levs, int n, long long steps, uns
 
 cudaError_t launch_task_build(const TBPlan& P, cudaStream_t s) {
     static bool attrs = false;
-    if (!attrs) {  // no shared memory: the whole L1 for the sets and lookups
-        cudaFuncSetAttribute(tb_build_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    if (!attrs) {  // the fallback's sets live in local memory: the whole L1 for them
         cudaFuncSetAttribute(tb_big_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
         attrs = true;
     }
     tb_offsets_kernel<<<1, 1, 0, s>>>(P);
-    long long gl = ((long long)P.task_cap + TB_BUILD_THREADS - 1) / TB_BUILD_THREADS;
-    const int g = (int)(gl < 1 ? 1 : (gl > 148 * 16 ? 148 * 16 : gl));
-    tb_build_kernel<<<g, TB_BUILD_THREADS, 0, s>>>(P);
-    tb_big_kernel<<<148 * 4, TB_BUILD_THREADS, 0, s>>>(P);
+    const long long gl = ((long long)P.task_cap + TBW_WARPS - 1) / TBW_WARPS;
+    const int g = (int)(gl < 1 ? 1 : (gl > 148 * 12 ? 148 * 12 : gl));
+    tb_warp_kernel<<<g, TBW_WARPS * 32, 0, s>>>(P);
+    tb_big_kernel<<<148, TB_BUILD_THREADS, 0, s>>>(P);
     tb_finish_kernel<<<1, 1, 0, s>>>(P);
     return cudaGetLastError();
 }

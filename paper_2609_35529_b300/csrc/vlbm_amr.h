@@ -110,6 +110,11 @@ constexpr int TASK_DEP_SLOT = 32;
 // per launch only) and the buffers of one task list.
 struct TBPlan {
     int nlev = 0, nphase = 0, nacc = 0;
+    // cyclic: the list is one coarse step that the kernel runs once per
+    // step, and a task's walk continues through the previous iteration
+    // (dependencies there stored as ~index); otherwise the list starts from
+    // a synchronised state
+    int cyclic = 0;
     TBLevel lev[4] = {};
     const TBPhase* ph = nullptr;       // [nphase]
     const TBAcc* acc = nullptr;        // per resource class (l * 3 + kind), in phase order
@@ -121,17 +126,18 @@ struct TBPlan {
     unsigned* done = nullptr;          // completion marks (left as they are)
     int task_cap = 0;
     long long dep_cap = 0;
-    int* need = nullptr;               // [5]: tasks of the last build, overflow area used, -, overflow flag,
-                                       // tasks of the second pass
-    int* big = nullptr;                // [task_cap] tasks of the second pass
+    int* need = nullptr;               // [5]: tasks of the last build, overflow area used, tasks of the
+                                       // fallback pass, overflow flag, tasks in the overflow area
+    int* big = nullptr;                // [task_cap] tasks of the fallback pass
     int* status = nullptr;             // hierarchy status word (ST_TASKCAP on overflow)
     Segment* seg = nullptr;            // the single-member segment of the launch
     int* prefix = nullptr;             // [2]
     int* ctl = nullptr;                // CTL_WORDS
 };
 // Builds the task list of the plan's phase sequence on the current lists:
-// phase offsets, then every task with its sorted dependencies (in one pass;
-// a second one for the tasks with more than TASK_DEP_SLOT); writes the
+// phase offsets, then every task with its sorted dependencies (a warp per
+// task; a one-thread fallback pass for tasks whose raw dependency entries
+// overflow the warp's buffer); writes the
 // launch's task count into seg, prefix and ctl.  When the overflow area is
 // exhausted the list is left empty (the launch does nothing) and
 // ST_TASKCAP is set in *status.

@@ -374,9 +374,10 @@ struct vlbm_hier {
         int task_cap = 0;
         long long dep_cap = 0;
         int build_kernels = 0;  // kernels the last dev_plan call queued (a task list build)
-        cudaGraphExec_t exec = nullptr;
-        std::vector<uintptr_t> key;
-    } dp[2];
+        // graphs of its persistent launch: [0] one iteration, [1] G iterations
+        cudaGraphExec_t exec[2] = {nullptr, nullptr};
+        std::vector<uintptr_t> key[2];
+    } dp[2];  // [0] the cyclic one-step list the device path runs; [1] a k-step list (self-test)
     // per-phase launches over the device lists: [0] one step, [1] G steps
     struct PhaseGraph {
         cudaGraphExec_t exec = nullptr;
@@ -757,7 +758,7 @@ struct Batch {
 
     void task_launch(int which, cudaStream_t s) {
         VCK(cudaMemsetAsync(ctl[which].p, 0, 2 * sizeof(int), s));  // claim and finish counters
-        VCK(launch_tasks(levs.p, segs[which].p, prefix[which].p, ctl[which].p, variant, max_ctas, s));
+        VCK(launch_tasks(levs.p, segs[which].p, prefix[which].p, ctl[which].p, variant, max_ctas, 1, s));
         if (audit && members.size() == 1) {
             auto& T = members[0]->tl[which];
             VCK(launch_audit_segments(T.apart.p, T.abseg.p, T.nseg, T.aout.p, s));
@@ -1553,10 +1554,13 @@ void plan_tables(int nlev, int nsteps, std::vector<TBPhase>& ph, std::vector<TBA
     beg[TASK_MAX_LEVELS * 3] = (int)acc.size();
 }
 
-// The task list of `k` coarse steps on the current layout, built on the
-// device when the layout changed.
-vlbm_hier::DevPlan& dev_plan(vlbm_hier* h, int which, int k) {
-    vlbm_hier::DevPlan& D = h->dp[which];
+// The task list on the current layout, built on the device when the layout
+// changed: cyclic -- one coarse step that the persistent kernel repeats once
+// per step (dp[0]); otherwise `k` coarse steps from a synchronised state
+// (dp[1]).
+vlbm_hier::DevPlan& dev_plan(vlbm_hier* h, int k, bool cyclic) {
+    vlbm_hier::DevPlan& D = h->dp[cyclic ? 0 : 1];
+    if (cyclic) k = 1;
     D.build_kernels = 0;
     cudaStream_t s = h->stream;
     if (D.steps != k) {
@@ -1569,7 +1573,8 @@ vlbm_hier::DevPlan& dev_plan(vlbm_hier* h, int which, int k) {
             if (P.kind == 0 && P.l < h->nlev) cap += (long long)h->lev[P.l].bx * h->lev[P.l].by;
             if (P.kind == 1 && P.l + 1 < h->nlev) cap += (long long)h->lev[P.l].bx * h->lev[P.l].by;
         }
-        if (cap >= (1LL << 31) - 1) throw Fail{VLBM_ERR_ARG, "hierarchy too large for one task list"};
+        // a cyclic list's tickets (tasks x iterations, up to 64) are ints too
+        if (cap >= ((1LL << 31) - 1) / (cyclic ? 64 : 1)) throw Fail{VLBM_ERR_ARG, "hierarchy too large for one task list"};
         if (acc.empty()) acc.push_back(TBAcc{0, 0, 0});
         D.ph.upload(h->mem, ph, s);
         D.acc.upload(h->mem, acc, s);
@@ -1590,12 +1595,13 @@ vlbm_hier::DevPlan& dev_plan(vlbm_hier* h, int which, int k) {
         D.deps.ensure(h->mem, (size_t)D.dep_cap);
         D.need.ensure(h->mem, 8);
         D.big.ensure(h->mem, (size_t)cap + 1);
-        const bool fresh = D.done.cap < (size_t)cap + 1;
+        // completion marks restart with the epoch below: a mark left from
+        // before the restart could otherwise pass for a later epoch's
         D.done.ensure(h->mem, (size_t)cap + 1);
-        if (fresh) VCK(cudaMemsetAsync(D.done.p, 0, D.done.cap * sizeof(unsigned), s));
+        VCK(cudaMemsetAsync(D.done.p, 0, D.done.cap * sizeof(unsigned), s));
         // the launch's segment and control words (the builder fills in the
-        // task count; the epoch only ever grows, so completion marks left by
-        // earlier launches never match)
+        // task count; from here on the epoch only grows, so the marks that
+        // launches of this plan leave stay below every later launch's)
         Segment sg{};
         sg.tasks = D.tasks.p;
         sg.deps = D.deps.p;
@@ -1625,6 +1631,7 @@ vlbm_hier::DevPlan& dev_plan(vlbm_hier* h, int which, int k) {
         P.nlev = h->nlev;
         P.nphase = D.nphase;
         P.nacc = D.nacc;
+        P.cyclic = cyclic ? 1 : 0;
         for (int l = 0; l < h->nlev; l++) {
             const LayoutDev& L = h->lev[l].dl;
             P.lev[l] = TBLevel{L.nx, L.ny, L.bx, L.by, L.px, L.py, L.list[LST_ACT], L.list[LST_RING],
@@ -1655,29 +1662,33 @@ vlbm_hier::DevPlan& dev_plan(vlbm_hier* h, int which, int k) {
     return D;
 }
 
-// ... and the graph of its persistent launch.
-cudaGraphExec_t dev_task_graph(vlbm_hier* h, int which, int k) {
-    vlbm_hier::DevPlan& D = dev_plan(h, which, k);
+// ... and the graph of its persistent launch: the cyclic list, `iters`
+// coarse steps ([which]: 0 one step, 1 G steps).
+cudaGraphExec_t dev_task_graph(vlbm_hier* h, int which, int iters) {
+    vlbm_hier::DevPlan& D = dev_plan(h, 1, true);
     cudaStream_t s = h->stream;
-    std::vector<uintptr_t> key = {(uintptr_t)h->atab.p, (uintptr_t)D.seg.p, (uintptr_t)D.prefix.p, (uintptr_t)D.ctl.p,
-                                  (uintptr_t)h->tune.variant, (uintptr_t)h->tune.max_ctas};
-    if (!D.exec || key != D.key) {
+    std::vector<uintptr_t> key = {(uintptr_t)h->atab.p,         (uintptr_t)D.seg.p,          (uintptr_t)D.prefix.p,
+                                  (uintptr_t)D.ctl.p,           (uintptr_t)h->tune.variant, (uintptr_t)h->tune.max_ctas,
+                                  (uintptr_t)iters};
+    cudaGraphExec_t& ex = D.exec[which];
+    if (!ex || key != D.key[which]) {
         const auto t0 = std::chrono::steady_clock::now();
-        if (D.exec) cudaGraphExecDestroy(D.exec);
-        D.exec = nullptr;
+        if (ex) cudaGraphExecDestroy(ex);
+        ex = nullptr;
         cudaGraph_t g = nullptr;
         VCK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaMemsetAsync(D.ctl.p, 0, 2 * sizeof(int), s);  // claim and finish counters
-        if (e == cudaSuccess) e = launch_tasks(h->atab.p, D.seg.p, D.prefix.p, D.ctl.p, h->tune.variant, h->tune.max_ctas, s);
+        if (e == cudaSuccess)
+            e = launch_tasks(h->atab.p, D.seg.p, D.prefix.p, D.ctl.p, h->tune.variant, h->tune.max_ctas, iters, s);
         cudaError_t e2 = cudaStreamEndCapture(s, &g);
         if (e == cudaSuccess) e = e2;
-        if (e == cudaSuccess) e = instantiate(&D.exec, g);
+        if (e == cudaSuccess) e = instantiate(&ex, g);
         if (g) cudaGraphDestroy(g);
         VCK(e);
-        D.key = key;
+        D.key[which] = key;
         h->times[VLBM_T_CAPTURE] += ms_since(t0);
     }
-    return D.exec;
+    return ex;
 }
 
 // One launch per level phase over the device lists (the per-phase schedule,
@@ -1739,7 +1750,7 @@ void dev_advance(vlbm_hier* h, long long n, int sched) {
     long long left = n;
     if (left >= G) {
         cudaGraphExec_t ex = sched == 1 ? dev_task_graph(h, 1, G) : dev_phase_graph(h, 1, G);
-        if (sched == 1) h->klaunch += h->dp[1].build_kernels;  // a task list build, if one was queued
+        if (sched == 1) h->klaunch += h->dp[0].build_kernels;  // a task list build, if one was queued
         const long long nk = graph_kernels(ex);
         for (; left >= G; left -= G) {
             VCK(cudaGraphLaunch(ex, s));
@@ -1761,9 +1772,11 @@ void dev_advance(vlbm_hier* h, long long n, int sched) {
 
 void release_dev_plans(vlbm_hier* h) {
     for (auto& D : h->dp) {
-        if (D.exec) cudaGraphExecDestroy(D.exec);
-        D.exec = nullptr;
-        D.key.clear();
+        for (int w = 0; w < 2; w++) {
+            if (D.exec[w]) cudaGraphExecDestroy(D.exec[w]);
+            D.exec[w] = nullptr;
+            D.key[w].clear();
+        }
         for (DArr<int>* a : {&D.acc_beg, &D.acc_pos, &D.off, &D.deps, &D.need, &D.prefix, &D.ctl, &D.big})
             a->release(h->mem);
         D.ph.release(h->mem);
@@ -2595,7 +2608,8 @@ vlbm_status vlbm_selftest_layout(uint64_t seed, int32_t cases, int64_t* mismatch
                 h->host_ok = false;
                 layout_changed(h);
                 const int k = 1 + (int)(rnd() % 3);
-                vlbm_hier::DevPlan& D = dev_plan(h, 1, k);
+                dev_plan(h, k, false);
+                dev_plan(h, 1, true);
                 VCK(cudaStreamSynchronize(h->stream));
                 int stw[2];
                 VCK(cudaMemcpy(stw, h->words, sizeof stw, cudaMemcpyDeviceToHost));
@@ -2641,35 +2655,57 @@ vlbm_status vlbm_selftest_layout(uint64_t seed, int32_t cases, int64_t* mismatch
                     lv[l].recon = &tl[l].recon;
                 }
                 // task lists: the host builder against the device's
+                auto compare_list = [&](const vlbm_hier::DevPlan& D, const std::vector<Task>& wt,
+                                        const std::vector<int>& wd, int step_shift, const char* what) {
+                    int need[5];
+                    VCK(cudaMemcpy(need, D.need.p, sizeof need, cudaMemcpyDeviceToHost));
+                    if (second_pass) *second_pass += need[4];
+                    if (need[0] != (int)wt.size()) {
+                        bad(std::string(what) + ": task count " + std::to_string(need[0]) + " vs " +
+                            std::to_string(wt.size()));
+                        return;
+                    }
+                    std::vector<Task> gt(wt.size());
+                    if (!gt.empty())
+                        VCK(cudaMemcpy(gt.data(), D.tasks.p, gt.size() * sizeof(Task), cudaMemcpyDeviceToHost));
+                    // the dependency array as far as any task's slot reaches
+                    long long reach = 0;
+                    for (const Task& T : gt) reach = std::max(reach, (long long)T.dep0 + T.ndep);
+                    std::vector<int> gd((size_t)reach);
+                    if (reach) VCK(cudaMemcpy(gd.data(), D.deps.p, (size_t)reach * sizeof(int), cudaMemcpyDeviceToHost));
+                    for (size_t i = 0; i < gt.size(); i++) {
+                        const Task &x = gt[i], &y = wt[i];
+                        const int ya = y.kind == 0 ? -1 : y.aslot;  // no audit slots on the device lists
+                        bool same = x.lid == y.lid && x.tx == y.tx && x.ty == y.ty && x.kind == y.kind && x.kk == y.kk &&
+                                    x.kkp == y.kkp && x.step + step_shift == y.step && x.ndep == y.ndep && x.aslot == ya;
+                        for (int q = 0; same && q < x.ndep; q++) same = gd[x.dep0 + q] == wd[y.dep0 + q];
+                        if (!same) {
+                            bad(std::string(what) + ": task " + std::to_string(i) + " of " + std::to_string(gt.size()) +
+                                " (kind " + std::to_string(y.kind) + ", level " + std::to_string(y.lid) + ", ndep " +
+                                std::to_string(x.ndep) + " vs " + std::to_string(y.ndep) + ")");
+                            break;
+                        }
+                    }
+                };
                 TaskLists want;
                 build_tasks(lv, k, want);
-                int need[5];
-                VCK(cudaMemcpy(need, D.need.p, sizeof need, cudaMemcpyDeviceToHost));
-                if (second_pass) *second_pass += need[4];
-                if (need[0] != (int)want.t.size()) {
-                    bad("task count " + std::to_string(need[0]) + " vs " + std::to_string(want.t.size()));
-                    continue;
+                compare_list(h->dp[1], want.t, want.d, 0, "k-step list");
+                // the cyclic one-step list is the second step of a two-step
+                // list from a synchronised state: dependencies into its first
+                // step become ~index, those within it lose the step's offset
+                TaskLists two;
+                build_tasks(lv, 2, two);
+                const int m = (int)two.t.size() / 2;
+                std::vector<Task> ct(two.t.begin() + m, two.t.end());
+                std::vector<int> cd;
+                for (Task& T : ct) {
+                    std::vector<int> v(two.d.begin() + T.dep0, two.d.begin() + T.dep0 + T.ndep);
+                    for (int& d : v) d = d >= m ? d - m : ~d;
+                    std::sort(v.begin(), v.end());
+                    T.dep0 = (int)cd.size();
+                    cd.insert(cd.end(), v.begin(), v.end());
                 }
-                std::vector<Task> gt(want.t.size());
-                if (!gt.empty()) VCK(cudaMemcpy(gt.data(), D.tasks.p, gt.size() * sizeof(Task), cudaMemcpyDeviceToHost));
-                // the dependency array as far as any task's slot reaches
-                long long reach = 0;
-                for (const Task& T : gt) reach = std::max(reach, (long long)T.dep0 + T.ndep);
-                std::vector<int> gd((size_t)reach);
-                if (reach) VCK(cudaMemcpy(gd.data(), D.deps.p, (size_t)reach * sizeof(int), cudaMemcpyDeviceToHost));
-                for (size_t i = 0; i < gt.size(); i++) {
-                    const Task &x = gt[i], &y = want.t[i];
-                    const int ya = y.kind == 0 ? -1 : y.aslot;  // no audit slots on the device lists
-                    bool same = x.lid == y.lid && x.tx == y.tx && x.ty == y.ty && x.kind == y.kind && x.kk == y.kk &&
-                                x.kkp == y.kkp && x.step == y.step && x.ndep == y.ndep && x.aslot == ya;
-                    for (int q = 0; same && q < x.ndep; q++) same = gd[x.dep0 + q] == want.d[y.dep0 + q];
-                    if (!same) {
-                        bad("task " + std::to_string(i) + " of " + std::to_string(gt.size()) + " (kind " +
-                            std::to_string(y.kind) + ", level " + std::to_string(y.lid) + ", ndep " +
-                            std::to_string(x.ndep) + " vs " + std::to_string(y.ndep) + ")");
-                        break;
-                    }
-                }
+                compare_list(h->dp[0], ct, cd, 1, "cyclic list");
             }
         });
         vlbm_destroy(h);

@@ -621,13 +621,19 @@ __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Completion marks: a task of launch epoch e is complete when its mark holds
+// 2 e.  Marks only grow (a mark left by an earlier launch, of this task list
+// or of one built before it, is at most 2 (e - 1)), so a kernel never
+// mistakes a stale mark for completion and no mark is ever reset between
+// launches, whichever task kernel ran them.
+//
 // Bounded wait on a task's completion mark: gives up after ~2^21 polls
 // (about a second), records a timeout in the hierarchy's status word and
 // returns, so that a broken schedule can never hang the GPU.
-__device__ __forceinline__ void wait_done(const unsigned* p, unsigned epoch, int* status) {
+__device__ __forceinline__ void wait_done(const unsigned* p, unsigned mark, int* status) {
     unsigned ns = 32;
     for (int it = 0; it < (1 << 21); it++) {
-        if (ld_acquire(p) == epoch) return;
+        if ((int)(ld_acquire(p) - mark) >= 0) return;
         // once any wait of this hierarchy has given up, stop waiting at all
         if ((it & 255) == 255 && (*(volatile int*)status & ST_TIMEOUT)) return;
         __nanosleep(ns);
@@ -661,27 +667,46 @@ __device__ __forceinline__ int find_segment(const int* __restrict__ prefix, int 
 // through L2 (ld.global.cg, cp.async.cg).
 
 
+// Iterations: a launch runs its task list `iters` times in a row, one coarse
+// step per iteration (iters > 1 only for a one-step list of one hierarchy).
+// Ticket t is task t % total of iteration t / total; iteration it of launch
+// epoch e completes a task with mark 2 (e + it).  A dependency entry d >= 0
+// is task d of the same iteration; d < 0 is task ~d of the previous
+// iteration, satisfied by stream order in the launch's first iteration.
+__device__ __forceinline__ void wait_deps(const Segment& S, const Task& T, int it, unsigned mark, int lane, int width,
+                                          int* status) {
+    for (int j = lane; j < T.ndep; j += width) {
+        const int d = S.deps[T.dep0 + j];
+        if (d >= 0) wait_done(S.done + d, mark, status);
+        else if (it > 0) wait_done(S.done + ~d, mark - 2u, status);
+    }
+}
+
 template <int P, int MINB>
 __global__ void __launch_bounds__(CTA_THREADS, MINB)
 task_kernel(const LevelDev* __restrict__ levs, const Segment* __restrict__ segs, const int* __restrict__ prefix,
-            int* ctl) {
+            int* ctl, int iters) {
     __shared__ int s_task[TILES_PER_CTA][2];
     const int g = threadIdx.x >> 6;
     const int lt = threadIdx.x & 63;
     const int cx = lt & 7, cy = lt >> 3;
     const unsigned epoch = (unsigned)ctl[CTL_EPOCH];
     const int total = ctl[CTL_TOTAL], nseg = ctl[CTL_NSEG];
+    const int tickets = total * iters;
     if (lt == 0) s_task[g][0] = atomicAdd(&ctl[CTL_CLAIM], 1);
     group_bar(g);
     for (int par = 0;; par ^= 1) {
         const int t = s_task[g][par];
-        if (t >= total) break;
-        const int sg = find_segment(prefix, nseg, t);
+        if (t >= tickets) break;
+        const int it = t / total, tt = t - it * total;
+        const int sg = find_segment(prefix, nseg, tt);
         const Segment S = segs[sg];
-        const int i = t - prefix[sg];
+        const int i = tt - prefix[sg];
         const Task T = S.tasks[i];
         const LevelDev& L = levs[T.lid + S.lid_base];
-        for (int j = lt; j < T.ndep; j += 64) wait_done(S.done + S.deps[T.dep0 + j], epoch, L.status);
+        const unsigned mark = 2u * (epoch + (unsigned)it);
+        const int step = T.step + it;
+        wait_deps(S, T, it, mark, lt, 64, L.status);
         if (lt == 0) s_task[g][par ^ 1] = atomicAdd(&ctl[CTL_CLAIM], 1);
         group_bar(g);
         if (T.kind == 0) {
@@ -689,27 +714,27 @@ task_kernel(const LevelDev* __restrict__ levs, const Segment* __restrict__ segs,
                 // audited sweep: keep the moments of the cell (0 off the
                 // active set) for the exact reduction after the launch
                 double W[4] = {0.0, 0.0, 0.0, 0.0};
-                sweep_cell<P, true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.kkp, T.step, W);
+                sweep_cell<P, true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.kkp, step, W);
                 double* o = S.aw + (size_t)T.aslot * AUDIT_SLOT + lt;
                 for (int k = 0; k < 4; k++) o[k * 64] = W[k];
             } else {
-                sweep_cell<P, true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.kkp, T.step);
+                sweep_cell<P, true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.kkp, step);
             }
         } else if (T.kind == 1) {
-            close_cell<true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.step);
+            close_cell<true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, step);
         } else {
             audit_task(S, T, g, lt);
         }
         group_bar(g);
         if (lt == 0) {
             __threadfence();
-            st_release(S.done + i, epoch);
-            if (atomicAdd(&ctl[CTL_FIN], 1) == total - 1) {
+            st_release(S.done + i, mark);
+            if (atomicAdd(&ctl[CTL_FIN], 1) == tickets - 1) {
                 // every task of the launch is complete: advance the parity of
                 // each hierarchy by the launch's step count, open the next epoch
-                if (ctl[CTL_FLIP])
+                if (ctl[CTL_FLIP] && (iters & 1))
                     for (int m = 0; m < nseg; m++) *segs[m].par0 ^= 1;
-                ctl[CTL_EPOCH] = (int)(epoch + 1);
+                ctl[CTL_EPOCH] = (int)(epoch + (unsigned)iters);
             }
         }
     }
@@ -717,55 +742,61 @@ task_kernel(const LevelDev* __restrict__ levs, const Segment* __restrict__ segs,
 
 // TK_HALF: the same schedule with every warp on its own -- a task (tile) is
 // two half-tasks of four rows, claimed as tickets 2 t and 2 t + 1 by any
-// two warps; each warp waits for the task's dependencies itself and
-// publishes its half by adding 1 to the task's mark, so a task of launch
-// epoch e is complete when its mark reaches 2 e.  No group barrier is left
-// in the loop.  Deadlock freedom is unchanged: the halves of every task a
-// half waits for were claimed before it.
+// two warps; each warp waits for the task's dependencies itself.  The first
+// half to finish raises the task's mark to 2 e - 1, the second (which sees
+// 2 e - 1 there) publishes 2 e.  No group barrier is left in the loop.
+// Deadlock freedom is unchanged: the halves of every task a half waits for
+// were claimed before it.
 template <int P, int MINB>
 __global__ void __launch_bounds__(CTA_THREADS, MINB)
 task_kernel_half(const LevelDev* __restrict__ levs, const Segment* __restrict__ segs,
-                 const int* __restrict__ prefix, int* ctl) {
+                 const int* __restrict__ prefix, int* ctl, int iters) {
     const int lane = threadIdx.x & 31;
     const unsigned epoch = (unsigned)ctl[CTL_EPOCH];
     const int total = ctl[CTL_TOTAL], nseg = ctl[CTL_NSEG];
-    const unsigned mark = 2u * epoch;
+    const int tickets = 2 * total * iters;
     for (;;) {
         int h = 0;
         if (lane == 0) h = atomicAdd(&ctl[CTL_CLAIM], 1);
         h = __shfl_sync(0xffffffffu, h, 0);
-        if (h >= 2 * total) break;
+        if (h >= tickets) break;
         const int t = h >> 1, half = h & 1;
-        const int sg = find_segment(prefix, nseg, t);
+        const int it = t / total, tt = t - it * total;
+        const int sg = find_segment(prefix, nseg, tt);
         const Segment S = segs[sg];
-        const int i = t - prefix[sg];
+        const int i = tt - prefix[sg];
         const Task T = S.tasks[i];
         const LevelDev& L = levs[T.lid + S.lid_base];
-        for (int j = lane; j < T.ndep; j += 32) wait_done(S.done + S.deps[T.dep0 + j], mark, L.status);
+        const unsigned mark = 2u * (epoch + (unsigned)it);
+        const int step = T.step + it;
+        wait_deps(S, T, it, mark, lane, 32, L.status);
         __syncwarp();
         const int cx = lane & 7, cy = half * 4 + (lane >> 3), lt = cy * 8 + cx;
         if (T.kind == 0) {
             if (S.aw && T.aslot >= 0) {
                 double W[4] = {0.0, 0.0, 0.0, 0.0};
-                sweep_cell<P, true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.kkp, T.step, W);
+                sweep_cell<P, true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.kkp, step, W);
                 double* o = S.aw + (size_t)T.aslot * AUDIT_SLOT + lt;
                 for (int k = 0; k < 4; k++) o[k * 64] = W[k];
             } else {
-                sweep_cell<P, true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.kkp, T.step);
+                sweep_cell<P, true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.kkp, step);
             }
         } else if (T.kind == 1) {
-            close_cell<true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.step);
+            close_cell<true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, step);
         } else if (half == 0) {  // the first half does the whole audit task
             audit_task_warp(S, T, lane);
         }
         __syncwarp();
         if (lane == 0) {
             __threadfence();
-            atomicAdd(S.done + i, 1u);
-            if (atomicAdd(&ctl[CTL_FIN], 1) == 2 * total - 1) {
-                if (ctl[CTL_FLIP])
+            if (atomicMax(S.done + i, mark - 1u) == mark - 1u) {
+                __threadfence();
+                st_release(S.done + i, mark);
+            }
+            if (atomicAdd(&ctl[CTL_FIN], 1) == tickets - 1) {
+                if (ctl[CTL_FLIP] && (iters & 1))
                     for (int m = 0; m < nseg; m++) *segs[m].par0 ^= 1;
-                ctl[CTL_EPOCH] = (int)(epoch + 1);
+                ctl[CTL_EPOCH] = (int)(epoch + (unsigned)iters);
             }
         }
     }
@@ -1313,12 +1344,12 @@ int task_variant_per_sm() {
 }
 
 template <int P, int B>
-void task_variant_launch(int g, const LevelDev* levs, const Segment* segs, const int* prefix, int* ctl,
+void task_variant_launch(int g, const LevelDev* levs, const Segment* segs, const int* prefix, int* ctl, int iters,
                          cudaStream_t s) {
     if constexpr ((P & TK_HALF) != 0)
-        task_kernel_half<P, B><<<g, CTA_THREADS, 0, s>>>(levs, segs, prefix, ctl);
+        task_kernel_half<P, B><<<g, CTA_THREADS, 0, s>>>(levs, segs, prefix, ctl, iters);
     else
-        task_kernel<P, B><<<g, CTA_THREADS, 0, s>>>(levs, segs, prefix, ctl);
+        task_kernel<P, B><<<g, CTA_THREADS, 0, s>>>(levs, segs, prefix, ctl, iters);
 }
 
 int task_kernel_ctas(int variant) {
@@ -1338,11 +1369,12 @@ int task_kernel_ctas(int variant) {
 }
 
 cudaError_t launch_tasks(const LevelDev* levs, const Segment* segs, const int* prefix, int* ctl, int variant, int ctas,
-                         cudaStream_t s) {
+                         int iters, cudaStream_t s) {
+    if (iters < 1) return cudaErrorInvalidValue;
     const int full = task_kernel_ctas(variant);  // also sets the kernel's shared-memory attributes
     const int g = ctas > 0 ? std::min(ctas, full) : full;
     switch (variant) {
-#define X(id, P, B) case id: task_variant_launch<P, B>(g, levs, segs, prefix, ctl, s); break;
+#define X(id, P, B) case id: task_variant_launch<P, B>(g, levs, segs, prefix, ctl, iters, s); break;
         VLBM_SWEEP_VARIANTS(X)
 #undef X
         default: return cudaErrorInvalidValue;

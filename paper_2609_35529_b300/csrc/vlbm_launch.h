@@ -15,8 +15,10 @@ cudaError_t launch_sensor(const LevelDev* levs, const Item* items, int n, int kk
                           const int* nc = nullptr);
 int sweep_variants();
 int task_kernel_ctas(int variant);
+// The persistent task kernel over the segments' task lists, `iters` times in
+// a row (one coarse step per iteration of a one-step list; 1 otherwise).
 cudaError_t launch_tasks(const LevelDev* levs, const Segment* segs, const int* prefix, int* ctl, int variant, int ctas,
-                         cudaStream_t s);
+                         int iters, cudaStream_t s);
 cudaError_t launch_audit_segments(const unsigned long long* slots, const int* seg, int nseg, double* out,
                                   cudaStream_t s);
 cudaError_t launch_close(const LevelDev* levs, const Item* items, int n, int kk, cudaStream_t s,

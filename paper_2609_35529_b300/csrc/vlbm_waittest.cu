@@ -68,7 +68,7 @@ extern "C" vlbm_status vlbm_selftest_timeout(double* elapsed_ms, int32_t* status
         h.lev.plane = TILE * TILE;
         h.lev.parent = h.lev.child = -1;
         if (ck(cudaMemcpyAsync(d, &h, sizeof h, cudaMemcpyHostToDevice, s)) && ck(cudaEventRecord(e0, s)) &&
-            ck(launch_tasks(&d->lev, &d->seg, d->prefix, d->ctl, 1, 1, s)) && ck(cudaEventRecord(e1, s)) &&
+            ck(launch_tasks(&d->lev, &d->seg, d->prefix, d->ctl, 1, 1, 1, s)) && ck(cudaEventRecord(e1, s)) &&
             ck(cudaStreamSynchronize(s))) {
             int w[2] = {0, 0};
             float ms = 0.f;

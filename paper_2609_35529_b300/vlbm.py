@@ -445,7 +445,7 @@ def selftest_rcp(seed, n):
 def selftest_layout(seed, cases):
     """Device-resident layouts against the host's layout rule, tile lists and
     task builder on seeded random hierarchies; returns (mismatches, tasks
-    that took the builder's second pass, first difference)."""
+    stored in the overflow area, first difference)."""
     bad = C.c_int64()
     big = C.c_int64()
     buf = C.create_string_buffer(512)

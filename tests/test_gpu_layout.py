@@ -30,7 +30,7 @@ def test_device_layouts_and_task_lists_equal_the_host_builders(V, seed):
     element for element."""
     bad, big, first = V.selftest_layout(seed, 40)
     assert bad == 0, first
-    assert big > 0  # some dense random layouts exercise the builder's second pass
+    assert big > 0  # some dense random layouts fill the overflow area
 
 
 @pytest.mark.parametrize("schedule", [1, 0, 2])
@@ -105,4 +105,28 @@ def test_device_regrid_nesting_and_layout_reads(V):
     compare(o, g, 3)
     g.restore(blob)
     g.advance(4)
+    compare(o, g, 3)
+
+
+def test_task_kernels_share_completion_marks(V):
+    """The persistent schedule switching between whole-tile and half-tile
+    task kernels on the same device-built task list, and task lists that grow
+    between regrids: completion marks left by either kernel never stall the
+    other (a stale mark is always below the launch's), results bit for bit
+    the oracle's."""
+    cs = I.shockbubble(nx0=128, ny0=64, nlev=3)
+    tol, buf, every = cs.amr["tol"], cs.amr["buffer"], cs.amr["every"]
+    g = V.Hierarchy.from_case(cs)
+    o = oracle_of(cs)
+    for _ in range(2):
+        g.regrid()
+        o.regrid_tagged(tol, buf, 8)
+    for cycle, var in enumerate([1, 3, 4, 0, 3, 2, 4, 1]):
+        g.set_tuning(variant=var, schedule=1, graph_steps=every if cycle % 2 else 2, persist_after=0)
+        g.advance(every)
+        o.advance(every)
+        if cycle % 3 != 2:  # some layouts live through a variant switch
+            g.regrid()
+            o.regrid_tagged(tol, buf, 8)
+    g.sync()
     compare(o, g, 3)

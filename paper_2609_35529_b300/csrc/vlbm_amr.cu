@@ -117,12 +117,23 @@ __global__ void derive_in_kernel(LayoutDev P, LayoutDev L, int level0) {
     }
 }
 
-__global__ void nest_check_kernel(LayoutDev L, int finest, int* status) {
-    const long long nb = (long long)L.bx * L.by;
+// The level of flat block index b of a set and the block's index on it.
+__device__ __forceinline__ int set_level(const LayoutSet& S, long long& b) {
+    int l = 0;
+    while (l + 1 < S.nl && b >= S.b0[l + 1]) l++;
+    b -= S.b0[l];
+    return l;
+}
+
+__global__ void nest_check_kernel(LayoutSet S, int* status) {
     bool bad = false;
-    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb; b += (long long)gridDim.x * blockDim.x) {
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < S.b0[S.nl];
+         g += (long long)gridDim.x * blockDim.x) {
+        long long b = g;
+        const int l = set_level(S, b);
+        const LayoutDev& L = S.L[l];
         if (!L.ncov[b]) continue;
-        if (finest || !L.nin[b]) {
+        if (l == S.nl - 1 || !L.nin[b]) {
             bad = true;
             continue;
         }
@@ -138,9 +149,11 @@ __global__ void nest_check_kernel(LayoutDev L, int finest, int* status) {
     if (bad) atomicOr(status, ST_NESTING);
 }
 
-__global__ void commit_maps_kernel(LayoutDev L) {
-    const long long nb = (long long)L.bx * L.by;
-    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb; b += (long long)gridDim.x * blockDim.x) {
+__global__ void commit_maps_kernel(LayoutSet S) {
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < S.b0[S.nl];
+         g += (long long)gridDim.x * blockDim.x) {
+        long long b = g;
+        const LayoutDev& L = S.L[set_level(S, b)];
         L.bin[b] = L.nin[b];
         L.bcov[b] = L.ncov[b];
     }
@@ -188,10 +201,21 @@ __device__ __forceinline__ Member member(const LayoutDev& L, long long b) {
     return m;
 }
 
-__global__ void lists_count_kernel(LayoutDev L, int mask) {
+// The level of the set's chunk (CTA) c and the chunk's index on it.
+__device__ __forceinline__ int chunk_level(const LayoutSet& S, int& c) {
+    int l = 0;
+    while (l + 1 < S.nl && c >= S.c0[l + 1]) l++;
+    c -= S.c0[l];
+    return l;
+}
+
+__global__ void lists_count_kernel(LayoutSet S) {
     __shared__ int sm[32];
+    int c = blockIdx.x;
+    const int l = chunk_level(S, c);
+    const LayoutDev& L = S.L[l];
+    const int mask = S.mask[l];
     const long long nb = (long long)L.bx * L.by;
-    const int c = blockIdx.x;
     int n[NLST] = {};
     for (int e = 0; e < LIST_E; e++) {
         const long long b = (long long)c * LAY_CHUNK + threadIdx.x * LIST_E + e;
@@ -207,12 +231,13 @@ __global__ void lists_count_kernel(LayoutDev L, int mask) {
     }
 }
 
-// one CTA per list: exclusive chunk offsets, the list length, and (act) the
-// reset of the active cell count
-__global__ void lists_scan_kernel(LayoutDev L, int mask) {
+// one CTA per (level, list): exclusive chunk offsets, the list length, and
+// (act) the reset of the active cell count
+__global__ void lists_scan_kernel(LayoutSet S) {
     __shared__ int sm[32];
-    const int k = blockIdx.x;
-    if (!(mask >> k & 1)) return;
+    const int l = blockIdx.x / NLST, k = blockIdx.x % NLST;
+    const LayoutDev& L = S.L[l];
+    if (!(S.mask[l] >> k & 1)) return;
     int carry = 0;
     for (int b = 0; b < L.nchunk; b += blockDim.x) {
         const int i = b + threadIdx.x;
@@ -228,10 +253,13 @@ __global__ void lists_scan_kernel(LayoutDev L, int mask) {
     }
 }
 
-__global__ void lists_scatter_kernel(LayoutDev L, int mask, int lid) {
+__global__ void lists_scatter_kernel(LayoutSet S) {
     __shared__ int sm[32];
+    int c = blockIdx.x;
+    const int lid = chunk_level(S, c);
+    const LayoutDev& L = S.L[lid];
+    const int mask = S.mask[lid];
     const long long nb = (long long)L.bx * L.by;
-    const int c = blockIdx.x;
     Member m[LIST_E];
     int n[NLST] = {};
     for (int e = 0; e < LIST_E; e++) {
@@ -274,10 +302,15 @@ __global__ void lists_scatter_kernel(LayoutDev L, int mask, int lid) {
 
 // bit 0: some sweep of the level pushes into the block (an active block
 // among the block and its four face neighbours, by the push targets of the
-// task builder); bit 1: a reflux close writes it (a ring block)
-__global__ void wmask_kernel(LayoutDev L) {
-    const long long nb = (long long)L.bx * L.by;
-    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb; b += (long long)gridDim.x * blockDim.x) {
+// task builder); bit 1: a reflux close writes it (a ring block).  For the
+// levels whose lists included the active one.
+__global__ void wmask_kernel(LayoutSet S) {
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < S.b0[S.nl];
+         g += (long long)gridDim.x * blockDim.x) {
+        long long b = g;
+        const int l = set_level(S, b);
+        if (!((S.mask[l] >> LST_ACT) & 1)) continue;
+        const LayoutDev& L = S.L[l];
         const int tx = (int)(b % L.bx), ty = (int)(b / L.bx);
         const int sdi[5] = {0, 1, -1, 0, 0}, sdj[5] = {0, 0, 0, 1, -1};
         uint8_t m = 0;
@@ -835,22 +868,39 @@ cudaError_t launch_derive_in(const LayoutDev* P, const LayoutDev& L, cudaStream_
     return cudaGetLastError();
 }
 
-cudaError_t launch_nest_check(const LayoutDev& L, bool finest, int* status, cudaStream_t s) {
-    nest_check_kernel<<<flat_blocks((long long)L.bx * L.by), 256, 0, s>>>(L, finest, status);
+LayoutSet layout_set(const LayoutDev* const* levs, const int* masks, int nl) {
+    LayoutSet S{};
+    S.nl = nl;
+    for (int l = 0; l < nl; l++) {
+        S.L[l] = *levs[l];
+        S.mask[l] = masks ? masks[l] : 0;
+        S.c0[l + 1] = S.c0[l] + levs[l]->nchunk;
+        S.b0[l + 1] = S.b0[l] + (long long)levs[l]->bx * levs[l]->by;
+    }
+    return S;
+}
+
+cudaError_t launch_nest_check(const LayoutDev* const* levs, int nl, int* status, cudaStream_t s) {
+    const LayoutSet S = layout_set(levs, nullptr, nl);
+    nest_check_kernel<<<flat_blocks(S.b0[nl]), 256, 0, s>>>(S, status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_commit_maps(const LayoutDev& L, cudaStream_t s) {
-    commit_maps_kernel<<<flat_blocks((long long)L.bx * L.by), 256, 0, s>>>(L);
+cudaError_t launch_commit_maps(const LayoutDev* const* levs, int nl, cudaStream_t s) {
+    const LayoutSet S = layout_set(levs, nullptr, nl);
+    commit_maps_kernel<<<flat_blocks(S.b0[nl]), 256, 0, s>>>(S);
     return cudaGetLastError();
 }
 
-cudaError_t launch_lists(const LayoutDev& L, int mask, int lid, cudaStream_t s) {
-    if (L.nchunk <= 0) return cudaSuccess;
-    lists_count_kernel<<<L.nchunk, LIST_T, 0, s>>>(L, mask);
-    lists_scan_kernel<<<NLST, 1024, 0, s>>>(L, mask);
-    lists_scatter_kernel<<<L.nchunk, LIST_T, 0, s>>>(L, mask, lid);
-    if ((mask >> LST_ACT) & 1) wmask_kernel<<<flat_blocks((long long)L.bx * L.by), 256, 0, s>>>(L);
+cudaError_t launch_lists(const LayoutDev* const* levs, const int* masks, int nl, cudaStream_t s) {
+    const LayoutSet S = layout_set(levs, masks, nl);
+    if (S.c0[nl] <= 0) return cudaSuccess;
+    lists_count_kernel<<<S.c0[nl], LIST_T, 0, s>>>(S);
+    lists_scan_kernel<<<NLST * nl, 1024, 0, s>>>(S);
+    lists_scatter_kernel<<<S.c0[nl], LIST_T, 0, s>>>(S);
+    bool act = false;
+    for (int l = 0; l < nl; l++) act = act || ((masks[l] >> LST_ACT) & 1);
+    if (act) wmask_kernel<<<flat_blocks(S.b0[nl]), 256, 0, s>>>(S);
     return cudaGetLastError();
 }
 

@@ -50,6 +50,16 @@ struct LayoutDev {
     int nchunk = 0;
 };
 
+// Up to four levels' layouts for one launch: chunk (CTA) and block offsets
+// of each level in the set.
+struct LayoutSet {
+    LayoutDev L[4];
+    int mask[4];
+    int c0[5];
+    long long b0[5];
+    int nl;
+};
+
 // New covered map of level L (l <= nlev - 2): the flagged blocks plus the
 // blocks holding the parents of the one-cell neighbourhood of the next
 // level's new covered blocks (F: level l + 1 when it is refinable, else
@@ -57,16 +67,19 @@ struct LayoutDev {
 cudaError_t launch_layout_rule(const LayoutDev& L, const LayoutDev* F, const uint8_t* bflag, cudaStream_t s);
 // New on-level map of L from its parent P's new maps (level 0: all blocks).
 cudaError_t launch_derive_in(const LayoutDev* P, const LayoutDev& L, cudaStream_t s);
-// Proper nesting of the new maps of L (covered blocks on the level, none on
-// the finest level, covered blocks of levels >= 1 with their four face
-// neighbours on the level); a violation sets ST_NESTING in *status.
-cudaError_t launch_nest_check(const LayoutDev& L, bool finest, int* status, cudaStream_t s);
-// Lists of L selected by `mask` (bits 1 << LST_*): act, ring, cov, in from
-// the current maps (with recon, act_idx, ring_idx and cells), exit and enter
-// from the current against the new maps.  Items carry lid.
-cudaError_t launch_lists(const LayoutDev& L, int mask, int lid, cudaStream_t s);
-// Copies the new maps over the current ones.
-cudaError_t launch_commit_maps(const LayoutDev& L, cudaStream_t s);
+// Proper nesting of the new maps of every level (covered blocks on the
+// level, none on the finest level -- the last of the set --, covered blocks
+// of levels >= 1 with their four face neighbours on the level); a violation
+// sets ST_NESTING in *status.
+cudaError_t launch_nest_check(const LayoutDev* const* levs, int nl, int* status, cudaStream_t s);
+// Lists of each level l selected by masks[l] (bits 1 << LST_*): act, ring,
+// cov, in from the current maps (with recon, act_idx, ring_idx, cells and
+// the write masks), exit and enter from the current against the new maps,
+// touch (on the level under either).  Items carry the level index.  Every
+// level in the same three or four launches.
+cudaError_t launch_lists(const LayoutDev* const* levs, const int* masks, int nl, cudaStream_t s);
+// Copies the new maps over the current ones, every level.
+cudaError_t launch_commit_maps(const LayoutDev* const* levs, int nl, cudaStream_t s);
 // Reverse footprints of parent level P from the reconstructing tiles of its
 // child level C (after C's lists); an overflow of FOOT_CAP sets ST_TASKCAP.
 cudaError_t launch_footprints(const LayoutDev& P, const LayoutDev& C, int* status, cudaStream_t s);

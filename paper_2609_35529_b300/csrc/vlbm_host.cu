@@ -322,7 +322,7 @@ struct vlbm_hier {
     std::string err = "no error";
     // scratch
     DArr<double> stage;     // W / f staging
-    DArr<uint8_t> stage8;   // valid masks, tags
+    DArr<uint8_t> stage8;   // valid masks
     DArr<unsigned long long> qmax;  // flux-jump sensor: max |Q_k| (bit patterns)
     DArr<unsigned long long> partial;  // audit partial sums (exact, 24 words per block)
     DArr<double> tot;      // audit result
@@ -1098,10 +1098,14 @@ void layout_changed(vlbm_hier* h) {
 // concatenated active tiles of the audits.
 void device_lists(vlbm_hier* h) {
     LayoutDev dls[VLBM_MAX_LEVELS];
+    const LayoutDev* lp[VLBM_MAX_LEVELS];
+    int masks[VLBM_MAX_LEVELS];
     for (int l = 0; l < h->nlev; l++) {
-        VCK(launch_lists(h->lev[l].dl, LISTS_ALL, l, h->stream));
         dls[l] = h->lev[l].dl;
+        lp[l] = &h->lev[l].dl;
+        masks[l] = LISTS_ALL;
     }
+    VCK(launch_lists(lp, masks, h->nlev, h->stream));
     VCK(launch_concat_act(dls, h->nlev, h->ditems, h->dcount, h->stream));
 }
 
@@ -1290,22 +1294,19 @@ void tag_begin(vlbm_hier* h) {
             VCK(launch_qmax(lvdev(h, l), h->listbuf.p, (int)h->listbuf.n, h->qmax.p, s));
         }
     }
-    const int px = h->cfg.bc[0] == VLBM_BC_PERIODIC, py = h->cfg.bc[2] == VLBM_BC_PERIODIC;
     size_t nb = 0;
     for (int l = 0; l <= h->nlev - 2; l++) nb += (size_t)h->lev[l].bx * h->lev[l].by;
     h->bflag.ensure(h->mem, std::max<size_t>(1, nb));
+    VCK(cudaMemsetAsync(h->bflag.p, 0, nb, s));
     size_t off = 0;
     for (int l = 0; l <= h->nlev - 2; l++) {
         Level& L = h->lev[l];
-        h->stage8.ensure(h->mem, (size_t)L.nx * L.ny);
-        VCK(cudaMemsetAsync(h->stage8.p, 0, (size_t)L.nx * L.ny, s));
         h->listbuf.upload(h->mem, L.in, s);
         if (fluxs)
-            VCK(launch_tag_flux(lvdev(h, l), h->listbuf.p, (int)L.in.size(), h->qmax.p, h->cfg.tag_tol, h->stage8.p,
-                                s));
+            VCK(launch_tag_flux(lvdev(h, l), h->listbuf.p, (int)L.in.size(), h->qmax.p, h->cfg.tag_tol,
+                                h->cfg.tag_buffer, h->bflag.p + off, s));
         else
-            VCK(launch_tag(lvdev(h, l), h->listbuf.p, (int)L.in.size(), tol2, h->stage8.p, s));
-        VCK(launch_blockflag(h->stage8.p, L.nx, L.ny, px, py, h->cfg.tag_buffer, h->bflag.p + off, s));
+            VCK(launch_tag(lvdev(h, l), h->listbuf.p, (int)L.in.size(), tol2, h->cfg.tag_buffer, h->bflag.p + off, s));
         off += (size_t)L.bx * L.by;
     }
     // status words first (8 bytes), then the flags
@@ -1362,13 +1363,9 @@ void check_tagging(const vlbm_hier* h) {
 // The scratch of a device regrid at its final size (allocated outside any
 // stream capture).
 void regrid_buffers(vlbm_hier* h) {
-    size_t nb = 0, cells = 1;
-    for (int l = 0; l <= h->nlev - 2; l++) {
-        nb += (size_t)h->lev[l].bx * h->lev[l].by;
-        cells = std::max(cells, (size_t)h->lev[l].nx * h->lev[l].ny);
-    }
+    size_t nb = 0;
+    for (int l = 0; l <= h->nlev - 2; l++) nb += (size_t)h->lev[l].bx * h->lev[l].by;
     h->bflag.ensure(h->mem, std::max<size_t>(1, nb));
-    h->stage8.ensure(h->mem, cells);
     h->qmax.ensure(h->mem, 4);
 }
 
@@ -1391,23 +1388,21 @@ void device_tags(vlbm_hier* h) {
             VCK(launch_qmax(lvdev(h, l), D.list[LST_IN], lcap(D), h->qmax.p, s, D.cnt + LST_IN));
         }
     }
-    const int px = h->cfg.bc[0] == VLBM_BC_PERIODIC, py = h->cfg.bc[2] == VLBM_BC_PERIODIC;
     size_t nb = 0;
     for (int l = 0; l <= nl - 2; l++) nb += (size_t)h->lev[l].bx * h->lev[l].by;
     h->bflag.ensure(h->mem, std::max<size_t>(1, nb));
+    VCK(cudaMemsetAsync(h->bflag.p, 0, nb, s));
     const double tol2 = h->cfg.tag_tol * h->cfg.tag_tol;
     size_t off = 0;
     for (int l = 0; l <= nl - 2; l++) {
         Level& L = h->lev[l];
         const LayoutDev& D = L.dl;
-        h->stage8.ensure(h->mem, (size_t)L.nx * L.ny);
-        VCK(cudaMemsetAsync(h->stage8.p, 0, (size_t)L.nx * L.ny, s));
         if (fluxs)
-            VCK(launch_tag_flux(lvdev(h, l), D.list[LST_IN], lcap(D), h->qmax.p, h->cfg.tag_tol, h->stage8.p, s,
-                                D.cnt + LST_IN));
+            VCK(launch_tag_flux(lvdev(h, l), D.list[LST_IN], lcap(D), h->qmax.p, h->cfg.tag_tol, h->cfg.tag_buffer,
+                                h->bflag.p + off, s, D.cnt + LST_IN));
         else
-            VCK(launch_tag(lvdev(h, l), D.list[LST_IN], lcap(D), tol2, h->stage8.p, s, D.cnt + LST_IN));
-        VCK(launch_blockflag(h->stage8.p, L.nx, L.ny, px, py, h->cfg.tag_buffer, h->bflag.p + off, s));
+            VCK(launch_tag(lvdev(h, l), D.list[LST_IN], lcap(D), tol2, h->cfg.tag_buffer, h->bflag.p + off, s,
+                           D.cnt + LST_IN));
         off += (size_t)L.bx * L.by;
     }
 }
@@ -1428,18 +1423,32 @@ void device_apply_flags(vlbm_hier* h, const uint8_t* bflag) {
     for (int l = nl - 2; l >= 0; l--) VCK(launch_layout_rule(*D[l], l + 1 <= nl - 2 ? D[l + 1] : nullptr, bflag + off[l], s));
     VCK(launch_derive_in(nullptr, *D[0], s));
     for (int l = 1; l < nl; l++) VCK(launch_derive_in(D[l - 1], *D[l], s));
-    for (int l = 0; l < nl; l++) VCK(launch_nest_check(*D[l], l == nl - 1, h->words + 1, s));
-    for (int l = 0; l < nl; l++) VCK(launch_lists(*D[l], l <= nl - 2 ? LISTS_MOVE : (1 << LST_TOUCH), l, s));
+    const LayoutDev* const* DL = D;
+    VCK(launch_nest_check(DL, nl, h->words + 1, s));
+    int masks[VLBM_MAX_LEVELS];
+    for (int l = 0; l < nl; l++) masks[l] = l <= nl - 2 ? LISTS_MOVE : (1 << LST_TOUCH);
+    VCK(launch_lists(DL, masks, nl, s));
     for (int l = nl - 2; l >= 0; l--)
         VCK(launch_merge(lvdev(h, l), D[l]->list[LST_EXIT], lcap(*D[l]), s, D[l]->cnt + LST_EXIT));
     for (int l = 0; l <= nl - 2; l++)
         VCK(launch_split(lvdev(h, l), lvdev(h, l + 1), D[l]->list[LST_ENTER], lcap(*D[l]), s, D[l]->cnt + LST_ENTER));
+    FlagsSet F{};
+    F.nl = nl;
+    int cap = 0;
     for (int l = 0; l < nl; l++) {
         Level& L = h->lev[l];
-        VCK(launch_flags_update(lvdev(h, l), D[l]->list[LST_TOUCH], lcap(*D[l]), D[l]->cnt + LST_TOUCH, D[l]->nin,
-                                D[l]->ncov, L.flags, L.flags_tmp, s));
-        VCK(launch_commit_maps(*D[l], s));
+        const LevelDev V = lvdev(h, l);
+        F.g[l] = FlagsSet::Geom{V.nx, V.ny, V.pitch, V.px, V.py};
+        F.items[l] = D[l]->list[LST_TOUCH];
+        F.nc[l] = D[l]->cnt + LST_TOUCH;
+        F.bin[l] = D[l]->nin;
+        F.bcov[l] = D[l]->ncov;
+        F.oldf[l] = L.flags;
+        F.newf[l] = L.flags_tmp;
+        cap = std::max(cap, lcap(*D[l]));
     }
+    VCK(launch_flags_update(F, cap, s));
+    VCK(launch_commit_maps(DL, nl, s));
     device_lists(h);
 }
 
@@ -1449,7 +1458,7 @@ void device_apply_flags(vlbm_hier* h, const uint8_t* bflag) {
 void device_regrid(vlbm_hier* h) {
     check_tagging(h);
     regrid_buffers(h);
-    std::vector<uintptr_t> key = {(uintptr_t)h->bflag.p, (uintptr_t)h->stage8.p, (uintptr_t)h->qmax.p,
+    std::vector<uintptr_t> key = {(uintptr_t)h->bflag.p, (uintptr_t)h->qmax.p,
                                   (uintptr_t)h->cfg.tag_sensor, (uintptr_t)h->ditems, (uintptr_t)h->words};
     for (int l = 0; l < h->nlev; l++) {
         key.push_back((uintptr_t)h->lev[l].flags);

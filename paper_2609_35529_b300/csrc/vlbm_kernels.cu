@@ -992,11 +992,45 @@ __device__ __forceinline__ double comp_rho(const LevelDev& L, long long c) {
     return (s[qoff(0, L.plane, c)] + s[qoff(4, L.plane, c)]) + (s[qoff(8, L.plane, c)] + s[qoff(12, L.plane, c)]);
 }
 
+// Flags every block (8 x 8 cells) holding a cell within `buffer` cells
+// (square neighbourhood) of tagged cell (x, y): cells beyond a periodic side
+// wrap, beyond another side they do not exist.  Several threads may flag one
+// block; they all store 1.
+__device__ __forceinline__ void flag_blocks_near(int x, int y, int nx, int ny, int px, int py, int buffer, int bxn,
+                                                 uint8_t* __restrict__ out) {
+    for (int ya = y - buffer; ya <= y + buffer;) {
+        int yy = ya;
+        if (yy < 0 || yy >= ny) {
+            if (!py) {
+                ya = yy < 0 ? 0 : y + buffer + 1;
+                continue;
+            }
+            yy = ((yy % ny) + ny) % ny;
+        }
+        const int jb = yy / TILE;
+        for (int xa = x - buffer; xa <= x + buffer;) {
+            int xx = xa;
+            if (xx < 0 || xx >= nx) {
+                if (!px) {
+                    xa = xx < 0 ? 0 : x + buffer + 1;
+                    continue;
+                }
+                xx = ((xx % nx) + nx) % nx;
+            }
+            const int ib = xx / TILE;
+            out[(long long)jb * bxn + ib] = 1;
+            xa += min((ib + 1) * TILE, nx) - xx;  // on to the next block
+        }
+        ya += min((jb + 1) * TILE, ny) - yy;
+    }
+}
+
 // Normalised density-gradient indicator: tag when
 // (rho_E - rho_W)^2 + (rho_N - rho_S)^2 > tol^2 (2 rho_C)^2; neighbours off
-// the level or beyond a non-periodic side take rho_C.
-__global__ void tag_kernel(LevelDev L, const Item* __restrict__ items, int nitems, double tol2, uint8_t* __restrict__ tags,
-                           const int* __restrict__ ncount) {
+// the level or beyond a non-periodic side take rho_C.  A tagged cell flags
+// the blocks within `buffer` cells of it in bflag (zeroed beforehand).
+__global__ void tag_kernel(LevelDev L, const Item* __restrict__ items, int nitems, double tol2, int buffer,
+                           uint8_t* __restrict__ bflag, const int* __restrict__ ncount) {
     if (ncount) nitems = *ncount;
     const int sub = threadIdx.x >> 6, cx = threadIdx.x & 7, cy = (threadIdx.x >> 3) & 7;
     for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
@@ -1021,7 +1055,7 @@ __global__ void tag_kernel(LevelDev L, const Item* __restrict__ items, int nitem
         const double d2 = rn[2] - rn[3];
         const double num = d1 * d1 + d2 * d2;
         const double t = 2.0 * rc;
-        tags[(long long)y * L.nx + x] = num > tol2 * (t * t);
+        if (num > tol2 * (t * t)) flag_blocks_near(x, y, L.nx, L.ny, L.px, L.py, buffer, (L.nx + TILE - 1) / TILE, bflag);
     }
 }
 
@@ -1068,10 +1102,10 @@ __global__ void qmax_kernel(LevelDev L, const Item* __restrict__ items, int nite
 // s_k = dx (div Q)_k / qmax_k, i.e. when |g_k| > (2 tol) qmax_k for some k,
 // g_k = (Qx_k(E) - Qx_k(W)) + (Qy_k(N) - Qy_k(S)) (central differences;
 // neighbours off the level or beyond a non-periodic side take the cell's
-// own flux).
+// own flux).  A tagged cell flags the blocks within `buffer` cells of it.
 __global__ void tag_flux_kernel(LevelDev L, const Item* __restrict__ items, int nitems,
-                                const unsigned long long* __restrict__ qmax, double tol,
-                                uint8_t* __restrict__ tags, const int* __restrict__ ncount) {
+                                const unsigned long long* __restrict__ qmax, double tol, int buffer,
+                                uint8_t* __restrict__ bflag, const int* __restrict__ ncount) {
     if (ncount) nitems = *ncount;
     const int sub = threadIdx.x >> 6, cx = threadIdx.x & 7, cy = (threadIdx.x >> 3) & 7;
     for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
@@ -1109,42 +1143,10 @@ __global__ void tag_flux_kernel(LevelDev L, const Item* __restrict__ items, int 
             const double lim = (2.0 * tol) * __longlong_as_double((long long)qmax[k]);
             t = t || fabs(g) > lim;
         }
-        tags[(long long)y * L.nx + x] = t;
+        if (t) flag_blocks_near(x, y, L.nx, L.ny, L.px, L.py, buffer, (L.nx + TILE - 1) / TILE, bflag);
     }
 }
 
-// A block (8 x 8 cells) is flagged when any tagged cell lies within
-// `buffer` cells (square neighbourhood) of it.
-__global__ void blockflag_kernel(const uint8_t* __restrict__ tags, int nx, int ny, int px, int py, int buffer,
-                                 uint8_t* __restrict__ out) {
-    const int bx = (nx + TILE - 1) / TILE, by = (ny + TILE - 1) / TILE;
-    const long long nb = (long long)bx * by;
-    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb; b += (long long)gridDim.x * blockDim.x) {
-        const int ib = (int)(b % bx), jb = (int)(b / bx);
-        uint8_t any = 0;
-        // the block's cells inside the domain, widened by `buffer`
-        const int ye = min(jb * TILE + TILE, ny) + buffer;
-        const int xe = min(ib * TILE + TILE, nx) + buffer;
-        for (int y = jb * TILE - buffer; y < ye && !any; y++) {
-            int yy = y;
-            if (yy < 0 || yy >= ny) {
-                if (!py) continue;
-                yy = (yy + ny) % ny;
-            }
-            for (int x = ib * TILE - buffer; x < xe; x++) {
-                int xx = x;
-                if (xx < 0 || xx >= nx) {
-                    if (!px) continue;
-                    xx = (xx + nx) % nx;
-                }
-                if (tags[(long long)yy * nx + xx]) { any = 1; break; }
-            }
-        }
-        out[b] = any;
-    }
-}
-
-// Cells leaving refinement take their merged value (Eq. 25).
 __global__ void merge_kernel(LevelDev L, const Item* __restrict__ items, int nitems, const int* __restrict__ ncount) {
     if (ncount) nitems = *ncount;
     const int sub = threadIdx.x >> 6, cx = threadIdx.x & 7, cy = (threadIdx.x >> 3) & 7;
@@ -1206,7 +1208,8 @@ __global__ void split_kernel(LevelDev C, LevelDev F, const Item* __restrict__ it
 // Per-cell flags of a level from its block maps (blk_in, blk_cov: one byte
 // per 8 x 8 block).  Faces that exist now but did not exist under the old
 // flags have no previous sample.
-__device__ __forceinline__ uint16_t cell_flags(const LevelDev& L, int x, int y, long long t, int bx,
+template <class Lv>
+__device__ __forceinline__ uint16_t cell_flags(const Lv& L, int x, int y, long long t, int bx,
                                                const uint8_t* __restrict__ blk_in,
                                                const uint8_t* __restrict__ blk_cov,
                                                const uint16_t* __restrict__ oldf) {
@@ -1253,23 +1256,27 @@ __global__ void flags_kernel(LevelDev L, const uint8_t* __restrict__ blk_in, con
     }
 }
 
-// The same for the listed blocks (those on the level before or after a
-// change of layout; length at *nc), into newf; copy = 1 then copies those
-// blocks of newf back into oldf.  Every other block is off the level on both
-// sides: its flags are zero and stay zero.
-__global__ void flags_blocks_kernel(LevelDev L, const Item* __restrict__ items, const int* __restrict__ nc,
-                                    const uint8_t* __restrict__ blk_in, const uint8_t* __restrict__ blk_cov,
-                                    uint16_t* __restrict__ oldf, uint16_t* __restrict__ newf, int copy) {
-    const int bx = (L.nx + TILE - 1) / TILE;
-    const int n = *nc;
+// The same for the listed blocks of every level (those on the level before
+// or after a change of layout; length at *nc), into newf; copy = 1 then
+// copies those blocks of newf back into oldf.  Every other block is off the
+// level on both sides: its flags are zero and stay zero.
+__global__ void flags_blocks_kernel(FlagsSet F, int copy) {
     const int sub = threadIdx.x >> 6, cx = threadIdx.x & 7, cy = (threadIdx.x >> 3) & 7;
-    for (int it = blockIdx.x * TILES_PER_CTA + sub; it < n; it += gridDim.x * TILES_PER_CTA) {
-        const Item w = items[it];
-        const int x = w.tx * TILE + cx, y = w.ty * TILE + cy;
-        if (y >= L.ny) continue;
-        const long long t = (long long)y * L.pitch + x;
-        if (copy) oldf[t] = newf[t];
-        else newf[t] = cell_flags(L, x, y, t, bx, blk_in, blk_cov, oldf);
+    for (int l = 0; l < F.nl; l++) {
+        const FlagsSet::Geom& L = F.g[l];
+        const int bx = (L.nx + TILE - 1) / TILE;
+        const int n = *F.nc[l];
+        const Item* __restrict__ items = F.items[l];
+        uint16_t* __restrict__ oldf = F.oldf[l];
+        uint16_t* __restrict__ newf = F.newf[l];
+        for (int it = blockIdx.x * TILES_PER_CTA + sub; it < n; it += gridDim.x * TILES_PER_CTA) {
+            const Item w = items[it];
+            const int x = w.tx * TILE + cx, y = w.ty * TILE + cy;
+            if (y >= L.ny) continue;
+            const long long t = (long long)y * L.pitch + x;
+            if (copy) oldf[t] = newf[t];
+            else newf[t] = cell_flags(L, x, y, t, bx, F.bin[l], F.bcov[l], oldf);
+        }
     }
 }
 
@@ -1417,7 +1424,18 @@ cudaError_t launch_gather_W(const LevelDev& L, double* W, long long ld, uint8_t*
     return cudaGetLastError();
 }
 
-int audit_blocks(int nitems) { return tile_grid(nitems, 148 * 4); }
+// One wave: the CTAs that fit on the device at once loop over the tiles.
+int audit_blocks(int nitems) {
+    static int resident = 0;
+    if (!resident) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, audit_kernel, 256, 0);
+        resident = std::max(1, sms * std::max(1, per));
+    }
+    return tile_grid(nitems, resident);
+}
 
 cudaError_t launch_audit(const LevelDev* levs, const Item* items, int n, unsigned long long* part, double* out,
                          cudaStream_t s, const int* nc) {
@@ -1434,10 +1452,10 @@ cudaError_t launch_avgdown(const LevelDev& C, const LevelDev& F, const Item* ite
     return cudaGetLastError();
 }
 
-cudaError_t launch_tag(const LevelDev& L, const Item* items, int n, double tol2, uint8_t* tags, cudaStream_t s,
-                       const int* nc) {
+cudaError_t launch_tag(const LevelDev& L, const Item* items, int n, double tol2, int buffer, uint8_t* bflag,
+                       cudaStream_t s, const int* nc) {
     if (n <= 0) return cudaSuccess;
-    tag_kernel<<<list_grid(n, nc), CTA_THREADS, 0, s>>>(L, items, n, tol2, tags, nc);
+    tag_kernel<<<list_grid(n, nc), CTA_THREADS, 0, s>>>(L, items, n, tol2, buffer, bflag, nc);
     return cudaGetLastError();
 }
 
@@ -1449,15 +1467,9 @@ cudaError_t launch_qmax(const LevelDev& L, const Item* items, int n, unsigned lo
 }
 
 cudaError_t launch_tag_flux(const LevelDev& L, const Item* items, int n, const unsigned long long* qmax, double tol,
-                            uint8_t* tags, cudaStream_t s, const int* nc) {
+                            int buffer, uint8_t* bflag, cudaStream_t s, const int* nc) {
     if (n <= 0) return cudaSuccess;
-    tag_flux_kernel<<<list_grid(n, nc), CTA_THREADS, 0, s>>>(L, items, n, qmax, tol, tags, nc);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_blockflag(const uint8_t* tags, int nx, int ny, int px, int py, int buffer, uint8_t* out, cudaStream_t s) {
-    const long long nb = (long long)((nx + TILE - 1) / TILE) * ((ny + TILE - 1) / TILE);
-    blockflag_kernel<<<flat_grid(nb), 256, 0, s>>>(tags, nx, ny, px, py, buffer, out);
+    tag_flux_kernel<<<list_grid(n, nc), CTA_THREADS, 0, s>>>(L, items, n, qmax, tol, buffer, bflag, nc);
     return cudaGetLastError();
 }
 
@@ -1480,11 +1492,10 @@ cudaError_t launch_flags(const LevelDev& L, const uint8_t* blk_in, const uint8_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_flags_update(const LevelDev& L, const Item* items, int cap, const int* nc, const uint8_t* blk_in,
-                                const uint8_t* blk_cov, uint16_t* flags, uint16_t* tmp, cudaStream_t s) {
-    const int g = list_grid(cap, nc);
-    flags_blocks_kernel<<<g, CTA_THREADS, 0, s>>>(L, items, nc, blk_in, blk_cov, flags, tmp, 0);
-    flags_blocks_kernel<<<g, CTA_THREADS, 0, s>>>(L, items, nc, blk_in, blk_cov, flags, tmp, 1);
+cudaError_t launch_flags_update(const FlagsSet& F, int cap, cudaStream_t s) {
+    const int g = list_grid(cap, F.nc[0]);
+    flags_blocks_kernel<<<g, CTA_THREADS, 0, s>>>(F, 0);
+    flags_blocks_kernel<<<g, CTA_THREADS, 0, s>>>(F, 1);
     return cudaGetLastError();
 }
 

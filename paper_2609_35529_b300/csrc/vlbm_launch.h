@@ -32,23 +32,36 @@ cudaError_t launch_audit(const LevelDev* levs, const Item* items, int n, unsigne
                          cudaStream_t s, const int* nc = nullptr);
 cudaError_t launch_avgdown(const LevelDev& C, const LevelDev& F, const Item* items, int n, cudaStream_t s,
                            const int* nc = nullptr);
-cudaError_t launch_tag(const LevelDev& L, const Item* items, int n, double tol2, uint8_t* tags, cudaStream_t s,
-                       const int* nc = nullptr);
+// The tag kernels flag, in bflag (zeroed by the caller), every block within
+// `buffer` cells of a tagged cell of the listed tiles.
+cudaError_t launch_tag(const LevelDev& L, const Item* items, int n, double tol2, int buffer, uint8_t* bflag,
+                       cudaStream_t s, const int* nc = nullptr);
 cudaError_t launch_qmax(const LevelDev& L, const Item* items, int n, unsigned long long* qmax, cudaStream_t s,
                         const int* nc = nullptr);
 cudaError_t launch_tag_flux(const LevelDev& L, const Item* items, int n, const unsigned long long* qmax, double tol,
-                            uint8_t* tags, cudaStream_t s, const int* nc = nullptr);
-cudaError_t launch_blockflag(const uint8_t* tags, int nx, int ny, int px, int py, int buffer, uint8_t* out,
-                             cudaStream_t s);
+                            int buffer, uint8_t* bflag, cudaStream_t s, const int* nc = nullptr);
 cudaError_t launch_merge(const LevelDev& L, const Item* items, int n, cudaStream_t s, const int* nc = nullptr);
 cudaError_t launch_split(const LevelDev& C, const LevelDev& F, const Item* items, int n, cudaStream_t s,
                          const int* nc = nullptr);
 cudaError_t launch_flags(const LevelDev& L, const uint8_t* blk_in, const uint8_t* blk_cov, const uint16_t* oldf,
                          uint16_t* newf, cudaStream_t s);
-// Flags of the listed blocks (on the level before or after a layout change;
-// length at *nc, capacity cap) from the new block maps, rebuilt in place
-// through tmp (which it overwrites).
-cudaError_t launch_flags_update(const LevelDev& L, const Item* items, int cap, const int* nc, const uint8_t* blk_in,
-                                const uint8_t* blk_cov, uint16_t* flags, uint16_t* tmp, cudaStream_t s);
+// Per level: the listed blocks (on the level before or after a layout
+// change; length at *nc[l]), the new block maps, the flags (rebuilt in
+// place) and their scratch (overwritten).
+struct FlagsSet {
+    struct Geom {
+        int nx, ny, pitch, px, py;
+    } g[4];
+    const Item* items[4];
+    const int* nc[4];
+    const uint8_t* bin[4];
+    const uint8_t* bcov[4];
+    uint16_t* oldf[4];
+    uint16_t* newf[4];
+    int nl;
+};
+// The flags of every level's listed blocks from the new block maps, in two
+// launches (cap: the largest list's capacity).
+cudaError_t launch_flags_update(const FlagsSet& F, int cap, cudaStream_t s);
 
 }  // namespace vlbm

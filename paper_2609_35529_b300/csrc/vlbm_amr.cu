@@ -717,103 +717,175 @@ __device__ __forceinline__ void tb_write(const TBPlan& P, const TB& tb, int p, i
     P.tasks[t] = T;
 }
 
-// One warp per task: the lanes walk the task's accesses in parallel and
-// append what they find (duplicates included) to the warp's shared buffer;
-// the distinct entries, ascending, go to the task's fixed TB_SMALL slot of
-// the dependency array (deps[t * TB_SMALL ..]), or to the overflow area
-// after the slots when there are more.  A task whose raw entries exceed the
+// Ascending sort of 64 keys held two per lane (element lane in a, element
+// lane + 32 in b) by a bitonic network: each 32-key half by warp shuffles,
+// then one merge of the halves.
+__device__ __forceinline__ void warp_bitonic32(int& v, int lane, bool ascending_last) {
+    for (int k = 2; k <= 32; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const int o = __shfl_xor_sync(0xffffffffu, v, j);
+            const bool up = k == 32 ? ascending_last : ((lane & k) == 0);
+            const bool lower = (lane & j) == 0;
+            v = (lower == up) ? min(v, o) : max(v, o);
+        }
+}
+
+__device__ __forceinline__ void warp_merge32(int& v, int lane) {
+    for (int j = 16; j > 0; j >>= 1) {
+        const int o = __shfl_xor_sync(0xffffffffu, v, j);
+        v = ((lane & j) == 0) ? min(v, o) : max(v, o);
+    }
+}
+
+__device__ __forceinline__ void warp_sort64(int& a, int& b, int lane) {
+    warp_bitonic32(a, lane, true);   // ascending
+    warp_bitonic32(b, lane, false);  // descending: a then b is bitonic
+    const int lo = min(a, b), hi = max(a, b);
+    a = lo;
+    b = hi;
+    warp_merge32(a, lane);
+    warp_merge32(b, lane);
+}
+
+// Two tasks per warp: each half-warp walks one task's accesses in parallel
+// and appends what it finds (duplicates included) to the task's shared
+// buffer; then the whole warp sorts each task's entries and keeps the
+// distinct ones, ascending, in the task's fixed TB_SMALL slot of the
+// dependency array (deps[t * TB_SMALL ..]), or in the overflow area after
+// the slots when there are more.  A task whose raw entries exceed its
 // buffer is left to the fallback pass.
 constexpr int TBW_WARPS = 4;
-constexpr int TBW_RAW = 768;
+constexpr int TBW_RAW = 384;  // raw entries per task
 
 __global__ void __launch_bounds__(TBW_WARPS * 32) tb_warp_kernel(TBPlan P) {
-    __shared__ int raw[TBW_WARPS][TBW_RAW];
+    __shared__ int raw[TBW_WARPS][2][TBW_RAW];
     __shared__ unsigned char keep[TBW_WARPS][TBW_RAW];
-    __shared__ int nraw[TBW_WARPS];
+    __shared__ int nraw[TBW_WARPS][2];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int half = lane >> 4, hl = lane & 15;
     const int total = P.off[P.nphase];
     if (total > P.task_cap) return;
     const TB tb = tb_global(P);
-    int* R = raw[w];
     unsigned char* K = keep[w];
     const long long base = (long long)P.task_cap * TB_SMALL;
-    for (int t = blockIdx.x * TBW_WARPS + w; t < total; t += gridDim.x * TBW_WARPS) {
-        const int p = tb.phase_of(t);
-        const TBPhase ph = tb.ph[p];
-        const TBLevel& L = P.lev[ph.l];
-        const int i = t - tb.off[p];
-        const Item it = ph.kind == 0 ? L.act[i] : L.ring[i];
-        int keys[16];
-        const int nk = (ph.kind == 0 && ph.l > 0 && L.recon[it.ty * L.bx + it.tx])
-                           ? footprint(P.lev[ph.l - 1], it.tx, it.ty, keys) : 0;
-        const int nq = ph.kind == 0 ? 6 + 3 * nk : 10;
-        if (lane == 0) nraw[w] = 0;
-        __syncwarp();
-        for (int q = lane; q < nq; q += 32) {
-            bool wr;
-            int ql, qk, qx, qy;
-            if (!tb.query(ph, it, keys, q, wr, ql, qk, qx, qy)) continue;
-            tb.deps_of(p, wr, ql, qk, qx, qy, [&](int d) {
-                const int at = atomicAdd(&nraw[w], 1);
-                if (at < TBW_RAW) R[at] = d;
-            });
-        }
-        __syncwarp();
-        const int n = nraw[w];
-        __syncwarp();
-        if (n > TBW_RAW) {
-            if (lane == 0) P.big[atomicAdd(P.need + 2, 1)] = t;
-            continue;
-        }
-        // entry j is kept when no earlier entry holds its value
-        int kept = 0;
-        for (int j = lane; j < n; j += 32) {
-            const int v = R[j];
-            bool first = true;
-            for (int k = 0; k < j && first; k++) first = R[k] != v;
-            K[j] = first;
-            kept += first;
-        }
-        const int nu = __reduce_add_sync(0xffffffffu, kept);
-        __syncwarp();
-        long long at = (long long)t * TB_SMALL;
-        if (nu > TB_SMALL) {
-            long long a = 0;
-            if (lane == 0) {
-                a = base + atomicAdd(P.need + 1, nu);
-                atomicAdd(P.need + 4, 1);
-                if (a + nu > P.dep_cap) {
-                    atomicOr(P.need + 3, 1);
-                    a = -1;
+    for (int tp = 2 * (blockIdx.x * TBW_WARPS + w); tp < total; tp += 2 * gridDim.x * TBW_WARPS) {
+        // the walks: half h on task tp + h
+        {
+            const int t = tp + half;
+            __syncwarp();  // the previous pair's buffers are read
+            if (hl == 0) nraw[w][half] = 0;
+            __syncwarp();
+            if (t < total) {
+                const int p = tb.phase_of(t);
+                const TBPhase ph = tb.ph[p];
+                const TBLevel& L = P.lev[ph.l];
+                const int i = t - tb.off[p];
+                const Item it = ph.kind == 0 ? L.act[i] : L.ring[i];
+                int keys[16];
+                const int nk = (ph.kind == 0 && ph.l > 0 && L.recon[it.ty * L.bx + it.tx])
+                                   ? footprint(P.lev[ph.l - 1], it.tx, it.ty, keys) : 0;
+                const int nq = ph.kind == 0 ? 6 + 3 * nk : 10;
+                int* R = raw[w][half];
+                int* cnt = &nraw[w][half];
+                for (int q = hl; q < nq; q += 16) {
+                    bool wr;
+                    int ql, qk, qx, qy;
+                    if (!tb.query(ph, it, keys, q, wr, ql, qk, qx, qy)) continue;
+                    tb.deps_of(p, wr, ql, qk, qx, qy, [&](int d) {
+                        const int at = atomicAdd(cnt, 1);
+                        if (at < TBW_RAW) R[at] = d;
+                    });
                 }
             }
-            at = __shfl_sync(0xffffffffu, a, 0);
+            __syncwarp();
         }
-        if (at >= 0) {
-            // a kept entry's place: the kept entries with smaller values
-            for (int j = lane; j < n; j += 32) {
-                if (!K[j]) continue;
-                const int v = R[j];
-                int r = 0;
-                for (int k = 0; k < n; k++) r += (K[k] && R[k] < v);
-                P.deps[at + r] = v;
+        for (int u = 0; u < 2; u++) {
+            const int t = tp + u;
+            if (t >= total) break;
+            const int* R = raw[w][u];
+            const int n = nraw[w][u];
+            if (n > TBW_RAW) {
+                if (lane == 0) P.big[atomicAdd(P.need + 2, 1)] = t;
+                continue;
             }
-            if (lane == 0) {
-                Task T;
-                T.lid = ph.l;
-                T.tx = it.tx;
-                T.ty = it.ty;
-                T.kind = (signed char)ph.kind;
-                T.kk = (signed char)ph.kk;
-                T.kkp = (signed char)(ph.kind == 0 ? ph.kkp : 0);
-                T.step = (signed char)ph.step;
-                T.dep0 = (int)at;
-                T.ndep = nu;
-                T.aslot = -1;
-                P.tasks[t] = T;
+            // up to 64 entries: sorted in registers (two per lane), kept where
+            // they differ from their predecessor; more: by ranks in shared memory
+            const bool small = n <= 64;
+            int va = 0x7fffffff, vb = 0x7fffffff;
+            unsigned keep_a = 0u, keep_b = 0u;
+            int nu = 0;
+            if (small) {
+                if (lane < n) va = R[lane];
+                if (lane + 32 < n) vb = R[lane + 32];
+                warp_sort64(va, vb, lane);
+                const int pa = __shfl_up_sync(0xffffffffu, va, 1), pb = __shfl_up_sync(0xffffffffu, vb, 1);
+                const int a31 = __shfl_sync(0xffffffffu, va, 31);
+                keep_a = __ballot_sync(0xffffffffu, lane < n && (lane == 0 || va != pa));
+                keep_b = __ballot_sync(0xffffffffu, lane + 32 < n && vb != (lane == 0 ? a31 : pb));
+                nu = __popc(keep_a) + __popc(keep_b);
+            } else {
+                // entry j is kept when no earlier entry holds its value
+                int kept = 0;
+                for (int j = lane; j < n; j += 32) {
+                    const int v = R[j];
+                    bool first = true;
+                    for (int k = 0; k < j && first; k++) first = R[k] != v;
+                    K[j] = first;
+                    kept += first;
+                }
+                nu = __reduce_add_sync(0xffffffffu, kept);
             }
+            __syncwarp();
+            long long at = (long long)t * TB_SMALL;
+            if (nu > TB_SMALL) {
+                long long a2 = 0;
+                if (lane == 0) {
+                    a2 = base + atomicAdd(P.need + 1, nu);
+                    atomicAdd(P.need + 4, 1);
+                    if (a2 + nu > P.dep_cap) {
+                        atomicOr(P.need + 3, 1);
+                        a2 = -1;
+                    }
+                }
+                at = __shfl_sync(0xffffffffu, a2, 0);
+            }
+            if (at >= 0) {
+                if (small) {
+                    const unsigned below = (1u << lane) - 1u;
+                    if (keep_a >> lane & 1u) P.deps[at + __popc(keep_a & below)] = va;
+                    if (keep_b >> lane & 1u) P.deps[at + __popc(keep_a) + __popc(keep_b & below)] = vb;
+                } else {
+                    // a kept entry's place: the kept entries with smaller values
+                    for (int j = lane; j < n; j += 32) {
+                        if (!K[j]) continue;
+                        const int v = R[j];
+                        int r = 0;
+                        for (int k = 0; k < n; k++) r += (K[k] && R[k] < v);
+                        P.deps[at + r] = v;
+                    }
+                }
+                if (lane == 0) {
+                    const int p = tb.phase_of(t);
+                    const TBPhase ph = tb.ph[p];
+                    const TBLevel& L = P.lev[ph.l];
+                    const int i = t - tb.off[p];
+                    const Item it = ph.kind == 0 ? L.act[i] : L.ring[i];
+                    Task T;
+                    T.lid = ph.l;
+                    T.tx = it.tx;
+                    T.ty = it.ty;
+                    T.kind = (signed char)ph.kind;
+                    T.kk = (signed char)ph.kk;
+                    T.kkp = (signed char)(ph.kind == 0 ? ph.kkp : 0);
+                    T.step = (signed char)ph.step;
+                    T.dep0 = (int)at;
+                    T.ndep = nu;
+                    T.aslot = -1;
+                    P.tasks[t] = T;
+                }
+            }
+            __syncwarp();
         }
-        __syncwarp();
     }
 }
 
@@ -940,7 +1012,7 @@ cudaError_t launch_task_build(const TBPlan& P, cudaStream_t s) {
         attrs = true;
     }
     tb_offsets_kernel<<<1, 1, 0, s>>>(P);
-    const long long gl = ((long long)P.task_cap + TBW_WARPS - 1) / TBW_WARPS;
+    const long long gl = ((long long)P.task_cap + 2 * TBW_WARPS - 1) / (2 * TBW_WARPS);
     const int g = (int)(gl < 1 ? 1 : (gl > 148 * 12 ? 148 * 12 : gl));
     tb_warp_kernel<<<g, TBW_WARPS * 32, 0, s>>>(P);
     tb_big_kernel<<<148, TB_BUILD_THREADS, 0, s>>>(P);

@@ -908,7 +908,16 @@ __global__ void gather_W_kernel(LevelDev L, double* __restrict__ W, long long ld
 
 // Exact per-CTA sums over the active cells of the listed tiles:
 // part[blk][0..23] = sum w W_k (k = 0..3), then sum w |W_k|, w = 4^-level,
-// as 192-bit fixed point (three words each).
+// as 192-bit fixed point (three words each).  The loads are pipelined: while
+// a thread group adds up one tile, the flags of its next tile and the list
+// entry of the one after are in flight.
+__device__ __forceinline__ uint32_t audit_flags(const LevelDev* __restrict__ levs, const Item& w, int cx, int cy) {
+    const LevelDev& L = levs[w.lid];
+    const int x = w.tx * TILE + cx, y = w.ty * TILE + cy;
+    if (x >= L.nx || y >= L.ny) return 0;
+    return L.flags[(long long)y * L.pitch + x];
+}
+
 __global__ void __launch_bounds__(256) audit_kernel(const LevelDev* __restrict__ levs, const Item* __restrict__ items,
                                                     int nitems, unsigned long long* __restrict__ part,
                                                     const int* __restrict__ ncount) {
@@ -918,19 +927,28 @@ __global__ void __launch_bounds__(256) audit_kernel(const LevelDev* __restrict__
     const int sub = threadIdx.x >> 6;
     const int cx = threadIdx.x & 7;
     const int cy = (threadIdx.x >> 3) & 7;
-    for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
-        const Item w = items[it];
-        const LevelDev& L = levs[w.lid];
-        const int x = w.tx * TILE + cx, y = w.ty * TILE + cy;
-        if (x >= L.nx || y >= L.ny) continue;
-        const long long c = (long long)y * L.pitch + x;
-        if ((L.flags[c] & (F_IN | F_COV)) != F_IN) continue;
-        const double* st = L.buf[state_buf(L)];
-        for (int k = 0; k < 4; k++) {
-            const double v = (st[qoff(0 + k, L.plane, c)] + st[qoff(4 + k, L.plane, c)]) +
-                             (st[qoff(8 + k, L.plane, c)] + st[qoff(12 + k, L.plane, c)]);
-            fix_accumulate(acc[k], acc[4 + k], v, -2 * L.level);
+    const int stride = gridDim.x * TILES_PER_CTA;
+    int it = blockIdx.x * TILES_PER_CTA + sub;
+    const Item none{0, 0, 0};
+    Item wa = it < nitems ? items[it] : none;
+    Item wb = it + stride < nitems ? items[it + stride] : none;
+    uint32_t fa = it < nitems ? audit_flags(levs, wa, cx, cy) : 0u;
+    for (; it < nitems; it += stride) {
+        const uint32_t fb = it + stride < nitems ? audit_flags(levs, wb, cx, cy) : 0u;
+        const Item wc = it + 2 * stride < nitems ? items[it + 2 * stride] : none;
+        if ((fa & (F_IN | F_COV)) == F_IN) {
+            const LevelDev& L = levs[wa.lid];
+            const long long c = (long long)(wa.ty * TILE + cy) * L.pitch + (wa.tx * TILE + cx);
+            const double* st = L.buf[state_buf(L)];
+            for (int k = 0; k < 4; k++) {
+                const double v = (st[qoff(0 + k, L.plane, c)] + st[qoff(4 + k, L.plane, c)]) +
+                                 (st[qoff(8 + k, L.plane, c)] + st[qoff(12 + k, L.plane, c)]);
+                fix_accumulate(acc[k], acc[4 + k], v, -2 * L.level);
+            }
         }
+        wa = wb;
+        fa = fb;
+        wb = wc;
     }
     __shared__ Fix192 sh[8][8];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -986,12 +1004,6 @@ __global__ void avgdown_kernel(LevelDev C, LevelDev F, const Item* __restrict__ 
     }
 }
 
-__device__ __forceinline__ double comp_rho(const LevelDev& L, long long c) {
-    const uint32_t fl = L.flags[c];
-    const double* s = composite_src(L, fl);
-    return (s[qoff(0, L.plane, c)] + s[qoff(4, L.plane, c)]) + (s[qoff(8, L.plane, c)] + s[qoff(12, L.plane, c)]);
-}
-
 // Flags every block (8 x 8 cells) holding a cell within `buffer` cells
 // (square neighbourhood) of tagged cell (x, y): cells beyond a periodic side
 // wrap, beyond another side they do not exist.  Several threads may flag one
@@ -1025,32 +1037,71 @@ __device__ __forceinline__ void flag_blocks_near(int x, int y, int nx, int ny, i
     }
 }
 
+// The composite moments W_0 .. W_{NK-1} of the 10 x 10 window around tile
+// w (the tile and a one-cell ring; sides wrap where periodic) into Ws[k],
+// with on = 1 where the cell is on the level: thread lt of the tile's group
+// stages its own cell and, for lt < 36, one cell of the ring.
+constexpr int WIN = TILE + 2;
+template <int NK>
+__device__ __forceinline__ void stage_window(const LevelDev& L, const Item& w, int lt, double (*Ws)[WIN * WIN],
+                                             uint8_t* on) {
+    for (int pass = 0; pass < 2; pass++) {
+        int hx, hy;
+        if (pass == 0) {
+            hx = (lt & 7) + 1;
+            hy = (lt >> 3) + 1;
+        } else {
+            if (lt >= 4 * (TILE + 1)) break;
+            if (lt < WIN) { hx = lt; hy = 0; }
+            else if (lt < 2 * WIN) { hx = lt - WIN; hy = WIN - 1; }
+            else if (lt < 2 * WIN + TILE) { hx = 0; hy = lt - 2 * WIN + 1; }
+            else { hx = WIN - 1; hy = lt - 2 * WIN - TILE + 1; }
+        }
+        int x = w.tx * TILE + hx - 1, y = w.ty * TILE + hy - 1;
+        bool ok = true;
+        if (x < 0) { if (L.px) x += L.nx; else ok = false; }
+        if (x >= L.nx) { if (L.px) x -= L.nx; else ok = false; }
+        if (y < 0) { if (L.py) y += L.ny; else ok = false; }
+        if (y >= L.ny) { if (L.py) y -= L.ny; else ok = false; }
+        ok = ok && x >= 0 && x < L.nx && y >= 0 && y < L.ny;  // cells past a narrow domain's side
+        uint8_t in = 0;
+        if (ok) {
+            const long long c = (long long)y * L.pitch + x;
+            const uint32_t fl = L.flags[c];
+            if (fl & F_IN) {
+                in = 1;
+                const double* src = composite_src(L, fl);
+                for (int k = 0; k < NK; k++)
+                    Ws[k][hy * WIN + hx] = (src[qoff(0 + k, L.plane, c)] + src[qoff(4 + k, L.plane, c)]) +
+                                           (src[qoff(8 + k, L.plane, c)] + src[qoff(12 + k, L.plane, c)]);
+            }
+        }
+        on[hy * WIN + hx] = in;
+    }
+}
+
 // Normalised density-gradient indicator: tag when
 // (rho_E - rho_W)^2 + (rho_N - rho_S)^2 > tol^2 (2 rho_C)^2; neighbours off
 // the level or beyond a non-periodic side take rho_C.  A tagged cell flags
 // the blocks within `buffer` cells of it in bflag (zeroed beforehand).
 __global__ void tag_kernel(LevelDev L, const Item* __restrict__ items, int nitems, double tol2, int buffer,
                            uint8_t* __restrict__ bflag, const int* __restrict__ ncount) {
+    __shared__ double sW[TILES_PER_CTA][1][WIN * WIN];
+    __shared__ uint8_t son[TILES_PER_CTA][WIN * WIN];
     if (ncount) nitems = *ncount;
-    const int sub = threadIdx.x >> 6, cx = threadIdx.x & 7, cy = (threadIdx.x >> 3) & 7;
+    const int sub = threadIdx.x >> 6, lt = threadIdx.x & 63, cx = lt & 7, cy = lt >> 3;
     for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
         const Item w = items[it];
+        group_bar(sub);  // the group's previous window is read
+        stage_window<1>(L, w, lt, sW[sub], son[sub]);
+        group_bar(sub);
         const int x = w.tx * TILE + cx, y = w.ty * TILE + cy;
-        if (x >= L.nx || y >= L.ny) continue;
-        const long long c = (long long)y * L.pitch + x;
-        if (!(L.flags[c] & F_IN)) continue;
-        const double rc = comp_rho(L, c);
+        const int hc = (cy + 1) * WIN + cx + 1;
+        if (x >= L.nx || y >= L.ny || !son[sub][hc]) continue;
+        const double rc = sW[sub][0][hc];
+        const int nb[4] = {hc + 1, hc - 1, hc + WIN, hc - WIN};  // E, W, N, S
         double rn[4];
-        for (int d = 0; d < 4; d++) {
-            int xx = x + kCX[d], yy = y + kCY[d];
-            bool ok = true;
-            if (xx < 0) { if (L.px) xx += L.nx; else ok = false; }
-            if (xx >= L.nx) { if (L.px) xx -= L.nx; else ok = false; }
-            if (yy < 0) { if (L.py) yy += L.ny; else ok = false; }
-            if (yy >= L.ny) { if (L.py) yy -= L.ny; else ok = false; }
-            const long long cn = (long long)yy * L.pitch + xx;
-            rn[d] = (ok && (L.flags[cn] & F_IN)) ? comp_rho(L, cn) : rc;
-        }
+        for (int d = 0; d < 4; d++) rn[d] = son[sub][nb[d]] ? sW[sub][0][nb[d]] : rc;
         const double d1 = rn[0] - rn[1];
         const double d2 = rn[2] - rn[3];
         const double num = d1 * d1 + d2 * d2;
@@ -1106,29 +1157,27 @@ __global__ void qmax_kernel(LevelDev L, const Item* __restrict__ items, int nite
 __global__ void tag_flux_kernel(LevelDev L, const Item* __restrict__ items, int nitems,
                                 const unsigned long long* __restrict__ qmax, double tol, int buffer,
                                 uint8_t* __restrict__ bflag, const int* __restrict__ ncount) {
+    __shared__ double sW[TILES_PER_CTA][4][WIN * WIN];
+    __shared__ uint8_t son[TILES_PER_CTA][WIN * WIN];
     if (ncount) nitems = *ncount;
-    const int sub = threadIdx.x >> 6, cx = threadIdx.x & 7, cy = (threadIdx.x >> 3) & 7;
+    const int sub = threadIdx.x >> 6, lt = threadIdx.x & 63, cx = lt & 7, cy = lt >> 3;
     for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
         const Item w = items[it];
+        group_bar(sub);  // the group's previous window is read
+        stage_window<4>(L, w, lt, sW[sub], son[sub]);
+        group_bar(sub);
         const int x = w.tx * TILE + cx, y = w.ty * TILE + cy;
-        if (x >= L.nx || y >= L.ny) continue;
-        const long long c = (long long)y * L.pitch + x;
-        if (!(L.flags[c] & F_IN)) continue;
+        const int hc = (cy + 1) * WIN + cx + 1;
+        if (x >= L.nx || y >= L.ny || !son[sub][hc]) continue;
         double W[4], Qcx[4], Qcy[4], p;
-        comp_W(L, c, W);
+        for (int k = 0; k < 4; k++) W[k] = sW[sub][k][hc];
         euler_flux(L.gm1, W, Qcx, Qcy, p);
+        const int nb[4] = {hc + 1, hc - 1, hc + WIN, hc - WIN};  // E, W, N, S
         double Qx[4][4], Qy[4][4];
         for (int d = 0; d < 4; d++) {
-            int xx = x + kCX[d], yy = y + kCY[d];
-            bool ok = true;
-            if (xx < 0) { if (L.px) xx += L.nx; else ok = false; }
-            if (xx >= L.nx) { if (L.px) xx -= L.nx; else ok = false; }
-            if (yy < 0) { if (L.py) yy += L.ny; else ok = false; }
-            if (yy >= L.ny) { if (L.py) yy -= L.ny; else ok = false; }
-            const long long cn = (long long)yy * L.pitch + xx;
-            if (ok && (L.flags[cn] & F_IN)) {
+            if (son[sub][nb[d]]) {
                 double Wn[4];
-                comp_W(L, cn, Wn);
+                for (int k = 0; k < 4; k++) Wn[k] = sW[sub][k][nb[d]];
                 euler_flux(L.gm1, Wn, Qx[d], Qy[d], p);
             } else {
                 for (int k = 0; k < 4; k++) {

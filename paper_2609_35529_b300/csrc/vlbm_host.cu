@@ -336,6 +336,12 @@ struct vlbm_hier {
     uint8_t* rg_pin = nullptr;
     size_t rg_cap = 0;
     cudaEvent_t rg_ev = nullptr;
+    // task-list builds run on aux, after ev_layout (recorded when a device
+    // regrid's layout is complete, for layout ev_layout_version); the main
+    // stream waits for ev_built before the persistent launch
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_layout = nullptr, ev_built = nullptr;
+    long long ev_layout_version = -1;
     vlbm_tuning tune{1, 0, 8, 1, 256};
     long long layout_steps = 0;  // coarse steps taken on the current layout
     // The layout lives on the device (Level::dl, always current); the host
@@ -1493,6 +1499,8 @@ void device_regrid(vlbm_hier* h) {
         VCK(launch_audit(h->atab.p, h->ditems, icap, h->partial.p, h->raud + 16 * slot, s, h->dcount));
     VCK(cudaGraphLaunch(h->rg_exec, s));
     h->klaunch += graph_kernels(h->rg_exec);
+    if (!h->ev_layout) VCK(cudaEventCreateWithFlags(&h->ev_layout, cudaEventDisableTiming));
+    VCK(cudaEventRecord(h->ev_layout, s));  // the new layout is complete here
     if (h->regrid_audit) {
         VCK(launch_audit(h->atab.p, h->ditems, icap, h->partial.p, h->raud + 16 * slot + 8, s, h->dcount));
         h->ra_n++;
@@ -1500,6 +1508,7 @@ void device_regrid(vlbm_hier* h) {
     }
     h->host_ok = false;
     layout_changed(h);
+    h->ev_layout_version = h->layout_version;
 }
 
 // ---- the sub-cycle over the device lists ---------------------------------------
@@ -1572,7 +1581,9 @@ vlbm_hier::DevPlan& dev_plan(vlbm_hier* h, int k, bool cyclic) {
     if (cyclic) k = 1;
     D.build_kernels = 0;
     cudaStream_t s = h->stream;
+    bool plan_fresh_ok = true;  // no upload queued on the main stream since the layout event
     if (D.steps != k) {
+        plan_fresh_ok = false;
         std::vector<TBPhase> ph;
         std::vector<TBAcc> acc;
         std::vector<int> beg, pos;
@@ -1629,10 +1640,30 @@ vlbm_hier::DevPlan& dev_plan(vlbm_hier* h, int k, bool cyclic) {
     }
     if (D.version != h->layout_version) {
         const auto t0 = std::chrono::steady_clock::now();
+        // The build reads only the layout: it runs on the auxiliary stream
+        // from the moment the regrid that made the layout is done, beside
+        // what the main stream does after it (the post-regrid audit), and
+        // the main stream waits for it.  Under a capture of the main stream,
+        // or when the layout came another way, it starts from the main
+        // stream's current end.
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        VCK(cudaStreamIsCapturing(s, &cs));
+        cudaStream_t bs = s;
+        if (cs == cudaStreamCaptureStatusNone) {
+            if (!h->aux) VCK(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
+            if (!h->ev_layout) VCK(cudaEventCreateWithFlags(&h->ev_layout, cudaEventDisableTiming));
+            if (!h->ev_built) VCK(cudaEventCreateWithFlags(&h->ev_built, cudaEventDisableTiming));
+            if (h->ev_layout_version != h->layout_version || !plan_fresh_ok) {
+                VCK(cudaEventRecord(h->ev_layout, s));
+                h->ev_layout_version = h->layout_version;
+            }
+            VCK(cudaStreamWaitEvent(h->aux, h->ev_layout, 0));
+            bs = h->aux;
+        }
         // the reverse footprints of the current layout (shared by both plans)
         if (h->foot_version != h->layout_version) {
             for (int l = 0; l + 1 < h->nlev; l++)
-                VCK(launch_footprints(h->lev[l].dl, h->lev[l + 1].dl, h->words + 1, s));
+                VCK(launch_footprints(h->lev[l].dl, h->lev[l + 1].dl, h->words + 1, bs));
             h->foot_version = h->layout_version;
             D.build_kernels += 2 * (h->nlev - 1);
         }
@@ -1662,7 +1693,11 @@ vlbm_hier::DevPlan& dev_plan(vlbm_hier* h, int k, bool cyclic) {
         P.seg = D.seg.p;
         P.prefix = D.prefix.p;
         P.ctl = D.ctl.p;
-        VCK(launch_task_build(P, s));
+        VCK(launch_task_build(P, bs));
+        if (bs != s) {
+            VCK(cudaEventRecord(h->ev_built, bs));
+            VCK(cudaStreamWaitEvent(s, h->ev_built, 0));
+        }
         D.build_kernels += 4;
         D.version = h->layout_version;
         h->times[VLBM_T_TASKS] += ms_since(t0);
@@ -1949,6 +1984,14 @@ void destroy_levels(vlbm_hier* h) {
     h->rg_cap = 0;
     if (h->rg_ev) cudaEventDestroy(h->rg_ev);
     h->rg_ev = nullptr;
+    if (h->aux) {
+        cudaStreamSynchronize(h->aux);
+        cudaStreamDestroy(h->aux);
+    }
+    h->aux = nullptr;
+    if (h->ev_layout) cudaEventDestroy(h->ev_layout);
+    if (h->ev_built) cudaEventDestroy(h->ev_built);
+    h->ev_layout = h->ev_built = nullptr;
     pin_free(h->hist, (size_t)h->hist_cap * 8 * sizeof(double));
     h->hist = nullptr;
     for (auto& L : h->tl) {

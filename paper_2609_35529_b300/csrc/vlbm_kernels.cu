@@ -985,8 +985,10 @@ __global__ void avgdown_kernel(LevelDev C, LevelDev F, const Item* __restrict__ 
                                const int* __restrict__ ncount) {
     if (ncount) nitems = *ncount;
     const int sub = threadIdx.x >> 6, cx = threadIdx.x & 7, cy = (threadIdx.x >> 3) & 7;
-    for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
-        const Item w = items[it];
+    // work item: (tile, field) -- the four populations of one field
+    for (int wi = blockIdx.x * TILES_PER_CTA + sub; wi < 4 * nitems; wi += gridDim.x * TILES_PER_CTA) {
+        const Item w = items[wi >> 2];
+        const int k = wi & 3;
         const int x = w.tx * TILE + cx, y = w.ty * TILE + cy;
         if (x >= C.nx || y >= C.ny) continue;
         const long long c = (long long)y * C.pitch + x;
@@ -998,7 +1000,7 @@ __global__ void avgdown_kernel(LevelDev C, LevelDev F, const Item* __restrict__ 
         const double* p10 = composite_src(F, F.flags[k10]);
         const double* p01 = composite_src(F, F.flags[k01]);
         const double* p11 = composite_src(F, F.flags[k11]);
-        for (int q = 0; q < 16; q++)
+        for (int q = 4 * k; q < 4 * k + 4; q++)
             out[qoff(q, C.plane, c)] = ((p00[qoff(q, F.plane, k00)] + p11[qoff(q, F.plane, k11)]) +
                                         (p10[qoff(q, F.plane, k10)] + p01[qoff(q, F.plane, k01)])) * 0.25;
     }
@@ -1199,13 +1201,15 @@ __global__ void tag_flux_kernel(LevelDev L, const Item* __restrict__ items, int 
 __global__ void merge_kernel(LevelDev L, const Item* __restrict__ items, int nitems, const int* __restrict__ ncount) {
     if (ncount) nitems = *ncount;
     const int sub = threadIdx.x >> 6, cx = threadIdx.x & 7, cy = (threadIdx.x >> 3) & 7;
-    for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
-        const Item w = items[it];
+    // work item: (tile, field) -- the four populations of one field
+    for (int wi = blockIdx.x * TILES_PER_CTA + sub; wi < 4 * nitems; wi += gridDim.x * TILES_PER_CTA) {
+        const Item w = items[wi >> 2];
+        const int k = wi & 3;
         const int x = w.tx * TILE + cx, y = w.ty * TILE + cy;
         if (x >= L.nx || y >= L.ny) continue;
         const long long c = (long long)y * L.pitch + x;
         const int sb = state_buf(L);
-        for (int q = 0; q < 16; q++) L.buf[sb][qoff(q, L.plane, c)] = L.buf[sb ^ 1][qoff(q, L.plane, c)];
+        for (int q = 4 * k; q < 4 * k + 4; q++) L.buf[sb][qoff(q, L.plane, c)] = L.buf[sb ^ 1][qoff(q, L.plane, c)];
     }
 }
 
@@ -1219,8 +1223,10 @@ __global__ void split_kernel(LevelDev C, LevelDev F, const Item* __restrict__ it
                              const int* __restrict__ ncount) {
     if (ncount) nitems = *ncount;
     const int sub = threadIdx.x >> 6, cx = threadIdx.x & 7, cy = (threadIdx.x >> 3) & 7;
-    for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
-        const Item w = items[it];
+    // work item: (tile, field) -- the four populations of one field
+    for (int wi = blockIdx.x * TILES_PER_CTA + sub; wi < 4 * nitems; wi += gridDim.x * TILES_PER_CTA) {
+        const Item w = items[wi >> 2];
+        const int k = wi & 3;
         const int x = w.tx * TILE + cx, y = w.ty * TILE + cy;
         if (x >= C.nx || y >= C.ny) continue;
         const long long c = (long long)y * C.pitch + x;
@@ -1240,7 +1246,7 @@ __global__ void split_kernel(LevelDev C, LevelDev F, const Item* __restrict__ it
         for (int d = 0; d < 4; d++) nsrc[d] = ok[d] ? composite_src(C, C.flags[nb[d]]) : st;
         double* fo = F.buf[state_buf(F)];
         const long long k00 = (long long)(2 * y) * F.pitch + 2 * x;
-        for (int q = 0; q < 16; q++) {
+        for (int q = 4 * k; q < 4 * k + 4; q++) {
             const double fc = st[qoff(q, C.plane, c)];
             const double vE = nsrc[0][qoff(q, C.plane, nb[0])], vW = nsrc[1][qoff(q, C.plane, nb[1])];
             const double vN = nsrc[2][qoff(q, C.plane, nb[2])], vS = nsrc[3][qoff(q, C.plane, nb[3])];
@@ -1497,7 +1503,7 @@ cudaError_t launch_audit(const LevelDev* levs, const Item* items, int n, unsigne
 cudaError_t launch_avgdown(const LevelDev& C, const LevelDev& F, const Item* items, int n, cudaStream_t s,
                            const int* nc) {
     if (n <= 0) return cudaSuccess;
-    avgdown_kernel<<<list_grid(n, nc), CTA_THREADS, 0, s>>>(C, F, items, n, nc);
+    avgdown_kernel<<<list_grid(4 * n, nc), CTA_THREADS, 0, s>>>(C, F, items, n, nc);
     return cudaGetLastError();
 }
 
@@ -1524,14 +1530,14 @@ cudaError_t launch_tag_flux(const LevelDev& L, const Item* items, int n, const u
 
 cudaError_t launch_merge(const LevelDev& L, const Item* items, int n, cudaStream_t s, const int* nc) {
     if (n <= 0) return cudaSuccess;
-    merge_kernel<<<list_grid(n, nc), CTA_THREADS, 0, s>>>(L, items, n, nc);
+    merge_kernel<<<list_grid(4 * n, nc), CTA_THREADS, 0, s>>>(L, items, n, nc);
     return cudaGetLastError();
 }
 
 cudaError_t launch_split(const LevelDev& C, const LevelDev& F, const Item* items, int n, cudaStream_t s,
                          const int* nc) {
     if (n <= 0) return cudaSuccess;
-    split_kernel<<<list_grid(n, nc), CTA_THREADS, 0, s>>>(C, F, items, n, nc);
+    split_kernel<<<list_grid(4 * n, nc), CTA_THREADS, 0, s>>>(C, F, items, n, nc);
     return cudaGetLastError();
 }
 

@@ -5,7 +5,10 @@
 // --fmad=false).  The expression order is fixed so that results do not
 // depend on the launch configuration.
 #include <cuda_runtime.h>
+
 #include <algorithm>
+#include <mutex>
+#include <unordered_map>
 #include <cstdint>
 
 #include "fix192.cuh"
@@ -908,62 +911,47 @@ __global__ void gather_W_kernel(LevelDev L, double* __restrict__ W, long long ld
 
 // Exact per-CTA sums over the active cells of the listed tiles:
 // part[blk][0..23] = sum w W_k (k = 0..3), then sum w |W_k|, w = 4^-level,
-// as 192-bit fixed point (three words each).  The loads are pipelined: while
-// a thread group adds up one tile, the flags of its next tile and the list
-// entry of the one after are in flight.
-__device__ __forceinline__ uint32_t audit_flags(const LevelDev* __restrict__ levs, const Item& w, int cx, int cy) {
-    const LevelDev& L = levs[w.lid];
-    const int x = w.tx * TILE + cx, y = w.ty * TILE + cy;
-    if (x >= L.nx || y >= L.ny) return 0;
-    return L.flags[(long long)y * L.pitch + x];
-}
-
+// as 192-bit fixed point (three words each).  A CTA takes one tile at a
+// time; its 64-thread group g adds up field k = g of the tile's cells, so a
+// thread holds two accumulators and many CTAs fit on an SM.
 __global__ void __launch_bounds__(256) audit_kernel(const LevelDev* __restrict__ levs, const Item* __restrict__ items,
                                                     int nitems, unsigned long long* __restrict__ part,
                                                     const int* __restrict__ ncount) {
     if (ncount) nitems = *ncount;
-    Fix192 acc[8];
-    for (int m = 0; m < 8; m++) acc[m] = fix_zero();
-    const int sub = threadIdx.x >> 6;
+    const int k = threadIdx.x >> 6;
     const int cx = threadIdx.x & 7;
     const int cy = (threadIdx.x >> 3) & 7;
-    const int stride = gridDim.x * TILES_PER_CTA;
-    int it = blockIdx.x * TILES_PER_CTA + sub;
-    const Item none{0, 0, 0};
-    Item wa = it < nitems ? items[it] : none;
-    Item wb = it + stride < nitems ? items[it + stride] : none;
-    uint32_t fa = it < nitems ? audit_flags(levs, wa, cx, cy) : 0u;
-    for (; it < nitems; it += stride) {
-        const uint32_t fb = it + stride < nitems ? audit_flags(levs, wb, cx, cy) : 0u;
-        const Item wc = it + 2 * stride < nitems ? items[it + 2 * stride] : none;
-        if ((fa & (F_IN | F_COV)) == F_IN) {
-            const LevelDev& L = levs[wa.lid];
-            const long long c = (long long)(wa.ty * TILE + cy) * L.pitch + (wa.tx * TILE + cx);
-            const double* st = L.buf[state_buf(L)];
-            for (int k = 0; k < 4; k++) {
-                const double v = (st[qoff(0 + k, L.plane, c)] + st[qoff(4 + k, L.plane, c)]) +
-                                 (st[qoff(8 + k, L.plane, c)] + st[qoff(12 + k, L.plane, c)]);
-                fix_accumulate(acc[k], acc[4 + k], v, -2 * L.level);
-            }
-        }
-        wa = wb;
-        fa = fb;
-        wb = wc;
+    Fix192 sum = fix_zero(), abs_sum = fix_zero();
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const Item w = items[it];
+        const LevelDev& L = levs[w.lid];
+        const int x = w.tx * TILE + cx, y = w.ty * TILE + cy;
+        if (x >= L.nx || y >= L.ny) continue;
+        const long long c = (long long)y * L.pitch + x;
+        if ((L.flags[c] & (F_IN | F_COV)) != F_IN) continue;
+        const double* st = L.buf[state_buf(L)];
+        const double v = (st[qoff(0 + k, L.plane, c)] + st[qoff(4 + k, L.plane, c)]) +
+                         (st[qoff(8 + k, L.plane, c)] + st[qoff(12 + k, L.plane, c)]);
+        fix_accumulate(sum, abs_sum, v, -2 * L.level);
     }
-    __shared__ Fix192 sh[8][8];
+    __shared__ Fix192 sh[8][2];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int m = 0; m < 8; m++) {
-        for (int o = 16; o > 0; o >>= 1) {
-            const Fix192 b = fix_shfl_down(acc[m], o);
-            fix_add(acc[m], b);
-        }
-        if (lane == 0) sh[wid][m] = acc[m];
+    for (int o = 16; o > 0; o >>= 1) {
+        const Fix192 a = fix_shfl_down(sum, o);
+        const Fix192 b = fix_shfl_down(abs_sum, o);
+        fix_add(sum, a);
+        fix_add(abs_sum, b);
+    }
+    if (lane == 0) {
+        sh[wid][0] = sum;
+        sh[wid][1] = abs_sum;
     }
     __syncthreads();
     if (threadIdx.x < 8) {
-        const int m = threadIdx.x;
-        Fix192 a = sh[0][m];
-        for (int w2 = 1; w2 < (int)(blockDim.x >> 5); w2++) fix_add(a, sh[w2][m]);
+        // m < 4: sum of field m (warps 2m, 2m + 1); m >= 4: its absolute sum
+        const int m = threadIdx.x, f = m & 3, j = m >> 2;
+        Fix192 a = sh[2 * f][j];
+        fix_add(a, sh[2 * f + 1][j]);
         for (int i = 0; i < 3; i++) part[(size_t)blockIdx.x * 24 + 3 * m + i] = a.w[i];
     }
 }
@@ -1086,7 +1074,8 @@ __device__ __forceinline__ void stage_window(const LevelDev& L, const Item& w, i
 // (rho_E - rho_W)^2 + (rho_N - rho_S)^2 > tol^2 (2 rho_C)^2; neighbours off
 // the level or beyond a non-periodic side take rho_C.  A tagged cell flags
 // the blocks within `buffer` cells of it in bflag (zeroed beforehand).
-__global__ void tag_kernel(LevelDev L, const Item* __restrict__ items, int nitems, double tol2, int buffer,
+__global__ void __launch_bounds__(CTA_THREADS, 6)
+tag_kernel(LevelDev L, const Item* __restrict__ items, int nitems, double tol2, int buffer,
                            uint8_t* __restrict__ bflag, const int* __restrict__ ncount) {
     __shared__ double sW[TILES_PER_CTA][1][WIN * WIN];
     __shared__ uint8_t son[TILES_PER_CTA][WIN * WIN];
@@ -1156,7 +1145,8 @@ __global__ void qmax_kernel(LevelDev L, const Item* __restrict__ items, int nite
 // g_k = (Qx_k(E) - Qx_k(W)) + (Qy_k(N) - Qy_k(S)) (central differences;
 // neighbours off the level or beyond a non-periodic side take the cell's
 // own flux).  A tagged cell flags the blocks within `buffer` cells of it.
-__global__ void tag_flux_kernel(LevelDev L, const Item* __restrict__ items, int nitems,
+__global__ void __launch_bounds__(CTA_THREADS, 4)
+tag_flux_kernel(LevelDev L, const Item* __restrict__ items, int nitems,
                                 const unsigned long long* __restrict__ qmax, double tol, int buffer,
                                 uint8_t* __restrict__ bflag, const int* __restrict__ ncount) {
     __shared__ double sW[TILES_PER_CTA][4][WIN * WIN];
@@ -1345,12 +1335,29 @@ static inline int tile_grid(int nitems, int max_ctas) {
     return g < 1 ? 1 : g;
 }
 
-// Grid of a launch over a tile list: n tiles, or -- when the list's length
-// lives in device memory (nc != nullptr) -- at most n tiles with a grid of
-// at most six CTAs per SM looping over the list.
-static inline int list_grid(int n, const int* nc, int max_ctas = 0) {
+// CTAs of CTA_THREADS threads of kernel fn that the device holds at once.
+static int resident_ctas(const void* fn) {
+    static std::mutex mu;
+    static std::unordered_map<const void*, int> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    auto f = cache.find(fn);
+    if (f != cache.end()) return f->second;
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, CTA_THREADS, 0);
+    const int r = std::max(1, sms * std::max(1, per));
+    cache[fn] = r;
+    return r;
+}
+
+// Grid of a launch of `kernel` over a tile list: n tiles, or -- when the
+// list's length lives in device memory (nc != nullptr) -- one wave of the
+// CTAs the device holds at once, looping over at most n tiles.
+template <class K>
+static inline int list_grid(K* kernel, int n, const int* nc, int max_ctas = 0) {
     int g = tile_grid(n, max_ctas);
-    if (nc && g > 148 * 6) g = 148 * 6;
+    if (nc) g = std::min(g, resident_ctas((const void*)kernel));
     return g;
 }
 
@@ -1369,22 +1376,25 @@ int sweep_variants() { return 5; }
 
 cudaError_t launch_sensor(const LevelDev* levs, const Item* items, int n, int kk, cudaStream_t s, const int* nc) {
     if (n <= 0) return cudaSuccess;
-    const int g = list_grid(n, nc);
-    sensor_prep_kernel<<<g, CTA_THREADS, 0, s>>>(levs, items, n, kk, nc);
-    sensor_rate_kernel<<<g, CTA_THREADS, 0, s>>>(levs, items, n, nc);
+    sensor_prep_kernel<<<list_grid(sensor_prep_kernel, n, nc), CTA_THREADS, 0, s>>>(levs, items, n, kk, nc);
+    sensor_rate_kernel<<<list_grid(sensor_rate_kernel, n, nc), CTA_THREADS, 0, s>>>(levs, items, n, nc);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sweep(const LevelDev* levs, const Item* items, int n, int kk, int kkp, int max_ctas, int variant,
                          cudaStream_t s, bool sensor, const int* nc) {
     if (n <= 0) return cudaSuccess;
-    const int g = list_grid(n, nc, max_ctas);
     if (sensor) {  // per-cell relaxation parameters: one form of the sweep
-        sweep_kernel<SW_SENSOR, 2><<<g, CTA_THREADS, 0, s>>>(levs, items, n, kk, kkp, nc);
+        sweep_kernel<SW_SENSOR, 2><<<list_grid(sweep_kernel<SW_SENSOR, 2>, n, nc, max_ctas), CTA_THREADS, 0, s>>>(
+            levs, items, n, kk, kkp, nc);
         return cudaGetLastError();
     }
     switch (variant) {
-#define X(id, P, B) case id: sweep_kernel<P, B><<<g, CTA_THREADS, 0, s>>>(levs, items, n, kk, kkp, nc); break;
+#define X(id, P, B)                                                                                       \
+    case id:                                                                                              \
+        sweep_kernel<P, B><<<list_grid(sweep_kernel<P, B>, n, nc, max_ctas), CTA_THREADS, 0, s>>>(levs, items, n, kk, \
+                                                                                                 kkp, nc); \
+        break;
         VLBM_SWEEP_VARIANTS(X)
 #undef X
         default: return cudaErrorInvalidValue;
@@ -1454,7 +1464,7 @@ cudaError_t launch_audit_segments(const unsigned long long* slots, const int* se
 
 cudaError_t launch_close(const LevelDev* levs, const Item* items, int n, int kk, cudaStream_t s, const int* nc) {
     if (n <= 0) return cudaSuccess;
-    close_kernel<<<list_grid(n, nc), CTA_THREADS, 0, s>>>(levs, items, n, kk, nc);
+    close_kernel<<<list_grid(close_kernel, n, nc), CTA_THREADS, 0, s>>>(levs, items, n, kk, nc);
     return cudaGetLastError();
 }
 
@@ -1489,7 +1499,7 @@ int audit_blocks(int nitems) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, audit_kernel, 256, 0);
         resident = std::max(1, sms * std::max(1, per));
     }
-    return tile_grid(nitems, resident);
+    return std::max(1, std::min(nitems, resident));  // a CTA per tile at a time
 }
 
 cudaError_t launch_audit(const LevelDev* levs, const Item* items, int n, unsigned long long* part, double* out,
@@ -1503,41 +1513,41 @@ cudaError_t launch_audit(const LevelDev* levs, const Item* items, int n, unsigne
 cudaError_t launch_avgdown(const LevelDev& C, const LevelDev& F, const Item* items, int n, cudaStream_t s,
                            const int* nc) {
     if (n <= 0) return cudaSuccess;
-    avgdown_kernel<<<list_grid(4 * n, nc), CTA_THREADS, 0, s>>>(C, F, items, n, nc);
+    avgdown_kernel<<<list_grid(avgdown_kernel, 4 * n, nc), CTA_THREADS, 0, s>>>(C, F, items, n, nc);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tag(const LevelDev& L, const Item* items, int n, double tol2, int buffer, uint8_t* bflag,
                        cudaStream_t s, const int* nc) {
     if (n <= 0) return cudaSuccess;
-    tag_kernel<<<list_grid(n, nc), CTA_THREADS, 0, s>>>(L, items, n, tol2, buffer, bflag, nc);
+    tag_kernel<<<list_grid(tag_kernel, n, nc), CTA_THREADS, 0, s>>>(L, items, n, tol2, buffer, bflag, nc);
     return cudaGetLastError();
 }
 
 cudaError_t launch_qmax(const LevelDev& L, const Item* items, int n, unsigned long long* qmax, cudaStream_t s,
                         const int* nc) {
     if (n <= 0) return cudaSuccess;
-    qmax_kernel<<<list_grid(n, nc), CTA_THREADS, 0, s>>>(L, items, n, qmax, nc);
+    qmax_kernel<<<list_grid(qmax_kernel, n, nc), CTA_THREADS, 0, s>>>(L, items, n, qmax, nc);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tag_flux(const LevelDev& L, const Item* items, int n, const unsigned long long* qmax, double tol,
                             int buffer, uint8_t* bflag, cudaStream_t s, const int* nc) {
     if (n <= 0) return cudaSuccess;
-    tag_flux_kernel<<<list_grid(n, nc), CTA_THREADS, 0, s>>>(L, items, n, qmax, tol, buffer, bflag, nc);
+    tag_flux_kernel<<<list_grid(tag_flux_kernel, n, nc), CTA_THREADS, 0, s>>>(L, items, n, qmax, tol, buffer, bflag, nc);
     return cudaGetLastError();
 }
 
 cudaError_t launch_merge(const LevelDev& L, const Item* items, int n, cudaStream_t s, const int* nc) {
     if (n <= 0) return cudaSuccess;
-    merge_kernel<<<list_grid(4 * n, nc), CTA_THREADS, 0, s>>>(L, items, n, nc);
+    merge_kernel<<<list_grid(merge_kernel, 4 * n, nc), CTA_THREADS, 0, s>>>(L, items, n, nc);
     return cudaGetLastError();
 }
 
 cudaError_t launch_split(const LevelDev& C, const LevelDev& F, const Item* items, int n, cudaStream_t s,
                          const int* nc) {
     if (n <= 0) return cudaSuccess;
-    split_kernel<<<list_grid(4 * n, nc), CTA_THREADS, 0, s>>>(C, F, items, n, nc);
+    split_kernel<<<list_grid(split_kernel, 4 * n, nc), CTA_THREADS, 0, s>>>(C, F, items, n, nc);
     return cudaGetLastError();
 }
 
@@ -1548,7 +1558,7 @@ cudaError_t launch_flags(const LevelDev& L, const uint8_t* blk_in, const uint8_t
 }
 
 cudaError_t launch_flags_update(const FlagsSet& F, int cap, cudaStream_t s) {
-    const int g = list_grid(cap, F.nc[0]);
+    const int g = list_grid(flags_blocks_kernel, cap, F.nc[0]);
     flags_blocks_kernel<<<g, CTA_THREADS, 0, s>>>(F, 0);
     flags_blocks_kernel<<<g, CTA_THREADS, 0, s>>>(F, 1);
     return cudaGetLastError();

@@ -93,11 +93,12 @@ def tune(make, target=None, steps=64, candidates=None, cache_file=None, verbose=
 
 
 ADAPTIVE_CANDIDATES = [
+    {"variant": 1, "schedule": 1, "max_ctas": 0},
+    {"variant": 0, "schedule": 1, "max_ctas": 0},
+    {"variant": 2, "schedule": 1, "max_ctas": 0},
+    {"variant": 3, "schedule": 1, "max_ctas": 0},
     {"variant": 1, "schedule": 0, "max_ctas": 0},
     {"variant": 0, "schedule": 0, "max_ctas": 0},
-    {"variant": 1, "schedule": 0, "max_ctas": 148 * 3},
-    {"variant": 1, "schedule": 1, "max_ctas": 0},
-    {"variant": 3, "schedule": 1, "max_ctas": 0},
 ]
 
 

@@ -325,6 +325,7 @@ struct vlbm_hier {
     DArr<uint8_t> stage8;   // valid masks
     DArr<unsigned long long> qmax;  // flux-jump sensor: max |Q_k| (bit patterns)
     DArr<unsigned long long> partial;  // audit partial sums (exact, 24 words per block)
+    DArr<unsigned> aticket;            // the audit's finishing counter (zero between audits)
     DArr<double> tot;      // audit result
     DArr<Item> listbuf;    // item lists for regrid kernels
     DArr<uint8_t> bflag;   // block flags
@@ -363,8 +364,12 @@ struct vlbm_hier {
     double* raud = nullptr;
     long long ra_n = 0, ra_read = 0;
     static constexpr long long RA_CAP = 4096;
-    cudaGraphExec_t rg_exec = nullptr;   // the device regrid, captured
+    // the device regrid, captured in two parts: [0] indicator to new maps
+    // and move lists (reads the populations), [1] merge / split, flags and
+    // lists (writes them)
+    cudaGraphExec_t rg_exec[2] = {nullptr, nullptr};
     std::vector<uintptr_t> rg_key;
+    cudaEvent_t ev_rg0 = nullptr, ev_audit = nullptr;
     // Task lists built on the device for the persistent schedule (no
     // per-step audit): [0] one coarse step, [1] tune.graph_steps steps
     struct DevPlan {
@@ -1418,22 +1423,26 @@ void device_tags(vlbm_hier* h) {
 // merge (finest first) and split (coarsest first) of the cells that change,
 // the per-cell flags, then the new maps and lists.  Expects the composite
 // state of the current layout (device_tags).
-void device_apply_flags(vlbm_hier* h, const uint8_t* bflag) {
+void device_apply_flags(vlbm_hier* h, const uint8_t* bflag, int part = -1) {
     cudaStream_t s = h->stream;
     const int nl = h->nlev;
     size_t off[VLBM_MAX_LEVELS] = {};
     for (int l = 1; l < nl; l++) off[l] = off[l - 1] + (size_t)h->lev[l - 1].bx * h->lev[l - 1].by;
     LayoutDev* D[VLBM_MAX_LEVELS];
     for (int l = 0; l < nl; l++) D[l] = &h->lev[l].dl;
-    VCK(cudaMemsetAsync(D[nl - 1]->ncov, 0, (size_t)lcap(*D[nl - 1]), s));
-    for (int l = nl - 2; l >= 0; l--) VCK(launch_layout_rule(*D[l], l + 1 <= nl - 2 ? D[l + 1] : nullptr, bflag + off[l], s));
-    VCK(launch_derive_in(nullptr, *D[0], s));
-    for (int l = 1; l < nl; l++) VCK(launch_derive_in(D[l - 1], *D[l], s));
     const LayoutDev* const* DL = D;
-    VCK(launch_nest_check(DL, nl, h->words + 1, s));
-    int masks[VLBM_MAX_LEVELS];
-    for (int l = 0; l < nl; l++) masks[l] = l <= nl - 2 ? LISTS_MOVE : (1 << LST_TOUCH);
-    VCK(launch_lists(DL, masks, nl, s));
+    if (part != 1) {
+        VCK(cudaMemsetAsync(D[nl - 1]->ncov, 0, (size_t)lcap(*D[nl - 1]), s));
+        for (int l = nl - 2; l >= 0; l--)
+            VCK(launch_layout_rule(*D[l], l + 1 <= nl - 2 ? D[l + 1] : nullptr, bflag + off[l], s));
+        VCK(launch_derive_in(nullptr, *D[0], s));
+        for (int l = 1; l < nl; l++) VCK(launch_derive_in(D[l - 1], *D[l], s));
+        VCK(launch_nest_check(DL, nl, h->words + 1, s));
+        int masks[VLBM_MAX_LEVELS];
+        for (int l = 0; l < nl; l++) masks[l] = l <= nl - 2 ? LISTS_MOVE : (1 << LST_TOUCH);
+        VCK(launch_lists(DL, masks, nl, s));
+    }
+    if (part == 0) return;
     for (int l = nl - 2; l >= 0; l--)
         VCK(launch_merge(lvdev(h, l), D[l]->list[LST_EXIT], lcap(*D[l]), s, D[l]->cnt + LST_EXIT));
     for (int l = 0; l <= nl - 2; l++)
@@ -1472,39 +1481,56 @@ void device_regrid(vlbm_hier* h) {
         key.push_back((uintptr_t)h->lev[l].buf[0]);
     }
     cudaStream_t s = h->stream;
-    if (!h->rg_exec || key != h->rg_key) {
+    if (!h->rg_exec[0] || !h->rg_exec[1] || key != h->rg_key) {
         const auto t0 = std::chrono::steady_clock::now();
-        if (h->rg_exec) cudaGraphExecDestroy(h->rg_exec);
-        h->rg_exec = nullptr;
-        cudaGraph_t g = nullptr;
-        VCK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        try {
-            device_tags(h);
-            device_apply_flags(h, h->bflag.p);
-        } catch (...) {
-            cudaStreamEndCapture(s, &g);
-            if (g) cudaGraphDestroy(g);
-            throw;
+        for (int part = 0; part < 2; part++) {
+            cudaGraphExec_t& ex = h->rg_exec[part];
+            if (ex) cudaGraphExecDestroy(ex);
+            ex = nullptr;
+            cudaGraph_t g = nullptr;
+            VCK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            try {
+                if (part == 0) device_tags(h);
+                device_apply_flags(h, h->bflag.p, part);
+            } catch (...) {
+                cudaStreamEndCapture(s, &g);
+                if (g) cudaGraphDestroy(g);
+                throw;
+            }
+            VCK(cudaStreamEndCapture(s, &g));
+            cudaError_t e = instantiate(&ex, g);
+            cudaGraphDestroy(g);
+            VCK(e);
         }
-        VCK(cudaStreamEndCapture(s, &g));
-        cudaError_t e = instantiate(&h->rg_exec, g);
-        cudaGraphDestroy(g);
-        VCK(e);
         h->rg_key = key;
         h->times[VLBM_T_CAPTURE] += ms_since(t0);
     }
+    for (cudaEvent_t* ev : {&h->ev_layout, &h->ev_rg0, &h->ev_audit})
+        if (!*ev) VCK(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+    if (!h->aux) VCK(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
     const long long slot = h->ra_n % vlbm_hier::RA_CAP;
     const int icap = (int)std::min<size_t>(h->ditems_cap, 1u << 30);
-    if (h->regrid_audit)
-        VCK(launch_audit(h->atab.p, h->ditems, icap, h->partial.p, h->raud + 16 * slot, s, h->dcount));
-    VCK(cudaGraphLaunch(h->rg_exec, s));
-    h->klaunch += graph_kernels(h->rg_exec);
-    if (!h->ev_layout) VCK(cudaEventCreateWithFlags(&h->ev_layout, cudaEventDisableTiming));
+    if (h->regrid_audit) {
+        // the audit before the regrid reads the active cells' state, which
+        // the first part (indicator, maps, move lists) leaves alone: it runs
+        // beside it on the auxiliary stream, and the second part (merge,
+        // split: writes) waits for it
+        VCK(cudaEventRecord(h->ev_rg0, s));
+        VCK(cudaStreamWaitEvent(h->aux, h->ev_rg0, 0));
+        VCK(launch_audit(h->atab.p, h->ditems, icap, h->partial.p, h->raud + 16 * slot, h->aticket.p, h->aux,
+                         h->dcount));
+        VCK(cudaEventRecord(h->ev_audit, h->aux));
+    }
+    VCK(cudaGraphLaunch(h->rg_exec[0], s));
+    if (h->regrid_audit) VCK(cudaStreamWaitEvent(s, h->ev_audit, 0));
+    VCK(cudaGraphLaunch(h->rg_exec[1], s));
+    h->klaunch += graph_kernels(h->rg_exec[0]) + graph_kernels(h->rg_exec[1]);
     VCK(cudaEventRecord(h->ev_layout, s));  // the new layout is complete here
     if (h->regrid_audit) {
-        VCK(launch_audit(h->atab.p, h->ditems, icap, h->partial.p, h->raud + 16 * slot + 8, s, h->dcount));
+        VCK(launch_audit(h->atab.p, h->ditems, icap, h->partial.p, h->raud + 16 * slot + 8, h->aticket.p, s,
+                         h->dcount));
         h->ra_n++;
-        h->klaunch += 4;  // two audits: partial sums and their rounding each
+        h->klaunch += 2;  // two audits
     }
     h->host_ok = false;
     layout_changed(h);
@@ -1836,8 +1862,10 @@ void release_dev_plans(vlbm_hier* h) {
         P.exec = nullptr;
         P.key.clear();
     }
-    if (h->rg_exec) cudaGraphExecDestroy(h->rg_exec);
-    h->rg_exec = nullptr;
+    for (auto& x : h->rg_exec) {
+        if (x) cudaGraphExecDestroy(x);
+        x = nullptr;
+    }
     h->rg_key.clear();
 }
 
@@ -1961,6 +1989,7 @@ void destroy_levels(vlbm_hier* h) {
     h->stage8.release(h->mem);
     h->qmax.release(h->mem);
     h->partial.release(h->mem);
+    h->aticket.release(h->mem);
     h->tot.release(h->mem);
     h->listbuf.release(h->mem);
     h->bflag.release(h->mem);
@@ -1989,9 +2018,10 @@ void destroy_levels(vlbm_hier* h) {
         cudaStreamDestroy(h->aux);
     }
     h->aux = nullptr;
-    if (h->ev_layout) cudaEventDestroy(h->ev_layout);
-    if (h->ev_built) cudaEventDestroy(h->ev_built);
-    h->ev_layout = h->ev_built = nullptr;
+    for (cudaEvent_t* ev : {&h->ev_layout, &h->ev_built, &h->ev_rg0, &h->ev_audit}) {
+        if (*ev) cudaEventDestroy(*ev);
+        *ev = nullptr;
+    }
     pin_free(h->hist, (size_t)h->hist_cap * 8 * sizeof(double));
     h->hist = nullptr;
     for (auto& L : h->tl) {
@@ -2133,6 +2163,8 @@ vlbm_status vlbm_create_hierarchy(const vlbm_config* cfg, const vlbm_allocator* 
         VCK(cudaMemsetAsync(h->lupc, 0, sizeof(unsigned long long), h->stream));
         VCK(cudaMemcpyAsync(h->parp, &h->words, sizeof(int*), cudaMemcpyHostToDevice, h->stream));
         h->partial.ensure(h->mem, (size_t)24 * audit_blocks((int)std::min<size_t>(h->ditems_cap, 1u << 30)));
+        h->aticket.ensure(h->mem, 1);
+        VCK(cudaMemsetAsync(h->aticket.p, 0, sizeof(unsigned), h->stream));
         h->tot.ensure(h->mem, 8);
         std::vector<uint8_t> bin[VLBM_MAX_LEVELS], bcov[VLBM_MAX_LEVELS];
         boxes_to_maps(h, h->boxes.data(), (int)h->boxes.size(), bcov);
@@ -2439,8 +2471,8 @@ vlbm_status vlbm_sync(vlbm_hier* h) {
 static void audit_impl(vlbm_hier* h, double* totals, double* abs_totals) {
     if (!h->hout) h->hout = (double*)pin_alloc(8 * sizeof(double));
     VCK(launch_audit(h->atab.p, h->ditems, (int)std::min<size_t>(h->ditems_cap, 1u << 30), h->partial.p, h->tot.p,
-                     h->stream, h->dcount));
-    h->klaunch += 2;
+                     h->aticket.p, h->stream, h->dcount));
+    h->klaunch += 1;
     VCK(cudaMemcpyAsync(h->hout, h->tot.p, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     VCK(cudaStreamSynchronize(h->stream));
     if (totals) std::memcpy(totals, h->hout, 4 * sizeof(double));

@@ -244,38 +244,41 @@ __device__ double sensor_beta_at(const LevelDev& L, int x, int y) {
 // the fused level sweep: collide, push-stream, boundary and coarse-to-fine
 // ---------------------------------------------------------------------------
 
-// Boundary values and reconstructed coarse-to-fine values for the incoming
-// populations of a cell whose upwind neighbour is outside the domain or in
-// coarser territory.  fs holds the cell's post-collision populations.
-template <bool COH>
-__device__ __noinline__ void sweep_special(const LevelDev* __restrict__ levs, const LevelDev& L, int x, int y,
-                                          long long c, uint32_t fl, const double* fs, double* dst, int kk,
-                                          int kkp, int step) {
-    // boundary conditions
-    if (fl & F_BND) {
-        for (int i = 0; i < 4; i++) {
-            int side = -1;
-            if (i == 0 && x == 0 && !L.px) side = 0;
-            if (i == 1 && x == L.nx - 1 && !L.px) side = 1;
-            if (i == 2 && y == 0 && !L.py) side = 2;
-            if (i == 3 && y == L.ny - 1 && !L.py) side = 3;
-            if (side < 0) continue;
-            const int bc = L.bc[side];
-            const int normal = side < 2 ? 1 : 2;
-            for (int k = 0; k < 4; k++) {
-                double v;
-                if (bc == BC_OUTFLOW) {
-                    v = fs[4 * i + k];
-                } else if (bc == BC_INFLOW) {
-                    v = L.feqb[side][4 * i + k];
-                } else {
-                    const double m = fs[4 * (i ^ 1) + k];
-                    v = (k == normal) ? -m : m;
-                }
-                dst[qoff(4 * i + k, L.plane, c)] = v;
+// Boundary values for the incoming populations of a cell whose upwind
+// neighbour lies beyond a non-periodic side of the domain; f holds the
+// cell's post-collision populations (constant indices only, so they stay in
+// registers).
+__device__ __forceinline__ void sweep_boundary(const LevelDev& L, int x, int y, long long c, const double (&f)[16],
+                                               double* dst) {
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        // side i: west (i = 0, x == 0), east, south, north
+        const bool on = i == 0 ? (x == 0 && !L.px)
+                                : i == 1 ? (x == L.nx - 1 && !L.px) : i == 2 ? (y == 0 && !L.py) : (y == L.ny - 1 && !L.py);
+        if (!on) continue;
+        const int bc = L.bc[i];
+        const int normal = i < 2 ? 1 : 2;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            double v;
+            if (bc == BC_OUTFLOW) {
+                v = f[4 * i + k];
+            } else if (bc == BC_INFLOW) {
+                v = L.feqb[i][4 * i + k];
+            } else {
+                const double m = f[4 * (i ^ 1) + k];
+                v = (k == normal) ? -m : m;
             }
+            dst[qoff(4 * i + k, L.plane, c)] = v;
         }
     }
+}
+
+// Reconstructed coarse-to-fine values for the incoming populations of a
+// cell whose upwind neighbour lies in coarser territory.
+template <bool COH>
+__device__ __noinline__ void sweep_recon(const LevelDev* __restrict__ levs, const LevelDev& L, int x, int y,
+                                        long long c, uint32_t fl, double* dst, int kk, int kkp, int step) {
     // coarse-to-fine reconstruction (Sec. 3.3, Eqs. 22-23)
     const uint32_t rec = (fl & F_RECON_MASK) >> F_RECON_SHIFT;
     if (!rec) return;
@@ -375,7 +378,8 @@ __device__ __forceinline__ void sweep_cell(const LevelDev* __restrict__ levs, co
     if (oxm) push(1, cxm);
     if (oyp) push(2, cyp);
     if (oym) push(3, cym);
-    if (fl & (F_BND | F_RECON_MASK)) sweep_special<COH>(levs, L, x, y, c, fl, f, dst, kk, kkp, step);
+    if (fl & F_BND) sweep_boundary(L, x, y, c, f, dst);
+    if (fl & F_RECON_MASK) sweep_recon<COH>(levs, L, x, y, c, fl, dst, kk, kkp, step);
 }
 
 // One step of one level for every tile in `items` (all of the same level
@@ -913,9 +917,39 @@ __global__ void gather_W_kernel(LevelDev L, double* __restrict__ W, long long ld
 // part[blk][0..23] = sum w W_k (k = 0..3), then sum w |W_k|, w = 4^-level,
 // as 192-bit fixed point (three words each).  A CTA takes one tile at a
 // time; its 64-thread group g adds up field k = g of the tile's cells, so a
-// thread holds two accumulators and many CTAs fit on an SM.
+// thread holds two accumulators and many CTAs fit on an SM.  The last CTA to
+// finish writes the rounded totals out[0..7] (ticket: a zeroed counter,
+// left zeroed).
+// The CTA that finishes last: out[m] = the correctly rounded sum of quantity
+// m over the partials of the launch's nb blocks, one quantity at a time.
+__device__ __noinline__ void audit_finish(const unsigned long long* part, int nb, double* out) {
+    __shared__ Fix192 red[8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int m = 0; m < 8; m++) {
+        Fix192 a = fix_zero();
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+            Fix192 v;
+            for (int j = 0; j < 3; j++) v.w[j] = __ldcg(part + (size_t)i * 24 + 3 * m + j);
+            fix_add(a, v);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const Fix192 b = fix_shfl_down(a, o);
+            fix_add(a, b);
+        }
+        if (lane == 0) red[wid] = a;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            Fix192 t = red[0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); w++) fix_add(t, red[w]);
+            out[m] = fix_to_double(t);
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(256) audit_kernel(const LevelDev* __restrict__ levs, const Item* __restrict__ items,
                                                     int nitems, unsigned long long* __restrict__ part,
+                                                    double* __restrict__ out, unsigned* __restrict__ ticket,
                                                     const int* __restrict__ ncount) {
     if (ncount) nitems = *ncount;
     const int k = threadIdx.x >> 6;
@@ -954,6 +988,18 @@ __global__ void __launch_bounds__(256) audit_kernel(const LevelDev* __restrict__
         fix_add(a, sh[2 * f + 1][j]);
         for (int i = 0; i < 3; i++) part[(size_t)blockIdx.x * 24 + 3 * m + i] = a.w[i];
     }
+    // the last CTA to finish adds up every CTA's partials and resets the ticket
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    audit_finish(part, gridDim.x, out);
+    if (threadIdx.x == 0) *ticket = 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -1503,10 +1549,9 @@ int audit_blocks(int nitems) {
 }
 
 cudaError_t launch_audit(const LevelDev* levs, const Item* items, int n, unsigned long long* part, double* out,
-                         cudaStream_t s, const int* nc) {
+                         unsigned* ticket, cudaStream_t s, const int* nc) {
     const int g = audit_blocks(n);
-    if (n > 0) audit_kernel<<<g, 256, 0, s>>>(levs, items, n, part, nc);
-    audit_segments_kernel<<<1, 256, 0, s>>>(part, nullptr, n > 0 ? g : 0, out);
+    audit_kernel<<<g, 256, 0, s>>>(levs, items, n, part, out, ticket, nc);
     return cudaGetLastError();
 }
 

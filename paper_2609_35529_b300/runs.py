@@ -2,21 +2,22 @@
 each one is about.  One JSON line per run on stdout.
 
   python -m paper_2609_35529_b300.runs [pulse] [vortex] [riemann] [riemann_sensor]
-                                      [shockbubble[=steps,every,schedule]]
+                                      [shockbubble[=steps,every,schedule,nx0]]
 
 pulse        two-level Gaussian pulse, periodic 64^2, 200 coarse steps:
              per-step conservation (fused audit) and the uniform-state run
 vortex       advected isentropic vortex, N = 128, 256, 512 with a central
              ratio-2 patch, one period (t = 10): L2 error of rho and |u|
-             against the exact solution (the initial state), the observed
+             against the exact solution at the final time, the observed
              order, and the same for uniform grids of N and 2N
 riemann      Lax-Liu configuration 3, 1024^2, three levels, t = 0.3:
              throughput, x<->y symmetry of the result (bitwise)
 riemann_sensor[=N,levels,beta_max_permille,C]  the same with the sensor-driven
              relaxation (beta between 0.5 and beta_max)
-shockbubble  adaptive shock-bubble, 2048 x 1024, up to three levels,
-             regrid every 4 coarse steps, 4000 steps: conservation audited
-             across every regrid, throughput including regrids
+shockbubble  adaptive shock-bubble, nx0 x nx0/2 (default 2048 x 1024), up to
+             three levels, regrid every 4 coarse steps on the device, 4000
+             steps on the persistent schedule (default): conservation audited
+             exactly across every regrid, throughput including regrids
 """
 import json
 import math
@@ -191,39 +192,39 @@ def run_riemann_sensor(N=1024, nlev=3, beta_max_permille=1000, c_sensor=64):
           "beta": [0.5, bmax], "c_sensor": c_sensor, "physical_to_end": True})
 
 
-def run_shockbubble(steps=4000, every=4, schedule=2):
-    """The adaptive run; the totals are audited (exactly) before and after
-    every regrid.  schedule 2 (auto) keeps the per-phase launches on layouts
-    that live only `every` steps."""
-    cs = I.shockbubble(steps=steps)
+def run_shockbubble(steps=4000, every=4, schedule=1, nx0=2048):
+    """The adaptive run (nx0 x nx0/2 coarse cells, three levels, a regrid
+    every `every` coarse steps, all on the device); the totals are audited
+    exactly before and after every regrid, on the device, and read back at
+    the end."""
+    cs = I.shockbubble(nx0=nx0, ny0=nx0 // 2, steps=steps)
     h = V.Hierarchy.from_case(cs)
-    h.set_tuning(schedule=schedule)
+    h.set_tuning(schedule=schedule, graph_steps=every, persist_after=0)
     for _ in range(cs.nlev - 1):
         h.regrid()
-    worst = 0.0
-    lups = 0
-    active = []
+    h.set_regrid_audit(True)
+    start = h.lups_done()
     t0 = now()
     done = 0
     while done < steps:
         n = min(every, steps - done)
-        lups += n * h.info()["lups_per_step"]
         h.advance(n)
         done += n
         if done < steps:
-            t_before, a_before = h.audit()
             h.regrid()
-            t_after, _ = h.audit()
-            d = np.abs(t_after - t_before)
-            worst = max(worst, float(np.max(np.where(a_before > 0, d / np.where(a_before > 0, a_before, 1), d))))
-        if done % 500 == 0:
-            active.append([done] + h.info()["active_cells"])
     h.sync()
     el = now() - t0
+    rows = h.regrid_audits()
+    worst = 0.0
+    if len(rows):
+        d = np.abs(rows[:, 8:12] - rows[:, 0:4])
+        a = rows[:, 4:8]
+        worst = float(np.max(np.where(a > 0, d / np.where(a > 0, a, 1), d)))
     emit({"run": "shockbubble", "coarse": [cs.nx0, cs.ny0], "levels": cs.nlev, "steps": steps, "schedule": schedule,
-          "regrids": (steps - 1) // every, "wall_s": el, "mlups_incl_regrid": lups / el / 1e6,
-          "max_rel_change_across_regrid": worst, "active_cells_every_500": active,
+          "regrids": (steps - 1) // every, "wall_s": el, "mlups_incl_regrid": (h.lups_done() - start) / el / 1e6,
+          "max_rel_change_across_regrid": worst, "active_cells_at_end": h.info()["active_cells"],
           "host_ms": h.host_times()})
+    h.close()
 
 
 def main(argv=None):

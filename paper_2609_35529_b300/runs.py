@@ -204,6 +204,7 @@ def run_shockbubble(steps=4000, every=4, schedule=1, nx0=2048):
         h.regrid()
     h.set_regrid_audit(True)
     start = h.lups_done()
+    per_step0 = h.info()["lups_per_step"]
     t0 = now()
     done = 0
     while done < steps:
@@ -222,7 +223,8 @@ def run_shockbubble(steps=4000, every=4, schedule=1, nx0=2048):
         worst = float(np.max(np.where(a > 0, d / np.where(a > 0, a, 1), d)))
     emit({"run": "shockbubble", "coarse": [cs.nx0, cs.ny0], "levels": cs.nlev, "steps": steps, "schedule": schedule,
           "regrids": (steps - 1) // every, "wall_s": el, "mlups_incl_regrid": (h.lups_done() - start) / el / 1e6,
-          "max_rel_change_across_regrid": worst, "active_cells_at_end": h.info()["active_cells"],
+          "max_rel_change_across_regrid": worst, "lups_per_step_at_start": per_step0,
+          "active_cells_at_end": h.info()["active_cells"],
           "host_ms": h.host_times()})
     h.close()
 

@@ -1418,11 +1418,13 @@ void device_tags(vlbm_hier* h) {
     }
 }
 
-// From block flags to the new layout, on the device: the layout rule
-// (finest refinable level first), the new on-level maps, the nesting check,
-// merge (finest first) and split (coarsest first) of the cells that change,
-// the per-cell flags, then the new maps and lists.  Expects the composite
-// state of the current layout (device_tags).
+// From block flags to the new layout, on the device.  Part 0 (reads the
+// populations only): the layout rule (finest refinable level first), the
+// new on-level maps, the nesting check, the exit / enter / touch lists and
+// the new layout's tile lists and index maps; part 1: merge (finest first)
+// and split (coarsest first) of the cells that change, the per-cell flags,
+// the new maps committed and the audit's tile list; part -1: both.  Expects
+// the composite state of the current layout (device_tags).
 void device_apply_flags(vlbm_hier* h, const uint8_t* bflag, int part = -1) {
     cudaStream_t s = h->stream;
     const int nl = h->nlev;
@@ -1441,6 +1443,20 @@ void device_apply_flags(vlbm_hier* h, const uint8_t* bflag, int part = -1) {
         int masks[VLBM_MAX_LEVELS];
         for (int l = 0; l < nl; l++) masks[l] = l <= nl - 2 ? LISTS_MOVE : (1 << LST_TOUCH);
         VCK(launch_lists(DL, masks, nl, s));
+        // the tile lists and index maps of the new layout, from the new maps
+        // (the current ones are committed in the second part): everything a
+        // task-list build reads is final once this part is done
+        LayoutDev NL[VLBM_MAX_LEVELS];
+        const LayoutDev* NP[VLBM_MAX_LEVELS];
+        for (int l = 0; l < nl; l++) {
+            NL[l] = *D[l];
+            NL[l].bin = D[l]->nin;
+            NL[l].bcov = D[l]->ncov;
+            NL[l].nin = NL[l].ncov = nullptr;
+            NP[l] = &NL[l];
+            masks[l] = LISTS_ALL;
+        }
+        VCK(launch_lists(NP, masks, nl, s));
     }
     if (part == 0) return;
     for (int l = nl - 2; l >= 0; l--)
@@ -1464,7 +1480,9 @@ void device_apply_flags(vlbm_hier* h, const uint8_t* bflag, int part = -1) {
     }
     VCK(launch_flags_update(F, cap, s));
     VCK(launch_commit_maps(DL, nl, s));
-    device_lists(h);
+    LayoutDev dls[VLBM_MAX_LEVELS];
+    for (int l = 0; l < nl; l++) dls[l] = *D[l];
+    VCK(launch_concat_act(dls, nl, h->ditems, h->dcount, s));
 }
 
 // A tag-driven regrid on the device: indicator, block flags, new layout,
@@ -1522,10 +1540,10 @@ void device_regrid(vlbm_hier* h) {
         VCK(cudaEventRecord(h->ev_audit, h->aux));
     }
     VCK(cudaGraphLaunch(h->rg_exec[0], s));
+    VCK(cudaEventRecord(h->ev_layout, s));  // the new layout's maps and lists are complete here
     if (h->regrid_audit) VCK(cudaStreamWaitEvent(s, h->ev_audit, 0));
     VCK(cudaGraphLaunch(h->rg_exec[1], s));
     h->klaunch += graph_kernels(h->rg_exec[0]) + graph_kernels(h->rg_exec[1]);
-    VCK(cudaEventRecord(h->ev_layout, s));  // the new layout is complete here
     if (h->regrid_audit) {
         VCK(launch_audit(h->atab.p, h->ditems, icap, h->partial.p, h->raud + 16 * slot + 8, h->aticket.p, s,
                          h->dcount));

@@ -287,6 +287,8 @@ def run(argv=None):
                     help="also measure the one-at-a-time capacity (whole trace offered at t = 0)")
     ap.add_argument("--capacity-only", action="store_true",
                     help="stop after the capacity measurements (no latency runs)")
+    ap.add_argument("--work-cap", type=float, default=0.0,
+                    help="admission cap on the residents' cell updates per coarse step, in millions (0: none)")
     args = ap.parse_args(argv)
     import sys
     log = (lambda *a: print(*a, file=sys.stderr, flush=True)) if args.verbose else (lambda *a: None)
@@ -303,7 +305,8 @@ def run(argv=None):
     # capacity: the whole trace offered at once (all arrivals at t = 0)
     for r in reqs:
         r.arrival = 0.0
-    _, cap_mlups, cap_wall = serve_batched(reqs, budget, stream=stream, setup_stream=setup)
+    wcap = args.work_cap * 1e6
+    _, cap_mlups, cap_wall = serve_batched(reqs, budget, stream=stream, setup_stream=setup, work_cap=wcap)
     log(f"capacity: {cap_mlups:.1f} MLUPS, {cap_wall:.1f} s, {serve_batched.breakdown}")
     cap1 = None
     if args.capacity_one:
@@ -317,7 +320,7 @@ def run(argv=None):
     rate = args.load * len(reqs) / cap_wall
     schedule(reqs, rate, args.seed)
     sample = set(r.rid for r in sorted(reqs, key=lambda r: r.lups)[: args.keep_sample])
-    tts_b, ml_b, wall_b = serve_batched(reqs, budget, stream, sample, setup_stream=setup, verify=True)
+    tts_b, ml_b, wall_b = serve_batched(reqs, budget, stream, sample, setup_stream=setup, verify=True, work_cap=wcap)
     breakdown = serve_batched.breakdown
     log(f"batched: {ml_b:.1f} MLUPS, {wall_b:.1f} s, {breakdown}")
     kept = {r.rid: r.result for r in reqs if r.rid in sample}
@@ -325,7 +328,7 @@ def run(argv=None):
     log(f"one at a time: {ml_1:.1f} MLUPS, {wall_1:.1f} s")
     out = {"requests": len(reqs), "total_lups": total, "capacity_mlups": round(cap_mlups, 1),
            "capacity_one_at_a_time_mlups": round(cap1, 1) if cap1 else None,
-           "rate_per_s": round(rate, 3), "load": args.load,
+           "rate_per_s": round(rate, 3), "load": args.load, "work_cap_mlup_per_step": args.work_cap,
            "batched": {"mlups": round(ml_b, 1), "p50_s": float(np.percentile(tts_b, 50)),
                        "p99_s": float(np.percentile(tts_b, 99)), "wall_s": wall_b, "breakdown": breakdown},
            "one_at_a_time": {"mlups": round(ml_1, 1), "p50_s": float(np.percentile(tts_1, 50)),
@@ -343,12 +346,15 @@ def run(argv=None):
 MAX_STEPS = 16
 
 
-def serve_batched(reqs, budget, stream=None, keep_ids=(), setup_stream=None, verify=False):
+def serve_batched(reqs, budget, stream=None, keep_ids=(), setup_stream=None, verify=False, work_cap=0):
     """Continuous batching over the engine.  New requests are set up on their
     own stream (`setup_stream`) so that their set-up overlaps the engine's
-    queued steps.  Returns per-request time-to-solution (s), the aggregate
-    MLUPS and the wall time; the final populations of the requests in
-    keep_ids are kept in `result`."""
+    queued steps.  work_cap > 0 admits a request only while the residents'
+    cell updates per coarse step stay within it (beyond the point where the
+    GPU is busy, more residents only share it more thinly, which delays the
+    long requests); the others wait in arrival order.  Returns per-request
+    time-to-solution (s), the aggregate MLUPS and the wall time; the final
+    populations of the requests in keep_ids are kept in `result`."""
     eng = V.Engine(budget, stream=stream)
     pending = sorted(reqs, key=lambda r: r.arrival)
     for r in reqs:
@@ -356,6 +362,7 @@ def serve_batched(reqs, budget, stream=None, keep_ids=(), setup_stream=None, ver
         r.case = None
     live = {}
     used = 0
+    work = 0.0
     nxt = 0
     pay = Payloads(reqs)
     t0 = time.perf_counter()
@@ -398,6 +405,7 @@ def serve_batched(reqs, budget, stream=None, keep_ids=(), setup_stream=None, ver
                     host_ms[k] = host_ms.get(k, 0.0) + v
                 h.close()
                 used -= r.bytes_est
+                work -= r.lups / max(1, r.steps)
             spent["finish_s"] += time.perf_counter() - tb
         # 2. admit arrived requests while the memory budget allows (a few per
         #    round, so that the queue of steps is refilled in between)
@@ -406,6 +414,8 @@ def serve_batched(reqs, budget, stream=None, keep_ids=(), setup_stream=None, ver
         while nxt < len(pending) and pending[nxt].arrival <= now and admitted < 4:
             r = pending[nxt]
             if live and used + r.bytes_est > budget:
+                break
+            if live and work_cap > 0 and work + r.lups / max(1, r.steps) > work_cap:
                 break
             ta = time.perf_counter()
             if r.case is None:
@@ -419,6 +429,7 @@ def serve_batched(reqs, budget, stream=None, keep_ids=(), setup_stream=None, ver
             r.case = None
             live[slot] = (r, h)
             used += r.bytes_est
+            work += r.lups / max(1, r.steps)
             nxt += 1
             admitted += 1
         if not live and nxt < len(pending):

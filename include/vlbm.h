@@ -455,10 +455,16 @@ void vlbm_destroy(vlbm_hier* h);
 
 /* ---- batching / serving engine ------------------------------------------ */
 
-/* An engine advances many resident hierarchies together: every engine step
- * is one coarse step of every resident, issued as one launch per phase of
- * the sub-cycle (level-0 sweep, level-1 sweeps, reflux closes, ...), each
- * processing the tiles of all residents.  mem_budget bounds the summed
+/* An engine advances many resident hierarchies together: the k coarse
+ * steps of one call run for every resident as one launch per phase of the
+ * sub-cycle covering the tiles of all residents (schedule 0, the default),
+ * or in one persistent launch of the task kernel (schedule 1: each
+ * resident's one-step task list, built on the device when its layout
+ * changes, merged phase-major with the others -- every resident's tasks of a
+ * phase before any resident's tasks of the next -- so no thread group waits
+ * at a small resident's phase boundary while others have ready work; the
+ * per-phase launches serve while a resident runs the sensor-driven
+ * relaxation).  mem_budget bounds the summed
  * device memory of the residents (0 = no bound).  alloc (may be NULL:
  * stream-ordered cudaMallocAsync) provides the engine's own device memory
  * (its launch tables); the residents' memory comes from their own handles.
@@ -475,10 +481,9 @@ vlbm_status vlbm_engine_admit(vlbm_engine* e, vlbm_hier* h, int64_t coarse_steps
                               int32_t regrid_every, int32_t* slot);
 
 /* Queues the next k coarse steps of every resident that can step, 1 <= k
- * <= max_steps, as many as no resident reaches its step count or an
- * adaptive resident its next regrid in between.  Every resident runs on
- * per-phase launches shared by all residents (one launch per level phase
- * covers the tiles of every resident); each resident's result is the same
+ * <= max_steps (at most 64), as many as no resident reaches its step count
+ * or an adaptive resident its next regrid in between, on the engine's
+ * schedule (vlbm_engine_set_schedule); each resident's result is the same
  * as when it is advanced alone.  An adaptive resident due for a regrid pauses: the
  * first half of its regrid is queued on a high-priority stream, a later
  * call finishes it once its block flags are on the host.  Asynchronous:
@@ -493,6 +498,12 @@ vlbm_status vlbm_engine_admit(vlbm_engine* e, vlbm_hier* h, int64_t coarse_steps
  * ERR_CUDA, errors of a resident's regrid. */
 vlbm_status vlbm_engine_advance(vlbm_engine* e, int32_t max_steps, int32_t* finished_slots, int32_t* nfinished,
                                 int32_t* steps);
+
+/* The engine's schedule: 0 (default) one launch per phase shared by all
+ * residents; 1 one persistent launch per call over every resident's
+ * device-built task list, phase-major.  Results do not depend on it.
+ * Errors: ERR_ARG (unknown schedule). */
+vlbm_status vlbm_engine_set_schedule(vlbm_engine* e, int32_t schedule);
 
 /* vlbm_engine_advance with max_steps = 1. */
 vlbm_status vlbm_engine_step(vlbm_engine* e, int32_t* finished_slots, int32_t* nfinished);

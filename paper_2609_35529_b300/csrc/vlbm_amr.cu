@@ -927,6 +927,55 @@ __global__ void tb_finish_kernel(TBPlan P) {
     P.ctl[CTL_TOTAL] = total;
 }
 
+// The chunk table of a persistent launch over several one-step task lists
+// (segments), phase-major: for each phase p, for each segment m, the run of
+// m's tasks of phase p (`offs[m][p] .. offs[m][p + 1]`).  A segment whose
+// build failed (its own task count, mctl[m][CTL_TOTAL], is not its phase
+// total) contributes nothing.  One CTA; entries p * nm + m in rounds of the
+// CTA's threads, two scans per round (tickets and non-empty chunks).
+__global__ void merge_chunks_kernel(const int* const* __restrict__ offs, const int* const* __restrict__ mctl, int nm,
+                                    int nphase, int* __restrict__ prefix, int2* __restrict__ chunks, int* ctl) {
+    __shared__ int sm[32];
+    __shared__ int carry_t, carry_c;
+    if (threadIdx.x == 0) carry_t = carry_c = 0;
+    __syncthreads();
+    const int ne = nphase * nm;
+    for (int r = 0; r < ne; r += blockDim.x) {
+        const int e = r + threadIdx.x;
+        int cnt = 0, a = 0, m = 0;
+        if (e < ne) {
+            const int p = e / nm;
+            m = e - p * nm;
+            const int* o = offs[m];
+            if (mctl[m][CTL_TOTAL] == o[nphase]) {
+                a = o[p];
+                cnt = o[p + 1] - a;
+            }
+        }
+        int tt, tc;
+        const int xt = cta_excl(cnt, sm, &tt);
+        const int xc = cta_excl(cnt > 0 ? 1 : 0, sm, &tc);
+        if (cnt > 0) {
+            prefix[carry_c + xc] = carry_t + xt;
+            chunks[carry_c + xc] = make_int2(m, a);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            carry_t += tt;
+            carry_c += tc;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        prefix[carry_c] = carry_t;
+        ctl[CTL_CLAIM] = 0;
+        ctl[CTL_FIN] = 0;
+        ctl[CTL_TOTAL] = carry_t;
+        ctl[CTL_NSEG] = nm;
+        ctl[CTL_NCHUNK] = carry_c;
+    }
+}
+
 }  // namespace
 
 
@@ -1002,6 +1051,12 @@ cudaError_t launch_count_lups(const LayoutDev* levs, int n, long long steps, uns
     const unsigned long long* c[4] = {nullptr, nullptr, nullptr, nullptr};
     for (int l = 0; l < n; l++) c[l] = levs[l].cells;
     count_lups_kernel<<<1, 1, 0, s>>>(c[0], c[1], c[2], c[3], n, steps, counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge_chunks(const int* const* offs, const int* const* mctl, int nm, int nphase, int* prefix,
+                                int2* chunks, int* ctl, cudaStream_t s) {
+    merge_chunks_kernel<<<1, 1024, 0, s>>>(offs, mctl, nm, nphase, prefix, chunks, ctl);
     return cudaGetLastError();
 }
 

@@ -155,5 +155,14 @@ struct TBPlan {
 // exhausted the list is left empty (the launch does nothing) and
 // ST_TASKCAP is set in *status.
 cudaError_t launch_task_build(const TBPlan& P, cudaStream_t s);
+// The chunk table of one persistent launch over nm one-step task lists with
+// the same phase sequence (nphase phases), phase-major: per phase, each
+// list's tasks of that phase in turn.  offs[m]: list m's phase offsets
+// (device, nphase + 1 ints); mctl[m]: its own control words (a list whose
+// build failed is left out).  Writes prefix (<= nphase * nm + 1), chunks
+// (<= nphase * nm) and the launch's control words (counters reset; the
+// epoch and the parity flip are left as they are).
+cudaError_t launch_merge_chunks(const int* const* offs, const int* const* mctl, int nm, int nphase, int* prefix,
+                                int2* chunks, int* ctl, cudaStream_t s);
 
 }  // namespace vlbm

@@ -129,6 +129,19 @@ struct Segment {
 };
 
 // control words of a persistent launch
-enum : int { CTL_CLAIM = 0, CTL_FIN = 1, CTL_EPOCH = 2, CTL_TOTAL = 3, CTL_NSEG = 4, CTL_FLIP = 5, CTL_WORDS = 8 };
+// Control words of a persistent launch: ticket and finish counters, launch
+// epoch, tasks per iteration, segments (hierarchies), flip of the level-0
+// parity after an odd number of one-step iterations, and chunks -- runs of
+// consecutive tickets that are consecutive tasks of one segment.
+enum : int {
+    CTL_CLAIM = 0,
+    CTL_FIN = 1,
+    CTL_EPOCH = 2,
+    CTL_TOTAL = 3,
+    CTL_NSEG = 4,
+    CTL_FLIP = 5,
+    CTL_NCHUNK = 6,
+    CTL_WORDS = 8
+};
 
 }  // namespace vlbm

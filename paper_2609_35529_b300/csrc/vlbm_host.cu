@@ -379,6 +379,7 @@ struct vlbm_hier {
         DArr<TBPhase> ph;
         DArr<TBAcc> acc;
         DArr<int> acc_beg, acc_pos, off, deps, need, prefix, ctl, big;
+        DArr<int2> chunks;
         DArr<Task> tasks;
         DArr<unsigned> done;
         DArr<Segment> seg;
@@ -497,9 +498,16 @@ struct Batch {
             close[l].release(*mem);
         }
         par.release(*mem);
+        dsegs.release(*mem);
+        doffs.release(*mem);
+        dmctl.release(*mem);
+        dprefix.release(*mem);
+        dctl.release(*mem);
+        dchunks.release(*mem);
         for (int w = 0; w < 2; w++) {
             segs[w].release(*mem);
             prefix[w].release(*mem);
+            chunks[w].release(*mem);
             ctl[w].release(*mem);
             captured[w].clear();
             seg_ok[w] = false;
@@ -744,12 +752,25 @@ struct Batch {
         }
     }
 
+    // ---- one persistent launch over every member's device-built list ------
+    // (the engine): per call, each member's one-step list (rebuilt on the
+    // device when its layout changed), a segment table, and the chunk table
+    // that orders the members' tasks phase-major -- every member's phase-p
+    // tasks before any member's phase p + 1 -- so that no thread group waits
+    // at one small member's phase boundary while others have ready work
+    DArr<Segment> dsegs;
+    DArr<const int*> doffs, dmctl;
+    DArr<int> dprefix, dctl;
+    DArr<int2> dchunks;
+    void device_steps(long long k, cudaStream_t s);
+
     // ---- persistent task schedule -----------------------------------------
     int schedule_mode = 1;  // 0: one launch per phase, 1: persistent task kernel
     bool audit = false;     // fused per-step audit (single-member batches)
     // segment tables of the persistent launches: [0] one step, [1] G steps
     DArr<Segment> segs[2];
     DArr<int> prefix[2];
+    DArr<int2> chunks[2];
     DArr<int> ctl[2];
     int ntotal[2] = {0, 0};
     bool seg_ok[2] = {false, false};
@@ -769,7 +790,8 @@ struct Batch {
 
     void task_launch(int which, cudaStream_t s) {
         VCK(cudaMemsetAsync(ctl[which].p, 0, 2 * sizeof(int), s));  // claim and finish counters
-        VCK(launch_tasks(levs.p, segs[which].p, prefix[which].p, ctl[which].p, variant, max_ctas, 1, s));
+        VCK(launch_tasks(levs.p, segs[which].p, prefix[which].p, chunks[which].p, ctl[which].p, variant, max_ctas, 1,
+                         s));
         if (audit && members.size() == 1) {
             auto& T = members[0]->tl[which];
             VCK(launch_audit_segments(T.apart.p, T.abseg.p, T.nseg, T.aout.p, s));
@@ -873,7 +895,8 @@ void Batch::member_tasks(vlbm_hier* h, int which, int nsteps, bool aud) {
 
 std::vector<uintptr_t> Batch::launch_key(int which) const {
     std::vector<uintptr_t> k = {(uintptr_t)levs.p, (uintptr_t)segs[which].p, (uintptr_t)prefix[which].p,
-                                (uintptr_t)ctl[which].p, (uintptr_t)variant, (uintptr_t)max_ctas,
+                                (uintptr_t)chunks[which].p, (uintptr_t)ctl[which].p, (uintptr_t)variant,
+                                (uintptr_t)max_ctas,
                                 (uintptr_t)(audit && members.size() == 1)};
     if (audit && members.size() == 1) {
         const auto& T = members[0]->tl[which];
@@ -942,11 +965,15 @@ void Batch::build_segments(int which, int nsteps, cudaStream_t s) {
     c[CTL_TOTAL] = pre.back();
     c[CTL_NSEG] = (int)members.size();
     c[CTL_FLIP] = nsteps & 1;
+    c[CTL_NCHUNK] = (int)sg.size();  // one chunk per segment: member by member
+    std::vector<int2> ch(sg.size());
+    for (size_t m = 0; m < sg.size(); m++) ch[m] = make_int2((int)m, 0);
     // pinned staging: the engine's queued steps keep running meanwhile
-    stage_begin(sg.size() * sizeof(Segment) + (pre.size() + c.size()) * sizeof(int));
+    stage_begin(sg.size() * sizeof(Segment) + (pre.size() + c.size()) * sizeof(int) + ch.size() * sizeof(int2));
     staged(segs[which], sg, s);
     staged(prefix[which], pre, s);
     staged(ctl[which], c, s);
+    staged(chunks[which], ch, s);
     stage_end(s);
 }
 
@@ -1674,9 +1701,11 @@ vlbm_hier::DevPlan& dev_plan(vlbm_hier* h, int k, bool cyclic) {
         sg.lid_base = 0;
         D.seg.upload(h->mem, std::vector<Segment>{sg}, s);
         D.prefix.upload(h->mem, std::vector<int>{0, 0}, s);
+        D.chunks.upload(h->mem, std::vector<int2>{make_int2(0, 0)}, s);
         std::vector<int> c(CTL_WORDS, 0);
         c[CTL_EPOCH] = 1;
         c[CTL_NSEG] = 1;
+        c[CTL_NCHUNK] = 1;
         c[CTL_FLIP] = k & 1;
         D.ctl.upload(h->mem, c, s);
         D.steps = k;
@@ -1755,9 +1784,9 @@ vlbm_hier::DevPlan& dev_plan(vlbm_hier* h, int k, bool cyclic) {
 cudaGraphExec_t dev_task_graph(vlbm_hier* h, int which, int iters) {
     vlbm_hier::DevPlan& D = dev_plan(h, 1, true);
     cudaStream_t s = h->stream;
-    std::vector<uintptr_t> key = {(uintptr_t)h->atab.p,         (uintptr_t)D.seg.p,          (uintptr_t)D.prefix.p,
-                                  (uintptr_t)D.ctl.p,           (uintptr_t)h->tune.variant, (uintptr_t)h->tune.max_ctas,
-                                  (uintptr_t)iters};
+    std::vector<uintptr_t> key = {(uintptr_t)h->atab.p,   (uintptr_t)D.seg.p,          (uintptr_t)D.prefix.p,
+                                  (uintptr_t)D.chunks.p, (uintptr_t)D.ctl.p,          (uintptr_t)h->tune.variant,
+                                  (uintptr_t)h->tune.max_ctas, (uintptr_t)iters};
     cudaGraphExec_t& ex = D.exec[which];
     if (!ex || key != D.key[which]) {
         const auto t0 = std::chrono::steady_clock::now();
@@ -1767,7 +1796,8 @@ cudaGraphExec_t dev_task_graph(vlbm_hier* h, int which, int iters) {
         VCK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaMemsetAsync(D.ctl.p, 0, 2 * sizeof(int), s);  // claim and finish counters
         if (e == cudaSuccess)
-            e = launch_tasks(h->atab.p, D.seg.p, D.prefix.p, D.ctl.p, h->tune.variant, h->tune.max_ctas, iters, s);
+            e = launch_tasks(h->atab.p, D.seg.p, D.prefix.p, D.chunks.p, D.ctl.p, h->tune.variant, h->tune.max_ctas,
+                             iters, s);
         cudaError_t e2 = cudaStreamEndCapture(s, &g);
         if (e == cudaSuccess) e = e2;
         if (e == cudaSuccess) e = instantiate(&ex, g);
@@ -1867,6 +1897,7 @@ void release_dev_plans(vlbm_hier* h) {
         }
         for (DArr<int>* a : {&D.acc_beg, &D.acc_pos, &D.off, &D.deps, &D.need, &D.prefix, &D.ctl, &D.big})
             a->release(h->mem);
+        D.chunks.release(h->mem);
         D.ph.release(h->mem);
         D.acc.release(h->mem);
         D.tasks.release(h->mem);
@@ -1891,6 +1922,62 @@ void invalidate(vlbm_hier* h);
 
 }  // namespace
 
+// k coarse steps of every member in one persistent launch (the engine).
+void Batch::device_steps(long long k, cudaStream_t s) {
+    const int nm = (int)members.size();
+    if (nm == 0 || k <= 0) return;
+    if (k > 64) throw Fail{VLBM_ERR_ARG, "at most 64 steps per persistent launch"};
+    // every member's one-step list on its current layout, built on the
+    // device (on the member's auxiliary stream; this stream waits for it)
+    for (vlbm_hier* h : members) {
+        cudaStream_t own = h->stream;
+        h->stream = s;
+        h->mem.s = s;
+        try {
+            dev_plan(h, 1, true);
+        } catch (...) {
+            h->stream = own;
+            h->mem.s = own;
+            throw;
+        }
+        h->stream = own;
+        h->mem.s = own;
+    }
+    std::vector<Segment> sg(nm);
+    std::vector<const int*> offs(nm), mctl(nm);
+    int base = 0, nphase = 0;
+    for (int m = 0; m < nm; m++) {
+        vlbm_hier* h = members[m];
+        const vlbm_hier::DevPlan& D = h->dp[0];
+        Segment S{};
+        S.tasks = D.tasks.p;
+        S.deps = D.deps.p;
+        S.done = D.done.p;
+        S.par0 = h->words;
+        S.lid_base = base;
+        sg[m] = S;
+        offs[m] = D.off.p;
+        mctl[m] = D.ctl.p;
+        base += h->nlev;
+        nphase = D.nphase;  // one phase sequence for every hierarchy (all levels up to the maximum)
+    }
+    if (!dctl.p) {
+        std::vector<int> c(CTL_WORDS, 0);
+        c[CTL_EPOCH] = 1;
+        c[CTL_FLIP] = 1;  // one-step lists
+        dctl.upload(*mem, c, s);
+    }
+    dprefix.ensure(*mem, (size_t)nphase * nm + 1);
+    dchunks.ensure(*mem, (size_t)nphase * nm + 1);
+    stage_begin(sg.size() * sizeof(Segment) + 2 * offs.size() * sizeof(const int*));
+    staged(dsegs, sg, s);
+    staged(doffs, offs, s);
+    staged(dmctl, mctl, s);
+    stage_end(s);
+    VCK(launch_merge_chunks(doffs.p, dmctl.p, nm, nphase, dprefix.p, dchunks.p, dctl.p, s));
+    VCK(launch_tasks(levs.p, dsegs.p, dprefix.p, dchunks.p, dctl.p, variant, max_ctas, (int)k, s));
+}
+
 // ----------------------------------------------------------------------------
 // engine
 // ----------------------------------------------------------------------------
@@ -1900,14 +1987,14 @@ struct vlbm_engine {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     DevMem mem;
-    // every resident runs on shared per-phase launches: one launch per level
-    // phase covers the tiles of all residents, so no resident's dependency
-    // chain holds up the others (the persistent task kernel claims tasks
-    // resident by resident, and its thread groups wait at the phase
-    // boundaries of each small resident in turn: measured 4158 against
-    // 5611 MLUPS on the serving trace); no task lists are needed, so
-    // admissions and regrids only rebuild the launch tables
+    // schedule 0 (default): shared per-phase launches, one launch per level
+    // phase covering the tiles of all residents; schedule 1: one persistent
+    // launch per call over every resident's device-built one-step task list,
+    // merged phase-major (measured slower on the serving trace: 4912 against
+    // 5710 MLUPS capacity, its per-call list builds and short launches of
+    // many small residents cost more than the launch gaps they save)
     Batch batch;
+    int schedule = 0;
     struct Res {
         vlbm_hier* h = nullptr;
         long long target = 0, done = 0, lups = 0;
@@ -2938,7 +3025,14 @@ vlbm_status vlbm_engine_create(size_t mem_budget, const vlbm_allocator* alloc, v
     e->mem.s = e->stream;
     e->batch.mem = &e->mem;
     e->batch.schedule_mode = 0;
+    e->batch.variant = 1;  // three CTAs per SM (the single-hierarchy default)
     *out = e;
+    return VLBM_OK;
+}
+
+vlbm_status vlbm_engine_set_schedule(vlbm_engine* e, int32_t schedule) {
+    if (!e || (schedule != 0 && schedule != 1)) return VLBM_ERR_ARG;
+    e->schedule = schedule;
     return VLBM_OK;
 }
 
@@ -3010,6 +3104,11 @@ vlbm_status vlbm_engine_admit(vlbm_engine* e, vlbm_hier* h, int64_t coarse_steps
     h->engine = e;
     e->dirty = true;
     if (coarse_steps == 0) e->res[s].finishing = true;
+    // completion marks the hierarchy's own launches left could pass for the
+    // engine's epochs: they restart with the engine
+    if (h->dp[0].done.p &&
+        cudaMemsetAsync(h->dp[0].done.p, 0, h->dp[0].done.cap * sizeof(unsigned), e->stream) != cudaSuccess)
+        return VLBM_ERR_CUDA;
     if (slot) *slot = s;
     return VLBM_OK;
 }
@@ -3135,7 +3234,10 @@ vlbm_status vlbm_engine_advance(vlbm_engine* e, int32_t max_steps, int32_t* fini
         // instantiating a graph each time would cost more than the launches
         if (k > 0) {
             t0 = std::chrono::steady_clock::now();
-            for (long long i = 0; i < k; i++) e->batch.one_step(e->stream);
+            if (e->schedule == 1 && !e->batch.sensor)
+                e->batch.device_steps(k, e->stream);
+            else
+                for (long long i = 0; i < k; i++) e->batch.one_step(e->stream);
             e->times[VLBM_ET_LAUNCH] += ms_since(t0);
             t0 = std::chrono::steady_clock::now();
             int& c = e->lead_i;

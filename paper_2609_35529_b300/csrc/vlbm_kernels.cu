@@ -649,7 +649,7 @@ __device__ __forceinline__ void wait_done(const unsigned* p, unsigned mark, int*
     atomicOr(status, ST_TIMEOUT);
 }
 
-// The segment holding ticket t and the task's index in it.
+// The chunk holding ticket t: prefix[c] <= t < prefix[c + 1].
 __device__ __forceinline__ int find_segment(const int* __restrict__ prefix, int nseg, int t) {
     int lo = 0, hi = nseg - 1;
     while (lo < hi) {
@@ -692,13 +692,13 @@ __device__ __forceinline__ void wait_deps(const Segment& S, const Task& T, int i
 template <int P, int MINB>
 __global__ void __launch_bounds__(CTA_THREADS, MINB)
 task_kernel(const LevelDev* __restrict__ levs, const Segment* __restrict__ segs, const int* __restrict__ prefix,
-            int* ctl, int iters) {
+            const int2* __restrict__ chunks, int* ctl, int iters) {
     __shared__ int s_task[TILES_PER_CTA][2];
     const int g = threadIdx.x >> 6;
     const int lt = threadIdx.x & 63;
     const int cx = lt & 7, cy = lt >> 3;
     const unsigned epoch = (unsigned)ctl[CTL_EPOCH];
-    const int total = ctl[CTL_TOTAL], nseg = ctl[CTL_NSEG];
+    const int total = ctl[CTL_TOTAL], nseg = ctl[CTL_NSEG], nchunk = ctl[CTL_NCHUNK];
     const int tickets = total * iters;
     if (lt == 0) s_task[g][0] = atomicAdd(&ctl[CTL_CLAIM], 1);
     group_bar(g);
@@ -706,9 +706,10 @@ task_kernel(const LevelDev* __restrict__ levs, const Segment* __restrict__ segs,
         const int t = s_task[g][par];
         if (t >= tickets) break;
         const int it = t / total, tt = t - it * total;
-        const int sg = find_segment(prefix, nseg, tt);
-        const Segment S = segs[sg];
-        const int i = tt - prefix[sg];
+        const int ck = find_segment(prefix, nchunk, tt);
+        const int2 chunk = chunks[ck];
+        const Segment S = segs[chunk.x];
+        const int i = chunk.y + (tt - prefix[ck]);
         const Task T = S.tasks[i];
         const LevelDev& L = levs[T.lid + S.lid_base];
         const unsigned mark = 2u * (epoch + (unsigned)it);
@@ -757,10 +758,10 @@ task_kernel(const LevelDev* __restrict__ levs, const Segment* __restrict__ segs,
 template <int P, int MINB>
 __global__ void __launch_bounds__(CTA_THREADS, MINB)
 task_kernel_half(const LevelDev* __restrict__ levs, const Segment* __restrict__ segs,
-                 const int* __restrict__ prefix, int* ctl, int iters) {
+                 const int* __restrict__ prefix, const int2* __restrict__ chunks, int* ctl, int iters) {
     const int lane = threadIdx.x & 31;
     const unsigned epoch = (unsigned)ctl[CTL_EPOCH];
-    const int total = ctl[CTL_TOTAL], nseg = ctl[CTL_NSEG];
+    const int total = ctl[CTL_TOTAL], nseg = ctl[CTL_NSEG], nchunk = ctl[CTL_NCHUNK];
     const int tickets = 2 * total * iters;
     for (;;) {
         int h = 0;
@@ -769,9 +770,10 @@ task_kernel_half(const LevelDev* __restrict__ levs, const Segment* __restrict__ 
         if (h >= tickets) break;
         const int t = h >> 1, half = h & 1;
         const int it = t / total, tt = t - it * total;
-        const int sg = find_segment(prefix, nseg, tt);
-        const Segment S = segs[sg];
-        const int i = tt - prefix[sg];
+        const int ck = find_segment(prefix, nchunk, tt);
+        const int2 chunk = chunks[ck];
+        const Segment S = segs[chunk.x];
+        const int i = chunk.y + (tt - prefix[ck]);
         const Task T = S.tasks[i];
         const LevelDev& L = levs[T.lid + S.lid_base];
         const unsigned mark = 2u * (epoch + (unsigned)it);
@@ -1462,12 +1464,12 @@ int task_variant_per_sm() {
 }
 
 template <int P, int B>
-void task_variant_launch(int g, const LevelDev* levs, const Segment* segs, const int* prefix, int* ctl, int iters,
-                         cudaStream_t s) {
+void task_variant_launch(int g, const LevelDev* levs, const Segment* segs, const int* prefix, const int2* chunks,
+                         int* ctl, int iters, cudaStream_t s) {
     if constexpr ((P & TK_HALF) != 0)
-        task_kernel_half<P, B><<<g, CTA_THREADS, 0, s>>>(levs, segs, prefix, ctl, iters);
+        task_kernel_half<P, B><<<g, CTA_THREADS, 0, s>>>(levs, segs, prefix, chunks, ctl, iters);
     else
-        task_kernel<P, B><<<g, CTA_THREADS, 0, s>>>(levs, segs, prefix, ctl, iters);
+        task_kernel<P, B><<<g, CTA_THREADS, 0, s>>>(levs, segs, prefix, chunks, ctl, iters);
 }
 
 int task_kernel_ctas(int variant) {
@@ -1486,13 +1488,13 @@ int task_kernel_ctas(int variant) {
     return cache[variant];
 }
 
-cudaError_t launch_tasks(const LevelDev* levs, const Segment* segs, const int* prefix, int* ctl, int variant, int ctas,
-                         int iters, cudaStream_t s) {
+cudaError_t launch_tasks(const LevelDev* levs, const Segment* segs, const int* prefix, const int2* chunks, int* ctl,
+                         int variant, int ctas, int iters, cudaStream_t s) {
     if (iters < 1) return cudaErrorInvalidValue;
     const int full = task_kernel_ctas(variant);  // also sets the kernel's shared-memory attributes
     const int g = ctas > 0 ? std::min(ctas, full) : full;
     switch (variant) {
-#define X(id, P, B) case id: task_variant_launch<P, B>(g, levs, segs, prefix, ctl, iters, s); break;
+#define X(id, P, B) case id: task_variant_launch<P, B>(g, levs, segs, prefix, chunks, ctl, iters, s); break;
         VLBM_SWEEP_VARIANTS(X)
 #undef X
         default: return cudaErrorInvalidValue;

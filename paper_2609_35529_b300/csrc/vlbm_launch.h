@@ -16,9 +16,12 @@ cudaError_t launch_sensor(const LevelDev* levs, const Item* items, int n, int kk
 int sweep_variants();
 int task_kernel_ctas(int variant);
 // The persistent task kernel over the segments' task lists, `iters` times in
-// a row (one coarse step per iteration of a one-step list; 1 otherwise).
-cudaError_t launch_tasks(const LevelDev* levs, const Segment* segs, const int* prefix, int* ctl, int variant, int ctas,
-                         int iters, cudaStream_t s);
+// a row (one coarse step per iteration of one-step lists; 1 otherwise).
+// Within an iteration, ticket t lies in chunk c (prefix[c] <= t <
+// prefix[c + 1]) and is task chunks[c].y + t - prefix[c] of segment
+// chunks[c].x; every segment's tasks appear in its own list order.
+cudaError_t launch_tasks(const LevelDev* levs, const Segment* segs, const int* prefix, const int2* chunks, int* ctl,
+                         int variant, int ctas, int iters, cudaStream_t s);
 cudaError_t launch_audit_segments(const unsigned long long* slots, const int* seg, int nseg, double* out,
                                   cudaStream_t s);
 cudaError_t launch_close(const LevelDev* levs, const Item* items, int n, int kk, cudaStream_t s,

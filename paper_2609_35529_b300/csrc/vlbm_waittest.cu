@@ -17,7 +17,7 @@ using namespace vlbm;
 
 extern "C" vlbm_status vlbm_selftest_timeout(double* elapsed_ms, int32_t* status_word) {
     if (!elapsed_ms || !status_word) return VLBM_ERR_ARG;
-    // device block: [words: par0, status][flags 8x8][done 2][deps 1][prefix 2][ctl]
+    // device block: [words: par0, status][flags 8x8][done 2][deps 1][prefix 2][chunk][ctl]
     // followed by the task, the segment and the level table
     struct Blob {
         int words[2];
@@ -25,6 +25,7 @@ extern "C" vlbm_status vlbm_selftest_timeout(double* elapsed_ms, int32_t* status
         unsigned done[2];
         int deps[1];
         int prefix[2];
+        int2 chunk[1];
         int ctl[CTL_WORDS];
         Task task;
         Segment seg;
@@ -48,6 +49,8 @@ extern "C" vlbm_status vlbm_selftest_timeout(double* elapsed_ms, int32_t* status
         h.ctl[CTL_EPOCH] = 1;
         h.ctl[CTL_TOTAL] = 1;
         h.ctl[CTL_NSEG] = 1;
+        h.ctl[CTL_NCHUNK] = 1;
+        h.chunk[0] = make_int2(0, 0);
         h.task.lid = 0;
         h.task.kind = 1;  // reflux close: a no-op on a tile without level cells
         h.task.dep0 = 0;
@@ -68,7 +71,7 @@ extern "C" vlbm_status vlbm_selftest_timeout(double* elapsed_ms, int32_t* status
         h.lev.plane = TILE * TILE;
         h.lev.parent = h.lev.child = -1;
         if (ck(cudaMemcpyAsync(d, &h, sizeof h, cudaMemcpyHostToDevice, s)) && ck(cudaEventRecord(e0, s)) &&
-            ck(launch_tasks(&d->lev, &d->seg, d->prefix, d->ctl, 1, 1, 1, s)) && ck(cudaEventRecord(e1, s)) &&
+            ck(launch_tasks(&d->lev, &d->seg, d->prefix, d->chunk, d->ctl, 1, 1, 1, s)) && ck(cudaEventRecord(e1, s)) &&
             ck(cudaStreamSynchronize(s))) {
             int w[2] = {0, 0};
             float ms = 0.f;

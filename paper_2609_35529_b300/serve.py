@@ -2,7 +2,8 @@
 
 Requests (2-D Riemann quadrant problems or isentropic vortices of different
 sizes and refinement layouts) arrive by a seeded Poisson process.  The loop
-admits arrived requests while the engine's device-memory budget allows
+admits arrived requests, in arrival order, while the engine's device-memory
+budget and a cap on the residents' cell updates per coarse step allow
 (setting each one up on its own high-priority stream, overlapping the
 queued work), lets the engine advance every resident request by up to 16
 coarse steps per call (each step: one launch per level phase covering the
@@ -287,8 +288,10 @@ def run(argv=None):
                     help="also measure the one-at-a-time capacity (whole trace offered at t = 0)")
     ap.add_argument("--capacity-only", action="store_true",
                     help="stop after the capacity measurements (no latency runs)")
-    ap.add_argument("--work-cap", type=float, default=0.0,
+    ap.add_argument("--work-cap", type=float, default=24.0,
                     help="admission cap on the residents' cell updates per coarse step, in millions (0: none)")
+    ap.add_argument("--engine-schedule", type=int, default=0,
+                    help="0: shared per-phase launches; 1: one persistent launch per engine call (phase-major)")
     args = ap.parse_args(argv)
     import sys
     log = (lambda *a: print(*a, file=sys.stderr, flush=True)) if args.verbose else (lambda *a: None)
@@ -306,7 +309,8 @@ def run(argv=None):
     for r in reqs:
         r.arrival = 0.0
     wcap = args.work_cap * 1e6
-    _, cap_mlups, cap_wall = serve_batched(reqs, budget, stream=stream, setup_stream=setup, work_cap=wcap)
+    _, cap_mlups, cap_wall = serve_batched(reqs, budget, stream=stream, setup_stream=setup, work_cap=wcap,
+                                           schedule=args.engine_schedule)
     log(f"capacity: {cap_mlups:.1f} MLUPS, {cap_wall:.1f} s, {serve_batched.breakdown}")
     cap1 = None
     if args.capacity_one:
@@ -320,7 +324,8 @@ def run(argv=None):
     rate = args.load * len(reqs) / cap_wall
     schedule(reqs, rate, args.seed)
     sample = set(r.rid for r in sorted(reqs, key=lambda r: r.lups)[: args.keep_sample])
-    tts_b, ml_b, wall_b = serve_batched(reqs, budget, stream, sample, setup_stream=setup, verify=True, work_cap=wcap)
+    tts_b, ml_b, wall_b = serve_batched(reqs, budget, stream, sample, setup_stream=setup, verify=True, work_cap=wcap,
+                                        schedule=args.engine_schedule)
     breakdown = serve_batched.breakdown
     log(f"batched: {ml_b:.1f} MLUPS, {wall_b:.1f} s, {breakdown}")
     kept = {r.rid: r.result for r in reqs if r.rid in sample}
@@ -329,6 +334,7 @@ def run(argv=None):
     out = {"requests": len(reqs), "total_lups": total, "capacity_mlups": round(cap_mlups, 1),
            "capacity_one_at_a_time_mlups": round(cap1, 1) if cap1 else None,
            "rate_per_s": round(rate, 3), "load": args.load, "work_cap_mlup_per_step": args.work_cap,
+           "engine_schedule": args.engine_schedule,
            "batched": {"mlups": round(ml_b, 1), "p50_s": float(np.percentile(tts_b, 50)),
                        "p99_s": float(np.percentile(tts_b, 99)), "wall_s": wall_b, "breakdown": breakdown},
            "one_at_a_time": {"mlups": round(ml_1, 1), "p50_s": float(np.percentile(tts_1, 50)),
@@ -346,7 +352,8 @@ def run(argv=None):
 MAX_STEPS = 16
 
 
-def serve_batched(reqs, budget, stream=None, keep_ids=(), setup_stream=None, verify=False, work_cap=0):
+def serve_batched(reqs, budget, stream=None, keep_ids=(), setup_stream=None, verify=False, work_cap=0,
+                  schedule=0):
     """Continuous batching over the engine.  New requests are set up on their
     own stream (`setup_stream`) so that their set-up overlaps the engine's
     queued steps.  work_cap > 0 admits a request only while the residents'
@@ -355,7 +362,7 @@ def serve_batched(reqs, budget, stream=None, keep_ids=(), setup_stream=None, ver
     long requests); the others wait in arrival order.  Returns per-request
     time-to-solution (s), the aggregate MLUPS and the wall time; the final
     populations of the requests in keep_ids are kept in `result`."""
-    eng = V.Engine(budget, stream=stream)
+    eng = V.Engine(budget, stream=stream, schedule=schedule)
     pending = sorted(reqs, key=lambda r: r.arrival)
     for r in reqs:
         r.lups_done = 0

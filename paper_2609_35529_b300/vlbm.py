@@ -108,6 +108,7 @@ def lib():
         "vlbm_engine_create": [C.c_size_t, C.POINTER(vlbm_allocator), vp, C.POINTER(vp)],
         "vlbm_engine_admit": [vp, vp, i64, i32, C.POINTER(i32)],
         "vlbm_engine_step": [vp, C.POINTER(i32), C.POINTER(i32)],
+        "vlbm_engine_set_schedule": [vp, i32],
         "vlbm_engine_advance": [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)],
         "vlbm_engine_release": [vp, i32],
         "vlbm_engine_usage": [vp, C.POINTER(i32), C.POINTER(i64)],
@@ -466,11 +467,12 @@ def selftest_timeout():
 
 
 class Engine:
-    """Continuous-batching engine (vlbm_engine): every coarse step advances
-    all resident hierarchies -- static ones in one persistent-kernel launch,
-    adaptive ones in one graph of per-phase launches."""
+    """Continuous-batching engine (vlbm_engine): each call advances every
+    resident hierarchy by the same coarse steps, on per-phase launches shared
+    by all residents (schedule 0) or in one persistent launch over their
+    device-built task lists merged phase-major (schedule 1)."""
 
-    def __init__(self, mem_budget=0, stream=None, allocator=None):
+    def __init__(self, mem_budget=0, stream=None, allocator=None, schedule=0):
         """allocator="torch" routes the engine's own device memory (its launch
         tables) through torch's caching allocator."""
         e = C.c_void_p()
@@ -481,6 +483,13 @@ class Engine:
             raise VlbmError(st, "vlbm_engine_create")
         self._e = e
         self.cap = 0
+        self.set_schedule(schedule)
+
+    def set_schedule(self, schedule):
+        """0: per-phase launches; 1: one persistent launch per call (phase-major)."""
+        st = lib().vlbm_engine_set_schedule(self._e, int(schedule))
+        if st != 0:
+            raise VlbmError(st, "vlbm_engine_set_schedule")
 
     def admit(self, hier, steps, regrid_every=0):
         slot = C.c_int32()

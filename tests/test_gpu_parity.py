@@ -285,7 +285,8 @@ def test_adaptive_shockbubble_flux_jump_sensor(V):
     assert info["active_cells"][1] > 0 and info["active_cells"][2] > 0
 
 
-def test_engine_results_equal_alone_and_in_mix(V):
+@pytest.mark.parametrize("schedule", [1, 0])
+def test_engine_results_equal_alone_and_in_mix(V, schedule):
     cases = [I.pulse2l(steps=30), I.riemann3(N=64, nlev=3, steps=25),
              I.smooth_random(40, 32, 1, [], seed=5, amp=0.2, steps=35)]
     alone = []
@@ -294,7 +295,7 @@ def test_engine_results_equal_alone_and_in_mix(V):
         g.advance(cs.steps)
         alone.append([g.get_populations(l) for l in range(cs.nlev)])
         g.close()
-    e = V.Engine(allocator="torch")  # the engine's launch tables from torch's caching allocator
+    e = V.Engine(allocator="torch", schedule=schedule)  # the engine's tables from torch's caching allocator
     hs = [V.Hierarchy.from_case(cs) for cs in cases]
     slots = [e.admit(h, cs.steps) for h, cs in zip(hs, cases)]
     done = set()
@@ -311,12 +312,14 @@ def test_engine_results_equal_alone_and_in_mix(V):
     e.close()
 
 
-@pytest.mark.parametrize("max_steps", [1, 5, 16])
-def test_engine_static_and_adaptive_residents_equal_alone(V, max_steps):
+@pytest.mark.parametrize("max_steps,schedule", [(1, 1), (5, 1), (16, 1), (1, 0), (16, 0)])
+def test_engine_static_and_adaptive_residents_equal_alone(V, max_steps, schedule):
     """Continuous batching with static residents and adaptive residents
-    regridding every 4 of their own steps (all on shared per-phase launches)
-    admitted at different times: every result is bit-identical to the same
-    request advanced alone, whatever the number of steps per engine call."""
+    regridding every 4 of their own steps, admitted at different times, on
+    one persistent launch per call (the residents' device-built task lists
+    merged phase-major) or on shared per-phase launches: every result is
+    bit-identical to the same request advanced alone, whatever the number of
+    steps per engine call."""
     def adaptive_case(steps):
         return I.shockbubble(nx0=64, ny0=32, nlev=3, steps=steps)
 
@@ -342,7 +345,7 @@ def test_engine_static_and_adaptive_residents_equal_alone(V, max_steps):
                 g.regrid()
         alone.append([g.get_populations(l) for l in range(cs.nlev)])
         g.close()
-    e = V.Engine()
+    e = V.Engine(schedule=schedule)
     hs, slots = [None] * len(specs), [None] * len(specs)
     done, t = set(), 0
     while len(done) < len(specs):

@@ -40,7 +40,7 @@ class FakeH:
 
 
 class FakeEngine:
-    def __init__(self, budget, stream=None, refuse=0.3, seed=0):
+    def __init__(self, budget, stream=None, refuse=0.3, seed=0, schedule=0):
         self.rng = random.Random(seed)
         self.refuse = refuse
         self.res = {}
@@ -166,3 +166,34 @@ def test_result_digest_sees_every_bit():
     W4 = W.copy()
     W4[0, a0, b0], W4[1, a0, b0] = W[1, a0, b0], W[0, a0, b0]  # two fields of one cell
     assert digest(W4, act) != d0
+
+
+@pytest.mark.timeout(120)
+def test_batched_loop_respects_the_work_cap(fakes, monkeypatch):
+    """With an admission cap on the residents' cell updates per step, a
+    request is admitted only while the residents (itself included) stay
+    within the cap, or when nothing else is resident; every request still
+    finishes exactly once, in arrival order of admission."""
+    made, calls = fakes
+    reqs = S.make_requests(16, seed=6, nmax=256)
+    for r in reqs:
+        r.arrival = 0.0
+        r.steps = 4 + r.rid % 5
+    per = {r.rid: r.lups / max(1, r.steps) for r in reqs}
+    cap = 2.5 * max(per.values())
+    loads = []
+    real_admit = FakeEngine.admit
+
+    def admit(self, h, steps, every=0):
+        s = real_admit(self, h, steps, every)
+        if s is not None:
+            loads.append((len(self.res), sum(per[v[0].r.rid] for v in self.res.values())))
+        return s
+
+    monkeypatch.setattr(FakeEngine, "admit", admit)
+    tts, mlups, wall = S.serve_batched(reqs, budget=1 << 40, work_cap=cap)
+    assert all(r.done_at is not None for r in reqs)
+    assert len(loads) == len(reqs)
+    assert all(n == 1 or w <= cap for n, w in loads)
+    assert max(n for n, _ in loads) < len(reqs)  # the cap held some requests back
+    assert not [h for h in made if not h.closed]

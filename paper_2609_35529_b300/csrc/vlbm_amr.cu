@@ -170,6 +170,12 @@ struct Member {
     uint8_t recon;  // active with a face neighbour off the level
 };
 
+// Whether block b changes its on-level or covered state with the new maps.
+__device__ __forceinline__ bool block_changed(const LayoutDev& L, long long b) {
+    const bool in = L.bin[b] != 0, nin = L.nin[b] != 0;
+    return in != nin || (in && L.bcov[b] != 0) != (nin && L.ncov[b] != 0);
+}
+
 __device__ __forceinline__ Member member(const LayoutDev& L, long long b) {
     Member m{0, 0};
     const int ib = (int)(b % L.bx), jb = (int)(b / L.bx);
@@ -196,7 +202,19 @@ __device__ __forceinline__ Member member(const LayoutDev& L, long long b) {
         const bool ncov = L.nin[b] && L.ncov[b];
         if (cov && !ncov) m.bits |= 1u << LST_EXIT;
         if (ncov && !cov) m.bits |= 1u << LST_ENTER;
-        if (in || L.nin[b]) m.bits |= 1u << LST_TOUCH;
+        // a cell's flags depend on its own block and its face-neighbour
+        // blocks (the upwind cell of a face may lie in either): they change
+        // only where one of those changes its on-level or covered state
+        if (in || L.nin[b]) {
+            bool ch = block_changed(L, b);
+            const int di[4] = {1, -1, 0, 0}, dj[4] = {0, 0, 1, -1};
+            for (int d = 0; d < 4 && !ch; d++) {
+                bool ok = true;
+                const int i2 = wrap_or(ib + di[d], L.bx, L.px, ok), j2 = wrap_or(jb + dj[d], L.by, L.py, ok);
+                if (ok) ch = block_changed(L, (long long)j2 * L.bx + i2);
+            }
+            if (ch) m.bits |= 1u << LST_TOUCH;
+        }
     }
     return m;
 }

@@ -75,7 +75,9 @@ cudaError_t launch_nest_check(const LayoutDev* const* levs, int nl, int* status,
 // Lists of each level l selected by masks[l] (bits 1 << LST_*): act, ring,
 // cov, in from the current maps (with recon, act_idx, ring_idx, cells and
 // the write masks), exit and enter from the current against the new maps,
-// touch (on the level under either).  Items carry the level index.  Every
+// touch (on the level under either, with the block or a face neighbour
+// changing its on-level or covered state: the blocks whose cell flags can
+// change).  Items carry the level index.  Every
 // level in the same three or four launches.
 cudaError_t launch_lists(const LayoutDev* const* levs, const int* masks, int nl, cudaStream_t s);
 // Copies the new maps over the current ones, every level.

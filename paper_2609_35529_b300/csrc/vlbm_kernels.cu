@@ -922,6 +922,14 @@ __global__ void gather_W_kernel(LevelDev L, double* __restrict__ W, long long ld
 // thread holds two accumulators and many CTAs fit on an SM.  The last CTA to
 // finish writes the rounded totals out[0..7] (ticket: a zeroed counter,
 // left zeroed).
+// Flags of cell (cx, cy) of tile w (0 beyond the level's extent).
+__device__ __forceinline__ uint32_t audit_flags(const LevelDev* __restrict__ levs, const Item& w, int cx, int cy) {
+    const LevelDev& L = levs[w.lid];
+    const int x = w.tx * TILE + cx, y = w.ty * TILE + cy;
+    if (x >= L.nx || y >= L.ny) return 0;
+    return L.flags[(long long)y * L.pitch + x];
+}
+
 // The CTA that finishes last: out[m] = the correctly rounded sum of quantity
 // m over the partials of the launch's nb blocks, one quantity at a time.
 __device__ __noinline__ void audit_finish(const unsigned long long* part, int nb, double* out) {
@@ -958,17 +966,30 @@ __global__ void __launch_bounds__(256) audit_kernel(const LevelDev* __restrict__
     const int cx = threadIdx.x & 7;
     const int cy = (threadIdx.x >> 3) & 7;
     Fix192 sum = fix_zero(), abs_sum = fix_zero();
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const Item w = items[it];
-        const LevelDev& L = levs[w.lid];
-        const int x = w.tx * TILE + cx, y = w.ty * TILE + cy;
-        if (x >= L.nx || y >= L.ny) continue;
-        const long long c = (long long)y * L.pitch + x;
-        if ((L.flags[c] & (F_IN | F_COV)) != F_IN) continue;
-        const double* st = L.buf[state_buf(L)];
-        const double v = (st[qoff(0 + k, L.plane, c)] + st[qoff(4 + k, L.plane, c)]) +
-                         (st[qoff(8 + k, L.plane, c)] + st[qoff(12 + k, L.plane, c)]);
-        fix_accumulate(sum, abs_sum, v, -2 * L.level);
+    // the loads are pipelined: the next tile's list entry is in flight while
+    // this tile's populations load, and its flags while they are added up
+    const Item none{0, 0, 0};
+    int it = blockIdx.x;
+    Item w = it < nitems ? items[it] : none;
+    uint32_t fl = it < nitems ? audit_flags(levs, w, cx, cy) : 0u;
+    for (; it < nitems; it += gridDim.x) {
+        const int nx = it + gridDim.x;
+        const Item wn = nx < nitems ? items[nx] : none;
+        double v = 0.0;
+        int lev = 0;
+        const bool on = (fl & (F_IN | F_COV)) == F_IN;
+        if (on) {
+            const LevelDev& L = levs[w.lid];
+            const long long c = (long long)(w.ty * TILE + cy) * L.pitch + (w.tx * TILE + cx);
+            const double* st = L.buf[state_buf(L)];
+            v = (st[qoff(0 + k, L.plane, c)] + st[qoff(4 + k, L.plane, c)]) +
+                (st[qoff(8 + k, L.plane, c)] + st[qoff(12 + k, L.plane, c)]);
+            lev = L.level;
+        }
+        const uint32_t fn = nx < nitems ? audit_flags(levs, wn, cx, cy) : 0u;
+        if (on) fix_accumulate(sum, abs_sum, v, -2 * lev);
+        w = wn;
+        fl = fn;
     }
     __shared__ Fix192 sh[8][2];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;

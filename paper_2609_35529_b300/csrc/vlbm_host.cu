@@ -1340,11 +1340,13 @@ void tag_begin(vlbm_hier* h) {
     for (int l = 0; l <= h->nlev - 2; l++) {
         Level& L = h->lev[l];
         h->listbuf.upload(h->mem, L.in, s);
+        const BlockMaps M{L.dl.bin, L.dl.bcov};
         if (fluxs)
-            VCK(launch_tag_flux(lvdev(h, l), h->listbuf.p, (int)L.in.size(), h->qmax.p, h->cfg.tag_tol,
+            VCK(launch_tag_flux(lvdev(h, l), M, h->listbuf.p, (int)L.in.size(), h->qmax.p, h->cfg.tag_tol,
                                 h->cfg.tag_buffer, h->bflag.p + off, s));
         else
-            VCK(launch_tag(lvdev(h, l), h->listbuf.p, (int)L.in.size(), tol2, h->cfg.tag_buffer, h->bflag.p + off, s));
+            VCK(launch_tag(lvdev(h, l), M, h->listbuf.p, (int)L.in.size(), tol2, h->cfg.tag_buffer, h->bflag.p + off,
+                           s));
         off += (size_t)L.bx * L.by;
     }
     // status words first (8 bytes), then the flags
@@ -1435,11 +1437,12 @@ void device_tags(vlbm_hier* h) {
     for (int l = 0; l <= nl - 2; l++) {
         Level& L = h->lev[l];
         const LayoutDev& D = L.dl;
+        const BlockMaps M{D.bin, D.bcov};
         if (fluxs)
-            VCK(launch_tag_flux(lvdev(h, l), D.list[LST_IN], lcap(D), h->qmax.p, h->cfg.tag_tol, h->cfg.tag_buffer,
+            VCK(launch_tag_flux(lvdev(h, l), M, D.list[LST_IN], lcap(D), h->qmax.p, h->cfg.tag_tol, h->cfg.tag_buffer,
                                 h->bflag.p + off, s, D.cnt + LST_IN));
         else
-            VCK(launch_tag(lvdev(h, l), D.list[LST_IN], lcap(D), tol2, h->cfg.tag_buffer, h->bflag.p + off, s,
+            VCK(launch_tag(lvdev(h, l), M, D.list[LST_IN], lcap(D), tol2, h->cfg.tag_buffer, h->bflag.p + off, s,
                            D.cnt + LST_IN));
         off += (size_t)L.bx * L.by;
     }

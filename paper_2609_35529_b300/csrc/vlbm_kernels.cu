@@ -1099,11 +1099,18 @@ __device__ __forceinline__ void flag_blocks_near(int x, int y, int nx, int ny, i
 // The composite moments W_0 .. W_{NK-1} of the 10 x 10 window around tile
 // w (the tile and a one-cell ring; sides wrap where periodic) into Ws[k],
 // with on = 1 where the cell is on the level: thread lt of the tile's group
-// stages its own cell and, for lt < 36, one cell of the ring.
+// stages its own cell and, for lt < 36, one cell of the ring.  Whether a
+// cell is on the level, and covered (its composite value then sits in the
+// scratch buffer), is read from the block maps bin / bcov (one byte per
+// 8 x 8 block, cached) rather than from the cell flags, so the population
+// loads do not wait for a flag load.
 constexpr int WIN = TILE + 2;
 template <int NK>
-__device__ __forceinline__ void stage_window(const LevelDev& L, const Item& w, int lt, double (*Ws)[WIN * WIN],
-                                             uint8_t* on) {
+__device__ __forceinline__ void stage_window(const LevelDev& L, const uint8_t* __restrict__ bin,
+                                             const uint8_t* __restrict__ bcov, const Item& w, int lt,
+                                             double (*Ws)[WIN * WIN], uint8_t* on) {
+    const int bx = (L.nx + TILE - 1) / TILE;
+    const int sb = state_buf(L);
     for (int pass = 0; pass < 2; pass++) {
         int hx, hy;
         if (pass == 0) {
@@ -1125,11 +1132,11 @@ __device__ __forceinline__ void stage_window(const LevelDev& L, const Item& w, i
         ok = ok && x >= 0 && x < L.nx && y >= 0 && y < L.ny;  // cells past a narrow domain's side
         uint8_t in = 0;
         if (ok) {
-            const long long c = (long long)y * L.pitch + x;
-            const uint32_t fl = L.flags[c];
-            if (fl & F_IN) {
+            const long long b = (long long)(y / TILE) * bx + x / TILE;
+            if (bin[b]) {
                 in = 1;
-                const double* src = composite_src(L, fl);
+                const long long c = (long long)y * L.pitch + x;
+                const double* src = L.buf[bcov[b] ? sb ^ 1 : sb];
                 for (int k = 0; k < NK; k++)
                     Ws[k][hy * WIN + hx] = (src[qoff(0 + k, L.plane, c)] + src[qoff(4 + k, L.plane, c)]) +
                                            (src[qoff(8 + k, L.plane, c)] + src[qoff(12 + k, L.plane, c)]);
@@ -1144,8 +1151,8 @@ __device__ __forceinline__ void stage_window(const LevelDev& L, const Item& w, i
 // the level or beyond a non-periodic side take rho_C.  A tagged cell flags
 // the blocks within `buffer` cells of it in bflag (zeroed beforehand).
 __global__ void __launch_bounds__(CTA_THREADS, 6)
-tag_kernel(LevelDev L, const Item* __restrict__ items, int nitems, double tol2, int buffer,
-                           uint8_t* __restrict__ bflag, const int* __restrict__ ncount) {
+tag_kernel(LevelDev L, BlockMaps M, const Item* __restrict__ items, int nitems, double tol2, int buffer,
+           uint8_t* __restrict__ bflag, const int* __restrict__ ncount) {
     __shared__ double sW[TILES_PER_CTA][1][WIN * WIN];
     __shared__ uint8_t son[TILES_PER_CTA][WIN * WIN];
     if (ncount) nitems = *ncount;
@@ -1153,7 +1160,7 @@ tag_kernel(LevelDev L, const Item* __restrict__ items, int nitems, double tol2, 
     for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
         const Item w = items[it];
         group_bar(sub);  // the group's previous window is read
-        stage_window<1>(L, w, lt, sW[sub], son[sub]);
+        stage_window<1>(L, M.bin, M.bcov, w, lt, sW[sub], son[sub]);
         group_bar(sub);
         const int x = w.tx * TILE + cx, y = w.ty * TILE + cy;
         const int hc = (cy + 1) * WIN + cx + 1;
@@ -1215,9 +1222,9 @@ __global__ void qmax_kernel(LevelDev L, const Item* __restrict__ items, int nite
 // neighbours off the level or beyond a non-periodic side take the cell's
 // own flux).  A tagged cell flags the blocks within `buffer` cells of it.
 __global__ void __launch_bounds__(CTA_THREADS, 4)
-tag_flux_kernel(LevelDev L, const Item* __restrict__ items, int nitems,
-                                const unsigned long long* __restrict__ qmax, double tol, int buffer,
-                                uint8_t* __restrict__ bflag, const int* __restrict__ ncount) {
+tag_flux_kernel(LevelDev L, BlockMaps M, const Item* __restrict__ items, int nitems,
+                const unsigned long long* __restrict__ qmax, double tol, int buffer, uint8_t* __restrict__ bflag,
+                const int* __restrict__ ncount) {
     __shared__ double sW[TILES_PER_CTA][4][WIN * WIN];
     __shared__ uint8_t son[TILES_PER_CTA][WIN * WIN];
     if (ncount) nitems = *ncount;
@@ -1225,7 +1232,7 @@ tag_flux_kernel(LevelDev L, const Item* __restrict__ items, int nitems,
     for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
         const Item w = items[it];
         group_bar(sub);  // the group's previous window is read
-        stage_window<4>(L, w, lt, sW[sub], son[sub]);
+        stage_window<4>(L, M.bin, M.bcov, w, lt, sW[sub], son[sub]);
         group_bar(sub);
         const int x = w.tx * TILE + cx, y = w.ty * TILE + cy;
         const int hc = (cy + 1) * WIN + cx + 1;
@@ -1585,10 +1592,10 @@ cudaError_t launch_avgdown(const LevelDev& C, const LevelDev& F, const Item* ite
     return cudaGetLastError();
 }
 
-cudaError_t launch_tag(const LevelDev& L, const Item* items, int n, double tol2, int buffer, uint8_t* bflag,
-                       cudaStream_t s, const int* nc) {
+cudaError_t launch_tag(const LevelDev& L, const BlockMaps& M, const Item* items, int n, double tol2, int buffer,
+                       uint8_t* bflag, cudaStream_t s, const int* nc) {
     if (n <= 0) return cudaSuccess;
-    tag_kernel<<<list_grid(tag_kernel, n, nc), CTA_THREADS, 0, s>>>(L, items, n, tol2, buffer, bflag, nc);
+    tag_kernel<<<list_grid(tag_kernel, n, nc), CTA_THREADS, 0, s>>>(L, M, items, n, tol2, buffer, bflag, nc);
     return cudaGetLastError();
 }
 
@@ -1599,10 +1606,12 @@ cudaError_t launch_qmax(const LevelDev& L, const Item* items, int n, unsigned lo
     return cudaGetLastError();
 }
 
-cudaError_t launch_tag_flux(const LevelDev& L, const Item* items, int n, const unsigned long long* qmax, double tol,
-                            int buffer, uint8_t* bflag, cudaStream_t s, const int* nc) {
+cudaError_t launch_tag_flux(const LevelDev& L, const BlockMaps& M, const Item* items, int n,
+                            const unsigned long long* qmax, double tol, int buffer, uint8_t* bflag, cudaStream_t s,
+                            const int* nc) {
     if (n <= 0) return cudaSuccess;
-    tag_flux_kernel<<<list_grid(tag_flux_kernel, n, nc), CTA_THREADS, 0, s>>>(L, items, n, qmax, tol, buffer, bflag, nc);
+    tag_flux_kernel<<<list_grid(tag_flux_kernel, n, nc), CTA_THREADS, 0, s>>>(L, M, items, n, qmax, tol, buffer, bflag,
+                                                                            nc);
     return cudaGetLastError();
 }
 

@@ -38,14 +38,20 @@ cudaError_t launch_audit(const LevelDev* levs, const Item* items, int n, unsigne
                          unsigned* ticket, cudaStream_t s, const int* nc = nullptr);
 cudaError_t launch_avgdown(const LevelDev& C, const LevelDev& F, const Item* items, int n, cudaStream_t s,
                            const int* nc = nullptr);
+// A level's block maps (one byte per 8 x 8 block): on the level, covered.
+struct BlockMaps {
+    const uint8_t* bin;
+    const uint8_t* bcov;
+};
 // The tag kernels flag, in bflag (zeroed by the caller), every block within
 // `buffer` cells of a tagged cell of the listed tiles.
-cudaError_t launch_tag(const LevelDev& L, const Item* items, int n, double tol2, int buffer, uint8_t* bflag,
-                       cudaStream_t s, const int* nc = nullptr);
+cudaError_t launch_tag(const LevelDev& L, const BlockMaps& M, const Item* items, int n, double tol2, int buffer,
+                       uint8_t* bflag, cudaStream_t s, const int* nc = nullptr);
 cudaError_t launch_qmax(const LevelDev& L, const Item* items, int n, unsigned long long* qmax, cudaStream_t s,
                         const int* nc = nullptr);
-cudaError_t launch_tag_flux(const LevelDev& L, const Item* items, int n, const unsigned long long* qmax, double tol,
-                            int buffer, uint8_t* bflag, cudaStream_t s, const int* nc = nullptr);
+cudaError_t launch_tag_flux(const LevelDev& L, const BlockMaps& M, const Item* items, int n,
+                            const unsigned long long* qmax, double tol, int buffer, uint8_t* bflag, cudaStream_t s,
+                            const int* nc = nullptr);
 cudaError_t launch_merge(const LevelDev& L, const Item* items, int n, cudaStream_t s, const int* nc = nullptr);
 cudaError_t launch_split(const LevelDev& C, const LevelDev& F, const Item* items, int n, cudaStream_t s,
                          const int* nc = nullptr);

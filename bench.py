@@ -58,13 +58,14 @@ BYTES_PER_LUP = 256
 FP64_OPS_PER_LUP = 62
 # DRAM traffic of the persistent task kernel per cell update on this
 # workload type: dram__bytes_read.sum + dram__bytes_write.sum of one ncu
-# capture of a task-kernel launch (four coarse steps) of the 1024 x 512
-# coarse shock-bubble with three adaptive levels, divided by the launch's
-# cell updates; valid while the kernel source is the one captured
+# capture of a task-kernel launch (four coarse steps, three CTAs per SM) of
+# the 1024 x 512 coarse shock-bubble with three adaptive levels, divided by
+# the launch's cell updates (the launch shape changes occupancy, not the
+# bytes moved); valid while the kernel source is the one captured
 # (TASK_SOURCE_SHA of csrc/vlbm_kernels.cu), else the line reports traffic
 # as null.
 TASK_DRAM_BYTES_PER_LUP = 200.1
-TASK_SOURCE_SHA = "8c1c2b6f4c46bbb8"
+TASK_SOURCE_SHA = "47bcbef55942d56b"
 
 
 def kernel_source_sha():

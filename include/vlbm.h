@@ -305,11 +305,14 @@ vlbm_status vlbm_profile(vlbm_hier* h, int64_t coarse_steps, vlbm_kernel_time* o
  * bounded and report VLBM_ERR_TIMEOUT; the task lists are built on the
  * device after every layout change (on the host when per-step totals are
  * on); schedule 2 (auto) uses schedule 0 until the current layout has lived
- * persist_after coarse steps and schedule 1 from then on (a task-list build
- * costs about what a few coarse steps of schedule 0 lose to schedule 1, so
- * an adaptive run that regrids every few steps keeps schedule 0), and
- * schedule 1 whenever per-step totals are on.  max_ctas caps the grid (0 =
- * one CTA per four tiles for schedule 0, all resident CTAs for schedule 1);
+ * persist_after coarse steps (default 2) and schedule 1 from then on, and
+ * schedule 1 whenever per-step totals are on (a device task-list build costs
+ * less than a coarse step of schedule 0 loses to schedule 1 on multi-level
+ * layouts, so only layouts that change every step or two keep schedule 0).
+ * The default tuning is variant 1, schedule 1, graph_steps 8.  max_ctas
+ * caps the grid (0 = no cap: schedule 0 takes one CTA per four tiles, or one
+ * wave of resident CTAs looping over a list whose length lives on the
+ * device; schedule 1 all resident CTAs);
  * graph_steps (1..64) is the number of coarse steps captured per CUDA graph.
  * vlbm_set_tuning returns ERR_ARG for an unknown variant or out-of-range
  * values (the tuning is then unchanged).  Results do not depend on the

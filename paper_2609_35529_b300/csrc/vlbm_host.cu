@@ -343,7 +343,7 @@ struct vlbm_hier {
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_layout = nullptr, ev_built = nullptr;
     long long ev_layout_version = -1;
-    vlbm_tuning tune{1, 0, 8, 1, 256};
+    vlbm_tuning tune{1, 0, 8, 1, 2};
     long long layout_steps = 0;  // coarse steps taken on the current layout
     // The layout lives on the device (Level::dl, always current); the host
     // copies (Level::bin, bcov and the tile lists) are current while host_ok.
@@ -2158,10 +2158,10 @@ int effective_schedule(const vlbm_hier* h) {
 
 // Schedule of the steps on the device lists.  Auto (2) keeps the per-phase
 // launches on a layout younger than persist_after coarse steps, as on the
-// host lists: building a layout's task lists on the device costs about as
-// much GPU time as a few coarse steps of the per-phase schedule lose to the
-// persistent one (measured on the 2048 x 1024 shock-bubble regridding every
-// 4 steps: 5030 MLUPS per phase, 4550 persistent with a build per regrid).
+// host lists.  A device build of a layout's one-step task list costs about
+// 0.1 ms on the 2048 x 1024 shock-bubble, less than the persistent kernel
+// saves in one coarse step (regridding every 4 steps: 5650 MLUPS
+// persistent, 5104 per phase), hence the default of 2.
 int dev_schedule_mode(const vlbm_hier* h) {
     if (h->sensor_on) return 0;
     if (h->tune.schedule != 2) return h->tune.schedule;

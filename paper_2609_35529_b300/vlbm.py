@@ -401,7 +401,7 @@ class Hierarchy:
                                                    C.byref(n)))
         return out[: n.value]
 
-    def set_tuning(self, variant=1, max_ctas=0, graph_steps=8, schedule=1, persist_after=256):
+    def set_tuning(self, variant=1, max_ctas=0, graph_steps=8, schedule=1, persist_after=2):
         """schedule: 0 per-phase launches, 1 persistent task kernel, 2 auto
         (per-phase until the layout has lived persist_after coarse steps)."""
         t = vlbm_tuning(variant, max_ctas, graph_steps, schedule, persist_after)

@@ -277,7 +277,7 @@ __device__ __forceinline__ void sweep_boundary(const LevelDev& L, int x, int y, 
 // Reconstructed coarse-to-fine values for the incoming populations of a
 // cell whose upwind neighbour lies in coarser territory.
 template <bool COH>
-__device__ __noinline__ void sweep_recon(const LevelDev* __restrict__ levs, const LevelDev& L, int x, int y,
+__device__ __forceinline__ void sweep_recon(const LevelDev* __restrict__ levs, const LevelDev& L, int x, int y,
                                         long long c, uint32_t fl, double* dst, int kk, int kkp, int step) {
     // coarse-to-fine reconstruction (Sec. 3.3, Eqs. 22-23)
     const uint32_t rec = (fl & F_RECON_MASK) >> F_RECON_SHIFT;

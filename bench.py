@@ -64,8 +64,8 @@ FP64_OPS_PER_LUP = 62
 # bytes moved); valid while the kernel source is the one captured
 # (TASK_SOURCE_SHA of csrc/vlbm_kernels.cu), else the line reports traffic
 # as null.
-TASK_DRAM_BYTES_PER_LUP = 200.1
-TASK_SOURCE_SHA = "47bcbef55942d56b"
+TASK_DRAM_BYTES_PER_LUP = 190.1
+TASK_SOURCE_SHA = "644dc3f5a7083fbb"
 
 
 def kernel_source_sha():

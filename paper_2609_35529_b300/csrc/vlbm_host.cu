@@ -3183,7 +3183,13 @@ vlbm_status vlbm_engine_advance(vlbm_engine* e, int32_t max_steps, int32_t* fini
             VCK(q);
             int st[2];
             VCK(cudaMemcpy(st, r.h->words, sizeof st, cudaMemcpyDeviceToHost));
-            if (st[1]) r.h->poisoned = true, r.h->err = "non-physical state";
+            if (st[1]) {
+                r.h->poisoned = true;
+                r.h->err = (st[1] & ST_NONPHYS)  ? "non-physical state"
+                           : (st[1] & ST_TIMEOUT) ? "a bounded device wait timed out"
+                           : (st[1] & ST_TASKCAP) ? "task list or footprint capacity exceeded"
+                                                  : "device status " + std::to_string(st[1]);
+            }
             r.finishing = false;
             r.reported = true;
             if (finished) finished[nf] = (int)i;
@@ -3237,7 +3243,11 @@ vlbm_status vlbm_engine_advance(vlbm_engine* e, int32_t max_steps, int32_t* fini
         // instantiating a graph each time would cost more than the launches
         if (k > 0) {
             t0 = std::chrono::steady_clock::now();
-            if (e->schedule == 1 && !e->batch.sensor)
+            // the persistent launch takes at most 64 steps, and its tickets
+            // (tasks of one step of every resident x steps) must fit an int
+            long long cap = 0;
+            for (vlbm_hier* h : e->batch.members) cap += h->dp[0].task_cap > 0 ? h->dp[0].task_cap : 1LL << 20;
+            if (e->schedule == 1 && !e->batch.sensor && k <= 64 && cap * k < (1LL << 31) - 1)
                 e->batch.device_steps(k, e->stream);
             else
                 for (long long i = 0; i < k; i++) e->batch.one_step(e->stream);

@@ -239,11 +239,17 @@ vlbm_status vlbm_lups_mark(vlbm_hier* h, int64_t* dst);
  * nothing).  on = 1: every tag-driven regrid that runs on the device
  * records, on the device and without synchronising, the exact totals of
  * vlbm_audit immediately before and immediately after it, into a ring of
- * the last 4096 regrids.  vlbm_get_regrid_audits copies the rows recorded
- * since the previous read (at most cap, oldest first) into out[n][16]:
- * totals before (4), |W| totals before (4), totals after (4), |W| totals
- * after (4); it synchronises.  Errors: ERR_ARG, ERR_OOM, ERR_CUDA,
- * ERR_STATE (and deferred errors on the read). */
+ * the last 4096 regrids.  The totals after a regrid are those of the state
+ * the regrid leaves: when the next steps run on the persistent schedule
+ * they come from that launch's first sweeps (which form every active
+ * cell's moments anyway) and a reduction in the same launch; otherwise, or
+ * when another call changes the state or reads the rows first, from a
+ * separate audit queued then -- the same values either way.
+ * vlbm_get_regrid_audits copies the rows recorded since the previous read
+ * (at most cap, oldest first) into out[n][16]: totals before (4), |W|
+ * totals before (4), totals after (4), |W| totals after (4); it
+ * synchronises.  Errors: ERR_ARG, ERR_OOM, ERR_CUDA, ERR_STATE (and
+ * deferred errors on the read). */
 vlbm_status vlbm_set_regrid_audit(vlbm_hier* h, int32_t on);
 vlbm_status vlbm_get_regrid_audits(vlbm_hier* h, double* out, int64_t cap, int64_t* n);
 

@@ -683,15 +683,30 @@ struct TB {
     }
 };
 
+// Audit slot of task i of phase ph (-1: not an audited sweep): the slots of
+// level l follow those of levels 0 .. l - 1.
+__device__ __forceinline__ int tb_slot_base(const TBPlan& P, int l) {
+    int b = 0;
+    for (int q = 0; q < l; q++) b += P.lev[q].cnt[LST_ACT];
+    return b;
+}
+
+__device__ __forceinline__ int tb_aslot(const TBPlan& P, const TBPhase& ph, int i) {
+    return (P.audit && ph.kind == 0 && ph.first && ph.l < P.nlev) ? tb_slot_base(P, ph.l) + i : -1;
+}
+
 __global__ void tb_offsets_kernel(TBPlan P) {
     if (threadIdx.x || blockIdx.x) return;
+    const int slots = P.audit ? tb_slot_base(P, P.nlev) : 0;
+    const int nblk = (slots + TB_AUDIT_BLOCK - 1) / TB_AUDIT_BLOCK;
     int o = 0;
     for (int p = 0; p < P.nphase; p++) {
         P.off[p] = o;
         const TBPhase ph = P.ph[p];
         int c = 0;
         if (ph.kind == 0) c = ph.l < P.nlev ? P.lev[ph.l].cnt[LST_ACT] : 0;
-        else c = ph.l + 1 < P.nlev ? P.lev[ph.l].cnt[LST_RING] : 0;
+        else if (ph.kind == 1) c = ph.l + 1 < P.nlev ? P.lev[ph.l].cnt[LST_RING] : 0;
+        else c = 4 * nblk;
         o += c;
     }
     P.off[P.nphase] = o;
@@ -700,6 +715,40 @@ __global__ void tb_offsets_kernel(TBPlan P) {
     P.need[2] = 0;
     P.need[3] = 0;
     P.need[4] = 0;
+    P.need[5] = slots;
+    P.need[6] = nblk;
+}
+
+// Reduction task t (phase p, kind 2) by one warp: block b = i / 4, field
+// k = i % 4; its dependencies are the sweeps owning the block's slots
+// (ascending: levels in phase order, each in list order); the field-0 task
+// also writes the block's slot range and its slots' weights.
+__device__ void tb_audit_task(const TBPlan& P, const int* off, int p, int t, int lane) {
+    const int i = t - off[p];
+    const int b = i >> 2, k = i & 3;
+    const int j0 = b * TB_AUDIT_BLOCK, j1 = min(j0 + TB_AUDIT_BLOCK, P.need[5]);
+    const int j = j0 + lane;
+    if (j < j1) {
+        int l = 0, base = 0;
+        while (l + 1 < P.nlev && j >= base + P.lev[l].cnt[LST_ACT]) base += P.lev[l++].cnt[LST_ACT];
+        P.deps[(long long)t * TB_SMALL + lane] = off[P.pfirst[l]] + (j - base);
+        if (k == 0) P.ascale[j] = -2 * l;
+    }
+    if (lane == 0) {
+        if (k == 0) P.arng[b] = make_int2(j0, j1);
+        Task T;
+        T.lid = 0;
+        T.tx = 0;
+        T.ty = 0;
+        T.kind = 2;
+        T.kk = (signed char)k;
+        T.kkp = 0;
+        T.step = 0;
+        T.dep0 = t * TB_SMALL;
+        T.ndep = j1 - j0;
+        T.aslot = b;
+        P.tasks[t] = T;
+    }
 }
 
 // Copies the plan's static tables into shared memory; returns the view.
@@ -731,7 +780,7 @@ __device__ __forceinline__ void tb_write(const TBPlan& P, const TB& tb, int p, i
     T.step = (signed char)ph.step;
     T.dep0 = (int)d0;
     T.ndep = S.n;
-    T.aslot = -1;
+    T.aslot = tb_aslot(P, ph, t - tb.off[p]);
     P.tasks[t] = T;
 }
 
@@ -793,8 +842,9 @@ __global__ void __launch_bounds__(TBW_WARPS * 32) tb_warp_kernel(TBPlan P) {
             __syncwarp();  // the previous pair's buffers are read
             if (hl == 0) nraw[w][half] = 0;
             __syncwarp();
-            if (t < total) {
-                const int p = tb.phase_of(t);
+            const int pw = t < total ? tb.phase_of(t) : 0;
+            if (t < total && tb.ph[pw].kind != 2) {
+                const int p = pw;
                 const TBPhase ph = tb.ph[p];
                 const TBLevel& L = P.lev[ph.l];
                 const int i = t - tb.off[p];
@@ -820,6 +870,11 @@ __global__ void __launch_bounds__(TBW_WARPS * 32) tb_warp_kernel(TBPlan P) {
         for (int u = 0; u < 2; u++) {
             const int t = tp + u;
             if (t >= total) break;
+            const int pt = tb.phase_of(t);
+            if (tb.ph[pt].kind == 2) {
+                tb_audit_task(P, tb.off, pt, t, lane);
+                continue;
+            }
             const int* R = raw[w][u];
             const int n = nraw[w][u];
             if (n > TBW_RAW) {
@@ -883,7 +938,7 @@ __global__ void __launch_bounds__(TBW_WARPS * 32) tb_warp_kernel(TBPlan P) {
                     }
                 }
                 if (lane == 0) {
-                    const int p = tb.phase_of(t);
+                    const int p = pt;
                     const TBPhase ph = tb.ph[p];
                     const TBLevel& L = P.lev[ph.l];
                     const int i = t - tb.off[p];
@@ -898,7 +953,7 @@ __global__ void __launch_bounds__(TBW_WARPS * 32) tb_warp_kernel(TBPlan P) {
                     T.step = (signed char)ph.step;
                     T.dep0 = (int)at;
                     T.ndep = nu;
-                    T.aslot = -1;
+                    T.aslot = tb_aslot(P, ph, i);
                     P.tasks[t] = T;
                 }
             }

@@ -98,6 +98,9 @@ cudaError_t launch_count_lups(const LayoutDev* levs, int n, long long steps, uns
 // of a resource (the same patterns as vlbm_tasks.h)
 enum : int { TB_OWN = 0, TB_STENCIL = 1, TB_FOOT = 2, TB_CHILD4 = 3, TB_OWNRING = 4 };
 
+// kind 0: sweeps of level l (sub-step kk of the parent's sub-step kkp; first:
+// the level's first sweep of the step), 1: closes of level l, 2: the audit
+// phase of a cyclic list (reduction tasks, see TBPlan::audit)
 struct TBPhase {
     int kind, l, kk, kkp, step, first;
 };
@@ -120,6 +123,9 @@ constexpr int TASK_RC = 4 * 3;  // resource classes: (level, buffer 0 / buffer 1
 // dependencies of task t at deps[t * TASK_DEP_SLOT ..] when they fit, else
 // in the overflow area after task_cap * TASK_DEP_SLOT entries
 constexpr int TASK_DEP_SLOT = 32;
+// audit slots per reduction block of a device-built list (its reduction
+// tasks' dependencies fit their fixed slots)
+constexpr int TB_AUDIT_BLOCK = 32;
 
 // Static tables of a phase sequence (depend on the level count and the steps
 // per launch only) and the buffers of one task list.
@@ -141,8 +147,19 @@ struct TBPlan {
     unsigned* done = nullptr;          // completion marks (left as they are)
     int task_cap = 0;
     long long dep_cap = 0;
-    int* need = nullptr;               // [5]: tasks of the last build, overflow area used, tasks of the
-                                       // fallback pass, overflow flag, tasks in the overflow area
+    int* need = nullptr;               // [7]: tasks of the last build, overflow area used, tasks of the
+                                       // fallback pass, overflow flag, tasks in the overflow area, audit
+                                       // slots, audit blocks
+    // Audited cyclic list: the first sweep of each level in the step gives
+    // each of its tiles an audit slot (levels in order, each in act-list
+    // order), and the audit phase holds four reduction tasks (one per field)
+    // per block of TB_AUDIT_BLOCK consecutive slots, each depending on the
+    // sweeps of its block's slots.  The kernel does this work only in the
+    // first iteration of a launch whose CTL_AUDIT word is set.
+    int audit = 0;
+    int pfirst[4] = {-1, -1, -1, -1};  // the first-sweep phase of each level
+    int* ascale = nullptr;             // [slots] weight exponent of the slot's level (-2 l)
+    int2* arng = nullptr;              // [blocks] slot range of each block
     int* big = nullptr;                // [task_cap] tasks of the fallback pass
     int* status = nullptr;             // hierarchy status word (ST_TASKCAP on overflow)
     Segment* seg = nullptr;            // the single-member segment of the launch

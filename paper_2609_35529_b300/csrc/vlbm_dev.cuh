@@ -141,6 +141,10 @@ enum : int {
     CTL_NSEG = 4,
     CTL_FLIP = 5,
     CTL_NCHUNK = 6,
+    // nonzero: the launch's first iteration is audited (its first sweep of
+    // each level keeps the moments, its reduction tasks add them up); zero:
+    // audited sweeps and reduction tasks do nothing
+    CTL_AUDIT = 7,
     CTL_WORDS = 8
 };
 

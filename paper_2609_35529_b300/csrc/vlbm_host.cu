@@ -339,8 +339,10 @@ struct vlbm_hier {
     cudaEvent_t rg_ev = nullptr;
     // task-list builds run on aux, after ev_layout (recorded when a device
     // regrid's layout is complete, for layout ev_layout_version); the main
-    // stream waits for ev_built before the persistent launch
-    cudaStream_t aux = nullptr;
+    // stream waits for ev_built before the persistent launch.  The audit
+    // before a device regrid runs on aux2, beside the regrid's first part
+    // and the build.
+    cudaStream_t aux = nullptr, aux2 = nullptr;
     cudaEvent_t ev_layout = nullptr, ev_built = nullptr;
     long long ev_layout_version = -1;
     vlbm_tuning tune{1, 0, 8, 1, 2};
@@ -363,6 +365,10 @@ struct vlbm_hier {
     bool regrid_audit = false;
     double* raud = nullptr;
     long long ra_n = 0, ra_read = 0;
+    // ring row whose totals after the regrid are still to come (-1: none):
+    // from the first step of the next persistent launch, or from a separate
+    // audit before anything else changes the state
+    long long after_pending = -1;
     static constexpr long long RA_CAP = 4096;
     // the device regrid, captured in two parts: [0] indicator to new maps
     // and move lists (reads the populations), [1] merge / split, flags and
@@ -386,6 +392,14 @@ struct vlbm_hier {
         int task_cap = 0;
         long long dep_cap = 0;
         int build_kernels = 0;  // kernels the last dev_plan call queued (a task list build)
+        // audited cyclic list (regrid audits on): the totals after a regrid
+        // come from the next launch's first sweeps (see TBPlan::audit)
+        bool audit = false;
+        int pfirst[4] = {-1, -1, -1, -1};
+        DArr<double> aw;
+        DArr<int> ascale;
+        DArr<int2> arng;
+        DArr<unsigned long long> apart;
         // graphs of its persistent launch: [0] one iteration, [1] G iterations
         cudaGraphExec_t exec[2] = {nullptr, nullptr};
         std::vector<uintptr_t> key[2];
@@ -966,6 +980,7 @@ void Batch::build_segments(int which, int nsteps, cudaStream_t s) {
     c[CTL_NSEG] = (int)members.size();
     c[CTL_FLIP] = nsteps & 1;
     c[CTL_NCHUNK] = (int)sg.size();  // one chunk per segment: member by member
+    c[CTL_AUDIT] = 1;                // a segment with audit slots audits every launch (one-pass lists)
     std::vector<int2> ch(sg.size());
     for (size_t m = 0; m < sg.size(); m++) ch[m] = make_int2((int)m, 0);
     // pinned staging: the engine's queued steps keep running meanwhile
@@ -1518,6 +1533,18 @@ void device_apply_flags(vlbm_hier* h, const uint8_t* bflag, int part = -1) {
 // A tag-driven regrid on the device: indicator, block flags, new layout,
 // merge / split, flags and lists, replayed as one captured graph (every
 // size involved is decided on the device, so the graph stays valid).
+// The totals after the last regrid, when still to come, by a separate
+// audit of the current state (nothing has changed it since the regrid).
+void settle_after_audit(vlbm_hier* h) {
+    if (h->after_pending < 0) return;
+    const long long slot = h->after_pending;
+    h->after_pending = -1;
+    const int icap = (int)std::min<size_t>(h->ditems_cap, 1u << 30);
+    VCK(launch_audit(h->atab.p, h->ditems, icap, h->partial.p, h->raud + 16 * slot + 8, h->aticket.p, h->stream,
+                     h->dcount));
+    h->klaunch += 1;
+}
+
 void device_regrid(vlbm_hier* h) {
     check_tagging(h);
     regrid_buffers(h);
@@ -1556,18 +1583,21 @@ void device_regrid(vlbm_hier* h) {
     for (cudaEvent_t* ev : {&h->ev_layout, &h->ev_rg0, &h->ev_audit})
         if (!*ev) VCK(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
     if (!h->aux) VCK(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
+    if (!h->aux2) VCK(cudaStreamCreateWithFlags(&h->aux2, cudaStreamNonBlocking));
+    settle_after_audit(h);  // the previous regrid's totals after, if still to come
     const long long slot = h->ra_n % vlbm_hier::RA_CAP;
     const int icap = (int)std::min<size_t>(h->ditems_cap, 1u << 30);
     if (h->regrid_audit) {
         // the audit before the regrid reads the active cells' state, which
         // the first part (indicator, maps, move lists) leaves alone: it runs
-        // beside it on the auxiliary stream, and the second part (merge,
-        // split: writes) waits for it
+        // on a stream of its own beside that part and the task-list build
+        // that follows it, and the second part (merge, split: writes) waits
+        // for it
         VCK(cudaEventRecord(h->ev_rg0, s));
-        VCK(cudaStreamWaitEvent(h->aux, h->ev_rg0, 0));
-        VCK(launch_audit(h->atab.p, h->ditems, icap, h->partial.p, h->raud + 16 * slot, h->aticket.p, h->aux,
+        VCK(cudaStreamWaitEvent(h->aux2, h->ev_rg0, 0));
+        VCK(launch_audit(h->atab.p, h->ditems, icap, h->partial.p, h->raud + 16 * slot, h->aticket.p, h->aux2,
                          h->dcount));
-        VCK(cudaEventRecord(h->ev_audit, h->aux));
+        VCK(cudaEventRecord(h->ev_audit, h->aux2));
     }
     VCK(cudaGraphLaunch(h->rg_exec[0], s));
     VCK(cudaEventRecord(h->ev_layout, s));  // the new layout's maps and lists are complete here
@@ -1575,10 +1605,12 @@ void device_regrid(vlbm_hier* h) {
     VCK(cudaGraphLaunch(h->rg_exec[1], s));
     h->klaunch += graph_kernels(h->rg_exec[0]) + graph_kernels(h->rg_exec[1]);
     if (h->regrid_audit) {
-        VCK(launch_audit(h->atab.p, h->ditems, icap, h->partial.p, h->raud + 16 * slot + 8, h->aticket.p, s,
-                         h->dcount));
+        // the totals after the regrid come later: from the first sweeps of
+        // the next persistent launch, which read every active cell's state
+        // anyway, or from a separate audit before anything else changes it
         h->ra_n++;
-        h->klaunch += 2;  // two audits
+        h->klaunch += 1;
+        h->after_pending = slot;
     }
     h->host_ok = false;
     layout_changed(h);
@@ -1588,10 +1620,11 @@ void device_regrid(vlbm_hier* h) {
 // ---- the sub-cycle over the device lists ---------------------------------------
 
 // Static tables of the phase sequence of `nsteps` coarse steps (the same
-// recursion as phases() in vlbm_tasks.h) and the accesses of its phases per
-// resource class (level, buffer 0 / 1 / flags), in phase order.
-void plan_tables(int nlev, int nsteps, std::vector<TBPhase>& ph, std::vector<TBAcc>& acc, std::vector<int>& beg,
-                 std::vector<int>& pos) {
+// recursion as phases() in vlbm_tasks.h, then the audit phase of a cyclic
+// list) and the accesses of its phases per resource class (level, buffer
+// 0 / 1 / flags), in phase order.
+void plan_tables(int nlev, int nsteps, bool audit_phase, std::vector<TBPhase>& ph, std::vector<TBAcc>& acc,
+                 std::vector<int>& beg, std::vector<int>& pos) {
     ph.clear();
     struct Rec {
         static void run(std::vector<TBPhase>& ph, int l, int kk, int kkp, int step, bool first) {
@@ -1604,11 +1637,15 @@ void plan_tables(int nlev, int nsteps, std::vector<TBPhase>& ph, std::vector<TBA
         }
     };
     for (int st = 0; st < nsteps; st++) Rec::run(ph, 0, 0, 0, st, true);
+    // the audit phase (reductions of the first sweeps' moments) touches no
+    // buffer: it orders nothing but its own tasks after their sweeps
+    if (audit_phase) ph.push_back(TBPhase{2, 0, 0, 0, 0, 0});
     auto src_of = [](int level, int kk, int step) { return level == 0 ? (step & 1) : (kk == 1 ? 0 : 1); };
     std::vector<TBAcc> per[TASK_MAX_LEVELS][3];
     for (int p = 0; p < (int)ph.size(); p++) {
         const TBPhase& P = ph[p];
         const int l = P.l;
+        if (P.kind == 2) continue;
         if (P.kind == 0) {
             if (l >= nlev) continue;
             const int bs = src_of(l, P.kk, P.step);
@@ -1653,20 +1690,41 @@ void plan_tables(int nlev, int nsteps, std::vector<TBPhase>& ph, std::vector<TBA
 vlbm_hier::DevPlan& dev_plan(vlbm_hier* h, int k, bool cyclic) {
     vlbm_hier::DevPlan& D = h->dp[cyclic ? 0 : 1];
     if (cyclic) k = 1;
+    // regrid audits of a hierarchy on its own: the totals after each regrid
+    // come from the next launch (the engine audits separately)
+    const bool audit = cyclic && h->regrid_audit && !h->engine;
     D.build_kernels = 0;
     cudaStream_t s = h->stream;
     bool plan_fresh_ok = true;  // no upload queued on the main stream since the layout event
-    if (D.steps != k) {
+    if (D.steps != k || D.audit != audit) {
         plan_fresh_ok = false;
         std::vector<TBPhase> ph;
         std::vector<TBAcc> acc;
         std::vector<int> beg, pos;
-        plan_tables(h->nlev, k, ph, acc, beg, pos);
-        long long cap = 0;
-        for (const TBPhase& P : ph) {
+        plan_tables(h->nlev, k, cyclic, ph, acc, beg, pos);
+        long long cap = 0, slot_cap = 0;
+        for (int l = 0; l < h->nlev; l++) slot_cap += (long long)h->lev[l].bx * h->lev[l].by;
+        const long long blk_cap = (slot_cap + TB_AUDIT_BLOCK - 1) / TB_AUDIT_BLOCK;
+        for (int l = 0; l < 4; l++) D.pfirst[l] = -1;
+        for (int p = 0; p < (int)ph.size(); p++) {
+            const TBPhase& P = ph[p];
             if (P.kind == 0 && P.l < h->nlev) cap += (long long)h->lev[P.l].bx * h->lev[P.l].by;
             if (P.kind == 1 && P.l + 1 < h->nlev) cap += (long long)h->lev[P.l].bx * h->lev[P.l].by;
+            if (P.kind == 2 && audit) cap += 4 * blk_cap;
+            if (P.kind == 0 && P.first && P.l < 4 && D.pfirst[P.l] < 0) D.pfirst[P.l] = p;
         }
+        if (audit) {
+            D.aw.ensure(h->mem, (size_t)slot_cap * AUDIT_SLOT);
+            D.ascale.ensure(h->mem, (size_t)slot_cap);
+            D.arng.ensure(h->mem, (size_t)blk_cap);
+            D.apart.ensure(h->mem, (size_t)blk_cap * 24);
+        } else {
+            D.aw.release(h->mem);
+            D.ascale.release(h->mem);
+            D.arng.release(h->mem);
+            D.apart.release(h->mem);
+        }
+        D.audit = audit;
         // a cyclic list's tickets (tasks x iterations, up to 64) are ints too
         if (cap >= ((1LL << 31) - 1) / (cyclic ? 64 : 1)) throw Fail{VLBM_ERR_ARG, "hierarchy too large for one task list"};
         if (acc.empty()) acc.push_back(TBAcc{0, 0, 0});
@@ -1700,6 +1758,10 @@ vlbm_hier::DevPlan& dev_plan(vlbm_hier* h, int k, bool cyclic) {
         sg.tasks = D.tasks.p;
         sg.deps = D.deps.p;
         sg.done = D.done.p;
+        sg.aw = audit ? D.aw.p : nullptr;
+        sg.arng = audit ? D.arng.p : nullptr;
+        sg.ascale = audit ? D.ascale.p : nullptr;
+        sg.apart = audit ? D.apart.p : nullptr;
         sg.par0 = h->words;
         sg.lid_base = 0;
         D.seg.upload(h->mem, std::vector<Segment>{sg}, s);
@@ -1769,6 +1831,10 @@ vlbm_hier::DevPlan& dev_plan(vlbm_hier* h, int k, bool cyclic) {
         P.seg = D.seg.p;
         P.prefix = D.prefix.p;
         P.ctl = D.ctl.p;
+        P.audit = D.audit ? 1 : 0;
+        for (int l = 0; l < 4; l++) P.pfirst[l] = D.pfirst[l];
+        P.ascale = D.ascale.p;
+        P.arng = D.arng.p;
         VCK(launch_task_build(P, bs));
         if (bs != s) {
             VCK(cudaEventRecord(h->ev_built, bs));
@@ -1868,24 +1934,35 @@ void count_lups(vlbm_hier* h, long long n) {
 void dev_advance(vlbm_hier* h, long long n, int sched) {
     cudaStream_t s = h->stream;
     const int G = h->tune.graph_steps;
+    // totals after the last regrid still to come: from the first launch's
+    // first step on the persistent schedule, else by a separate audit now
+    if (h->after_pending >= 0 && (sched != 1 || n <= 0)) settle_after_audit(h);
+    auto launch = [&](cudaGraphExec_t ex, long long nk) {
+        vlbm_hier::DevPlan& D = h->dp[0];
+        const bool fused = sched == 1 && h->after_pending >= 0 && D.audit;
+        if (h->after_pending >= 0 && !fused) settle_after_audit(h);
+        if (fused) VCK(cudaMemsetAsync(D.ctl.p + CTL_AUDIT, 1, sizeof(int), s));  // nonzero: audited
+        VCK(cudaGraphLaunch(ex, s));
+        h->klaunch += nk;
+        if (fused) {
+            VCK(launch_audit_blocks(D.apart.p, D.need.p + 6, h->raud + 16 * h->after_pending + 8,
+                                    D.ctl.p + CTL_AUDIT, s));
+            h->after_pending = -1;
+            h->klaunch += 1;
+        }
+    };
     long long left = n;
     if (left >= G) {
         cudaGraphExec_t ex = sched == 1 ? dev_task_graph(h, 1, G) : dev_phase_graph(h, 1, G);
         if (sched == 1) h->klaunch += h->dp[0].build_kernels;  // a task list build, if one was queued
         const long long nk = graph_kernels(ex);
-        for (; left >= G; left -= G) {
-            VCK(cudaGraphLaunch(ex, s));
-            h->klaunch += nk;
-        }
+        for (; left >= G; left -= G) launch(ex, nk);
     }
     if (left > 0) {
         cudaGraphExec_t ex = sched == 1 ? dev_task_graph(h, 0, 1) : dev_phase_graph(h, 0, 1);
         if (sched == 1) h->klaunch += h->dp[0].build_kernels;
         const long long nk = graph_kernels(ex);
-        for (; left > 0; left--) {
-            VCK(cudaGraphLaunch(ex, s));
-            h->klaunch += nk;
-        }
+        for (; left > 0; left--) launch(ex, nk);
     }
     count_lups(h, n);
     h->klaunch += 1;
@@ -1898,8 +1975,12 @@ void release_dev_plans(vlbm_hier* h) {
             D.exec[w] = nullptr;
             D.key[w].clear();
         }
-        for (DArr<int>* a : {&D.acc_beg, &D.acc_pos, &D.off, &D.deps, &D.need, &D.prefix, &D.ctl, &D.big})
+        for (DArr<int>* a : {&D.acc_beg, &D.acc_pos, &D.off, &D.deps, &D.need, &D.prefix, &D.ctl, &D.big, &D.ascale})
             a->release(h->mem);
+        D.aw.release(h->mem);
+        D.arng.release(h->mem);
+        D.apart.release(h->mem);
+        D.audit = false;
         D.chunks.release(h->mem);
         D.ph.release(h->mem);
         D.acc.release(h->mem);
@@ -2121,11 +2202,13 @@ void destroy_levels(vlbm_hier* h) {
     h->rg_cap = 0;
     if (h->rg_ev) cudaEventDestroy(h->rg_ev);
     h->rg_ev = nullptr;
-    if (h->aux) {
-        cudaStreamSynchronize(h->aux);
-        cudaStreamDestroy(h->aux);
+    for (cudaStream_t* st : {&h->aux, &h->aux2}) {
+        if (*st) {
+            cudaStreamSynchronize(*st);
+            cudaStreamDestroy(*st);
+        }
+        *st = nullptr;
     }
-    h->aux = nullptr;
     for (cudaEvent_t* ev : {&h->ev_layout, &h->ev_built, &h->ev_rg0, &h->ev_audit}) {
         if (*ev) cudaEventDestroy(*ev);
         *ev = nullptr;
@@ -2316,6 +2399,7 @@ const char* vlbm_last_error(const vlbm_hier* h) { return h ? h->err.c_str() : "n
 vlbm_status vlbm_set_state(vlbm_hier* h, int32_t level, const double* W, int64_t ld, int32_t on_device) {
     return run(h, [&] {
         if (level < 0 || level >= h->nlev || !W) throw Fail{VLBM_ERR_ARG, "bad level or W"};
+        settle_after_audit(h);
         Level& L = h->lev[level];
         if (ld < L.nx) throw Fail{VLBM_ERR_ARG, "ld < nx"};
         const double* src = W;
@@ -2336,6 +2420,7 @@ static vlbm_status pop_copy(vlbm_hier* h, int32_t level, double* f, int64_t ld, 
         if (level < 0 || level >= h->nlev || !f) throw Fail{VLBM_ERR_ARG, "bad level or f"};
         Level& L = h->lev[level];
         if (ld < L.nx) throw Fail{VLBM_ERR_ARG, "ld < nx"};
+        if (!to_ext) settle_after_audit(h);
         const size_t n = (size_t)16 * ld * L.ny;
         double* ext = f;
         if (!on_device) {
@@ -2376,6 +2461,7 @@ vlbm_status vlbm_advance(vlbm_hier* h, int64_t coarse_steps) {
     return run(h, [&] {
         if (coarse_steps < 0) throw Fail{VLBM_ERR_ARG, "negative step count"};
         if (h->engine) throw Fail{VLBM_ERR_ARG, "hierarchy is resident in an engine"};
+        if (h->step_audit) settle_after_audit(h);
         if (!h->step_audit) {
             // on the device lists: nothing here waits for the GPU
             long long left = coarse_steps;
@@ -2508,6 +2594,7 @@ vlbm_status vlbm_checkpoint_load(vlbm_hier* h, const void* blob, size_t bytes) {
         for (int i = 0; i < 4; i++) same = same && H.bc[i] == h->cfg.bc[i];
         if (!same) throw Fail{VLBM_ERR_ARG, "checkpoint made under another configuration"};
         if (bytes < ckpt_bytes(h)) throw Fail{VLBM_ERR_ARG, "blob too small"};
+        settle_after_audit(h);
         VCK(cudaStreamSynchronize(h->stream));
         const char* p = (const char*)blob + sizeof H;
         std::vector<uint8_t> bin[VLBM_MAX_LEVELS], bcov[VLBM_MAX_LEVELS];
@@ -2634,6 +2721,7 @@ vlbm_status vlbm_get_layout(vlbm_hier* h, int32_t level, uint8_t* in, uint8_t* r
 vlbm_status vlbm_regrid_masks(vlbm_hier* h, const uint8_t* const* ref) {
     return run(h, [&] {
         check_status(h);
+        settle_after_audit(h);
         std::vector<uint8_t> bcov[VLBM_MAX_LEVELS];
         masks_to_maps(h, ref, bcov);
         regrid_to(h, bcov, false);
@@ -2644,6 +2732,7 @@ vlbm_status vlbm_regrid_masks(vlbm_hier* h, const uint8_t* const* ref) {
 vlbm_status vlbm_regrid(vlbm_hier* h, const vlbm_box* boxes, int32_t nboxes) {
     return run(h, [&] {
         auto t0 = std::chrono::steady_clock::now();
+        settle_after_audit(h);
         if (boxes || nboxes > 0) {
             std::vector<uint8_t> bcov[VLBM_MAX_LEVELS];
             check_status(h);
@@ -2927,12 +3016,14 @@ vlbm_status vlbm_set_regrid_audit(vlbm_hier* h, int32_t on) {
         }
         h->regrid_audit = on != 0;
         h->ra_n = h->ra_read = 0;
+        h->after_pending = -1;  // its row is dropped with the others
     });
 }
 
 vlbm_status vlbm_get_regrid_audits(vlbm_hier* h, double* out, int64_t cap, int64_t* n) {
     return run(h, [&] {
         if (!n || cap < 0 || (cap > 0 && !out)) throw Fail{VLBM_ERR_ARG, "bad arguments"};
+        settle_after_audit(h);
         VCK(cudaStreamSynchronize(h->stream));
         check_status(h);
         long long avail = h->ra_n - h->ra_read;
@@ -2982,6 +3073,7 @@ vlbm_status vlbm_profile(vlbm_hier* h, int64_t coarse_steps, vlbm_kernel_time* o
     return run(h, [&] {
         if (coarse_steps < 0 || !out || !n) throw Fail{VLBM_ERR_ARG, "bad profile arguments"};
         if (h->engine) throw Fail{VLBM_ERR_ARG, "hierarchy is resident in an engine"};
+        settle_after_audit(h);
         ensure_own_batch(h, effective_schedule(h));  // profile() launches phase by phase
         count_lups(h, coarse_steps);
         long long cells[VLBM_MAX_LEVELS] = {};
@@ -3075,7 +3167,8 @@ vlbm_status vlbm_engine_admit(vlbm_engine* e, vlbm_hier* h, int64_t coarse_steps
         if (r.live) used += (long long)r.h->device_bytes();
     if (e->budget && (size_t)(used + (long long)h->device_bytes()) > e->budget) return VLBM_ERR_OOM;
     // the hierarchy's own queue must be drained before it joins the engine,
-    // with its layout on the host
+    // with its layout on the host (and the totals after its last regrid)
+    if (run(h, [&] { settle_after_audit(h); }) != VLBM_OK) return VLBM_ERR_CUDA;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return VLBM_ERR_CUDA;
     if (run(h, [&] { ensure_host(h); }) != VLBM_OK) return VLBM_ERR_CUDA;
     int s = -1;

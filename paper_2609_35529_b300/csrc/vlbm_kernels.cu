@@ -488,14 +488,58 @@ __device__ __forceinline__ void win_fold(Fix192& acc, Win128& w, int base) {
     w.lo = w.hi = 0ull;
 }
 
+// A thread's running exact sums (sum, abs_sum) with the 128-bit window in
+// front of them: add(v, sc) takes v * 2^sc, flush() folds the window in.
+struct WinSum {
+    Win128 ws{0ull, 0ull}, wa{0ull, 0ull};
+    int base = -1, nfast = 0;
+
+    __device__ __forceinline__ void add(double v, int sc, Fix192& sum, Fix192& abs_sum) {
+        const unsigned long long B = (unsigned long long)__double_as_longlong(v);
+        if ((B << 1) == 0ull) return;  // +-0
+        const int E = (int)((B >> 52) & 0x7FFull);
+        const int sh = E - 947 + sc;  // position of the significand's lsb (2^-128 units)
+        if (base < 0 && E != 0 && E != 2047) base = min(max(sh - 32, 0), 64);
+        const int d = sh - base;
+        if (E == 0 || E == 2047 || base < 0 || d < 0 || d > 63) {
+            fix_accumulate(sum, abs_sum, v, sc);
+            return;
+        }
+        const unsigned long long m = (B & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+        const unsigned long long lo = m << d;
+        const unsigned long long hi = d ? m >> (64 - d) : 0ull;
+        // |v| into the magnitude window
+        const unsigned long long a0 = wa.lo + lo;
+        wa.hi += hi + (a0 < lo ? 1ull : 0ull);
+        wa.lo = a0;
+        // +-|v| into the signed window
+        if (B >> 63) {
+            const unsigned long long brw = ws.lo < lo ? 1ull : 0ull;
+            ws.lo -= lo;
+            ws.hi -= hi + brw;
+        } else {
+            const unsigned long long s0 = ws.lo + lo;
+            ws.hi += hi + (s0 < lo ? 1ull : 0ull);
+            ws.lo = s0;
+        }
+        if (++nfast == 1023) flush(sum, abs_sum);
+    }
+
+    __device__ __forceinline__ void flush(Fix192& sum, Fix192& abs_sum) {
+        if (base < 0) return;
+        win_fold(sum, ws, base);
+        win_fold(abs_sum, wa, base);
+        nfast = 0;
+    }
+};
+
 // Exact per-thread sums of v_j * 2^scale[j] for v_j = aw[j * AUDIT_SLOT +
 // col], slots j in [j0, j1), into sum and abs_sum (192-bit), through the
 // 128-bit window; COH: loads through L2 (data written in the same launch).
 template <bool COH>
 __device__ __forceinline__ void audit_thread_sums(const double* __restrict__ aw, const int* __restrict__ scale,
                                                   int j0, int j1, int col, Fix192& sum, Fix192& abs_sum) {
-    Win128 ws{0ull, 0ull}, wa{0ull, 0ull};
-    int base = -1, nfast = 0;
+    WinSum acc;
     // AUDIT_BATCH loads in flight per thread, then their accumulation
     constexpr int AUDIT_BATCH = 8;
     for (int jb = j0; jb < j1; jb += AUDIT_BATCH) {
@@ -509,47 +553,9 @@ __device__ __forceinline__ void audit_thread_sums(const double* __restrict__ aw,
             sb[u] = j < j1 ? (COH ? __ldcg(scale + j) : __ldg(scale + j)) : 0;
         }
 #pragma unroll
-        for (int u = 0; u < AUDIT_BATCH; u++) {
-            const double v = vb[u];
-            const unsigned long long B = (unsigned long long)__double_as_longlong(v);
-            if ((B << 1) == 0ull) continue;  // +-0
-            const int E = (int)((B >> 52) & 0x7FFull);
-            const int sc = sb[u];
-            const int sh = E - 947 + sc;  // position of the significand's lsb (2^-128 units)
-            if (base < 0 && E != 0 && E != 2047) base = min(max(sh - 32, 0), 64);
-            const int d = sh - base;
-            if (E == 0 || E == 2047 || base < 0 || d < 0 || d > 63) {
-                fix_accumulate(sum, abs_sum, v, sc);
-                continue;
-            }
-            const unsigned long long m = (B & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
-            const unsigned long long lo = m << d;
-            const unsigned long long hi = d ? m >> (64 - d) : 0ull;
-            // |v| into the magnitude window
-            const unsigned long long a0 = wa.lo + lo;
-            wa.hi += hi + (a0 < lo ? 1ull : 0ull);
-            wa.lo = a0;
-            // +-|v| into the signed window
-            if (B >> 63) {
-                const unsigned long long brw = ws.lo < lo ? 1ull : 0ull;
-                ws.lo -= lo;
-                ws.hi -= hi + brw;
-            } else {
-                const unsigned long long s0 = ws.lo + lo;
-                ws.hi += hi + (s0 < lo ? 1ull : 0ull);
-                ws.lo = s0;
-            }
-            if (++nfast == 1023) {
-                win_fold(sum, ws, base);
-                win_fold(abs_sum, wa, base);
-                nfast = 0;
-            }
-        }
+        for (int u = 0; u < AUDIT_BATCH; u++) acc.add(vb[u], sb[u], sum, abs_sum);
     }
-    if (base >= 0) {
-        win_fold(sum, ws, base);
-        win_fold(abs_sum, wa, base);
-    }
+    acc.flush(sum, abs_sum);
 }
 
 // Barrier of one 64-thread group (named barrier 1 + g).
@@ -699,6 +705,7 @@ task_kernel(const LevelDev* __restrict__ levs, const Segment* __restrict__ segs,
     const int cx = lt & 7, cy = lt >> 3;
     const unsigned epoch = (unsigned)ctl[CTL_EPOCH];
     const int total = ctl[CTL_TOTAL], nseg = ctl[CTL_NSEG], nchunk = ctl[CTL_NCHUNK];
+    const bool audit = ctl[CTL_AUDIT] != 0;
     const int tickets = total * iters;
     if (lt == 0) s_task[g][0] = atomicAdd(&ctl[CTL_CLAIM], 1);
     group_bar(g);
@@ -714,11 +721,14 @@ task_kernel(const LevelDev* __restrict__ levs, const Segment* __restrict__ segs,
         const LevelDev& L = levs[T.lid + S.lid_base];
         const unsigned mark = 2u * (epoch + (unsigned)it);
         const int step = T.step + it;
-        wait_deps(S, T, it, mark, lt, 64, L.status);
+        // audit work (moments kept, reduction tasks) in the first iteration
+        // of an audited launch only; a reduction task is empty otherwise
+        const bool aud = audit && it == 0;
+        if (T.kind != 2 || aud) wait_deps(S, T, it, mark, lt, 64, L.status);
         if (lt == 0) s_task[g][par ^ 1] = atomicAdd(&ctl[CTL_CLAIM], 1);
         group_bar(g);
         if (T.kind == 0) {
-            if (S.aw && T.aslot >= 0) {
+            if (aud && S.aw && T.aslot >= 0) {
                 // audited sweep: keep the moments of the cell (0 off the
                 // active set) for the exact reduction after the launch
                 double W[4] = {0.0, 0.0, 0.0, 0.0};
@@ -730,7 +740,7 @@ task_kernel(const LevelDev* __restrict__ levs, const Segment* __restrict__ segs,
             }
         } else if (T.kind == 1) {
             close_cell<true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, step);
-        } else {
+        } else if (aud) {
             audit_task(S, T, g, lt);
         }
         group_bar(g);
@@ -762,6 +772,7 @@ task_kernel_half(const LevelDev* __restrict__ levs, const Segment* __restrict__ 
     const int lane = threadIdx.x & 31;
     const unsigned epoch = (unsigned)ctl[CTL_EPOCH];
     const int total = ctl[CTL_TOTAL], nseg = ctl[CTL_NSEG], nchunk = ctl[CTL_NCHUNK];
+    const bool audit = ctl[CTL_AUDIT] != 0;
     const int tickets = 2 * total * iters;
     for (;;) {
         int h = 0;
@@ -778,11 +789,12 @@ task_kernel_half(const LevelDev* __restrict__ levs, const Segment* __restrict__ 
         const LevelDev& L = levs[T.lid + S.lid_base];
         const unsigned mark = 2u * (epoch + (unsigned)it);
         const int step = T.step + it;
-        wait_deps(S, T, it, mark, lane, 32, L.status);
+        const bool aud = audit && it == 0;
+        if (T.kind != 2 || aud) wait_deps(S, T, it, mark, lane, 32, L.status);
         __syncwarp();
         const int cx = lane & 7, cy = half * 4 + (lane >> 3), lt = cy * 8 + cx;
         if (T.kind == 0) {
-            if (S.aw && T.aslot >= 0) {
+            if (aud && S.aw && T.aslot >= 0) {
                 double W[4] = {0.0, 0.0, 0.0, 0.0};
                 sweep_cell<P, true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, T.kkp, step, W);
                 double* o = S.aw + (size_t)T.aslot * AUDIT_SLOT + lt;
@@ -792,7 +804,7 @@ task_kernel_half(const LevelDev* __restrict__ levs, const Segment* __restrict__ 
             }
         } else if (T.kind == 1) {
             close_cell<true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, step);
-        } else if (half == 0) {  // the first half does the whole audit task
+        } else if (aud && half == 0) {  // the first half does the whole audit task
             audit_task_warp(S, T, lane);
         }
         __syncwarp();
@@ -922,39 +934,53 @@ __global__ void gather_W_kernel(LevelDev L, double* __restrict__ W, long long ld
 // thread holds two accumulators and many CTAs fit on an SM.  The last CTA to
 // finish writes the rounded totals out[0..7] (ticket: a zeroed counter,
 // left zeroed).
-// Flags of cell (cx, cy) of tile w (0 beyond the level's extent).
-__device__ __forceinline__ uint32_t audit_flags(const LevelDev* __restrict__ levs, const Item& w, int cx, int cy) {
+
+// One thread's view of one tile: the flags and the four populations of its
+// (field, cell), loaded without waiting for them.
+struct AuditCell {
+    uint32_t fl;
+    int lev;
+    double f0, f1, f2, f3;
+};
+
+__device__ __forceinline__ AuditCell audit_load(const LevelDev* __restrict__ levs, const Item* __restrict__ items,
+                                                int it, int nitems, int k, int cx, int cy) {
+    AuditCell a{0u, 0, 0.0, 0.0, 0.0, 0.0};
+    if (it >= nitems) return a;
+    const Item w = items[it];
     const LevelDev& L = levs[w.lid];
     const int x = w.tx * TILE + cx, y = w.ty * TILE + cy;
-    if (x >= L.nx || y >= L.ny) return 0;
-    return L.flags[(long long)y * L.pitch + x];
+    if (x >= L.nx || y >= L.ny) return a;
+    const long long c = (long long)y * L.pitch + x;
+    const double* st = L.buf[state_buf(L)];
+    a.fl = L.flags[c];
+    a.lev = L.level;
+    // every cell of the level's extent has storage: the populations load
+    // alongside the flags, and only active cells are added up
+    a.f0 = __ldcs(st + qoff(0 + k, L.plane, c));
+    a.f1 = __ldcs(st + qoff(4 + k, L.plane, c));
+    a.f2 = __ldcs(st + qoff(8 + k, L.plane, c));
+    a.f3 = __ldcs(st + qoff(12 + k, L.plane, c));
+    return a;
 }
 
 // The CTA that finishes last: out[m] = the correctly rounded sum of quantity
-// m over the partials of the launch's nb blocks, one quantity at a time.
+// m over the partials of the launch's nb blocks; warp m of the CTA takes
+// quantity m.
 __device__ __noinline__ void audit_finish(const unsigned long long* part, int nb, double* out) {
-    __shared__ Fix192 red[8];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int m = 0; m < 8; m++) {
-        Fix192 a = fix_zero();
-        for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-            Fix192 v;
-            for (int j = 0; j < 3; j++) v.w[j] = __ldcg(part + (size_t)i * 24 + 3 * m + j);
-            fix_add(a, v);
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const Fix192 b = fix_shfl_down(a, o);
-            fix_add(a, b);
-        }
-        if (lane == 0) red[wid] = a;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            Fix192 t = red[0];
-            for (int w = 1; w < (int)(blockDim.x >> 5); w++) fix_add(t, red[w]);
-            out[m] = fix_to_double(t);
-        }
-        __syncthreads();
+    const int lane = threadIdx.x & 31, m = threadIdx.x >> 5;
+    if (m >= 8) return;
+    Fix192 a = fix_zero();
+    for (int i = lane; i < nb; i += 32) {
+        Fix192 v;
+        for (int j = 0; j < 3; j++) v.w[j] = __ldcg(part + (size_t)i * 24 + 3 * m + j);
+        fix_add(a, v);
     }
+    for (int o = 16; o > 0; o >>= 1) {
+        const Fix192 b = fix_shfl_down(a, o);
+        fix_add(a, b);
+    }
+    if (lane == 0) out[m] = fix_to_double(a);
 }
 
 __global__ void __launch_bounds__(256) audit_kernel(const LevelDev* __restrict__ levs, const Item* __restrict__ items,
@@ -966,31 +992,16 @@ __global__ void __launch_bounds__(256) audit_kernel(const LevelDev* __restrict__
     const int cx = threadIdx.x & 7;
     const int cy = (threadIdx.x >> 3) & 7;
     Fix192 sum = fix_zero(), abs_sum = fix_zero();
-    // the loads are pipelined: the next tile's list entry is in flight while
-    // this tile's populations load, and its flags while they are added up
-    const Item none{0, 0, 0};
-    int it = blockIdx.x;
-    Item w = it < nitems ? items[it] : none;
-    uint32_t fl = it < nitems ? audit_flags(levs, w, cx, cy) : 0u;
-    for (; it < nitems; it += gridDim.x) {
-        const int nx = it + gridDim.x;
-        const Item wn = nx < nitems ? items[nx] : none;
-        double v = 0.0;
-        int lev = 0;
-        const bool on = (fl & (F_IN | F_COV)) == F_IN;
-        if (on) {
-            const LevelDev& L = levs[w.lid];
-            const long long c = (long long)(w.ty * TILE + cy) * L.pitch + (w.tx * TILE + cx);
-            const double* st = L.buf[state_buf(L)];
-            v = (st[qoff(0 + k, L.plane, c)] + st[qoff(4 + k, L.plane, c)]) +
-                (st[qoff(8 + k, L.plane, c)] + st[qoff(12 + k, L.plane, c)]);
-            lev = L.level;
-        }
-        const uint32_t fn = nx < nitems ? audit_flags(levs, wn, cx, cy) : 0u;
-        if (on) fix_accumulate(sum, abs_sum, v, -2 * lev);
-        w = wn;
-        fl = fn;
+    WinSum acc;
+    // the next tile's flags and populations are in flight while this tile's
+    // are added up
+    AuditCell cur = audit_load(levs, items, blockIdx.x, nitems, k, cx, cy);
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const AuditCell nxt = audit_load(levs, items, it + gridDim.x, nitems, k, cx, cy);
+        if ((cur.fl & (F_IN | F_COV)) == F_IN) acc.add((cur.f0 + cur.f1) + (cur.f2 + cur.f3), -2 * cur.lev, sum, abs_sum);
+        cur = nxt;
     }
+    acc.flush(sum, abs_sum);
     __shared__ Fix192 sh[8][2];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int o = 16; o > 0; o >>= 1) {
@@ -1023,6 +1034,16 @@ __global__ void __launch_bounds__(256) audit_kernel(const LevelDev* __restrict__
     __threadfence();
     audit_finish(part, gridDim.x, out);
     if (threadIdx.x == 0) *ticket = 0u;
+}
+
+// Totals of an audited persistent launch: out[m] = the correctly rounded sum
+// of quantity m over the *nblk reduction blocks' partials (24 words each);
+// then closes the launch's audit gate (*gate = 0).  One CTA of 256 threads.
+__global__ void __launch_bounds__(256) audit_blocks_kernel(const unsigned long long* __restrict__ part,
+                                                           const int* __restrict__ nblk, double* __restrict__ out,
+                                                           int* gate) {
+    audit_finish(part, *nblk, out);
+    if (threadIdx.x == 0) *gate = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -1527,6 +1548,12 @@ cudaError_t launch_tasks(const LevelDev* levs, const Segment* segs, const int* p
 #undef X
         default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_audit_blocks(const unsigned long long* part, const int* nblk, double* out, int* gate,
+                                cudaStream_t s) {
+    audit_blocks_kernel<<<1, 256, 0, s>>>(part, nblk, out, gate);
     return cudaGetLastError();
 }
 

@@ -24,6 +24,11 @@ cudaError_t launch_tasks(const LevelDev* levs, const Segment* segs, const int* p
                          int variant, int ctas, int iters, cudaStream_t s);
 cudaError_t launch_audit_segments(const unsigned long long* slots, const int* seg, int nseg, double* out,
                                   cudaStream_t s);
+// Totals of an audited persistent launch from its reduction blocks' exact
+// partials (*nblk blocks of 24 words, device count) into out[0..7]; clears
+// *gate (the launch's CTL_AUDIT word) afterwards.
+cudaError_t launch_audit_blocks(const unsigned long long* part, const int* nblk, double* out, int* gate,
+                                cudaStream_t s);
 cudaError_t launch_close(const LevelDev* levs, const Item* items, int n, int kk, cudaStream_t s,
                          const int* nc = nullptr);
 cudaError_t launch_end_step(int* const* par, int n, cudaStream_t s);

@@ -259,6 +259,43 @@ def test_adaptive_shockbubble_small(V):
     assert info["active_cells"][1] > 0 and info["active_cells"][2] > 0
 
 
+@pytest.mark.parametrize("schedule,graph_steps,variant", [(1, 4, 1), (1, 1, 3), (0, 4, 1)])
+def test_regrid_audit_rows_equal_separate_audits(V, schedule, graph_steps, variant):
+    """The exact totals recorded before and after each device regrid equal
+    separate audits of the same states, however the totals after a regrid
+    are taken: from the first sweeps of the next persistent launch (their
+    moments reduced by tasks of the same launch), or by a separate audit
+    (per-phase steps, a second regrid with no step between, or reading the
+    rows before the next step)."""
+    cs = I.shockbubble(nx0=128, ny0=64, nlev=3)
+    g = V.Hierarchy.from_case(cs)
+    g.set_tuning(variant=variant, schedule=schedule, graph_steps=graph_steps, persist_after=0)
+    for _ in range(2):
+        g.regrid()
+    g.set_regrid_audit(True)
+    want = []
+    for cycle in range(7):
+        g.advance(4)
+        b = g.audit()
+        g.regrid()
+        want.append((b, g.audit()))
+        if cycle == 3:  # a second regrid straight after the first
+            b = g.audit()
+            g.regrid()
+            want.append((b, g.audit()))
+    g.advance(3)
+    rows = g.regrid_audits()
+    b = g.audit()
+    g.regrid()
+    want.append((b, g.audit()))
+    rows = np.concatenate([rows, g.regrid_audits()])  # the last row's totals after: read before any step
+    assert rows.shape == (len(want), 16)
+    for r, ((t0, a0), (t1, a1)) in zip(rows, want):
+        assert np.array_equal(r[0:4], t0) and np.array_equal(r[4:8], a0)
+        assert np.array_equal(r[8:12], t1) and np.array_equal(r[12:16], a1)
+        assert drift(t0, t1, a0) < 1e-14
+
+
 def test_adaptive_shockbubble_flux_jump_sensor(V):
     """The same adaptive run driven by the paper's flux-jump sensor (Sec. 3.4,
     Eq. amr-sigma, tol 0.01): tags, layouts and populations match the oracle

@@ -347,6 +347,17 @@ vlbm_status vlbm_get_tuning(const vlbm_hier* h, vlbm_tuning* t);
 vlbm_status vlbm_selftest_rcp(uint64_t seed, int64_t n, uint64_t* mismatches, uint64_t* unsettled,
                               double first_bad[2]);
 
+/* Self-test of the correctly rounded division a / b that the relaxation
+ * sensor uses (the reciprocal above, then two remainder corrections by
+ * fused multiply-add): over n test pairs (SplitMix64 stream from `seed`;
+ * quotients of the sensor's kinds, operands over the whole binary64 range
+ * with random signs, exponents next to the fast path's bounds, zeros,
+ * subnormals, infinities, NaNs, raw bit patterns) *mismatches counts
+ * quotients whose bits differ from the FP64 division; first_bad (may be
+ * NULL) receives the first offending (a, b, result).  Runs on the current
+ * device and synchronises it.  Errors: ERR_ARG, ERR_OOM, ERR_CUDA. */
+vlbm_status vlbm_selftest_div(uint64_t seed, int64_t n, uint64_t* mismatches, double first_bad[3]);
+
 /* Sensor-driven relaxation (Sec. 2.2, Eq. sensor-B).  on = 1: every level
  * step first evaluates, on the level's pre-collision state,
  *   s_k   = dx (div Q)_k / qmax_k (central differences), qmax_k =

@@ -108,6 +108,30 @@ __device__ __forceinline__ unsigned long long rcp_seed_dev(unsigned long long M)
 }
 
 __device__ __forceinline__ double rcp_rn(double x) { return rcp_rn_with(x, rcp_seed_dev); }
+
+// a / b correctly rounded (the IEEE quotient), given y = RN(1/b): one FP64
+// multiply and four fma in place of the division's longer sequence.
+// q0 = RN(a y) lies within two ulps of a / b; a correction q <- RN(q + r y)
+// with the remainder r = a - b q (one fma) then leaves q within one ulp, so
+// the next remainder is exact, and with y within half an ulp of 1/b the
+// second correction gives RN(a / b) (Markstein's theorem; Muller et al.,
+// Handbook of Floating-Point Arithmetic, on division by Newton-Raphson
+// iteration).  Operands of magnitude outside [2^-500, 2^501) -- zero,
+// subnormal, huge, infinite, NaN -- where a remainder or the quotient could
+// leave the normal range take the division itself.
+__device__ __forceinline__ double div_rn_y(double a, double b, double y) {
+    const unsigned ea = (unsigned)((unsigned long long)__double_as_longlong(a) >> 52) & 0x7FFu;
+    const unsigned eb = (unsigned)((unsigned long long)__double_as_longlong(b) >> 52) & 0x7FFu;
+    if (ea - 523u > 1000u || eb - 523u > 1000u) return a / b;
+    double q = a * y;
+    double r = fma(-q, b, a);
+    q = fma(r, y, q);
+    r = fma(-q, b, a);
+    return fma(r, y, q);
+}
+
+// a / b with the reciprocal of b on the integer pipes.
+__device__ __forceinline__ double div_rn(double a, double b) { return div_rn_y(a, b, rcp_rn(b)); }
 #endif
 
 }  // namespace vlbm

@@ -73,12 +73,13 @@ struct LevelDev {
     double wscale;    // area weight 4^-level
     double feqb[4][16];
     // sensor-driven relaxation (sens == nullptr: constant beta): planes of
-    // sens: 0-3 Qx, 4-7 Qy, 8 u, 9 v (from the pre-collision state of the
-    // level step), 10 s, 11 theta; plane stride `plane`
+    // sens: 0-3 Qx, 4-7 Qy, 8 u, 9 v, 12-15 W (from the pre-collision state
+    // of the level step), 10 s, 11 theta; plane stride `plane`.  rc = 1 / c
+    // (rounded to nearest).
     double* sens;
-    double beta_max, beta_min, csens, eps, ninth, c, iq[4];
+    double beta_max, beta_min, csens, eps, ninth, c, rc, iq[4];
 };
-constexpr int SENS_PLANES = 12;
+constexpr int SENS_PLANES = 16;
 
 #ifdef __CUDACC__
 #define VLBM_HD __host__ __device__

@@ -473,6 +473,7 @@ struct vlbm_hier {
         d.eps = s_eps;
         d.ninth = 1.0 / 9.0;
         d.c = cfg.c;
+        d.rc = 1.0 / cfg.c;
         for (int k = 0; k < 4; k++) d.iq[k] = s_iq[k];
         return d;
     }

@@ -28,7 +28,7 @@ __device__ __constant__ int kCY[4] = {0, 0, 1, -1};
 // Euler flux Q(W) with the ideal-gas closure (Sec. 2.1, Eq. 1).
 __device__ __forceinline__ void euler_flux(double gm1, const double W[4], double Qx[4], double Qy[4],
                                            double& p_out) {
-    const double inv = 1.0 / W[0];
+    const double inv = rcp_rn(W[0]);  // = 1.0 / W[0], on the integer pipes
     const double u = W[1] * inv;
     const double v = W[2] * inv;
     const double ruu = W[1] * u;
@@ -62,9 +62,24 @@ enum : int { SW_SENSOR = 1024 };
 
 // BGK relaxation (Eq. 6) in place: f <- 2 beta f^eq(W) + (1 - 2 beta) f with
 // 2 beta f^eq_{+-alpha} = (beta/2) W +- (beta/c) Q_alpha (Eq. 4, D = 2):
-// f* = fma(+-beta/c, Q_alpha, fma(1 - 2 beta, f, (beta/2) W)).  The one
-// division 1/rho is the correctly rounded reciprocal on the integer pipes
-// (the same bits as 1.0 / rho).  Returns whether the state is physical.
+// f* = fma(+-beta/c, Q_alpha, fma(1 - 2 beta, f, (beta/2) W)), for given
+// moments W and fluxes Q.
+__device__ __forceinline__ void relax(double f[16], const double W[4], const double Qx[4], const double Qy[4],
+                                      double om, double hb, double bcs) {
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const double A = hb * W[k];
+        f[k] = fma(bcs, Qx[k], fma(om, f[k], A));
+        f[4 + k] = fma(-bcs, Qx[k], fma(om, f[4 + k], A));
+        f[8 + k] = fma(bcs, Qy[k], fma(om, f[8 + k], A));
+        f[12 + k] = fma(-bcs, Qy[k], fma(om, f[12 + k], A));
+    }
+}
+
+// The collision of a cell: moments and Euler flux of its populations, then
+// the relaxation.  The one division 1/rho is the correctly rounded
+// reciprocal on the integer pipes (the same bits as 1.0 / rho).  Returns
+// whether the state is physical.
 __device__ __forceinline__ bool collide(double f[16], double om, double hb, double bcs, double gm1,
                                         double* Wout = nullptr) {
     double W[4], Qx[4], Qy[4];
@@ -87,14 +102,7 @@ __device__ __forceinline__ bool collide(double f[16], double om, double hb, doub
     Qy[1] = W[1] * v;
     Qy[2] = rvv + p;
     Qy[3] = H * v;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        const double A = hb * W[k];
-        f[k] = fma(bcs, Qx[k], fma(om, f[k], A));
-        f[4 + k] = fma(-bcs, Qx[k], fma(om, f[4 + k], A));
-        f[8 + k] = fma(bcs, Qy[k], fma(om, f[8 + k], A));
-        f[12 + k] = fma(-bcs, Qy[k], fma(om, f[12 + k], A));
-    }
+    relax(f, W, Qx, Qy, om, hb, bcs);
     return physical(W[0], p);
 }
 
@@ -159,7 +167,8 @@ __device__ __forceinline__ long long sens_nb(const LevelDev& L, int x, int y, in
     return (L.flags[cn] & (F_IN | F_COV)) == F_IN ? cn : c;
 }
 
-// Pass 1: Q, u, v of every active cell from the level step's source buffer.
+// Pass 1: W, Q, u, v of every active cell from the level step's source
+// buffer (the sweep relaxes with these W and Q), and the state's check.
 __global__ void sensor_prep_kernel(const LevelDev* __restrict__ levs, const Item* __restrict__ items, int nitems,
                                    int kk, const int* __restrict__ ncount) {
     if (ncount) nitems = *ncount;
@@ -180,13 +189,16 @@ __global__ void sensor_prep_kernel(const LevelDev* __restrict__ levs, const Item
             W[k] = (src[qoff(0 + k, L.plane, c)] + src[qoff(4 + k, L.plane, c)]) +
                    (src[qoff(8 + k, L.plane, c)] + src[qoff(12 + k, L.plane, c)]);
         euler_flux(L.gm1, W, Qx, Qy, p);
-        const double inv = 1.0 / W[0];
+        const double inv = rcp_rn(W[0]);  // = 1.0 / W[0]
         for (int k = 0; k < 4; k++) {
             L.sens[k * L.plane + c] = Qx[k];
             L.sens[(4 + k) * L.plane + c] = Qy[k];
+            L.sens[(12 + k) * L.plane + c] = W[k];
         }
         L.sens[8 * L.plane + c] = W[1] * inv;
         L.sens[9 * L.plane + c] = W[2] * inv;
+        // the sweep takes W and Q from here: the state's check is made here
+        if (!physical(W[0], p)) atomicOr(L.status, ST_NONPHYS);
     }
 }
 
@@ -217,7 +229,7 @@ __global__ void sensor_rate_kernel(const LevelDev* __restrict__ levs, const Item
         const double dil = (S[8 * P + e] - S[8 * P + ww]) + (S[9 * P + n] - S[9 * P + so]);
         const double vort = (S[9 * P + e] - S[9 * P + ww]) - (S[8 * P + n] - S[8 * P + so]);
         const double d2 = dil * dil;
-        L.sens[11 * P + c] = dil < 0.0 ? d2 / ((d2 + vort * vort) + L.eps) : 0.0;
+        L.sens[11 * P + c] = dil < 0.0 ? div_rn(d2, (d2 + vort * vort) + L.eps) : 0.0;
     }
 }
 
@@ -353,8 +365,20 @@ __device__ __forceinline__ void sweep_cell(const LevelDev* __restrict__ levs, co
     bool ok;
     if constexpr ((P & SW_SENSOR) != 0) {
         if (L.sens) {
+            // the moments and fluxes of the sensor's first pass (the same
+            // populations, the same expressions) and the cell's own beta
             const double b = sensor_beta_at(L, x, y);
-            ok = collide(f, 1.0 - 2.0 * b, 0.5 * b, b / L.c, L.gm1, Wout);
+            double W[4], Qx[4], Qy[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                W[k] = ld<COH>(L.sens + (12 + k) * plane + c);
+                Qx[k] = ld<COH>(L.sens + k * plane + c);
+                Qy[k] = ld<COH>(L.sens + (4 + k) * plane + c);
+            }
+            if (Wout)
+                for (int k = 0; k < 4; k++) Wout[k] = W[k];
+            relax(f, W, Qx, Qy, 1.0 - 2.0 * b, 0.5 * b, div_rn_y(b, L.c, L.rc));  // b / c
+            ok = true;  // the first pass checked the state
         } else {
             ok = collide(f, L.om, L.hb, L.bcs, L.gm1, Wout);
         }

@@ -129,6 +129,8 @@ def lib():
     L.vlbm_selftest_timeout.restype = C.c_int
     L.vlbm_selftest_rcp.argtypes = [C.c_uint64, i64, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), dp]
     L.vlbm_selftest_rcp.restype = C.c_int
+    L.vlbm_selftest_div.argtypes = [C.c_uint64, i64, C.POINTER(C.c_uint64), dp]
+    L.vlbm_selftest_div.restype = C.c_int
     L.vlbm_selftest_layout.argtypes = [C.c_uint64, i32, C.POINTER(i64), C.POINTER(i64), C.c_char_p, i32]
     L.vlbm_selftest_layout.restype = C.c_int
     L.vlbm_totals_static.argtypes = [vp, i64, i32, i32, C.c_double, vp, vp]
@@ -441,6 +443,18 @@ def selftest_rcp(seed, n):
     if st != 0:
         raise VlbmError(st, "vlbm_selftest_rcp")
     return int(bad.value), int(uns.value), tuple(first)
+
+
+def selftest_div(seed, n):
+    """Bitwise check of the sensor's division (integer-pipe reciprocal and
+    two remainder corrections) against the FP64 division on n seeded pairs;
+    returns (mismatches, first offending (a, b, result))."""
+    bad = C.c_uint64()
+    first = (C.c_double * 3)()
+    st = lib().vlbm_selftest_div(int(seed), int(n), C.byref(bad), first)
+    if st != 0:
+        raise VlbmError(st, "vlbm_selftest_div")
+    return int(bad.value), tuple(first)
 
 
 def selftest_layout(seed, cases):

@@ -42,3 +42,17 @@ def test_reciprocal_is_the_ieee_division_on_the_gpu(seed):
     build.build()
     bad, unsettled, first = vlbm.selftest_rcp(seed, 1 << 28)
     assert bad == 0 and unsettled == 0, (bad, unsettled, first)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("seed", [1, 2])
+def test_division_is_the_ieee_division_on_the_gpu(seed):
+    """The sensor's quotients (integer-pipe reciprocal, then two remainder
+    corrections) are the FP64 division's bits on 2^28 seeded pairs."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2609_35529_b300 import build, vlbm
+    build.build()
+    bad, first = vlbm.selftest_div(seed, 1 << 28)
+    assert bad == 0, (bad, first)

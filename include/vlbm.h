@@ -371,9 +371,10 @@ vlbm_status vlbm_selftest_div(uint64_t seed, int64_t n, uint64_t* mismatches, do
  * where s_bar, theta_bar are 3 x 3 box filters and beta_max is cfg->beta;
  * neighbours that are not active cells of the level take the cell's own
  * value.  W remains a collision invariant cell by cell, so conservation is
- * unchanged.  The hierarchy then advances with one launch per phase (two
- * sensor passes before each level sweep); the persistent schedule and
- * per-step totals are not available with the sensor.  on = 0: constant
+ * unchanged.  Two sensor passes precede each level sweep: two launches on
+ * schedule 0; on schedule 1 tasks of the persistent launch that depend on
+ * the tiles they read (one kernel form: the tuning's variant does not
+ * apply).  Per-step totals are not available with the sensor.  on = 0: constant
  * beta again.  Synchronises.  Errors: ERR_ARG (parameters: 0 <= beta_min
  * <= beta, c_sensor >= 0, eps >= 0; resident in an engine; per-step totals
  * on), ERR_OOM, ERR_CUDA, ERR_STATE. */

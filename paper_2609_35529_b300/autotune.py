@@ -11,7 +11,7 @@ regrids, where a layout lives only a few steps and the persistent schedule
 pays for a task list at every regrid.
 
 The signature is what the cost depends on: the level sizes, the active
-cells per level and beta.
+cells per level, beta and whether the sensor-driven relaxation is on.
 Results are cached in memory and, optionally, in a JSON file.
 """
 import json
@@ -39,10 +39,22 @@ DEFAULT_CANDIDATES = [
 _cache = {}
 
 
+# With the sensor-driven relaxation the sweep carries the sensor's filters
+# and its two passes are tasks of their own: the launch shapes rank
+# differently (more resident CTAs pay for the spills).
+SENSOR_CANDIDATES = [
+    {"variant": 1, "schedule": 1, "graph_steps": 8, "max_ctas": 0},
+    {"variant": 2, "schedule": 1, "graph_steps": 8, "max_ctas": 0},
+    {"variant": 3, "schedule": 1, "graph_steps": 8, "max_ctas": 0},
+    {"variant": 1, "schedule": 0, "graph_steps": 8, "max_ctas": 0},
+]
+
+
 def signature(h):
     info = h.info()
     return "|".join([",".join(map(str, info["nx"])), ",".join(map(str, info["ny"])),
-                     ",".join(map(str, info["active_cells"])), "om-1" if info["beta"] == 1.0 else "om"])
+                     ",".join(map(str, info["active_cells"])), "om-1" if info["beta"] == 1.0 else "om",
+                     "sensor" if getattr(h, "sensor_on", False) else "const"])
 
 
 def measure(h, cand, steps):

@@ -546,6 +546,18 @@ struct TB {
                 if (i >= 0) emit(base + i);
                 break;
             }
+            case TB_BOX9: {
+                const TBLevel& V = P.lev[l];
+                for (int d = 0; d < 9; d++) {
+                    const int dx = d % 3 - 1, dy = d / 3 - 1;
+                    bool ok = true;
+                    const int sx = wrap_or(tx - dx, V.bx, V.px, ok), sy = wrap_or(ty - dy, V.by, V.py, ok);
+                    if (!ok) continue;
+                    const int i = V.act_idx[sy * V.bx + sx];
+                    if (i >= 0) emit(base + i);
+                }
+                break;
+            }
         }
     }
 
@@ -567,13 +579,13 @@ struct TB {
     // swap across the wrap.
     template <class Emit>
     __device__ __forceinline__ void deps_of(int p, bool write, int l, int kind, int tx, int ty, Emit&& emit) const {
-        if (!write) {
+        if (!write && kind < 3) {
             const int m = wmask(l, tx, ty);
             if (kind == 2 ? !(m & 2) : !m) return;
         }
         bool readers = false;
         for (int pass = 0; pass < 1 + P.cyclic; pass++) {
-            const int rc = l * 3 + (pass && l == 0 && kind < 2 ? kind ^ 1 : kind);
+            const int rc = l * TB_NRES + (pass && l == 0 && kind < 2 ? kind ^ 1 : kind);
             const int a0 = acc_beg[rc];
             const int e0 = pass ? acc_beg[rc + 1] : acc_pos[rc * (P.nphase + 1) + p];
             for (int e = e0 - 1; e >= a0; e--) {
@@ -598,14 +610,40 @@ struct TB {
     // Access q (0 <= q < nq) of a task of phase ph on tile it: false when
     // the access falls off a non-periodic side or outside the finer level.
     // Sweeps: q = 0 reads the tile's source buffer, q = 1..5 write the
-    // destination buffer of the tile and its four neighbours (push), and a
-    // reconstructing tile reads both buffers and the flags of each coarse
-    // footprint tile (q = 6 + 3 k + r); closes: q = 0..7 read the two buffers
-    // of the four child tiles, q = 8, 9 write the tile's destination buffer
-    // and flags.
-    __device__ __forceinline__ bool query(const TBPhase& ph, const Item& it, const int* keys, int q, bool& write,
-                                          int& l, int& kind, int& tx, int& ty) const {
+    // destination buffer of the tile and its four neighbours (push), a
+    // reconstructing tile reads both buffers and the flags of each of its nk
+    // coarse footprint tiles (q = 6 + 3 k + r), and with the sensor the
+    // sweep reads its tile's first-pass planes (q = 6 + 3 nk) and the
+    // second-pass planes of the 3 x 3 tiles around it; closes: q = 0..7 read
+    // the two buffers of the four child tiles, q = 8, 9 write the tile's
+    // destination buffer and flags; the sensor's first pass reads the
+    // source buffer and writes its planes (q = 0, 1), its second pass reads
+    // the first-pass planes of the tile and its four neighbours and writes
+    // its own planes (q = 0..4, 5).
+    __device__ __forceinline__ bool query(const TBPhase& ph, const Item& it, const int* keys, int nk, int q,
+                                          bool& write, int& l, int& kind, int& tx, int& ty) const {
         l = ph.l;
+        if (ph.kind == 3 || ph.kind == 4 || (ph.kind == 0 && q >= 6 + 3 * nk)) {
+            const TBLevel& L = P.lev[l];
+            int dx = 0, dy = 0;
+            if (ph.kind == 3) {
+                write = q == 1;
+                kind = q == 0 ? src_of(l, ph.kk, ph.step) : 3;
+            } else if (ph.kind == 4) {
+                write = q == 5;
+                kind = q == 5 ? 4 : 3;
+                if (q < 5) dx = kSDI[q], dy = kSDJ[q];
+            } else {
+                const int j = q - (6 + 3 * nk);
+                write = false;
+                kind = j == 0 ? 3 : 4;
+                if (j > 0) dx = (j - 1) % 3 - 1, dy = (j - 1) / 3 - 1;
+            }
+            bool ok = true;
+            tx = wrap_or(it.tx + dx, L.bx, L.px, ok);
+            ty = wrap_or(it.ty + dy, L.by, L.py, ok);
+            return ok;
+        }
         if (ph.kind == 0) {
             const int bs = src_of(l, ph.kk, ph.step);
             if (q == 0) {
@@ -659,16 +697,27 @@ struct TB {
         const int l = ph.l;
         const TBLevel& L = P.lev[l];
         const int i = t - off[p];
-        it = ph.kind == 0 ? L.act[i] : L.ring[i];
+        it = ph.kind == 1 ? L.ring[i] : L.act[i];
         S.n = 0;
         S.ovf = false;
         int keys[16];
         const int nk = (ph.kind == 0 && l > 0 && L.recon[it.ty * L.bx + it.tx]) ? footprint(P.lev[l - 1], it.tx, it.ty, keys) : 0;
-        const int nq = ph.kind == 0 ? 6 + 3 * nk : 10;
+        const int nq = num_queries(ph, nk);
         for (int q = 0; q < nq; q++) {
             bool wr;
             int ql, qk, qx, qy;
-            if (query(ph, it, keys, q, wr, ql, qk, qx, qy)) deps_of(p, wr, ql, qk, qx, qy, [&](int d) { S.add(d); });
+            if (query(ph, it, keys, nk, q, wr, ql, qk, qx, qy)) deps_of(p, wr, ql, qk, qx, qy, [&](int d) { S.add(d); });
+        }
+    }
+
+    // accesses of a task of phase ph with nk footprint tiles
+    __device__ __forceinline__ int num_queries(const TBPhase& ph, int nk) const {
+        switch (ph.kind) {
+            case 0: return 6 + 3 * nk + (P.sensor ? 10 : 0);
+            case 1: return 10;
+            case 3: return 2;
+            case 4: return 6;
+            default: return 0;
         }
     }
 
@@ -704,7 +753,7 @@ __global__ void tb_offsets_kernel(TBPlan P) {
         P.off[p] = o;
         const TBPhase ph = P.ph[p];
         int c = 0;
-        if (ph.kind == 0) c = ph.l < P.nlev ? P.lev[ph.l].cnt[LST_ACT] : 0;
+        if (ph.kind == 0 || ph.kind >= 3) c = ph.l < P.nlev ? P.lev[ph.l].cnt[LST_ACT] : 0;
         else if (ph.kind == 1) c = ph.l + 1 < P.nlev ? P.lev[ph.l].cnt[LST_RING] : 0;
         else c = 4 * nblk;
         o += c;
@@ -776,7 +825,7 @@ __device__ __forceinline__ void tb_write(const TBPlan& P, const TB& tb, int p, i
     T.ty = it.ty;
     T.kind = (signed char)ph.kind;
     T.kk = (signed char)ph.kk;
-    T.kkp = (signed char)(ph.kind == 0 ? ph.kkp : 0);
+    T.kkp = (signed char)(ph.kind != 1 ? ph.kkp : 0);
     T.step = (signed char)ph.step;
     T.dep0 = (int)d0;
     T.ndep = S.n;
@@ -848,17 +897,17 @@ __global__ void __launch_bounds__(TBW_WARPS * 32) tb_warp_kernel(TBPlan P) {
                 const TBPhase ph = tb.ph[p];
                 const TBLevel& L = P.lev[ph.l];
                 const int i = t - tb.off[p];
-                const Item it = ph.kind == 0 ? L.act[i] : L.ring[i];
+                const Item it = ph.kind == 1 ? L.ring[i] : L.act[i];
                 int keys[16];
                 const int nk = (ph.kind == 0 && ph.l > 0 && L.recon[it.ty * L.bx + it.tx])
                                    ? footprint(P.lev[ph.l - 1], it.tx, it.ty, keys) : 0;
-                const int nq = ph.kind == 0 ? 6 + 3 * nk : 10;
+                const int nq = tb.num_queries(ph, nk);
                 int* R = raw[w][half];
                 int* cnt = &nraw[w][half];
                 for (int q = hl; q < nq; q += 16) {
                     bool wr;
                     int ql, qk, qx, qy;
-                    if (!tb.query(ph, it, keys, q, wr, ql, qk, qx, qy)) continue;
+                    if (!tb.query(ph, it, keys, nk, q, wr, ql, qk, qx, qy)) continue;
                     tb.deps_of(p, wr, ql, qk, qx, qy, [&](int d) {
                         const int at = atomicAdd(cnt, 1);
                         if (at < TBW_RAW) R[at] = d;
@@ -942,14 +991,14 @@ __global__ void __launch_bounds__(TBW_WARPS * 32) tb_warp_kernel(TBPlan P) {
                     const TBPhase ph = tb.ph[p];
                     const TBLevel& L = P.lev[ph.l];
                     const int i = t - tb.off[p];
-                    const Item it = ph.kind == 0 ? L.act[i] : L.ring[i];
+                    const Item it = ph.kind == 1 ? L.ring[i] : L.act[i];
                     Task T;
                     T.lid = ph.l;
                     T.tx = it.tx;
                     T.ty = it.ty;
                     T.kind = (signed char)ph.kind;
                     T.kk = (signed char)ph.kk;
-                    T.kkp = (signed char)(ph.kind == 0 ? ph.kkp : 0);
+                    T.kkp = (signed char)(ph.kind != 1 ? ph.kkp : 0);
                     T.step = (signed char)ph.step;
                     T.dep0 = (int)at;
                     T.ndep = nu;

@@ -96,11 +96,15 @@ cudaError_t launch_count_lups(const LayoutDev* levs, int n, long long steps, uns
 
 // access patterns of the task builder: which tasks of a phase touch a tile
 // of a resource (the same patterns as vlbm_tasks.h)
-enum : int { TB_OWN = 0, TB_STENCIL = 1, TB_FOOT = 2, TB_CHILD4 = 3, TB_OWNRING = 4 };
+// (TB_BOX9: the 3 x 3 tiles around each task's tile, the relaxation
+// sensor's filters)
+enum : int { TB_OWN = 0, TB_STENCIL = 1, TB_FOOT = 2, TB_CHILD4 = 3, TB_OWNRING = 4, TB_BOX9 = 5 };
 
 // kind 0: sweeps of level l (sub-step kk of the parent's sub-step kkp; first:
 // the level's first sweep of the step), 1: closes of level l, 2: the audit
-// phase of a cyclic list (reduction tasks, see TBPlan::audit)
+// phase of a cyclic list (reduction tasks, see TBPlan::audit), 3 and 4: the
+// relaxation sensor's two passes before each sweep phase (W, Q, u, v; then
+// s and theta), on the sweep's tiles
 struct TBPhase {
     int kind, l, kk, kkp, step, first;
 };
@@ -119,7 +123,10 @@ struct TBLevel {
     const int* fidx;
     const int* cnt;  // [NLST]
 };
-constexpr int TASK_RC = 4 * 3;  // resource classes: (level, buffer 0 / buffer 1 / flags)
+// resources of a level: buffer 0, buffer 1, flags, the sensor's first-pass
+// planes, its second-pass planes
+constexpr int TB_NRES = 5;
+constexpr int TASK_RC = 4 * TB_NRES;  // resource classes (level, resource)
 // dependencies of task t at deps[t * TASK_DEP_SLOT ..] when they fit, else
 // in the overflow area after task_cap * TASK_DEP_SLOT entries
 constexpr int TASK_DEP_SLOT = 32;
@@ -138,9 +145,9 @@ struct TBPlan {
     int cyclic = 0;
     TBLevel lev[4] = {};
     const TBPhase* ph = nullptr;       // [nphase]
-    const TBAcc* acc = nullptr;        // per resource class (l * 3 + kind), in phase order
-    const int* acc_beg = nullptr;      // [4 * 3 + 1]
-    const int* acc_pos = nullptr;      // [(l * 3 + kind) * (nphase + 1) + p]: first entry at or after phase p
+    const TBAcc* acc = nullptr;        // per resource class (l * TB_NRES + kind), in phase order
+    const int* acc_beg = nullptr;      // [TASK_RC + 1]
+    const int* acc_pos = nullptr;      // [(l * TB_NRES + kind) * (nphase + 1) + p]: first entry at or after phase p
     int* off = nullptr;                // [nphase + 1] task offsets of the phases (computed)
     Task* tasks = nullptr;             // [task_cap]
     int* deps = nullptr;               // [dep_cap]: fixed slots, then the overflow area
@@ -157,6 +164,10 @@ struct TBPlan {
     // sweeps of its block's slots.  The kernel does this work only in the
     // first iteration of a launch whose CTL_AUDIT word is set.
     int audit = 0;
+    // the relaxation sensor's passes are in the list: the sweeps also read
+    // their tile's first-pass planes and the second-pass planes of the 3 x 3
+    // tiles around it
+    int sensor = 0;
     int pfirst[4] = {-1, -1, -1, -1};  // the first-sweep phase of each level
     int* ascale = nullptr;             // [slots] weight exponent of the slot's level (-2 l)
     int2* arng = nullptr;              // [blocks] slot range of each block

@@ -395,6 +395,7 @@ struct vlbm_hier {
         // audited cyclic list (regrid audits on): the totals after a regrid
         // come from the next launch's first sweeps (see TBPlan::audit)
         bool audit = false;
+        bool sensor = false;  // the relaxation sensor's passes are tasks of the list
         int pfirst[4] = {-1, -1, -1, -1};
         DArr<double> aw;
         DArr<int> ascale;
@@ -1624,30 +1625,45 @@ void device_regrid(vlbm_hier* h) {
 // recursion as phases() in vlbm_tasks.h, then the audit phase of a cyclic
 // list) and the accesses of its phases per resource class (level, buffer
 // 0 / 1 / flags), in phase order.
-void plan_tables(int nlev, int nsteps, bool audit_phase, std::vector<TBPhase>& ph, std::vector<TBAcc>& acc,
-                 std::vector<int>& beg, std::vector<int>& pos) {
+void plan_tables(int nlev, int nsteps, bool audit_phase, bool sensor, std::vector<TBPhase>& ph,
+                 std::vector<TBAcc>& acc, std::vector<int>& beg, std::vector<int>& pos) {
     ph.clear();
     struct Rec {
-        static void run(std::vector<TBPhase>& ph, int l, int kk, int kkp, int step, bool first) {
+        static void run(std::vector<TBPhase>& ph, bool sensor, int l, int kk, int kkp, int step, bool first) {
+            if (sensor) {  // the relaxation sensor's two passes over the level's state
+                ph.push_back(TBPhase{3, l, kk, kkp, step, 0});
+                ph.push_back(TBPhase{4, l, kk, kkp, step, 0});
+            }
             ph.push_back(TBPhase{0, l, kk, kkp, step, first ? 1 : 0});
             if (l + 1 < TASK_MAX_LEVELS) {
-                run(ph, l + 1, 1, kk, step, first);
-                run(ph, l + 1, 2, kk, step, false);
+                run(ph, sensor, l + 1, 1, kk, step, first);
+                run(ph, sensor, l + 1, 2, kk, step, false);
                 ph.push_back(TBPhase{1, l, kk, 0, step, 0});
             }
         }
     };
-    for (int st = 0; st < nsteps; st++) Rec::run(ph, 0, 0, 0, st, true);
+    for (int st = 0; st < nsteps; st++) Rec::run(ph, sensor, 0, 0, 0, st, true);
     // the audit phase (reductions of the first sweeps' moments) touches no
     // buffer: it orders nothing but its own tasks after their sweeps
     if (audit_phase) ph.push_back(TBPhase{2, 0, 0, 0, 0, 0});
     auto src_of = [](int level, int kk, int step) { return level == 0 ? (step & 1) : (kk == 1 ? 0 : 1); };
-    std::vector<TBAcc> per[TASK_MAX_LEVELS][3];
+    // resources per level: buffer 0, buffer 1, flags, the sensor's
+    // first-pass planes (3), its second-pass planes (4)
+    std::vector<TBAcc> per[TASK_MAX_LEVELS][TB_NRES];
     for (int p = 0; p < (int)ph.size(); p++) {
         const TBPhase& P = ph[p];
         const int l = P.l;
         if (P.kind == 2) continue;
-        if (P.kind == 0) {
+        if (P.kind >= 3) {
+            if (l >= nlev) continue;
+            if (P.kind == 3) {
+                per[l][src_of(l, P.kk, P.step)].push_back({p, 0, TB_OWN});
+                per[l][3].push_back({p, 1, TB_OWN});
+            } else {
+                per[l][3].push_back({p, 0, TB_STENCIL});
+                per[l][4].push_back({p, 1, TB_OWN});
+            }
+        } else if (P.kind == 0) {
             if (l >= nlev) continue;
             const int bs = src_of(l, P.kk, P.step);
             per[l][bs].push_back({p, 0, TB_OWN});
@@ -1657,6 +1673,10 @@ void plan_tables(int nlev, int nsteps, bool audit_phase, std::vector<TBPhase>& p
                 per[l - 1][pbs].push_back({p, 0, TB_FOOT});
                 per[l - 1][pbs ^ 1].push_back({p, 0, TB_FOOT});
                 per[l - 1][2].push_back({p, 0, TB_FOOT});
+            }
+            if (sensor) {
+                per[l][3].push_back({p, 0, TB_OWN});
+                per[l][4].push_back({p, 0, TB_BOX9});
             }
         } else {
             if (l + 1 >= nlev) continue;
@@ -1669,10 +1689,10 @@ void plan_tables(int nlev, int nsteps, bool audit_phase, std::vector<TBPhase>& p
     }
     const int np = (int)ph.size();
     acc.clear();
-    beg.assign(TASK_MAX_LEVELS * 3 + 1, 0);
-    pos.assign((size_t)TASK_MAX_LEVELS * 3 * (np + 1), 0);
-    for (int rc = 0; rc < TASK_MAX_LEVELS * 3; rc++) {
-        const std::vector<TBAcc>& A = per[rc / 3][rc % 3];
+    beg.assign(TASK_RC + 1, 0);
+    pos.assign((size_t)TASK_RC * (np + 1), 0);
+    for (int rc = 0; rc < TASK_RC; rc++) {
+        const std::vector<TBAcc>& A = per[rc / TB_NRES][rc % TB_NRES];
         beg[rc] = (int)acc.size();
         int e = 0;
         for (int p = 0; p <= np; p++) {
@@ -1681,7 +1701,7 @@ void plan_tables(int nlev, int nsteps, bool audit_phase, std::vector<TBPhase>& p
         }
         acc.insert(acc.end(), A.begin(), A.end());
     }
-    beg[TASK_MAX_LEVELS * 3] = (int)acc.size();
+    beg[TASK_RC] = (int)acc.size();
 }
 
 // The task list on the current layout, built on the device when the layout
@@ -1694,22 +1714,23 @@ vlbm_hier::DevPlan& dev_plan(vlbm_hier* h, int k, bool cyclic) {
     // regrid audits of a hierarchy on its own: the totals after each regrid
     // come from the next launch (the engine audits separately)
     const bool audit = cyclic && h->regrid_audit && !h->engine;
+    const bool sensor = cyclic && h->sensor_on;
     D.build_kernels = 0;
     cudaStream_t s = h->stream;
     bool plan_fresh_ok = true;  // no upload queued on the main stream since the layout event
-    if (D.steps != k || D.audit != audit) {
+    if (D.steps != k || D.audit != audit || D.sensor != sensor) {
         plan_fresh_ok = false;
         std::vector<TBPhase> ph;
         std::vector<TBAcc> acc;
         std::vector<int> beg, pos;
-        plan_tables(h->nlev, k, cyclic, ph, acc, beg, pos);
+        plan_tables(h->nlev, k, cyclic, sensor, ph, acc, beg, pos);
         long long cap = 0, slot_cap = 0;
         for (int l = 0; l < h->nlev; l++) slot_cap += (long long)h->lev[l].bx * h->lev[l].by;
         const long long blk_cap = (slot_cap + TB_AUDIT_BLOCK - 1) / TB_AUDIT_BLOCK;
         for (int l = 0; l < 4; l++) D.pfirst[l] = -1;
         for (int p = 0; p < (int)ph.size(); p++) {
             const TBPhase& P = ph[p];
-            if (P.kind == 0 && P.l < h->nlev) cap += (long long)h->lev[P.l].bx * h->lev[P.l].by;
+            if ((P.kind == 0 || P.kind >= 3) && P.l < h->nlev) cap += (long long)h->lev[P.l].bx * h->lev[P.l].by;
             if (P.kind == 1 && P.l + 1 < h->nlev) cap += (long long)h->lev[P.l].bx * h->lev[P.l].by;
             if (P.kind == 2 && audit) cap += 4 * blk_cap;
             if (P.kind == 0 && P.first && P.l < 4 && D.pfirst[P.l] < 0) D.pfirst[P.l] = p;
@@ -1726,6 +1747,7 @@ vlbm_hier::DevPlan& dev_plan(vlbm_hier* h, int k, bool cyclic) {
             D.apart.release(h->mem);
         }
         D.audit = audit;
+        D.sensor = sensor;
         // a cyclic list's tickets (tasks x iterations, up to 64) are ints too
         if (cap >= ((1LL << 31) - 1) / (cyclic ? 64 : 1)) throw Fail{VLBM_ERR_ARG, "hierarchy too large for one task list"};
         if (acc.empty()) acc.push_back(TBAcc{0, 0, 0});
@@ -1833,6 +1855,7 @@ vlbm_hier::DevPlan& dev_plan(vlbm_hier* h, int k, bool cyclic) {
         P.prefix = D.prefix.p;
         P.ctl = D.ctl.p;
         P.audit = D.audit ? 1 : 0;
+        P.sensor = D.sensor ? 1 : 0;
         for (int l = 0; l < 4; l++) P.pfirst[l] = D.pfirst[l];
         P.ascale = D.ascale.p;
         P.arng = D.arng.p;
@@ -1856,7 +1879,7 @@ cudaGraphExec_t dev_task_graph(vlbm_hier* h, int which, int iters) {
     cudaStream_t s = h->stream;
     std::vector<uintptr_t> key = {(uintptr_t)h->atab.p,   (uintptr_t)D.seg.p,          (uintptr_t)D.prefix.p,
                                   (uintptr_t)D.chunks.p, (uintptr_t)D.ctl.p,          (uintptr_t)h->tune.variant,
-                                  (uintptr_t)h->tune.max_ctas, (uintptr_t)iters};
+                                  (uintptr_t)h->tune.max_ctas, (uintptr_t)iters,     (uintptr_t)D.sensor};
     cudaGraphExec_t& ex = D.exec[which];
     if (!ex || key != D.key[which]) {
         const auto t0 = std::chrono::steady_clock::now();
@@ -1867,7 +1890,7 @@ cudaGraphExec_t dev_task_graph(vlbm_hier* h, int which, int iters) {
         cudaError_t e = cudaMemsetAsync(D.ctl.p, 0, 2 * sizeof(int), s);  // claim and finish counters
         if (e == cudaSuccess)
             e = launch_tasks(h->atab.p, D.seg.p, D.prefix.p, D.chunks.p, D.ctl.p, h->tune.variant, h->tune.max_ctas,
-                             iters, s);
+                             iters, s, D.sensor);
         cudaError_t e2 = cudaStreamEndCapture(s, &g);
         if (e == cudaSuccess) e = e2;
         if (e == cudaSuccess) e = instantiate(&ex, g);
@@ -2247,7 +2270,6 @@ int effective_schedule(const vlbm_hier* h) {
 // saves in one coarse step (regridding every 4 steps: 5650 MLUPS
 // persistent, 5104 per phase), hence the default of 2.
 int dev_schedule_mode(const vlbm_hier* h) {
-    if (h->sensor_on) return 0;
     if (h->tune.schedule != 2) return h->tune.schedule;
     return h->layout_steps >= h->tune.persist_after ? 1 : 0;
 }

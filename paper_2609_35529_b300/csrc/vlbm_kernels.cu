@@ -57,7 +57,7 @@ __device__ __forceinline__ bool physical(double rho, double p) {
 // persistent task kernel runs half tiles per warp (task_kernel_half).
 enum : int { TK_HALF = 512 };
 // The sweep reads the relaxation parameter of each cell from the sensor
-// planes (sensor-driven relaxation; per-phase schedule only).
+// planes (sensor-driven relaxation).
 enum : int { SW_SENSOR = 1024 };
 
 // BGK relaxation (Eq. 6) in place: f <- 2 beta f^eq(W) + (1 - 2 beta) f with
@@ -167,8 +167,66 @@ __device__ __forceinline__ long long sens_nb(const LevelDev& L, int x, int y, in
     return (L.flags[cn] & (F_IN | F_COV)) == F_IN ? cn : c;
 }
 
-// Pass 1: W, Q, u, v of every active cell from the level step's source
-// buffer (the sweep relaxes with these W and Q), and the state's check.
+// Pass 1 on cell (x, y): W, Q, u, v from the level step's source buffer
+// (the sweep relaxes with these W and Q), and the state's check.  COH:
+// loads through L2 (data written earlier in the same launch).
+template <bool COH>
+__device__ __forceinline__ void sensor_prep_cell(const LevelDev& L, int x, int y, int kk, int step) {
+    if (x >= L.nx || y >= L.ny) return;
+    const long long c = (long long)y * L.pitch + x;
+    if ((L.flags[c] & (F_IN | F_COV)) != F_IN) return;
+    const double* src;
+    double* dst;
+    level_bufs(L, kk, step, src, dst);
+    const long long P = L.plane;
+    double W[4], Qx[4], Qy[4], p;
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+        W[k] = (ld<COH>(src + qoff(0 + k, P, c)) + ld<COH>(src + qoff(4 + k, P, c))) +
+               (ld<COH>(src + qoff(8 + k, P, c)) + ld<COH>(src + qoff(12 + k, P, c)));
+    euler_flux(L.gm1, W, Qx, Qy, p);
+    const double inv = rcp_rn(W[0]);  // = 1.0 / W[0]
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        L.sens[k * P + c] = Qx[k];
+        L.sens[(4 + k) * P + c] = Qy[k];
+        L.sens[(12 + k) * P + c] = W[k];
+    }
+    L.sens[8 * P + c] = W[1] * inv;
+    L.sens[9 * P + c] = W[2] * inv;
+    // the sweep takes W and Q from here: the state's check is made here
+    if (!physical(W[0], p)) atomicOr(L.status, ST_NONPHYS);
+}
+
+// Pass 2 on cell (x, y): s and theta.
+template <bool COH>
+__device__ __forceinline__ void sensor_rate_cell(const LevelDev& L, int x, int y) {
+    if (x >= L.nx || y >= L.ny) return;
+    const long long c = (long long)y * L.pitch + x;
+    if ((L.flags[c] & (F_IN | F_COV)) != F_IN) return;
+    const long long e = sens_nb(L, x, y, 1, 0, c), ww = sens_nb(L, x, y, -1, 0, c);
+    const long long n = sens_nb(L, x, y, 0, 1, c), so = sens_nb(L, x, y, 0, -1, c);
+    const double* S = L.sens;
+    const long long P = L.plane;
+    double sh[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const double g = (ld<COH>(S + k * P + e) - ld<COH>(S + k * P + ww)) +
+                         (ld<COH>(S + (4 + k) * P + n) - ld<COH>(S + (4 + k) * P + so));
+        sh[k] = g * L.iq[k];
+    }
+    // fields paired (rho, rho E), (rho u, rho v): invariant under x <-> y
+    L.sens[10 * P + c] = sqrt(0.25 * ((sh[0] * sh[0] + sh[3] * sh[3]) + (sh[1] * sh[1] + sh[2] * sh[2])));
+    const double ue = ld<COH>(S + 8 * P + e), uw = ld<COH>(S + 8 * P + ww);
+    const double un = ld<COH>(S + 8 * P + n), us = ld<COH>(S + 8 * P + so);
+    const double ve = ld<COH>(S + 9 * P + e), vw = ld<COH>(S + 9 * P + ww);
+    const double vn = ld<COH>(S + 9 * P + n), vs = ld<COH>(S + 9 * P + so);
+    const double dil = (ue - uw) + (vn - vs);
+    const double vort = (ve - vw) - (un - us);
+    const double d2 = dil * dil;
+    L.sens[11 * P + c] = dil < 0.0 ? div_rn(d2, (d2 + vort * vort) + L.eps) : 0.0;
+}
+
 __global__ void sensor_prep_kernel(const LevelDev* __restrict__ levs, const Item* __restrict__ items, int nitems,
                                    int kk, const int* __restrict__ ncount) {
     if (ncount) nitems = *ncount;
@@ -176,33 +234,10 @@ __global__ void sensor_prep_kernel(const LevelDev* __restrict__ levs, const Item
     for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
         const Item w = items[it];
         const LevelDev& L = levs[w.lid];
-        if (!L.sens) continue;
-        const int x = w.tx * TILE + cx, y = w.ty * TILE + cy;
-        if (x >= L.nx || y >= L.ny) continue;
-        const long long c = (long long)y * L.pitch + x;
-        if ((L.flags[c] & (F_IN | F_COV)) != F_IN) continue;
-        const double* src;
-        double* dst;
-        level_bufs(L, kk, 0, src, dst);
-        double W[4], Qx[4], Qy[4], p;
-        for (int k = 0; k < 4; k++)
-            W[k] = (src[qoff(0 + k, L.plane, c)] + src[qoff(4 + k, L.plane, c)]) +
-                   (src[qoff(8 + k, L.plane, c)] + src[qoff(12 + k, L.plane, c)]);
-        euler_flux(L.gm1, W, Qx, Qy, p);
-        const double inv = rcp_rn(W[0]);  // = 1.0 / W[0]
-        for (int k = 0; k < 4; k++) {
-            L.sens[k * L.plane + c] = Qx[k];
-            L.sens[(4 + k) * L.plane + c] = Qy[k];
-            L.sens[(12 + k) * L.plane + c] = W[k];
-        }
-        L.sens[8 * L.plane + c] = W[1] * inv;
-        L.sens[9 * L.plane + c] = W[2] * inv;
-        // the sweep takes W and Q from here: the state's check is made here
-        if (!physical(W[0], p)) atomicOr(L.status, ST_NONPHYS);
+        if (L.sens) sensor_prep_cell<false>(L, w.tx * TILE + cx, w.ty * TILE + cy, kk, 0);
     }
 }
 
-// Pass 2: s and theta of every active cell.
 __global__ void sensor_rate_kernel(const LevelDev* __restrict__ levs, const Item* __restrict__ items, int nitems,
                                    const int* __restrict__ ncount) {
     if (ncount) nitems = *ncount;
@@ -210,30 +245,12 @@ __global__ void sensor_rate_kernel(const LevelDev* __restrict__ levs, const Item
     for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
         const Item w = items[it];
         const LevelDev& L = levs[w.lid];
-        if (!L.sens) continue;
-        const int x = w.tx * TILE + cx, y = w.ty * TILE + cy;
-        if (x >= L.nx || y >= L.ny) continue;
-        const long long c = (long long)y * L.pitch + x;
-        if ((L.flags[c] & (F_IN | F_COV)) != F_IN) continue;
-        const long long e = sens_nb(L, x, y, 1, 0, c), ww = sens_nb(L, x, y, -1, 0, c);
-        const long long n = sens_nb(L, x, y, 0, 1, c), so = sens_nb(L, x, y, 0, -1, c);
-        const double* S = L.sens;
-        const long long P = L.plane;
-        double sh[4];
-        for (int k = 0; k < 4; k++) {
-            const double g = (S[k * P + e] - S[k * P + ww]) + (S[(4 + k) * P + n] - S[(4 + k) * P + so]);
-            sh[k] = g * L.iq[k];
-        }
-        // fields paired (rho, rho E), (rho u, rho v): invariant under x <-> y
-        L.sens[10 * P + c] = sqrt(0.25 * ((sh[0] * sh[0] + sh[3] * sh[3]) + (sh[1] * sh[1] + sh[2] * sh[2])));
-        const double dil = (S[8 * P + e] - S[8 * P + ww]) + (S[9 * P + n] - S[9 * P + so]);
-        const double vort = (S[9 * P + e] - S[9 * P + ww]) - (S[8 * P + n] - S[8 * P + so]);
-        const double d2 = dil * dil;
-        L.sens[11 * P + c] = dil < 0.0 ? div_rn(d2, (d2 + vort * vort) + L.eps) : 0.0;
+        if (L.sens) sensor_rate_cell<false>(L, w.tx * TILE + cx, w.ty * TILE + cy);
     }
 }
 
 // The relaxation parameter of active cell (x, y) from the 3 x 3 filters.
+template <bool COH>
 __device__ double sensor_beta_at(const LevelDev& L, int x, int y) {
     const long long c = (long long)y * L.pitch + x;
     const double* Ss = L.sens + 10 * L.plane;
@@ -244,8 +261,10 @@ __device__ double sensor_beta_at(const LevelDev& L, int x, int y) {
     const long long n = sens_nb(L, x, y, 0, 1, c), so = sens_nb(L, x, y, 0, -1, c);
     const long long ne = sens_nb(L, x, y, 1, 1, c), sw = sens_nb(L, x, y, -1, -1, c);
     const long long nw = sens_nb(L, x, y, -1, 1, c), se = sens_nb(L, x, y, 1, -1, c);
-    const double as = (Ss[c] + ((Ss[e] + Ss[w]) + (Ss[n] + Ss[so]))) + ((Ss[ne] + Ss[sw]) + (Ss[nw] + Ss[se]));
-    const double at = (St[c] + ((St[e] + St[w]) + (St[n] + St[so]))) + ((St[ne] + St[sw]) + (St[nw] + St[se]));
+    auto S = [&](long long i) { return ld<COH>(Ss + i); };
+    auto T = [&](long long i) { return ld<COH>(St + i); };
+    const double as = (S(c) + ((S(e) + S(w)) + (S(n) + S(so)))) + ((S(ne) + S(sw)) + (S(nw) + S(se)));
+    const double at = (T(c) + ((T(e) + T(w)) + (T(n) + T(so)))) + ((T(ne) + T(sw)) + (T(nw) + T(se)));
     double z = (L.csens * (L.ninth * as)) * (L.ninth * at);
     if (z < 0.0) z = 0.0;
     if (z > 1.0) z = 1.0;
@@ -367,7 +386,7 @@ __device__ __forceinline__ void sweep_cell(const LevelDev* __restrict__ levs, co
         if (L.sens) {
             // the moments and fluxes of the sensor's first pass (the same
             // populations, the same expressions) and the cell's own beta
-            const double b = sensor_beta_at(L, x, y);
+            const double b = sensor_beta_at<COH>(L, x, y);
             double W[4], Qx[4], Qy[4];
 #pragma unroll
             for (int k = 0; k < 4; k++) {
@@ -764,8 +783,12 @@ task_kernel(const LevelDev* __restrict__ levs, const Segment* __restrict__ segs,
             }
         } else if (T.kind == 1) {
             close_cell<true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, step);
-        } else if (aud) {
-            audit_task(S, T, g, lt);
+        } else if (T.kind == 2) {
+            if (aud) audit_task(S, T, g, lt);
+        } else if constexpr ((P & SW_SENSOR) != 0) {
+            // the relaxation sensor's passes of the level step (kinds 3, 4)
+            if (T.kind == 3) sensor_prep_cell<true>(L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, step);
+            else sensor_rate_cell<true>(L, T.tx * TILE + cx, T.ty * TILE + cy);
         }
         group_bar(g);
         if (lt == 0) {
@@ -828,8 +851,11 @@ task_kernel_half(const LevelDev* __restrict__ levs, const Segment* __restrict__ 
             }
         } else if (T.kind == 1) {
             close_cell<true>(levs, L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, step);
-        } else if (aud && half == 0) {  // the first half does the whole audit task
-            audit_task_warp(S, T, lane);
+        } else if (T.kind == 2) {
+            if (aud && half == 0) audit_task_warp(S, T, lane);  // the first half does the whole audit task
+        } else if constexpr ((P & SW_SENSOR) != 0) {
+            if (T.kind == 3) sensor_prep_cell<true>(L, T.tx * TILE + cx, T.ty * TILE + cy, T.kk, step);
+            else sensor_rate_cell<true>(L, T.tx * TILE + cx, T.ty * TILE + cy);
         }
         __syncwarp();
         if (lane == 0) {
@@ -1562,8 +1588,33 @@ int task_kernel_ctas(int variant) {
 }
 
 cudaError_t launch_tasks(const LevelDev* levs, const Segment* segs, const int* prefix, const int2* chunks, int* ctl,
-                         int variant, int ctas, int iters, cudaStream_t s) {
+                         int variant, int ctas, int iters, cudaStream_t s, bool sensor) {
     if (iters < 1) return cudaErrorInvalidValue;
+    if (sensor) {
+        // lists with the relaxation sensor's passes: the variant's launch
+        // shape, in the kernel form that runs them
+        static int full_s[16] = {0};
+        if (variant < 0 || variant >= 16) return cudaErrorInvalidValue;
+        if (!full_s[variant]) {
+            int dev = 0, sms = 0, per = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            switch (variant) {
+#define X(id, P, B) case id: per = task_variant_per_sm<(P) | SW_SENSOR, B>(); break;
+                VLBM_SWEEP_VARIANTS(X)
+#undef X
+                default: return cudaErrorInvalidValue;
+            }
+            full_s[variant] = sms * std::max(1, per);
+        }
+        const int gs = ctas > 0 ? std::min(ctas, full_s[variant]) : full_s[variant];
+        switch (variant) {
+#define X(id, P, B) case id: task_variant_launch<(P) | SW_SENSOR, B>(gs, levs, segs, prefix, chunks, ctl, iters, s); break;
+            VLBM_SWEEP_VARIANTS(X)
+#undef X
+        }
+        return cudaGetLastError();
+    }
     const int full = task_kernel_ctas(variant);  // also sets the kernel's shared-memory attributes
     const int g = ctas > 0 ? std::min(ctas, full) : full;
     switch (variant) {

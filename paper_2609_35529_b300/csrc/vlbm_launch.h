@@ -20,8 +20,11 @@ int task_kernel_ctas(int variant);
 // Within an iteration, ticket t lies in chunk c (prefix[c] <= t <
 // prefix[c + 1]) and is task chunks[c].y + t - prefix[c] of segment
 // chunks[c].x; every segment's tasks appear in its own list order.
+// sensor: the lists hold the relaxation sensor's passes (task kinds 3, 4)
+// and the sweeps take each cell's beta from them (the variant's launch
+// shape, in the kernel form that runs them).
 cudaError_t launch_tasks(const LevelDev* levs, const Segment* segs, const int* prefix, const int2* chunks, int* ctl,
-                         int variant, int ctas, int iters, cudaStream_t s);
+                         int variant, int ctas, int iters, cudaStream_t s, bool sensor = false);
 cudaError_t launch_audit_segments(const unsigned long long* slots, const int* seg, int nseg, double* out,
                                   cudaStream_t s);
 // Totals of an audited persistent launch from its reduction blocks' exact

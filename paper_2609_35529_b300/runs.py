@@ -26,6 +26,7 @@ import time
 
 import numpy as np
 
+from . import autotune
 from . import inputs as I
 from . import vlbm as V
 
@@ -159,8 +160,14 @@ def run_riemann_sensor(N=1024, nlev=3, beta_max_permille=1000, c_sensor=64):
     problem; the sensor lowers beta only at compressions."""
     bmax = beta_max_permille / 1000.0
     cs = I.riemann3(N=N, nlev=nlev, beta=bmax)
-    h = V.Hierarchy.from_case(cs)
-    h.set_sensor(True, beta_min=0.5, c_sensor=float(c_sensor))
+
+    def make():
+        g = V.Hierarchy.from_case(cs)
+        g.set_sensor(True, beta_min=0.5, c_sensor=float(c_sensor))
+        return g
+
+    h = make()
+    best, _ = autotune.tune(make, target=h, steps=32, candidates=autotune.SENSOR_CANDIDATES)
     lups = h.info()["lups_per_step"]
     h.advance(4)
     h.sync()
@@ -186,7 +193,7 @@ def run_riemann_sensor(N=1024, nlev=3, beta_max_permille=1000, c_sensor=64):
         act_l = (a == 1) & (b == 0)
         ft = f.transpose(0, 1, 3, 2)[[2, 3, 0, 1]][:, [0, 2, 1, 3]]
         sym = sym and bool(np.array_equal(f[:, :, act_l], ft[:, :, act_l]))
-    emit({"run": "riemann3-sensor", "N": N, "levels": nlev, "steps": cs.steps, "lups_per_step": lups,
+    emit({"run": "riemann3-sensor", "N": N, "levels": nlev, "steps": cs.steps, "lups_per_step": lups, "tuning": best,
           "wall_s": el, "mlups": lups * (cs.steps - 4) / el / 1e6, "transpose_symmetric_bitwise": sym,
           "rho_min": float(W[0][act].min()), "rho_max": float(W[0][act].max()), "p_min": float(p[act].min()),
           "beta": [0.5, bmax], "c_sensor": c_sensor, "physical_to_end": True})

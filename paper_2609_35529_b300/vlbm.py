@@ -358,6 +358,7 @@ class Hierarchy:
         """Sensor-driven relaxation (vlbm_set_sensor): beta_max is the
         hierarchy's beta; the flux maxima are fixed from the current state."""
         _check(self._h, lib().vlbm_set_sensor(self._h, int(on), beta_min, c_sensor, eps))
+        self.sensor_on = bool(on)
 
     HOST_TIMERS = ("tag", "layout", "regrid", "build", "tasks", "capture", "regrids", "task_lists")
 

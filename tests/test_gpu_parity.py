@@ -582,14 +582,16 @@ def test_bounded_wait_gives_up_and_context_survives(V):
     compare(o, g, cs.nlev)
 
 
-@pytest.mark.parametrize("which", ["smooth3", "laxliu3", "laxliu3_128"])
-def test_sensor_driven_relaxation_matches_oracle(V, which):
+@pytest.mark.parametrize("which,schedule,variant", [("smooth3", 1, 1), ("smooth3", 1, 2), ("smooth3", 1, 3),
+                                                    ("smooth3", 0, 1), ("laxliu3", 1, 2), ("laxliu3", 0, 1),
+                                                    ("laxliu3_128", 1, 2)])
+def test_sensor_driven_relaxation_matches_oracle(V, which, schedule, variant):
     """The sensor-driven relaxation (Sec. 2.2, Eq. sensor-B; per-cell beta
     from the flux-jump rate and the Ducros gate, two sensor passes before
-    every level sweep) reproduces the oracle bit for bit: a three-level
-    ragged periodic field with the sensor acting, and Lax-Liu 3 on three
-    levels with outflow boundaries (where the sensor keeps the run
-    physical)."""
+    every level sweep: separate launches, or tasks of the persistent launch)
+    reproduces the oracle bit for bit: a three-level ragged periodic field
+    with the sensor acting, and Lax-Liu 3 on three levels with outflow
+    boundaries (where the sensor keeps the run physical)."""
     if which == "smooth3":
         nx0, ny0 = 44, 36
         refs = I.box_refs(nx0, ny0, 3, [(0, 8, 8, 16, 16)])
@@ -604,6 +606,7 @@ def test_sensor_driven_relaxation_matches_oracle(V, which):
         cs = I.riemann3(N=128, nlev=3, beta=1.0)
         kw = dict(beta_min=0.5, c_sensor=64.0)
     g = V.Hierarchy.from_case(cs)
+    g.set_tuning(variant=variant, schedule=schedule, graph_steps=4)
     o = oracle_of(cs)
     g.set_sensor(True, **kw)
     o.set_sensor(True, **kw)

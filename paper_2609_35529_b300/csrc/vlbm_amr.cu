@@ -1036,24 +1036,30 @@ __global__ void __launch_bounds__(TB_BUILD_THREADS) tb_big_kernel(TBPlan P) {
     }
 }
 
+// The launch's counts: the list's tasks up to the audit phase (run once per
+// iteration) and the audit phase's reduction tasks after them (run once, by
+// an audited launch).
 __global__ void tb_finish_kernel(TBPlan P) {
     if (threadIdx.x || blockIdx.x) return;
-    int total = P.off[P.nphase];
-    if (P.need[3] != 0 || total > P.task_cap) {
+    const bool ap = P.nphase > 0 && P.ph[P.nphase - 1].kind == 2;
+    int total = ap ? P.off[P.nphase - 1] : P.off[P.nphase];
+    int naud = P.off[P.nphase] - total;
+    if (P.need[3] != 0 || P.off[P.nphase] > P.task_cap) {
         atomicOr(P.status, ST_TASKCAP);
-        total = 0;
+        total = naud = 0;
     }
     P.seg->ntasks = total;
     P.prefix[0] = 0;
     P.prefix[1] = total;
     P.ctl[CTL_TOTAL] = total;
+    P.ctl[CTL_NAUD] = naud;
 }
 
 // The chunk table of a persistent launch over several one-step task lists
 // (segments), phase-major: for each phase p, for each segment m, the run of
 // m's tasks of phase p (`offs[m][p] .. offs[m][p + 1]`).  A segment whose
-// build failed (its own task count, mctl[m][CTL_TOTAL], is not its phase
-// total) contributes nothing.  One CTA; entries p * nm + m in rounds of the
+// build failed (its own task counts, mctl[m][CTL_TOTAL] + mctl[m][CTL_NAUD],
+// are not its phase total) contributes nothing.  One CTA; entries p * nm + m in rounds of the
 // CTA's threads, two scans per round (tickets and non-empty chunks).
 __global__ void merge_chunks_kernel(const int* const* __restrict__ offs, const int* const* __restrict__ mctl, int nm,
                                     int nphase, int* __restrict__ prefix, int2* __restrict__ chunks, int* ctl) {
@@ -1069,7 +1075,7 @@ __global__ void merge_chunks_kernel(const int* const* __restrict__ offs, const i
             const int p = e / nm;
             m = e - p * nm;
             const int* o = offs[m];
-            if (mctl[m][CTL_TOTAL] == o[nphase]) {
+            if (mctl[m][CTL_TOTAL] + mctl[m][CTL_NAUD] == o[nphase]) {
                 a = o[p];
                 cnt = o[p + 1] - a;
             }

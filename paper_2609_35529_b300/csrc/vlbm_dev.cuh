@@ -142,11 +142,13 @@ enum : int {
     CTL_NSEG = 4,
     CTL_FLIP = 5,
     CTL_NCHUNK = 6,
-    // nonzero: the launch's first iteration is audited (its first sweep of
-    // each level keeps the moments, its reduction tasks add them up); zero:
-    // audited sweeps and reduction tasks do nothing
+    // nonzero: the launch's first iteration is audited -- its first sweep
+    // of each level keeps the moments, and the CTL_NAUD reduction tasks
+    // stored after the list's CTL_TOTAL tasks add them up, once, after the
+    // last iteration's tickets; zero: neither
     CTL_AUDIT = 7,
-    CTL_WORDS = 8
+    CTL_NAUD = 8,
+    CTL_WORDS = 16
 };
 
 }  // namespace vlbm

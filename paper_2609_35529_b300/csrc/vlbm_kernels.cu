@@ -749,17 +749,27 @@ task_kernel(const LevelDev* __restrict__ levs, const Segment* __restrict__ segs,
     const unsigned epoch = (unsigned)ctl[CTL_EPOCH];
     const int total = ctl[CTL_TOTAL], nseg = ctl[CTL_NSEG], nchunk = ctl[CTL_NCHUNK];
     const bool audit = ctl[CTL_AUDIT] != 0;
-    const int tickets = total * iters;
+    const int cyc = total * iters;
+    const int tickets = cyc + (audit ? ctl[CTL_NAUD] : 0);
     if (lt == 0) s_task[g][0] = atomicAdd(&ctl[CTL_CLAIM], 1);
     group_bar(g);
     for (int par = 0;; par ^= 1) {
         const int t = s_task[g][par];
         if (t >= tickets) break;
-        const int it = t / total, tt = t - it * total;
-        const int ck = find_segment(prefix, nchunk, tt);
-        const int2 chunk = chunks[ck];
-        const Segment S = segs[chunk.x];
-        const int i = chunk.y + (tt - prefix[ck]);
+        int it, i;
+        Segment S;
+        if (t < cyc) {
+            it = t / total;
+            const int tt = t - it * total;
+            const int ck = find_segment(prefix, nchunk, tt);
+            const int2 chunk = chunks[ck];
+            S = segs[chunk.x];
+            i = chunk.y + (tt - prefix[ck]);
+        } else {  // an audited launch's reduction tasks (one list), after every iteration
+            it = 0;
+            S = segs[0];
+            i = total + (t - cyc);
+        }
         const Task T = S.tasks[i];
         const LevelDev& L = levs[T.lid + S.lid_base];
         const unsigned mark = 2u * (epoch + (unsigned)it);
@@ -820,18 +830,28 @@ task_kernel_half(const LevelDev* __restrict__ levs, const Segment* __restrict__ 
     const unsigned epoch = (unsigned)ctl[CTL_EPOCH];
     const int total = ctl[CTL_TOTAL], nseg = ctl[CTL_NSEG], nchunk = ctl[CTL_NCHUNK];
     const bool audit = ctl[CTL_AUDIT] != 0;
-    const int tickets = 2 * total * iters;
+    const int cyc = total * iters;
+    const int tickets = 2 * (cyc + (audit ? ctl[CTL_NAUD] : 0));
     for (;;) {
         int h = 0;
         if (lane == 0) h = atomicAdd(&ctl[CTL_CLAIM], 1);
         h = __shfl_sync(0xffffffffu, h, 0);
         if (h >= tickets) break;
         const int t = h >> 1, half = h & 1;
-        const int it = t / total, tt = t - it * total;
-        const int ck = find_segment(prefix, nchunk, tt);
-        const int2 chunk = chunks[ck];
-        const Segment S = segs[chunk.x];
-        const int i = chunk.y + (tt - prefix[ck]);
+        int it, i;
+        Segment S;
+        if (t < cyc) {
+            it = t / total;
+            const int tt = t - it * total;
+            const int ck = find_segment(prefix, nchunk, tt);
+            const int2 chunk = chunks[ck];
+            S = segs[chunk.x];
+            i = chunk.y + (tt - prefix[ck]);
+        } else {  // an audited launch's reduction tasks (one list), after every iteration
+            it = 0;
+            S = segs[0];
+            i = total + (t - cyc);
+        }
         const Task T = S.tasks[i];
         const LevelDev& L = levs[T.lid + S.lid_base];
         const unsigned mark = 2u * (epoch + (unsigned)it);

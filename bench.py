@@ -64,8 +64,8 @@ FP64_OPS_PER_LUP = 62
 # bytes moved); valid while the kernel source is the one captured
 # (TASK_SOURCE_SHA of csrc/vlbm_kernels.cu), else the line reports traffic
 # as null.
-TASK_DRAM_BYTES_PER_LUP = 190.1
-TASK_SOURCE_SHA = "644dc3f5a7083fbb"
+TASK_DRAM_BYTES_PER_LUP = 195.8
+TASK_SOURCE_SHA = "d24258b8ed4ef7f0"
 
 
 def kernel_source_sha():
@@ -356,7 +356,7 @@ def main():
     # launch shape: the project's autotuner on scratch hierarchies of the
     # same workload (regrid cycles), or a fixed schedule
     if args.schedule < 0:
-        tune, trials = autotune.tune_adaptive(make, every, cycles=6)
+        tune, trials = autotune.tune_adaptive(make, every, cycles=16, prepare=lambda g: g.set_regrid_audit(True))
     else:
         tune = {"variant": 1, "schedule": args.schedule, "max_ctas": 0, "graph_steps": every, "persist_after": 0}
         trials = {}

@@ -997,25 +997,27 @@ __global__ void gather_W_kernel(LevelDev L, double* __restrict__ W, long long ld
 // conservation audit: exact sums
 // ---------------------------------------------------------------------------
 
-// Exact per-CTA sums over the active cells of the listed tiles:
-// part[blk][0..23] = sum w W_k (k = 0..3), then sum w |W_k|, w = 4^-level,
-// as 192-bit fixed point (three words each).  A CTA takes one tile at a
-// time; its 64-thread group g adds up field k = g of the tile's cells, so a
-// thread holds two accumulators and many CTAs fit on an SM.  The last CTA to
-// finish writes the rounded totals out[0..7] (ticket: a zeroed counter,
-// left zeroed).
+// Exact per-CTA sums over the cells of the listed active tiles (a tile is
+// entirely active, entirely covered or entirely off its level, so every
+// cell of an active tile within the domain is active; the cell flags are
+// not read): part[blk][0..23] = sum w W_k (k = 0..3), then sum w |W_k|,
+// w = 4^-level, as 192-bit fixed point (three words each).  A CTA takes one
+// tile at a time; its 64-thread group g adds up field k = g of the tile's
+// cells, so a thread holds two accumulators and many CTAs fit on an SM.
+// The last CTA to finish writes the rounded totals out[0..7] (ticket: a
+// zeroed counter, left zeroed).
 
-// One thread's view of one tile: the flags and the four populations of its
-// (field, cell), loaded without waiting for them.
+// One thread's view of one tile: whether its cell lies in the domain, and
+// the four populations of its (field, cell), loaded without waiting for them.
 struct AuditCell {
-    uint32_t fl;
+    bool on;
     int lev;
     double f0, f1, f2, f3;
 };
 
 __device__ __forceinline__ AuditCell audit_load(const LevelDev* __restrict__ levs, const Item* __restrict__ items,
                                                 int it, int nitems, int k, int cx, int cy) {
-    AuditCell a{0u, 0, 0.0, 0.0, 0.0, 0.0};
+    AuditCell a{false, 0, 0.0, 0.0, 0.0, 0.0};
     if (it >= nitems) return a;
     const Item w = items[it];
     const LevelDev& L = levs[w.lid];
@@ -1023,10 +1025,8 @@ __device__ __forceinline__ AuditCell audit_load(const LevelDev* __restrict__ lev
     if (x >= L.nx || y >= L.ny) return a;
     const long long c = (long long)y * L.pitch + x;
     const double* st = L.buf[state_buf(L)];
-    a.fl = L.flags[c];
+    a.on = true;
     a.lev = L.level;
-    // every cell of the level's extent has storage: the populations load
-    // alongside the flags, and only active cells are added up
     a.f0 = __ldcs(st + qoff(0 + k, L.plane, c));
     a.f1 = __ldcs(st + qoff(4 + k, L.plane, c));
     a.f2 = __ldcs(st + qoff(8 + k, L.plane, c));
@@ -1068,7 +1068,7 @@ __global__ void __launch_bounds__(256) audit_kernel(const LevelDev* __restrict__
     AuditCell cur = audit_load(levs, items, blockIdx.x, nitems, k, cx, cy);
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const AuditCell nxt = audit_load(levs, items, it + gridDim.x, nitems, k, cx, cy);
-        if ((cur.fl & (F_IN | F_COV)) == F_IN) acc.add((cur.f0 + cur.f1) + (cur.f2 + cur.f3), -2 * cur.lev, sum, abs_sum);
+        if (cur.on) acc.add((cur.f0 + cur.f1) + (cur.f2 + cur.f3), -2 * cur.lev, sum, abs_sum);
         cur = nxt;
     }
     acc.flush(sum, abs_sum);
@@ -1108,11 +1108,32 @@ __global__ void __launch_bounds__(256) audit_kernel(const LevelDev* __restrict__
 
 // Totals of an audited persistent launch: out[m] = the correctly rounded sum
 // of quantity m over the *nblk reduction blocks' partials (24 words each);
-// then closes the launch's audit gate (*gate = 0).  One CTA of 256 threads.
-__global__ void __launch_bounds__(256) audit_blocks_kernel(const unsigned long long* __restrict__ part,
-                                                           const int* __restrict__ nblk, double* __restrict__ out,
-                                                           int* gate) {
-    audit_finish(part, *nblk, out);
+// then closes the launch's audit gate (*gate = 0).  One CTA of 1024
+// threads: warp w adds up quantity w % 8 over every fourth run of 32
+// blocks, and the four warps of a quantity are combined at the end.
+__global__ void __launch_bounds__(1024) audit_blocks_kernel(const unsigned long long* __restrict__ part,
+                                                            const int* __restrict__ nblk, double* __restrict__ out,
+                                                            int* gate) {
+    __shared__ Fix192 red[4][8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, m = w & 7, j = w >> 3;
+    const int nb = *nblk;
+    Fix192 a = fix_zero();
+    for (int i = j * 32 + lane; i < nb; i += 128) {
+        Fix192 v;
+        for (int q = 0; q < 3; q++) v.w[q] = part[(size_t)i * 24 + 3 * m + q];
+        fix_add(a, v);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const Fix192 b = fix_shfl_down(a, o);
+        fix_add(a, b);
+    }
+    if (lane == 0) red[j][m] = a;
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        Fix192 t = red[0][threadIdx.x];
+        for (int q = 1; q < 4; q++) fix_add(t, red[q][threadIdx.x]);
+        out[threadIdx.x] = fix_to_double(t);
+    }
     if (threadIdx.x == 0) *gate = 0;
 }
 
@@ -1648,7 +1669,7 @@ cudaError_t launch_tasks(const LevelDev* levs, const Segment* segs, const int* p
 
 cudaError_t launch_audit_blocks(const unsigned long long* part, const int* nblk, double* out, int* gate,
                                 cudaStream_t s) {
-    audit_blocks_kernel<<<1, 256, 0, s>>>(part, nblk, out, gate);
+    audit_blocks_kernel<<<1, 1024, 0, s>>>(part, nblk, out, gate);
     return cudaGetLastError();
 }
 

@@ -39,9 +39,9 @@ cudaError_t launch_feq_init(const LevelDev& L, const double* W, long long ld, do
 cudaError_t launch_copy_pop(const LevelDev& L, double* ext, long long ld, int to_ext, cudaStream_t s);
 cudaError_t launch_gather_W(const LevelDev& L, double* W, long long ld, uint8_t* valid, cudaStream_t s);
 int audit_blocks(int nitems);
-// Exact totals of the active cells of the listed tiles into out[0..7] in one
+// Exact totals of the cells of the listed active tiles into out[0..7] in one
 // launch (part: 24 words per CTA of audit_blocks(n); ticket: a zeroed word,
-// left zeroed).
+// left zeroed).  Reads the tiles' populations and the level table only.
 cudaError_t launch_audit(const LevelDev* levs, const Item* items, int n, unsigned long long* part, double* out,
                          unsigned* ticket, cudaStream_t s, const int* nc = nullptr);
 cudaError_t launch_avgdown(const LevelDev& C, const LevelDev& F, const Item* items, int n, cudaStream_t s,

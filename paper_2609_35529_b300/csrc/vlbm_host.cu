@@ -343,6 +343,9 @@ struct vlbm_hier {
     // before a device regrid runs on aux2, beside the regrid's first part
     // and the build.
     cudaStream_t aux = nullptr, aux2 = nullptr;
+    // the side branch of the captured regrid graph (tagging of levels >= 1)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaEvent_t ev_layout = nullptr, ev_built = nullptr;
     long long ev_layout_version = -1;
     vlbm_tuning tune{1, 0, 8, 1, 2};
@@ -1430,38 +1433,54 @@ void device_tags(vlbm_hier* h) {
     check_tagging(h);
     cudaStream_t s = h->stream;
     const int nl = h->nlev;
-    // composite state: the average of the children in every covered cell,
-    // finest level first
-    for (int l = nl - 2; l >= 0; l--) {
-        const LayoutDev& D = h->lev[l].dl;
-        VCK(launch_avgdown(lvdev(h, l), lvdev(h, l + 1), D.list[LST_COV], lcap(D), s, D.cnt + LST_COV));
-    }
     const bool fluxs = h->cfg.tag_sensor == VLBM_SENSOR_FLUX;
-    if (fluxs) {
-        h->qmax.ensure(h->mem, 4);
-        VCK(cudaMemsetAsync(h->qmax.p, 0, 4 * sizeof(unsigned long long), s));
-        for (int l = 0; l < nl; l++) {
-            const LayoutDev& D = h->lev[l].dl;
-            VCK(launch_qmax(lvdev(h, l), D.list[LST_IN], lcap(D), h->qmax.p, s, D.cnt + LST_IN));
-        }
-    }
     size_t nb = 0;
     for (int l = 0; l <= nl - 2; l++) nb += (size_t)h->lev[l].bx * h->lev[l].by;
     h->bflag.ensure(h->mem, std::max<size_t>(1, nb));
     VCK(cudaMemsetAsync(h->bflag.p, 0, nb, s));
     const double tol2 = h->cfg.tag_tol * h->cfg.tag_tol;
-    size_t off = 0;
+    size_t off[VLBM_MAX_LEVELS] = {};
+    for (int l = 1; l <= nl - 2; l++) off[l] = off[l - 1] + (size_t)h->lev[l - 1].bx * h->lev[l - 1].by;
+    auto tag = [&](int l, cudaStream_t st) {
+        const LayoutDev& D = h->lev[l].dl;
+        VCK(launch_tag(lvdev(h, l), BlockMaps{D.bin, D.bcov}, D.list[LST_IN], lcap(D), tol2, h->cfg.tag_buffer,
+                       h->bflag.p + off[l], st, D.cnt + LST_IN));
+    };
+    // composite state: the average of the children in every covered cell,
+    // finest level first.  With the density indicator a level l >= 1 is
+    // tagged on the side stream as soon as its composite state is complete,
+    // beside the averaging and tagging of the coarser levels (a fork and a
+    // join of the captured graph).
+    bool forked = false;
+    for (int l = nl - 2; l >= 0; l--) {
+        const LayoutDev& D = h->lev[l].dl;
+        VCK(launch_avgdown(lvdev(h, l), lvdev(h, l + 1), D.list[LST_COV], lcap(D), s, D.cnt + LST_COV));
+        if (!fluxs && l >= 1) {
+            VCK(cudaEventRecord(h->ev_fork, s));
+            VCK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+            tag(l, h->side);
+            forked = true;
+        }
+    }
+    if (!fluxs) {
+        tag(0, s);
+        if (forked) {
+            VCK(cudaEventRecord(h->ev_join, h->side));
+            VCK(cudaStreamWaitEvent(s, h->ev_join, 0));
+        }
+        return;
+    }
+    // the flux-jump indicator: the flux maxima over every level first
+    h->qmax.ensure(h->mem, 4);
+    VCK(cudaMemsetAsync(h->qmax.p, 0, 4 * sizeof(unsigned long long), s));
+    for (int l = 0; l < nl; l++) {
+        const LayoutDev& D = h->lev[l].dl;
+        VCK(launch_qmax(lvdev(h, l), D.list[LST_IN], lcap(D), h->qmax.p, s, D.cnt + LST_IN));
+    }
     for (int l = 0; l <= nl - 2; l++) {
-        Level& L = h->lev[l];
-        const LayoutDev& D = L.dl;
-        const BlockMaps M{D.bin, D.bcov};
-        if (fluxs)
-            VCK(launch_tag_flux(lvdev(h, l), M, D.list[LST_IN], lcap(D), h->qmax.p, h->cfg.tag_tol, h->cfg.tag_buffer,
-                                h->bflag.p + off, s, D.cnt + LST_IN));
-        else
-            VCK(launch_tag(lvdev(h, l), M, D.list[LST_IN], lcap(D), tol2, h->cfg.tag_buffer, h->bflag.p + off, s,
-                           D.cnt + LST_IN));
-        off += (size_t)L.bx * L.by;
+        const LayoutDev& D = h->lev[l].dl;
+        VCK(launch_tag_flux(lvdev(h, l), BlockMaps{D.bin, D.bcov}, D.list[LST_IN], lcap(D), h->qmax.p,
+                            h->cfg.tag_tol, h->cfg.tag_buffer, h->bflag.p + off[l], s, D.cnt + LST_IN));
     }
 }
 
@@ -1532,9 +1551,6 @@ void device_apply_flags(vlbm_hier* h, const uint8_t* bflag, int part = -1) {
     VCK(launch_concat_act(dls, nl, h->ditems, h->dcount, s));
 }
 
-// A tag-driven regrid on the device: indicator, block flags, new layout,
-// merge / split, flags and lists, replayed as one captured graph (every
-// size involved is decided on the device, so the graph stays valid).
 // The totals after the last regrid, when still to come, by a separate
 // audit of the current state (nothing has changed it since the regrid).
 void settle_after_audit(vlbm_hier* h) {
@@ -1547,6 +1563,9 @@ void settle_after_audit(vlbm_hier* h) {
     h->klaunch += 1;
 }
 
+// A tag-driven regrid on the device: indicator, block flags, new layout,
+// merge / split, flags and lists, replayed as two captured graphs (every
+// size involved is decided on the device, so the graphs stay valid).
 void device_regrid(vlbm_hier* h) {
     check_tagging(h);
     regrid_buffers(h);
@@ -1560,6 +1579,9 @@ void device_regrid(vlbm_hier* h) {
     cudaStream_t s = h->stream;
     if (!h->rg_exec[0] || !h->rg_exec[1] || key != h->rg_key) {
         const auto t0 = std::chrono::steady_clock::now();
+        if (!h->side) VCK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+        for (cudaEvent_t* ev : {&h->ev_fork, &h->ev_join})
+            if (!*ev) VCK(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
         for (int part = 0; part < 2; part++) {
             cudaGraphExec_t& ex = h->rg_exec[part];
             if (ex) cudaGraphExecDestroy(ex);
@@ -2226,14 +2248,14 @@ void destroy_levels(vlbm_hier* h) {
     h->rg_cap = 0;
     if (h->rg_ev) cudaEventDestroy(h->rg_ev);
     h->rg_ev = nullptr;
-    for (cudaStream_t* st : {&h->aux, &h->aux2}) {
+    for (cudaStream_t* st : {&h->aux, &h->aux2, &h->side}) {
         if (*st) {
             cudaStreamSynchronize(*st);
             cudaStreamDestroy(*st);
         }
         *st = nullptr;
     }
-    for (cudaEvent_t* ev : {&h->ev_layout, &h->ev_built, &h->ev_rg0, &h->ev_audit}) {
+    for (cudaEvent_t* ev : {&h->ev_layout, &h->ev_built, &h->ev_rg0, &h->ev_audit, &h->ev_fork, &h->ev_join}) {
         if (*ev) cudaEventDestroy(*ev);
         *ev = nullptr;
     }

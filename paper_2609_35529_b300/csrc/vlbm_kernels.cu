@@ -1258,10 +1258,34 @@ __device__ __forceinline__ void stage_window(const LevelDev& L, const uint8_t* _
     }
 }
 
+// Binary exponent of |x| from its bits (biased: 0 for zero and subnormals,
+// 2047 for infinities and NaN).
+__device__ __forceinline__ int bexp(double x) {
+    return (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FFull);
+}
+
+// Whether d1^2 + d2^2 > tol2 (2 rc)^2 is false by the exponents alone: with
+// |d| < 2^(Ed + 1) for the larger difference and tol2 >= 2^Et, rc >= 2^Ec,
+// the left side is below 2^(2 Ed + 3) and the right side at least
+// 2^(Et + 2 Ec + 2); when 2 Ed + 3 <= Et + 2 Ec + 1 the left side is below
+// half the right side, far outside the few ulps by which the rounded
+// products and sum can move either side, so the rounded comparison is false
+// too.  Only for moderate exponents (|Ed|, |Ec|, |Et| <= 200 unbiased, or a
+// zero or subnormal difference), where no product under- or overflows;
+// otherwise the full test decides.  et: the unbiased exponent of tol2, or a
+// value below -200 to disable.
+__device__ __forceinline__ bool tag_below_by_exponents(double d1, double d2, double rc, int et) {
+    const int ec = bexp(rc) - 1023, ed = max(bexp(d1), bexp(d2)) - 1023;
+    if (et < -200 || et > 200 || ec < -200 || ec > 200 || ed > 200) return false;
+    return 2 * ed + 3 <= et + 2 * ec + 1;
+}
+
 // Normalised density-gradient indicator: tag when
 // (rho_E - rho_W)^2 + (rho_N - rho_S)^2 > tol^2 (2 rho_C)^2; neighbours off
 // the level or beyond a non-periodic side take rho_C.  A tagged cell flags
 // the blocks within `buffer` cells of it in bflag (zeroed beforehand).
+// Cells whose differences are far below the threshold are settled by their
+// exponents (tag_below_by_exponents); the rest by the test as written.
 __global__ void __launch_bounds__(CTA_THREADS, 6)
 tag_kernel(LevelDev L, BlockMaps M, const Item* __restrict__ items, int nitems, double tol2, int buffer,
            uint8_t* __restrict__ bflag, const int* __restrict__ ncount) {
@@ -1269,6 +1293,8 @@ tag_kernel(LevelDev L, BlockMaps M, const Item* __restrict__ items, int nitems, 
     __shared__ uint8_t son[TILES_PER_CTA][WIN * WIN];
     if (ncount) nitems = *ncount;
     const int sub = threadIdx.x >> 6, lt = threadIdx.x & 63, cx = lt & 7, cy = lt >> 3;
+    // the exponent of tol2 for the shortcut (normal tol2 only)
+    const int et = (bexp(tol2) == 0 || bexp(tol2) == 2047 || !(tol2 > 0.0)) ? -1000 : bexp(tol2) - 1023;
     for (int it = blockIdx.x * TILES_PER_CTA + sub; it < nitems; it += gridDim.x * TILES_PER_CTA) {
         const Item w = items[it];
         group_bar(sub);  // the group's previous window is read
@@ -1283,6 +1309,7 @@ tag_kernel(LevelDev L, BlockMaps M, const Item* __restrict__ items, int nitems, 
         for (int d = 0; d < 4; d++) rn[d] = son[sub][nb[d]] ? sW[sub][0][nb[d]] : rc;
         const double d1 = rn[0] - rn[1];
         const double d2 = rn[2] - rn[3];
+        if (tag_below_by_exponents(d1, d2, rc, et)) continue;
         const double num = d1 * d1 + d2 * d2;
         const double t = 2.0 * rc;
         if (num > tol2 * (t * t)) flag_blocks_near(x, y, L.nx, L.ny, L.px, L.py, buffer, (L.nx + TILE - 1) / TILE, bflag);

@@ -298,7 +298,7 @@ __global__ void lists_scatter_kernel(LayoutSet S) {
         const long long b = (long long)c * LAY_CHUNK + threadIdx.x * LIST_E + e;
         if (b >= nb) break;
         const int ib = (int)(b % L.bx), jb = (int)(b / L.bx);
-        const Item it{lid, (unsigned short)ib, (unsigned short)jb};
+        const Item it{L.level, (unsigned short)ib, (unsigned short)jb};
         const uint8_t bits = m[e].bits & mask;
         for (int k = 0; k < NLST; k++)
             if (bits >> k & 1) L.list[k][off[k]++] = it;

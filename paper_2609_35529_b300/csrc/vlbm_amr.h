@@ -50,13 +50,13 @@ struct LayoutDev {
     int nchunk = 0;
 };
 
-// Up to four levels' layouts for one launch: chunk (CTA) and block offsets
-// of each level in the set.
+// Up to eight layouts for one launch (the levels, or also the new-map views
+// of the same levels): chunk (CTA) and block offsets of each in the set.
 struct LayoutSet {
-    LayoutDev L[4];
-    int mask[4];
-    int c0[5];
-    long long b0[5];
+    LayoutDev L[8];
+    int mask[8];
+    int c0[9];
+    long long b0[9];
     int nl;
 };
 
@@ -72,7 +72,9 @@ cudaError_t launch_derive_in(const LayoutDev* P, const LayoutDev& L, cudaStream_
 // of levels >= 1 with their four face neighbours on the level); a violation
 // sets ST_NESTING in *status.
 cudaError_t launch_nest_check(const LayoutDev* const* levs, int nl, int* status, cudaStream_t s);
-// Lists of each level l selected by masks[l] (bits 1 << LST_*): act, ring,
+// Lists of each layout l of levs[0 .. nl) (nl <= 8; a level may appear twice,
+// as its current maps and as a view of its new maps, with disjoint masks)
+// selected by masks[l] (bits 1 << LST_*): act, ring,
 // cov, in from the current maps (with recon, act_idx, ring_idx, cells and
 // the write masks), exit and enter from the current against the new maps,
 // touch (on the level under either, with the block or a face neighbour

@@ -1506,23 +1506,25 @@ void device_apply_flags(vlbm_hier* h, const uint8_t* bflag, int part = -1) {
         VCK(launch_derive_in(nullptr, *D[0], s));
         for (int l = 1; l < nl; l++) VCK(launch_derive_in(D[l - 1], *D[l], s));
         VCK(launch_nest_check(DL, nl, h->words + 1, s));
-        int masks[VLBM_MAX_LEVELS];
-        for (int l = 0; l < nl; l++) masks[l] = l <= nl - 2 ? LISTS_MOVE : (1 << LST_TOUCH);
-        VCK(launch_lists(DL, masks, nl, s));
-        // the tile lists and index maps of the new layout, from the new maps
-        // (the current ones are committed in the second part): everything a
-        // task-list build reads is final once this part is done
+        // in the same three launches: the exit / enter / touch lists from the
+        // current against the new maps, and the tile lists and index maps of
+        // the new layout from a view of the new maps (the current ones are
+        // committed in the second part): everything a task-list build reads
+        // is final once this part is done
+        int masks[2 * VLBM_MAX_LEVELS];
         LayoutDev NL[VLBM_MAX_LEVELS];
-        const LayoutDev* NP[VLBM_MAX_LEVELS];
+        const LayoutDev* SL[2 * VLBM_MAX_LEVELS];
         for (int l = 0; l < nl; l++) {
+            SL[l] = D[l];
+            masks[l] = l <= nl - 2 ? LISTS_MOVE : (1 << LST_TOUCH);
             NL[l] = *D[l];
             NL[l].bin = D[l]->nin;
             NL[l].bcov = D[l]->ncov;
             NL[l].nin = NL[l].ncov = nullptr;
-            NP[l] = &NL[l];
-            masks[l] = LISTS_ALL;
+            SL[nl + l] = &NL[l];
+            masks[nl + l] = LISTS_ALL;
         }
-        VCK(launch_lists(NP, masks, nl, s));
+        VCK(launch_lists(SL, masks, 2 * nl, s));
     }
     if (part == 0) return;
     for (int l = nl - 2; l >= 0; l--)

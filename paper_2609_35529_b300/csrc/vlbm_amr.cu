@@ -104,25 +104,32 @@ __global__ void layout_rule_kernel(LayoutDev L, LayoutDev F, int has_f, const ui
     }
 }
 
-__global__ void derive_in_kernel(LayoutDev P, LayoutDev L, int level0) {
-    const long long nb = (long long)L.bx * L.by;
-    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb; b += (long long)gridDim.x * blockDim.x) {
-        if (level0) {
-            L.nin[b] = 1;
-            continue;
-        }
-        const int ib = (int)(b % L.bx), jb = (int)(b / L.bx);
-        const long long pb = (long long)(jb >> 1) * P.bx + (ib >> 1);
-        L.nin[b] = (P.nin[pb] && P.ncov[pb]) ? 1 : 0;
-    }
-}
-
 // The level of flat block index b of a set and the block's index on it.
 __device__ __forceinline__ int set_level(const LayoutSet& S, long long& b) {
     int l = 0;
     while (l + 1 < S.nl && b >= S.b0[l + 1]) l++;
     b -= S.b0[l];
     return l;
+}
+
+// New on-level maps of every level of the set: level 0 holds every block; a
+// block of level l >= 1 is on it when its parent is on level l - 1 and
+// covered there, i.e. when every ancestor's block is covered in the new maps.
+__global__ void derive_in_kernel(LayoutSet S) {
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < S.b0[S.nl];
+         g += (long long)gridDim.x * blockDim.x) {
+        long long b = g;
+        const int l = set_level(S, b);
+        const LayoutDev& L = S.L[l];
+        int ib = (int)(b % L.bx), jb = (int)(b / L.bx);
+        bool in = true;
+        for (int q = l - 1; q >= 0 && in; q--) {
+            ib >>= 1;
+            jb >>= 1;
+            in = S.L[q].ncov[(long long)jb * S.L[q].bx + ib] != 0;
+        }
+        L.nin[b] = in ? 1 : 0;
+    }
 }
 
 __global__ void nest_check_kernel(LayoutSet S, int* status) {
@@ -1112,10 +1119,6 @@ cudaError_t launch_layout_rule(const LayoutDev& L, const LayoutDev* F, const uin
     return cudaGetLastError();
 }
 
-cudaError_t launch_derive_in(const LayoutDev* P, const LayoutDev& L, cudaStream_t s) {
-    derive_in_kernel<<<flat_blocks((long long)L.bx * L.by), 256, 0, s>>>(P ? *P : L, L, P == nullptr);
-    return cudaGetLastError();
-}
 
 LayoutSet layout_set(const LayoutDev* const* levs, const int* masks, int nl) {
     LayoutSet S{};
@@ -1127,6 +1130,12 @@ LayoutSet layout_set(const LayoutDev* const* levs, const int* masks, int nl) {
         S.b0[l + 1] = S.b0[l] + (long long)levs[l]->bx * levs[l]->by;
     }
     return S;
+}
+
+cudaError_t launch_derive_in(const LayoutDev* const* levs, int nl, cudaStream_t s) {
+    const LayoutSet S = layout_set(levs, nullptr, nl);
+    derive_in_kernel<<<flat_blocks(S.b0[nl]), 256, 0, s>>>(S);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_nest_check(const LayoutDev* const* levs, int nl, int* status, cudaStream_t s) {

@@ -65,8 +65,10 @@ struct LayoutSet {
 // level's new covered blocks (F: level l + 1 when it is refinable, else
 // nullptr).  The same rule as the host's layout_rule.
 cudaError_t launch_layout_rule(const LayoutDev& L, const LayoutDev* F, const uint8_t* bflag, cudaStream_t s);
-// New on-level map of L from its parent P's new maps (level 0: all blocks).
-cudaError_t launch_derive_in(const LayoutDev* P, const LayoutDev& L, cudaStream_t s);
+// New on-level maps of levels 0 .. nl - 1 from the new covered maps (level
+// 0: all blocks; level l: the blocks whose ancestors are all covered), in
+// one launch.
+cudaError_t launch_derive_in(const LayoutDev* const* levs, int nl, cudaStream_t s);
 // Proper nesting of the new maps of every level (covered blocks on the
 // level, none on the finest level -- the last of the set --, covered blocks
 // of levels >= 1 with their four face neighbours on the level); a violation

@@ -1503,8 +1503,7 @@ void device_apply_flags(vlbm_hier* h, const uint8_t* bflag, int part = -1) {
         VCK(cudaMemsetAsync(D[nl - 1]->ncov, 0, (size_t)lcap(*D[nl - 1]), s));
         for (int l = nl - 2; l >= 0; l--)
             VCK(launch_layout_rule(*D[l], l + 1 <= nl - 2 ? D[l + 1] : nullptr, bflag + off[l], s));
-        VCK(launch_derive_in(nullptr, *D[0], s));
-        for (int l = 1; l < nl; l++) VCK(launch_derive_in(D[l - 1], *D[l], s));
+        VCK(launch_derive_in(DL, nl, s));
         VCK(launch_nest_check(DL, nl, h->words + 1, s));
         // in the same three launches: the exit / enter / touch lists from the
         // current against the new maps, and the tile lists and index maps of

@@ -64,8 +64,8 @@ FP64_OPS_PER_LUP = 62
 # bytes moved); valid while the kernel source is the one captured
 # (TASK_SOURCE_SHA of csrc/vlbm_kernels.cu), else the line reports traffic
 # as null.
-TASK_DRAM_BYTES_PER_LUP = 195.7
-TASK_SOURCE_SHA = "a6d85f48bb35cd24"
+TASK_DRAM_BYTES_PER_LUP = 195.8
+TASK_SOURCE_SHA = "924ac9fe68b50a1c"
 
 
 def kernel_source_sha():

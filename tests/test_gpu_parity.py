@@ -259,19 +259,23 @@ def test_adaptive_shockbubble_small(V):
     assert info["active_cells"][1] > 0 and info["active_cells"][2] > 0
 
 
-@pytest.mark.parametrize("schedule,graph_steps,variant", [(1, 4, 1), (1, 1, 3), (0, 4, 1)])
-def test_regrid_audit_rows_equal_separate_audits(V, schedule, graph_steps, variant):
+@pytest.mark.parametrize("schedule,graph_steps,variant,sensor", [(1, 4, 1, False), (1, 1, 3, False), (0, 4, 1, False),
+                                                                 (1, 4, 2, True)])
+def test_regrid_audit_rows_equal_separate_audits(V, schedule, graph_steps, variant, sensor):
     """The exact totals recorded before and after each device regrid equal
     separate audits of the same states, however the totals after a regrid
     are taken: from the first sweeps of the next persistent launch (their
-    moments reduced by tasks of the same launch), or by a separate audit
-    (per-phase steps, a second regrid with no step between, or reading the
-    rows before the next step)."""
+    moments reduced by tasks of the same launch; also with the relaxation
+    sensor's passes in the list), or by a separate audit (per-phase steps, a
+    second regrid with no step between, or reading the rows before the next
+    step)."""
     cs = I.shockbubble(nx0=128, ny0=64, nlev=3)
     g = V.Hierarchy.from_case(cs)
     g.set_tuning(variant=variant, schedule=schedule, graph_steps=graph_steps, persist_after=0)
     for _ in range(2):
         g.regrid()
+    if sensor:
+        g.set_sensor(True, beta_min=0.5, c_sensor=16.0)
     g.set_regrid_audit(True)
     want = []
     for cycle in range(7):
@@ -294,6 +298,32 @@ def test_regrid_audit_rows_equal_separate_audits(V, schedule, graph_steps, varia
         assert np.array_equal(r[0:4], t0) and np.array_equal(r[4:8], a0)
         assert np.array_equal(r[8:12], t1) and np.array_equal(r[12:16], a1)
         assert drift(t0, t1, a0) < 1e-14
+
+
+def test_regrid_audit_row_settled_when_an_engine_admits_the_hierarchy(V):
+    """A hierarchy admitted to an engine right after a device regrid gets
+    that regrid's totals after from a separate audit at admission, equal to
+    an audit of the same state."""
+    cs = I.shockbubble(nx0=128, ny0=64, nlev=3)
+    g = V.Hierarchy.from_case(cs)
+    for _ in range(2):
+        g.regrid()
+    g.set_regrid_audit(True)
+    g.advance(4)
+    b = g.audit()
+    g.regrid()
+    a = g.audit()
+    e = V.Engine()
+    slot = e.admit(g, 4)
+    done = []
+    while not done:
+        done, _ = e.advance(4)
+    e.release(slot)
+    e.close()
+    rows = g.regrid_audits()
+    assert rows.shape == (1, 16)
+    assert np.array_equal(rows[0, 0:4], b[0]) and np.array_equal(rows[0, 4:8], b[1])
+    assert np.array_equal(rows[0, 8:12], a[0]) and np.array_equal(rows[0, 12:16], a[1])
 
 
 def test_adaptive_shockbubble_flux_jump_sensor(V):

@@ -870,32 +870,35 @@ __device__ __forceinline__ void warp_sort64(int& a, int& b, int lane) {
     warp_merge32(b, lane);
 }
 
-// Two tasks per warp: each half-warp walks one task's accesses in parallel
-// and appends what it finds (duplicates included) to the task's shared
-// buffer; then the whole warp sorts each task's entries and keeps the
+// Four tasks per warp: each quarter-warp walks one task's accesses in
+// parallel (a sweep has six, a close ten, so eight lanes per task keep the
+// warp busy) and appends what it finds (duplicates included) to the task's
+// shared buffer; then the whole warp sorts each task's entries and keeps the
 // distinct ones, ascending, in the task's fixed TB_SMALL slot of the
 // dependency array (deps[t * TB_SMALL ..]), or in the overflow area after
 // the slots when there are more.  A task whose raw entries exceed its
 // buffer is left to the fallback pass.
 constexpr int TBW_WARPS = 4;
-constexpr int TBW_RAW = 384;  // raw entries per task
+constexpr int TBW_TASKS = 4;   // tasks per warp
+constexpr int TBW_LANES = 32 / TBW_TASKS;
+constexpr int TBW_RAW = 256;   // raw entries per task
 
 __global__ void __launch_bounds__(TBW_WARPS * 32) tb_warp_kernel(TBPlan P) {
-    __shared__ int raw[TBW_WARPS][2][TBW_RAW];
+    __shared__ int raw[TBW_WARPS][TBW_TASKS][TBW_RAW];
     __shared__ unsigned char keep[TBW_WARPS][TBW_RAW];
-    __shared__ int nraw[TBW_WARPS][2];
+    __shared__ int nraw[TBW_WARPS][TBW_TASKS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int half = lane >> 4, hl = lane & 15;
+    const int half = lane / TBW_LANES, hl = lane % TBW_LANES;
     const int total = P.off[P.nphase];
     if (total > P.task_cap) return;
     const TB tb = tb_global(P);
     unsigned char* K = keep[w];
     const long long base = (long long)P.task_cap * TB_SMALL;
-    for (int tp = 2 * (blockIdx.x * TBW_WARPS + w); tp < total; tp += 2 * gridDim.x * TBW_WARPS) {
-        // the walks: half h on task tp + h
+    for (int tp = TBW_TASKS * (blockIdx.x * TBW_WARPS + w); tp < total; tp += TBW_TASKS * gridDim.x * TBW_WARPS) {
+        // the walks: lane group h on task tp + h
         {
             const int t = tp + half;
-            __syncwarp();  // the previous pair's buffers are read
+            __syncwarp();  // the previous tasks' buffers are read
             if (hl == 0) nraw[w][half] = 0;
             __syncwarp();
             const int pw = t < total ? tb.phase_of(t) : 0;
@@ -911,7 +914,7 @@ __global__ void __launch_bounds__(TBW_WARPS * 32) tb_warp_kernel(TBPlan P) {
                 const int nq = tb.num_queries(ph, nk);
                 int* R = raw[w][half];
                 int* cnt = &nraw[w][half];
-                for (int q = hl; q < nq; q += 16) {
+                for (int q = hl; q < nq; q += TBW_LANES) {
                     bool wr;
                     int ql, qk, qx, qy;
                     if (!tb.query(ph, it, keys, nk, q, wr, ql, qk, qx, qy)) continue;
@@ -923,7 +926,7 @@ __global__ void __launch_bounds__(TBW_WARPS * 32) tb_warp_kernel(TBPlan P) {
             }
             __syncwarp();
         }
-        for (int u = 0; u < 2; u++) {
+        for (int u = 0; u < TBW_TASKS; u++) {
             const int t = tp + u;
             if (t >= total) break;
             const int pt = tb.phase_of(t);
@@ -1204,7 +1207,7 @@ cudaError_t launch_task_build(const TBPlan& P, cudaStream_t s) {
         attrs = true;
     }
     tb_offsets_kernel<<<1, 1, 0, s>>>(P);
-    const long long gl = ((long long)P.task_cap + 2 * TBW_WARPS - 1) / (2 * TBW_WARPS);
+    const long long gl = ((long long)P.task_cap + TBW_TASKS * TBW_WARPS - 1) / (TBW_TASKS * TBW_WARPS);
     const int g = (int)(gl < 1 ? 1 : (gl > 148 * 12 ? 148 * 12 : gl));
     tb_warp_kernel<<<g, TBW_WARPS * 32, 0, s>>>(P);
     tb_big_kernel<<<148, TB_BUILD_THREADS, 0, s>>>(P);

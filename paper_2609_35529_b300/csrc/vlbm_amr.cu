@@ -751,28 +751,38 @@ __device__ __forceinline__ int tb_aslot(const TBPlan& P, const TBPhase& ph, int 
     return (P.audit && ph.kind == 0 && ph.first && ph.l < P.nlev) ? tb_slot_base(P, ph.l) + i : -1;
 }
 
+// Phase offsets by a scan over the phases in rounds of the CTA's threads
+// (one CTA), and the build's counters reset.
 __global__ void tb_offsets_kernel(TBPlan P) {
-    if (threadIdx.x || blockIdx.x) return;
+    __shared__ int sm[32];
     const int slots = P.audit ? tb_slot_base(P, P.nlev) : 0;
     const int nblk = (slots + TB_AUDIT_BLOCK - 1) / TB_AUDIT_BLOCK;
-    int o = 0;
-    for (int p = 0; p < P.nphase; p++) {
-        P.off[p] = o;
-        const TBPhase ph = P.ph[p];
+    int carry = 0;
+    for (int r = 0; r < P.nphase; r += blockDim.x) {
+        const int p = r + threadIdx.x;
         int c = 0;
-        if (ph.kind == 0 || ph.kind >= 3) c = ph.l < P.nlev ? P.lev[ph.l].cnt[LST_ACT] : 0;
-        else if (ph.kind == 1) c = ph.l + 1 < P.nlev ? P.lev[ph.l].cnt[LST_RING] : 0;
-        else c = 4 * nblk;
-        o += c;
+        if (p < P.nphase) {
+            const TBPhase ph = P.ph[p];
+            if (ph.kind == 0 || ph.kind >= 3) c = ph.l < P.nlev ? P.lev[ph.l].cnt[LST_ACT] : 0;
+            else if (ph.kind == 1) c = ph.l + 1 < P.nlev ? P.lev[ph.l].cnt[LST_RING] : 0;
+            else c = 4 * nblk;
+        }
+        int tot;
+        const int x = cta_excl(c, sm, &tot);
+        if (p < P.nphase) P.off[p] = carry + x;
+        carry += tot;
     }
-    P.off[P.nphase] = o;
-    P.need[0] = o;
-    P.need[1] = 0;
-    P.need[2] = 0;
-    P.need[3] = 0;
-    P.need[4] = 0;
-    P.need[5] = slots;
-    P.need[6] = nblk;
+    if (threadIdx.x == 0) {
+        P.off[P.nphase] = carry;
+        P.need[0] = carry;
+        P.need[1] = 0;
+        P.need[2] = 0;
+        P.need[3] = 0;
+        P.need[4] = 0;
+        P.need[5] = slots;
+        P.need[6] = nblk;
+        P.need[7] = 0;  // tb_big_kernel's finishing ticket
+    }
 }
 
 // Reduction task t (phase p, kind 2) by one warp: block b = i / 4, field
@@ -1021,36 +1031,10 @@ __global__ void __launch_bounds__(TBW_WARPS * 32) tb_warp_kernel(TBPlan P) {
     }
 }
 
-// Fallback pass: the tasks whose raw entries overflowed the warp buffer,
-// one thread each with a local-memory set of up to TB_MAXDEP distinct
-// dependencies, into the overflow area.
-__global__ void __launch_bounds__(TB_BUILD_THREADS) tb_big_kernel(TBPlan P) {
-    const int nbig = P.need[2];
-    if (nbig == 0) return;
-    const TB tb = tb_global(P);
-    int buf[TB_MAXDEP];
-    DepSet S{buf, 1, TB_MAXDEP, 0, false};
-    const long long base = (long long)P.task_cap * TB_SMALL;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nbig; i += gridDim.x * blockDim.x) {
-        const int t = P.big[i];
-        const int p = tb.phase_of(t);
-        Item it;
-        tb.deps(p, t, S, it);
-        const long long at = base + atomicAdd(P.need + 1, S.n);
-        if (S.ovf || at + S.n > P.dep_cap) {
-            atomicOr(P.need + 3, 1);
-            continue;
-        }
-        if (S.n > TB_SMALL) atomicAdd(P.need + 4, 1);
-        tb_write(P, tb, p, t, it, S, at);
-    }
-}
-
 // The launch's counts: the list's tasks up to the audit phase (run once per
 // iteration) and the audit phase's reduction tasks after them (run once, by
 // an audited launch).
-__global__ void tb_finish_kernel(TBPlan P) {
-    if (threadIdx.x || blockIdx.x) return;
+__device__ void tb_finish(const TBPlan& P) {
     const bool ap = P.nphase > 0 && P.ph[P.nphase - 1].kind == 2;
     int total = ap ? P.off[P.nphase - 1] : P.off[P.nphase];
     int naud = P.off[P.nphase] - total;
@@ -1063,6 +1047,44 @@ __global__ void tb_finish_kernel(TBPlan P) {
     P.prefix[1] = total;
     P.ctl[CTL_TOTAL] = total;
     P.ctl[CTL_NAUD] = naud;
+}
+
+// Fallback pass: the tasks whose raw entries overflowed the warp buffer,
+// one thread each with a local-memory set of up to TB_MAXDEP distinct
+// dependencies, into the overflow area; the last CTA to finish writes the
+// launch's counts (tb_finish).
+__global__ void __launch_bounds__(TB_BUILD_THREADS) tb_big_kernel(TBPlan P) {
+    const int nbig = P.need[2];
+    if (nbig > 0) {
+        const TB tb = tb_global(P);
+        int buf[TB_MAXDEP];
+        DepSet S{buf, 1, TB_MAXDEP, 0, false};
+        const long long base = (long long)P.task_cap * TB_SMALL;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nbig; i += gridDim.x * blockDim.x) {
+            const int t = P.big[i];
+            const int p = tb.phase_of(t);
+            Item it;
+            tb.deps(p, t, S, it);
+            const long long at = base + atomicAdd(P.need + 1, S.n);
+            if (S.ovf || at + S.n > P.dep_cap) {
+                atomicOr(P.need + 3, 1);
+                continue;
+            }
+            if (S.n > TB_SMALL) atomicAdd(P.need + 4, 1);
+            tb_write(P, tb, p, t, it, S, at);
+        }
+    }
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(P.need + 7, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        tb_finish(P);
+    }
 }
 
 // The chunk table of a persistent launch over several one-step task lists
@@ -1206,12 +1228,11 @@ cudaError_t launch_task_build(const TBPlan& P, cudaStream_t s) {
         cudaFuncSetAttribute(tb_big_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
         attrs = true;
     }
-    tb_offsets_kernel<<<1, 1, 0, s>>>(P);
+    tb_offsets_kernel<<<1, 256, 0, s>>>(P);
     const long long gl = ((long long)P.task_cap + TBW_TASKS * TBW_WARPS - 1) / (TBW_TASKS * TBW_WARPS);
     const int g = (int)(gl < 1 ? 1 : (gl > 148 * 12 ? 148 * 12 : gl));
     tb_warp_kernel<<<g, TBW_WARPS * 32, 0, s>>>(P);
     tb_big_kernel<<<148, TB_BUILD_THREADS, 0, s>>>(P);
-    tb_finish_kernel<<<1, 1, 0, s>>>(P);
     return cudaGetLastError();
 }
 

@@ -158,9 +158,9 @@ struct TBPlan {
     unsigned* done = nullptr;          // completion marks (left as they are)
     int task_cap = 0;
     long long dep_cap = 0;
-    int* need = nullptr;               // [7]: tasks of the last build, overflow area used, tasks of the
+    int* need = nullptr;               // [8]: tasks of the last build, overflow area used, tasks of the
                                        // fallback pass, overflow flag, tasks in the overflow area, audit
-                                       // slots, audit blocks
+                                       // slots, audit blocks, the fallback pass's finishing ticket
     // Audited cyclic list: the first sweep of each level in the step gives
     // each of its tiles an audit slot (levels in order, each in act-list
     // order), and the audit phase holds four reduction tasks (one per field)
@@ -182,10 +182,10 @@ struct TBPlan {
     int* ctl = nullptr;                // CTL_WORDS
 };
 // Builds the task list of the plan's phase sequence on the current lists:
-// phase offsets, then every task with its sorted dependencies (a warp per
-// task; a one-thread fallback pass for tasks whose raw dependency entries
-// overflow the warp's buffer); writes the
-// launch's task count into seg, prefix and ctl.  When the overflow area is
+// phase offsets, then every task with its sorted dependencies (four tasks
+// per warp; a one-thread fallback pass for tasks whose raw dependency
+// entries overflow the warp's buffer, whose last CTA writes the launch's
+// task count into seg, prefix and ctl).  When the overflow area is
 // exhausted the list is left empty (the launch does nothing) and
 // ST_TASKCAP is set in *status.
 cudaError_t launch_task_build(const TBPlan& P, cudaStream_t s);

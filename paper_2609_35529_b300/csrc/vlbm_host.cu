@@ -1887,7 +1887,7 @@ vlbm_hier::DevPlan& dev_plan(vlbm_hier* h, int k, bool cyclic) {
             VCK(cudaEventRecord(h->ev_built, bs));
             VCK(cudaStreamWaitEvent(s, h->ev_built, 0));
         }
-        D.build_kernels += 4;
+        D.build_kernels += 3;  // offsets, the warp pass, the fallback pass
         D.version = h->layout_version;
         h->times[VLBM_T_TASKS] += ms_since(t0);
         h->times[VLBM_T_NTASKLISTS] += 1;

@@ -325,34 +325,6 @@ __global__ void lists_scatter_kernel(LayoutSet S) {
     }
 }
 
-// bit 0: some sweep of the level pushes into the block (an active block
-// among the block and its four face neighbours, by the push targets of the
-// task builder); bit 1: a reflux close writes it (a ring block).  For the
-// levels whose lists included the active one.
-__global__ void wmask_kernel(LayoutSet S) {
-    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < S.b0[S.nl];
-         g += (long long)gridDim.x * blockDim.x) {
-        long long b = g;
-        const int l = set_level(S, b);
-        if (!((S.mask[l] >> LST_ACT) & 1)) continue;
-        const LayoutDev& L = S.L[l];
-        const int tx = (int)(b % L.bx), ty = (int)(b / L.bx);
-        const int sdi[5] = {0, 1, -1, 0, 0}, sdj[5] = {0, 0, 0, 1, -1};
-        uint8_t m = 0;
-        for (int d = 0; d < 5 && !m; d++) {
-            bool ok = true;
-            const int sx = wrap_or(tx - sdi[d], L.bx, L.px, ok), sy = wrap_or(ty - sdj[d], L.by, L.py, ok);
-            if (!ok) continue;
-            bool ok2 = true;
-            const int rx = wrap_or(sx + sdi[d], L.bx, L.px, ok2), ry = wrap_or(sy + sdj[d], L.by, L.py, ok2);
-            if (!ok2 || rx != tx || ry != ty) continue;
-            if (L.act_idx[(long long)sy * L.bx + sx] >= 0) m = 1;
-        }
-        if (L.ring_idx[b] >= 0) m |= 2;
-        L.wm[b] = m;
-    }
-}
-
 // parent tiles under the reconstruction footprint of child tile (tx, ty):
 // the parent cells 4 t - 1 .. 4 t + 4 on each axis, wrapped or dropped
 __device__ int foot_keys(const LayoutDev& P, int tx, int ty, int* keys) {
@@ -568,11 +540,23 @@ struct TB {
         }
     }
 
-    // bit 0: some sweep of level l pushes into the tile; bit 1: a close writes it
+    // bit 0: some sweep of level l pushes into the tile (an active tile among
+    // it and its four face neighbours, by the push targets); bit 1: a close
+    // writes it (a ring tile of a refinable level)
     __device__ int wmask(int l, int tx, int ty) const {
         const TBLevel& V = P.lev[l];
-        const int m = V.wm[ty * V.bx + tx];
-        return (l + 1 < P.nlev) ? m : (m & 1);
+        int m = 0;
+        for (int d = 0; d < 5 && !m; d++) {
+            bool ok = true;
+            const int sx = wrap_or(tx - kSDI[d], V.bx, V.px, ok), sy = wrap_or(ty - kSDJ[d], V.by, V.py, ok);
+            if (!ok) continue;
+            bool ok2 = true;
+            const int rx = wrap_or(sx + kSDI[d], V.bx, V.px, ok2), ry = wrap_or(sy + kSDJ[d], V.by, V.py, ok2);
+            if (!ok2 || rx != tx || ry != ty) continue;
+            if (V.act_idx[sy * V.bx + sx] >= 0) m = 1;
+        }
+        if (l + 1 < P.nlev && V.ring_idx[ty * V.bx + tx] >= 0) m |= 2;
+        return m;
     }
 
     // The tasks that the access (write or read, level l, resource kind, tile
@@ -1181,9 +1165,6 @@ cudaError_t launch_lists(const LayoutDev* const* levs, const int* masks, int nl,
     lists_count_kernel<<<S.c0[nl], LIST_T, 0, s>>>(S);
     lists_scan_kernel<<<NLST * nl, 1024, 0, s>>>(S);
     lists_scatter_kernel<<<S.c0[nl], LIST_T, 0, s>>>(S);
-    bool act = false;
-    for (int l = 0; l < nl; l++) act = act || ((masks[l] >> LST_ACT) & 1);
-    if (act) wmask_kernel<<<flat_blocks(S.b0[nl]), 256, 0, s>>>(S);
     return cudaGetLastError();
 }
 

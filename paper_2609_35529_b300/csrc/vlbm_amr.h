@@ -37,7 +37,6 @@ struct LayoutDev {
     uint8_t *nin = nullptr, *ncov = nullptr;  // the layout being installed
     uint8_t* recon = nullptr;                 // active block with a face neighbour off the level
     int *act_idx = nullptr, *ring_idx = nullptr;  // block -> index in the act / ring list, or -1
-    uint8_t* wm = nullptr;                    // bit 0: a sweep pushes into the block; bit 1: ring block
     // refinable levels: per block, the indices in the next level's act list
     // of the reconstructing tiles whose footprint holds the block (at most
     // FOOT_CAP, fidx[b * FOOT_CAP + j], j < fcnt[b])
@@ -77,12 +76,11 @@ cudaError_t launch_nest_check(const LayoutDev* const* levs, int nl, int* status,
 // Lists of each layout l of levs[0 .. nl) (nl <= 8; a level may appear twice,
 // as its current maps and as a view of its new maps, with disjoint masks)
 // selected by masks[l] (bits 1 << LST_*): act, ring,
-// cov, in from the current maps (with recon, act_idx, ring_idx, cells and
-// the write masks), exit and enter from the current against the new maps,
-// touch (on the level under either, with the block or a face neighbour
-// changing its on-level or covered state: the blocks whose cell flags can
-// change).  Items carry the level index.  Every
-// level in the same three or four launches.
+// cov, in from the current maps (with recon, act_idx, ring_idx and cells),
+// exit and enter from the current against the new maps, touch (on the
+// level under either, with the block or a face neighbour changing its
+// on-level or covered state: the blocks whose cell flags can change).
+// Items carry the level index.  Every layout in the same three launches.
 cudaError_t launch_lists(const LayoutDev* const* levs, const int* masks, int nl, cudaStream_t s);
 // Copies the new maps over the current ones, every level.
 cudaError_t launch_commit_maps(const LayoutDev* const* levs, int nl, cudaStream_t s);
@@ -122,7 +120,6 @@ struct TBLevel {
     const int* act_idx;
     const int* ring_idx;
     const uint8_t* recon;
-    const uint8_t* wm;
     const int* fcnt;  // reverse footprints (refinable levels)
     const int* fidx;
     const int* cnt;  // [NLST]

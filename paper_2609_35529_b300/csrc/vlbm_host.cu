@@ -1235,7 +1235,6 @@ void alloc_layout(vlbm_hier* h, int l) {
     D.recon = (uint8_t*)h->mem.get(nb);
     D.act_idx = (int*)h->mem.get(nb * sizeof(int));
     D.ring_idx = (int*)h->mem.get(nb * sizeof(int));
-    D.wm = (uint8_t*)h->mem.get(nb);
     if (l + 1 < h->nlev) {
         D.fcnt = (int*)h->mem.get(nb * sizeof(int));
         D.fidx = (int*)h->mem.get(nb * FOOT_CAP * sizeof(int));
@@ -1245,7 +1244,7 @@ void alloc_layout(vlbm_hier* h, int l) {
     D.cnt = (int*)h->mem.get(NLST * sizeof(int));
     D.cells = (unsigned long long*)h->mem.get(sizeof(unsigned long long));
     D.chunk = (int*)h->mem.get((size_t)NLST * D.nchunk * sizeof(int));
-    for (uint8_t* m : {D.bin, D.bcov, D.nin, D.ncov, D.recon, D.wm}) VCK(cudaMemsetAsync(m, 0, nb, s));
+    for (uint8_t* m : {D.bin, D.bcov, D.nin, D.ncov, D.recon}) VCK(cudaMemsetAsync(m, 0, nb, s));
     VCK(cudaMemsetAsync(D.act_idx, 0xff, nb * sizeof(int), s));
     VCK(cudaMemsetAsync(D.ring_idx, 0xff, nb * sizeof(int), s));
     VCK(cudaMemsetAsync(D.cnt, 0, NLST * sizeof(int), s));
@@ -1257,7 +1256,7 @@ void free_layout(vlbm_hier* h, int l) {
     LayoutDev& D = L.dl;
     if (!D.bin) return;
     const size_t nb = (size_t)L.bx * L.by;
-    for (uint8_t* m : {D.bin, D.bcov, D.nin, D.ncov, D.recon, D.wm}) h->mem.put(m, nb);
+    for (uint8_t* m : {D.bin, D.bcov, D.nin, D.ncov, D.recon}) h->mem.put(m, nb);
     h->mem.put(D.act_idx, nb * sizeof(int));
     h->mem.put(D.ring_idx, nb * sizeof(int));
     if (D.fcnt) {
@@ -1526,6 +1525,21 @@ void device_apply_flags(vlbm_hier* h, const uint8_t* bflag, int part = -1) {
         VCK(launch_lists(SL, masks, 2 * nl, s));
     }
     if (part == 0) return;
+    // the new maps committed and the audit's tile list concatenated touch
+    // nothing that merge, split and the flags read or write: a parallel
+    // branch (the maps and lists of the new layout are final after part 0)
+    if (!h->side) VCK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    for (cudaEvent_t* ev : {&h->ev_fork, &h->ev_join})
+        if (!*ev) VCK(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+    VCK(cudaEventRecord(h->ev_fork, s));
+    VCK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+    VCK(launch_commit_maps(DL, nl, h->side));
+    {
+        LayoutDev dls[VLBM_MAX_LEVELS];
+        for (int l = 0; l < nl; l++) dls[l] = *D[l];
+        VCK(launch_concat_act(dls, nl, h->ditems, h->dcount, h->side));
+    }
+    VCK(cudaEventRecord(h->ev_join, h->side));
     for (int l = nl - 2; l >= 0; l--)
         VCK(launch_merge(lvdev(h, l), D[l]->list[LST_EXIT], lcap(*D[l]), s, D[l]->cnt + LST_EXIT));
     for (int l = 0; l <= nl - 2; l++)
@@ -1546,10 +1560,7 @@ void device_apply_flags(vlbm_hier* h, const uint8_t* bflag, int part = -1) {
         cap = std::max(cap, lcap(*D[l]));
     }
     VCK(launch_flags_update(F, cap, s));
-    VCK(launch_commit_maps(DL, nl, s));
-    LayoutDev dls[VLBM_MAX_LEVELS];
-    for (int l = 0; l < nl; l++) dls[l] = *D[l];
-    VCK(launch_concat_act(dls, nl, h->ditems, h->dcount, s));
+    VCK(cudaStreamWaitEvent(s, h->ev_join, 0));
 }
 
 // The totals after the last regrid, when still to come, by a separate
@@ -1859,7 +1870,7 @@ vlbm_hier::DevPlan& dev_plan(vlbm_hier* h, int k, bool cyclic) {
         for (int l = 0; l < h->nlev; l++) {
             const LayoutDev& L = h->lev[l].dl;
             P.lev[l] = TBLevel{L.nx, L.ny, L.bx, L.by, L.px, L.py, L.list[LST_ACT], L.list[LST_RING],
-                               L.act_idx, L.ring_idx, L.recon, L.wm, L.fcnt, L.fidx, L.cnt};
+                               L.act_idx, L.ring_idx, L.recon, L.fcnt, L.fidx, L.cnt};
         }
         P.ph = D.ph.p;
         P.acc = D.acc.p;

@@ -343,10 +343,21 @@ __device__ int foot_keys(const LayoutDev& P, int tx, int ty, int* keys) {
     return ns;
 }
 
-__global__ void footprints_kernel(LayoutDev P, LayoutDev C, int* status) {
-    const int n = C.cnt[LST_ACT];
+// Reverse footprints of every refinable level of the set: for each
+// reconstructing tile i of level l >= 1 and each tile of level l - 1 under
+// its footprint, i joins that tile's entries (counts past FOOT_CAP are kept,
+// and the readers take at most FOOT_CAP of them).
+__global__ void footprints_kernel(LayoutSet S, int* status) {
+    int off[9];  // S.nl <= 8
+    off[0] = off[1] = 0;
+    for (int l = 1; l < S.nl; l++) off[l + 1] = off[l] + S.L[l].cnt[LST_ACT];
     bool ovf = false;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < off[S.nl]; g += gridDim.x * blockDim.x) {
+        int l = 1;
+        while (g >= off[l + 1]) l++;
+        const LayoutDev& C = S.L[l];
+        const LayoutDev& P = S.L[l - 1];
+        const int i = g - off[l];
         const Item it = C.list[LST_ACT][i];
         if (!C.recon[(long long)it.ty * C.bx + it.tx]) continue;
         int keys[16];
@@ -358,12 +369,6 @@ __global__ void footprints_kernel(LayoutDev P, LayoutDev C, int* status) {
         }
     }
     if (ovf) atomicOr(status, ST_TASKCAP);
-}
-
-__global__ void foot_clamp_kernel(LayoutDev P) {
-    const long long nb = (long long)P.bx * P.by;
-    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb; b += (long long)gridDim.x * blockDim.x)
-        if (P.fcnt[b] > FOOT_CAP) P.fcnt[b] = FOOT_CAP;
 }
 
 struct ActRef {
@@ -510,7 +515,7 @@ struct TB {
             case TB_FOOT: {  // reconstructing tiles of level l + 1 whose footprint holds (tx, ty)
                 const TBLevel& Pl = P.lev[l];
                 const int key = ty * Pl.bx + tx;
-                const int n = Pl.fcnt[key];
+                const int n = min(Pl.fcnt[key], FOOT_CAP);
                 for (int j = 0; j < n; j++) emit(base + Pl.fidx[key * FOOT_CAP + j]);
                 break;
             }
@@ -1168,11 +1173,15 @@ cudaError_t launch_lists(const LayoutDev* const* levs, const int* masks, int nl,
     return cudaGetLastError();
 }
 
-cudaError_t launch_footprints(const LayoutDev& P, const LayoutDev& C, int* status, cudaStream_t s) {
-    const long long nb = (long long)P.bx * P.by;
-    cudaMemsetAsync(P.fcnt, 0, nb * sizeof(int), s);
-    footprints_kernel<<<flat_blocks((long long)C.bx * C.by), 256, 0, s>>>(P, C, status);
-    foot_clamp_kernel<<<flat_blocks(nb), 256, 0, s>>>(P);
+cudaError_t launch_footprints(const LayoutDev* const* levs, int nl, int* status, cudaStream_t s) {
+    if (nl < 2) return cudaSuccess;
+    long long nc = 0;
+    for (int l = 0; l + 1 < nl; l++) {
+        cudaMemsetAsync(levs[l]->fcnt, 0, (size_t)levs[l]->bx * levs[l]->by * sizeof(int), s);
+        nc += (long long)levs[l + 1]->bx * levs[l + 1]->by;
+    }
+    const LayoutSet S = layout_set(levs, nullptr, nl);
+    footprints_kernel<<<flat_blocks(nc), 256, 0, s>>>(S, status);
     return cudaGetLastError();
 }
 

@@ -39,7 +39,7 @@ struct LayoutDev {
     int *act_idx = nullptr, *ring_idx = nullptr;  // block -> index in the act / ring list, or -1
     // refinable levels: per block, the indices in the next level's act list
     // of the reconstructing tiles whose footprint holds the block (at most
-    // FOOT_CAP, fidx[b * FOOT_CAP + j], j < fcnt[b])
+    // FOOT_CAP, fidx[b * FOOT_CAP + j], j < min(fcnt[b], FOOT_CAP))
     int* fcnt = nullptr;
     int* fidx = nullptr;
     Item* list[NLST] = {};
@@ -84,9 +84,11 @@ cudaError_t launch_nest_check(const LayoutDev* const* levs, int nl, int* status,
 cudaError_t launch_lists(const LayoutDev* const* levs, const int* masks, int nl, cudaStream_t s);
 // Copies the new maps over the current ones, every level.
 cudaError_t launch_commit_maps(const LayoutDev* const* levs, int nl, cudaStream_t s);
-// Reverse footprints of parent level P from the reconstructing tiles of its
-// child level C (after C's lists); an overflow of FOOT_CAP sets ST_TASKCAP.
-cudaError_t launch_footprints(const LayoutDev& P, const LayoutDev& C, int* status, cudaStream_t s);
+// Reverse footprints of every refinable level of levs[0 .. nl) from the
+// reconstructing tiles of the level below it (after the lists), in one
+// launch; an overflow of FOOT_CAP sets ST_TASKCAP (and readers take at most
+// FOOT_CAP entries).
+cudaError_t launch_footprints(const LayoutDev* const* levs, int nl, int* status, cudaStream_t s);
 // Concatenates the act lists of levels 0..n-1 into out (lid = level), with
 // the total in *n_out.
 cudaError_t launch_concat_act(const LayoutDev* levs, int n, Item* out, int* n_out, cudaStream_t s);

@@ -1857,10 +1857,11 @@ vlbm_hier::DevPlan& dev_plan(vlbm_hier* h, int k, bool cyclic) {
         }
         // the reverse footprints of the current layout (shared by both plans)
         if (h->foot_version != h->layout_version) {
-            for (int l = 0; l + 1 < h->nlev; l++)
-                VCK(launch_footprints(h->lev[l].dl, h->lev[l + 1].dl, h->words + 1, bs));
+            const LayoutDev* FL[VLBM_MAX_LEVELS];
+            for (int l = 0; l < h->nlev; l++) FL[l] = &h->lev[l].dl;
+            VCK(launch_footprints(FL, h->nlev, h->words + 1, bs));
             h->foot_version = h->layout_version;
-            D.build_kernels += 2 * (h->nlev - 1);
+            D.build_kernels += h->nlev > 1 ? 1 : 0;
         }
         TBPlan P;
         P.nlev = h->nlev;

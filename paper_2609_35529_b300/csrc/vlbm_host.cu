@@ -2288,12 +2288,13 @@ void destroy_levels(vlbm_hier* h) {
     }
 }
 
-// Schedule of the next steps: 2 (auto) takes the per-phase launches on a
-// layout younger than persist_after coarse steps -- an adaptive run that
-// regrids often never pays for a task list -- and the persistent task
-// kernel after that, or whenever per-step totals are on.
+// Schedule of the next steps on the host-built lists (per-step totals,
+// profiling): 2 (auto) takes the per-phase launches on a layout younger than
+// persist_after coarse steps -- an adaptive run that regrids often never
+// pays for a task list -- and the persistent task kernel after that, or
+// whenever per-step totals are on.
 int effective_schedule(const vlbm_hier* h) {
-    if (h->sensor_on) return 0;  // the sensor passes run between per-phase launches
+    if (h->sensor_on) return 0;  // host-built lists hold no sensor passes
     if (h->tune.schedule != 2) return h->tune.schedule;
     return (h->step_audit || h->layout_steps >= h->tune.persist_after) ? 1 : 0;
 }
